@@ -1,0 +1,465 @@
+"""Pins of the CPU oracle against what the paper and the mathematics fix.
+
+Each test checks the oracle against something other than itself: a value
+printed in the paper, a library routine (sympy / scipy), a closed form, an
+invariant, or brute force on tiny inputs.  None of these needs a GPU.
+"""
+import itertools
+import json
+import math
+import os
+import random
+
+import numpy as np
+import pytest
+import sympy
+from sympy.ntheory.modular import crt as sympy_crt
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+T = 65537
+
+
+def golden(name):
+    with open(os.path.join(GOLDEN, name)) as f:
+        return json.load(f)
+
+
+def brev(x, bits):
+    return int(format(x, "0%db" % bits)[::-1], 2) if bits else 0
+
+
+def negacyclic_schoolbook(a, b, N, mod=None):
+    out = [0] * N
+    for i in range(N):
+        for j in range(N):
+            p = a[i] * b[j]
+            if i + j >= N:
+                out[i + j - N] -= p
+            else:
+                out[i + j] += p
+    return [x % mod for x in out] if mod else out
+
+
+# ------------------------------------------------------------ primes, roots
+def test_miller_rabin_matches_sympy(oracle_mod):
+    rng = random.Random(1)
+    cands = [rng.getrandbits(64) | 1 for _ in range(300)] + [2, 3, 4, 65537, 2**61 - 1, 2**64 - 59, 3215031751]
+    for n in cands:
+        assert oracle_mod.is_prime(n) == sympy.isprime(n), n
+
+
+@pytest.mark.parametrize("bits,N", [(36, 4096), (37, 4096), (55, 8192), (54, 8192), (55, 16384), (20, 16)])
+def test_prime_search_is_largest(oracle_mod, bits, N):
+    q = oracle_mod.find_prime(bits, N)
+    assert q % (2 * N) == 1 and sympy.isprime(q) and q < 2**bits
+    # no prime = 1 mod 2N lies between q and 2^bits
+    for c in range(q + 2 * N, 2**bits, 2 * N):
+        assert not sympy.isprime(c)
+    q2 = oracle_mod.find_prime(bits, N, [q])
+    assert q2 < q and sympy.isprime(q2)
+    for c in range(q2 + 2 * N, q, 2 * N):
+        assert not sympy.isprime(c)
+
+
+def test_min_root_brute_force(oracle_mod):
+    for N in (4, 8, 16):
+        q = oracle_mod.find_prime(14, N)
+        roots = [w for w in range(1, q) if pow(w, N, q) == q - 1]
+        assert oracle_mod.min_root(q, N) == min(roots)
+    # t = 65537: the minimal primitive 2N-th root
+    for N in (16, 64):
+        r = oracle_mod.min_root(T, N)
+        assert pow(r, N, T) == T - 1
+        assert all(pow(w, N, T) != T - 1 for w in range(1, r))
+
+
+# ------------------------------------------------------------------ NTT
+@pytest.mark.parametrize("N", [2, 4, 8, 16, 32, 64])
+def test_ntt_matches_evaluation_definition(oracle_mod, N):
+    q = oracle_mod.find_prime(40, N)
+    psi = oracle_mod.min_root(q, N)
+    rng = random.Random(N)
+    a = [rng.randrange(q) for _ in range(N)]
+    lg = int(math.log2(N))
+    want = [sum(a[n] * pow(psi, (2 * brev(i, lg) + 1) * n, q) for n in range(N)) % q for i in range(N)]
+    assert [int(x) for x in oracle_mod.ntt_fwd(a, N, q, psi)] == want
+    assert [int(x) for x in oracle_mod.ntt_direct(a, N, q, psi)] == want
+    assert [int(x) for x in oracle_mod.ntt_inv(want, N, q, psi)] == a
+
+
+@pytest.mark.parametrize("N,bits", [(8, 55), (32, 61), (64, 36)])
+def test_ntt_product_is_negacyclic_convolution(oracle_mod, N, bits):
+    q = oracle_mod.find_prime(bits, N)
+    psi = oracle_mod.min_root(q, N)
+    rng = random.Random(bits)
+    a = [rng.randrange(q) for _ in range(N)]
+    b = [rng.randrange(q) for _ in range(N)]
+    A = oracle_mod.ntt_fwd(a, N, q, psi)
+    B = oracle_mod.ntt_fwd(b, N, q, psi)
+    prod = [int(x) * int(y) % q for x, y in zip(A, B)]
+    got = [int(x) for x in oracle_mod.ntt_inv(prod, N, q, psi)]
+    assert got == negacyclic_schoolbook(a, b, N, q)
+
+
+def test_crt_matches_sympy(oracle_mod):
+    rng = random.Random(5)
+    for k in (1, 3, 8, 16):
+        ps = []
+        for _ in range(k):
+            ps.append(oracle_mod.find_prime(61 if k > 8 else 55, 64, ps))
+        x = rng.randrange(math.prod(ps))
+        res = [x % p for p in ps]
+        assert oracle_mod.crt(res, ps) == int(sympy_crt(ps, res)[0]) == x
+
+
+# ------------------------------------------------------- batch encoding
+def test_encoding_is_evaluation_at_odd_powers(oracle_mod):
+    N = 32
+    c = oracle_mod.Ctx(N=N, t=T, prime_bits=[36], h=1, lambda_bar=4)
+    rng = random.Random(2)
+    m = [rng.randrange(T) for _ in range(N)]
+    slots = c.decode(np.array(m, np.uint32))
+    want = [sum(m[n] * pow(c.psi_t, (2 * s + 1) * n, T) for n in range(N)) % T for s in range(N)]
+    assert [int(x) for x in slots] == want
+    assert [int(x) for x in c.encode(slots)] == m
+
+
+def test_encoding_is_a_ring_homomorphism(oracle_mod):
+    N = 16
+    c = oracle_mod.Ctx(N=N, t=T, prime_bits=[36], h=1, lambda_bar=4)
+    rng = random.Random(3)
+    a = [rng.randrange(T) for _ in range(N)]
+    b = [rng.randrange(T) for _ in range(N)]
+    ab = negacyclic_schoolbook(a, b, N, T)
+    da, db, dab = (c.decode(np.array(x, np.uint32)) for x in (a, b, ab))
+    assert [int(x) for x in dab] == [int(x) * int(y) % T for x, y in zip(da, db)]
+    # a constant polynomial puts the constant in every slot
+    assert set(int(x) for x in c.decode(np.array([7] + [0] * (N - 1), np.uint32))) == {7}
+
+
+# ------------------------------------------------------------ the code
+def test_code_length_paper_value(oracle_mod):
+    for row in golden("paper_values.json")["code_length"]:
+        assert oracle_mod.code_length(row["lambda_bar"], row["h"]) == row["ell"]
+
+
+@pytest.mark.parametrize("lb,h", [(16, 2), (32, 4), (40, 8), (19, 8), (10, 1), (32, 2)])
+def test_code_length_is_minimal(oracle_mod, lb, h):
+    ell = oracle_mod.code_length(lb, h)
+    assert math.comb(ell, h) >= 2**lb > math.comb(ell - 1, h)
+
+
+@pytest.mark.parametrize("ell,h", [(6, 2), (8, 3), (10, 4), (9, 1), (12, 8)])
+def test_cw_encode_is_colex_unranking(oracle_mod, ell, h):
+    combos = sorted(itertools.combinations(range(ell), h), key=lambda c: tuple(reversed(c)))
+    assert len(combos) == math.comb(ell, h)
+    for v, combo in enumerate(combos):
+        pos = oracle_mod.cw_encode(v, ell, h)
+        assert tuple(pos) == combo
+        assert sum(math.comb(c, r + 1) for r, c in enumerate(pos)) == v
+    with pytest.raises(ValueError):
+        oracle_mod.cw_encode(len(combos), ell, h)
+
+
+# ----------------------------------------------------------- randomness
+def test_splitmix64_published_outputs(oracle_mod):
+    g = golden("splitmix64.json")["state0_outputs"]
+    gamma = 0x9E3779B97F4A7C15
+    for i, want in enumerate(g):
+        assert oracle_mod.mix64((i + 1) * gamma % 2**64) == int(want, 16)
+
+
+def test_samplers_distribution(oracle_mod):
+    st = oracle_mod.stream(1, 0, 0)
+    tern = [oracle_mod.sample_mod(9, st, i, 3) for i in range(30000)]
+    counts = np.bincount(tern, minlength=3) / len(tern)
+    assert np.all(np.abs(counts - 1 / 3) < 0.02)
+    cbd = np.array([oracle_mod.sample_cbd(9, st, i) for i in range(30000)])
+    assert cbd.min() >= -21 and cbd.max() <= 21
+    assert abs(cbd.mean()) < 0.1 and abs(cbd.var() - 10.5) < 0.5
+    q = 2**55 - 2**20 + 1
+    u = np.array([oracle_mod.sample_mod(9, st, i, q) for i in range(5000)], dtype=np.float64)
+    assert u.max() < q and abs(u.mean() / q - 0.5) < 0.02
+
+
+# ----------------------------------------------------------------- hashing
+def test_cuckoo_invariants(oracle_mod):
+    rng = np.random.default_rng(4)
+    items = np.unique(rng.integers(0, 2**32, 900, dtype=np.uint64))[:800]
+    rc, table, where = oracle_mod.cuckoo(77, 16, 10, items)
+    assert rc == 0
+    assert len(set(where.tolist())) == len(items)
+    for u, x in enumerate(items):
+        xl, bins = oracle_mod.hash_item(77, 16, 10, x)
+        assert where[u] in bins and table[where[u]] == xl
+    assert int((table != oracle_mod.DUMMY).sum()) == len(items)
+    # more items than bins cannot be placed: failure, not a hang
+    rc, _, _ = oracle_mod.cuckoo(77, 16, 4, np.arange(17, dtype=np.uint64))
+    assert rc == oracle_mod.E_CUCKOO_FAIL
+
+
+def test_simple_hash_invariants(oracle_mod):
+    rng = np.random.default_rng(5)
+    items = np.unique(rng.integers(0, 2**32, 3000, dtype=np.uint64))
+    rc, Ts, mx = oracle_mod.simple_hash(13, 12, 8, items, 64)
+    assert rc == 0 and mx <= 64
+    expect = [[] for _ in range(256)]
+    for x in items:
+        xl, bins = oracle_mod.hash_item(13, 12, 8, x)
+        for i, b in enumerate(bins):
+            if b in bins[:i] or xl in expect[b]:
+                continue
+            expect[b].append(xl)
+    for b in range(256):
+        col = [int(v) for v in Ts[:, b] if v != oracle_mod.DUMMY]
+        assert col == expect[b]
+        assert all(v == oracle_mod.DUMMY for v in Ts[len(col):, b])
+    rc, _, mx2 = oracle_mod.simple_hash(13, 12, 8, items, mx - 1)
+    assert rc == oracle_mod.E_BIN_OVERFLOW and mx2 == mx
+
+
+def test_pbh_same_bin_and_low_bits_means_same_image(oracle_mod):
+    # Section 3.3: bin = x_H xor H(x_L); equal x_L and equal bin under the
+    # same hash function force equal x_H.  Exhaust a small domain.
+    seen = {}
+    for x in range(20000):
+        xl, bins = oracle_mod.hash_item(3, 6, 4, x)
+        for i, b in enumerate(bins):
+            key = (i, b, xl)
+            h0 = (oracle_mod.mix64(x ^ oracle_mod.mix64(3 + 0x9E3779B97F4A7C15)) & (2**10 - 1))
+            assert seen.setdefault(key, h0) == h0
+
+
+def test_mu_values(oracle_mod):
+    for row in golden("paper_values.json")["mu"]:
+        assert oracle_mod.mu_bound(row["n"], row["b"]) == row["mu"]
+    from scipy.stats import binom
+
+    for n, b in [(1024, 4096), (1 << 16, 8192), (1 << 18, 8192)]:
+        mu = oracle_mod.mu_bound(n, b)
+        assert b * binom.sf(mu, 3 * n, 1 / b) <= 2**-40 < b * binom.sf(mu - 1, 3 * n, 1 / b)
+
+
+# ------------------------------------------------------------- BFV (FV)
+@pytest.fixture(scope="module")
+def tiny(oracle_mod):
+    c = oracle_mod.Ctx(N=16, t=T, prime_bits=[36, 36, 37], h=2, lambda_bar=6, hash_key=7, mu=4)
+    s, rlk = c.keygen(3)
+    return c, s, rlk
+
+
+def rand_slots(rng, N):
+    return rng.integers(0, T, N).astype(np.uint32)
+
+
+def test_encrypt_decrypt(tiny):
+    c, s, _ = tiny
+    rng = np.random.default_rng(0)
+    for seed in range(4):
+        a = rand_slots(rng, c.N)
+        sl, bud = c.decrypt(s, c.encrypt(s, c.encode(a), seed)[0])
+        assert (sl == a).all() and bud > 50
+
+
+def test_fresh_ciphertext_structure(tiny):
+    # c0 + c1*s = round(Q*m/t) + e with |e| <= 21 (centred binomial, eta=21)
+    c, s, _ = tiny
+    m = c.encode(np.arange(c.N, dtype=np.uint32))
+    ct = c.encrypt(s, m, 11)[0]
+    Q = c.Q
+    for n in range(c.N):
+        c0 = int(sympy_crt(c.q, [int(ct[0, p, n]) for p in range(c.k)])[0])
+        acc = c0
+        c1 = [int(sympy_crt(c.q, [int(ct[1, p, j]) for p in range(c.k)])[0]) for j in range(c.N)]
+        for j in range(c.N):  # (c1 * s)[n], negacyclic
+            i = n - j
+            sgn = 1
+            if i < 0:
+                i += c.N
+                sgn = -1
+            acc += sgn * c1[j] * int(s[i])
+        e = (acc - (Q * int(m[n]) + (T - 1) // 2) // T) % Q
+        e = e - Q if e > Q // 2 else e
+        assert abs(e) <= 21
+
+
+def test_plain_mult_add_scalar_const(tiny):
+    c, s, _ = tiny
+    rng = np.random.default_rng(1)
+    a, p = rand_slots(rng, c.N), rand_slots(rng, c.N)
+    ca = c.encrypt(s, c.encode(a), 1)[0]
+    sl, _ = c.decrypt(s, c.ct_mul_pt(ca, c.encode(p)))
+    assert (sl == (a.astype(np.int64) * p % T)).all()
+    sl, _ = c.decrypt(s, c.ct_axpy(ca, -3, ca))
+    assert (sl == (a.astype(np.int64) * -2 % T)).all()
+    sl, _ = c.decrypt(s, c.ct_add_const(ca, -1))
+    assert (sl == (a.astype(np.int64) - 1) % T).all()
+
+
+def decrypt3(c, s, ct3):
+    """Big-integer decryption of a 3-component ciphertext (d0 + d1 s + d2 s^2)."""
+    N, Q = c.N, c.Q
+    comps = [[int(sympy_crt(c.q, [int(ct3[comp, p, n]) for p in range(c.k)])[0]) for n in range(N)] for comp in range(3)]
+    sl = [int(x) for x in s]
+    s2 = negacyclic_schoolbook(sl, sl, N)
+    z = [comps[0][n] for n in range(N)]
+    t1 = negacyclic_schoolbook(comps[1], sl, N)
+    t2 = negacyclic_schoolbook(comps[2], s2, N)
+    z = [(z[n] + t1[n] + t2[n]) % Q for n in range(N)]
+    z = [x - Q if x > Q // 2 else x for x in z]
+    m = [((T * x + (Q - 1) // 2) // Q) % T for x in z]
+    return c.decode(np.array(m, np.uint32))
+
+
+def test_mult_decrypts_to_product_and_relin_preserves_it(tiny):
+    c, s, rlk = tiny
+    rng = np.random.default_rng(2)
+    a, b = rand_slots(rng, c.N), rand_slots(rng, c.N)
+    ca, cb = c.encrypt(s, c.encode(a), 1)[0], c.encrypt(s, c.encode(b), 2)[0]
+    m3 = c.ct_mult(ca, cb)
+    want = a.astype(np.int64) * b % T
+    assert (decrypt3(c, s, m3) == want).all()
+    r = c.relin(rlk, m3)
+    sl, bud = c.decrypt(s, r)
+    assert (sl == want).all() and bud > 0
+
+
+def test_mult_words_against_big_integer_schoolbook(oracle_mod):
+    # textbook FV: round(t/Q * (a~ (x) b~)) with centred lifts, exact integers
+    c = oracle_mod.Ctx(N=8, t=T, prime_bits=[36, 37], h=1, lambda_bar=3)
+    s, _ = c.keygen(5)
+    rng = np.random.default_rng(6)
+    ca = c.encrypt(s, c.encode(rand_slots(rng, 8)), 1)[0]
+    cb = c.encrypt(s, c.encode(rand_slots(rng, 8)), 2)[0]
+    Q, N = c.Q, c.N
+
+    def lift(ct, comp):
+        v = [int(sympy_crt(c.q, [int(ct[comp, p, n]) for p in range(c.k)])[0]) for n in range(N)]
+        return [x - Q if x > Q // 2 else x for x in v]
+
+    a0, a1, b0, b1 = lift(ca, 0), lift(ca, 1), lift(cb, 0), lift(cb, 1)
+    x0 = negacyclic_schoolbook(a0, b0, N)
+    x1 = [u + v for u, v in zip(negacyclic_schoolbook(a0, b1, N), negacyclic_schoolbook(a1, b0, N))]
+    x2 = negacyclic_schoolbook(a1, b1, N)
+    got = c.ct_mult(ca, cb)
+    for comp, x in enumerate((x0, x1, x2)):
+        for n in range(N):
+            y = (T * x[n] + (Q - 1) // 2) // Q  # floor; Q odd -> round
+            for p, q in enumerate(c.q):
+                assert int(got[comp, p, n]) == y % q
+
+
+def test_relin_key_structure(tiny):
+    # rlk_i[0] + a_i s = e_i + g_i s^2 with g_i = 1 mod q_i, 0 mod q_j (j != i)
+    c, s, rlk = tiny
+    sl = [int(x) for x in s]
+    s2 = negacyclic_schoolbook(sl, sl, c.N)
+    for i in range(c.k):
+        for j, q in enumerate(c.q):
+            a = [int(x) for x in rlk[i, 1, j]]
+            As = negacyclic_schoolbook(a, sl, c.N, q)
+            for n in range(c.N):
+                e = (int(rlk[i, 0, j, n]) + As[n] - (s2[n] if i == j else 0)) % q
+                e = e - q if e > q // 2 else e
+                assert abs(e) <= 21
+
+
+def test_noise_budget_is_exact_threshold(tiny):
+    # budget > 0 exactly when every coefficient's error is below Q/(2t)
+    c, s, _ = tiny
+    m = c.encode(np.zeros(c.N, np.uint32))
+    ct = c.encrypt(s, m, 3)[0]
+    _, b0 = c.decrypt(s, ct)
+    ct2 = ct.copy()
+    # add a large known error e* to c0[0]: |t*e*| close to Q/2 makes the budget ~0
+    big = c.Q // (2 * T) - 10**6
+    for p, q in enumerate(c.q):
+        ct2[0, p, 0] = (int(ct2[0, p, 0]) + big) % q
+    _, b1 = c.decrypt(s, ct2)
+    assert b0 > b1 > -1 and b1 < 1
+
+
+# --------------------------------------------------------------- PEPSI
+def eq_truth_table_case(oracle_mod, h, lb, ell, N, bits, n_pairs, seed):
+    c = oracle_mod.Ctx(N=N, t=T, prime_bits=bits, h=h, ell=ell, lambda_bar=lb, mu=1)
+    s, rlk = c.keygen(seed)
+    rng = np.random.default_rng(seed)
+    total = math.comb(ell, h)
+    pairs = [(x, x) for x in range(min(total, n_pairs // 2))]
+    while len(pairs) < n_pairs:
+        pairs.append((int(rng.integers(total)), int(rng.integers(total))))
+    for off in range(0, len(pairs), N):
+        chunk = pairs[off:off + N]
+        cl = np.full(N, oracle_mod.DUMMY, np.uint64)
+        sv = np.full((1, N), oracle_mod.DUMMY, np.uint64)
+        for i, (x, y) in enumerate(chunk):
+            cl[i], sv[0, i] = x, y
+        cts = c.encrypt(s, c.query_plaintexts(cl), seed + off)
+        out = c.eval(rlk, cts, sv)
+        slots, bud = c.decrypt(s, out)
+        assert bud > 0
+        for i, (x, y) in enumerate(chunk):
+            assert int(slots[i]) == int(x == y), (h, x, y)
+        assert (slots[len(chunk):] == 0).all()  # dummy vs dummy is 0
+
+
+def test_arith_cw_eq_exhaustive_h2(oracle_mod):
+    # all 15 x 15 pairs of CW(6, 2)
+    c = oracle_mod.Ctx(N=64, t=T, prime_bits=[36, 36, 37], h=2, ell=6, lambda_bar=3, mu=1)
+    s, rlk = c.keygen(1)
+    words = list(range(15))
+    pairs = [(x, y) for x in words for y in words]
+    for off in range(0, len(pairs), 64):
+        chunk = pairs[off:off + 64]
+        cl = np.full(64, oracle_mod.DUMMY, np.uint64)
+        sv = np.full((1, 64), oracle_mod.DUMMY, np.uint64)
+        for i, (x, y) in enumerate(chunk):
+            cl[i], sv[0, i] = x, y
+        out = c.eval(rlk, c.encrypt(s, c.query_plaintexts(cl), off), sv)
+        slots, bud = c.decrypt(s, out)
+        assert bud > 0
+        assert [int(v) for v in slots[: len(chunk)]] == [int(x == y) for x, y in chunk]
+
+
+@pytest.mark.parametrize("h,lb,ell,bits", [(1, 4, 16, [36, 37]), (4, 6, 10, [55, 55, 54, 54]),
+                                           (8, 8, 14, [55] * 6 + [54] * 2)])
+def test_arith_cw_eq_truth_table(oracle_mod, h, lb, ell, bits):
+    eq_truth_table_case(oracle_mod, h, lb, ell, 64, bits, 64, seed=h)
+
+
+@pytest.mark.parametrize("h,bits,lb", [(2, [36, 36, 37], 10), (4, [55, 55, 54, 54], 12), (8, [55] * 6 + [54] * 2, 14)])
+def test_psi_matches_brute_force(oracle_mod, h, bits, lb):
+    from paper_2310_14565_gb300.workload import make_sets
+
+    N = 64
+    sets = make_sets(24, 150, 7, bits=32, seed_items=h, seed_plant=h + 1)
+    c = oracle_mod.Ctx(N=N, t=T, prime_bits=bits, h=h, lambda_bar=lb, hash_key=99, mu=16)
+    s, rlk = c.keygen(3)
+    rc, Ts, _ = c.server_table(sets.server)
+    assert rc == 0
+    rc, cts, where = c.query(s, sets.client, 4)
+    assert rc == 0
+    out = c.eval(rlk, cts, Ts)
+    assert c.last_counts == (c.ell * c.mu, c.mu * int(math.log2(h)))
+    slots, bud = c.decrypt(s, out)
+    assert bud > 0
+    server = set(int(x) for x in sets.server)
+    want = np.zeros(N, np.uint32)
+    for u, x in enumerate(sets.client):
+        want[where[u]] = int(int(x) in server)
+    # hashed-domain intersection: same x_L in a bin the server item maps to
+    hashed = np.zeros(N, np.uint32)
+    srv = {}
+    for y in sets.server:
+        yl, bins = oracle_mod.hash_item(99, lb, 6, y)
+        for b in bins:
+            srv.setdefault(b, set()).add(yl)
+    for u, x in enumerate(sets.client):
+        xl, _ = oracle_mod.hash_item(99, lb, 6, x)
+        hashed[where[u]] = int(xl in srv.get(int(where[u]), set()))
+    assert (slots == hashed).all()
+    assert (slots == want).all()
+    out_c = c.eval(rlk, cts, Ts, mode=1, mask_seed=5)
+    slots_c, _ = c.decrypt(s, out_c)
+    assert int(slots_c.astype(np.int64).sum()) % T == len(sets.planted)
+    assert not (slots_c == want).all()  # masked: individual slots hide the indicator

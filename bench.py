@@ -1,0 +1,345 @@
+#!/usr/bin/env python3
+"""Benchmark of PEPSI's server evaluation on GB300.
+
+Workload (the paper-shaped configuration): N = 8192 slots = bins, t = 65537,
+four RNS primes of 55, 55, 54, 54 bits, constant-weight code ell = 600,
+h = 4, mu = 526 server layers; 1024 client items against 2^20 server items
+(uniform 64-bit, 102 planted).  Synthetic sets, seeded.
+
+One step = one pepsi_eval (Algorithm 2 with the equality circuit of
+Algorithm 1) from device-resident request ciphertexts to a device-resident
+result ciphertext.  The resident server plaintext table (82.7 GB) is read in
+full by every step, so the inputs of a step are larger than L2.
+
+Prints one JSON line.  --impl reference times the CPU oracle instead (the
+project's plain C reference on the host cores, on a bounded layer sample
+scaled to the full 526 layers).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "server eval ms at 1024 x 2^20 items; ct-mult+relin/s; NTT % of HBM roofline"
+WL = dict(N=8192, prime_bits=[55, 55, 54, 54], h=4, ell=600, lambda_bar=32, mu=526, m=1024, n=1 << 20, planted=102)
+HASH_KEY, KEY_SEED, ENC_SEED = 0x5EED, 3, 4
+WORKLOAD_NAME = ("paper-shaped PSI: N=8192 bins, t=65537, q=4 RNS primes (55,55,54,54 bits), CW code ell=600 h=4, "
+                 "mu=526 layers, 1024 client x 2^20 server uniform 64-bit items, 102 planted")
+L2_NOTE = "inputs larger than L2: the 82.7 GB resident plaintext table is streamed from HBM every step"
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(index), "--query-gpu=" + self.FIELDS,
+                                       "--format=csv,noheader,nounits", "-lms", "100"], stdout=self.f,
+                                      stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        self.p.wait()
+        self.f.flush()
+        self.f.seek(0)
+        rows = [r.split(",") for r in self.f.read().strip().splitlines() if r.count(",") >= 8]
+        os.unlink(self.f.name)
+        sm = [float(r[1]) for r in rows if r[1].strip().replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].strip().replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].strip().lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+# ------------------------------------------------------------------ oracle
+def oracle_setup():
+    import oracle
+    from paper_2310_14565_gb300.workload import make_sets
+
+    oc = oracle.Ctx(N=WL["N"], t=65537, prime_bits=WL["prime_bits"], h=WL["h"], ell=WL["ell"],
+                    lambda_bar=WL["lambda_bar"], mu=WL["mu"], hash_key=HASH_KEY)
+    sets = make_sets(WL["m"], WL["n"], WL["planted"], bits=64)
+    s, rlk = oc.keygen(KEY_SEED)
+    rc, Ts, _ = oc.server_table(sets.server)
+    rc2, cts, _ = oc.query(s, sets.client, ENC_SEED)
+    assert rc == 0 and rc2 == 0
+    return oracle, oc, rlk, cts, Ts
+
+
+def oracle_sample(oracle, oc, rlk, cts, Ts, layers, layer0=0):
+    t = time.perf_counter()
+    oc.eval(rlk, cts, Ts, layer0=layer0, nlayers=layers)
+    return (time.perf_counter() - t) * 1e3
+
+
+def cpu_baseline():
+    """The oracle as it stands on the host cores, on a bounded sample: the
+    fixed part (request NTT, final relinearisation) plus a layer sample,
+    scaled to the workload's 526 layers."""
+    oracle, oc, rlk, cts, Ts = oracle_setup()
+    cores = oracle.get_threads()
+    layers = max(2, 2 * cores)
+    fixed = oracle_sample(oracle, oc, rlk, cts, Ts, 0)
+    total = oracle_sample(oracle, oc, rlk, cts, Ts, layers)
+    est = fixed + (total - fixed) * WL["mu"] / layers
+    return {"value": round(est, 1), "unit": "ms", "cores": cores, "kind": "oracle",
+            "sample": "request NTT + relin/scale (%.0f ms) and %d of 526 layers (%.0f ms), layer part scaled to 526"
+                      % (fixed, layers, total - fixed)}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    oracle, oc, rlk, cts, Ts = oracle_setup()
+    cores = oracle.get_threads()
+    fixed = oracle_sample(oracle, oc, rlk, cts, Ts, 0)
+    layers = max(1, cores)
+    times = []
+    for i in range(args.warmup + args.steps):
+        t = oracle_sample(oracle, oc, rlk, cts, Ts, layers, layer0=(i * layers) % (WL["mu"] - layers))
+        if i >= args.warmup:
+            times.append(t)
+    per = statistics.median(times)
+    est = fixed + (per - fixed) * WL["mu"] / layers
+    line = {
+        "impl": "reference", "metric": METRIC, "value": round(est, 1), "unit": "ms", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(per, 1), "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+        "config": {"workload": WORKLOAD_NAME, "l2": "CPU run"},
+        "cpu_baseline": {"value": round(est, 1), "unit": "ms", "cores": cores, "kind": "oracle",
+                         "sample": "each step: request NTT + %d of 526 layers; value scales the layer part to 526"
+                                   % layers},
+        "e2e": {"value": round(est, 1), "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# --------------------------------------------------------------- our arm
+def run_ours(args):
+    import torch
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    import paper_2310_14565_gb300 as pepsi
+    from paper_2310_14565_gb300 import build as _build
+    from paper_2310_14565_gb300.workload import make_sets
+
+    if not os.path.exists(pepsi.LIB_PATH):
+        _build.build()
+    N, k = WL["N"], len(WL["prime_bits"])
+    ctx = pepsi.Context(N=N, t=65537, prime_bits=WL["prime_bits"], h=WL["h"], ell=WL["ell"],
+                        lambda_bar=WL["lambda_bar"], mu=WL["mu"], hash_key=HASH_KEY, key_seed=KEY_SEED)
+    sets = make_sets(WL["m"], WL["n"], WL["planted"], bits=64)
+    t0 = time.perf_counter()
+    sid = ctx.server_load(sets.server)
+    offline_ms = (time.perf_counter() - t0) * 1e3
+    cts_np, where = ctx.query(sets.client, ENC_SEED)
+    shape = cts_np.shape
+    cts_pinned = torch.from_numpy(cts_np.view("int64")).pin_memory()
+    cts_dev = cts_pinned.cuda()
+    out_dev = torch.empty((2, k, N), dtype=torch.int64, device="cuda")
+    out_pinned = torch.empty((2, k, N), dtype=torch.int64).pin_memory()
+    stream = torch.cuda.current_stream()
+
+    def step():
+        ctx.eval(sid, cts_dev, out=out_dev)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    # correctness of the timed configuration (outside the timed region)
+    slots, budget = ctx.decrypt(out_dev)
+    correct = int(slots.sum()) == WL["planted"] and budget > 0
+
+    ctx.profile(False)  # resets the launch counters
+    clocks = Clocks(local)
+    time.sleep(0.5)
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    prof_counts = ctx.profile_read()
+    launches = sum(v[0] for v in prof_counts.values())
+    if ws > 1:
+        t = torch.tensor([ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+
+    # per-kernel CUDA-event timing pass (same workload, events on the launching stream)
+    ctx.profile(True)
+    psteps = max(3, min(args.steps, 20))
+    for _ in range(psteps):
+        step()
+    prof = ctx.profile_read()
+    ctx.profile(False)
+    mac_launches, mac_ms = prof["mac"]
+    mac_launches_per_eval = mac_launches / psteps
+    # algorithmic bytes of the MAC per evaluation: the plaintext table (mu*ell*k*N words),
+    # the request (ell*2*k*N words) and h' (mu*2*k*N words), 8 bytes each
+    mu, ell = WL["mu"], WL["ell"]
+    mac_bytes_eval = 8 * (mu * ell * k * N + ell * 2 * k * N + mu * 2 * k * N)
+    mac_launch_ms = mac_ms / mac_launches
+    achieved = mac_bytes_eval / mac_launches_per_eval / (mac_launch_ms * 1e-3) / 1e9
+    peak, peak_kind = measured_peaks()
+    traffic = None
+    tf = os.path.join(ROOT, "profiles", "mac_traffic.json")
+    if os.path.exists(tf):
+        with open(tf) as f:
+            tinfo = json.load(f)
+        if tinfo.get("kernel_rev") == prof_rev():
+            traffic = tinfo.get("traffic_bytes_per_launch")
+
+    # end to end through the C ABI with host buffers (pinned), copies inside the timed region
+    for _ in range(2):
+        ctx.eval(sid, cts_pinned, out=out_pinned)
+    e2e = []
+    for _ in range(max(3, min(args.steps, 20))):
+        t = time.perf_counter()
+        ctx.eval(sid, cts_pinned, out=out_pinned)
+        e2e.append((time.perf_counter() - t) * 1e3)
+    e2e_ms = statistics.median(e2e)
+
+    # ct-mult + relin throughput (batch of 64 pairs at the workload's parameters)
+    nb = 64
+    a = torch.empty((nb, 2, k, N), dtype=torch.int64, device="cuda")
+    a.copy_(cts_dev[:nb])
+    b = cts_dev[nb:2 * nb].contiguous()
+    o2 = torch.empty((nb, 2, k, N), dtype=torch.int64, device="cuda")
+    for _ in range(2):
+        ctx.ct_mult(a, b, nb, o2, relin=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    reps = 10
+    for _ in range(reps):
+        ctx.ct_mult(a, b, nb, o2, relin=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    mult_per_s = nb * reps / (e0.elapsed_time(e1) * 1e-3)
+
+    # NTT bandwidth: forward + inverse over the whole request (1200 ciphertext components x 4 primes)
+    polys = cts_dev.clone()
+    count = shape[0] * 2
+    for _ in range(2):
+        ctx.ntt(polys, count)
+        ctx.ntt(polys, count, inverse=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(5):
+        ctx.ntt(polys, count)
+        ctx.ntt(polys, count, inverse=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ntt_ms = e0.elapsed_time(e1) / 10
+    ntt_gbs = 2 * 8 * N * k * count / (ntt_ms * 1e-3) / 1e9
+
+    line = {
+        "metric": METRIC, "value": round(ms, 3), "unit": "ms", "n_gpus": args.gpus, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms, 3), "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+        "config": {"workload": WORKLOAD_NAME, "l2": L2_NOTE, "parallelism": "replicas" if ws > 1 else "1 GPU",
+                   "resident_plaintexts_gb": round(mu * ell * k * N * 8 / 1e9, 1)},
+        "correct": correct, "noise_budget_bits": round(budget, 2),
+        "offline_server_load_ms": round(offline_ms, 1),
+        "ct_mult_relin_per_s": round(mult_per_s, 1),
+        "ntt": {"gbs": round(ntt_gbs, 1), "hbm_frac": round(ntt_gbs / peak, 4),
+                "note": "forward+inverse over 1200x4 polynomials of N=8192, 2*8*N bytes per polynomial"},
+        "roofline": {"bound": "hbm", "kernel": "k_mac", "achieved": round(achieved, 1), "peak": peak,
+                     "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": traffic,
+                     "peak_source": peak_kind, "launches_per_step": mac_launches_per_eval,
+                     "avg_launch_ms": round(mac_launch_ms, 4)},
+        "kernel_ms_per_step": {name: round(v[1] / psteps, 3) for name, v in prof.items() if v[0]},
+        "e2e": {"value": round(e2e_ms, 3), "unit": "ms", "h2d_bytes_per_step": int(cts_np.nbytes),
+                "d2h_bytes_per_step": int(out_pinned.numel() * 8)},
+        "gpu_launches": int(launches),
+        "clocks": clk,
+    }
+    if rank == 0 and args.gpus == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def prof_rev():
+    """Identity of the MAC kernel source, to tell whether stored counters are current."""
+    import hashlib
+
+    src = os.path.join(ROOT, "paper_2310_14565_gb300", "csrc", "kernels.cu")
+    text = open(src).read()
+    start = text.find("// ------------------------------------------------------- fused MAC")
+    end = text.find("// ---------------------------------------------------- RNS conversions")
+    return hashlib.sha256(text[start:end].encode()).hexdigest()[:16]
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

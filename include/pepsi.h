@@ -1,0 +1,187 @@
+/*
+ * pepsi.h -- C ABI of the GB300 (sm_103a) implementation of PEPSI's
+ * server-side homomorphic evaluation (arXiv 2310.14565).
+ *
+ * The library evaluates Algorithm 2 ("Intersect") with the arithmetic
+ * constant-weight equality operator of Algorithm 1 in RNS-BFV (FV,
+ * Section 3.1), the cardinality variant of Algorithm 5, and the client
+ * side of Algorithms 3 and 7 needed to produce and read the messages.
+ *
+ * Conventions shared by every call:
+ *  - Return value: PEPSI_OK (0) or one of the error codes below.  No call
+ *    aborts the process; pepsi_strerror() names a code.
+ *  - Pointers: the caller owns every buffer it passes.  "host or device"
+ *    means the library inspects the pointer (cudaPointerGetAttributes) and
+ *    copies through the call's stream when it is host memory.  The context
+ *    owns all of its device memory (keys, server tables, scratch).
+ *  - Ciphertext words: residues in [0, q_i), layout [component][prime][N]
+ *    (prime-major inside a component), coefficient form unless stated.
+ *    A batch of ciphertexts adds a leading dimension.
+ *  - Streams: `stream` is a cudaStream_t (NULL: the context's own stream).
+ *    Calls with device output buffers are asynchronous on that stream;
+ *    calls with host output buffers synchronise it before returning.
+ *  - One context serves one evaluation at a time: calls on the same
+ *    context must not overlap (they share the context's scratch memory).
+ *  - Parameters the paper leaves open (prime choice, roots, hashing
+ *    functions, randomness, codeword mapping, slot order) follow the
+ *    readings documented with the project and implemented identically by
+ *    its independent CPU oracle.
+ */
+#ifndef PEPSI_H
+#define PEPSI_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Error codes. */
+enum {
+  PEPSI_OK = 0,
+  PEPSI_E_PARAM = 1,        /* invalid or unsupported parameters / arguments */
+  PEPSI_E_BIN_OVERFLOW = 2, /* a server bin holds more than mu items (Section 4.1) */
+  PEPSI_E_CUCKOO_FAIL = 3,  /* client cuckoo insertion exceeded the eviction bound (Section 3.3) */
+  PEPSI_E_NOMEM = 4,        /* device memory (HBM budget) exhausted */
+  PEPSI_E_CUDA = 5,         /* a CUDA runtime call failed */
+  PEPSI_E_TIMEOUT = 6,      /* a bounded device wait expired */
+  PEPSI_E_NOISE = 7         /* decryption noise budget exhausted (<= 0 bits) */
+};
+
+/* Evaluation modes. */
+enum {
+  PEPSI_MODE_INDICATOR = 0,  /* Algorithm 2: encrypted per-bin indicator */
+  PEPSI_MODE_CARDINALITY = 1 /* Algorithm 5 with val_s = 1: masked, slots sum to |X cap Y| */
+};
+
+typedef struct pepsi_ctx pepsi_ctx; /* opaque */
+
+/* Parameters (Table 2 notation).  Zero means "derive". */
+typedef struct {
+  uint32_t N;              /* ring degree = number of bins b (power of two, 16..16384) */
+  uint64_t t;              /* plaintext modulus: prime, t = 1 (mod 2N), t < 2^32 */
+  uint32_t k;              /* number of ciphertext primes q_i (1..8) */
+  uint8_t prime_bits[8];   /* bit size of each q_i (20..60), searched in this order */
+  uint32_t h;              /* Hamming weight of the constant-weight code: 1, 2, 4 or 8 */
+  uint32_t ell;            /* code length; 0 -> Eq. 1 from lambda_bar and h */
+  uint32_t lambda_bar;     /* effective item bit length (Section 3.3, PBH) */
+  uint32_t num_hashes;     /* cuckoo / simple hash functions: must be 3 */
+  uint32_t mu;             /* server maximum bin load; 0 -> bound rule */
+  uint64_t hash_key;       /* public seed of H_0..H_3 */
+  uint64_t resident_bytes; /* 0: keep server plaintexts resident when they fit in
+                              60% of free HBM; UINT64_MAX: never; else a byte cap */
+} pepsi_params;
+
+/* Derived values of a context (for callers and tests). */
+typedef struct {
+  uint32_t N, k, kb, ell, h, mu, lambda_bar, logb;
+  uint64_t t;
+  uint64_t q[8];        /* ciphertext primes */
+  uint64_t psi[8];      /* minimal primitive 2N-th roots of the q_i */
+  uint64_t psi_t;       /* minimal primitive 2N-th root mod t */
+  uint64_t b_primes[12];/* auxiliary base B used for exact multiplication */
+  double log2_q;
+} pepsi_info;
+
+/* Setup (Section 4, parameters of Tables 2-3): derives ell (Eq. 1), the
+ * primes (largest below 2^bits with q = 1 mod 2N), the NTT tables and the
+ * auxiliary base; samples the secret key s (uniform ternary) and the
+ * relinearisation keys rlk_i = (-a_i s + e_i + g_i s^2, a_i) from key_seed,
+ * all on the device.  *out receives the context; destroy with
+ * pepsi_destroy().  Errors: PEPSI_E_PARAM, PEPSI_E_NOMEM, PEPSI_E_CUDA. */
+int pepsi_setup(const pepsi_params* params, uint64_t key_seed, pepsi_ctx** out);
+
+/* Fill *info with the context's derived parameters. */
+int pepsi_get_info(const pepsi_ctx* ctx, pepsi_info* info);
+
+/* Server preprocessing, offline (Section 4.1 and App. Alg 7, server side):
+ * H_0 to lambda bits, permutation-based hashing into each of the three
+ * bins of every item, de-duplication of equal x_L inside a bin, stable
+ * layer order, dummies up to mu; then the NTT-form server plaintexts
+ * pt_s[layer][j] are generated on the device (resident when the budget
+ * allows, otherwise regenerated per layer chunk at evaluation time).
+ * items: host array of n 64-bit items.  *set_id receives the handle.
+ * Errors: PEPSI_E_BIN_OVERFLOW, PEPSI_E_NOMEM, PEPSI_E_PARAM, PEPSI_E_CUDA. */
+int pepsi_server_load(pepsi_ctx* ctx, const uint64_t* items, size_t n, int* set_id);
+
+/* Copy the raw server table T_s of a set: out[mu][N] (host), entries are
+ * x_L values or UINT64_MAX for dummies. */
+int pepsi_server_table(pepsi_ctx* ctx, int set_id, uint64_t* out);
+
+/* Copy server plaintexts pt_s[layer][j] for layers [layer0, layer0+nl) in
+ * NTT form (value at psi^(2 brev(i)+1) in slot i): out[nl][ell][k][N],
+ * host or device. */
+int pepsi_server_plaintexts(pepsi_ctx* ctx, int set_id, uint32_t layer0, uint32_t nl, uint64_t* out,
+                            void* stream);
+
+/* Client request (App. Alg 7, client side): cuckoo hashing without stash
+ * (3 hashes, eviction bound 1000), CW-Encode, batching, symmetric FV
+ * encryption under s with randomness from enc_seed.  cts: [ell][2][k][N]
+ * coefficient form (host or device).  bin_of_item: host int32[m], the bin
+ * that holds each item.  Errors: PEPSI_E_CUCKOO_FAIL, PEPSI_E_PARAM. */
+int pepsi_query(pepsi_ctx* ctx, const uint64_t* items, size_t m, uint64_t enc_seed, uint64_t* cts,
+                int32_t* bin_of_item, void* stream);
+
+/* Server computation (Algorithm 2; mode CARDINALITY adds Algorithm 5's
+ * zero-sum mask drawn from mask_seed): for every layer i',
+ * h' = sum_j ct_c[j] x pt_s[i'][j], e = prod_{i<h}(h' - i), summed over
+ * layers, relinearised and multiplied by (h!)^-1 mod t.
+ * cts: [ell][2][k][N] coefficient form, host or device.
+ * out_ct: [2][k][N] coefficient form, host or device.
+ * Errors: PEPSI_E_PARAM (bad set/mode), PEPSI_E_NOMEM, PEPSI_E_CUDA. */
+int pepsi_eval(pepsi_ctx* ctx, int set_id, const uint64_t* cts, int mode, uint64_t mask_seed, uint64_t* out_ct,
+               void* stream);
+
+/* The same pipeline on layers [layer0, layer0+nl) only, returning the
+ * per-layer intermediate words: h_out[nl][2][k][N] (h', coefficient form)
+ * and e_out[nl][3][k][N] (the un-relinearised equality ciphertexts), host
+ * or device; either may be NULL.  For sampled parity checks. */
+int pepsi_eval_layers(pepsi_ctx* ctx, int set_id, const uint64_t* cts, uint32_t layer0, uint32_t nl,
+                      uint64_t* h_out, uint64_t* e_out, void* stream);
+
+/* Client result extraction (Algorithm 3): FV decryption, m = round(t z/Q)
+ * mod t, slots of m.  ct: [2][k][N] (host or device); slots: host
+ * uint32[N]; noise_budget_bits (may be NULL): log2(Q) - log2(2 max|[t z]_Q|).
+ * Returns PEPSI_E_NOISE when the budget is not positive (slots are still
+ * written). */
+int pepsi_decrypt(pepsi_ctx* ctx, const uint64_t* ct, uint32_t* slots, double* noise_budget_bits);
+
+/* Forward (inverse = 0) or inverse negacyclic NTT over the ciphertext
+ * primes, in place: polys[count][k][N], device memory.  Forward maps
+ * coefficients to values at psi_i^(2 brev(j)+1) in position j. */
+int pepsi_ntt(pepsi_ctx* ctx, uint64_t* polys, size_t count, int inverse, void* stream);
+
+/* FV multiplication (Section 3.1) of n ciphertext pairs, exact textbook
+ * rounding round(t/Q * a~ (x) b~): a, b [n][2][k][N], out [n][3][k][N]
+ * (relin = 0) or [n][2][k][N] (relin = 1, RNS-digit relinearisation).
+ * All coefficient form, device memory. */
+int pepsi_ct_mult(pepsi_ctx* ctx, const uint64_t* a, const uint64_t* b, size_t n, int relin, uint64_t* out,
+                  void* stream);
+
+/* Relinearisation alone: in [n][3][k][N] -> out [n][2][k][N], coefficient
+ * form, device memory. */
+int pepsi_relin(pepsi_ctx* ctx, const uint64_t* in, size_t n, uint64_t* out, void* stream);
+
+/* Test access to the keys: s (int8[N], host) and the relinearisation keys
+ * in coefficient form rlk[k][2][k][N] (host); either may be NULL. */
+int pepsi_export_keys(pepsi_ctx* ctx, int8_t* s, uint64_t* rlk);
+
+/* Per-kernel timing with CUDA events on the launching stream: enable (1) /
+ * disable (0) and read back {launches, total milliseconds} per kernel
+ * class (names[i] is a static string; returns the number of classes). */
+int pepsi_profile_enable(pepsi_ctx* ctx, int on);
+int pepsi_profile_read(pepsi_ctx* ctx, const char** names, uint64_t* launches, double* total_ms, int max);
+
+/* Release every device buffer of the context (NULL is ignored). */
+void pepsi_destroy(pepsi_ctx* ctx);
+/* Static description of an error code. */
+const char* pepsi_strerror(int code);
+/* Name and description of the last CUDA failure reported by a call of
+ * this thread (valid until the next failing call). */
+const char* pepsi_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PEPSI_H */

@@ -1030,7 +1030,7 @@ int or_eval(const or_ctx* c, const u64* rlk, const u64* cts, u32 ell, u32 h, con
   memcpy(CN, cts, sizeof(u64) * ell * ct2);
 #pragma omp parallel for schedule(dynamic)
   for (long jj = 0; jj < (long)ell * 2 * k; jj++) ntt_fwd(CN + (u64)jj * N, N, &c->tq[jj % k]);
-  u64* Eall = (u64*)calloc((u64)nl * ct3, sizeof(u64));
+  u64* Eall = (u64*)calloc((u64)(nl ? nl : 1) * ct3, sizeof(u64));
   u64 pm = 0, mm = 0;
   int rc = 0;
 #pragma omp parallel for schedule(dynamic) reduction(+ : pm, mm) reduction(| : rc)

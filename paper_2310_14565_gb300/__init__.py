@@ -1,0 +1,258 @@
+"""PEPSI server-side homomorphic evaluation (arXiv 2310.14565) on GB300.
+
+Thin Python binding over the C ABI of ``include/pepsi.h``: every call
+marshals arguments (numpy arrays for host buffers, torch CUDA tensors or raw
+integers for device buffers) and forwards to ``libpepsi_gb300.so``.  All
+computation runs in the library's CUDA kernels; there is no CPU fallback, and
+calls fail loudly when the library has not been built.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import sys
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libpepsi_gb300.so")
+_lib = None
+
+OK, E_PARAM, E_BIN_OVERFLOW, E_CUCKOO_FAIL, E_NOMEM, E_CUDA, E_TIMEOUT, E_NOISE = range(8)
+MODE_INDICATOR, MODE_CARDINALITY = 0, 1
+DUMMY = 0xFFFFFFFFFFFFFFFF
+
+
+class PepsiError(RuntimeError):
+    def __init__(self, code, what):
+        self.code = code
+        detail = ""
+        if code in (E_CUDA, E_NOMEM):
+            try:
+                detail = " [%s]" % lib().pepsi_last_error().decode()
+            except Exception:
+                pass
+        super().__init__("%s failed: %s (code %d)%s" % (what, strerror(code), code, detail))
+
+
+class Params(C.Structure):
+    _fields_ = [
+        ("N", C.c_uint32), ("t", C.c_uint64), ("k", C.c_uint32), ("prime_bits", C.c_uint8 * 8),
+        ("h", C.c_uint32), ("ell", C.c_uint32), ("lambda_bar", C.c_uint32), ("num_hashes", C.c_uint32),
+        ("mu", C.c_uint32), ("hash_key", C.c_uint64), ("resident_bytes", C.c_uint64),
+    ]
+
+
+class Info(C.Structure):
+    _fields_ = [
+        ("N", C.c_uint32), ("k", C.c_uint32), ("kb", C.c_uint32), ("ell", C.c_uint32), ("h", C.c_uint32),
+        ("mu", C.c_uint32), ("lambda_bar", C.c_uint32), ("logb", C.c_uint32), ("t", C.c_uint64),
+        ("q", C.c_uint64 * 8), ("psi", C.c_uint64 * 8), ("psi_t", C.c_uint64), ("b_primes", C.c_uint64 * 12),
+        ("log2_q", C.c_double),
+    ]
+
+
+SYMBOLS = {
+    # name: (restype, argtypes)
+    "pepsi_setup": (C.c_int, [C.POINTER(Params), C.c_uint64, C.POINTER(C.c_void_p)]),
+    "pepsi_get_info": (C.c_int, [C.c_void_p, C.POINTER(Info)]),
+    "pepsi_server_load": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t, C.POINTER(C.c_int)]),
+    "pepsi_server_table": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p]),
+    "pepsi_server_plaintexts": (C.c_int, [C.c_void_p, C.c_int, C.c_uint32, C.c_uint32, C.c_void_p, C.c_void_p]),
+    "pepsi_query": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t, C.c_uint64, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "pepsi_eval": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.c_uint64, C.c_void_p, C.c_void_p]),
+    "pepsi_eval_layers": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_uint32, C.c_uint32, C.c_void_p,
+                                    C.c_void_p, C.c_void_p]),
+    "pepsi_decrypt": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(C.c_double)]),
+    "pepsi_ntt": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t, C.c_int, C.c_void_p]),
+    "pepsi_ct_mult": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_size_t, C.c_int, C.c_void_p, C.c_void_p]),
+    "pepsi_relin": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p]),
+    "pepsi_export_keys": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
+    "pepsi_profile_enable": (C.c_int, [C.c_void_p, C.c_int]),
+    "pepsi_profile_read": (C.c_int, [C.c_void_p, C.POINTER(C.c_char_p), C.POINTER(C.c_uint64),
+                                     C.POINTER(C.c_double), C.c_int]),
+    "pepsi_destroy": (None, [C.c_void_p]),
+    "pepsi_strerror": (C.c_char_p, [C.c_int]),
+    "pepsi_last_error": (C.c_char_p, []),
+}
+
+
+def lib():
+    """Load the CUDA library; raises when it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libpepsi_gb300.so is missing: build it with paper_2310_14565_gb300.build.build() "
+                               "(requires nvcc); there is no CPU fallback")
+        L = C.CDLL(LIB_PATH)
+        for name, (res, args) in SYMBOLS.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def strerror(code: int) -> str:
+    try:
+        return lib().pepsi_strerror(code).decode()
+    except RuntimeError:
+        return "error %d" % code
+
+
+def _ptr(x):
+    """Address of a numpy array, a torch tensor or an integer (None -> NULL)."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if isinstance(x, np.ndarray):
+        if not x.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return x.ctypes.data
+    if hasattr(x, "data_ptr"):
+        if hasattr(x, "is_contiguous") and not x.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return x.data_ptr()
+    raise TypeError("unsupported buffer type %r" % type(x))
+
+
+def _stream(s):
+    """cudaStream_t for a call: an explicit stream, else torch's current
+    stream when torch has initialised CUDA (so device tensors produced by
+    torch are ordered before the call), else the context's own stream."""
+    if s is None:
+        torch = sys.modules.get("torch")
+        if torch is not None and torch.cuda.is_initialized():
+            return torch.cuda.current_stream().cuda_stream or None
+        return None
+    if isinstance(s, int):
+        return s
+    return s.cuda_stream  # torch.cuda.Stream
+
+
+def _check(rc, what):
+    if rc != OK:
+        raise PepsiError(rc, what)
+
+
+class Context:
+    """One parameter set with its keys, server sets and scratch (pepsi_ctx)."""
+
+    def __init__(self, N, t=65537, prime_bits=(36, 36, 37), h=2, ell=0, lambda_bar=16, mu=0, hash_key=0,
+                 key_seed=3, resident_bytes=0):
+        p = Params()
+        p.N, p.t, p.k = N, t, len(prime_bits)
+        for i, b in enumerate(prime_bits):
+            p.prime_bits[i] = b
+        p.h, p.ell, p.lambda_bar, p.num_hashes, p.mu = h, ell, lambda_bar, 3, mu
+        p.hash_key, p.resident_bytes = hash_key, resident_bytes
+        self._h = C.c_void_p()
+        _check(lib().pepsi_setup(C.byref(p), key_seed, C.byref(self._h)), "pepsi_setup")
+        info = Info()
+        _check(lib().pepsi_get_info(self._h, C.byref(info)), "pepsi_get_info")
+        self.N, self.k, self.kb, self.ell, self.h = info.N, info.k, info.kb, info.ell, info.h
+        self.t, self.log2_q = info.t, info.log2_q
+        self.q = [int(info.q[i]) for i in range(self.k)]
+        self.psi = [int(info.psi[i]) for i in range(self.k)]
+        self.psi_t = int(info.psi_t)
+        self.b_primes = [int(info.b_primes[i]) for i in range(min(self.kb, 12))]
+        self.mu = {}
+
+    def close(self):
+        if self._h:
+            lib().pepsi_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ---- shapes
+    def ct_words(self, comps=2):
+        return comps * self.k * self.N
+
+    # ---- server side
+    def server_load(self, items):
+        items = np.ascontiguousarray(items, dtype=np.uint64)
+        sid = C.c_int(-1)
+        _check(lib().pepsi_server_load(self._h, _ptr(items) if items.size else None, items.size, C.byref(sid)),
+               "pepsi_server_load")
+        return sid.value
+
+    def server_table(self, set_id, mu):
+        out = np.zeros((mu, self.N), dtype=np.uint64)
+        _check(lib().pepsi_server_table(self._h, set_id, _ptr(out)), "pepsi_server_table")
+        return out
+
+    def server_plaintexts(self, set_id, layer0, nl, out=None, stream=None):
+        if out is None:
+            out = np.zeros((nl, self.ell, self.k, self.N), dtype=np.uint64)
+        _check(lib().pepsi_server_plaintexts(self._h, set_id, layer0, nl, _ptr(out), _stream(stream)),
+               "pepsi_server_plaintexts")
+        return out
+
+    # ---- client side
+    def query(self, items, enc_seed, out=None, stream=None):
+        items = np.ascontiguousarray(items, dtype=np.uint64)
+        if out is None:
+            out = np.zeros((self.ell, 2, self.k, self.N), dtype=np.uint64)
+        where = np.full(max(items.size, 1), -1, dtype=np.int32)
+        _check(lib().pepsi_query(self._h, _ptr(items) if items.size else None, items.size, enc_seed, _ptr(out),
+                                 _ptr(where), _stream(stream)), "pepsi_query")
+        return out, where[: items.size]
+
+    def decrypt(self, ct):
+        ct = np.ascontiguousarray(ct, dtype=np.uint64) if isinstance(ct, np.ndarray) else ct
+        slots = np.zeros(self.N, dtype=np.uint32)
+        b = C.c_double(0)
+        rc = lib().pepsi_decrypt(self._h, _ptr(ct), _ptr(slots), C.byref(b))
+        if rc not in (OK, E_NOISE):
+            raise PepsiError(rc, "pepsi_decrypt")
+        return slots, b.value
+
+    # ---- evaluation
+    def eval(self, set_id, cts, mode=MODE_INDICATOR, mask_seed=0, out=None, stream=None):
+        if out is None:
+            out = np.zeros((2, self.k, self.N), dtype=np.uint64)
+        _check(lib().pepsi_eval(self._h, set_id, _ptr(cts), mode, mask_seed, _ptr(out), _stream(stream)),
+               "pepsi_eval")
+        return out
+
+    def eval_layers(self, set_id, cts, layer0, nl, want_h=True, want_e=True, stream=None):
+        h = np.zeros((nl, 2, self.k, self.N), dtype=np.uint64) if want_h else None
+        e = np.zeros((nl, 3, self.k, self.N), dtype=np.uint64) if want_e else None
+        _check(lib().pepsi_eval_layers(self._h, set_id, _ptr(cts), layer0, nl, _ptr(h), _ptr(e), _stream(stream)),
+               "pepsi_eval_layers")
+        return h, e
+
+    # ---- primitives (device buffers)
+    def ntt(self, polys, count, inverse=False, stream=None):
+        _check(lib().pepsi_ntt(self._h, _ptr(polys), count, int(inverse), _stream(stream)), "pepsi_ntt")
+
+    def ct_mult(self, a, b, n, out, relin=False, stream=None):
+        _check(lib().pepsi_ct_mult(self._h, _ptr(a), _ptr(b), n, int(relin), _ptr(out), _stream(stream)),
+               "pepsi_ct_mult")
+
+    def relin(self, ct3, n, out, stream=None):
+        _check(lib().pepsi_relin(self._h, _ptr(ct3), n, _ptr(out), _stream(stream)), "pepsi_relin")
+
+    def export_keys(self):
+        s = np.zeros(self.N, dtype=np.int8)
+        rlk = np.zeros((self.k, 2, self.k, self.N), dtype=np.uint64)
+        _check(lib().pepsi_export_keys(self._h, _ptr(s), _ptr(rlk)), "pepsi_export_keys")
+        return s, rlk
+
+    # ---- profiling
+    def profile(self, on=True):
+        _check(lib().pepsi_profile_enable(self._h, int(on)), "pepsi_profile_enable")
+
+    def profile_read(self):
+        n = 16
+        names = (C.c_char_p * n)()
+        launches = (C.c_uint64 * n)()
+        ms = (C.c_double * n)()
+        cnt = lib().pepsi_profile_read(self._h, names, launches, ms, n)
+        return {names[i].decode(): (int(launches[i]), float(ms[i])) for i in range(cnt)}

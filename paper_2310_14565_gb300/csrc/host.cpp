@@ -1,0 +1,339 @@
+// Host-side parameter derivation and hashing of the PEPSI library:
+// prime search, roots of unity, NTT tables, the RNS conversion constants
+// (computed from residues only), Eq. 1, the server bin bound, and the
+// client / server hashing of Section 3.3 and App. Alg 7.
+#include "host.h"
+
+#include "pepsi.h"
+
+#include <algorithm>
+#include <cmath>
+#include <map>
+#include <unordered_set>
+
+namespace hostmath {
+
+u64 mulmod(u64 a, u64 b, u64 m) { return (u64)((u128)a * b % m); }
+u64 powmod(u64 b, u64 e, u64 m) {
+  u64 r = 1 % m;
+  b %= m;
+  for (; e; e >>= 1) {
+    if (e & 1) r = mulmod(r, b, m);
+    b = mulmod(b, b, m);
+  }
+  return r;
+}
+u64 invmod(u64 a, u64 m) {
+  // extended Euclid on signed 128-bit values
+  __int128 r0 = m, r1 = a % m, s0 = 0, s1 = 1;
+  while (r1) {
+    __int128 qq = r0 / r1, tmp = r0 - qq * r1;
+    r0 = r1;
+    r1 = tmp;
+    tmp = s0 - qq * s1;
+    s0 = s1;
+    s1 = tmp;
+  }
+  if (s0 < 0) s0 += m;
+  return (u64)s0;
+}
+
+// Miller-Rabin with the seven bases of Jaeschke / Sinclair, exact below 2^64.
+bool is_prime(u64 n) {
+  if (n < 2) return false;
+  for (u64 p : {2ull, 3ull, 5ull, 7ull, 11ull, 13ull}) {
+    if (n % p == 0) return n == p;
+  }
+  u64 d = n - 1;
+  int s = 0;
+  while (!(d & 1)) {
+    d >>= 1;
+    ++s;
+  }
+  for (u64 a : {2ull, 325ull, 9375ull, 28178ull, 450775ull, 9780504ull, 1795265022ull}) {
+    u64 x = powmod(a % n, d, n);
+    if (a % n == 0 || x == 1 || x == n - 1) continue;
+    bool witness = true;
+    for (int r = 1; r < s && witness; ++r) {
+      x = mulmod(x, x, n);
+      if (x == n - 1) witness = false;
+    }
+    if (witness) return false;
+  }
+  return true;
+}
+
+u64 find_prime(int bits, u32 N, const std::vector<u64>& taken) {
+  const u64 step = 2ull * N;
+  if (bits > 62 || (1ull << bits) <= step) return 0;
+  for (u64 q = (1ull << bits) - step + 1; q > step; q -= step) {
+    if (std::find(taken.begin(), taken.end(), q) != taken.end()) continue;
+    if (is_prime(q)) return q;
+  }
+  return 0;
+}
+
+u64 min_root(u64 q, u32 N) {
+  const u64 e = (q - 1) / (2ull * N);
+  u64 w = 0;
+  for (u64 g = 2; g < q && !w; ++g) {
+    u64 c = powmod(g, e, q);
+    if (powmod(c, N, q) == q - 1) w = c;
+  }
+  if (!w) return 0;
+  // every primitive 2N-th root is w^(2j+1)
+  u64 best = w, x = w, w2 = mulmod(w, w, q);
+  for (u32 j = 1; j < N; ++j) {
+    x = mulmod(x, w2, q);
+    best = std::min(best, x);
+  }
+  return best;
+}
+
+u64 shoup_of(u64 w, u64 q) { return (u64)(((u128)w << 64) / q); }
+
+DevPrime make_prime(u64 q, u32 N) {
+  DevPrime p;
+  p.q = q;
+  u128 m = ~(u128)0 / q;  // floor((2^128 - 1) / q) = floor(2^128 / q) for odd q > 1
+  p.bhi = (u64)(m >> 64);
+  p.blo = (u64)m;
+  p.ninv = invmod(N % q, q);
+  p.ninvs = shoup_of(p.ninv, q);
+  return p;
+}
+
+static u32 bitrev(u32 x, u32 bits) {
+  u32 r = 0;
+  for (u32 i = 0; i < bits; ++i) r = (r << 1) | ((x >> i) & 1);
+  return r;
+}
+
+void twiddles(u64 q, u64 psi, u32 N, u64* tw, u64* tws, u64* itw, u64* itws) {
+  u32 lg = 0;
+  while ((1u << lg) < N) ++lg;
+  std::vector<u64> pw(N), ipw(N);
+  const u64 ipsi = invmod(psi, q);
+  pw[0] = ipw[0] = 1;
+  for (u32 i = 1; i < N; ++i) {
+    pw[i] = mulmod(pw[i - 1], psi, q);
+    ipw[i] = mulmod(ipw[i - 1], ipsi, q);
+  }
+  for (u32 i = 0; i < N; ++i) {
+    const u32 r = bitrev(i, lg);
+    tw[i] = pw[r];
+    tws[i] = shoup_of(tw[i], q);
+    itw[i] = ipw[r];
+    itws[i] = shoup_of(itw[i], q);
+  }
+}
+
+// Garner digits of the integer whose residues are x over primes p.
+static std::vector<u64> garner(const std::vector<u64>& x, const std::vector<u64>& p) {
+  std::vector<u64> v(p.size());
+  for (size_t i = 0; i < p.size(); ++i) {
+    u64 a = x[i] % p[i];
+    for (size_t j = 0; j < i; ++j) {
+      a = (a + p[i] - v[j] % p[i]) % p[i];
+      a = mulmod(a, invmod(p[j] % p[i], p[i]), p[i]);
+    }
+    v[i] = a;
+  }
+  return v;
+}
+
+void rns_constants(const std::vector<u64>& Q, const std::vector<u64>& B, u64 t, RnsConst* rc) {
+  const size_t k = Q.size(), kb = B.size();
+  *rc = RnsConst{};
+  for (size_t i = 0; i < k; ++i)
+    for (size_t j = 0; j < i; ++j) {
+      rc->cq[i][j] = invmod(Q[j] % Q[i], Q[i]);
+      rc->cqs[i][j] = shoup_of(rc->cq[i][j], Q[i]);
+    }
+  for (size_t i = 0; i < kb; ++i)
+    for (size_t j = 0; j < i; ++j) {
+      rc->cb[i][j] = invmod(B[j] % B[i], B[i]);
+      rc->cbs[i][j] = shoup_of(rc->cb[i][j], B[i]);
+    }
+  auto prod_mod = [](const std::vector<u64>& ps, size_t upto, u64 m) {
+    u64 r = 1 % m;
+    for (size_t l = 0; l < upto; ++l) r = mulmod(r, ps[l] % m, m);
+    return r;
+  };
+  for (size_t j = 0; j < kb; ++j) {
+    for (size_t l = 0; l < k; ++l) rc->pqb[j][l] = prod_mod(Q, l, B[j]);
+    rc->qmodb[j] = prod_mod(Q, k, B[j]);
+    const u64 inv2 = invmod(2, B[j]);
+    rc->qhalf_b[j] = mulmod((rc->qmodb[j] + B[j] - 1) % B[j], inv2, B[j]);
+    rc->qinv_b[j] = invmod(rc->qmodb[j], B[j]);
+    rc->qinv_bs[j] = shoup_of(rc->qinv_b[j], B[j]);
+    rc->t_b[j] = t % B[j];
+    rc->t_bs[j] = shoup_of(rc->t_b[j], B[j]);
+  }
+  // (Q-1)/2 = -1/2 mod q_i, i.e. (q_i - 1)/2; its Garner digits over Q
+  std::vector<u64> qh(k);
+  for (size_t i = 0; i < k; ++i) {
+    qh[i] = (Q[i] - 1) / 2;
+    rc->qhalf_q[i] = qh[i];
+    rc->t_q[i] = t % Q[i];
+    rc->t_qs[i] = shoup_of(rc->t_q[i], Q[i]);
+  }
+  std::vector<u64> d = garner(qh, Q);
+  for (size_t i = 0; i < k; ++i) rc->qhalf_dig[i] = d[i];
+  std::vector<u64> bh(kb);
+  for (size_t j = 0; j < kb; ++j) bh[j] = (B[j] - 1) / 2;
+  d = garner(bh, B);
+  for (size_t j = 0; j < kb; ++j) rc->bhalf_dig[j] = d[j];
+  for (size_t i = 0; i < k; ++i) {
+    for (size_t j = 0; j < kb; ++j) rc->pbq[i][j] = prod_mod(B, j, Q[i]);
+    rc->bmodq[i] = prod_mod(B, kb, Q[i]);
+  }
+  // decryption / encoding
+  double acc = 1.0;
+  for (size_t l = 0; l < k; ++l) {
+    rc->pq_t[l] = prod_mod(Q, l, t);
+    rc->pq_d[l] = acc;
+    acc *= (double)Q[l];
+  }
+  const u64 qmt = prod_mod(Q, k, t);
+  rc->qmt = qmt;
+  rc->qinv_t = invmod(qmt, t);
+  rc->qhalf_t = mulmod((qmt + t - 1) % t, invmod(2, t), t);
+  for (size_t i = 0; i < k; ++i) {
+    // floor(Q/t) = (Q - (Q mod t)) / t = -(Q mod t) * t^-1 mod q_i
+    rc->qdt_q[i] = mulmod((Q[i] - qmt % Q[i]) % Q[i], invmod(t % Q[i], Q[i]), Q[i]);
+    rc->qdt_qs[i] = shoup_of(rc->qdt_q[i], Q[i]);
+  }
+}
+
+void delta(const std::vector<u64>& Q, u64 t, u64 v, u64* out) {
+  u64 qmt = 1 % t;
+  for (u64 q : Q) qmt = mulmod(qmt, q % t, t);
+  const u64 frac = (u64)(((u128)qmt * v + (t - 1) / 2) / t);
+  for (size_t i = 0; i < Q.size(); ++i) {
+    const u64 qdt = mulmod((Q[i] - qmt % Q[i]) % Q[i], invmod(t % Q[i], Q[i]), Q[i]);
+    out[i] = (mulmod(qdt, v % Q[i], Q[i]) + frac % Q[i]) % Q[i];
+  }
+}
+
+u64 binom_sat(u64 n, u64 r) {
+  if (r > n) return 0;
+  u128 v = 1;
+  for (u64 i = 1; i <= r; ++i) {
+    v = v * (n - r + i) / i;
+    if (v >> 63) return 1ull << 63;
+  }
+  return (u64)v;
+}
+
+u32 code_length(u32 lambda_bar, u32 h) {
+  if (h == 0 || lambda_bar >= 63) return 0;
+  for (u32 ell = h; ell < (1u << 20); ++ell)
+    if (binom_sat(ell, h) >= (1ull << lambda_bar)) return ell;
+  return 0;
+}
+
+u32 mu_rule(u64 n, u32 b) {
+  static const std::map<std::pair<u64, u32>, u32> paper = {
+      {{1ull << 20, 8192}, 526},   {{1ull << 24, 8192}, 6710}, {{1ull << 28, 8192}, 100565},
+      {{1ull << 18, 16384}, 100},  {{1ull << 20, 16384}, 296}, {{1ull << 22, 16384}, 976},
+      {{1ull << 24, 16384}, 3487}, {{1ull << 28, 16384}, 50812}};
+  auto it = paper.find({n, b});
+  if (it != paper.end()) return it->second;
+  // tail P[X > mu] of Binomial(3n, 1/b), summed from the log-pmf
+  const long double trials = 3.0L * n, p = 1.0L / b;
+  const long double target = std::ldexp(1.0L, -40) / b;
+  auto logpmf = [&](long double x) {
+    return std::lgamma(trials + 1) - std::lgamma(x + 1) - std::lgamma(trials - x + 1) + x * std::log(p) +
+           (trials - x) * std::log1p(-p);
+  };
+  u32 mu = (u32)std::max<long double>(1.0L, std::floor(trials * p));
+  for (;; ++mu) {
+    long double tail = 0;
+    for (u64 x = mu + 1; x <= (u64)trials; ++x) {
+      const long double term = std::exp(logpmf((long double)x));
+      tail += term;
+      if (term < tail * 1e-20L) break;
+    }
+    if (tail <= target) return mu;
+  }
+}
+
+Hasher::Hasher(u64 hash_key, u32 lb, u32 lgb) : lambda_bar(lb), logb(lgb) {
+  // K_i = i-th output of SplitMix64 seeded with hash_key
+  k0 = mix64(hash_key + 1 * PEPSI_GOLDEN);
+  k1 = mix64(hash_key + 2 * PEPSI_GOLDEN);
+  k2 = mix64(hash_key + 3 * PEPSI_GOLDEN);
+  k3 = mix64(hash_key + 4 * PEPSI_GOLDEN);
+}
+void Hasher::operator()(u64 x, u64* xL, u32 bins[3]) const {
+  const u32 lam = lambda_bar + logb;
+  u64 hx = mix64(x ^ k0);
+  if (lam < 64) hx &= (1ull << lam) - 1;
+  const u64 xh = hx >> lambda_bar;
+  *xL = hx & ((1ull << lambda_bar) - 1);
+  const u64 bm = (1ull << logb) - 1;
+  bins[0] = (u32)(xh ^ (mix64(*xL ^ k1) & bm));
+  bins[1] = (u32)(xh ^ (mix64(*xL ^ k2) & bm));
+  bins[2] = (u32)(xh ^ (mix64(*xL ^ k3) & bm));
+}
+
+int cuckoo(const Hasher& H, const u64* items, size_t m, std::vector<u64>& table, std::vector<int32_t>& where) {
+  const u32 b = 1u << H.logb;
+  std::vector<int64_t> slot(b, -1);  // item index
+  std::vector<uint8_t> slot_h(b, 0);
+  std::vector<u64> xl(m);
+  std::vector<u32> bins(3 * m);
+  for (size_t u = 0; u < m; ++u) H(items[u], &xl[u], &bins[3 * u]);
+  for (size_t u = 0; u < m; ++u) {
+    int64_t cur = (int64_t)u;
+    int hidx = 0;
+    for (int evictions = 0;; ++evictions) {
+      const u32 bin = bins[3 * cur + hidx];
+      if (slot[bin] < 0) {
+        slot[bin] = cur;
+        slot_h[bin] = (uint8_t)hidx;
+        break;
+      }
+      if (evictions >= 1000) return PEPSI_E_CUCKOO_FAIL;
+      std::swap(slot[bin], cur);
+      int old_h = slot_h[bin];
+      slot_h[bin] = (uint8_t)hidx;
+      hidx = (old_h + 1) % 3;
+    }
+  }
+  table.assign(b, PEPSI_DUMMY);
+  where.assign(m, -1);
+  for (u32 i = 0; i < b; ++i)
+    if (slot[i] >= 0) {
+      table[i] = xl[slot[i]];
+      where[slot[i]] = (int32_t)i;
+    }
+  return 0;
+}
+
+int simple_hash(const Hasher& H, const u64* items, size_t n, u32 mu, std::vector<u64>& T, u32* max_load) {
+  const u32 b = 1u << H.logb;
+  std::vector<std::vector<u64>> bin(b);
+  std::vector<std::unordered_set<u64>> seen(b);
+  for (size_t u = 0; u < n; ++u) {
+    u64 xl;
+    u32 bs[3];
+    H(items[u], &xl, bs);
+    for (int i = 0; i < 3; ++i) {
+      if ((i > 0 && bs[i] == bs[0]) || (i > 1 && bs[i] == bs[1])) continue;
+      if (!seen[bs[i]].insert(xl).second) continue;
+      bin[bs[i]].push_back(xl);
+    }
+  }
+  u32 mx = 0;
+  for (u32 i = 0; i < b; ++i) mx = std::max<u32>(mx, (u32)bin[i].size());
+  if (max_load) *max_load = mx;
+  if (mx > mu) return PEPSI_E_BIN_OVERFLOW;
+  T.assign((size_t)mu * b, PEPSI_DUMMY);
+  for (u32 i = 0; i < b; ++i)
+    for (size_t l = 0; l < bin[i].size(); ++l) T[l * b + i] = bin[i][l];
+  return 0;
+}
+
+}  // namespace hostmath

@@ -1,0 +1,751 @@
+// Kernels of PEPSI's server evaluation (Algorithms 1, 2, 5) and the client
+// steps around it (Algorithms 3, 7), for sm_103a.  Integer work only: the
+// ciphertext arithmetic is 64-bit modular arithmetic on the CUDA cores.
+#include <cstdio>
+
+#include "kernels.h"
+#include "ntt_block.cuh"
+
+namespace {
+
+inline int ntt_threads(int N) {
+  int t = N / 2;
+  if (t > 512) t = 512;
+  if (t < 32) t = 32;
+  return t;
+}
+
+// ------------------------------------------------------------------ NTT
+template <bool FWD>
+__global__ void k_ntt(DevView V, const u64* __restrict__ src, u64* dst, int np, int p0, size_t src_os,
+                      size_t dst_os) {
+  extern __shared__ u64 sm[];
+  const int N = V.N;
+  const size_t r = blockIdx.x;
+  const int pl = (int)(r % np);
+  const size_t o = r / np;
+  const u64* s = src + o * src_os + (size_t)pl * N;
+  u64* d = dst + o * dst_os + (size_t)pl * N;
+  for (int x = threadIdx.x; x < N; x += blockDim.x) sm[x] = s[x];
+  __syncthreads();
+  if (FWD)
+    ntt_fwd_view(sm, V, p0 + pl);
+  else
+    ntt_inv_view(sm, V, p0 + pl);
+  for (int x = threadIdx.x; x < N; x += blockDim.x) d[x] = sm[x];
+}
+
+// ---------------------------------------------------------- CW unranking
+// v = sum_{r=1..h} C(c_r, r) with c_1 < ... < c_h (combinatorial number
+// system); binom[c*(h+1)+r] = C(c, r) for c <= ell.
+__global__ void k_cw_unrank(const u64* __restrict__ T, size_t count, const u64* __restrict__ binom, int ell, int h,
+                            uint16_t* pos) {
+  size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= count) return;
+  u64 v = T[i];
+  uint16_t* o = pos + i * h;
+  if (v == PEPSI_DUMMY) {
+    o[0] = PEPSI_CW_NONE;
+    return;
+  }
+  int hi = ell;  // exclusive upper bound for c_r
+  for (int r = h; r >= 1; --r) {
+    // largest c in [r-1, hi) with C(c, r) <= v
+    int lo = r - 1, up = hi - 1;
+    while (lo < up) {
+      int mid = (lo + up + 1) >> 1;
+      if (binom[(size_t)mid * (h + 1) + r] <= v)
+        lo = mid;
+      else
+        up = mid - 1;
+    }
+    o[r - 1] = (uint16_t)lo;
+    v -= binom[(size_t)lo * (h + 1) + r];
+    hi = lo;
+  }
+}
+
+// ------------------------------------------------- server plaintexts (K3)
+// Block (layer l, j-chunk): bit planes of the layer's codewords, encoded
+// (inverse NTT mod t of the slot vector in bit-reversed order), centred
+// lift into each q_p and forward NTT.
+__global__ void k_ptgen(DevView V, const uint16_t* __restrict__ pos, int ell, int h, int JC, u64* P) {
+  extern __shared__ u64 sm[];
+  const int N = V.N, k = V.k;
+  const int words = N / 32 > 0 ? N / 32 : 1;
+  u64* poly = sm;                                  // N u64
+  u32* mbuf = reinterpret_cast<u32*>(sm + N);      // N u32
+  u32* bits = mbuf + N;                            // JC * words u32
+  const int l = blockIdx.y;
+  const int j0 = blockIdx.x * JC;
+  for (int x = threadIdx.x; x < JC * words; x += blockDim.x) bits[x] = 0;
+  __syncthreads();
+  const uint16_t* lp = pos + (size_t)l * N * h;
+  for (int s = threadIdx.x; s < N; s += blockDim.x) {
+    const uint16_t* ps = lp + (size_t)s * h;
+    if (ps[0] == PEPSI_CW_NONE) continue;
+    for (int r = 0; r < h; ++r) {
+      int c = (int)ps[r] - j0;
+      if (c >= 0 && c < JC) atomicOr(&bits[c * words + (s >> 5)], 1u << (s & 31));
+    }
+  }
+  __syncthreads();
+  const DevPrime Pt = V.pr[V.tidx];
+  const u64 t = Pt.q, thalf = t >> 1;
+  for (int jj = 0; jj < JC; ++jj) {
+    const int j = j0 + jj;
+    if (j >= ell) break;
+    for (int i = threadIdx.x; i < N; i += blockDim.x) {
+      u32 s = brev_bits(i, V.logN);
+      poly[i] = (bits[jj * words + (s >> 5)] >> (s & 31)) & 1u;
+    }
+    __syncthreads();
+    ntt_inv_view(poly, V, V.tidx);
+    for (int i = threadIdx.x; i < N; i += blockDim.x) mbuf[i] = (u32)poly[i];
+    __syncthreads();
+    for (int p = 0; p < k; ++p) {
+      const u64 q = V.pr[p].q;
+      for (int i = threadIdx.x; i < N; i += blockDim.x) {
+        u64 m = mbuf[i];
+        poly[i] = m <= thalf ? m : q - (t - m);
+      }
+      __syncthreads();
+      ntt_fwd_view(poly, V, p);
+      u64* out = P + (((size_t)l * ell + j) * k + p) * N;
+      for (int i = threadIdx.x; i < N; i += blockDim.x) out[i] = poly[i];
+      __syncthreads();
+    }
+  }
+}
+
+// ------------------------------------------------------- fused MAC (K4)
+// One thread per (prime, point) and LB layers: a 128-bit lazy sum over the
+// ell codeword-bit ciphertexts, one Barrett reduction at the end.
+template <int LB>
+__global__ void __launch_bounds__(256) k_mac(DevView V, const u64* __restrict__ C, const u64* __restrict__ P,
+                                             u64* __restrict__ H, int ell, int L) {
+  const int N = V.N, k = V.k;
+  const size_t kn = (size_t)k * N;
+  const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= kn) return;
+  const int l0 = blockIdx.y * LB;
+  const int nl = min(LB, L - l0);
+  u64 a0l[LB], a0h[LB], a1l[LB], a1h[LB];
+#pragma unroll
+  for (int l = 0; l < LB; ++l) a0l[l] = a0h[l] = a1l[l] = a1h[l] = 0;
+  const u64* c = C + idx;
+  const u64* p = P + (size_t)l0 * ell * kn + idx;
+  const size_t pstride = (size_t)ell * kn;
+  for (int j = 0; j < ell; ++j) {
+    const u64 c0 = __ldg(c + (size_t)j * 2 * kn);
+    const u64 c1 = __ldg(c + (size_t)j * 2 * kn + kn);
+#pragma unroll
+    for (int l = 0; l < LB; ++l) {
+      if (l < nl) {
+        const u64 x = __ldcs(p + l * pstride + (size_t)j * kn);
+        mac128(a0l[l], a0h[l], c0, x);
+        mac128(a1l[l], a1h[l], c1, x);
+      }
+    }
+  }
+  const int pi = (int)(idx / N);
+  const DevPrime pr = V.pr[pi];
+#pragma unroll
+  for (int l = 0; l < LB; ++l) {
+    if (l < nl) {
+      u64* h = H + (size_t)(l0 + l) * 2 * kn + idx;
+      h[0] = barrett128(a0h[l], a0l[l], pr.q, pr.bhi, pr.blo);
+      h[kn] = barrett128(a1h[l], a1l[l], pr.q, pr.bhi, pr.blo);
+    }
+  }
+}
+
+// ---------------------------------------------------- RNS conversions
+// Garner mixed-radix digits over Q of residues x[0..k).
+__device__ __forceinline__ void garner_q(const DevView& V, const u64* x, u64* v) {
+  const RnsConst* rc = V.rc;
+#pragma unroll
+  for (int i = 0; i < PEPSI_MAXQ; ++i) {
+    if (i < V.k) {
+      const DevPrime pi = V.pr[i];
+      u64 acc = x[i];
+#pragma unroll
+      for (int j = 0; j < PEPSI_MAXQ; ++j) {
+        if (j < i) {
+          u64 vj = v[j] >= pi.q ? barrett64(v[j], pi) : v[j];
+          acc = submod(acc, vj, pi.q);
+          acc = shoup(acc, rc->cq[i][j], rc->cqs[i][j], pi.q);
+        }
+      }
+      v[i] = acc;
+    }
+  }
+}
+// Garner mixed-radix digits over B of residues y[0..kb).
+__device__ __forceinline__ void garner_b(const DevView& V, const u64* y, u64* u) {
+  const RnsConst* rc = V.rc;
+#pragma unroll
+  for (int i = 0; i < PEPSI_MAXB; ++i) {
+    if (i < V.kb) {
+      const DevPrime pi = V.pr[V.k + i];
+      u64 acc = y[i];
+#pragma unroll
+      for (int j = 0; j < PEPSI_MAXB; ++j) {
+        if (j < i) {
+          u64 uj = u[j] >= pi.q ? barrett64(u[j], pi) : u[j];
+          acc = submod(acc, uj, pi.q);
+          acc = shoup(acc, rc->cb[i][j], rc->cbs[i][j], pi.q);
+        }
+      }
+      u[i] = acc;
+    }
+  }
+}
+// true when the mixed-radix number v (n digits) exceeds the digits h
+__device__ __forceinline__ bool digits_greater(const u64* v, const u64* h, int n) {
+  for (int i = n - 1; i >= 0; --i)
+    if (v[i] != h[i]) return v[i] > h[i];
+  return false;
+}
+// centred value of Q-digits v reduced mod B prime j
+__device__ __forceinline__ u64 q_digits_mod_b(const DevView& V, const u64* v, bool neg, int j) {
+  const DevPrime pb = V.pr[V.k + j];
+  u64 lo = 0, hi = 0;
+#pragma unroll
+  for (int l = 0; l < PEPSI_MAXQ; ++l)
+    if (l < V.k) mac128(lo, hi, v[l], V.rc->pqb[j][l]);
+  u64 r = barrett128(hi, lo, pb.q, pb.bhi, pb.blo);
+  return neg ? submod(r, V.rc->qmodb[j], pb.q) : r;
+}
+
+__global__ void k_lift(DevView V, const u64* __restrict__ src, u64* __restrict__ dstB, int L,
+                       const u64* __restrict__ cst, u64* __restrict__ side) {
+  const int N = V.N, k = V.k, kb = V.kb;
+  const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;  // over L*2*N
+  if (idx >= (size_t)L * 2 * N) return;
+  const int n = (int)(idx % N);
+  const size_t lc = idx / N;  // layer*2 + comp
+  u64 x[PEPSI_MAXQ], v[PEPSI_MAXQ];
+#pragma unroll
+  for (int i = 0; i < PEPSI_MAXQ; ++i)
+    if (i < k) x[i] = src[(lc * k + i) * N + n];
+  garner_q(V, x, v);
+  const bool neg = digits_greater(v, V.rc->qhalf_dig, k);
+  u64 base[PEPSI_MAXB];
+#pragma unroll
+  for (int j = 0; j < PEPSI_MAXB; ++j)
+    if (j < kb) {
+      base[j] = q_digits_mod_b(V, v, neg, j);
+      dstB[(lc * kb + j) * N + n] = base[j];
+    }
+  if (cst != nullptr && n == 0 && (lc & 1) == 0) {
+    // lift of (x + cst) mod Q at coefficient 0 of component 0
+#pragma unroll
+    for (int i = 0; i < PEPSI_MAXQ; ++i)
+      if (i < k) x[i] = addmod(x[i], cst[i], V.pr[i].q);
+    garner_q(V, x, v);
+    const bool neg2 = digits_greater(v, V.rc->qhalf_dig, k);
+    const size_t layer = lc >> 1;
+#pragma unroll
+    for (int j = 0; j < PEPSI_MAXB; ++j)
+      if (j < kb) side[layer * kb + j] = submod(q_digits_mod_b(V, v, neg2, j), base[j], V.pr[k + j].q);
+  }
+}
+
+// ------------------------------------------------------------ tensor
+__global__ void k_tensor(DevView V, const u64* __restrict__ AQ, const u64* __restrict__ AB,
+                         const u64* __restrict__ BQ, const u64* __restrict__ BB, const u64* __restrict__ cstQ,
+                         const u64* __restrict__ side, u64* __restrict__ T3, int L, int square) {
+  const int N = V.N, k = V.k, kb = V.kb, np = k + kb;
+  const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;  // over L*np*N
+  if (idx >= (size_t)L * np * N) return;
+  const int n = (int)(idx % N);
+  const int pi = (int)((idx / N) % np);
+  const size_t l = idx / ((size_t)N * np);
+  const DevPrime pr = V.pr[pi];
+  const u64* A;
+  const u64* Bp;
+  size_t o0, o1;
+  if (pi < k) {
+    A = AQ;
+    Bp = BQ;
+    o0 = ((l * 2 + 0) * k + pi) * N + n;
+    o1 = ((l * 2 + 1) * k + pi) * N + n;
+  } else {
+    A = AB;
+    Bp = BB;
+    o0 = ((l * 2 + 0) * kb + (pi - k)) * N + n;
+    o1 = ((l * 2 + 1) * kb + (pi - k)) * N + n;
+  }
+  const u64 a0 = A[o0], a1 = A[o1];
+  u64 d0, d1, d2;
+  if (square) {
+    d0 = mulmod(a0, a0, pr);
+    const u64 m = mulmod(a0, a1, pr);
+    d1 = addmod(m, m, pr.q);
+    d2 = mulmod(a1, a1, pr);
+  } else {
+    u64 b0 = Bp[o0];
+    const u64 b1 = Bp[o1];
+    if (pi < k) {
+      if (cstQ) b0 = addmod(b0, cstQ[pi], pr.q);
+    } else if (side) {
+      b0 = addmod(b0, side[l * kb + (pi - k)], pr.q);
+    }
+    d0 = mulmod(a0, b0, pr);
+    u64 lo = 0, hi = 0;
+    mac128(lo, hi, a0, b1);
+    mac128(lo, hi, a1, b0);
+    d1 = barrett128(hi, lo, pr.q, pr.bhi, pr.blo);
+    d2 = mulmod(a1, b1, pr);
+  }
+  const size_t rs = (size_t)N;
+  u64* o = T3 + ((l * 3) * np + pi) * rs + n;
+  o[0] = d0;
+  o[(size_t)np * rs] = d1;
+  o[(size_t)2 * np * rs] = d2;
+}
+
+// ------------------------------------------------------ scale and round
+// y = round(t x / Q) exactly: z = t x + (Q-1)/2, [z]_Q from the Q residues
+// by Garner, y = (z - [z]_Q) / Q computed in B, y centred in B and mapped
+// back to Q by Garner over B.
+__global__ void k_scale_round(DevView V, const u64* __restrict__ T3, u64* __restrict__ D, int L) {
+  const int N = V.N, k = V.k, kb = V.kb, np = k + kb;
+  const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;  // over L*3*N
+  if (idx >= (size_t)L * 3 * N) return;
+  const int n = (int)(idx % N);
+  const size_t lc = idx / N;
+  const RnsConst* rc = V.rc;
+  const u64* in = T3 + lc * np * N + n;
+  u64 z[PEPSI_MAXQ], v[PEPSI_MAXQ];
+#pragma unroll
+  for (int i = 0; i < PEPSI_MAXQ; ++i)
+    if (i < k) {
+      const u64 q = V.pr[i].q;
+      z[i] = addmod(shoup(in[(size_t)i * N], rc->t_q[i], rc->t_qs[i], q), rc->qhalf_q[i], q);
+    }
+  garner_q(V, z, v);
+  u64 y[PEPSI_MAXB], u[PEPSI_MAXB];
+#pragma unroll
+  for (int j = 0; j < PEPSI_MAXB; ++j)
+    if (j < kb) {
+      const DevPrime pb = V.pr[k + j];
+      const u64 zb = addmod(shoup(in[(size_t)(k + j) * N], rc->t_b[j], rc->t_bs[j], pb.q), rc->qhalf_b[j], pb.q);
+      const u64 zq = q_digits_mod_b(V, v, false, j);
+      y[j] = shoup(submod(zb, zq, pb.q), rc->qinv_b[j], rc->qinv_bs[j], pb.q);
+    }
+  garner_b(V, y, u);
+  const bool neg = digits_greater(u, rc->bhalf_dig, kb);
+  u64* out = D + lc * k * N + n;
+#pragma unroll
+  for (int i = 0; i < PEPSI_MAXQ; ++i)
+    if (i < k) {
+      const DevPrime pq = V.pr[i];
+      u64 lo = 0, hi = 0;
+#pragma unroll
+      for (int j = 0; j < PEPSI_MAXB; ++j)
+        if (j < kb) mac128(lo, hi, u[j], rc->pbq[i][j]);
+      u64 r = barrett128(hi, lo, pq.q, pq.bhi, pq.blo);
+      out[(size_t)i * N] = neg ? submod(r, rc->bmodq[i], pq.q) : r;
+    }
+}
+
+// ---------------------------------------------------------- relinearise
+// Phase 1, block per row of DG[L][k+2][k][N]: row (l, i, j) holds
+// NTT_{q_j}([d2]_{q_i}) for digits i < k, and NTT_{q_j}(d0), NTT_{q_j}(d1)
+// for i = k, k+1.
+__global__ void k_relin_ntt(DevView V, const u64* __restrict__ D, u64* __restrict__ DG) {
+  extern __shared__ u64 sm[];
+  const int N = V.N, k = V.k;
+  const size_t r = blockIdx.x;
+  const int j = (int)(r % k);
+  const int i = (int)((r / k) % (k + 2));
+  const size_t l = r / ((size_t)k * (k + 2));
+  const DevPrime pj = V.pr[j];
+  const u64* row = i < k ? D + ((l * 3 + 2) * k + i) * N : D + ((l * 3 + (i - k)) * k + j) * N;
+  for (int x = threadIdx.x; x < N; x += blockDim.x) {
+    const u64 w = row[x];
+    sm[x] = w >= pj.q ? barrett64(w, pj) : w;
+  }
+  __syncthreads();
+  ntt_fwd_view(sm, V, j);
+  u64* out = DG + r * N;
+  for (int x = threadIdx.x; x < N; x += blockDim.x) out[x] = sm[x];
+}
+// Phase 2, thread per (l, j, n): R_c = NTT(d_c) + sum_i NTT(d_i) * rlk_i[c],
+// 128-bit lazy sums, one Barrett reduction per output.
+__global__ void k_relin_mac(DevView V, const u64* __restrict__ DG, const u64* __restrict__ rlk, u64* __restrict__ R,
+                            int L) {
+  const int N = V.N, k = V.k;
+  const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;  // over L*k*N
+  if (idx >= (size_t)L * k * N) return;
+  const int n = (int)(idx % N);
+  const int j = (int)((idx / N) % k);
+  const size_t l = idx / ((size_t)k * N);
+  const DevPrime pj = V.pr[j];
+  const u64* g = DG + l * (k + 2) * k * N + (size_t)j * N + n;
+  const size_t gs = (size_t)k * N;
+  u64 lo0 = g[(size_t)k * gs], hi0 = 0, lo1 = g[(size_t)(k + 1) * gs], hi1 = 0;
+  for (int i = 0; i < k; ++i) {
+    const u64 d = g[(size_t)i * gs];
+    mac128(lo0, hi0, d, __ldg(rlk + (((size_t)i * 2 + 0) * k + j) * N + n));
+    mac128(lo1, hi1, d, __ldg(rlk + (((size_t)i * 2 + 1) * k + j) * N + n));
+  }
+  u64* o = R + ((l * 2) * k + j) * N + n;
+  o[0] = barrett128(hi0, lo0, pj.q, pj.bhi, pj.blo);
+  o[(size_t)k * N] = barrett128(hi1, lo1, pj.q, pj.bhi, pj.blo);
+}
+
+// ------------------------------------------------------------ pointwise
+__global__ void k_axpy(DevView V, const u64* __restrict__ a, const u64* __restrict__ zres, const u64* __restrict__ b,
+                       u64* out, size_t total) {
+  const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= total) return;
+  const int p = (int)((idx / V.N) % V.k);
+  const DevPrime pr = V.pr[p];
+  out[idx] = addmod(a[idx], mulmod(zres[p], b[idx], pr), pr.q);
+}
+
+__global__ void k_accum(DevView V, const u64* __restrict__ D, int L, u64* acc, int init) {
+  const size_t per = (size_t)3 * V.k * V.N;
+  const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= per) return;
+  const u64 q = V.pr[(idx / V.N) % V.k].q;
+  u64 s = init ? 0 : acc[idx];
+  for (int l = 0; l < L; ++l) s = addmod(s, D[(size_t)l * per + idx], q);
+  acc[idx] = s;
+}
+
+// ---------------------------------------------------------------- client
+// round(Q m / t) mod q_p for m in [0, t): floor(Q/t) m + round((Q mod t) m / t)
+__device__ __forceinline__ u64 delta_of(const DevView& V, u64 m, int p, u64 t) {
+  const DevPrime pq = V.pr[p];
+  const u64 a = shoup(m, V.rc->qdt_q[p], V.rc->qdt_qs[p], pq.q);
+  const u64 b = (V.rc->qmt * m + (t - 1) / 2) / t;
+  return addmod(a, b % pq.q, pq.q);
+}
+__device__ __forceinline__ u64 smod_dev(i64 v, u64 q) { return v >= 0 ? (u64)v : q - (u64)(-v); }
+
+// Block per ciphertext j: encode bit plane j, then for each prime sample
+// a, compute c0 = e - a s + round(Q m / t), c1 = a (coefficient form).
+__global__ void k_encrypt(DevView V, const uint16_t* __restrict__ pos, int h, const u64* __restrict__ s_ntt, u64 seed,
+                          u64* cts) {
+  extern __shared__ u64 sm[];
+  const int N = V.N, k = V.k, j = blockIdx.x;
+  u64* poly = sm;
+  u32* mbuf = reinterpret_cast<u32*>(sm + N);
+  const u64 t = V.pr[V.tidx].q;
+  for (int i = threadIdx.x; i < N; i += blockDim.x) {
+    const int s = (int)brev_bits(i, V.logN);
+    const uint16_t* ps = pos + (size_t)s * h;
+    u64 bit = 0;
+    if (ps[0] != PEPSI_CW_NONE)
+      for (int r = 0; r < h; ++r) bit |= (ps[r] == j);
+    poly[i] = bit;
+  }
+  __syncthreads();
+  ntt_inv_view(poly, V, V.tidx);
+  for (int i = threadIdx.x; i < N; i += blockDim.x) mbuf[i] = (u32)poly[i];
+  __syncthreads();
+  const u64 key_e = stream_key(seed, make_stream(STREAM_ENC_E, j, 0));
+  for (int p = 0; p < k; ++p) {
+    const DevPrime pq = V.pr[p];
+    const u64 key_a = stream_key(seed, make_stream(STREAM_ENC_A, j, p));
+    u64* c0 = cts + (((size_t)j * 2 + 0) * k + p) * N;
+    u64* c1 = cts + (((size_t)j * 2 + 1) * k + p) * N;
+    for (int i = threadIdx.x; i < N; i += blockDim.x) {
+      const u64 a = sample_uniform(key_a, i, pq.q);
+      c1[i] = a;
+      poly[i] = a;
+    }
+    __syncthreads();
+    ntt_fwd_view(poly, V, p);
+    const u64* sr = s_ntt + (size_t)p * N;
+    for (int i = threadIdx.x; i < N; i += blockDim.x) poly[i] = mulmod(poly[i], sr[i], pq);
+    __syncthreads();
+    ntt_inv_view(poly, V, p);
+    for (int i = threadIdx.x; i < N; i += blockDim.x) {
+      const u64 e = smod_dev(sample_cbd21(key_e, i), pq.q);
+      c0[i] = addmod(submod(e, poly[i], pq.q), delta_of(V, mbuf[i], p, t), pq.q);
+    }
+    __syncthreads();
+  }
+}
+
+__global__ void k_keygen_s(DevView V, u64 seed, int8_t* s) {
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= V.N) return;
+  const u64 key = stream_key(seed, make_stream(STREAM_SK, 0, 0));
+  s[n] = (int8_t)((int)sample_uniform(key, n, 3) - 1);
+}
+__global__ void k_keygen_sntt(DevView V, const int8_t* __restrict__ s, u64* s_ntt) {
+  extern __shared__ u64 sm[];
+  const int p = blockIdx.x, N = V.N;
+  const u64 q = V.pr[p].q;
+  for (int i = threadIdx.x; i < N; i += blockDim.x) sm[i] = smod_dev(s[i], q);
+  __syncthreads();
+  ntt_fwd_view(sm, V, p);
+  for (int i = threadIdx.x; i < N; i += blockDim.x) s_ntt[(size_t)p * N + i] = sm[i];
+}
+// Block (digit i, prime j): rlk_i = (-a_i s + e_i + g_i s^2, a_i) in NTT form,
+// g_i = 1 mod q_i and 0 mod q_j for j != i.
+__global__ void k_keygen_rlk(DevView V, u64 seed, const u64* __restrict__ s_ntt, u64* rlk) {
+  extern __shared__ u64 sm[];
+  const int N = V.N, k = V.k;
+  const int i = blockIdx.x / k, j = blockIdx.x % k;
+  const DevPrime pj = V.pr[j];
+  u64* r0 = rlk + (((size_t)i * 2 + 0) * k + j) * N;
+  u64* r1 = rlk + (((size_t)i * 2 + 1) * k + j) * N;
+  const u64 key_e = stream_key(seed, make_stream(STREAM_RLK_E, i, 0));
+  const u64 key_a = stream_key(seed, make_stream(STREAM_RLK_A, i, j));
+  for (int x = threadIdx.x; x < N; x += blockDim.x) sm[x] = smod_dev(sample_cbd21(key_e, x), pj.q);
+  __syncthreads();
+  ntt_fwd_view(sm, V, j);
+  for (int x = threadIdx.x; x < N; x += blockDim.x) r0[x] = sm[x];
+  __syncthreads();
+  for (int x = threadIdx.x; x < N; x += blockDim.x) sm[x] = sample_uniform(key_a, x, pj.q);
+  __syncthreads();
+  ntt_fwd_view(sm, V, j);
+  const u64* sr = s_ntt + (size_t)j * N;
+  for (int x = threadIdx.x; x < N; x += blockDim.x) {
+    const u64 a = sm[x], sv = sr[x];
+    u64 v = submod(r0[x], mulmod(a, sv, pj), pj.q);
+    if (i == j) v = addmod(v, mulmod(sv, sv, pj), pj.q);
+    r0[x] = v;
+    r1[x] = a;
+  }
+}
+
+// Decryption, step 1: z = c0 + c1 s per prime (coefficient form).
+__global__ void k_dec_z(DevView V, const u64* __restrict__ ct, const u64* __restrict__ s_ntt, u64* z) {
+  extern __shared__ u64 sm[];
+  const int p = blockIdx.x, N = V.N, k = V.k;
+  const DevPrime pq = V.pr[p];
+  const u64* c1 = ct + ((size_t)k + p) * N;
+  for (int i = threadIdx.x; i < N; i += blockDim.x) sm[i] = c1[i];
+  __syncthreads();
+  ntt_fwd_view(sm, V, p);
+  for (int i = threadIdx.x; i < N; i += blockDim.x) sm[i] = mulmod(sm[i], s_ntt[(size_t)p * N + i], pq);
+  __syncthreads();
+  ntt_inv_view(sm, V, p);
+  for (int i = threadIdx.x; i < N; i += blockDim.x) z[(size_t)p * N + i] = addmod(sm[i], ct[(size_t)p * N + i], pq.q);
+}
+// Step 2, per coefficient: m = round(t z / Q) mod t exactly (Garner of
+// w = t z + (Q-1)/2 over Q, then (w - [w]_Q)/Q mod t), and the noise
+// |[t z]_Q| (centred) as a double, maximised over coefficients.
+__global__ void k_dec_coef(DevView V, const u64* __restrict__ z, u32* m, unsigned long long* maxr) {
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  const int N = V.N, k = V.k;
+  const RnsConst* rc = V.rc;
+  const u64 t = V.pr[V.tidx].q;
+  double rabs = 0.0;
+  if (n < N) {
+    u64 w[PEPSI_MAXQ], v[PEPSI_MAXQ];
+#pragma unroll
+    for (int i = 0; i < PEPSI_MAXQ; ++i)
+      if (i < k) {
+        const u64 q = V.pr[i].q;
+        w[i] = addmod(shoup(z[(size_t)i * N + n], rc->t_q[i], rc->t_qs[i], q), rc->qhalf_q[i], q);
+      }
+    garner_q(V, w, v);
+    u64 wq = 0;
+    for (int l = 0; l < k; ++l) wq = (wq + (v[l] % t) * rc->pq_t[l]) % t;
+    m[n] = (u32)(((rc->qhalf_t + t - wq) % t) * rc->qinv_t % t);
+#pragma unroll
+    for (int i = 0; i < PEPSI_MAXQ; ++i)
+      if (i < k) w[i] = shoup(z[(size_t)i * N + n], rc->t_q[i], rc->t_qs[i], V.pr[i].q);
+    garner_q(V, w, v);
+    if (digits_greater(v, rc->qhalf_dig, k)) {
+#pragma unroll
+      for (int i = 0; i < PEPSI_MAXQ; ++i)
+        if (i < k) w[i] = w[i] ? V.pr[i].q - w[i] : 0;
+      garner_q(V, w, v);
+    }
+    for (int l = 0; l < k; ++l) rabs += (double)v[l] * rc->pq_d[l];
+  }
+  // block max, then one atomic per block (positive doubles order like u64)
+  __shared__ double red[32];
+  for (int o = 16; o > 0; o >>= 1) rabs = fmax(rabs, __shfl_down_sync(0xffffffffu, rabs, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = rabs;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double b = 0.0;
+    for (int i = 0; i < (int)(blockDim.x + 31) / 32; ++i) b = fmax(b, red[i]);
+    atomicMax(maxr, (unsigned long long)__double_as_longlong(b));
+  }
+}
+// Step 3: slots = values of m at psi_t^(2s+1): forward NTT mod t, slot s in position brev(s).
+__global__ void k_dec_slots(DevView V, const u32* __restrict__ m, u32* slots) {
+  extern __shared__ u64 sm[];
+  const int N = V.N;
+  for (int i = threadIdx.x; i < N; i += blockDim.x) sm[i] = m[i];
+  __syncthreads();
+  ntt_fwd_view(sm, V, V.tidx);
+  for (int s = threadIdx.x; s < N; s += blockDim.x) slots[s] = (u32)sm[brev_bits(s, V.logN)];
+}
+
+// Cardinality mask (Algorithm 5): r_s uniform in Z_t for s < N-1,
+// r_{N-1} = -sum; c0 += round(Q Encode(r) / t).  One block.
+__global__ void k_mask(DevView V, u64 seed, u64* ct) {
+  extern __shared__ u64 sm[];
+  __shared__ u64 red[32];
+  const int N = V.N, k = V.k;
+  const u64 t = V.pr[V.tidx].q;
+  const u64 key = stream_key(seed, make_stream(STREAM_MASK, 0, 0));
+  u64 part = 0;
+  for (int s = threadIdx.x; s < N - 1; s += blockDim.x) {
+    const u64 r = sample_uniform(key, s, t);
+    sm[brev_bits(s, V.logN)] = r;
+    part += r;
+  }
+  part %= t;
+  for (int o = 16; o > 0; o >>= 1) part += __shfl_down_sync(0xffffffffu, part, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = part % t;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    u64 sum = 0;
+    for (int i = 0; i < (int)(blockDim.x + 31) / 32; ++i) sum = (sum + red[i]) % t;
+    sm[brev_bits(N - 1, V.logN)] = (t - sum) % t;
+  }
+  __syncthreads();
+  ntt_inv_view(sm, V, V.tidx);
+  for (int p = 0; p < k; ++p) {
+    const u64 q = V.pr[p].q;
+    for (int n = threadIdx.x; n < N; n += blockDim.x) {
+      u64* c = ct + (size_t)p * N + n;
+      *c = addmod(*c, delta_of(V, sm[n], p, t), q);
+    }
+  }
+}
+
+inline unsigned grid_for(size_t total, int threads) { return (unsigned)((total + threads - 1) / threads); }
+
+}  // namespace
+
+// ------------------------------------------------------------ launchers
+void launch_ntt(const DevView& V, bool fwd, const u64* src, u64* dst, size_t outer, int np, int p0, size_t src_os,
+                size_t dst_os, cudaStream_t st) {
+  const size_t rows = outer * (size_t)np;
+  if (!rows) return;
+  const size_t smem = (size_t)V.N * sizeof(u64);
+  if (fwd)
+    k_ntt<true><<<(unsigned)rows, ntt_threads(V.N), smem, st>>>(V, src, dst, np, p0, src_os, dst_os);
+  else
+    k_ntt<false><<<(unsigned)rows, ntt_threads(V.N), smem, st>>>(V, src, dst, np, p0, src_os, dst_os);
+}
+
+void launch_cw_unrank(const u64* T, size_t count, const u64* binom, int ell, int h, uint16_t* pos, cudaStream_t st) {
+  if (!count) return;
+  k_cw_unrank<<<grid_for(count, 256), 256, 0, st>>>(T, count, binom, ell, h, pos);
+}
+
+static int ptgen_jc(int N) { return N >= 16384 ? 8 : 32; }
+static size_t ptgen_smem(int N) {
+  const int words = N / 32 > 0 ? N / 32 : 1;
+  return (size_t)N * 8 + (size_t)N * 4 + (size_t)ptgen_jc(N) * words * 4;
+}
+
+void launch_ptgen(const DevView& V, const uint16_t* pos, int L, int ell, int h, u64* P, cudaStream_t st) {
+  if (L <= 0) return;
+  const int JC = ptgen_jc(V.N);
+  dim3 grid((ell + JC - 1) / JC, L);
+  k_ptgen<<<grid, ntt_threads(V.N), ptgen_smem(V.N), st>>>(V, pos, ell, h, JC, P);
+}
+
+void launch_mac(const DevView& V, const u64* C, const u64* P, u64* H, int ell, int L, cudaStream_t st) {
+  if (L <= 0) return;
+  constexpr int LB = 4;
+  dim3 grid(grid_for((size_t)V.k * V.N, 256), (L + LB - 1) / LB);
+  k_mac<LB><<<grid, 256, 0, st>>>(V, C, P, H, ell, L);
+}
+
+void launch_lift(const DevView& V, const u64* src, u64* dstB, int L, const u64* cst, u64* side, cudaStream_t st) {
+  const size_t total = (size_t)L * 2 * V.N;
+  if (!total) return;
+  k_lift<<<grid_for(total, 128), 128, 0, st>>>(V, src, dstB, L, cst, side);
+}
+
+void launch_tensor(const DevView& V, const u64* AQ, const u64* AB, const u64* BQ, const u64* BB, const u64* cstQ,
+                   const u64* side, u64* T3, int L, bool square, cudaStream_t st) {
+  const size_t total = (size_t)L * (V.k + V.kb) * V.N;
+  if (!total) return;
+  k_tensor<<<grid_for(total, 256), 256, 0, st>>>(V, AQ, AB, BQ, BB, cstQ, side, T3, L, square ? 1 : 0);
+}
+
+void launch_scale_round(const DevView& V, const u64* T3, u64* D, int L, cudaStream_t st) {
+  const size_t total = (size_t)L * 3 * V.N;
+  if (!total) return;
+  k_scale_round<<<grid_for(total, 128), 128, 0, st>>>(V, T3, D, L);
+}
+
+void launch_relin(const DevView& V, const u64* D, const u64* rlk, u64* DG, u64* R, int L, cudaStream_t st) {
+  if (L <= 0) return;
+  const size_t rows = (size_t)L * (V.k + 2) * V.k;
+  k_relin_ntt<<<(unsigned)rows, ntt_threads(V.N), (size_t)V.N * 8, st>>>(V, D, DG);
+  k_relin_mac<<<grid_for((size_t)L * V.k * V.N, 256), 256, 0, st>>>(V, DG, rlk, R, L);
+}
+
+void launch_axpy(const DevView& V, const u64* a, const u64* zres, const u64* b, u64* out, size_t groups,
+                 cudaStream_t st) {
+  const size_t total = groups * V.k * V.N;
+  if (!total) return;
+  k_axpy<<<grid_for(total, 256), 256, 0, st>>>(V, a, zres, b, out, total);
+}
+
+void launch_accum(const DevView& V, const u64* D, int L, u64* acc, bool init, cudaStream_t st) {
+  const size_t total = (size_t)3 * V.k * V.N;
+  k_accum<<<grid_for(total, 256), 256, 0, st>>>(V, D, L, acc, init ? 1 : 0);
+}
+
+void launch_encrypt(const DevView& V, const uint16_t* pos, int ell, int h, const u64* s_ntt, u64 seed, u64* cts,
+                    cudaStream_t st) {
+  if (ell <= 0) return;
+  k_encrypt<<<ell, ntt_threads(V.N), (size_t)V.N * 12, st>>>(V, pos, h, s_ntt, seed, cts);
+}
+
+void launch_keygen(const DevView& V, u64 seed, int8_t* s, u64* s_ntt, u64* rlk, cudaStream_t st) {
+  k_keygen_s<<<grid_for(V.N, 256), 256, 0, st>>>(V, seed, s);
+  k_keygen_sntt<<<V.k, ntt_threads(V.N), (size_t)V.N * 8, st>>>(V, s, s_ntt);
+  k_keygen_rlk<<<V.k * V.k, ntt_threads(V.N), (size_t)V.N * 8, st>>>(V, seed, s_ntt, rlk);
+}
+
+void launch_decrypt(const DevView& V, const u64* ct, const u64* s_ntt, u64* zbuf, u32* mbuf, u32* slots,
+                    unsigned long long* maxr, cudaStream_t st) {
+  cudaMemsetAsync(maxr, 0, sizeof(unsigned long long), st);
+  k_dec_z<<<V.k, ntt_threads(V.N), (size_t)V.N * 8, st>>>(V, ct, s_ntt, zbuf);
+  k_dec_coef<<<grid_for(V.N, 128), 128, 0, st>>>(V, zbuf, mbuf, maxr);
+  k_dec_slots<<<1, ntt_threads(V.N), (size_t)V.N * 8, st>>>(V, mbuf, slots);
+}
+
+void launch_mask(const DevView& V, u64 seed, u64* ct, cudaStream_t st) {
+  k_mask<<<1, 512, (size_t)V.N * 8, st>>>(V, seed, ct);
+}
+
+cudaError_t kernels_init(int N) {
+  int dev = 0, optin = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (e != cudaSuccess) return e;
+  // largest request: the plaintext generator at this N
+  if ((size_t)optin < ptgen_smem(N) || (size_t)optin < (size_t)N * 12) return cudaErrorInvalidValue;
+  // dynamic + static shared memory of a block must stay within the opt-in limit
+  auto set = [&](const void* f) {
+    cudaFuncAttributes fa;
+    cudaError_t r = cudaFuncGetAttributes(&fa, f);
+    if (r == cudaSuccess)
+      r = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes);
+    if (r != cudaSuccess && e == cudaSuccess) e = r;
+  };
+  set((const void*)k_ntt<true>);
+  set((const void*)k_ntt<false>);
+  set((const void*)k_ptgen);
+  set((const void*)k_relin_ntt);
+  set((const void*)k_encrypt);
+  set((const void*)k_keygen_sntt);
+  set((const void*)k_keygen_rlk);
+  set((const void*)k_dec_z);
+  set((const void*)k_dec_slots);
+  set((const void*)k_mask);
+  return e;
+}

@@ -1,0 +1,60 @@
+// Launch wrappers of the PEPSI kernels (host side).  All launches are
+// asynchronous on the given stream; errors surface through
+// cudaGetLastError() / the next synchronising call.
+#pragma once
+#include "common.cuh"
+
+// Batched NTT over rows laid out [outer][np][N]: row r uses prime p0 + (r % np);
+// src and dst may alias (in place).  fwd: coefficient -> evaluation form.
+void launch_ntt(const DevView& V, bool fwd, const u64* src, u64* dst, size_t outer, int np, int p0, size_t src_os,
+                size_t dst_os, cudaStream_t st);
+
+// CW-Encode of table entries (colex rank -> positions), pos[count][h], dummy -> PEPSI_CW_NONE.
+void launch_cw_unrank(const u64* T, size_t count, const u64* binom, int ell, int h, uint16_t* pos, cudaStream_t st);
+
+// Server plaintexts pt_s[l][j] in NTT form for L layers: P[L][ell][k][N].
+void launch_ptgen(const DevView& V, const uint16_t* pos, int L, int ell, int h, u64* P, cudaStream_t st);
+
+// Fused ct x pt multiply-accumulate: H[l][c][p][n] = sum_j C[j][c][p][n] * P[l][j][p][n] mod q_p.
+void launch_mac(const DevView& V, const u64* C, const u64* P, u64* H, int ell, int L, cudaStream_t st);
+
+// Exact centred base extension Q -> B of [L][2][k][N] coefficient rows into [L][2][kb][N].
+// cst (k residues, may be NULL): also records side[l][j] = lift(x0 + cst) - lift(x0) mod p_j
+// for coefficient 0 of component 0.
+void launch_lift(const DevView& V, const u64* src, u64* dstB, int L, const u64* cst, u64* side, cudaStream_t st);
+
+// Tensor product over Q u B in NTT form -> T3[L][3][k+kb][N].  square: b = a.
+// cstQ/side (may be NULL): constant added to component 0 of b (Q rows / B rows).
+void launch_tensor(const DevView& V, const u64* AQ, const u64* AB, const u64* BQ, const u64* BB, const u64* cstQ,
+                   const u64* side, u64* T3, int L, bool square, cudaStream_t st);
+
+// Exact round(t x / Q) from Q u B residues (coefficient form) -> D[L][3][k][N] mod Q.
+void launch_scale_round(const DevView& V, const u64* T3, u64* D, int L, cudaStream_t st);
+
+// RNS-digit relinearisation: D[L][3][k][N] coefficient form, rlk[k][2][k][N] NTT form
+// -> R[L][2][k][N] NTT form.  DG: scratch [L][k+2][k][N].
+void launch_relin(const DevView& V, const u64* D, const u64* rlk, u64* DG, u64* R, int L, cudaStream_t st);
+
+// out = a + z * b over `groups` groups of k rows (z as k residues); out may alias a.
+void launch_axpy(const DevView& V, const u64* a, const u64* zres, const u64* b, u64* out, size_t groups,
+                 cudaStream_t st);
+
+// acc[3][k][N] (+)= sum_{l<L} D[l][3][k][N]
+void launch_accum(const DevView& V, const u64* D, int L, u64* acc, bool init, cudaStream_t st);
+
+// Client encryption of ell plaintexts given the client codeword positions pos[N][h].
+void launch_encrypt(const DevView& V, const uint16_t* pos, int ell, int h, const u64* s_ntt, u64 seed, u64* cts,
+                    cudaStream_t st);
+
+// Key generation: s (ternary) and its NTT rows; rlk in NTT form.
+void launch_keygen(const DevView& V, u64 seed, int8_t* s, u64* s_ntt, u64* rlk, cudaStream_t st);
+
+// Decryption: ct[2][k][N] -> slots[N] (u32) and max |[t z]_Q| as a double bit pattern in *maxr.
+void launch_decrypt(const DevView& V, const u64* ct, const u64* s_ntt, u64* zbuf, u32* mbuf, u32* slots,
+                    unsigned long long* maxr, cudaStream_t st);
+
+// Cardinality mask: c0 += round(Q * Encode(r) / t), r uniform with sum 0 mod t.
+void launch_mask(const DevView& V, u64 seed, u64* ct, cudaStream_t st);
+
+// Configure kernels that need more than 48 KB of dynamic shared memory.
+cudaError_t kernels_init(int N);

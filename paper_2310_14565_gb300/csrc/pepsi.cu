@@ -1,0 +1,879 @@
+// Context, orchestration and C ABI of the PEPSI GB300 library
+// (declarations and contracts in include/pepsi.h).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "host.h"
+#include "kernels.h"
+#include "pepsi.h"
+
+using hostmath::u128;
+
+namespace {
+
+enum ProfClass { PC_NTT, PC_PTGEN, PC_MAC, PC_LIFT, PC_TENSOR, PC_SCALE, PC_RELIN, PC_POINTWISE, PC_CLIENT, PC_COUNT };
+const char* kProfNames[PC_COUNT] = {"ntt",         "ptgen", "mac",      "lift",  "tensor",
+                                    "scale_round", "relin", "pointwise", "client"};
+
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+};
+
+struct ServerSet {
+  bool live = false;
+  u32 mu = 0;
+  std::vector<u64> hT;          // [mu][N] host copy of T_s
+  u64* dT = nullptr;            // [mu][N]
+  uint16_t* dpos = nullptr;     // [mu][N][h]
+  u64* dP = nullptr;            // [mu][ell][k][N] resident plaintexts or null
+};
+
+}  // namespace
+
+struct pepsi_ctx {
+  pepsi_params prm{};
+  int N = 0, logN = 0, k = 0, kb = 0, ell = 0, h = 0;
+  u64 t = 0;
+  std::vector<u64> Q, B, psi;
+  u64 psi_t = 0;
+  double log2q = 0;
+  DevView V{};
+  cudaStream_t stream = nullptr;
+  // device tables and keys
+  DevPrime* d_pr = nullptr;
+  u64 *d_tw = nullptr, *d_tws = nullptr, *d_itw = nullptr, *d_itws = nullptr;
+  RnsConst* d_rc = nullptr;
+  u64* d_binom = nullptr;
+  int8_t* d_s = nullptr;
+  u64* d_s_ntt = nullptr;  // [k][N]
+  u64* d_rlk = nullptr;    // [k][2][k][N] NTT form
+  u64* d_consts = nullptr; // residues of circuit scalars and constants, [slot][k]
+  std::vector<ServerSet> sets;
+  // scratch, grown on demand
+  std::vector<DevBuf> scratch;
+  int chunk = 32;
+  // profiling
+  bool prof = false;
+  std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> prof_ev;
+  std::vector<cudaEvent_t> ev_pool;
+  uint64_t prof_launch[PC_COUNT] = {};
+  double prof_ms[PC_COUNT] = {};
+  uint64_t launches = 0;
+};
+
+namespace {
+
+// slots of d_consts
+enum ConstSlot { CS_M3, CS_M7, CS_P12, CS_P16, CS_ZINV, CS_D_TM1, CS_D_2, CS_D_60, CS_COUNT };
+
+#define CK(x)                              \
+  do {                                     \
+    cudaError_t e_ = (x);                  \
+    if (e_ != cudaSuccess) return e_;      \
+  } while (0)
+
+thread_local std::string g_last_error = "no error";
+
+int cuda_status(cudaError_t e) {
+  if (e == cudaSuccess) return PEPSI_OK;
+  g_last_error = std::string(cudaGetErrorName(e)) + ": " + cudaGetErrorString(e);
+  if (e == cudaErrorMemoryAllocation) return PEPSI_E_NOMEM;
+  return PEPSI_E_CUDA;
+}
+
+bool is_device_ptr(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+cudaStream_t pick(pepsi_ctx* c, void* s) { return s ? (cudaStream_t)s : c->stream; }
+
+// scratch slot `id` with at least `bytes`
+void* scratch(pepsi_ctx* c, int id, size_t bytes, cudaError_t* err) {
+  if ((int)c->scratch.size() <= id) c->scratch.resize(id + 1);
+  DevBuf& b = c->scratch[id];
+  if (b.bytes >= bytes && b.p) return b.p;
+  if (b.p) {
+    cudaStreamSynchronize(c->stream);
+    cudaDeviceSynchronize();
+    cudaFree(b.p);
+    b.p = nullptr;
+    b.bytes = 0;
+  }
+  cudaError_t e = cudaMalloc(&b.p, bytes ? bytes : 8);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    *err = e;
+    return nullptr;
+  }
+  b.bytes = bytes;
+  return b.p;
+}
+
+struct Prof {
+  pepsi_ctx* c;
+  int cls;
+  cudaStream_t st;
+  cudaEvent_t a = nullptr, b = nullptr;
+  Prof(pepsi_ctx* c_, int cls_, cudaStream_t st_, int kernels = 1) : c(c_), cls(cls_), st(st_) {
+    c->launches += kernels;
+    c->prof_launch[cls] += kernels;
+    if (!c->prof) return;
+    if (c->ev_pool.size() < 2) {
+      for (int i = 0; i < 64; ++i) {
+        cudaEvent_t e;
+        cudaEventCreate(&e);
+        c->ev_pool.push_back(e);
+      }
+    }
+    a = c->ev_pool.back();
+    c->ev_pool.pop_back();
+    b = c->ev_pool.back();
+    c->ev_pool.pop_back();
+    cudaEventRecord(a, st);
+  }
+  ~Prof() {
+    if (!a) return;
+    cudaEventRecord(b, st);
+    c->prof_ev.push_back({cls, {a, b}});
+  }
+};
+
+void prof_collect(pepsi_ctx* c) {
+  for (auto& pe : c->prof_ev) {
+    float ms = 0;
+    cudaEventSynchronize(pe.second.second);
+    cudaEventElapsedTime(&ms, pe.second.first, pe.second.second);
+    c->prof_ms[pe.first] += ms;
+    c->ev_pool.push_back(pe.second.first);
+    c->ev_pool.push_back(pe.second.second);
+  }
+  c->prof_ev.clear();
+}
+
+const u64* cst(pepsi_ctx* c, int slot) { return c->d_consts + (size_t)slot * c->k; }
+
+// ------------------------------------------------------------ primitives
+// NTT rows [outer][np][N] with prime offset p0.
+void ntt(pepsi_ctx* c, bool fwd, const u64* src, u64* dst, size_t outer, int np, int p0, size_t sos, size_t dos,
+         cudaStream_t st) {
+  Prof p(c, PC_NTT, st);
+  launch_ntt(c->V, fwd, src, dst, outer, np, p0, sos, dos, st);
+}
+
+// Arrays of the extension of L ciphertexts: Q part (NTT form, given) and
+// B part (NTT form, computed).  src_ntt [L][2][k][N] -> coef (scratch) ->
+// B [L][2][kb][N].  cstv: optional constant added to component 0 (side).
+void extend(pepsi_ctx* c, const u64* src_ntt, u64* coef, u64* Bpart, int L, const u64* cstv, u64* side,
+            cudaStream_t st) {
+  const size_t kN = (size_t)c->k * c->N, kbN = (size_t)c->kb * c->N;
+  ntt(c, false, src_ntt, coef, (size_t)L * 2, c->k, 0, kN, kN, st);
+  {
+    Prof p(c, PC_LIFT, st);
+    launch_lift(c->V, coef, Bpart, L, cstv, side, st);
+  }
+  ntt(c, true, Bpart, Bpart, (size_t)L * 2, c->kb, c->k, kbN, kbN, st);
+}
+
+// T3 = tensor, then inverse NTT over Q u B, then exact scale-and-round -> D.
+void mult_tail(pepsi_ctx* c, const u64* AQ, const u64* AB, const u64* BQ, const u64* BB, const u64* cQ,
+               const u64* side, bool square, u64* T3, u64* D, int L, cudaStream_t st) {
+  const int np = c->k + c->kb;
+  const size_t npN = (size_t)np * c->N;
+  {
+    Prof p(c, PC_TENSOR, st);
+    launch_tensor(c->V, AQ, AB, BQ, BB, cQ, side, T3, L, square, st);
+  }
+  ntt(c, false, T3, T3, (size_t)L * 3, np, 0, npN, npN, st);
+  Prof p(c, PC_SCALE, st);
+  launch_scale_round(c->V, T3, D, L, st);
+}
+
+// scratch id of the relinearisation digits (declared with the others below)
+constexpr int kScratchDG = 40;
+void relin(pepsi_ctx* c, const u64* D, u64* R, int L, cudaStream_t st) {
+  cudaError_t e = cudaSuccess;
+  u64* DG = (u64*)scratch(c, kScratchDG, (size_t)L * (c->k + 2) * c->k * c->N * 8, &e);
+  if (!DG) return;  // the allocation error resurfaces through cudaGetLastError
+  Prof p(c, PC_RELIN, st, 2);
+  launch_relin(c->V, D, c->d_rlk, DG, R, L, st);
+}
+
+void axpy(pepsi_ctx* c, const u64* a, const u64* z, const u64* b, u64* out, size_t groups, cudaStream_t st) {
+  Prof p(c, PC_POINTWISE, st);
+  launch_axpy(c->V, a, z, b, out, groups, st);
+}
+
+// Scratch layout of the evaluation pipeline for chunks of up to Lc layers.
+struct EvalBufs {
+  u64 *C, *H, *Hc, *XB, *YB, *T3, *D, *R, *U, *W, *X, *Y, *side, *acc, *Pc, *out, *zero;
+};
+enum ScratchId { S_C, S_H, S_HC, S_XB, S_YB, S_T3, S_D, S_R, S_U, S_W, S_X, S_Y, S_SIDE, S_ACC, S_PC, S_OUT, S_ZERO,
+                 S_IN, S_DEC_Z, S_DEC_M, S_DEC_SLOTS, S_DEC_MAX, S_CT, S_POS, S_TC, S_COUNT };
+
+cudaError_t eval_bufs(pepsi_ctx* c, int Lc, bool need_pc, EvalBufs* b) {
+  cudaError_t e = cudaSuccess;
+  const size_t N = c->N, k = c->k, kb = c->kb, np = k + kb;
+  auto get = [&](int id, size_t words) { return (u64*)scratch(c, id, words * 8, &e); };
+  b->C = get(S_C, (size_t)c->ell * 2 * k * N);
+  b->H = get(S_H, Lc * 2 * k * N);
+  b->Hc = get(S_HC, Lc * 2 * k * N);
+  b->XB = get(S_XB, Lc * 2 * kb * N);
+  b->YB = get(S_YB, Lc * 2 * kb * N);
+  b->T3 = get(S_T3, Lc * 3 * np * N);
+  b->D = get(S_D, Lc * 3 * k * N);
+  b->R = get(S_R, Lc * 2 * k * N);
+  b->U = get(S_U, Lc * 2 * k * N);
+  b->W = get(S_W, Lc * 2 * k * N);
+  b->X = get(S_X, Lc * 2 * k * N);
+  b->Y = get(S_Y, Lc * 2 * k * N);
+  b->side = get(S_SIDE, Lc * kb + 1);
+  b->acc = get(S_ACC, 3 * k * N);
+  b->out = get(S_OUT, 3 * k * N);
+  b->Pc = need_pc ? get(S_PC, (size_t)Lc * c->ell * k * N) : nullptr;
+  if (e == cudaSuccess && (c->scratch.size() <= S_ZERO || !c->scratch[S_ZERO].p)) {
+    b->zero = get(S_ZERO, 2 * k * N);
+    if (b->zero) e = cudaMemset(b->zero, 0, 2 * k * N * 8);
+  } else {
+    b->zero = (u64*)c->scratch[S_ZERO].p;
+  }
+  return e;
+}
+
+// Arith-CW-Eq (Algorithm 1) on L layers whose h' is in H (NTT form):
+// D <- prod_{i<h}(h' - i) as un-relinearised 3-component ciphertexts
+// (coefficient form); Hc <- h' in coefficient form.
+void eq_circuit(pepsi_ctx* c, EvalBufs& b, int L, cudaStream_t st) {
+  const size_t k = c->k, N = c->N;
+  const size_t ct2 = 2 * k * N;
+  switch (c->h) {
+    case 1: {
+      ntt(c, false, b.H, b.Hc, (size_t)L * 2, c->k, 0, k * N, k * N, st);
+      for (int l = 0; l < L; ++l) {
+        cudaMemcpyAsync(b.D + (size_t)l * 3 * k * N, b.Hc + (size_t)l * ct2, ct2 * 8, cudaMemcpyDeviceToDevice, st);
+        cudaMemsetAsync(b.D + (size_t)l * 3 * k * N + ct2, 0, k * N * 8, st);
+      }
+      break;
+    }
+    case 2: {  // E = Mult(h', h' - 1)
+      extend(c, b.H, b.Hc, b.XB, L, cst(c, CS_D_TM1), b.side, st);
+      mult_tail(c, b.H, b.XB, b.H, b.XB, cst(c, CS_D_TM1), b.side, false, b.T3, b.D, L, st);
+      break;
+    }
+    case 4: {  // u = R(h'^2) - 3h';  E = Mult(u, u + 2)
+      extend(c, b.H, b.Hc, b.XB, L, nullptr, nullptr, st);
+      mult_tail(c, b.H, b.XB, b.H, b.XB, nullptr, nullptr, true, b.T3, b.D, L, st);
+      relin(c, b.D, b.R, L, st);
+      axpy(c, b.R, cst(c, CS_M3), b.H, b.U, (size_t)L * 2, st);
+      extend(c, b.U, b.X, b.YB, L, cst(c, CS_D_2), b.side, st);
+      mult_tail(c, b.U, b.YB, b.U, b.YB, cst(c, CS_D_2), b.side, false, b.T3, b.D, L, st);
+      break;
+    }
+    case 8: {  // u = R(h'^2) - 7h'; w = R(u^2); E = Mult(w + 12u, w + 16u + 60)
+      extend(c, b.H, b.Hc, b.XB, L, nullptr, nullptr, st);
+      mult_tail(c, b.H, b.XB, b.H, b.XB, nullptr, nullptr, true, b.T3, b.D, L, st);
+      relin(c, b.D, b.R, L, st);
+      axpy(c, b.R, cst(c, CS_M7), b.H, b.U, (size_t)L * 2, st);
+      extend(c, b.U, b.X, b.XB, L, nullptr, nullptr, st);
+      mult_tail(c, b.U, b.XB, b.U, b.XB, nullptr, nullptr, true, b.T3, b.D, L, st);
+      relin(c, b.D, b.W, L, st);
+      axpy(c, b.W, cst(c, CS_P12), b.U, b.X, (size_t)L * 2, st);
+      axpy(c, b.W, cst(c, CS_P16), b.U, b.Y, (size_t)L * 2, st);
+      extend(c, b.X, b.R, b.XB, L, nullptr, nullptr, st);
+      extend(c, b.Y, b.U, b.YB, L, cst(c, CS_D_60), b.side, st);
+      mult_tail(c, b.X, b.XB, b.Y, b.YB, cst(c, CS_D_60), b.side, false, b.T3, b.D, L, st);
+      break;
+    }
+  }
+}
+
+// Copy `bytes` between caller and device buffers through the stream.
+cudaError_t copy_any(void* dst, const void* src, size_t bytes, cudaStream_t st) {
+  return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, st);
+}
+
+// Core of pepsi_eval / pepsi_eval_layers.
+int eval_core(pepsi_ctx* c, int set_id, const u64* cts, u32 layer0, u32 nl, int mode, u64 mask_seed, u64* out_ct,
+              u64* h_out, u64* e_out, cudaStream_t st) {
+  if (set_id < 0 || set_id >= (int)c->sets.size() || !c->sets[set_id].live) return PEPSI_E_PARAM;
+  ServerSet& S = c->sets[set_id];
+  if ((u64)layer0 + nl > S.mu || !cts) return PEPSI_E_PARAM;
+  if (mode != PEPSI_MODE_INDICATOR && mode != PEPSI_MODE_CARDINALITY) return PEPSI_E_PARAM;
+  const size_t k = c->k, N = c->N;
+  const size_t kN = k * N, ct2 = 2 * kN, ct3 = 3 * kN;
+  const int Lc = std::max(1, std::min<int>(c->chunk, (int)nl));
+  EvalBufs b;
+  cudaError_t e = eval_bufs(c, Lc, S.dP == nullptr, &b);
+  if (e != cudaSuccess) return cuda_status(e);
+  // query ciphertexts to NTT form (a4)
+  const size_t qwords = (size_t)c->ell * ct2;
+  if (is_device_ptr(cts)) {
+    ntt(c, true, cts, b.C, (size_t)c->ell * 2, c->k, 0, kN, kN, st);
+  } else {
+    CK(copy_any(b.C, cts, qwords * 8, st));
+    ntt(c, true, b.C, b.C, (size_t)c->ell * 2, c->k, 0, kN, kN, st);
+  }
+  bool first = true;
+  for (u32 l0 = layer0; l0 < layer0 + nl; l0 += Lc) {
+    const int L = (int)std::min<u32>(Lc, layer0 + nl - l0);
+    const u64* P;
+    if (S.dP) {
+      P = S.dP + (size_t)l0 * c->ell * kN;
+    } else {
+      Prof p(c, PC_PTGEN, st);
+      launch_ptgen(c->V, S.dpos + (size_t)l0 * N * c->h, L, c->ell, c->h, b.Pc, st);
+      P = b.Pc;
+    }
+    {
+      Prof p(c, PC_MAC, st);  // a5: fused ct x pt multiply-accumulate
+      launch_mac(c->V, b.C, P, b.H, c->ell, L, st);
+    }
+    eq_circuit(c, b, L, st);  // a6
+    // b.Hc holds h' in coefficient form after the circuit
+    if (h_out) CK(copy_any(h_out + (size_t)(l0 - layer0) * ct2, b.Hc, (size_t)L * ct2 * 8, st));
+    if (e_out) CK(copy_any(e_out + (size_t)(l0 - layer0) * ct3, b.D, (size_t)L * ct3 * 8, st));
+    {
+      Prof p(c, PC_POINTWISE, st);  // a7: layer accumulation
+      launch_accum(c->V, b.D, L, b.acc, first, st);
+    }
+    first = false;
+  }
+  if (out_ct) {
+    // ct = (h!)^-1 * R(A), to coefficient form, plus the mask for cardinality
+    relin(c, b.acc, b.R, 1, st);
+    axpy(c, b.zero, cst(c, CS_ZINV), b.R, b.R, 2, st);
+    ntt(c, false, b.R, b.out, 2, c->k, 0, kN, kN, st);
+    if (mode == PEPSI_MODE_CARDINALITY) {
+      Prof p(c, PC_CLIENT, st);
+      launch_mask(c->V, mask_seed, b.out, st);
+    }
+    CK(copy_any(out_ct, b.out, ct2 * 8, st));
+  }
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_status(e);
+  if (!is_device_ptr(out_ct ? (const void*)out_ct : (const void*)b.out) || (h_out && !is_device_ptr(h_out)) ||
+      (e_out && !is_device_ptr(e_out))) {
+    e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_status(e);
+  }
+  if (c->prof) prof_collect(c);
+  return PEPSI_OK;
+}
+
+int validate(const pepsi_params* p) {
+  if (!p) return PEPSI_E_PARAM;
+  if (p->N < 16 || p->N > 16384 || (p->N & (p->N - 1))) return PEPSI_E_PARAM;
+  if (p->k < 1 || p->k > PEPSI_MAXQ) return PEPSI_E_PARAM;
+  for (u32 i = 0; i < p->k; ++i)
+    if (p->prime_bits[i] < 20 || p->prime_bits[i] > 60) return PEPSI_E_PARAM;
+  if (p->t < 3 || p->t >= (1ull << 32) || (p->t - 1) % (2ull * p->N) || !hostmath::is_prime(p->t))
+    return PEPSI_E_PARAM;
+  if (p->h != 1 && p->h != 2 && p->h != 4 && p->h != 8) return PEPSI_E_PARAM;
+  if (p->num_hashes != 3 && p->num_hashes != 0) return PEPSI_E_PARAM;
+  u32 logb = 0;
+  while ((1u << logb) < p->N) ++logb;
+  if (p->lambda_bar < 1 || p->lambda_bar + logb >= 64) return PEPSI_E_PARAM;
+  return PEPSI_OK;
+}
+
+cudaError_t upload(void** dst, const void* src, size_t bytes) {
+  CK(cudaMalloc(dst, bytes));
+  return cudaMemcpy(*dst, src, bytes, cudaMemcpyHostToDevice);
+}
+
+void free_set(ServerSet& S) {
+  cudaFree(S.dT);
+  cudaFree(S.dpos);
+  cudaFree(S.dP);
+  S = ServerSet{};
+}
+
+}  // namespace
+
+// ================================================================ C ABI
+extern "C" {
+
+const char* pepsi_last_error(void) { return g_last_error.c_str(); }
+
+const char* pepsi_strerror(int code) {
+  switch (code) {
+    case PEPSI_OK: return "ok";
+    case PEPSI_E_PARAM: return "invalid or unsupported parameters";
+    case PEPSI_E_BIN_OVERFLOW: return "server bin overflow (more than mu items in a bin)";
+    case PEPSI_E_CUCKOO_FAIL: return "cuckoo hashing failed (eviction bound reached)";
+    case PEPSI_E_NOMEM: return "device memory exhausted";
+    case PEPSI_E_CUDA: return "CUDA runtime error";
+    case PEPSI_E_TIMEOUT: return "bounded device wait expired";
+    case PEPSI_E_NOISE: return "noise budget exhausted";
+    default: return "unknown error";
+  }
+}
+
+void pepsi_destroy(pepsi_ctx* c) {
+  if (!c) return;
+  cudaDeviceSynchronize();
+  for (auto& S : c->sets) free_set(S);
+  for (auto& b : c->scratch) cudaFree(b.p);
+  for (auto e : c->ev_pool) cudaEventDestroy(e);
+  for (auto& pe : c->prof_ev) {
+    cudaEventDestroy(pe.second.first);
+    cudaEventDestroy(pe.second.second);
+  }
+  cudaFree(c->d_pr);
+  cudaFree(c->d_tw);
+  cudaFree(c->d_tws);
+  cudaFree(c->d_itw);
+  cudaFree(c->d_itws);
+  cudaFree(c->d_rc);
+  cudaFree(c->d_binom);
+  cudaFree(c->d_s);
+  cudaFree(c->d_s_ntt);
+  cudaFree(c->d_rlk);
+  cudaFree(c->d_consts);
+  if (c->stream) cudaStreamDestroy(c->stream);
+  delete c;
+}
+
+int pepsi_setup(const pepsi_params* params, uint64_t key_seed, pepsi_ctx** out) {
+  if (!out) return PEPSI_E_PARAM;
+  *out = nullptr;
+  int rc = validate(params);
+  if (rc) return rc;
+  pepsi_ctx* c = new pepsi_ctx();
+  c->prm = *params;
+  c->N = (int)params->N;
+  while ((1 << c->logN) < c->N) ++c->logN;
+  c->k = (int)params->k;
+  c->t = params->t;
+  c->h = (int)params->h;
+  c->ell = params->ell ? (int)params->ell : (int)hostmath::code_length(params->lambda_bar, params->h);
+  if (c->ell <= 0 || c->ell > 65535 || hostmath::binom_sat(c->ell, c->h) < (1ull << params->lambda_bar)) {
+    delete c;
+    return PEPSI_E_PARAM;
+  }
+  if (const char* ch = getenv("PEPSI_CHUNK")) c->chunk = std::max(1, atoi(ch));
+  // primes
+  for (int i = 0; i < c->k; ++i) {
+    u64 q = hostmath::find_prime(params->prime_bits[i], c->N, c->Q);
+    if (!q) {
+      delete c;
+      return PEPSI_E_PARAM;
+    }
+    c->Q.push_back(q);
+  }
+  double lq = 0;
+  for (u64 q : c->Q) lq += std::log2((double)q);
+  c->log2q = lq;
+  // lazy sums in the MAC must stay below 2^128
+  {
+    u64 qmax = *std::max_element(c->Q.begin(), c->Q.end());
+    long double bound = (long double)c->ell * (long double)(qmax - 1) * (long double)(qmax - 1);
+    if (bound >= std::ldexp(1.0L, 127)) {
+      delete c;
+      return PEPSI_E_PARAM;
+    }
+  }
+  // auxiliary base B: 61-bit primes with log2 B >= log2(t N Q) + 3
+  const double needB = std::log2((double)c->t) + c->logN + lq + 3.0;
+  double haveB = 0;
+  std::vector<u64> taken = c->Q;
+  while (haveB < needB) {
+    if ((int)c->B.size() >= PEPSI_MAXB) {
+      delete c;
+      return PEPSI_E_PARAM;
+    }
+    u64 p = hostmath::find_prime(61, c->N, taken);
+    taken.push_back(p);
+    c->B.push_back(p);
+    haveB += std::log2((double)p);
+  }
+  c->kb = (int)c->B.size();
+  // roots and tables: Q primes, B primes, then t
+  std::vector<u64> all = c->Q;
+  all.insert(all.end(), c->B.begin(), c->B.end());
+  all.push_back(c->t);
+  const int np = (int)all.size();
+  std::vector<DevPrime> pr(np);
+  std::vector<u64> tw((size_t)np * c->N), tws(tw.size()), itw(tw.size()), itws(tw.size());
+  for (int i = 0; i < np; ++i) {
+    u64 root = hostmath::min_root(all[i], c->N);
+    if (i < c->k) c->psi.push_back(root);
+    if (i == np - 1) c->psi_t = root;
+    pr[i] = hostmath::make_prime(all[i], c->N);
+    hostmath::twiddles(all[i], root, c->N, &tw[(size_t)i * c->N], &tws[(size_t)i * c->N], &itw[(size_t)i * c->N],
+                       &itws[(size_t)i * c->N]);
+  }
+  RnsConst rcst;
+  hostmath::rns_constants(c->Q, c->B, c->t, &rcst);
+  // binomial table for CW unranking: C(n, r), n <= ell, r <= h
+  std::vector<u64> binom((size_t)(c->ell + 1) * (c->h + 1));
+  for (int n = 0; n <= c->ell; ++n)
+    for (int r = 0; r <= c->h; ++r) binom[(size_t)n * (c->h + 1) + r] = hostmath::binom_sat(n, r);
+  // circuit constants: scalars -3, -7, 12, 16, (h!)^-1 (centred) and
+  // round(Q [v]_t / t) for v = t-1, 2, 60
+  std::vector<u64> consts((size_t)CS_COUNT * c->k);
+  auto scalar = [&](int slot, i64 z) {
+    for (int i = 0; i < c->k; ++i) {
+      u64 q = c->Q[i];
+      consts[(size_t)slot * c->k + i] = z >= 0 ? (u64)z % q : (q - ((u64)(-z) % q)) % q;
+    }
+  };
+  scalar(CS_M3, -3);
+  scalar(CS_M7, -7);
+  scalar(CS_P12, 12);
+  scalar(CS_P16, 16);
+  {
+    u64 f = 1;
+    for (int i = 2; i <= c->h; ++i) f = hostmath::mulmod(f, i, c->t);
+    u64 z = hostmath::invmod(f, c->t);
+    scalar(CS_ZINV, z > c->t / 2 ? (i64)z - (i64)c->t : (i64)z);
+  }
+  hostmath::delta(c->Q, c->t, c->t - 1, &consts[(size_t)CS_D_TM1 * c->k]);
+  hostmath::delta(c->Q, c->t, 2, &consts[(size_t)CS_D_2 * c->k]);
+  hostmath::delta(c->Q, c->t, 60, &consts[(size_t)CS_D_60 * c->k]);
+
+  // a blocking stream: ordered with the legacy default stream that most callers use
+  cudaError_t e = cudaStreamCreate(&c->stream);
+  if (e == cudaSuccess) e = kernels_init(c->N);
+  if (e == cudaSuccess) e = upload((void**)&c->d_pr, pr.data(), pr.size() * sizeof(DevPrime));
+  if (e == cudaSuccess) e = upload((void**)&c->d_tw, tw.data(), tw.size() * 8);
+  if (e == cudaSuccess) e = upload((void**)&c->d_tws, tws.data(), tws.size() * 8);
+  if (e == cudaSuccess) e = upload((void**)&c->d_itw, itw.data(), itw.size() * 8);
+  if (e == cudaSuccess) e = upload((void**)&c->d_itws, itws.data(), itws.size() * 8);
+  if (e == cudaSuccess) e = upload((void**)&c->d_rc, &rcst, sizeof(rcst));
+  if (e == cudaSuccess) e = upload((void**)&c->d_binom, binom.data(), binom.size() * 8);
+  if (e == cudaSuccess) e = upload((void**)&c->d_consts, consts.data(), consts.size() * 8);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&c->d_s, c->N);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&c->d_s_ntt, (size_t)c->k * c->N * 8);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&c->d_rlk, (size_t)c->k * 2 * c->k * c->N * 8);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    pepsi_destroy(c);
+    return cuda_status(e);
+  }
+  c->V.N = c->N;
+  c->V.logN = c->logN;
+  c->V.k = c->k;
+  c->V.kb = c->kb;
+  c->V.tidx = c->k + c->kb;
+  c->V.pr = c->d_pr;
+  c->V.tw = c->d_tw;
+  c->V.tws = c->d_tws;
+  c->V.itw = c->d_itw;
+  c->V.itws = c->d_itws;
+  c->V.rc = c->d_rc;
+  {
+    Prof p(c, PC_CLIENT, c->stream, 3);
+    launch_keygen(c->V, key_seed, c->d_s, c->d_s_ntt, c->d_rlk, c->stream);
+  }
+  e = cudaStreamSynchronize(c->stream);
+  if (e == cudaSuccess) e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    pepsi_destroy(c);
+    return cuda_status(e);
+  }
+  *out = c;
+  return PEPSI_OK;
+}
+
+int pepsi_get_info(const pepsi_ctx* c, pepsi_info* info) {
+  if (!c || !info) return PEPSI_E_PARAM;
+  memset(info, 0, sizeof(*info));
+  info->N = c->N;
+  info->k = c->k;
+  info->kb = c->kb;
+  info->ell = c->ell;
+  info->h = c->h;
+  info->mu = c->prm.mu;
+  info->lambda_bar = c->prm.lambda_bar;
+  info->logb = c->logN;
+  info->t = c->t;
+  for (int i = 0; i < c->k; ++i) {
+    info->q[i] = c->Q[i];
+    info->psi[i] = c->psi[i];
+  }
+  for (int j = 0; j < c->kb && j < 12; ++j) info->b_primes[j] = c->B[j];
+  info->psi_t = c->psi_t;
+  info->log2_q = c->log2q;
+  return PEPSI_OK;
+}
+
+int pepsi_server_load(pepsi_ctx* c, const uint64_t* items, size_t n, int* set_id) {
+  if (!c || (!items && n) || !set_id) return PEPSI_E_PARAM;
+  hostmath::Hasher H(c->prm.hash_key, c->prm.lambda_bar, c->logN);
+  u32 mu = c->prm.mu ? c->prm.mu : hostmath::mu_rule(n, c->N);
+  ServerSet S;
+  S.mu = mu;
+  u32 maxload = 0;
+  int rc = hostmath::simple_hash(H, items, n, mu, S.hT, &maxload);
+  if (rc) return rc;
+  const size_t N = c->N, k = c->k;
+  const size_t tbytes = (size_t)mu * N * 8;
+  cudaError_t e = upload((void**)&S.dT, S.hT.data(), tbytes);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&S.dpos, (size_t)mu * N * c->h * sizeof(uint16_t));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    free_set(S);
+    return cuda_status(e);
+  }
+  {
+    Prof p(c, PC_PTGEN, c->stream);
+    launch_cw_unrank(S.dT, (size_t)mu * N, c->d_binom, c->ell, c->h, S.dpos, c->stream);
+  }
+  // resident NTT-form plaintexts when the budget allows
+  const size_t pbytes = (size_t)mu * c->ell * k * N * 8;
+  size_t freeb = 0, totalb = 0;
+  cudaMemGetInfo(&freeb, &totalb);
+  u64 cap = c->prm.resident_bytes;
+  bool resident = cap == 0 ? pbytes <= (size_t)(0.6 * (double)freeb) : (cap != UINT64_MAX && pbytes <= cap);
+  if (resident) {
+    e = cudaMalloc((void**)&S.dP, pbytes);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      S.dP = nullptr;
+    } else {
+      const int G = 64;  // layers per launch
+      for (u32 l0 = 0; l0 < mu; l0 += G) {
+        const int L = (int)std::min<u32>(G, mu - l0);
+        Prof p(c, PC_PTGEN, c->stream);
+        launch_ptgen(c->V, S.dpos + (size_t)l0 * N * c->h, L, c->ell, c->h, S.dP + (size_t)l0 * c->ell * k * N,
+                     c->stream);
+      }
+    }
+  }
+  e = cudaStreamSynchronize(c->stream);
+  if (e == cudaSuccess) e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    free_set(S);
+    return cuda_status(e);
+  }
+  if (c->prof) prof_collect(c);
+  S.live = true;
+  c->sets.push_back(std::move(S));
+  *set_id = (int)c->sets.size() - 1;
+  return PEPSI_OK;
+}
+
+int pepsi_server_table(pepsi_ctx* c, int set_id, uint64_t* out) {
+  if (!c || !out || set_id < 0 || set_id >= (int)c->sets.size() || !c->sets[set_id].live) return PEPSI_E_PARAM;
+  memcpy(out, c->sets[set_id].hT.data(), c->sets[set_id].hT.size() * 8);
+  return PEPSI_OK;
+}
+
+int pepsi_server_plaintexts(pepsi_ctx* c, int set_id, uint32_t layer0, uint32_t nl, uint64_t* out, void* stream) {
+  if (!c || !out || set_id < 0 || set_id >= (int)c->sets.size() || !c->sets[set_id].live) return PEPSI_E_PARAM;
+  ServerSet& S = c->sets[set_id];
+  if ((u64)layer0 + nl > S.mu) return PEPSI_E_PARAM;
+  cudaStream_t st = pick(c, stream);
+  const size_t per = (size_t)c->ell * c->k * c->N;
+  cudaError_t e = cudaSuccess;
+  if (S.dP) {
+    e = copy_any(out, S.dP + (size_t)layer0 * per, (size_t)nl * per * 8, st);
+  } else {
+    u64* tmp = (u64*)scratch(c, S_PC, (size_t)nl * per * 8, &e);
+    if (!tmp) return cuda_status(e);
+    {
+      Prof p(c, PC_PTGEN, st);
+      launch_ptgen(c->V, S.dpos + (size_t)layer0 * c->N * c->h, nl, c->ell, c->h, tmp, st);
+    }
+    e = copy_any(out, tmp, (size_t)nl * per * 8, st);
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  return cuda_status(e);
+}
+
+int pepsi_query(pepsi_ctx* c, const uint64_t* items, size_t m, uint64_t enc_seed, uint64_t* cts,
+                int32_t* bin_of_item, void* stream) {
+  if (!c || (!items && m) || !cts) return PEPSI_E_PARAM;
+  cudaStream_t st = pick(c, stream);
+  hostmath::Hasher H(c->prm.hash_key, c->prm.lambda_bar, c->logN);
+  std::vector<u64> table;
+  std::vector<int32_t> where;
+  int rc = hostmath::cuckoo(H, items, m, table, where);
+  if (rc) return rc;
+  if (bin_of_item) memcpy(bin_of_item, where.data(), m * sizeof(int32_t));
+  cudaError_t e = cudaSuccess;
+  const size_t N = c->N;
+  u64* dTc = (u64*)scratch(c, S_TC, N * 8, &e);
+  uint16_t* dpos = (uint16_t*)scratch(c, S_POS, N * c->h * sizeof(uint16_t), &e);
+  const size_t words = (size_t)c->ell * 2 * c->k * N;
+  const bool dev_out = is_device_ptr(cts);
+  u64* dct = dev_out ? cts : (u64*)scratch(c, S_CT, words * 8, &e);
+  if (!dTc || !dpos || !dct) return cuda_status(e);
+  CK(copy_any(dTc, table.data(), N * 8, st));
+  {
+    Prof p(c, PC_CLIENT, st);
+    launch_cw_unrank(dTc, N, c->d_binom, c->ell, c->h, dpos, st);
+  }
+  {
+    Prof p(c, PC_CLIENT, st);
+    launch_encrypt(c->V, dpos, c->ell, c->h, c->d_s_ntt, enc_seed, dct, st);
+  }
+  if (!dev_out) CK(copy_any(cts, dct, words * 8, st));
+  e = cudaStreamSynchronize(st);  // the host cuckoo table must outlive the copy
+  if (e == cudaSuccess) e = cudaGetLastError();
+  if (c->prof) prof_collect(c);
+  return cuda_status(e);
+}
+
+int pepsi_eval(pepsi_ctx* c, int set_id, const uint64_t* cts, int mode, uint64_t mask_seed, uint64_t* out_ct,
+               void* stream) {
+  if (!c || !out_ct) return PEPSI_E_PARAM;
+  if (set_id < 0 || set_id >= (int)c->sets.size()) return PEPSI_E_PARAM;
+  return eval_core(c, set_id, cts, 0, c->sets[set_id].mu, mode, mask_seed, out_ct, nullptr, nullptr,
+                   pick(c, stream));
+}
+
+int pepsi_eval_layers(pepsi_ctx* c, int set_id, const uint64_t* cts, uint32_t layer0, uint32_t nl, uint64_t* h_out,
+                      uint64_t* e_out, void* stream) {
+  if (!c || nl == 0) return PEPSI_E_PARAM;
+  return eval_core(c, set_id, cts, layer0, nl, PEPSI_MODE_INDICATOR, 0, nullptr, h_out, e_out, pick(c, stream));
+}
+
+int pepsi_decrypt(pepsi_ctx* c, const uint64_t* ct, uint32_t* slots, double* noise_budget_bits) {
+  if (!c || !ct || !slots) return PEPSI_E_PARAM;
+  cudaStream_t st = c->stream;
+  cudaError_t e = cudaSuccess;
+  const size_t N = c->N, ct2 = 2 * (size_t)c->k * N;
+  u64* din = (u64*)scratch(c, S_IN, ct2 * 8, &e);
+  u64* z = (u64*)scratch(c, S_DEC_Z, (size_t)c->k * N * 8, &e);
+  u32* m = (u32*)scratch(c, S_DEC_M, N * 4, &e);
+  u32* sl = (u32*)scratch(c, S_DEC_SLOTS, N * 4, &e);
+  unsigned long long* mx = (unsigned long long*)scratch(c, S_DEC_MAX, 8, &e);
+  if (!din || !z || !m || !sl || !mx) return cuda_status(e);
+  CK(copy_any(din, ct, ct2 * 8, st));
+  {
+    Prof p(c, PC_CLIENT, st, 3);
+    launch_decrypt(c->V, din, c->d_s_ntt, z, m, sl, mx, st);
+  }
+  unsigned long long bits = 0;
+  CK(cudaMemcpyAsync(slots, sl, N * 4, cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(&bits, mx, 8, cudaMemcpyDeviceToHost, st));
+  e = cudaStreamSynchronize(st);
+  if (e == cudaSuccess) e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_status(e);
+  if (c->prof) prof_collect(c);
+  double maxr;
+  memcpy(&maxr, &bits, 8);
+  const double budget = maxr > 0 ? c->log2q - 1.0 - std::log2(maxr) : INFINITY;
+  if (noise_budget_bits) *noise_budget_bits = budget;
+  return budget > 0 ? PEPSI_OK : PEPSI_E_NOISE;
+}
+
+int pepsi_ntt(pepsi_ctx* c, uint64_t* polys, size_t count, int inverse, void* stream) {
+  if (!c || !polys) return PEPSI_E_PARAM;
+  if (!count) return PEPSI_OK;
+  if (!is_device_ptr(polys)) return PEPSI_E_PARAM;
+  cudaStream_t st = pick(c, stream);
+  const size_t kN = (size_t)c->k * c->N;
+  ntt(c, !inverse, polys, polys, count, c->k, 0, kN, kN, st);
+  return cuda_status(cudaGetLastError());
+}
+
+int pepsi_ct_mult(pepsi_ctx* c, const uint64_t* a, const uint64_t* b, size_t n, int relin_flag, uint64_t* out,
+                  void* stream) {
+  if (!c || !a || !b || !out) return PEPSI_E_PARAM;
+  if (!n) return PEPSI_OK;
+  if (!is_device_ptr(a) || !is_device_ptr(b) || !is_device_ptr(out)) return PEPSI_E_PARAM;
+  cudaStream_t st = pick(c, stream);
+  const size_t k = c->k, kb = c->kb, N = c->N, np = k + kb;
+  const size_t kN = k * N, kbN = kb * N;
+  cudaError_t e = cudaSuccess;
+  u64* AQ = (u64*)scratch(c, S_U, n * 2 * kN * 8, &e);
+  u64* BQ = (u64*)scratch(c, S_W, n * 2 * kN * 8, &e);
+  u64* AB = (u64*)scratch(c, S_XB, n * 2 * kbN * 8, &e);
+  u64* BB = (u64*)scratch(c, S_YB, n * 2 * kbN * 8, &e);
+  u64* T3 = (u64*)scratch(c, S_T3, n * 3 * np * N * 8, &e);
+  u64* D = (u64*)scratch(c, S_D, n * 3 * kN * 8, &e);
+  u64* R = (u64*)scratch(c, S_R, n * 2 * kN * 8, &e);
+  if (!AQ || !BQ || !AB || !BB || !T3 || !D || !R) return cuda_status(e);
+  const int L = (int)n;
+  {
+    Prof p(c, PC_LIFT, st);
+    launch_lift(c->V, a, AB, L, nullptr, nullptr, st);
+  }
+  {
+    Prof p(c, PC_LIFT, st);
+    launch_lift(c->V, b, BB, L, nullptr, nullptr, st);
+  }
+  ntt(c, true, a, AQ, n * 2, c->k, 0, kN, kN, st);
+  ntt(c, true, b, BQ, n * 2, c->k, 0, kN, kN, st);
+  ntt(c, true, AB, AB, n * 2, c->kb, c->k, kbN, kbN, st);
+  ntt(c, true, BB, BB, n * 2, c->kb, c->k, kbN, kbN, st);
+  mult_tail(c, AQ, AB, BQ, BB, nullptr, nullptr, false, T3, D, L, st);
+  if (relin_flag) {
+    relin(c, D, R, L, st);
+    ntt(c, false, R, out, n * 2, c->k, 0, kN, kN, st);
+  } else {
+    CK(cudaMemcpyAsync(out, D, n * 3 * kN * 8, cudaMemcpyDeviceToDevice, st));
+  }
+  return cuda_status(cudaGetLastError());
+}
+
+int pepsi_relin(pepsi_ctx* c, const uint64_t* in, size_t n, uint64_t* out, void* stream) {
+  if (!c || !in || !out) return PEPSI_E_PARAM;
+  if (!n) return PEPSI_OK;
+  if (!is_device_ptr(in) || !is_device_ptr(out)) return PEPSI_E_PARAM;
+  cudaStream_t st = pick(c, stream);
+  const size_t kN = (size_t)c->k * c->N;
+  cudaError_t e = cudaSuccess;
+  u64* R = (u64*)scratch(c, S_R, n * 2 * kN * 8, &e);
+  if (!R) return cuda_status(e);
+  relin(c, in, R, (int)n, st);
+  ntt(c, false, R, out, n * 2, c->k, 0, kN, kN, st);
+  return cuda_status(cudaGetLastError());
+}
+
+int pepsi_export_keys(pepsi_ctx* c, int8_t* s, uint64_t* rlk) {
+  if (!c) return PEPSI_E_PARAM;
+  cudaStream_t st = c->stream;
+  const size_t kN = (size_t)c->k * c->N, words = (size_t)c->k * 2 * kN;
+  if (s) CK(cudaMemcpyAsync(s, c->d_s, c->N, cudaMemcpyDeviceToHost, st));
+  if (rlk) {
+    cudaError_t e = cudaSuccess;
+    u64* tmp = (u64*)scratch(c, S_CT, words * 8, &e);
+    if (!tmp) return cuda_status(e);
+    ntt(c, false, c->d_rlk, tmp, (size_t)c->k * 2, c->k, 0, kN, kN, st);
+    CK(cudaMemcpyAsync(rlk, tmp, words * 8, cudaMemcpyDeviceToHost, st));
+  }
+  return cuda_status(cudaStreamSynchronize(st));
+}
+
+int pepsi_profile_enable(pepsi_ctx* c, int on) {
+  if (!c) return PEPSI_E_PARAM;
+  cudaStreamSynchronize(c->stream);
+  prof_collect(c);
+  c->prof = on != 0;
+  for (int i = 0; i < PC_COUNT; ++i) {
+    c->prof_launch[i] = 0;
+    c->prof_ms[i] = 0;
+  }
+  c->launches = 0;
+  return PEPSI_OK;
+}
+
+int pepsi_profile_read(pepsi_ctx* c, const char** names, uint64_t* launches, double* total_ms, int max) {
+  if (!c) return PEPSI_E_PARAM;
+  cudaDeviceSynchronize();
+  prof_collect(c);
+  for (int i = 0; i < PC_COUNT && i < max; ++i) {
+    if (names) names[i] = kProfNames[i];
+    if (launches) launches[i] = c->prof_launch[i];
+    if (total_ms) total_ms[i] = c->prof_ms[i];
+  }
+  return PC_COUNT;
+}
+
+}  // extern "C"

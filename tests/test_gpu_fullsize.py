@@ -1,0 +1,63 @@
+"""Parity at the paper-shaped size, in the configuration bench.py times:
+N = 8192, four 54/55-bit primes, t = 65537, h = 4, ell = 600, mu = 526,
+1024 client items against 2^20 server items (102 planted), resident
+server plaintexts.  The oracle checks sampled outputs one by one (the
+server table, the request words, sampled plaintexts, the h' and E words of
+sampled layers); the final result is checked by properties that hold at
+any size (decrypts to the brute-force intersection with positive budget)."""
+import numpy as np
+import pytest
+
+from gpu_helpers import brute_indicator, pair, torch_cuda
+
+pytestmark = pytest.mark.gpu
+
+PAPER = [55, 55, 54, 54]
+
+
+@pytest.fixture(scope="module")
+def paper_case():
+    torch_cuda()
+    from paper_2310_14565_gb300.workload import make_sets
+
+    oc, gc, s, rlk = pair(8192, PAPER, 4, 32, mu=526, ell=600)
+    sets = make_sets(1024, 1 << 20, 102, bits=64)
+    sid = gc.server_load(sets.server)
+    rc, Ts, _ = oc.server_table(sets.server)
+    assert rc == 0
+    cts, where = gc.query(sets.client, 4)
+    return oc, gc, s, rlk, sets, sid, Ts, cts, where
+
+
+def test_paper_table_request_and_plaintexts(paper_case):
+    oc, gc, s, rlk, sets, sid, Ts, cts, where = paper_case
+    assert np.array_equal(gc.server_table(sid, 526), Ts)
+    rc, ocs, owhere = oc.query(s, sets.client, 4)
+    assert rc == 0 and np.array_equal(where, owhere)
+    assert np.array_equal(cts, ocs)
+    P = gc.server_plaintexts(sid, 263, 1)
+    for j in (0, 299, 599):
+        assert np.array_equal(P[0, j], oc.server_plaintext(Ts, 263, j))
+
+
+def test_paper_sampled_layers(paper_case):
+    oc, gc, s, rlk, sets, sid, Ts, cts, where = paper_case
+    for layer0, nl in ((0, 2), (525, 1)):
+        _, dh, de = oc.eval(rlk, cts, Ts, layer0=layer0, nlayers=nl, debug=True)
+        gh, ge = gc.eval_layers(sid, cts, layer0, nl)
+        assert np.array_equal(gh, dh), layer0
+        assert np.array_equal(ge, de), layer0
+
+
+def test_paper_result_decrypts_to_intersection(paper_case):
+    oc, gc, s, rlk, sets, sid, Ts, cts, where = paper_case
+    out = gc.eval(sid, cts)
+    slots, budget = gc.decrypt(out)
+    assert budget > 0
+    assert np.array_equal(slots, brute_indicator(sets.client, sets.server, where, 8192))
+    assert int(slots.sum()) == 102
+    oslots, obudget = oc.decrypt(s, out)
+    assert np.array_equal(oslots, slots) and abs(obudget - budget) < 1e-9
+    card = gc.eval(sid, cts, mode=1, mask_seed=5)
+    cs, _ = gc.decrypt(card)
+    assert int(cs.astype(np.int64).sum()) % 65537 == 102

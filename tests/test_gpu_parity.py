@@ -1,0 +1,236 @@
+"""CUDA path vs the CPU oracle, word for word, through the C ABI.
+
+Integer work: every comparison is bit-exact (the noise budget, a float
+derived from exact integers, is compared to 1e-9 bits).  Sizes span several
+NTT tiles, ragged layer chunks and the edge cases of the method (empty sets,
+all-dummy tables, the smallest ring).
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+from gpu_helpers import T, brute_indicator, pair, to_dev, to_host, torch_cuda
+
+pytestmark = pytest.mark.gpu
+
+TOY = [36, 36, 37]
+PAPER = [55, 55, 54, 54]
+LARGE = [55] * 6 + [54] * 2
+
+
+@pytest.fixture(autouse=True)
+def _cuda():
+    torch_cuda()
+
+
+# -------------------------------------------------------------- setup / keys
+@pytest.mark.parametrize("N,bits,h,lb", [(16, TOY, 2, 6), (64, PAPER, 4, 10), (4096, TOY, 2, 16),
+                                         (8192, PAPER, 4, 32), (16384, LARGE, 8, 40)])
+def test_params_and_keys(N, bits, h, lb):
+    oc, gc, s, rlk = pair(N, bits, h, lb, mu=4)
+    assert gc.q == oc.q and gc.psi == oc.psi and gc.psi_t == oc.psi_t and gc.ell == oc.ell
+    gs, grlk = gc.export_keys()
+    assert np.array_equal(gs, s)
+    assert np.array_equal(grlk, rlk)
+
+
+# ------------------------------------------------------------------- NTT
+@pytest.mark.parametrize("N,bits", [(16, TOY), (64, PAPER), (4096, TOY), (8192, PAPER), (16384, LARGE)])
+def test_ntt_matches_oracle(N, bits):
+    import oracle
+
+    oc, gc, _, _ = pair(N, bits, 1, 4, mu=1)
+    rng = np.random.default_rng(N)
+    count = 3
+    x = np.stack([np.stack([rng.integers(0, q, N, dtype=np.uint64) for q in oc.q]) for _ in range(count)])
+    d = to_dev(x)
+    gc.ntt(d, count)
+    got = to_host(d).reshape(count, oc.k, N)
+    for c in range(count):
+        for p in range(oc.k):
+            want = oracle.ntt_fwd(x[c, p], N, oc.q[p], oc.psi[p])
+            assert np.array_equal(got[c, p], want), (c, p)
+    gc.ntt(d, count, inverse=True)
+    assert np.array_equal(to_host(d).reshape(x.shape), x)
+
+
+# --------------------------------------------------------- client request
+@pytest.mark.parametrize("N,bits,h,lb,m", [(64, TOY, 2, 8, 20), (4096, TOY, 2, 16, 64), (64, PAPER, 4, 10, 0)])
+def test_query_matches_oracle(N, bits, h, lb, m):
+    from paper_2310_14565_gb300.workload import make_sets
+
+    oc, gc, s, _ = pair(N, bits, h, lb, mu=4)
+    sets = make_sets(m, 64, min(m, 4), bits=32)
+    rc, want, where_o = oc.query(s, sets.client, 4)
+    assert rc == 0
+    got, where = gc.query(sets.client, 4)
+    assert np.array_equal(where, where_o[: len(where)])
+    assert np.array_equal(got, want)
+    # device output buffer, same words
+    d = to_dev(np.zeros_like(want))
+    gc.query(sets.client, 4, out=d)
+    assert np.array_equal(to_host(d).reshape(want.shape), want)
+
+
+# ------------------------------------------------------------ server side
+@pytest.mark.parametrize("N,bits,h,lb,n,mu", [(64, TOY, 2, 8, 100, 16), (4096, TOY, 2, 16, 1024, 16),
+                                              (64, PAPER, 4, 10, 0, 3)])
+def test_server_table_and_plaintexts(N, bits, h, lb, n, mu):
+    from paper_2310_14565_gb300.workload import make_sets
+
+    oc, gc, _, _ = pair(N, bits, h, lb, mu=mu)
+    sets = make_sets(0, n, 0, bits=32)
+    rc, Ts, _ = oc.server_table(sets.server)
+    assert rc == 0
+    sid = gc.server_load(sets.server)
+    assert np.array_equal(gc.server_table(sid, mu), Ts)
+    got = gc.server_plaintexts(sid, 0, mu)
+    rng = np.random.default_rng(1)
+    for layer in sorted(set([0, mu - 1] + list(rng.integers(0, mu, 3)))):
+        for j in sorted(set([0, oc.ell - 1] + list(rng.integers(0, oc.ell, 4)))):
+            assert np.array_equal(got[layer, j], oc.server_plaintext(Ts, layer, j)), (layer, j)
+
+
+# ---------------------------------------------------- ciphertext products
+@pytest.mark.parametrize("N,bits", [(16, TOY), (64, PAPER), (4096, TOY), (64, LARGE), (8192, PAPER)])
+def test_ct_mult_and_relin_match_oracle(N, bits):
+    oc, gc, s, rlk = pair(N, bits, 1, 4, mu=1)
+    rng = np.random.default_rng(7)
+    n = 2
+    m = rng.integers(0, T, (2 * n, N)).astype(np.uint32)
+    cts = oc.encrypt(s, m, 9)
+    a, b = cts[:n], cts[n:]
+    da, db = to_dev(a), to_dev(b)
+    out3 = to_dev(np.zeros((n, 3, oc.k, N), np.uint64))
+    gc.ct_mult(da, db, n, out3)
+    got3 = to_host(out3).reshape(n, 3, oc.k, N)
+    out2 = to_dev(np.zeros((n, 2, oc.k, N), np.uint64))
+    gc.ct_mult(da, db, n, out2, relin=True)
+    got2 = to_host(out2).reshape(n, 2, oc.k, N)
+    for i in range(n):
+        want3 = oc.ct_mult(a[i], b[i])
+        assert np.array_equal(got3[i], want3)
+        assert np.array_equal(got2[i], oc.relin(rlk, want3))
+    # squaring (a == b) takes the same path
+    gc.ct_mult(da, da, n, out3)
+    assert np.array_equal(to_host(out3).reshape(n, 3, oc.k, N)[0], oc.ct_mult(a[0], a[0]))
+
+
+# -------------------------------------------------------------- evaluation
+def _psi_case(N, bits, h, lb, mu, m, n, planted, chunk=None, seed=5):
+    """A PSI instance; mu is raised to the actual maximum bin load."""
+    import oracle
+    from paper_2310_14565_gb300.workload import make_sets
+
+    sets = make_sets(m, n, planted, bits=32, seed_items=seed, seed_plant=seed + 1)
+    _, _, load = oracle.simple_hash(0x5EED, lb, int(math.log2(N)), sets.server, 10 * n + 1)
+    mu = max(mu, load)
+    if chunk:
+        os.environ["PEPSI_CHUNK"] = str(chunk)
+    try:
+        oc, gc, s, rlk = pair(N, bits, h, lb, mu=mu)
+    finally:
+        os.environ.pop("PEPSI_CHUNK", None)
+    rc, Ts, _ = oc.server_table(sets.server)
+    assert rc == 0
+    rc, cts, where = oc.query(s, sets.client, 4)
+    assert rc == 0
+    sid = gc.server_load(sets.server)
+    gcts, gwhere = gc.query(sets.client, 4)
+    assert np.array_equal(gcts, cts)
+    return oc, gc, s, rlk, sets, Ts, cts, where, sid
+
+
+@pytest.mark.parametrize("h,bits,lb", [(1, TOY, 6), (2, TOY, 8), (4, PAPER, 10), (8, LARGE, 12)])
+def test_eval_layers_match_oracle(h, bits, lb):
+    oc, gc, s, rlk, sets, Ts, cts, where, sid = _psi_case(64, bits, h, lb, mu=5, m=20, n=80, planted=5, chunk=2)
+    mu = Ts.shape[0]
+    want_out, dh, de = oc.eval(rlk, cts, Ts, debug=True)
+    gh, ge = gc.eval_layers(sid, cts, 0, mu)
+    assert np.array_equal(gh, dh)
+    assert np.array_equal(ge, de)
+    gh2, ge2 = gc.eval_layers(sid, cts, mu - 2, 2)  # a ragged sub-range
+    assert np.array_equal(gh2, dh[mu - 2:]) and np.array_equal(ge2, de[mu - 2:])
+
+
+@pytest.mark.parametrize("h,bits,lb,N", [(2, TOY, 8, 64), (4, PAPER, 10, 64), (8, LARGE, 12, 64), (2, TOY, 6, 16)])
+def test_eval_matches_oracle_both_modes(h, bits, lb, N):
+    oc, gc, s, rlk, sets, Ts, cts, where, sid = _psi_case(N, bits, h, lb, mu=6, m=min(20, N // 2), n=70,
+                                                          planted=4, chunk=4)
+    for mode in (0, 1):
+        want = oc.eval(rlk, cts, Ts, mode=mode, mask_seed=5)
+        got = gc.eval(sid, cts, mode=mode, mask_seed=5)
+        assert np.array_equal(got, want), mode
+        gslots, gb = gc.decrypt(got)
+        oslots, ob = oc.decrypt(s, want)
+        assert np.array_equal(gslots, oslots)
+        assert abs(gb - ob) < 1e-9 and gb > 0
+        if mode == 0:
+            assert np.array_equal(gslots, brute_indicator(sets.client, sets.server, where, N))
+        else:
+            assert int(gslots.astype(np.int64).sum()) % T == len(sets.planted)
+
+
+def test_eval_device_buffers_and_stream():
+    torch = torch_cuda()
+    oc, gc, s, rlk, sets, Ts, cts, where, sid = _psi_case(64, PAPER, 4, 10, mu=4, m=16, n=60, planted=3)
+    want = oc.eval(rlk, cts, Ts)
+    dct = to_dev(cts)
+    dout = to_dev(np.zeros((2, oc.k, 64), np.uint64))
+    st = torch.cuda.Stream()
+    gc.eval(sid, dct, out=dout, stream=st)
+    st.synchronize()
+    assert np.array_equal(to_host(dout).reshape(want.shape), want)
+    slots, b = gc.decrypt(dout)
+    assert np.array_equal(slots, oc.decrypt(s, want)[0])
+
+
+def test_toy_config_full_parity():
+    """Toy configuration: N=4096, 3 primes (36,36,37), h=2, ell=363, mu=16,
+    64 client / 1024 server 32-bit items, 16 planted."""
+    oc, gc, s, rlk, sets, Ts, cts, where, sid = _psi_case(4096, TOY, 2, 16, mu=16, m=64, n=1024, planted=16)
+    want = oc.eval(rlk, cts, Ts)
+    got = gc.eval(sid, cts)
+    assert np.array_equal(got, want)
+    slots, b = gc.decrypt(got)
+    assert b > 0
+    assert np.array_equal(slots, brute_indicator(sets.client, sets.server, where, 4096))
+    assert int(slots.sum()) == 16
+
+
+# ------------------------------------------------------------- edge cases
+def test_empty_sets_and_all_dummy_table():
+    oc, gc, s, rlk = pair(64, TOY, 2, 8, mu=3)
+    sid = gc.server_load(np.zeros(0, np.uint64))
+    rc, Ts, _ = oc.server_table(np.zeros(0, np.uint64))
+    assert (Ts == np.uint64(0xFFFFFFFFFFFFFFFF)).all()
+    cts, where = gc.query(np.zeros(0, np.uint64), 4)
+    rc, ocs, _ = oc.query(s, np.zeros(0, np.uint64), 4)
+    assert np.array_equal(cts, ocs)
+    got = gc.eval(sid, cts)
+    assert np.array_equal(got, oc.eval(rlk, cts, Ts))
+    slots, b = gc.decrypt(got)
+    assert not slots.any() and b > 0
+
+
+def test_protocol_failures_are_error_codes():
+    import paper_2310_14565_gb300 as pepsi
+
+    oc, gc, s, rlk = pair(16, TOY, 2, 6, mu=1)
+    with pytest.raises(pepsi.PepsiError) as e:
+        gc.server_load(np.arange(200, dtype=np.uint64))  # mu = 1 cannot hold 600 insertions into 16 bins
+    assert e.value.code == pepsi.E_BIN_OVERFLOW
+    with pytest.raises(pepsi.PepsiError) as e:
+        gc.query(np.arange(17, dtype=np.uint64), 1)  # 17 items, 16 bins, no stash
+    assert e.value.code == pepsi.E_CUCKOO_FAIL
+    with pytest.raises(pepsi.PepsiError) as e:
+        gc.eval(7, np.zeros((gc.ell, 2, gc.k, 16), np.uint64))
+    assert e.value.code == pepsi.E_PARAM
+    with pytest.raises(pepsi.PepsiError) as e:
+        pepsi.Context(N=48, prime_bits=TOY)
+    assert e.value.code == pepsi.E_PARAM
+    with pytest.raises(pepsi.PepsiError) as e:
+        pepsi.Context(N=64, prime_bits=TOY, h=3)
+    assert e.value.code == pepsi.E_PARAM

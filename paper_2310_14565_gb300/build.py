@@ -49,7 +49,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
             cmd = [nv, "-c", path, "-o", obj] + common
             cmd += ARCH + ["-lineinfo", "--expt-relaxed-constexpr"]
             if not src.endswith(".cu"):
-                cmd += ["-x", "cu"]
+                cmd += ["-x", "cu", "-diag-suppress", "20208"]
             jobs.append(cmd)
 
     def run(cmd):

@@ -163,6 +163,28 @@ int pepsi_ct_mult(pepsi_ctx* ctx, const uint64_t* a, const uint64_t* b, size_t n
  * form, device memory. */
 int pepsi_relin(pepsi_ctx* ctx, const uint64_t* in, size_t n, uint64_t* out, void* stream);
 
+/* Size of the fixed device array used by pepsi_relin_noalloc. */
+#define PEPSI_NOALLOC_SCRATCH_BYTES (16u << 20)
+
+/* Relinearisation that allocates nothing, for callers that cannot call
+ * cudaMalloc: code running where another allocator has already reserved the
+ * device memory (so cudaMalloc fails), and request loops that must not pay
+ * for an allocation or for the device-wide synchronisation of cudaFree.
+ * The paper has no counterpart; it is the same operation as pepsi_relin
+ * (same arguments, same output words), with its scratch in a fixed device
+ * array of PEPSI_NOALLOC_SCRATCH_BYTES (16 MiB) that every GPU loading the
+ * library holds until the process exits.
+ * in: [n][3][k][N], out: [n][2][k][N], coefficient form, device memory.
+ * The first call on a device looks up the array's device address (once per
+ * device, with that device current); make that first call before any
+ * stream capture.  All calls share the one array and it keeps the last
+ * call's contents, so calls that overlap on the GPU (other streams, other
+ * threads, other contexts) race: serialise them.  Errors: PEPSI_E_PARAM
+ * when n ciphertexts need more than the array holds,
+ * n * ((k+2) + 2) * k * N * 8 bytes (pepsi_last_error gives the sizes), or
+ * when a buffer is not device memory; PEPSI_E_CUDA. */
+int pepsi_relin_noalloc(pepsi_ctx* ctx, const uint64_t* in, size_t n, uint64_t* out, void* stream);
+
 /* Test access to the keys: s (int8[N], host) and the relinearisation keys
  * in coefficient form rlk[k][2][k][N] (host); either may be NULL. */
 int pepsi_export_keys(pepsi_ctx* ctx, int8_t* s, uint64_t* rlk);

@@ -67,6 +67,7 @@ SYMBOLS = {
     "pepsi_ntt": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t, C.c_int, C.c_void_p]),
     "pepsi_ct_mult": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_size_t, C.c_int, C.c_void_p, C.c_void_p]),
     "pepsi_relin": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p]),
+    "pepsi_relin_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p]),
     "pepsi_export_keys": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     "pepsi_profile_enable": (C.c_int, [C.c_void_p, C.c_int]),
     "pepsi_profile_read": (C.c_int, [C.c_void_p, C.POINTER(C.c_char_p), C.POINTER(C.c_uint64),
@@ -238,6 +239,16 @@ class Context:
 
     def relin(self, ct3, n, out, stream=None):
         _check(lib().pepsi_relin(self._h, _ptr(ct3), n, _ptr(out), _stream(stream)), "pepsi_relin")
+
+    def relin_noalloc(self, ct3, n, out, stream=None):
+        """pepsi_relin without any allocation: scratch in the library's fixed
+        16 MiB device array (shared by all calls; do not overlap calls)."""
+        rc = lib().pepsi_relin_noalloc(self._h, _ptr(ct3), n, _ptr(out), _stream(stream))
+        if rc != OK:
+            err = PepsiError(rc, "pepsi_relin_noalloc")
+            if rc == E_PARAM:
+                err.args = (err.args[0] + " [%s]" % lib().pepsi_last_error().decode(),)
+            raise err
 
     def export_keys(self):
         s = np.zeros(self.N, dtype=np.int8)

@@ -7,6 +7,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -400,6 +401,39 @@ void free_set(ServerSet& S) {
   S = ServerSet{};
 }
 
+}  // namespace
+
+// ====================================================== no-allocation path
+// Relinearisation whose scratch lives in a fixed device array instead of
+// memory from cudaMalloc, for callers that cannot allocate (see
+// pepsi_relin_noalloc in pepsi.h).  The array is part of this module: every
+// device that loads the library holds PEPSI_NOALLOC_SCRATCH_BYTES of it
+// until the process exits, and all calls share it.
+static __device__ __align__(256) u64 g_noalloc_scratch[PEPSI_NOALLOC_SCRATCH_BYTES / sizeof(u64)];
+
+namespace {
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+u64* g_noalloc_addr[kMaxDevices] = {};
+
+// Device address of the array on the current device.  In host code the
+// array's name only stands for it; cudaGetSymbolAddress gives the address
+// that kernels may use.  Looked up once per device, with that device current.
+int noalloc_scratch(u64** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_status(e);
+  if (dev < 0 || dev >= kMaxDevices) return PEPSI_E_PARAM;
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_addr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return cuda_status(e);
+    g_noalloc_addr[dev] = static_cast<u64*>(p);
+  }
+  *out = g_noalloc_addr[dev];
+  return PEPSI_OK;
+}
 }  // namespace
 
 // ================================================================ C ABI
@@ -833,6 +867,30 @@ int pepsi_relin(pepsi_ctx* c, const uint64_t* in, size_t n, uint64_t* out, void*
   if (!R) return cuda_status(e);
   relin(c, in, R, (int)n, st);
   ntt(c, false, R, out, n * 2, c->k, 0, kN, kN, st);
+  return cuda_status(cudaGetLastError());
+}
+
+int pepsi_relin_noalloc(pepsi_ctx* c, const uint64_t* in, size_t n, uint64_t* out, void* stream) {
+  if (!c || !in || !out) return PEPSI_E_PARAM;
+  if (!n) return PEPSI_OK;
+  const size_t kN = (size_t)c->k * c->N;
+  const size_t dg_words = n * (size_t)(c->k + 2) * kN, r_words = n * 2 * kN;
+  const size_t need = (dg_words + r_words) * sizeof(u64);
+  if (need > PEPSI_NOALLOC_SCRATCH_BYTES) {
+    g_last_error = "pepsi_relin_noalloc: " + std::to_string(n) + " ciphertexts need " + std::to_string(need) +
+                   " bytes of scratch, the fixed array holds " + std::to_string((size_t)PEPSI_NOALLOC_SCRATCH_BYTES);
+    return PEPSI_E_PARAM;
+  }
+  if (!is_device_ptr(in) || !is_device_ptr(out)) return PEPSI_E_PARAM;
+  u64* base = nullptr;
+  int rc = noalloc_scratch(&base);
+  if (rc) return rc;
+  u64* DG = base;
+  u64* R = base + dg_words;
+  cudaStream_t st = pick(c, stream);
+  // every word of DG and R is written before it is read: nothing to clear
+  launch_relin(c->V, in, c->d_rlk, DG, R, (int)n, st);
+  launch_ntt(c->V, false, R, out, n * 2, c->k, 0, kN, kN, st);
   return cuda_status(cudaGetLastError());
 }
 

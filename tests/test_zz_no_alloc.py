@@ -1,0 +1,52 @@
+"""pepsi_relin_noalloc: relinearisation for callers that cannot allocate
+device memory (another allocator already holds it, or the caller's loop must
+not pay for cudaMalloc / the synchronisation of cudaFree).  Its scratch is a
+fixed 16 MiB device array inside the library, shared by all calls and left
+holding the last call's contents.  Checked through the C ABI against
+pepsi_relin, which allocates its scratch, on two calls in a row with
+different inputs: the second call must not see stale words of the first.
+
+This file is collected last on purpose, so that a run stopping at the first
+failure has already run every other test."""
+import numpy as np
+import pytest
+
+from gpu_helpers import T, pair, to_dev, to_host, torch_cuda
+
+pytestmark = pytest.mark.gpu
+
+
+def _three_component_cts(oc, s, n, seed):
+    rng = np.random.default_rng(seed)
+    m = rng.integers(0, T, (2 * n, oc.N)).astype(np.uint32)
+    cts = oc.encrypt(s, m, seed)
+    return np.stack([oc.ct_mult(cts[i], cts[n + i]) for i in range(n)])
+
+
+@pytest.mark.parametrize("N,bits,n", [(8192, [55, 55, 54, 54], 3), (64, [36, 36, 37], 5)])
+def test_relin_noalloc_matches_relin_on_two_calls(N, bits, n):
+    torch_cuda()
+    oc, gc, s, rlk = pair(N, bits, 1, 4, mu=1)
+    for call, seed in enumerate((11, 12)):
+        ct3 = to_dev(_three_component_cts(oc, s, n, seed))
+        want = to_dev(np.zeros((n, 2, oc.k, N), np.uint64))
+        gc.relin(ct3, n, want)
+        got = to_dev(np.full((n, 2, oc.k, N), 7, np.uint64))
+        gc.relin_noalloc(ct3, n, got)
+        assert np.array_equal(to_host(got), to_host(want)), call
+        slots, budget = oc.decrypt(s, to_host(got).reshape(n, 2, oc.k, N)[0])
+        assert budget > 0
+
+
+def test_relin_noalloc_rejects_oversized_requests():
+    import paper_2310_14565_gb300 as pepsi
+
+    torch_cuda()
+    oc, gc, s, rlk = pair(8192, [55, 55, 54, 54], 1, 4, mu=1)
+    per_ct = (6 + 2) * 4 * 8192 * 8  # ((k+2) + 2) * k * N words of 8 bytes
+    n = (16 << 20) // per_ct + 1
+    ct3 = to_dev(np.zeros((n, 3, 4, 8192), np.uint64))
+    out = to_dev(np.zeros((n, 2, 4, 8192), np.uint64))
+    with pytest.raises(pepsi.PepsiError) as e:
+        gc.relin_noalloc(ct3, n, out)
+    assert e.value.code == pepsi.E_PARAM and "bytes of scratch" in str(e.value)

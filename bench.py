@@ -31,6 +31,8 @@ sys.path.insert(0, ROOT)
 
 METRIC = "server eval ms at 1024 x 2^20 items; ct-mult+relin/s; NTT % of HBM roofline"
 WL = dict(N=8192, prime_bits=[55, 55, 54, 54], h=4, ell=600, lambda_bar=32, mu=526, m=1024, n=1 << 20, planted=102)
+# small case of the same kernels for profiler captures (5.5 GB of resident plaintexts, > L2)
+WL_SMALL = dict(WL, mu=35, n=1 << 14)
 HASH_KEY, KEY_SEED, ENC_SEED = 0x5EED, 3, 4
 WORKLOAD_NAME = ("paper-shaped PSI: N=8192 bins, t=65537, q=4 RNS primes (55,55,54,54 bits), CW code ell=600 h=4, "
                  "mu=526 layers, 1024 client x 2^20 server uniform 64-bit items, 102 planted")
@@ -333,7 +335,14 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--case", choices=["paper", "small"], default="paper",
+                    help="small: the same kernels on 2^14 server items (mu=35), for profiler captures")
     args = ap.parse_args()
+    if args.case == "small":
+        global WORKLOAD_NAME
+        WL.update(WL_SMALL)
+        WORKLOAD_NAME = WORKLOAD_NAME.replace("mu=526", "mu=35").replace("2^20", "2^14") + " (profiling case)"
+        args.no_cpu_baseline = True
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":

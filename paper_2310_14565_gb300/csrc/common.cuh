@@ -24,10 +24,14 @@ typedef int64_t i64;
 #define PEPSI_DUMMY 0xFFFFFFFFFFFFFFFFull
 #define PEPSI_CW_NONE 0xFFFFu
 
-// One modulus: value, Barrett constant floor(2^128/q) = bhi:blo, N^-1 (Shoup).
+// One modulus: value, Barrett constant floor(2^128/q) = bhi:blo, N^-1 (Shoup),
+// and the split point s = ceil(bits(q)/2) of the split operand format
+// (hi << 32 | lo with x = hi 2^s + lo) used by the multiply-accumulate.
 struct DevPrime {
-  u64 q, bhi, blo, ninv, ninvs;
+  u64 q, bhi, blo, ninv, ninvs, split;
 };
+__host__ __device__ __forceinline__ u64 to_split(u64 x, u64 s) { return ((x >> s) << 32) | (x & ((1ull << s) - 1)); }
+__host__ __device__ __forceinline__ u64 from_split(u64 w, u64 s) { return ((w >> 32) << s) | (w & 0xFFFFFFFFull); }
 
 // Constants of the exact RNS conversions (all residues reduced, Shoup
 // companions where the value multiplies a varying operand).

@@ -100,6 +100,8 @@ DevPrime make_prime(u64 q, u32 N) {
   p.blo = (u64)m;
   p.ninv = invmod(N % q, q);
   p.ninvs = shoup_of(p.ninv, q);
+  int bits = 64 - __builtin_clzll(q);
+  p.split = (u64)((bits + 1) / 2);
   return p;
 }
 

@@ -1,6 +1,9 @@
 // Kernels of PEPSI's server evaluation (Algorithms 1, 2, 5) and the client
 // steps around it (Algorithms 3, 7), for sm_103a.  Integer work only: the
 // ciphertext arithmetic is 64-bit modular arithmetic on the CUDA cores.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
 #include <cstdio>
 
 #include "kernels.h"
@@ -68,7 +71,7 @@ __global__ void k_cw_unrank(const u64* __restrict__ T, size_t count, const u64* 
 // ------------------------------------------------- server plaintexts (K3)
 // Block (layer l, j-chunk): bit planes of the layer's codewords, encoded
 // (inverse NTT mod t of the slot vector in bit-reversed order), centred
-// lift into each q_p and forward NTT.
+// lift into each q_p and forward NTT; stored in the split operand format.
 __global__ void k_ptgen(DevView V, const uint16_t* __restrict__ pos, int ell, int h, int JC, u64* P) {
   extern __shared__ u64 sm[];
   const int N = V.N, k = V.k;
@@ -112,52 +115,220 @@ __global__ void k_ptgen(DevView V, const uint16_t* __restrict__ pos, int ell, in
       __syncthreads();
       ntt_fwd_view(poly, V, p);
       u64* out = P + (((size_t)l * ell + j) * k + p) * N;
-      for (int i = threadIdx.x; i < N; i += blockDim.x) out[i] = poly[i];
+      const u64 sp = V.pr[p].split;
+      for (int i = threadIdx.x; i < N; i += blockDim.x) out[i] = to_split(poly[i], sp);
       __syncthreads();
     }
   }
 }
 
 // ------------------------------------------------------- fused MAC (K4)
-// One thread per (prime, point) and LB layers: a 128-bit lazy sum over the
-// ell codeword-bit ciphertexts, one Barrett reduction at the end.
-template <int LB>
-__global__ void __launch_bounds__(256) k_mac(DevView V, const u64* __restrict__ C, const u64* __restrict__ P,
-                                             u64* __restrict__ H, int ell, int L) {
-  const int N = V.N, k = V.k;
-  const size_t kn = (size_t)k * N;
-  const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= kn) return;
-  const int l0 = blockIdx.y * LB;
+// h'[l] = sum_j C[j] * P[l][j] pointwise in the NTT domain, for both
+// ciphertext components.  A block owns TN consecutive (prime, point) words
+// and LB layers.  One producer thread streams P and C tiles of JS codeword
+// bits through NST shared-memory stages, each stage two tiled TMA copies
+// (cp.async.bulk.tensor.3d: a TN x JS x LB box of P and a TN x 2 x JS box of
+// C, completion counted on a "full" mbarrier); consumer warps release a
+// stage through an "empty" mbarrier.  Boxes that cross the end of a
+// dimension are zero-filled by the copy engine, and zeros add nothing.
+// Each consumer thread owns one point and LPT layers.  Operands are in the
+// split format (x = hi 2^s + lo, both halves below 2^32): a 64-bit product
+// is four 32x32->64 multiply-adds into three 64-bit partial sums, folded
+// into the reduced accumulator before they can overflow.  Every mbarrier
+// wait is bounded (about one second); on expiry the block waits, again
+// bounded, for its own copies in flight, sets *err and returns.
+namespace mac {
+constexpr int TN = 128, LB = 8, LPT = 2, JS = 4, NST = 4;
+constexpr int LG = LB / LPT;                    // layer slices per block
+constexpr int CONSUMER_WARPS = (TN / 32) * LG;  // 16
+constexpr int THREADS = (CONSUMER_WARPS + 1) * 32;
+constexpr int P_WORDS = LB * JS * TN, C_WORDS = 2 * JS * TN;
+constexpr int STAGE_WORDS = P_WORDS + C_WORDS;
+constexpr size_t SMEM = (size_t)NST * STAGE_WORDS * 8 + 2 * NST * 8 + 16 + 128;
+}  // namespace mac
+
+__device__ __forceinline__ u64 globaltimer_ns() {
+  u64 t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ void mbar_init(u32 addr, u32 count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(addr), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(u32 addr, u32 bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(addr), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(u32 addr) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(addr) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(u32 addr, u32 parity) {
+  u32 ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(addr), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Wait for phase `parity` of an mbarrier for at most about one second.
+__device__ __forceinline__ bool mbar_wait_bounded(u32 addr, u32 parity) {
+  if (mbar_try_wait(addr, parity)) return true;
+  const u64 t0 = globaltimer_ns();
+  while (!mbar_try_wait(addr, parity))
+    if (globaltimer_ns() - t0 > 1000000000ull) return false;
+  return true;
+}
+__device__ __forceinline__ void tma_load_3d(u32 dst, const CUtensorMap* tm, int c0, int c1, int c2, u32 bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(
+          dst),
+      "l"(reinterpret_cast<u64>(tm)), "r"(c0), "r"(c1), "r"(c2), "r"(bar)
+      : "memory");
+}
+// acc += a * b for 32-bit a, b into a 64-bit sum (one wide multiply-add)
+__device__ __forceinline__ void mad_wide(u64& acc, u32 a, u32 b) {
+  asm("mad.wide.u32 %0, %1, %2, %0;" : "+l"(acc) : "r"(a), "r"(b));
+}
+__device__ __forceinline__ void fold_into(u64& acc, u64& S0, u64& S1, u64& S2, u64 s, const DevPrime& pr) {
+  u64 lo = S0, hi = 0;
+  const u64 a = S1 << s;
+  hi += S1 >> (64 - s);
+  lo += a;
+  hi += lo < a;
+  const u64 b = S2 << (2 * s);
+  hi += S2 >> (64 - 2 * s);
+  lo += b;
+  hi += lo < b;
+  acc = addmod(acc, barrett128(hi, lo, pr.q, pr.bhi, pr.blo), pr.q);
+  S0 = S1 = S2 = 0;
+}
+
+__global__ void __launch_bounds__(mac::THREADS, 1)
+    k_mac(DevView V, const __grid_constant__ CUtensorMap tmP, const __grid_constant__ CUtensorMap tmC,
+          u64* __restrict__ H, int ell, int L, int fold_stages, int* err) {
+  using namespace mac;
+  extern __shared__ __align__(128) u64 sm_raw[];
+  // 128-byte aligned stage buffers for the tensor copies
+  u64* sm = reinterpret_cast<u64*>((reinterpret_cast<uintptr_t>(sm_raw) + 127) & ~(uintptr_t)127);
+  const size_t kN = (size_t)V.k * V.N;
+  const int l0 = blockIdx.x * LB;
   const int nl = min(LB, L - l0);
-  u64 a0l[LB], a0h[LB], a1l[LB], a1h[LB];
-#pragma unroll
-  for (int l = 0; l < LB; ++l) a0l[l] = a0h[l] = a1l[l] = a1h[l] = 0;
-  const u64* c = C + idx;
-  const u64* p = P + (size_t)l0 * ell * kn + idx;
-  const size_t pstride = (size_t)ell * kn;
-  for (int j = 0; j < ell; ++j) {
-    const u64 c0 = __ldg(c + (size_t)j * 2 * kn);
-    const u64 c1 = __ldg(c + (size_t)j * 2 * kn + kn);
-#pragma unroll
-    for (int l = 0; l < LB; ++l) {
-      if (l < nl) {
-        const u64 x = __ldcs(p + l * pstride + (size_t)j * kn);
-        mac128(a0l[l], a0h[l], c0, x);
-        mac128(a1l[l], a1h[l], c1, x);
+  const size_t idx0 = (size_t)blockIdx.y * TN;
+  const int cnt = (int)min((size_t)TN, kN - idx0);
+  const int nst = (ell + JS - 1) / JS;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const u32 sbase = (u32)__cvta_generic_to_shared(sm);
+  const u32 full0 = sbase + (u32)(NST * STAGE_WORDS * 8), empty0 = full0 + NST * 8;
+  int* abort_flag = reinterpret_cast<int*>(sm + NST * STAGE_WORDS + 2 * NST);
+  if (threadIdx.x == 0) {
+    for (int b = 0; b < NST; ++b) {
+      mbar_init(full0 + 8 * b, 1);
+      mbar_init(empty0 + 8 * b, CONSUMER_WARPS);
+    }
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  bool ok = true;
+  int issued = 0;  // producer: stages issued
+  if (warp == CONSUMER_WARPS) {
+    // ---------------- producer: one thread issues two tensor copies per stage
+    if (lane == 0) {
+      asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<u64>(&tmP)) : "memory");
+      asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<u64>(&tmC)) : "memory");
+      for (int st = 0; st < nst; ++st) {
+        const int buf = st % NST;
+        if (st >= NST && !mbar_wait_bounded(empty0 + 8 * buf, (u32)(((st / NST) - 1) & 1))) {
+          ok = false;
+          break;
+        }
+        const u32 bar = full0 + 8 * buf;
+        const u32 sb = sbase + (u32)(buf * STAGE_WORDS * 8);
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        mbar_expect_tx(bar, (u32)STAGE_WORDS * 8);
+        tma_load_3d(sb, &tmP, (int)idx0, st * JS, l0, bar);
+        tma_load_3d(sb + (u32)P_WORDS * 8, &tmC, (int)idx0, 0, st * JS, bar);
+        issued = st + 1;
       }
     }
-  }
-  const int pi = (int)(idx / N);
-  const DevPrime pr = V.pr[pi];
+  } else {
+    // ---------------- consumer warps
+    const int tp = (warp % (TN / 32)) * 32 + lane;  // point within the tile
+    const int g = warp / (TN / 32);                 // layer slice
+    const bool active = tp < cnt;
+    const size_t idx = idx0 + (active ? tp : 0);
+    const DevPrime pr = V.pr[idx / V.N];
+    const u64 sp = pr.split;
+    u64 S0[LPT][2], S1[LPT][2], S2[LPT][2], acc[LPT][2];
 #pragma unroll
-  for (int l = 0; l < LB; ++l) {
-    if (l < nl) {
-      u64* h = H + (size_t)(l0 + l) * 2 * kn + idx;
-      h[0] = barrett128(a0h[l], a0l[l], pr.q, pr.bhi, pr.blo);
-      h[kn] = barrett128(a1h[l], a1l[l], pr.q, pr.bhi, pr.blo);
+    for (int l = 0; l < LPT; ++l)
+#pragma unroll
+      for (int c = 0; c < 2; ++c) S0[l][c] = S1[l][c] = S2[l][c] = acc[l][c] = 0;
+    int since = 0;
+    for (int st = 0; st < nst; ++st) {
+      const int buf = st % NST;
+      if (!mbar_wait_bounded(full0 + 8 * buf, (u32)((st / NST) & 1))) {
+        ok = false;
+        break;
+      }
+      const u64* ps = sm + (size_t)buf * STAGE_WORDS + (size_t)g * LPT * JS * TN + tp;
+      const u64* cs = sm + (size_t)buf * STAGE_WORDS + P_WORDS + tp;
+#pragma unroll
+      for (int jj = 0; jj < JS; ++jj) {
+        const u64 c0 = cs[(jj * 2) * TN], c1 = cs[(jj * 2 + 1) * TN];
+        const u32 c0l = (u32)c0, c0h = (u32)(c0 >> 32), c1l = (u32)c1, c1h = (u32)(c1 >> 32);
+#pragma unroll
+        for (int l = 0; l < LPT; ++l) {
+          const u64 x = ps[(l * JS + jj) * TN];
+          const u32 xl = (u32)x, xh = (u32)(x >> 32);
+          mad_wide(S0[l][0], c0l, xl);
+          mad_wide(S1[l][0], c0l, xh);
+          mad_wide(S1[l][0], c0h, xl);
+          mad_wide(S2[l][0], c0h, xh);
+          mad_wide(S0[l][1], c1l, xl);
+          mad_wide(S1[l][1], c1l, xh);
+          mad_wide(S1[l][1], c1h, xl);
+          mad_wide(S2[l][1], c1h, xh);
+        }
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(empty0 + 8 * buf);
+      if (++since == fold_stages) {
+#pragma unroll
+        for (int l = 0; l < LPT; ++l)
+#pragma unroll
+          for (int c = 0; c < 2; ++c) fold_into(acc[l][c], S0[l][c], S1[l][c], S2[l][c], sp, pr);
+        since = 0;
+      }
+    }
+    if (ok && active) {
+#pragma unroll
+      for (int l = 0; l < LPT; ++l)
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+          fold_into(acc[l][c], S0[l][c], S1[l][c], S2[l][c], sp, pr);
+          const int layer = g * LPT + l;
+          if (layer < nl) H[((size_t)(l0 + layer) * 2 + c) * kN + idx] = acc[l][c];
+        }
     }
   }
+  if (!ok) atomicExch(abort_flag, 1);
+  __syncthreads();
+  if (*abort_flag && warp == CONSUMER_WARPS && lane == 0) {
+    // copies of the last NST issued stages may still be landing: wait for them
+    for (int st = max(0, issued - NST); st < issued; ++st)
+      mbar_wait_bounded(full0 + 8 * (st % NST), (u32)((st / NST) & 1));
+    atomicExch(err, 1);
+  }
+}
+
+// In-place conversion of [rows][N] words between the reduced and the split
+// operand format; row r uses prime r % k.
+__global__ void k_split(DevView V, u64* x, size_t total, int to) {
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= total) return;
+  const u64 s = V.pr[(i / V.N) % V.k].split;
+  x[i] = to ? to_split(x[i], s) : from_split(x[i], s);
 }
 
 // ---------------------------------------------------- RNS conversions
@@ -653,11 +824,50 @@ void launch_ptgen(const DevView& V, const uint16_t* pos, int L, int ell, int h, 
   k_ptgen<<<grid, ntt_threads(V.N), ptgen_smem(V.N), st>>>(V, pos, ell, h, JC, P);
 }
 
-void launch_mac(const DevView& V, const u64* C, const u64* P, u64* H, int ell, int L, cudaStream_t st) {
-  if (L <= 0) return;
-  constexpr int LB = 4;
-  dim3 grid(grid_for((size_t)V.k * V.N, 256), (L + LB - 1) / LB);
-  k_mac<LB><<<grid, 256, 0, st>>>(V, C, P, H, ell, L);
+namespace {
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }
+  return fn;
+}
+// 3-D tensor of 64-bit words: dims (d0, d1, d2), row strides s1, s2 in words, box (b0, b1, b2)
+bool encode3d(CUtensorMap* tm, const u64* base, u64 d0, u64 d1, u64 d2, u64 s1, u64 s2, u32 b0, u32 b1, u32 b2) {
+  auto enc = tensor_map_encoder();
+  if (!enc) return false;
+  const cuuint64_t dims[3] = {d0, d1, d2};
+  const cuuint64_t strides[2] = {s1 * 8, s2 * 8};
+  const cuuint32_t box[3] = {b0, b1, b2};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  return enc(tm, CU_TENSOR_MAP_DATA_TYPE_UINT64, 3, const_cast<u64*>(base), dims, strides, box, estr,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+}  // namespace
+
+cudaError_t launch_mac(const DevView& V, const u64* C, const u64* P, u64* H, int ell, int L, int fold, int* err,
+                       cudaStream_t st) {
+  if (L <= 0) return cudaSuccess;
+  const u64 kN = (u64)V.k * V.N;
+  CUtensorMap tmP, tmC;
+  if (!encode3d(&tmP, P, kN, ell, L, kN, (u64)ell * kN, mac::TN, mac::JS, mac::LB) ||
+      !encode3d(&tmC, C, kN, 2, ell, kN, 2 * kN, mac::TN, 2, mac::JS))
+    return cudaErrorInvalidValue;
+  const int fold_stages = fold / mac::JS > 0 ? fold / mac::JS : 1;
+  dim3 grid((L + mac::LB - 1) / mac::LB, (unsigned)((kN + mac::TN - 1) / mac::TN));
+  k_mac<<<grid, mac::THREADS, mac::SMEM, st>>>(V, tmP, tmC, H, ell, L, fold_stages, err);
+  return cudaSuccess;
+}
+
+void launch_split(const DevView& V, u64* x, size_t groups, bool to, cudaStream_t st) {
+  const size_t total = groups * V.k * V.N;
+  if (!total) return;
+  k_split<<<grid_for(total, 256), 256, 0, st>>>(V, x, total, to ? 1 : 0);
 }
 
 void launch_lift(const DevView& V, const u64* src, u64* dstB, int L, const u64* cst, u64* side, cudaStream_t st) {
@@ -740,6 +950,7 @@ cudaError_t kernels_init(int N) {
   set((const void*)k_ntt<true>);
   set((const void*)k_ntt<false>);
   set((const void*)k_ptgen);
+  set((const void*)k_mac);
   set((const void*)k_relin_ntt);
   set((const void*)k_encrypt);
   set((const void*)k_keygen_sntt);

@@ -12,11 +12,18 @@ void launch_ntt(const DevView& V, bool fwd, const u64* src, u64* dst, size_t out
 // CW-Encode of table entries (colex rank -> positions), pos[count][h], dummy -> PEPSI_CW_NONE.
 void launch_cw_unrank(const u64* T, size_t count, const u64* binom, int ell, int h, uint16_t* pos, cudaStream_t st);
 
-// Server plaintexts pt_s[l][j] in NTT form for L layers: P[L][ell][k][N].
+// Server plaintexts pt_s[l][j] in NTT form for L layers: P[L][ell][k][N], split operand format.
 void launch_ptgen(const DevView& V, const uint16_t* pos, int L, int ell, int h, u64* P, cudaStream_t st);
 
 // Fused ct x pt multiply-accumulate: H[l][c][p][n] = sum_j C[j][c][p][n] * P[l][j][p][n] mod q_p.
-void launch_mac(const DevView& V, const u64* C, const u64* P, u64* H, int ell, int L, cudaStream_t st);
+// C and P in the split operand format, H reduced.  fold: terms between folds of the
+// 64-bit partial sums.  *err is set when a bounded wait for a TMA copy expires.
+// Returns cudaErrorInvalidValue when the tensor maps of the copies cannot be encoded.
+cudaError_t launch_mac(const DevView& V, const u64* C, const u64* P, u64* H, int ell, int L, int fold, int* err,
+                       cudaStream_t st);
+
+// In-place conversion of groups of k rows to (to = true) or from the split operand format.
+void launch_split(const DevView& V, u64* x, size_t groups, bool to, cudaStream_t st);
 
 // Exact centred base extension Q -> B of [L][2][k][N] coefficient rows into [L][2][kb][N].
 // cst (k residues, may be NULL): also records side[l][j] = lift(x0 + cst) - lift(x0) mod p_j

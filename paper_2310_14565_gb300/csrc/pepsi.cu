@@ -57,6 +57,8 @@ struct pepsi_ctx {
   u64* d_s_ntt = nullptr;  // [k][N]
   u64* d_rlk = nullptr;    // [k][2][k][N] NTT form
   u64* d_consts = nullptr; // residues of circuit scalars and constants, [slot][k]
+  int* d_err = nullptr;     // set by kernels whose bounded wait expired
+  int mac_fold = 1;         // terms between folds of the MAC partial sums
   std::vector<ServerSet> sets;
   // scratch, grown on demand
   std::vector<DevBuf> scratch;
@@ -75,10 +77,16 @@ namespace {
 // slots of d_consts
 enum ConstSlot { CS_M3, CS_M7, CS_P12, CS_P16, CS_ZINV, CS_D_TM1, CS_D_2, CS_D_60, CS_COUNT };
 
+// CK: in functions returning cudaError_t; CKS: in functions returning a PEPSI status
 #define CK(x)                              \
   do {                                     \
     cudaError_t e_ = (x);                  \
     if (e_ != cudaSuccess) return e_;      \
+  } while (0)
+#define CKS(x)                                  \
+  do {                                          \
+    cudaError_t e_ = (x);                       \
+    if (e_ != cudaSuccess) return cuda_status(e_); \
   } while (0)
 
 thread_local std::string g_last_error = "no error";
@@ -222,7 +230,7 @@ struct EvalBufs {
   u64 *C, *H, *Hc, *XB, *YB, *T3, *D, *R, *U, *W, *X, *Y, *side, *acc, *Pc, *out, *zero;
 };
 enum ScratchId { S_C, S_H, S_HC, S_XB, S_YB, S_T3, S_D, S_R, S_U, S_W, S_X, S_Y, S_SIDE, S_ACC, S_PC, S_OUT, S_ZERO,
-                 S_IN, S_DEC_Z, S_DEC_M, S_DEC_SLOTS, S_DEC_MAX, S_CT, S_POS, S_TC, S_COUNT };
+                 S_IN, S_DEC_Z, S_DEC_M, S_DEC_SLOTS, S_DEC_MAX, S_CT, S_POS, S_TC, S_HALL, S_COUNT };
 
 cudaError_t eval_bufs(pepsi_ctx* c, int Lc, bool need_pc, EvalBufs* b) {
   cudaError_t e = cudaSuccess;
@@ -300,6 +308,14 @@ void eq_circuit(pepsi_ctx* c, EvalBufs& b, int L, cudaStream_t st) {
   }
 }
 
+// Read and clear the device error flag (the stream must be synchronised).
+bool take_error_flag(pepsi_ctx* c) {
+  int v = 0;
+  if (cudaMemcpy(&v, c->d_err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return false;
+  if (v) cudaMemset(c->d_err, 0, sizeof(int));
+  return v != 0;
+}
+
 // Copy `bytes` between caller and device buffers through the stream.
 cudaError_t copy_any(void* dst, const void* src, size_t bytes, cudaStream_t st) {
   return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, st);
@@ -318,33 +334,45 @@ int eval_core(pepsi_ctx* c, int set_id, const u64* cts, u32 layer0, u32 nl, int 
   EvalBufs b;
   cudaError_t e = eval_bufs(c, Lc, S.dP == nullptr, &b);
   if (e != cudaSuccess) return cuda_status(e);
-  // query ciphertexts to NTT form (a4)
+  // query ciphertexts to NTT form (a4), then to the split operand format of the MAC
   const size_t qwords = (size_t)c->ell * ct2;
   if (is_device_ptr(cts)) {
     ntt(c, true, cts, b.C, (size_t)c->ell * 2, c->k, 0, kN, kN, st);
   } else {
-    CK(copy_any(b.C, cts, qwords * 8, st));
+    CKS(copy_any(b.C, cts, qwords * 8, st));
     ntt(c, true, b.C, b.C, (size_t)c->ell * 2, c->k, 0, kN, kN, st);
+  }
+  {
+    Prof p(c, PC_POINTWISE, st);
+    launch_split(c->V, b.C, (size_t)c->ell * 2, true, st);
+  }
+  // a5 with a resident table: one multiply-accumulate launch over all layers,
+  // so the request is read from HBM once
+  u64* Hall = nullptr;
+  if (S.dP) {
+    Hall = (u64*)scratch(c, S_HALL, (size_t)nl * ct2 * 8, &e);
+    if (!Hall) return cuda_status(e);
+    Prof p(c, PC_MAC, st);
+    CKS(launch_mac(c->V, b.C, S.dP + (size_t)layer0 * c->ell * kN, Hall, c->ell, (int)nl, c->mac_fold, c->d_err,
+                  st));
   }
   bool first = true;
   for (u32 l0 = layer0; l0 < layer0 + nl; l0 += Lc) {
     const int L = (int)std::min<u32>(Lc, layer0 + nl - l0);
-    const u64* P;
-    if (S.dP) {
-      P = S.dP + (size_t)l0 * c->ell * kN;
+    if (Hall) {
+      b.H = Hall + (size_t)(l0 - layer0) * ct2;
     } else {
-      Prof p(c, PC_PTGEN, st);
-      launch_ptgen(c->V, S.dpos + (size_t)l0 * N * c->h, L, c->ell, c->h, b.Pc, st);
-      P = b.Pc;
-    }
-    {
-      Prof p(c, PC_MAC, st);  // a5: fused ct x pt multiply-accumulate
-      launch_mac(c->V, b.C, P, b.H, c->ell, L, st);
+      {
+        Prof p(c, PC_PTGEN, st);
+        launch_ptgen(c->V, S.dpos + (size_t)l0 * N * c->h, L, c->ell, c->h, b.Pc, st);
+      }
+      Prof p(c, PC_MAC, st);  // a5: fused ct x pt multiply-accumulate on the regenerated chunk
+      CKS(launch_mac(c->V, b.C, b.Pc, b.H, c->ell, L, c->mac_fold, c->d_err, st));
     }
     eq_circuit(c, b, L, st);  // a6
     // b.Hc holds h' in coefficient form after the circuit
-    if (h_out) CK(copy_any(h_out + (size_t)(l0 - layer0) * ct2, b.Hc, (size_t)L * ct2 * 8, st));
-    if (e_out) CK(copy_any(e_out + (size_t)(l0 - layer0) * ct3, b.D, (size_t)L * ct3 * 8, st));
+    if (h_out) CKS(copy_any(h_out + (size_t)(l0 - layer0) * ct2, b.Hc, (size_t)L * ct2 * 8, st));
+    if (e_out) CKS(copy_any(e_out + (size_t)(l0 - layer0) * ct3, b.D, (size_t)L * ct3 * 8, st));
     {
       Prof p(c, PC_POINTWISE, st);  // a7: layer accumulation
       launch_accum(c->V, b.D, L, b.acc, first, st);
@@ -360,7 +388,7 @@ int eval_core(pepsi_ctx* c, int set_id, const u64* cts, u32 layer0, u32 nl, int 
       Prof p(c, PC_CLIENT, st);
       launch_mask(c->V, mask_seed, b.out, st);
     }
-    CK(copy_any(out_ct, b.out, ct2 * 8, st));
+    CKS(copy_any(out_ct, b.out, ct2 * 8, st));
   }
   e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_status(e);
@@ -368,6 +396,7 @@ int eval_core(pepsi_ctx* c, int set_id, const u64* cts, u32 layer0, u32 nl, int 
       (e_out && !is_device_ptr(e_out))) {
     e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return cuda_status(e);
+    if (take_error_flag(c)) return PEPSI_E_TIMEOUT;
   }
   if (c->prof) prof_collect(c);
   return PEPSI_OK;
@@ -476,6 +505,7 @@ void pepsi_destroy(pepsi_ctx* c) {
   cudaFree(c->d_s_ntt);
   cudaFree(c->d_rlk);
   cudaFree(c->d_consts);
+  cudaFree(c->d_err);
   if (c->stream) cudaStreamDestroy(c->stream);
   delete c;
 }
@@ -534,6 +564,16 @@ int pepsi_setup(const pepsi_params* params, uint64_t key_seed, pepsi_ctx** out) 
     haveB += std::log2((double)p);
   }
   c->kb = (int)c->B.size();
+  // MAC partial sums: a 32x32-bit product term is below 2^max(bits+1, 2s);
+  // 2^(63 - that) terms fit in 64 bits
+  {
+    int worst = 0;
+    for (u64 q : c->Q) {
+      const int bits = 64 - __builtin_clzll(q), sp = (bits + 1) / 2;
+      worst = std::max(worst, std::max(bits + 1, 2 * sp));
+    }
+    c->mac_fold = 1 << std::min(20, 63 - worst);
+  }
   // roots and tables: Q primes, B primes, then t
   std::vector<u64> all = c->Q;
   all.insert(all.end(), c->B.begin(), c->B.end());
@@ -589,6 +629,8 @@ int pepsi_setup(const pepsi_params* params, uint64_t key_seed, pepsi_ctx** out) 
   if (e == cudaSuccess) e = upload((void**)&c->d_rc, &rcst, sizeof(rcst));
   if (e == cudaSuccess) e = upload((void**)&c->d_binom, binom.data(), binom.size() * 8);
   if (e == cudaSuccess) e = upload((void**)&c->d_consts, consts.data(), consts.size() * 8);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&c->d_err, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemset(c->d_err, 0, sizeof(int));
   if (e == cudaSuccess) e = cudaMalloc((void**)&c->d_s, c->N);
   if (e == cudaSuccess) e = cudaMalloc((void**)&c->d_s_ntt, (size_t)c->k * c->N * 8);
   if (e == cudaSuccess) e = cudaMalloc((void**)&c->d_rlk, (size_t)c->k * 2 * c->k * c->N * 8);
@@ -713,17 +755,16 @@ int pepsi_server_plaintexts(pepsi_ctx* c, int set_id, uint32_t layer0, uint32_t 
   cudaStream_t st = pick(c, stream);
   const size_t per = (size_t)c->ell * c->k * c->N;
   cudaError_t e = cudaSuccess;
+  u64* tmp = (u64*)scratch(c, S_PC, (size_t)nl * per * 8, &e);
+  if (!tmp) return cuda_status(e);
   if (S.dP) {
-    e = copy_any(out, S.dP + (size_t)layer0 * per, (size_t)nl * per * 8, st);
+    CKS(cudaMemcpyAsync(tmp, S.dP + (size_t)layer0 * per, (size_t)nl * per * 8, cudaMemcpyDeviceToDevice, st));
   } else {
-    u64* tmp = (u64*)scratch(c, S_PC, (size_t)nl * per * 8, &e);
-    if (!tmp) return cuda_status(e);
-    {
-      Prof p(c, PC_PTGEN, st);
-      launch_ptgen(c->V, S.dpos + (size_t)layer0 * c->N * c->h, nl, c->ell, c->h, tmp, st);
-    }
-    e = copy_any(out, tmp, (size_t)nl * per * 8, st);
+    Prof p(c, PC_PTGEN, st);
+    launch_ptgen(c->V, S.dpos + (size_t)layer0 * c->N * c->h, nl, c->ell, c->h, tmp, st);
   }
+  launch_split(c->V, tmp, (size_t)nl * c->ell, false, st);  // stored split; returned reduced
+  e = copy_any(out, tmp, (size_t)nl * per * 8, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   return cuda_status(e);
 }
@@ -746,7 +787,7 @@ int pepsi_query(pepsi_ctx* c, const uint64_t* items, size_t m, uint64_t enc_seed
   const bool dev_out = is_device_ptr(cts);
   u64* dct = dev_out ? cts : (u64*)scratch(c, S_CT, words * 8, &e);
   if (!dTc || !dpos || !dct) return cuda_status(e);
-  CK(copy_any(dTc, table.data(), N * 8, st));
+  CKS(copy_any(dTc, table.data(), N * 8, st));
   {
     Prof p(c, PC_CLIENT, st);
     launch_cw_unrank(dTc, N, c->d_binom, c->ell, c->h, dpos, st);
@@ -755,7 +796,7 @@ int pepsi_query(pepsi_ctx* c, const uint64_t* items, size_t m, uint64_t enc_seed
     Prof p(c, PC_CLIENT, st);
     launch_encrypt(c->V, dpos, c->ell, c->h, c->d_s_ntt, enc_seed, dct, st);
   }
-  if (!dev_out) CK(copy_any(cts, dct, words * 8, st));
+  if (!dev_out) CKS(copy_any(cts, dct, words * 8, st));
   e = cudaStreamSynchronize(st);  // the host cuckoo table must outlive the copy
   if (e == cudaSuccess) e = cudaGetLastError();
   if (c->prof) prof_collect(c);
@@ -787,14 +828,14 @@ int pepsi_decrypt(pepsi_ctx* c, const uint64_t* ct, uint32_t* slots, double* noi
   u32* sl = (u32*)scratch(c, S_DEC_SLOTS, N * 4, &e);
   unsigned long long* mx = (unsigned long long*)scratch(c, S_DEC_MAX, 8, &e);
   if (!din || !z || !m || !sl || !mx) return cuda_status(e);
-  CK(copy_any(din, ct, ct2 * 8, st));
+  CKS(copy_any(din, ct, ct2 * 8, st));
   {
     Prof p(c, PC_CLIENT, st, 3);
     launch_decrypt(c->V, din, c->d_s_ntt, z, m, sl, mx, st);
   }
   unsigned long long bits = 0;
-  CK(cudaMemcpyAsync(slots, sl, N * 4, cudaMemcpyDeviceToHost, st));
-  CK(cudaMemcpyAsync(&bits, mx, 8, cudaMemcpyDeviceToHost, st));
+  CKS(cudaMemcpyAsync(slots, sl, N * 4, cudaMemcpyDeviceToHost, st));
+  CKS(cudaMemcpyAsync(&bits, mx, 8, cudaMemcpyDeviceToHost, st));
   e = cudaStreamSynchronize(st);
   if (e == cudaSuccess) e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_status(e);
@@ -851,7 +892,7 @@ int pepsi_ct_mult(pepsi_ctx* c, const uint64_t* a, const uint64_t* b, size_t n, 
     relin(c, D, R, L, st);
     ntt(c, false, R, out, n * 2, c->k, 0, kN, kN, st);
   } else {
-    CK(cudaMemcpyAsync(out, D, n * 3 * kN * 8, cudaMemcpyDeviceToDevice, st));
+    CKS(cudaMemcpyAsync(out, D, n * 3 * kN * 8, cudaMemcpyDeviceToDevice, st));
   }
   return cuda_status(cudaGetLastError());
 }
@@ -898,13 +939,13 @@ int pepsi_export_keys(pepsi_ctx* c, int8_t* s, uint64_t* rlk) {
   if (!c) return PEPSI_E_PARAM;
   cudaStream_t st = c->stream;
   const size_t kN = (size_t)c->k * c->N, words = (size_t)c->k * 2 * kN;
-  if (s) CK(cudaMemcpyAsync(s, c->d_s, c->N, cudaMemcpyDeviceToHost, st));
+  if (s) CKS(cudaMemcpyAsync(s, c->d_s, c->N, cudaMemcpyDeviceToHost, st));
   if (rlk) {
     cudaError_t e = cudaSuccess;
     u64* tmp = (u64*)scratch(c, S_CT, words * 8, &e);
     if (!tmp) return cuda_status(e);
     ntt(c, false, c->d_rlk, tmp, (size_t)c->k * 2, c->k, 0, kN, kN, st);
-    CK(cudaMemcpyAsync(rlk, tmp, words * 8, cudaMemcpyDeviceToHost, st));
+    CKS(cudaMemcpyAsync(rlk, tmp, words * 8, cudaMemcpyDeviceToHost, st));
   }
   return cuda_status(cudaStreamSynchronize(st));
 }

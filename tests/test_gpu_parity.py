@@ -234,3 +234,24 @@ def test_protocol_failures_are_error_codes():
     with pytest.raises(pepsi.PepsiError) as e:
         pepsi.Context(N=64, prime_bits=TOY, h=3)
     assert e.value.code == pepsi.E_PARAM
+
+
+def test_streamed_plaintexts_match_resident():
+    """Server plaintexts regenerated per layer chunk (table not resident)
+    give the same words as the resident table."""
+    import paper_2310_14565_gb300 as pepsi
+
+    oc, gc, s, rlk, sets, Ts, cts, where, sid = _psi_case(64, PAPER, 4, 10, mu=6, m=20, n=70, planted=4, chunk=3)
+    mu = Ts.shape[0]
+    os.environ["PEPSI_CHUNK"] = "3"
+    try:
+        g2 = pepsi.Context(N=64, t=T, prime_bits=PAPER, h=4, lambda_bar=10, mu=mu, hash_key=0x5EED, key_seed=3,
+                           resident_bytes=(1 << 64) - 1)
+    finally:
+        os.environ.pop("PEPSI_CHUNK", None)
+    sid2 = g2.server_load(sets.server)
+    want = oc.eval(rlk, cts, Ts)
+    assert np.array_equal(g2.eval(sid2, cts), want)
+    assert np.array_equal(gc.eval(sid, cts), want)
+    P = g2.server_plaintexts(sid2, 0, mu)
+    assert np.array_equal(P[mu - 1, 3], oc.server_plaintext(Ts, mu - 1, 3))

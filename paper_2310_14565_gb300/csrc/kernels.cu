@@ -11,16 +11,19 @@
 
 namespace {
 
+// Threads of a block running the register-blocked NTT: one per group of 8
+// elements, at most NTT_MAX_THREADS (the kernels below are compiled for it).
+constexpr int NTT_MAX_THREADS = 512;
 inline int ntt_threads(int N) {
-  int t = N / 2;
-  if (t > 512) t = 512;
+  int t = N / 8;
+  if (t > NTT_MAX_THREADS) t = NTT_MAX_THREADS;
   if (t < 32) t = 32;
   return t;
 }
 
 // ------------------------------------------------------------------ NTT
 template <bool FWD>
-__global__ void k_ntt(DevView V, const u64* __restrict__ src, u64* dst, int np, int p0, size_t src_os,
+__global__ void __launch_bounds__(NTT_MAX_THREADS, 2) k_ntt(DevView V, const u64* __restrict__ src, u64* dst, int np, int p0, size_t src_os,
                       size_t dst_os) {
   extern __shared__ u64 sm[];
   const int N = V.N;
@@ -29,13 +32,13 @@ __global__ void k_ntt(DevView V, const u64* __restrict__ src, u64* dst, int np, 
   const size_t o = r / np;
   const u64* s = src + o * src_os + (size_t)pl * N;
   u64* d = dst + o * dst_os + (size_t)pl * N;
-  for (int x = threadIdx.x; x < N; x += blockDim.x) sm[x] = s[x];
+  for (int x = threadIdx.x; x < N; x += blockDim.x) sm[nsw(x)] = s[x];
   __syncthreads();
   if (FWD)
     ntt_fwd_view(sm, V, p0 + pl);
   else
     ntt_inv_view(sm, V, p0 + pl);
-  for (int x = threadIdx.x; x < N; x += blockDim.x) d[x] = sm[x];
+  for (int x = threadIdx.x; x < N; x += blockDim.x) d[x] = sm[nsw(x)];
 }
 
 // ---------------------------------------------------------- CW unranking
@@ -72,7 +75,7 @@ __global__ void k_cw_unrank(const u64* __restrict__ T, size_t count, const u64* 
 // Block (layer l, j-chunk): bit planes of the layer's codewords, encoded
 // (inverse NTT mod t of the slot vector in bit-reversed order), centred
 // lift into each q_p and forward NTT; stored in the split operand format.
-__global__ void k_ptgen(DevView V, const uint16_t* __restrict__ pos, int ell, int h, int JC, u64* P) {
+__global__ void __launch_bounds__(NTT_MAX_THREADS, 2) k_ptgen(DevView V, const uint16_t* __restrict__ pos, int ell, int h, int JC, u64* P) {
   extern __shared__ u64 sm[];
   const int N = V.N, k = V.k;
   const int words = N / 32 > 0 ? N / 32 : 1;
@@ -100,23 +103,23 @@ __global__ void k_ptgen(DevView V, const uint16_t* __restrict__ pos, int ell, in
     if (j >= ell) break;
     for (int i = threadIdx.x; i < N; i += blockDim.x) {
       u32 s = brev_bits(i, V.logN);
-      poly[i] = (bits[jj * words + (s >> 5)] >> (s & 31)) & 1u;
+      poly[nsw(i)] = (bits[jj * words + (s >> 5)] >> (s & 31)) & 1u;
     }
     __syncthreads();
     ntt_inv_view(poly, V, V.tidx);
-    for (int i = threadIdx.x; i < N; i += blockDim.x) mbuf[i] = (u32)poly[i];
+    for (int i = threadIdx.x; i < N; i += blockDim.x) mbuf[i] = (u32)poly[nsw(i)];
     __syncthreads();
     for (int p = 0; p < k; ++p) {
       const u64 q = V.pr[p].q;
       for (int i = threadIdx.x; i < N; i += blockDim.x) {
         u64 m = mbuf[i];
-        poly[i] = m <= thalf ? m : q - (t - m);
+        poly[nsw(i)] = m <= thalf ? m : q - (t - m);
       }
       __syncthreads();
       ntt_fwd_view(poly, V, p);
       u64* out = P + (((size_t)l * ell + j) * k + p) * N;
       const u64 sp = V.pr[p].split;
-      for (int i = threadIdx.x; i < N; i += blockDim.x) out[i] = to_split(poly[i], sp);
+      for (int i = threadIdx.x; i < N; i += blockDim.x) out[i] = to_split(poly[nsw(i)], sp);
       __syncthreads();
     }
   }
@@ -526,7 +529,7 @@ __global__ void k_scale_round(DevView V, const u64* __restrict__ T3, u64* __rest
 // Phase 1, block per row of DG[L][k+2][k][N]: row (l, i, j) holds
 // NTT_{q_j}([d2]_{q_i}) for digits i < k, and NTT_{q_j}(d0), NTT_{q_j}(d1)
 // for i = k, k+1.
-__global__ void k_relin_ntt(DevView V, const u64* __restrict__ D, u64* __restrict__ DG) {
+__global__ void __launch_bounds__(NTT_MAX_THREADS, 2) k_relin_ntt(DevView V, const u64* __restrict__ D, u64* __restrict__ DG) {
   extern __shared__ u64 sm[];
   const int N = V.N, k = V.k;
   const size_t r = blockIdx.x;
@@ -537,12 +540,12 @@ __global__ void k_relin_ntt(DevView V, const u64* __restrict__ D, u64* __restric
   const u64* row = i < k ? D + ((l * 3 + 2) * k + i) * N : D + ((l * 3 + (i - k)) * k + j) * N;
   for (int x = threadIdx.x; x < N; x += blockDim.x) {
     const u64 w = row[x];
-    sm[x] = w >= pj.q ? barrett64(w, pj) : w;
+    sm[nsw(x)] = w >= pj.q ? barrett64(w, pj) : w;
   }
   __syncthreads();
   ntt_fwd_view(sm, V, j);
   u64* out = DG + r * N;
-  for (int x = threadIdx.x; x < N; x += blockDim.x) out[x] = sm[x];
+  for (int x = threadIdx.x; x < N; x += blockDim.x) out[x] = sm[nsw(x)];
 }
 // Phase 2, thread per (l, j, n): R_c = NTT(d_c) + sum_i NTT(d_i) * rlk_i[c],
 // 128-bit lazy sums, one Barrett reduction per output.
@@ -600,7 +603,7 @@ __device__ __forceinline__ u64 smod_dev(i64 v, u64 q) { return v >= 0 ? (u64)v :
 
 // Block per ciphertext j: encode bit plane j, then for each prime sample
 // a, compute c0 = e - a s + round(Q m / t), c1 = a (coefficient form).
-__global__ void k_encrypt(DevView V, const uint16_t* __restrict__ pos, int h, const u64* __restrict__ s_ntt, u64 seed,
+__global__ void __launch_bounds__(NTT_MAX_THREADS, 2) k_encrypt(DevView V, const uint16_t* __restrict__ pos, int h, const u64* __restrict__ s_ntt, u64 seed,
                           u64* cts) {
   extern __shared__ u64 sm[];
   const int N = V.N, k = V.k, j = blockIdx.x;
@@ -613,11 +616,11 @@ __global__ void k_encrypt(DevView V, const uint16_t* __restrict__ pos, int h, co
     u64 bit = 0;
     if (ps[0] != PEPSI_CW_NONE)
       for (int r = 0; r < h; ++r) bit |= (ps[r] == j);
-    poly[i] = bit;
+    poly[nsw(i)] = bit;
   }
   __syncthreads();
   ntt_inv_view(poly, V, V.tidx);
-  for (int i = threadIdx.x; i < N; i += blockDim.x) mbuf[i] = (u32)poly[i];
+  for (int i = threadIdx.x; i < N; i += blockDim.x) mbuf[i] = (u32)poly[nsw(i)];
   __syncthreads();
   const u64 key_e = stream_key(seed, make_stream(STREAM_ENC_E, j, 0));
   for (int p = 0; p < k; ++p) {
@@ -628,17 +631,17 @@ __global__ void k_encrypt(DevView V, const uint16_t* __restrict__ pos, int h, co
     for (int i = threadIdx.x; i < N; i += blockDim.x) {
       const u64 a = sample_uniform(key_a, i, pq.q);
       c1[i] = a;
-      poly[i] = a;
+      poly[nsw(i)] = a;
     }
     __syncthreads();
     ntt_fwd_view(poly, V, p);
     const u64* sr = s_ntt + (size_t)p * N;
-    for (int i = threadIdx.x; i < N; i += blockDim.x) poly[i] = mulmod(poly[i], sr[i], pq);
+    for (int i = threadIdx.x; i < N; i += blockDim.x) poly[nsw(i)] = mulmod(poly[nsw(i)], sr[i], pq);
     __syncthreads();
     ntt_inv_view(poly, V, p);
     for (int i = threadIdx.x; i < N; i += blockDim.x) {
       const u64 e = smod_dev(sample_cbd21(key_e, i), pq.q);
-      c0[i] = addmod(submod(e, poly[i], pq.q), delta_of(V, mbuf[i], p, t), pq.q);
+      c0[i] = addmod(submod(e, poly[nsw(i)], pq.q), delta_of(V, mbuf[i], p, t), pq.q);
     }
     __syncthreads();
   }
@@ -650,18 +653,18 @@ __global__ void k_keygen_s(DevView V, u64 seed, int8_t* s) {
   const u64 key = stream_key(seed, make_stream(STREAM_SK, 0, 0));
   s[n] = (int8_t)((int)sample_uniform(key, n, 3) - 1);
 }
-__global__ void k_keygen_sntt(DevView V, const int8_t* __restrict__ s, u64* s_ntt) {
+__global__ void __launch_bounds__(NTT_MAX_THREADS, 2) k_keygen_sntt(DevView V, const int8_t* __restrict__ s, u64* s_ntt) {
   extern __shared__ u64 sm[];
   const int p = blockIdx.x, N = V.N;
   const u64 q = V.pr[p].q;
-  for (int i = threadIdx.x; i < N; i += blockDim.x) sm[i] = smod_dev(s[i], q);
+  for (int i = threadIdx.x; i < N; i += blockDim.x) sm[nsw(i)] = smod_dev(s[i], q);
   __syncthreads();
   ntt_fwd_view(sm, V, p);
-  for (int i = threadIdx.x; i < N; i += blockDim.x) s_ntt[(size_t)p * N + i] = sm[i];
+  for (int i = threadIdx.x; i < N; i += blockDim.x) s_ntt[(size_t)p * N + i] = sm[nsw(i)];
 }
 // Block (digit i, prime j): rlk_i = (-a_i s + e_i + g_i s^2, a_i) in NTT form,
 // g_i = 1 mod q_i and 0 mod q_j for j != i.
-__global__ void k_keygen_rlk(DevView V, u64 seed, const u64* __restrict__ s_ntt, u64* rlk) {
+__global__ void __launch_bounds__(NTT_MAX_THREADS, 2) k_keygen_rlk(DevView V, u64 seed, const u64* __restrict__ s_ntt, u64* rlk) {
   extern __shared__ u64 sm[];
   const int N = V.N, k = V.k;
   const int i = blockIdx.x / k, j = blockIdx.x % k;
@@ -670,17 +673,17 @@ __global__ void k_keygen_rlk(DevView V, u64 seed, const u64* __restrict__ s_ntt,
   u64* r1 = rlk + (((size_t)i * 2 + 1) * k + j) * N;
   const u64 key_e = stream_key(seed, make_stream(STREAM_RLK_E, i, 0));
   const u64 key_a = stream_key(seed, make_stream(STREAM_RLK_A, i, j));
-  for (int x = threadIdx.x; x < N; x += blockDim.x) sm[x] = smod_dev(sample_cbd21(key_e, x), pj.q);
+  for (int x = threadIdx.x; x < N; x += blockDim.x) sm[nsw(x)] = smod_dev(sample_cbd21(key_e, x), pj.q);
   __syncthreads();
   ntt_fwd_view(sm, V, j);
-  for (int x = threadIdx.x; x < N; x += blockDim.x) r0[x] = sm[x];
+  for (int x = threadIdx.x; x < N; x += blockDim.x) r0[x] = sm[nsw(x)];
   __syncthreads();
-  for (int x = threadIdx.x; x < N; x += blockDim.x) sm[x] = sample_uniform(key_a, x, pj.q);
+  for (int x = threadIdx.x; x < N; x += blockDim.x) sm[nsw(x)] = sample_uniform(key_a, x, pj.q);
   __syncthreads();
   ntt_fwd_view(sm, V, j);
   const u64* sr = s_ntt + (size_t)j * N;
   for (int x = threadIdx.x; x < N; x += blockDim.x) {
-    const u64 a = sm[x], sv = sr[x];
+    const u64 a = sm[nsw(x)], sv = sr[x];
     u64 v = submod(r0[x], mulmod(a, sv, pj), pj.q);
     if (i == j) v = addmod(v, mulmod(sv, sv, pj), pj.q);
     r0[x] = v;
@@ -689,18 +692,18 @@ __global__ void k_keygen_rlk(DevView V, u64 seed, const u64* __restrict__ s_ntt,
 }
 
 // Decryption, step 1: z = c0 + c1 s per prime (coefficient form).
-__global__ void k_dec_z(DevView V, const u64* __restrict__ ct, const u64* __restrict__ s_ntt, u64* z) {
+__global__ void __launch_bounds__(NTT_MAX_THREADS, 2) k_dec_z(DevView V, const u64* __restrict__ ct, const u64* __restrict__ s_ntt, u64* z) {
   extern __shared__ u64 sm[];
   const int p = blockIdx.x, N = V.N, k = V.k;
   const DevPrime pq = V.pr[p];
   const u64* c1 = ct + ((size_t)k + p) * N;
-  for (int i = threadIdx.x; i < N; i += blockDim.x) sm[i] = c1[i];
+  for (int i = threadIdx.x; i < N; i += blockDim.x) sm[nsw(i)] = c1[i];
   __syncthreads();
   ntt_fwd_view(sm, V, p);
-  for (int i = threadIdx.x; i < N; i += blockDim.x) sm[i] = mulmod(sm[i], s_ntt[(size_t)p * N + i], pq);
+  for (int i = threadIdx.x; i < N; i += blockDim.x) sm[nsw(i)] = mulmod(sm[nsw(i)], s_ntt[(size_t)p * N + i], pq);
   __syncthreads();
   ntt_inv_view(sm, V, p);
-  for (int i = threadIdx.x; i < N; i += blockDim.x) z[(size_t)p * N + i] = addmod(sm[i], ct[(size_t)p * N + i], pq.q);
+  for (int i = threadIdx.x; i < N; i += blockDim.x) z[(size_t)p * N + i] = addmod(sm[nsw(i)], ct[(size_t)p * N + i], pq.q);
 }
 // Step 2, per coefficient: m = round(t z / Q) mod t exactly (Garner of
 // w = t z + (Q-1)/2 over Q, then (w - [w]_Q)/Q mod t), and the noise
@@ -747,18 +750,18 @@ __global__ void k_dec_coef(DevView V, const u64* __restrict__ z, u32* m, unsigne
   }
 }
 // Step 3: slots = values of m at psi_t^(2s+1): forward NTT mod t, slot s in position brev(s).
-__global__ void k_dec_slots(DevView V, const u32* __restrict__ m, u32* slots) {
+__global__ void __launch_bounds__(NTT_MAX_THREADS, 2) k_dec_slots(DevView V, const u32* __restrict__ m, u32* slots) {
   extern __shared__ u64 sm[];
   const int N = V.N;
-  for (int i = threadIdx.x; i < N; i += blockDim.x) sm[i] = m[i];
+  for (int i = threadIdx.x; i < N; i += blockDim.x) sm[nsw(i)] = m[i];
   __syncthreads();
   ntt_fwd_view(sm, V, V.tidx);
-  for (int s = threadIdx.x; s < N; s += blockDim.x) slots[s] = (u32)sm[brev_bits(s, V.logN)];
+  for (int s = threadIdx.x; s < N; s += blockDim.x) slots[s] = (u32)sm[nsw(brev_bits(s, V.logN))];
 }
 
 // Cardinality mask (Algorithm 5): r_s uniform in Z_t for s < N-1,
 // r_{N-1} = -sum; c0 += round(Q Encode(r) / t).  One block.
-__global__ void k_mask(DevView V, u64 seed, u64* ct) {
+__global__ void __launch_bounds__(NTT_MAX_THREADS, 2) k_mask(DevView V, u64 seed, u64* ct) {
   extern __shared__ u64 sm[];
   __shared__ u64 red[32];
   const int N = V.N, k = V.k;
@@ -767,7 +770,7 @@ __global__ void k_mask(DevView V, u64 seed, u64* ct) {
   u64 part = 0;
   for (int s = threadIdx.x; s < N - 1; s += blockDim.x) {
     const u64 r = sample_uniform(key, s, t);
-    sm[brev_bits(s, V.logN)] = r;
+    sm[nsw(brev_bits(s, V.logN))] = r;
     part += r;
   }
   part %= t;
@@ -777,7 +780,7 @@ __global__ void k_mask(DevView V, u64 seed, u64* ct) {
   if (threadIdx.x == 0) {
     u64 sum = 0;
     for (int i = 0; i < (int)(blockDim.x + 31) / 32; ++i) sum = (sum + red[i]) % t;
-    sm[brev_bits(N - 1, V.logN)] = (t - sum) % t;
+    sm[nsw(brev_bits(N - 1, V.logN))] = (t - sum) % t;
   }
   __syncthreads();
   ntt_inv_view(sm, V, V.tidx);
@@ -785,7 +788,7 @@ __global__ void k_mask(DevView V, u64 seed, u64* ct) {
     const u64 q = V.pr[p].q;
     for (int n = threadIdx.x; n < N; n += blockDim.x) {
       u64* c = ct + (size_t)p * N + n;
-      *c = addmod(*c, delta_of(V, sm[n], p, t), q);
+      *c = addmod(*c, delta_of(V, sm[nsw(n)], p, t), q);
     }
   }
 }

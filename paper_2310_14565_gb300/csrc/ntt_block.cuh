@@ -4,65 +4,157 @@
 // position i out (radix-2 Cooley-Tukey with twiddles psi^brev(m+i), the
 // merged negacyclic form of Longa-Naehrig), Harvey's lazy butterflies.
 // Inverse: Gentleman-Sande with psi^-brev(m+i), then the factor N^-1.
-// Every thread of the block must call these (they contain __syncthreads).
+//
+// The log2 N radix-2 stages run in phases of RR <= 3 consecutive stages.  The butterflies of stages [s0, s0+RR) only combine the 2^RR
+// elements base + i * (N >> (s0+RR)), i < 2^RR, so a thread loads such a
+// group into registers, runs the RR stages there and stores it back: one
+// shared-memory round trip and one barrier per phase instead of per stage.
+// Every thread of the block must call these (they contain __syncthreads);
+// any block size works (threads loop over the groups).
+//
+// Shared-memory layout: logical element x lives at word nsw(x) = x ^ ((x >> 4)
+// & 15).  Groups of a phase are read at element strides 2^k; with the XOR of
+// the higher index bits into the low four, the 16 words a half-warp reads
+// fall into 16 different 8-byte bank pairs for every such stride, and runs
+// of consecutive elements stay conflict-free.  Callers filling or reading
+// the array index it through nsw().
 #pragma once
 #include "common.cuh"
+
+__device__ __forceinline__ int nsw(int x) { return x ^ ((x >> 4) & 15); }
+
+namespace nttd {
+
+// Phase sizes for log2 N stages: 3-stage phases, then the remainder.
+__device__ __forceinline__ int phase_plan(int logN, int* r) {
+  int n = 0, rest = logN;
+  while (rest >= 3) {
+    r[n++] = 3;
+    rest -= 3;
+  }
+  if (rest) r[n++] = rest;
+  return n;
+}
+
+template <int RR>
+__device__ __forceinline__ void fwd_phase(u64* a, int N, int logN, int s0, u64 q, const u64* __restrict__ tw,
+                                          const u64* __restrict__ tws, bool last) {
+  constexpr int E = 1 << RR;
+  const int slog = logN - s0 - RR;  // log2 of the element stride inside a group
+  const int groups = N >> RR;
+  const u64 q2 = 2 * q;
+  for (int g = threadIdx.x; g < groups; g += blockDim.x) {
+    const int base = ((g >> slog) << (slog + RR)) + (g & ((1 << slog) - 1));
+    u64 x[E];
+#pragma unroll
+    for (int i = 0; i < E; ++i) x[i] = a[nsw(base + (i << slog))];
+#pragma unroll
+    for (int ss = 0; ss < RR; ++ss) {
+      const int s = s0 + ss;
+      const int half = 1 << (RR - 1 - ss);
+#pragma unroll
+      for (int i = 0; i < E; ++i) {
+        if ((i & half) == 0) {
+          const int ti = (1 << s) + ((base + (i << slog)) >> (logN - s));
+          const u64 W = __ldg(tw + ti), Ws = __ldg(tws + ti);
+          u64 U = x[i];
+          U = U >= q2 ? U - q2 : U;
+          const u64 T = shoup_lazy(x[i + half], W, Ws, q);
+          x[i] = U + T;
+          x[i + half] = U + q2 - T;
+        }
+      }
+    }
+    if (last) {
+#pragma unroll
+      for (int i = 0; i < E; ++i) {
+        u64 v = x[i];
+        v = v >= q2 ? v - q2 : v;
+        x[i] = v >= q ? v - q : v;
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < E; ++i) a[nsw(base + (i << slog))] = x[i];
+  }
+}
+
+template <int RR>
+__device__ __forceinline__ void inv_phase(u64* a, int N, int logN, int s0, u64 q, const u64* __restrict__ itw,
+                                          const u64* __restrict__ itws, bool last, u64 ninv, u64 ninvs) {
+  constexpr int E = 1 << RR;
+  const int slog = logN - s0 - RR;
+  const int groups = N >> RR;
+  const u64 q2 = 2 * q;
+  for (int g = threadIdx.x; g < groups; g += blockDim.x) {
+    const int base = ((g >> slog) << (slog + RR)) + (g & ((1 << slog) - 1));
+    u64 x[E];
+#pragma unroll
+    for (int i = 0; i < E; ++i) x[i] = a[nsw(base + (i << slog))];
+#pragma unroll
+    for (int ss = RR - 1; ss >= 0; --ss) {
+      const int s = s0 + ss;
+      const int half = 1 << (RR - 1 - ss);
+#pragma unroll
+      for (int i = 0; i < E; ++i) {
+        if ((i & half) == 0) {
+          const int ti = (1 << s) + ((base + (i << slog)) >> (logN - s));
+          const u64 W = __ldg(itw + ti), Ws = __ldg(itws + ti);
+          const u64 U = x[i], V = x[i + half];
+          u64 S = U + V;
+          S = S >= q2 ? S - q2 : S;
+          x[i] = S;
+          x[i + half] = shoup_lazy(U + q2 - V, W, Ws, q);
+        }
+      }
+    }
+    if (last) {
+#pragma unroll
+      for (int i = 0; i < E; ++i) {
+        const u64 v = shoup_lazy(x[i], ninv, ninvs, q);
+        x[i] = v >= q ? v - q : v;
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < E; ++i) a[nsw(base + (i << slog))] = x[i];
+  }
+}
+
+}  // namespace nttd
 
 // a[0..N) in [0, 4q) on entry, [0, q) on exit.
 __device__ __forceinline__ void ntt_fwd_block(u64* a, int N, int logN, u64 q, const u64* __restrict__ tw,
                                               const u64* __restrict__ tws) {
-  const u64 q2 = 2 * q;
-  const int half = N >> 1;
-  for (int s = 0; s < logN; ++s) {
-    const int m = 1 << s;
-    const int lenlog = logN - 1 - s;
-    const int len = 1 << lenlog;
-    for (int b = threadIdx.x; b < half; b += blockDim.x) {
-      const int i = b >> lenlog;
-      const int j = (i << (lenlog + 1)) + (b & (len - 1));
-      const u64 W = __ldg(tw + m + i), Ws = __ldg(tws + m + i);
-      u64 U = a[j];
-      U = U >= q2 ? U - q2 : U;
-      const u64 T = shoup_lazy(a[j + len], W, Ws, q);
-      a[j] = U + T;
-      a[j + len] = U + q2 - T;
+  int r[16];
+  const int np = nttd::phase_plan(logN, r);
+  int s0 = 0;
+  for (int p = 0; p < np; ++p) {
+    const bool last = p == np - 1;
+    switch (r[p]) {
+      case 3: nttd::fwd_phase<3>(a, N, logN, s0, q, tw, tws, last); break;
+      case 2: nttd::fwd_phase<2>(a, N, logN, s0, q, tw, tws, last); break;
+      default: nttd::fwd_phase<1>(a, N, logN, s0, q, tw, tws, last); break;
     }
+    s0 += r[p];
     __syncthreads();
   }
-  for (int x = threadIdx.x; x < N; x += blockDim.x) {
-    u64 v = a[x];
-    v = v >= q2 ? v - q2 : v;
-    a[x] = v >= q ? v - q : v;
-  }
-  __syncthreads();
 }
 
 // a[0..N) in [0, 2q) on entry, [0, q) on exit.
 __device__ __forceinline__ void ntt_inv_block(u64* a, int N, int logN, u64 q, const u64* __restrict__ itw,
                                               const u64* __restrict__ itws, u64 ninv, u64 ninvs) {
-  const u64 q2 = 2 * q;
-  const int half = N >> 1;
-  for (int s = logN - 1; s >= 0; --s) {
-    const int m = 1 << s;
-    const int lenlog = logN - 1 - s;
-    const int len = 1 << lenlog;
-    for (int b = threadIdx.x; b < half; b += blockDim.x) {
-      const int i = b >> lenlog;
-      const int j = (i << (lenlog + 1)) + (b & (len - 1));
-      const u64 W = __ldg(itw + m + i), Ws = __ldg(itws + m + i);
-      const u64 U = a[j], V = a[j + len];
-      u64 S = U + V;
-      S = S >= q2 ? S - q2 : S;
-      a[j] = S;
-      a[j + len] = shoup_lazy(U + q2 - V, W, Ws, q);
+  int r[16];
+  const int np = nttd::phase_plan(logN, r);
+  int s0 = logN;
+  for (int p = np - 1; p >= 0; --p) {
+    s0 -= r[p];
+    const bool last = p == 0;
+    switch (r[p]) {
+      case 3: nttd::inv_phase<3>(a, N, logN, s0, q, itw, itws, last, ninv, ninvs); break;
+      case 2: nttd::inv_phase<2>(a, N, logN, s0, q, itw, itws, last, ninv, ninvs); break;
+      default: nttd::inv_phase<1>(a, N, logN, s0, q, itw, itws, last, ninv, ninvs); break;
     }
     __syncthreads();
   }
-  for (int x = threadIdx.x; x < N; x += blockDim.x) {
-    u64 v = shoup_lazy(a[x], ninv, ninvs, q);
-    a[x] = v >= q ? v - q : v;
-  }
-  __syncthreads();
 }
 
 __device__ __forceinline__ void ntt_fwd_view(u64* a, const DevView& V, int pi) {

@@ -61,6 +61,14 @@ struct RnsConst {
   u64 qmt;                  // Q mod t
 };
 
+// Primes (Q then B) and conversion constants passed by value to the exact
+// RNS kernels, so that they are read from the kernel parameter space.
+struct RnsArgs {
+  DevPrime pr[PEPSI_MAXQ + PEPSI_MAXB];
+  RnsConst rc;
+  int N, k, kb;
+};
+
 // Everything a kernel needs to know about one parameter set.
 struct DevView {
   int N, logN, k, kb, tidx;  // tidx: index of t among the moduli (= k + kb)
@@ -68,6 +76,7 @@ struct DevView {
   const u64 *tw, *tws;       // [np][N] psi^brev(i) and Shoup companion
   const u64 *itw, *itws;     // [np][N] psi^-brev(i) and Shoup companion
   const RnsConst* rc;
+  const RnsArgs* host_args;  // host copy for by-value launches (not dereferenced on the device)
 };
 
 // ---------------------------------------------------------------- arithmetic

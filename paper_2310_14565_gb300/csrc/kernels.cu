@@ -335,94 +335,113 @@ __global__ void k_split(DevView V, u64* x, size_t total, int to) {
 }
 
 // ---------------------------------------------------- RNS conversions
-// Garner mixed-radix digits over Q of residues x[0..k).
-__device__ __forceinline__ void garner_q(const DevView& V, const u64* x, u64* v) {
-  const RnsConst* rc = V.rc;
+// Templated on the numbers of Q and B primes (0: read them at run time) so
+// that digit arrays stay in registers; primes and constants come by value
+// in the kernel parameter space (RnsArgs).
+
+// Garner mixed-radix digits v over Q of residues x.
+template <int K>
+__device__ __forceinline__ void garner_q(const RnsArgs& A, const u64* x, u64* v) {
+  constexpr int M = K ? K : PEPSI_MAXQ;
 #pragma unroll
-  for (int i = 0; i < PEPSI_MAXQ; ++i) {
-    if (i < V.k) {
-      const DevPrime pi = V.pr[i];
+  for (int i = 0; i < M; ++i) {
+    if (K || i < A.k) {
+      const DevPrime pi = A.pr[i];
       u64 acc = x[i];
 #pragma unroll
-      for (int j = 0; j < PEPSI_MAXQ; ++j) {
+      for (int j = 0; j < M; ++j) {
         if (j < i) {
-          u64 vj = v[j] >= pi.q ? barrett64(v[j], pi) : v[j];
+          const u64 vj = v[j] >= pi.q ? barrett64(v[j], pi) : v[j];
           acc = submod(acc, vj, pi.q);
-          acc = shoup(acc, rc->cq[i][j], rc->cqs[i][j], pi.q);
+          acc = shoup(acc, A.rc.cq[i][j], A.rc.cqs[i][j], pi.q);
         }
       }
       v[i] = acc;
     }
   }
 }
-// Garner mixed-radix digits over B of residues y[0..kb).
-__device__ __forceinline__ void garner_b(const DevView& V, const u64* y, u64* u) {
-  const RnsConst* rc = V.rc;
+// Garner mixed-radix digits u over B of residues y.
+template <int K, int KB>
+__device__ __forceinline__ void garner_b(const RnsArgs& A, const u64* y, u64* u) {
+  constexpr int M = KB ? KB : PEPSI_MAXB;
+  const int k = K ? K : A.k;
 #pragma unroll
-  for (int i = 0; i < PEPSI_MAXB; ++i) {
-    if (i < V.kb) {
-      const DevPrime pi = V.pr[V.k + i];
+  for (int i = 0; i < M; ++i) {
+    if (KB || i < A.kb) {
+      const DevPrime pi = A.pr[k + i];
       u64 acc = y[i];
 #pragma unroll
-      for (int j = 0; j < PEPSI_MAXB; ++j) {
+      for (int j = 0; j < M; ++j) {
         if (j < i) {
-          u64 uj = u[j] >= pi.q ? barrett64(u[j], pi) : u[j];
+          const u64 uj = u[j] >= pi.q ? barrett64(u[j], pi) : u[j];
           acc = submod(acc, uj, pi.q);
-          acc = shoup(acc, rc->cb[i][j], rc->cbs[i][j], pi.q);
+          acc = shoup(acc, A.rc.cb[i][j], A.rc.cbs[i][j], pi.q);
         }
       }
       u[i] = acc;
     }
   }
 }
-// true when the mixed-radix number v (n digits) exceeds the digits h
+// true when the mixed-radix number v (n digits, M at most) exceeds h
+template <int M>
 __device__ __forceinline__ bool digits_greater(const u64* v, const u64* h, int n) {
-  for (int i = n - 1; i >= 0; --i)
-    if (v[i] != h[i]) return v[i] > h[i];
-  return false;
+  bool gt = false, decided = false;
+#pragma unroll
+  for (int i = M - 1; i >= 0; --i) {
+    if (i < n && !decided && v[i] != h[i]) {
+      gt = v[i] > h[i];
+      decided = true;
+    }
+  }
+  return gt;
 }
-// centred value of Q-digits v reduced mod B prime j
-__device__ __forceinline__ u64 q_digits_mod_b(const DevView& V, const u64* v, bool neg, int j) {
-  const DevPrime pb = V.pr[V.k + j];
+// value of the Q-digits v (centred when neg) reduced mod B prime j
+template <int K>
+__device__ __forceinline__ u64 q_digits_mod_b(const RnsArgs& A, const u64* v, bool neg, int j) {
+  constexpr int M = K ? K : PEPSI_MAXQ;
+  const int k = K ? K : A.k;
+  const DevPrime pb = A.pr[k + j];
   u64 lo = 0, hi = 0;
 #pragma unroll
-  for (int l = 0; l < PEPSI_MAXQ; ++l)
-    if (l < V.k) mac128(lo, hi, v[l], V.rc->pqb[j][l]);
-  u64 r = barrett128(hi, lo, pb.q, pb.bhi, pb.blo);
-  return neg ? submod(r, V.rc->qmodb[j], pb.q) : r;
+  for (int l = 0; l < M; ++l)
+    if (K || l < A.k) mac128(lo, hi, v[l], A.rc.pqb[j][l]);
+  const u64 r = barrett128(hi, lo, pb.q, pb.bhi, pb.blo);
+  return neg ? submod(r, A.rc.qmodb[j], pb.q) : r;
 }
 
-__global__ void k_lift(DevView V, const u64* __restrict__ src, u64* __restrict__ dstB, int L,
-                       const u64* __restrict__ cst, u64* __restrict__ side) {
-  const int N = V.N, k = V.k, kb = V.kb;
+template <int K, int KB>
+__global__ void k_lift(const __grid_constant__ RnsArgs A, const u64* __restrict__ src, u64* __restrict__ dstB,
+                       int L, const u64* __restrict__ cst, u64* __restrict__ side) {
+  constexpr int MQ = K ? K : PEPSI_MAXQ, MB = KB ? KB : PEPSI_MAXB;
+  const int N = A.N, k = K ? K : A.k, kb = KB ? KB : A.kb;
   const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;  // over L*2*N
   if (idx >= (size_t)L * 2 * N) return;
   const int n = (int)(idx % N);
   const size_t lc = idx / N;  // layer*2 + comp
-  u64 x[PEPSI_MAXQ], v[PEPSI_MAXQ];
+  u64 x[MQ], v[MQ];
 #pragma unroll
-  for (int i = 0; i < PEPSI_MAXQ; ++i)
-    if (i < k) x[i] = src[(lc * k + i) * N + n];
-  garner_q(V, x, v);
-  const bool neg = digits_greater(v, V.rc->qhalf_dig, k);
-  u64 base[PEPSI_MAXB];
+  for (int i = 0; i < MQ; ++i)
+    if (K || i < k) x[i] = src[(lc * k + i) * N + n];
+  garner_q<K>(A, x, v);
+  const bool neg = digits_greater<MQ>(v, A.rc.qhalf_dig, k);
+  u64 base[MB];
 #pragma unroll
-  for (int j = 0; j < PEPSI_MAXB; ++j)
-    if (j < kb) {
-      base[j] = q_digits_mod_b(V, v, neg, j);
+  for (int j = 0; j < MB; ++j)
+    if (KB || j < kb) {
+      base[j] = q_digits_mod_b<K>(A, v, neg, j);
       dstB[(lc * kb + j) * N + n] = base[j];
     }
   if (cst != nullptr && n == 0 && (lc & 1) == 0) {
     // lift of (x + cst) mod Q at coefficient 0 of component 0
 #pragma unroll
-    for (int i = 0; i < PEPSI_MAXQ; ++i)
-      if (i < k) x[i] = addmod(x[i], cst[i], V.pr[i].q);
-    garner_q(V, x, v);
-    const bool neg2 = digits_greater(v, V.rc->qhalf_dig, k);
+    for (int i = 0; i < MQ; ++i)
+      if (K || i < k) x[i] = addmod(x[i], cst[i], A.pr[i].q);
+    garner_q<K>(A, x, v);
+    const bool neg2 = digits_greater<MQ>(v, A.rc.qhalf_dig, k);
     const size_t layer = lc >> 1;
 #pragma unroll
-    for (int j = 0; j < PEPSI_MAXB; ++j)
-      if (j < kb) side[layer * kb + j] = submod(q_digits_mod_b(V, v, neg2, j), base[j], V.pr[k + j].q);
+    for (int j = 0; j < MB; ++j)
+      if (KB || j < kb) side[layer * kb + j] = submod(q_digits_mod_b<K>(A, v, neg2, j), base[j], A.pr[k + j].q);
   }
 }
 
@@ -484,44 +503,46 @@ __global__ void k_tensor(DevView V, const u64* __restrict__ AQ, const u64* __res
 // y = round(t x / Q) exactly: z = t x + (Q-1)/2, [z]_Q from the Q residues
 // by Garner, y = (z - [z]_Q) / Q computed in B, y centred in B and mapped
 // back to Q by Garner over B.
-__global__ void k_scale_round(DevView V, const u64* __restrict__ T3, u64* __restrict__ D, int L) {
-  const int N = V.N, k = V.k, kb = V.kb, np = k + kb;
+template <int K, int KB>
+__global__ void k_scale_round(const __grid_constant__ RnsArgs A, const u64* __restrict__ T3, u64* __restrict__ D,
+                              int L) {
+  constexpr int MQ = K ? K : PEPSI_MAXQ, MB = KB ? KB : PEPSI_MAXB;
+  const int N = A.N, k = K ? K : A.k, kb = KB ? KB : A.kb, np = k + kb;
   const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;  // over L*3*N
   if (idx >= (size_t)L * 3 * N) return;
   const int n = (int)(idx % N);
   const size_t lc = idx / N;
-  const RnsConst* rc = V.rc;
   const u64* in = T3 + lc * np * N + n;
-  u64 z[PEPSI_MAXQ], v[PEPSI_MAXQ];
+  u64 z[MQ], v[MQ];
 #pragma unroll
-  for (int i = 0; i < PEPSI_MAXQ; ++i)
-    if (i < k) {
-      const u64 q = V.pr[i].q;
-      z[i] = addmod(shoup(in[(size_t)i * N], rc->t_q[i], rc->t_qs[i], q), rc->qhalf_q[i], q);
+  for (int i = 0; i < MQ; ++i)
+    if (K || i < k) {
+      const u64 q = A.pr[i].q;
+      z[i] = addmod(shoup(in[(size_t)i * N], A.rc.t_q[i], A.rc.t_qs[i], q), A.rc.qhalf_q[i], q);
     }
-  garner_q(V, z, v);
-  u64 y[PEPSI_MAXB], u[PEPSI_MAXB];
+  garner_q<K>(A, z, v);
+  u64 y[MB], u[MB];
 #pragma unroll
-  for (int j = 0; j < PEPSI_MAXB; ++j)
-    if (j < kb) {
-      const DevPrime pb = V.pr[k + j];
-      const u64 zb = addmod(shoup(in[(size_t)(k + j) * N], rc->t_b[j], rc->t_bs[j], pb.q), rc->qhalf_b[j], pb.q);
-      const u64 zq = q_digits_mod_b(V, v, false, j);
-      y[j] = shoup(submod(zb, zq, pb.q), rc->qinv_b[j], rc->qinv_bs[j], pb.q);
+  for (int j = 0; j < MB; ++j)
+    if (KB || j < kb) {
+      const DevPrime pb = A.pr[k + j];
+      const u64 zb = addmod(shoup(in[(size_t)(k + j) * N], A.rc.t_b[j], A.rc.t_bs[j], pb.q), A.rc.qhalf_b[j], pb.q);
+      const u64 zq = q_digits_mod_b<K>(A, v, false, j);
+      y[j] = shoup(submod(zb, zq, pb.q), A.rc.qinv_b[j], A.rc.qinv_bs[j], pb.q);
     }
-  garner_b(V, y, u);
-  const bool neg = digits_greater(u, rc->bhalf_dig, kb);
+  garner_b<K, KB>(A, y, u);
+  const bool neg = digits_greater<MB>(u, A.rc.bhalf_dig, kb);
   u64* out = D + lc * k * N + n;
 #pragma unroll
-  for (int i = 0; i < PEPSI_MAXQ; ++i)
-    if (i < k) {
-      const DevPrime pq = V.pr[i];
+  for (int i = 0; i < MQ; ++i)
+    if (K || i < k) {
+      const DevPrime pq = A.pr[i];
       u64 lo = 0, hi = 0;
 #pragma unroll
-      for (int j = 0; j < PEPSI_MAXB; ++j)
-        if (j < kb) mac128(lo, hi, u[j], rc->pbq[i][j]);
-      u64 r = barrett128(hi, lo, pq.q, pq.bhi, pq.blo);
-      out[(size_t)i * N] = neg ? submod(r, rc->bmodq[i], pq.q) : r;
+      for (int j = 0; j < MB; ++j)
+        if (KB || j < kb) mac128(lo, hi, u[j], A.rc.pbq[i][j]);
+      const u64 r = barrett128(hi, lo, pq.q, pq.bhi, pq.blo);
+      out[(size_t)i * N] = neg ? submod(r, A.rc.bmodq[i], pq.q) : r;
     }
 }
 
@@ -708,10 +729,11 @@ __global__ void __launch_bounds__(NTT_MAX_THREADS, 2) k_dec_z(DevView V, const u
 // Step 2, per coefficient: m = round(t z / Q) mod t exactly (Garner of
 // w = t z + (Q-1)/2 over Q, then (w - [w]_Q)/Q mod t), and the noise
 // |[t z]_Q| (centred) as a double, maximised over coefficients.
-__global__ void k_dec_coef(DevView V, const u64* __restrict__ z, u32* m, unsigned long long* maxr) {
+__global__ void k_dec_coef(const __grid_constant__ RnsArgs A, DevView V, const u64* __restrict__ z, u32* m,
+                           unsigned long long* maxr) {
   const int n = blockIdx.x * blockDim.x + threadIdx.x;
   const int N = V.N, k = V.k;
-  const RnsConst* rc = V.rc;
+  const RnsConst* rc = &A.rc;
   const u64 t = V.pr[V.tidx].q;
   double rabs = 0.0;
   if (n < N) {
@@ -722,21 +744,25 @@ __global__ void k_dec_coef(DevView V, const u64* __restrict__ z, u32* m, unsigne
         const u64 q = V.pr[i].q;
         w[i] = addmod(shoup(z[(size_t)i * N + n], rc->t_q[i], rc->t_qs[i], q), rc->qhalf_q[i], q);
       }
-    garner_q(V, w, v);
+    garner_q<0>(A, w, v);
     u64 wq = 0;
-    for (int l = 0; l < k; ++l) wq = (wq + (v[l] % t) * rc->pq_t[l]) % t;
+#pragma unroll
+    for (int l = 0; l < PEPSI_MAXQ; ++l)
+      if (l < k) wq = (wq + (v[l] % t) * rc->pq_t[l]) % t;
     m[n] = (u32)(((rc->qhalf_t + t - wq) % t) * rc->qinv_t % t);
 #pragma unroll
     for (int i = 0; i < PEPSI_MAXQ; ++i)
       if (i < k) w[i] = shoup(z[(size_t)i * N + n], rc->t_q[i], rc->t_qs[i], V.pr[i].q);
-    garner_q(V, w, v);
-    if (digits_greater(v, rc->qhalf_dig, k)) {
+    garner_q<0>(A, w, v);
+    if (digits_greater<PEPSI_MAXQ>(v, rc->qhalf_dig, k)) {
 #pragma unroll
       for (int i = 0; i < PEPSI_MAXQ; ++i)
         if (i < k) w[i] = w[i] ? V.pr[i].q - w[i] : 0;
-      garner_q(V, w, v);
+      garner_q<0>(A, w, v);
     }
-    for (int l = 0; l < k; ++l) rabs += (double)v[l] * rc->pq_d[l];
+#pragma unroll
+    for (int l = 0; l < PEPSI_MAXQ; ++l)
+      if (l < k) rabs += (double)v[l] * rc->pq_d[l];
   }
   // block max, then one atomic per block (positive doubles order like u64)
   __shared__ double red[32];
@@ -873,10 +899,23 @@ void launch_split(const DevView& V, u64* x, size_t groups, bool to, cudaStream_t
   k_split<<<grid_for(total, 256), 256, 0, st>>>(V, x, total, to ? 1 : 0);
 }
 
+// instantiate F<K, KB> for the prime counts in use, else the run-time generic version
+#define PEPSI_RNS_DISPATCH(V, LAUNCH)                 \
+  switch ((V).k * 16 + (V).kb) {                      \
+    case 3 * 16 + 3: LAUNCH(3, 3); break;             \
+    case 4 * 16 + 4: LAUNCH(4, 4); break;             \
+    case 4 * 16 + 5: LAUNCH(4, 5); break;             \
+    case 8 * 16 + 8: LAUNCH(8, 8); break;             \
+    case 8 * 16 + 9: LAUNCH(8, 9); break;             \
+    default: LAUNCH(0, 0); break;                     \
+  }
+
 void launch_lift(const DevView& V, const u64* src, u64* dstB, int L, const u64* cst, u64* side, cudaStream_t st) {
   const size_t total = (size_t)L * 2 * V.N;
   if (!total) return;
-  k_lift<<<grid_for(total, 128), 128, 0, st>>>(V, src, dstB, L, cst, side);
+#define LIFT(KQ, KBB) k_lift<KQ, KBB><<<grid_for(total, 128), 128, 0, st>>>(*V.host_args, src, dstB, L, cst, side)
+  PEPSI_RNS_DISPATCH(V, LIFT)
+#undef LIFT
 }
 
 void launch_tensor(const DevView& V, const u64* AQ, const u64* AB, const u64* BQ, const u64* BB, const u64* cstQ,
@@ -889,7 +928,9 @@ void launch_tensor(const DevView& V, const u64* AQ, const u64* AB, const u64* BQ
 void launch_scale_round(const DevView& V, const u64* T3, u64* D, int L, cudaStream_t st) {
   const size_t total = (size_t)L * 3 * V.N;
   if (!total) return;
-  k_scale_round<<<grid_for(total, 128), 128, 0, st>>>(V, T3, D, L);
+#define SCALE(KQ, KBB) k_scale_round<KQ, KBB><<<grid_for(total, 128), 128, 0, st>>>(*V.host_args, T3, D, L)
+  PEPSI_RNS_DISPATCH(V, SCALE)
+#undef SCALE
 }
 
 void launch_relin(const DevView& V, const u64* D, const u64* rlk, u64* DG, u64* R, int L, cudaStream_t st) {
@@ -927,7 +968,7 @@ void launch_decrypt(const DevView& V, const u64* ct, const u64* s_ntt, u64* zbuf
                     unsigned long long* maxr, cudaStream_t st) {
   cudaMemsetAsync(maxr, 0, sizeof(unsigned long long), st);
   k_dec_z<<<V.k, ntt_threads(V.N), (size_t)V.N * 8, st>>>(V, ct, s_ntt, zbuf);
-  k_dec_coef<<<grid_for(V.N, 128), 128, 0, st>>>(V, zbuf, mbuf, maxr);
+  k_dec_coef<<<grid_for(V.N, 128), 128, 0, st>>>(*V.host_args, V, zbuf, mbuf, maxr);
   k_dec_slots<<<1, ntt_threads(V.N), (size_t)V.N * 8, st>>>(V, mbuf, slots);
 }
 

@@ -47,6 +47,7 @@ struct pepsi_ctx {
   u64 psi_t = 0;
   double log2q = 0;
   DevView V{};
+  RnsArgs rargs{};  // host copy of the by-value RNS kernel parameters
   cudaStream_t stream = nullptr;
   // device tables and keys
   DevPrime* d_pr = nullptr;
@@ -650,6 +651,12 @@ int pepsi_setup(const pepsi_params* params, uint64_t key_seed, pepsi_ctx** out) 
   c->V.itw = c->d_itw;
   c->V.itws = c->d_itws;
   c->V.rc = c->d_rc;
+  for (int i = 0; i < c->k + c->kb; ++i) c->rargs.pr[i] = pr[i];
+  c->rargs.rc = rcst;
+  c->rargs.N = c->N;
+  c->rargs.k = c->k;
+  c->rargs.kb = c->kb;
+  c->V.host_args = &c->rargs;
   {
     Prof p(c, PC_CLIENT, c->stream, 3);
     launch_keygen(c->V, key_seed, c->d_s, c->d_s_ntt, c->d_rlk, c->stream);

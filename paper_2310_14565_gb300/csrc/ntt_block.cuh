@@ -52,11 +52,20 @@ __device__ __forceinline__ void fwd_phase(u64* a, int N, int logN, int s0, u64 q
     for (int ss = 0; ss < RR; ++ss) {
       const int s = s0 + ss;
       const int half = 1 << (RR - 1 - ss);
+      // base has zero bits where i * stride lands, so the twiddle index of
+      // butterfly i splits into a group part and i >> (RR - ss): stage ss of
+      // the phase needs only 2^ss distinct twiddles
+      const int tbase = (1 << s) + (base >> (logN - s));
+      u64 Wt[1 << (RR - 1)], Wst[1 << (RR - 1)];
+#pragma unroll
+      for (int d = 0; d < (1 << ss); ++d) {
+        Wt[d] = __ldg(tw + tbase + d);
+        Wst[d] = __ldg(tws + tbase + d);
+      }
 #pragma unroll
       for (int i = 0; i < E; ++i) {
         if ((i & half) == 0) {
-          const int ti = (1 << s) + ((base + (i << slog)) >> (logN - s));
-          const u64 W = __ldg(tw + ti), Ws = __ldg(tws + ti);
+          const u64 W = Wt[i >> (RR - ss)], Ws = Wst[i >> (RR - ss)];
           u64 U = x[i];
           U = U >= q2 ? U - q2 : U;
           const u64 T = shoup_lazy(x[i + half], W, Ws, q);
@@ -94,11 +103,17 @@ __device__ __forceinline__ void inv_phase(u64* a, int N, int logN, int s0, u64 q
     for (int ss = RR - 1; ss >= 0; --ss) {
       const int s = s0 + ss;
       const int half = 1 << (RR - 1 - ss);
+      const int tbase = (1 << s) + (base >> (logN - s));
+      u64 Wt[1 << (RR - 1)], Wst[1 << (RR - 1)];
+#pragma unroll
+      for (int d = 0; d < (1 << ss); ++d) {
+        Wt[d] = __ldg(itw + tbase + d);
+        Wst[d] = __ldg(itws + tbase + d);
+      }
 #pragma unroll
       for (int i = 0; i < E; ++i) {
         if ((i & half) == 0) {
-          const int ti = (1 << s) + ((base + (i << slog)) >> (logN - s));
-          const u64 W = __ldg(itw + ti), Ws = __ldg(itws + ti);
+          const u64 W = Wt[i >> (RR - ss)], Ws = Wst[i >> (RR - ss)];
           const u64 U = x[i], V = x[i + half];
           u64 S = U + V;
           S = S >= q2 ? S - q2 : S;

@@ -247,6 +247,38 @@ def run_ours(args):
         e2e.append((time.perf_counter() - t) * 1e3)
     e2e_ms = statistics.median(e2e)
 
+    # batched form: 4 requests on the same server set in one pepsi_eval_batch call,
+    # against 4 sequential pepsi_eval calls (same outputs)
+    nbq = 4
+    reqs = [cts_dev] + [torch.from_numpy(ctx.query(sets.client, ENC_SEED + 1 + i)[0].view("int64")).cuda()
+                        for i in range(nbq - 1)]
+    bouts = [torch.empty((2, k, N), dtype=torch.int64, device="cuda") for _ in range(nbq)]
+    souts = [torch.empty((2, k, N), dtype=torch.int64, device="cuda") for _ in range(nbq)]
+    for _ in range(2):
+        ctx.eval_batch([sid] * nbq, reqs, outs=bouts)
+        for i in range(nbq):
+            ctx.eval(sid, reqs[i], out=souts[i])
+    torch.cuda.synchronize()
+    same = all(torch.equal(bouts[i], souts[i]) for i in range(nbq))
+    breps = max(2, min(args.steps // nbq, 8))
+    e0.record(stream)
+    for _ in range(breps):
+        ctx.eval_batch([sid] * nbq, reqs, outs=bouts)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    batch_ms = e0.elapsed_time(e1) / breps
+    e0.record(stream)
+    for _ in range(breps):
+        for i in range(nbq):
+            ctx.eval(sid, reqs[i], out=souts[i])
+    e1.record(stream)
+    torch.cuda.synchronize()
+    seq_ms = e0.elapsed_time(e1) / breps
+    batched = {"requests": nbq, "ms_per_request": round(batch_ms / nbq, 3),
+               "sequential_ms_per_request": round(seq_ms / nbq, 3), "speedup": round(seq_ms / batch_ms, 3),
+               "queries_per_s": round(1e3 * nbq / batch_ms, 2), "identical_outputs": bool(same)}
+    del reqs, bouts, souts
+
     # ct-mult + relin throughput (batch of 64 pairs at the workload's parameters)
     nb = 64
     a = torch.empty((nb, 2, k, N), dtype=torch.int64, device="cuda")
@@ -298,6 +330,7 @@ def run_ours(args):
         "kernel_ms_per_step": {name: round(v[1] / psteps, 3) for name, v in prof.items() if v[0]},
         "e2e": {"value": round(e2e_ms, 3), "unit": "ms", "h2d_bytes_per_step": int(cts_np.nbytes),
                 "d2h_bytes_per_step": int(out_pinned.numel() * 8)},
+        "batched": batched,
         "gpu_launches": int(launches),
         "clocks": clk,
     }

@@ -133,6 +133,17 @@ int pepsi_query(pepsi_ctx* ctx, const uint64_t* items, size_t m, uint64_t enc_se
 int pepsi_eval(pepsi_ctx* ctx, int set_id, const uint64_t* cts, int mode, uint64_t mask_seed, uint64_t* out_ct,
                void* stream);
 
+/* Several requests in one call: request i is evaluated against server set
+ * set_ids[i] exactly as by pepsi_eval (same output words), with mode
+ * modes[i] (NULL: all indicator) and mask seed mask_seeds[i] (NULL: 0).
+ * Requests on the same set are processed in groups of up to 4 whose
+ * multiply-accumulate reads the server plaintexts once for the whole group
+ * (or generates each plaintext chunk once, when the table is not
+ * resident).  cts[i]: [ell][2][k][N], out_cts[i]: [2][k][N], each host or
+ * device.  Errors as pepsi_eval. */
+int pepsi_eval_batch(pepsi_ctx* ctx, int nq, const int* set_ids, const uint64_t* const* cts, const int* modes,
+                     const uint64_t* mask_seeds, uint64_t* const* out_cts, void* stream);
+
 /* The same pipeline on layers [layer0, layer0+nl) only, returning the
  * per-layer intermediate words: h_out[nl][2][k][N] (h', coefficient form)
  * and e_out[nl][3][k][N] (the un-relinearised equality ciphertexts), host

@@ -61,6 +61,8 @@ SYMBOLS = {
     "pepsi_server_plaintexts": (C.c_int, [C.c_void_p, C.c_int, C.c_uint32, C.c_uint32, C.c_void_p, C.c_void_p]),
     "pepsi_query": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t, C.c_uint64, C.c_void_p, C.c_void_p, C.c_void_p]),
     "pepsi_eval": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.c_uint64, C.c_void_p, C.c_void_p]),
+    "pepsi_eval_batch": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_void_p),
+                                   C.POINTER(C.c_int), C.POINTER(C.c_uint64), C.POINTER(C.c_void_p), C.c_void_p]),
     "pepsi_eval_layers": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_uint32, C.c_uint32, C.c_void_p,
                                     C.c_void_p, C.c_void_p]),
     "pepsi_decrypt": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(C.c_double)]),
@@ -221,6 +223,19 @@ class Context:
         _check(lib().pepsi_eval(self._h, set_id, _ptr(cts), mode, mask_seed, _ptr(out), _stream(stream)),
                "pepsi_eval")
         return out
+
+    def eval_batch(self, set_ids, cts_list, modes=None, mask_seeds=None, outs=None, stream=None):
+        """pepsi_eval_batch: one output ciphertext per request."""
+        nq = len(cts_list)
+        if outs is None:
+            outs = [np.zeros((2, self.k, self.N), dtype=np.uint64) for _ in range(nq)]
+        sid = (C.c_int * nq)(*set_ids)
+        cp = (C.c_void_p * nq)(*[_ptr(x) for x in cts_list])
+        op = (C.c_void_p * nq)(*[_ptr(x) for x in outs])
+        md = (C.c_int * nq)(*modes) if modes is not None else None
+        ms = (C.c_uint64 * nq)(*mask_seeds) if mask_seeds is not None else None
+        _check(lib().pepsi_eval_batch(self._h, nq, sid, cp, md, ms, op, _stream(stream)), "pepsi_eval_batch")
+        return outs
 
     def eval_layers(self, set_id, cts, layer0, nl, want_h=True, want_e=True, stream=None):
         h = np.zeros((nl, 2, self.k, self.N), dtype=np.uint64) if want_h else None

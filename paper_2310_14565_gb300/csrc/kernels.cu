@@ -325,6 +325,144 @@ __global__ void __launch_bounds__(mac::THREADS, 1)
   }
 }
 
+// Multi-request variant: QB requests (2..4) against the same plaintexts.
+// Each P tile is read once and feeds 2*QB multiply-accumulates per word;
+// the requests' tiles come as one 4-D TMA box (points x components x bits x
+// requests).  A block owns 128 points and 4 layers; each consumer thread one
+// point and one layer for all QB requests.  Same pipeline, split operands,
+// folding and bounded waits as k_mac.
+namespace macq {
+constexpr int TN = 128, LB = 4, JS = 4, NST = 4, QMAX = 4;
+constexpr int CONSUMER_WARPS = (TN / 32) * LB;  // 16
+constexpr int THREADS = (CONSUMER_WARPS + 1) * 32;
+constexpr int P_WORDS = LB * JS * TN;
+constexpr int STAGE_WORDS = P_WORDS + QMAX * 2 * JS * TN;
+constexpr size_t SMEM = (size_t)NST * STAGE_WORDS * 8 + 2 * NST * 8 + 16 + 128;
+}  // namespace macq
+
+__device__ __forceinline__ void tma_load_4d(u32 dst, const CUtensorMap* tm, int c0, int c1, int c2, int c3, u32 bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], "
+      "[%6];" ::"r"(dst),
+      "l"(reinterpret_cast<u64>(tm)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(bar)
+      : "memory");
+}
+
+template <int QB>
+__global__ void __launch_bounds__(macq::THREADS, 1)
+    k_mac_multi(DevView V, const __grid_constant__ CUtensorMap tmP, const __grid_constant__ CUtensorMap tmC,
+                u64* __restrict__ H, size_t hq, int ell, int L, int fold_stages, int* err) {
+  using namespace macq;
+  extern __shared__ __align__(128) u64 sm_raw[];
+  u64* sm = reinterpret_cast<u64*>((reinterpret_cast<uintptr_t>(sm_raw) + 127) & ~(uintptr_t)127);
+  const size_t kN = (size_t)V.k * V.N;
+  const int l0 = blockIdx.x * LB;
+  const size_t idx0 = (size_t)blockIdx.y * TN;
+  const int cnt = (int)min((size_t)TN, kN - idx0);
+  const int nst = (ell + JS - 1) / JS;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const u32 sbase = (u32)__cvta_generic_to_shared(sm);
+  const u32 full0 = sbase + (u32)(NST * STAGE_WORDS * 8), empty0 = full0 + NST * 8;
+  int* abort_flag = reinterpret_cast<int*>(sm + NST * STAGE_WORDS + 2 * NST);
+  if (threadIdx.x == 0) {
+    for (int b = 0; b < NST; ++b) {
+      mbar_init(full0 + 8 * b, 1);
+      mbar_init(empty0 + 8 * b, CONSUMER_WARPS);
+    }
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  bool ok = true;
+  int issued = 0;
+  if (warp == CONSUMER_WARPS) {
+    if (lane == 0) {
+      asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<u64>(&tmP)) : "memory");
+      asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<u64>(&tmC)) : "memory");
+      const u32 bytes = (u32)(P_WORDS + QB * 2 * JS * TN) * 8;
+      for (int st = 0; st < nst; ++st) {
+        const int buf = st % NST;
+        if (st >= NST && !mbar_wait_bounded(empty0 + 8 * buf, (u32)(((st / NST) - 1) & 1))) {
+          ok = false;
+          break;
+        }
+        const u32 bar = full0 + 8 * buf;
+        const u32 sb = sbase + (u32)(buf * STAGE_WORDS * 8);
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        mbar_expect_tx(bar, bytes);
+        tma_load_3d(sb, &tmP, (int)idx0, st * JS, l0, bar);
+        tma_load_4d(sb + (u32)P_WORDS * 8, &tmC, (int)idx0, 0, st * JS, 0, bar);
+        issued = st + 1;
+      }
+    }
+  } else {
+    const int tp = (warp % (TN / 32)) * 32 + lane;
+    const int g = warp / (TN / 32);  // layer within the block
+    const bool active = tp < cnt;
+    const size_t idx = idx0 + (active ? tp : 0);
+    const DevPrime pr = V.pr[idx / V.N];
+    const u64 sp = pr.split;
+    u64 S0[QB][2], S1[QB][2], S2[QB][2], acc[QB][2];
+#pragma unroll
+    for (int q = 0; q < QB; ++q)
+#pragma unroll
+      for (int c = 0; c < 2; ++c) S0[q][c] = S1[q][c] = S2[q][c] = acc[q][c] = 0;
+    int since = 0;
+    for (int st = 0; st < nst; ++st) {
+      const int buf = st % NST;
+      if (!mbar_wait_bounded(full0 + 8 * buf, (u32)((st / NST) & 1))) {
+        ok = false;
+        break;
+      }
+      const u64* ps = sm + (size_t)buf * STAGE_WORDS + (size_t)g * JS * TN + tp;
+      const u64* cs = sm + (size_t)buf * STAGE_WORDS + P_WORDS + tp;
+#pragma unroll
+      for (int jj = 0; jj < JS; ++jj) {
+        const u64 x = ps[jj * TN];
+        const u32 xl = (u32)x, xh = (u32)(x >> 32);
+#pragma unroll
+        for (int q = 0; q < QB; ++q) {
+          const u64 c0 = cs[((q * JS + jj) * 2) * TN], c1 = cs[((q * JS + jj) * 2 + 1) * TN];
+          const u32 c0l = (u32)c0, c0h = (u32)(c0 >> 32), c1l = (u32)c1, c1h = (u32)(c1 >> 32);
+          mad_wide(S0[q][0], c0l, xl);
+          mad_wide(S1[q][0], c0l, xh);
+          mad_wide(S1[q][0], c0h, xl);
+          mad_wide(S2[q][0], c0h, xh);
+          mad_wide(S0[q][1], c1l, xl);
+          mad_wide(S1[q][1], c1l, xh);
+          mad_wide(S1[q][1], c1h, xl);
+          mad_wide(S2[q][1], c1h, xh);
+        }
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(empty0 + 8 * buf);
+      if (++since == fold_stages) {
+#pragma unroll
+        for (int q = 0; q < QB; ++q)
+#pragma unroll
+          for (int c = 0; c < 2; ++c) fold_into(acc[q][c], S0[q][c], S1[q][c], S2[q][c], sp, pr);
+        since = 0;
+      }
+    }
+    if (ok && active && l0 + g < L) {
+#pragma unroll
+      for (int q = 0; q < QB; ++q)
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+          fold_into(acc[q][c], S0[q][c], S1[q][c], S2[q][c], sp, pr);
+          H[(size_t)q * hq + ((size_t)(l0 + g) * 2 + c) * kN + idx] = acc[q][c];
+        }
+    }
+  }
+  if (!ok) atomicExch(abort_flag, 1);
+  __syncthreads();
+  if (*abort_flag && warp == CONSUMER_WARPS && lane == 0) {
+    for (int st = max(0, issued - NST); st < issued; ++st)
+      mbar_wait_bounded(full0 + 8 * (st % NST), (u32)((st / NST) & 1));
+    atomicExch(err, 1);
+  }
+}
+
 // In-place conversion of [rows][N] words between the reduced and the split
 // operand format; row r uses prime r % k.
 __global__ void k_split(DevView V, u64* x, size_t total, int to) {
@@ -877,7 +1015,39 @@ bool encode3d(CUtensorMap* tm, const u64* base, u64 d0, u64 d1, u64 d2, u64 s1, 
              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
+bool encode4d(CUtensorMap* tm, const u64* base, u64 d0, u64 d1, u64 d2, u64 d3, u64 s1, u64 s2, u64 s3, u32 b0,
+              u32 b1, u32 b2, u32 b3) {
+  auto enc = tensor_map_encoder();
+  if (!enc) return false;
+  const cuuint64_t dims[4] = {d0, d1, d2, d3};
+  const cuuint64_t strides[3] = {s1 * 8, s2 * 8, s3 * 8};
+  const cuuint32_t box[4] = {b0, b1, b2, b3};
+  const cuuint32_t estr[4] = {1, 1, 1, 1};
+  return enc(tm, CU_TENSOR_MAP_DATA_TYPE_UINT64, 4, const_cast<u64*>(base), dims, strides, box, estr,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
 }  // namespace
+
+cudaError_t launch_mac_multi(const DevView& V, const u64* C, int nq, const u64* P, u64* H, size_t hq, int ell, int L,
+                             int fold, int* err, cudaStream_t st) {
+  if (L <= 0 || nq <= 0) return cudaSuccess;
+  if (nq > macq::QMAX) return cudaErrorInvalidValue;
+  const u64 kN = (u64)V.k * V.N;
+  CUtensorMap tmP, tmC;
+  if (!encode3d(&tmP, P, kN, ell, L, kN, (u64)ell * kN, macq::TN, macq::JS, macq::LB) ||
+      !encode4d(&tmC, C, kN, 2, ell, nq, kN, 2 * kN, (u64)ell * 2 * kN, macq::TN, 2, macq::JS, nq))
+    return cudaErrorInvalidValue;
+  const int fold_stages = fold / macq::JS > 0 ? fold / macq::JS : 1;
+  dim3 grid((L + macq::LB - 1) / macq::LB, (unsigned)((kN + macq::TN - 1) / macq::TN));
+  switch (nq) {
+    case 1: k_mac_multi<1><<<grid, macq::THREADS, macq::SMEM, st>>>(V, tmP, tmC, H, hq, ell, L, fold_stages, err); break;
+    case 2: k_mac_multi<2><<<grid, macq::THREADS, macq::SMEM, st>>>(V, tmP, tmC, H, hq, ell, L, fold_stages, err); break;
+    case 3: k_mac_multi<3><<<grid, macq::THREADS, macq::SMEM, st>>>(V, tmP, tmC, H, hq, ell, L, fold_stages, err); break;
+    default: k_mac_multi<4><<<grid, macq::THREADS, macq::SMEM, st>>>(V, tmP, tmC, H, hq, ell, L, fold_stages, err); break;
+  }
+  return cudaSuccess;
+}
 
 cudaError_t launch_mac(const DevView& V, const u64* C, const u64* P, u64* H, int ell, int L, int fold, int* err,
                        cudaStream_t st) {
@@ -995,6 +1165,10 @@ cudaError_t kernels_init(int N) {
   set((const void*)k_ntt<false>);
   set((const void*)k_ptgen);
   set((const void*)k_mac);
+  set((const void*)k_mac_multi<1>);
+  set((const void*)k_mac_multi<2>);
+  set((const void*)k_mac_multi<3>);
+  set((const void*)k_mac_multi<4>);
   set((const void*)k_relin_ntt);
   set((const void*)k_encrypt);
   set((const void*)k_keygen_sntt);

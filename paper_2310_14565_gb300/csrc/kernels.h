@@ -22,6 +22,12 @@ void launch_ptgen(const DevView& V, const uint16_t* pos, int L, int ell, int h, 
 cudaError_t launch_mac(const DevView& V, const u64* C, const u64* P, u64* H, int ell, int L, int fold, int* err,
                        cudaStream_t st);
 
+// The same for nq <= 4 requests sharing the plaintexts: C holds the requests back to back
+// ([nq][ell][2][k][N], split format), H[q] starts at H + q * hq.
+cudaError_t launch_mac_multi(const DevView& V, const u64* C, int nq, const u64* P, u64* H, size_t hq, int ell, int L,
+                             int fold, int* err, cudaStream_t st);
+constexpr int PEPSI_MAC_MAX_REQUESTS = 4;
+
 // In-place conversion of groups of k rows to (to = true) or from the split operand format.
 void launch_split(const DevView& V, u64* x, size_t groups, bool to, cudaStream_t st);
 

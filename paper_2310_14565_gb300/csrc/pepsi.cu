@@ -322,6 +322,36 @@ cudaError_t copy_any(void* dst, const void* src, size_t bytes, cudaStream_t st) 
   return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, st);
 }
 
+// a4: request ciphertexts (host or device) to NTT form, then to the split
+// operand format of the multiply-accumulate, into C.
+cudaError_t prepare_request(pepsi_ctx* c, const u64* cts, u64* C, cudaStream_t st) {
+  const size_t kN = (size_t)c->k * c->N, words = (size_t)c->ell * 2 * kN;
+  if (is_device_ptr(cts)) {
+    ntt(c, true, cts, C, (size_t)c->ell * 2, c->k, 0, kN, kN, st);
+  } else {
+    CK(copy_any(C, cts, words * 8, st));
+    ntt(c, true, C, C, (size_t)c->ell * 2, c->k, 0, kN, kN, st);
+  }
+  Prof p(c, PC_POINTWISE, st);
+  launch_split(c->V, C, (size_t)c->ell * 2, true, st);
+  return cudaSuccess;
+}
+
+// a7 output: ct = (h!)^-1 * R(A) to coefficient form, plus the mask of
+// Algorithm 5 in cardinality mode, copied to out (host or device).
+cudaError_t finish_request(pepsi_ctx* c, EvalBufs& b, const u64* acc, int mode, u64 mask_seed, u64* out,
+                           cudaStream_t st) {
+  const size_t kN = (size_t)c->k * c->N;
+  relin(c, acc, b.R, 1, st);
+  axpy(c, b.zero, cst(c, CS_ZINV), b.R, b.R, 2, st);
+  ntt(c, false, b.R, b.out, 2, c->k, 0, kN, kN, st);
+  if (mode == PEPSI_MODE_CARDINALITY) {
+    Prof p(c, PC_CLIENT, st);
+    launch_mask(c->V, mask_seed, b.out, st);
+  }
+  return copy_any(out, b.out, 2 * kN * 8, st);
+}
+
 // Core of pepsi_eval / pepsi_eval_layers.
 int eval_core(pepsi_ctx* c, int set_id, const u64* cts, u32 layer0, u32 nl, int mode, u64 mask_seed, u64* out_ct,
               u64* h_out, u64* e_out, cudaStream_t st) {
@@ -335,18 +365,7 @@ int eval_core(pepsi_ctx* c, int set_id, const u64* cts, u32 layer0, u32 nl, int 
   EvalBufs b;
   cudaError_t e = eval_bufs(c, Lc, S.dP == nullptr, &b);
   if (e != cudaSuccess) return cuda_status(e);
-  // query ciphertexts to NTT form (a4), then to the split operand format of the MAC
-  const size_t qwords = (size_t)c->ell * ct2;
-  if (is_device_ptr(cts)) {
-    ntt(c, true, cts, b.C, (size_t)c->ell * 2, c->k, 0, kN, kN, st);
-  } else {
-    CKS(copy_any(b.C, cts, qwords * 8, st));
-    ntt(c, true, b.C, b.C, (size_t)c->ell * 2, c->k, 0, kN, kN, st);
-  }
-  {
-    Prof p(c, PC_POINTWISE, st);
-    launch_split(c->V, b.C, (size_t)c->ell * 2, true, st);
-  }
+  CKS(prepare_request(c, cts, b.C, st));
   // a5 with a resident table: one multiply-accumulate launch over all layers,
   // so the request is read from HBM once
   u64* Hall = nullptr;
@@ -380,21 +399,87 @@ int eval_core(pepsi_ctx* c, int set_id, const u64* cts, u32 layer0, u32 nl, int 
     }
     first = false;
   }
-  if (out_ct) {
-    // ct = (h!)^-1 * R(A), to coefficient form, plus the mask for cardinality
-    relin(c, b.acc, b.R, 1, st);
-    axpy(c, b.zero, cst(c, CS_ZINV), b.R, b.R, 2, st);
-    ntt(c, false, b.R, b.out, 2, c->k, 0, kN, kN, st);
-    if (mode == PEPSI_MODE_CARDINALITY) {
-      Prof p(c, PC_CLIENT, st);
-      launch_mask(c->V, mask_seed, b.out, st);
-    }
-    CKS(copy_any(out_ct, b.out, ct2 * 8, st));
-  }
+  if (out_ct) CKS(finish_request(c, b, b.acc, mode, mask_seed, out_ct, st));
   e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_status(e);
   if (!is_device_ptr(out_ct ? (const void*)out_ct : (const void*)b.out) || (h_out && !is_device_ptr(h_out)) ||
       (e_out && !is_device_ptr(e_out))) {
+    e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_status(e);
+    if (take_error_flag(c)) return PEPSI_E_TIMEOUT;
+  }
+  if (c->prof) prof_collect(c);
+  return PEPSI_OK;
+}
+
+// Core of pepsi_eval_batch: requests grouped by server set, up to
+// PEPSI_MAC_MAX_REQUESTS per group; each group's multiply-accumulate reads
+// the plaintexts once (resident table) or generates each chunk once
+// (streamed table); the equality circuits then run request by request.
+enum { S_CB = 41, S_HB = 42, S_ACCB = 43 };
+int eval_batch_core(pepsi_ctx* c, int nq, const int* set_ids, const u64* const* cts, const int* modes,
+                    const u64* mask_seeds, u64* const* outs, cudaStream_t st) {
+  const size_t k = c->k, N = c->N, kN = k * N, ct2 = 2 * kN, ct3 = 3 * kN;
+  const size_t cwords = (size_t)c->ell * ct2;
+  for (int i = 0; i < nq; ++i) {
+    if (set_ids[i] < 0 || set_ids[i] >= (int)c->sets.size() || !c->sets[set_ids[i]].live || !cts[i] || !outs[i])
+      return PEPSI_E_PARAM;
+    const int mode = modes ? modes[i] : PEPSI_MODE_INDICATOR;
+    if (mode != PEPSI_MODE_INDICATOR && mode != PEPSI_MODE_CARDINALITY) return PEPSI_E_PARAM;
+  }
+  std::vector<char> done(nq, 0);
+  bool any_host = false;
+  for (int i0 = 0; i0 < nq; ++i0) {
+    if (done[i0]) continue;
+    // the next group: up to the limit of not yet evaluated requests on this set
+    std::vector<int> grp;
+    for (int i = i0; i < nq && (int)grp.size() < PEPSI_MAC_MAX_REQUESTS; ++i)
+      if (!done[i] && set_ids[i] == set_ids[i0]) grp.push_back(i);
+    for (int i : grp) done[i] = 1;
+    const int G = (int)grp.size();
+    ServerSet& S = c->sets[set_ids[i0]];
+    const u32 mu = S.mu;
+    const int Lc = std::max(1, std::min<int>(c->chunk, (int)mu));
+    EvalBufs b;
+    cudaError_t e = eval_bufs(c, Lc, S.dP == nullptr, &b);
+    if (e != cudaSuccess) return cuda_status(e);
+    u64* CB = (u64*)scratch(c, S_CB, (size_t)G * cwords * 8, &e);
+    const size_t hq = (size_t)(S.dP ? mu : Lc) * ct2;
+    u64* HB = (u64*)scratch(c, S_HB, (size_t)G * hq * 8, &e);
+    u64* ACC = (u64*)scratch(c, S_ACCB, (size_t)G * ct3 * 8, &e);
+    if (!CB || !HB || !ACC) return cuda_status(e);
+    for (int g = 0; g < G; ++g) CKS(prepare_request(c, cts[grp[g]], CB + (size_t)g * cwords, st));
+    if (S.dP) {
+      Prof p(c, PC_MAC, st);
+      CKS(launch_mac_multi(c->V, CB, G, S.dP, HB, hq, c->ell, (int)mu, c->mac_fold, c->d_err, st));
+    }
+    for (u32 l0 = 0; l0 < mu; l0 += Lc) {
+      const int L = (int)std::min<u32>(Lc, mu - l0);
+      if (!S.dP) {
+        {
+          Prof p(c, PC_PTGEN, st);
+          launch_ptgen(c->V, S.dpos + (size_t)l0 * N * c->h, L, c->ell, c->h, b.Pc, st);
+        }
+        Prof p(c, PC_MAC, st);
+        CKS(launch_mac_multi(c->V, CB, G, b.Pc, HB, hq, c->ell, L, c->mac_fold, c->d_err, st));
+      }
+      for (int g = 0; g < G; ++g) {
+        b.H = HB + (size_t)g * hq + (S.dP ? (size_t)l0 * ct2 : 0);
+        eq_circuit(c, b, L, st);
+        Prof p(c, PC_POINTWISE, st);
+        launch_accum(c->V, b.D, L, ACC + (size_t)g * ct3, l0 == 0, st);
+      }
+    }
+    for (int g = 0; g < G; ++g) {
+      const int i = grp[g];
+      CKS(finish_request(c, b, ACC + (size_t)g * ct3, modes ? modes[i] : PEPSI_MODE_INDICATOR,
+                         mask_seeds ? mask_seeds[i] : 0, outs[i], st));
+      any_host |= !is_device_ptr(outs[i]);
+    }
+  }
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_status(e);
+  if (any_host) {
     e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return cuda_status(e);
     if (take_error_flag(c)) return PEPSI_E_TIMEOUT;
@@ -816,6 +901,13 @@ int pepsi_eval(pepsi_ctx* c, int set_id, const uint64_t* cts, int mode, uint64_t
   if (set_id < 0 || set_id >= (int)c->sets.size()) return PEPSI_E_PARAM;
   return eval_core(c, set_id, cts, 0, c->sets[set_id].mu, mode, mask_seed, out_ct, nullptr, nullptr,
                    pick(c, stream));
+}
+
+int pepsi_eval_batch(pepsi_ctx* c, int nq, const int* set_ids, const uint64_t* const* cts, const int* modes,
+                     const uint64_t* mask_seeds, uint64_t* const* out_cts, void* stream) {
+  if (!c || nq < 0 || (nq && (!set_ids || !cts || !out_cts))) return PEPSI_E_PARAM;
+  if (!nq) return PEPSI_OK;
+  return eval_batch_core(c, nq, set_ids, cts, modes, mask_seeds, out_cts, pick(c, stream));
 }
 
 int pepsi_eval_layers(pepsi_ctx* c, int set_id, const uint64_t* cts, uint32_t layer0, uint32_t nl, uint64_t* h_out,

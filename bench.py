@@ -274,7 +274,12 @@ def run_ours(args):
     e1.record(stream)
     torch.cuda.synchronize()
     seq_ms = e0.elapsed_time(e1) / breps
+    ctx.profile(True)
+    ctx.eval_batch([sid] * nbq, reqs, outs=bouts)
+    bprof = ctx.profile_read()
+    ctx.profile(False)
     batched = {"requests": nbq, "ms_per_request": round(batch_ms / nbq, 3),
+               "kernel_ms_per_call": {n: round(v[1], 3) for n, v in bprof.items() if v[0]},
                "sequential_ms_per_request": round(seq_ms / nbq, 3), "speedup": round(seq_ms / batch_ms, 3),
                "queries_per_s": round(1e3 * nbq / batch_ms, 2), "identical_outputs": bool(same)}
     del reqs, bouts, souts
@@ -312,6 +317,15 @@ def run_ours(args):
     ntt_ms = e0.elapsed_time(e1) / 10
     ntt_gbs = 2 * 8 * N * k * count / (ntt_ms * 1e-3) / 1e9
 
+    # integer-pipe peaks (measured here) and the MAC's use of the wide multiply-add:
+    # 2 components x 4 split products per plaintext word
+    wide_peak = pepsi.int_peak(True)
+    mad32_peak = pepsi.int_peak(False)
+    mac_wide_rate = 8.0 * mu * ell * k * N / (mac_launch_ms * 1e-3)
+    int_pipe = {"mad_wide_u32_per_s": round(wide_peak / 1e12, 3), "mad_u32_per_s": round(mad32_peak / 1e12, 3),
+                "unit": "T ops/s", "mac_mad_wide_frac": round(mac_wide_rate / wide_peak, 4),
+                "note": "k_mac issues 8 mad.wide.u32 per plaintext word (2 components x 4 split products)"}
+
     line = {
         "metric": METRIC, "value": round(ms, 3), "unit": "ms", "n_gpus": args.gpus, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms, 3), "higher_is_better": False, "scaling": "weak",
@@ -331,6 +345,7 @@ def run_ours(args):
         "e2e": {"value": round(e2e_ms, 3), "unit": "ms", "h2d_bytes_per_step": int(cts_np.nbytes),
                 "d2h_bytes_per_step": int(out_pinned.numel() * 8)},
         "batched": batched,
+        "int_pipe": int_pipe,
         "gpu_launches": int(launches),
         "clocks": clk,
     }

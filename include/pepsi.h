@@ -136,7 +136,7 @@ int pepsi_eval(pepsi_ctx* ctx, int set_id, const uint64_t* cts, int mode, uint64
 /* Several requests in one call: request i is evaluated against server set
  * set_ids[i] exactly as by pepsi_eval (same output words), with mode
  * modes[i] (NULL: all indicator) and mask seed mask_seeds[i] (NULL: 0).
- * Requests on the same set are processed in groups of up to 4 whose
+ * Requests on the same set are processed in groups of up to 2 whose
  * multiply-accumulate reads the server plaintexts once for the whole group
  * (or generates each plaintext chunk once, when the table is not
  * resident).  cts[i]: [ell][2][k][N], out_cts[i]: [2][k][N], each host or
@@ -199,6 +199,14 @@ int pepsi_relin_noalloc(pepsi_ctx* ctx, const uint64_t* in, size_t n, uint64_t* 
 /* Test access to the keys: s (int8[N], host) and the relinearisation keys
  * in coefficient form rlk[k][2][k][N] (host); either may be NULL. */
 int pepsi_export_keys(pepsi_ctx* ctx, int8_t* s, uint64_t* rlk);
+
+/* Measurement helper (no paper counterpart): the integer-pipe throughput of
+ * the multiply forms the kernels use, measured on the current device with
+ * independent chains on every SM.  wide = 1: 32x32->64 multiply-adds
+ * (mad.wide.u32, the MAC's inner operation); wide = 0: 32-bit multiply-adds.
+ * *ops_per_s receives operations per second for the whole GPU.  Allocates
+ * 8 bytes of device memory for the duration of the call. */
+int pepsi_int_peak(int wide, double* ops_per_s);
 
 /* Per-kernel timing with CUDA events on the launching stream: enable (1) /
  * disable (0) and read back {launches, total milliseconds} per kernel

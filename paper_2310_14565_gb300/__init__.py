@@ -74,6 +74,7 @@ SYMBOLS = {
     "pepsi_profile_enable": (C.c_int, [C.c_void_p, C.c_int]),
     "pepsi_profile_read": (C.c_int, [C.c_void_p, C.POINTER(C.c_char_p), C.POINTER(C.c_uint64),
                                      C.POINTER(C.c_double), C.c_int]),
+    "pepsi_int_peak": (C.c_int, [C.c_int, C.POINTER(C.c_double)]),
     "pepsi_destroy": (None, [C.c_void_p]),
     "pepsi_strerror": (C.c_char_p, [C.c_int]),
     "pepsi_last_error": (C.c_char_p, []),
@@ -137,6 +138,13 @@ def _stream(s):
 def _check(rc, what):
     if rc != OK:
         raise PepsiError(rc, what)
+
+
+def int_peak(wide=True):
+    """Measured integer multiply-add throughput of the current GPU (ops/s)."""
+    v = C.c_double(0)
+    _check(lib().pepsi_int_peak(int(wide), C.byref(v)), "pepsi_int_peak")
+    return v.value
 
 
 class Context:

@@ -4,6 +4,7 @@
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
+#include <algorithm>
 #include <cstdio>
 
 #include "kernels.h"
@@ -192,6 +193,21 @@ __device__ __forceinline__ void tma_load_3d(u32 dst, const CUtensorMap* tm, int 
 __device__ __forceinline__ void mad_wide(u64& acc, u32 a, u32 b) {
   asm("mad.wide.u32 %0, %1, %2, %0;" : "+l"(acc) : "r"(a), "r"(b));
 }
+// S0 + S1 2^s + S2 2^2s reduced mod q back into S0 (S1 = S2 = 0); S0 then
+// restarts below q, which the fold interval leaves room for.
+__device__ __forceinline__ void fold_inplace(u64& S0, u64& S1, u64& S2, u64 s, const DevPrime& pr) {
+  u64 lo = S0, hi = 0;
+  const u64 a = S1 << s;
+  hi += S1 >> (64 - s);
+  lo += a;
+  hi += lo < a;
+  const u64 b = S2 << (2 * s);
+  hi += S2 >> (64 - 2 * s);
+  lo += b;
+  hi += lo < b;
+  S0 = barrett128(hi, lo, pr.q, pr.bhi, pr.blo);
+  S1 = S2 = 0;
+}
 __device__ __forceinline__ void fold_into(u64& acc, u64& S0, u64& S1, u64& S2, u64 s, const DevPrime& pr) {
   u64 lo = S0, hi = 0;
   const u64 a = S1 << s;
@@ -325,15 +341,17 @@ __global__ void __launch_bounds__(mac::THREADS, 1)
   }
 }
 
-// Multi-request variant: QB requests (2..4) against the same plaintexts.
+// Multi-request variant: QB requests (1 or 2) against the same plaintexts.
 // Each P tile is read once and feeds 2*QB multiply-accumulates per word;
 // the requests' tiles come as one 4-D TMA box (points x components x bits x
-// requests).  A block owns 128 points and 4 layers; each consumer thread one
-// point and one layer for all QB requests.  Same pipeline, split operands,
-// folding and bounded waits as k_mac.
+// requests).  Same tiling as k_mac (128 points x 8 layers per block, each
+// consumer thread one point and two layers, here for all QB requests), so a
+// request word loaded from shared memory serves two layers.  Same pipeline,
+// split operands, folding and bounded waits as k_mac.
 namespace macq {
-constexpr int TN = 128, LB = 4, JS = 4, NST = 4, QMAX = 4;
-constexpr int CONSUMER_WARPS = (TN / 32) * LB;  // 16
+constexpr int TN = 128, LB = 8, LPT = 2, JS = 4, NST = 4, QMAX = 2;
+constexpr int LG = LB / LPT;
+constexpr int CONSUMER_WARPS = (TN / 32) * LG;  // 16
 constexpr int THREADS = (CONSUMER_WARPS + 1) * 32;
 constexpr int P_WORDS = LB * JS * TN;
 constexpr int STAGE_WORDS = P_WORDS + QMAX * 2 * JS * TN;
@@ -357,6 +375,7 @@ __global__ void __launch_bounds__(macq::THREADS, 1)
   u64* sm = reinterpret_cast<u64*>((reinterpret_cast<uintptr_t>(sm_raw) + 127) & ~(uintptr_t)127);
   const size_t kN = (size_t)V.k * V.N;
   const int l0 = blockIdx.x * LB;
+  const int nl = min(LB, L - l0);
   const size_t idx0 = (size_t)blockIdx.y * TN;
   const int cnt = (int)min((size_t)TN, kN - idx0);
   const int nst = (ell + JS - 1) / JS;
@@ -397,16 +416,18 @@ __global__ void __launch_bounds__(macq::THREADS, 1)
     }
   } else {
     const int tp = (warp % (TN / 32)) * 32 + lane;
-    const int g = warp / (TN / 32);  // layer within the block
+    const int g = warp / (TN / 32);  // layer slice
     const bool active = tp < cnt;
     const size_t idx = idx0 + (active ? tp : 0);
     const DevPrime pr = V.pr[idx / V.N];
     const u64 sp = pr.split;
-    u64 S0[QB][2], S1[QB][2], S2[QB][2], acc[QB][2];
+    u64 S0[LPT][QB][2], S1[LPT][QB][2], S2[LPT][QB][2];
 #pragma unroll
-    for (int q = 0; q < QB; ++q)
+    for (int l = 0; l < LPT; ++l)
 #pragma unroll
-      for (int c = 0; c < 2; ++c) S0[q][c] = S1[q][c] = S2[q][c] = acc[q][c] = 0;
+      for (int q = 0; q < QB; ++q)
+#pragma unroll
+        for (int c = 0; c < 2; ++c) S0[l][q][c] = S1[l][q][c] = S2[l][q][c] = 0;
     int since = 0;
     for (int st = 0; st < nst; ++st) {
       const int buf = st % NST;
@@ -414,44 +435,57 @@ __global__ void __launch_bounds__(macq::THREADS, 1)
         ok = false;
         break;
       }
-      const u64* ps = sm + (size_t)buf * STAGE_WORDS + (size_t)g * JS * TN + tp;
+      const u64* ps = sm + (size_t)buf * STAGE_WORDS + (size_t)g * LPT * JS * TN + tp;
       const u64* cs = sm + (size_t)buf * STAGE_WORDS + P_WORDS + tp;
 #pragma unroll
       for (int jj = 0; jj < JS; ++jj) {
-        const u64 x = ps[jj * TN];
-        const u32 xl = (u32)x, xh = (u32)(x >> 32);
+        u32 cl[QB][2], ch[QB][2];
 #pragma unroll
-        for (int q = 0; q < QB; ++q) {
-          const u64 c0 = cs[((q * JS + jj) * 2) * TN], c1 = cs[((q * JS + jj) * 2 + 1) * TN];
-          const u32 c0l = (u32)c0, c0h = (u32)(c0 >> 32), c1l = (u32)c1, c1h = (u32)(c1 >> 32);
-          mad_wide(S0[q][0], c0l, xl);
-          mad_wide(S1[q][0], c0l, xh);
-          mad_wide(S1[q][0], c0h, xl);
-          mad_wide(S2[q][0], c0h, xh);
-          mad_wide(S0[q][1], c1l, xl);
-          mad_wide(S1[q][1], c1l, xh);
-          mad_wide(S1[q][1], c1h, xl);
-          mad_wide(S2[q][1], c1h, xh);
+        for (int q = 0; q < QB; ++q)
+#pragma unroll
+          for (int c = 0; c < 2; ++c) {
+            const u64 w = cs[((q * JS + jj) * 2 + c) * TN];
+            cl[q][c] = (u32)w;
+            ch[q][c] = (u32)(w >> 32);
+          }
+#pragma unroll
+        for (int l = 0; l < LPT; ++l) {
+          const u64 x = ps[(l * JS + jj) * TN];
+          const u32 xl = (u32)x, xh = (u32)(x >> 32);
+#pragma unroll
+          for (int q = 0; q < QB; ++q)
+#pragma unroll
+            for (int c = 0; c < 2; ++c) {
+              mad_wide(S0[l][q][c], cl[q][c], xl);
+              mad_wide(S1[l][q][c], cl[q][c], xh);
+              mad_wide(S1[l][q][c], ch[q][c], xl);
+              mad_wide(S2[l][q][c], ch[q][c], xh);
+            }
         }
       }
       __syncwarp();
       if (lane == 0) mbar_arrive(empty0 + 8 * buf);
       if (++since == fold_stages) {
 #pragma unroll
-        for (int q = 0; q < QB; ++q)
+        for (int l = 0; l < LPT; ++l)
 #pragma unroll
-          for (int c = 0; c < 2; ++c) fold_into(acc[q][c], S0[q][c], S1[q][c], S2[q][c], sp, pr);
+          for (int q = 0; q < QB; ++q)
+#pragma unroll
+            for (int c = 0; c < 2; ++c) fold_inplace(S0[l][q][c], S1[l][q][c], S2[l][q][c], sp, pr);
         since = 0;
       }
     }
-    if (ok && active && l0 + g < L) {
+    if (ok && active) {
 #pragma unroll
-      for (int q = 0; q < QB; ++q)
+      for (int l = 0; l < LPT; ++l)
 #pragma unroll
-        for (int c = 0; c < 2; ++c) {
-          fold_into(acc[q][c], S0[q][c], S1[q][c], S2[q][c], sp, pr);
-          H[(size_t)q * hq + ((size_t)(l0 + g) * 2 + c) * kN + idx] = acc[q][c];
-        }
+        for (int q = 0; q < QB; ++q)
+#pragma unroll
+          for (int c = 0; c < 2; ++c) {
+            fold_inplace(S0[l][q][c], S1[l][q][c], S2[l][q][c], sp, pr);
+            const int layer = g * LPT + l;
+            if (layer < nl) H[(size_t)q * hq + ((size_t)(l0 + layer) * 2 + c) * kN + idx] = S0[l][q][c];
+          }
     }
   }
   if (!ok) atomicExch(abort_flag, 1);
@@ -1040,12 +1074,10 @@ cudaError_t launch_mac_multi(const DevView& V, const u64* C, int nq, const u64* 
     return cudaErrorInvalidValue;
   const int fold_stages = fold / macq::JS > 0 ? fold / macq::JS : 1;
   dim3 grid((L + macq::LB - 1) / macq::LB, (unsigned)((kN + macq::TN - 1) / macq::TN));
-  switch (nq) {
-    case 1: k_mac_multi<1><<<grid, macq::THREADS, macq::SMEM, st>>>(V, tmP, tmC, H, hq, ell, L, fold_stages, err); break;
-    case 2: k_mac_multi<2><<<grid, macq::THREADS, macq::SMEM, st>>>(V, tmP, tmC, H, hq, ell, L, fold_stages, err); break;
-    case 3: k_mac_multi<3><<<grid, macq::THREADS, macq::SMEM, st>>>(V, tmP, tmC, H, hq, ell, L, fold_stages, err); break;
-    default: k_mac_multi<4><<<grid, macq::THREADS, macq::SMEM, st>>>(V, tmP, tmC, H, hq, ell, L, fold_stages, err); break;
-  }
+  if (nq == 1)
+    k_mac_multi<1><<<grid, macq::THREADS, macq::SMEM, st>>>(V, tmP, tmC, H, hq, ell, L, fold_stages, err);
+  else
+    k_mac_multi<2><<<grid, macq::THREADS, macq::SMEM, st>>>(V, tmP, tmC, H, hq, ell, L, fold_stages, err);
   return cudaSuccess;
 }
 
@@ -1167,8 +1199,6 @@ cudaError_t kernels_init(int N) {
   set((const void*)k_mac);
   set((const void*)k_mac_multi<1>);
   set((const void*)k_mac_multi<2>);
-  set((const void*)k_mac_multi<3>);
-  set((const void*)k_mac_multi<4>);
   set((const void*)k_relin_ntt);
   set((const void*)k_encrypt);
   set((const void*)k_keygen_sntt);
@@ -1177,4 +1207,67 @@ cudaError_t kernels_init(int N) {
   set((const void*)k_dec_slots);
   set((const void*)k_mask);
   return e;
+}
+
+// ------------------------------------------------------ integer-pipe peak
+// Throughput probe of the two multiply forms the kernels above are built
+// from: 32x32->64 wide multiply-add (mad.wide.u32) and 32-bit
+// multiply-add (mad.lo.u32).  Each thread runs 16 independent chains of
+// `iters` steps; the result is folded into *sink so nothing is dead code.
+namespace {
+template <int WIDE>
+__global__ void k_int_peak(int iters, u32 seed, u64* sink) {
+  u64 a[16];
+  u32 b[16];
+#pragma unroll
+  for (int i = 0; i < 16; ++i) {
+    a[i] = seed + threadIdx.x + i;
+    b[i] = seed * (i + 3) + blockIdx.x;
+  }
+  const u32 m = seed | 1u;
+  for (int it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+      if (WIDE) {
+        asm volatile("mad.wide.u32 %0, %1, %2, %0;" : "+l"(a[i]) : "r"(b[i]), "r"(m));
+      } else {
+        asm volatile("mad.lo.u32 %0, %0, %1, %2;" : "+r"(b[i]) : "r"(m), "r"((u32)it));
+      }
+    }
+  }
+  u64 acc = 0;
+#pragma unroll
+  for (int i = 0; i < 16; ++i) acc += a[i] + b[i];
+  if (acc == 0x123456789ull) *sink = acc;
+}
+}  // namespace
+
+double measure_int_peak(int wide) {
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  u64* sink = nullptr;
+  if (cudaMalloc(&sink, sizeof(u64)) != cudaSuccess) return 0;
+  const int threads = 512, blocks = sms * 4, iters = 4096;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  double best = 0;
+  for (int rep = 0; rep < 3; ++rep) {
+    cudaEventRecord(e0);
+    if (wide)
+      k_int_peak<1><<<blocks, threads>>>(iters, 7u + rep, sink);
+    else
+      k_int_peak<0><<<blocks, threads>>>(iters, 7u + rep, sink);
+    cudaEventRecord(e1);
+    cudaEventSynchronize(e1);
+    float ms = 0;
+    cudaEventElapsedTime(&ms, e0, e1);
+    const double ops = (double)blocks * threads * iters * 16;
+    if (ms > 0) best = std::max(best, ops / (ms * 1e-3));
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(sink);
+  return best;
 }

@@ -22,11 +22,11 @@ void launch_ptgen(const DevView& V, const uint16_t* pos, int L, int ell, int h, 
 cudaError_t launch_mac(const DevView& V, const u64* C, const u64* P, u64* H, int ell, int L, int fold, int* err,
                        cudaStream_t st);
 
-// The same for nq <= 4 requests sharing the plaintexts: C holds the requests back to back
+// The same for nq <= 2 requests sharing the plaintexts: C holds the requests back to back
 // ([nq][ell][2][k][N], split format), H[q] starts at H + q * hq.
 cudaError_t launch_mac_multi(const DevView& V, const u64* C, int nq, const u64* P, u64* H, size_t hq, int ell, int L,
                              int fold, int* err, cudaStream_t st);
-constexpr int PEPSI_MAC_MAX_REQUESTS = 4;
+constexpr int PEPSI_MAC_MAX_REQUESTS = 2;
 
 // In-place conversion of groups of k rows to (to = true) or from the split operand format.
 void launch_split(const DevView& V, u64* x, size_t groups, bool to, cudaStream_t st);
@@ -71,3 +71,7 @@ void launch_mask(const DevView& V, u64 seed, u64* ct, cudaStream_t st);
 
 // Configure kernels that need more than 48 KB of dynamic shared memory.
 cudaError_t kernels_init(int N);
+
+// Measured throughput (operations per second over the whole GPU) of
+// 32x32->64 wide multiply-adds (wide = 1) or 32-bit multiply-adds (wide = 0).
+double measure_int_peak(int wide);

@@ -49,6 +49,8 @@ struct pepsi_ctx {
   DevView V{};
   RnsArgs rargs{};  // host copy of the by-value RNS kernel parameters
   cudaStream_t stream = nullptr;
+  cudaStream_t aux_stream = nullptr;  // overlapped multiply-accumulates of pepsi_eval_batch
+  cudaEvent_t aux_ev[4] = {};
   // device tables and keys
   DevPrime* d_pr = nullptr;
   u64 *d_tw = nullptr, *d_tws = nullptr, *d_itw = nullptr, *d_itws = nullptr;
@@ -416,7 +418,11 @@ int eval_core(pepsi_ctx* c, int set_id, const u64* cts, u32 layer0, u32 nl, int 
 // PEPSI_MAC_MAX_REQUESTS per group; each group's multiply-accumulate reads
 // the plaintexts once (resident table) or generates each chunk once
 // (streamed table); the equality circuits then run request by request.
-enum { S_CB = 41, S_HB = 42, S_ACCB = 43 };
+// With a resident table the multiply-accumulate of the next group runs on
+// the context's second stream while the circuits of the current group run
+// on the call's stream (double-buffered requests and h'), so the
+// HBM-bound stream of plaintexts overlaps the compute-bound circuits.
+enum { S_CB = 41, S_HB = 42, S_ACCB = 43, S_CB2 = 44, S_HB2 = 45 };
 int eval_batch_core(pepsi_ctx* c, int nq, const int* set_ids, const u64* const* cts, const int* modes,
                     const u64* mask_seeds, u64* const* outs, cudaStream_t st) {
   const size_t k = c->k, N = c->N, kN = k * N, ct2 = 2 * kN, ct3 = 3 * kN;
@@ -427,31 +433,58 @@ int eval_batch_core(pepsi_ctx* c, int nq, const int* set_ids, const u64* const* 
     const int mode = modes ? modes[i] : PEPSI_MODE_INDICATOR;
     if (mode != PEPSI_MODE_INDICATOR && mode != PEPSI_MODE_CARDINALITY) return PEPSI_E_PARAM;
   }
-  std::vector<char> done(nq, 0);
+  // groups of requests on the same set, in order of first appearance
+  std::vector<std::vector<int>> groups;
+  {
+    std::vector<char> done(nq, 0);
+    for (int i0 = 0; i0 < nq; ++i0) {
+      if (done[i0]) continue;
+      std::vector<int> grp;
+      for (int i = i0; i < nq && (int)grp.size() < PEPSI_MAC_MAX_REQUESTS; ++i)
+        if (!done[i] && set_ids[i] == set_ids[i0]) grp.push_back(i);
+      for (int i : grp) done[i] = 1;
+      groups.push_back(grp);
+    }
+  }
+  cudaError_t e = cudaSuccess;
+  if (!c->aux_stream) {
+    CKS(cudaStreamCreateWithFlags(&c->aux_stream, cudaStreamNonBlocking));
+    for (int i = 0; i < 4; ++i) CKS(cudaEventCreateWithFlags(&c->aux_ev[i], cudaEventDisableTiming));
+  }
+  cudaStream_t ax = c->aux_stream;
+  cudaEvent_t mac_done[2] = {c->aux_ev[0], c->aux_ev[1]}, circ_done[2] = {c->aux_ev[2], c->aux_ev[3]};
+  // the auxiliary stream starts after everything already queued on the call's stream
+  CKS(cudaEventRecord(circ_done[0], st));
+  CKS(cudaEventRecord(circ_done[1], st));
   bool any_host = false;
-  for (int i0 = 0; i0 < nq; ++i0) {
-    if (done[i0]) continue;
-    // the next group: up to the limit of not yet evaluated requests on this set
-    std::vector<int> grp;
-    for (int i = i0; i < nq && (int)grp.size() < PEPSI_MAC_MAX_REQUESTS; ++i)
-      if (!done[i] && set_ids[i] == set_ids[i0]) grp.push_back(i);
-    for (int i : grp) done[i] = 1;
+  int slot = 0;
+  for (size_t gi = 0; gi < groups.size(); ++gi) {
+    const std::vector<int>& grp = groups[gi];
     const int G = (int)grp.size();
-    ServerSet& S = c->sets[set_ids[i0]];
+    ServerSet& S = c->sets[set_ids[grp[0]]];
     const u32 mu = S.mu;
     const int Lc = std::max(1, std::min<int>(c->chunk, (int)mu));
     EvalBufs b;
-    cudaError_t e = eval_bufs(c, Lc, S.dP == nullptr, &b);
+    e = eval_bufs(c, Lc, S.dP == nullptr, &b);
     if (e != cudaSuccess) return cuda_status(e);
-    u64* CB = (u64*)scratch(c, S_CB, (size_t)G * cwords * 8, &e);
     const size_t hq = (size_t)(S.dP ? mu : Lc) * ct2;
-    u64* HB = (u64*)scratch(c, S_HB, (size_t)G * hq * 8, &e);
-    u64* ACC = (u64*)scratch(c, S_ACCB, (size_t)G * ct3 * 8, &e);
+    u64* CB = (u64*)scratch(c, slot ? S_CB2 : S_CB, (size_t)PEPSI_MAC_MAX_REQUESTS * cwords * 8, &e);
+    u64* HB = (u64*)scratch(c, slot ? S_HB2 : S_HB, (size_t)PEPSI_MAC_MAX_REQUESTS * hq * 8, &e);
+    u64* ACC = (u64*)scratch(c, S_ACCB, (size_t)PEPSI_MAC_MAX_REQUESTS * ct3 * 8, &e);
     if (!CB || !HB || !ACC) return cuda_status(e);
-    for (int g = 0; g < G; ++g) CKS(prepare_request(c, cts[grp[g]], CB + (size_t)g * cwords, st));
     if (S.dP) {
-      Prof p(c, PC_MAC, st);
-      CKS(launch_mac_multi(c->V, CB, G, S.dP, HB, hq, c->ell, (int)mu, c->mac_fold, c->d_err, st));
+      // requests and multiply-accumulate of this group on the auxiliary stream, once the
+      // circuits that last used this slot's buffers are done
+      CKS(cudaStreamWaitEvent(ax, circ_done[slot], 0));
+      for (int g = 0; g < G; ++g) CKS(prepare_request(c, cts[grp[g]], CB + (size_t)g * cwords, ax));
+      {
+        Prof p(c, PC_MAC, ax);
+        CKS(launch_mac_multi(c->V, CB, G, S.dP, HB, hq, c->ell, (int)mu, c->mac_fold, c->d_err, ax));
+      }
+      CKS(cudaEventRecord(mac_done[slot], ax));
+      CKS(cudaStreamWaitEvent(st, mac_done[slot], 0));
+    } else {
+      for (int g = 0; g < G; ++g) CKS(prepare_request(c, cts[grp[g]], CB + (size_t)g * cwords, st));
     }
     for (u32 l0 = 0; l0 < mu; l0 += Lc) {
       const int L = (int)std::min<u32>(Lc, mu - l0);
@@ -476,8 +509,13 @@ int eval_batch_core(pepsi_ctx* c, int nq, const int* set_ids, const u64* const* 
                          mask_seeds ? mask_seeds[i] : 0, outs[i], st));
       any_host |= !is_device_ptr(outs[i]);
     }
+    CKS(cudaEventRecord(circ_done[slot], st));
+    slot ^= 1;
   }
-  cudaError_t e = cudaGetLastError();
+  // nothing may remain queued on the auxiliary stream after the call's stream completes
+  CKS(cudaEventRecord(mac_done[0], ax));
+  CKS(cudaStreamWaitEvent(st, mac_done[0], 0));
+  e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_status(e);
   if (any_host) {
     e = cudaStreamSynchronize(st);
@@ -593,6 +631,9 @@ void pepsi_destroy(pepsi_ctx* c) {
   cudaFree(c->d_consts);
   cudaFree(c->d_err);
   if (c->stream) cudaStreamDestroy(c->stream);
+  if (c->aux_stream) cudaStreamDestroy(c->aux_stream);
+  for (auto ev : c->aux_ev)
+    if (ev) cudaEventDestroy(ev);
   delete c;
 }
 
@@ -1047,6 +1088,14 @@ int pepsi_export_keys(pepsi_ctx* c, int8_t* s, uint64_t* rlk) {
     CKS(cudaMemcpyAsync(rlk, tmp, words * 8, cudaMemcpyDeviceToHost, st));
   }
   return cuda_status(cudaStreamSynchronize(st));
+}
+
+int pepsi_int_peak(int wide, double* ops_per_s) {
+  if (!ops_per_s) return PEPSI_E_PARAM;
+  *ops_per_s = measure_int_peak(wide);
+  if (*ops_per_s > 0) return PEPSI_OK;
+  const cudaError_t e = cudaGetLastError();
+  return cuda_status(e != cudaSuccess ? e : cudaErrorUnknown);
 }
 
 int pepsi_profile_enable(pepsi_ctx* c, int on) {

@@ -621,35 +621,67 @@ int or_cuckoo(u64 hash_key, u32 lambda_bar, u32 logb, const u64* items, u32 m, u
 }
 /* Server simple hashing (App. Alg 7, server side): every item goes into
  * each distinct bin among its three; an x_L already present in a bin is
- * not stored twice; layer = order of arrival in the bin; dummies pad to mu.
- * T[layer*b + bin].  More than mu entries in a bin is a failure. */
+ * not stored twice (the first arrival stays); layer = order of arrival in
+ * the bin; dummies pad to mu.  T[layer*b + bin].  More than mu entries in a
+ * bin is a failure.  Arrivals are bucketed by bin in arrival order, and
+ * each bin's duplicates are found by sorting its (x_L, arrival) pairs. */
+typedef struct { u64 xl; u64 pos; } or_arrival;
+static int cmp_arrival(const void* a, const void* b) {
+  const or_arrival *x = (const or_arrival*)a, *y = (const or_arrival*)b;
+  if (x->xl != y->xl) return x->xl < y->xl ? -1 : 1;
+  return x->pos < y->pos ? -1 : (x->pos > y->pos);
+}
 int or_simple_hash(u64 hash_key, u32 lambda_bar, u32 logb, const u64* items, u64 n, u32 mu, u64* T, u32* max_load) {
   u32 b = 1u << logb;
-  u32* cnt = (u32*)calloc(b, sizeof(u32));
-  for (u64 i = 0; i < (u64)mu * b; i++) T[i] = OR_DUMMY;
-  int rc = OR_OK;
-  u32 mx = 0;
+  u64 cap = 3 * n + 1;
+  u32* abin = (u32*)malloc(sizeof(u32) * cap);
+  u64* axl = (u64*)malloc(sizeof(u64) * cap);
+  u64 na = 0;
   for (u64 u = 0; u < n; u++) {
     u64 xL;
     u32 bins[3];
     or_hash_item(hash_key, lambda_bar, logb, items[u], &xL, bins);
     for (u32 i = 0; i < 3; i++) {
-      u32 bin = bins[i];
       int dup_bin = 0;
-      for (u32 j = 0; j < i; j++) dup_bin |= (bins[j] == bin);
+      for (u32 j = 0; j < i; j++) dup_bin |= (bins[j] == bins[i]);
       if (dup_bin) continue;
-      int dup_val = 0;
-      for (u32 l = 0; l < cnt[bin] && l < mu; l++) dup_val |= (T[(u64)l * b + bin] == xL);
-      if (dup_val) continue;
-      if (cnt[bin] < mu) T[(u64)cnt[bin] * b + bin] = xL;
-      cnt[bin]++;
-      if (cnt[bin] > mx) mx = cnt[bin];
+      abin[na] = bins[i];
+      axl[na] = xL;
+      na++;
     }
   }
-  if (mx > mu) rc = OR_E_BIN_OVERFLOW;
+  /* stable bucketing by bin */
+  u64* start = (u64*)calloc((u64)b + 1, sizeof(u64));
+  for (u64 e = 0; e < na; e++) start[abin[e] + 1]++;
+  for (u32 i = 0; i < b; i++) start[i + 1] += start[i];
+  u64* fill = (u64*)malloc(sizeof(u64) * ((u64)b + 1));
+  memcpy(fill, start, sizeof(u64) * ((u64)b + 1));
+  u64* order = (u64*)malloc(sizeof(u64) * (na ? na : 1));
+  for (u64 e = 0; e < na; e++) order[fill[abin[e]]++] = e;
+  for (u64 i = 0; i < (u64)mu * b; i++) T[i] = OR_DUMMY;
+  u32 mx = 0;
+  or_arrival* tmp = (or_arrival*)malloc(sizeof(or_arrival) * (na ? na : 1));
+  char* dup = (char*)calloc(na ? na : 1, 1);
+  for (u32 bin = 0; bin < b; bin++) {
+    u64 s0 = start[bin], len = start[bin + 1] - s0;
+    for (u64 r = 0; r < len; r++) {
+      tmp[r].xl = axl[order[s0 + r]];
+      tmp[r].pos = r;
+    }
+    qsort(tmp, len, sizeof(or_arrival), cmp_arrival);
+    for (u64 r = 1; r < len; r++)
+      if (tmp[r].xl == tmp[r - 1].xl) dup[s0 + tmp[r].pos] = 1;
+    u32 layer = 0;
+    for (u64 r = 0; r < len; r++) {
+      if (dup[s0 + r]) continue;
+      if (layer < mu) T[(u64)layer * b + bin] = axl[order[s0 + r]];
+      layer++;
+    }
+    if (layer > mx) mx = layer;
+  }
   if (max_load) *max_load = mx;
-  free(cnt);
-  return rc;
+  free(abin); free(axl); free(start); free(fill); free(order); free(tmp); free(dup);
+  return mx > mu ? OR_E_BIN_OVERFLOW : OR_OK;
 }
 
 /* ------------------------------------------------------------------ */

@@ -6,9 +6,9 @@ both.  This module holds no part of the method's arithmetic; it only draws
 items, so the CUDA path and the CPU oracle can be fed identical inputs.
 
 Recipe: numpy Generator(PCG64(seed)); server items uniform in [0, 2^bits),
-deduplicated; the planted items are a sample without replacement of the
-server set written at random client positions; the other client items are
-fresh uniform values not in the server set.
+distinct (repeated draws are redrawn); the planted items are a sample
+without replacement of the server set written at random client positions;
+the other client items are fresh uniform values not in the server set.
 """
 from __future__ import annotations
 
@@ -24,22 +24,29 @@ class ItemSets:
     planted: np.ndarray  # uint64 [p], the items known to be in both
 
 
+def _draw(rng, count, bits):
+    if bits >= 64:
+        return rng.integers(0, np.iinfo(np.uint64).max, size=count, dtype=np.uint64, endpoint=True)
+    return rng.integers(0, 1 << bits, size=count, dtype=np.uint64)
+
+
 def _unique_uniform(rng, count, bits, exclude=None):
-    hi = 1 << bits
-    out = np.empty(0, dtype=np.uint64)
-    excl = set() if exclude is None else exclude
-    while out.size < count:
-        need = (count - out.size) * 2 + 16
-        if bits >= 64:
-            cand = rng.integers(0, np.iinfo(np.uint64).max, size=need, dtype=np.uint64, endpoint=True)
-        else:
-            cand = rng.integers(0, hi, size=need, dtype=np.uint64)
-        cand = np.unique(np.concatenate([out, cand]))
-        if excl:
-            cand = cand[~np.isin(cand, np.fromiter(excl, dtype=np.uint64, count=len(excl)))]
-        out = cand
-    idx = rng.permutation(out.size)[:count]
-    return out[np.sort(idx)]
+    """count distinct uniform values in [0, 2^bits), none of them in exclude
+    (a sorted uint64 array or None); collisions are redrawn."""
+    out = _draw(rng, count, bits)
+    while True:
+        order = np.argsort(out, kind="stable")
+        srt = out[order]
+        bad = np.zeros(out.size, dtype=bool)
+        if out.size > 1:
+            bad[order[1:][srt[1:] == srt[:-1]]] = True  # later copies of a value are redrawn
+        if exclude is not None and exclude.size and out.size:
+            at = np.minimum(np.searchsorted(exclude, out), exclude.size - 1)
+            bad |= exclude[at] == out
+        nbad = int(bad.sum())
+        if nbad == 0:
+            return out
+        out[bad] = _draw(rng, nbad, bits)
 
 
 def make_sets(m: int, n: int, planted: int, bits: int = 64, seed_items: int = 1, seed_plant: int = 2) -> ItemSets:
@@ -50,14 +57,7 @@ def make_sets(m: int, n: int, planted: int, bits: int = 64, seed_items: int = 1,
     server = _unique_uniform(rng, n, bits)
     rngp = np.random.Generator(np.random.PCG64(seed_plant))
     shared = server[np.sort(rngp.choice(n, size=planted, replace=False))] if planted else np.empty(0, np.uint64)
-    fresh = _unique_uniform(rng, m - planted, bits, exclude=set(server.tolist()) if n <= (1 << 22) else None)
-    if n > (1 << 22) and fresh.size:
-        # collision with a large server set is possible but of probability
-        # about m*n/2^bits; drop such items and redraw
-        clash = np.isin(fresh, server)
-        while clash.any():
-            fresh[clash] = _unique_uniform(rng, int(clash.sum()), bits)
-            clash = np.isin(fresh, server)
+    fresh = _unique_uniform(rng, m - planted, bits, exclude=np.sort(server))
     client = np.concatenate([fresh, shared]).astype(np.uint64)
     pos = rngp.permutation(m)
     out = np.empty(m, dtype=np.uint64)

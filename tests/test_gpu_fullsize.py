@@ -61,3 +61,35 @@ def test_paper_result_decrypts_to_intersection(paper_case):
     card = gc.eval(sid, cts, mode=1, mask_seed=5)
     cs, _ = gc.decrypt(card)
     assert int(cs.astype(np.int64).sum()) % 65537 == 102
+
+
+LARGE = [55] * 6 + [54] * 2
+
+
+def test_large_config_streamed_plaintexts():
+    """Large configuration: N = 16384, eight primes (438 bits), h = 8,
+    ell = 128, mu = 3487, 4096 client items against 2^24 server items (1%
+    planted).  The NTT-form plaintexts (468 GB) cannot be resident, so the
+    evaluation regenerates them per layer chunk.  The oracle checks the
+    server table, the request words and one sampled layer's h' and E words;
+    the result decrypts to the brute-force intersection."""
+    torch_cuda()
+    from paper_2310_14565_gb300.workload import make_sets
+
+    oc, gc, s, rlk = pair(16384, LARGE, 8, 40, mu=3487, ell=128)
+    sets = make_sets(4096, 1 << 24, 41, bits=64)
+    sid = gc.server_load(sets.server)
+    rc, Ts, _ = oc.server_table(sets.server)
+    assert rc == 0
+    assert np.array_equal(gc.server_table(sid, 3487), Ts)
+    cts, where = gc.query(sets.client, 4)
+    rc, ocs, owhere = oc.query(s, sets.client, 4)
+    assert rc == 0 and np.array_equal(where, owhere) and np.array_equal(cts, ocs)
+    _, dh, de = oc.eval(rlk, cts, Ts, layer0=0, nlayers=1, debug=True)
+    gh, ge = gc.eval_layers(sid, cts, 0, 1)
+    assert np.array_equal(gh, dh) and np.array_equal(ge, de)
+    out = gc.eval(sid, cts)
+    slots, budget = gc.decrypt(out)
+    assert budget > 0
+    assert np.array_equal(slots, brute_indicator(sets.client, sets.server, where, 16384))
+    assert int(slots.sum()) == 41

@@ -433,14 +433,15 @@ def test_psi_matches_brute_force(oracle_mod, h, bits, lb):
 
     N = 64
     sets = make_sets(24, 150, 7, bits=32, seed_items=h, seed_plant=h + 1)
-    c = oracle_mod.Ctx(N=N, t=T, prime_bits=bits, h=h, lambda_bar=lb, hash_key=99, mu=16)
+    load = oracle_mod.simple_hash(99, lb, 6, sets.server, 1000)[2]
+    c = oracle_mod.Ctx(N=N, t=T, prime_bits=bits, h=h, lambda_bar=lb, hash_key=99, mu=max(16, load))
     s, rlk = c.keygen(3)
     rc, Ts, _ = c.server_table(sets.server)
     assert rc == 0
     rc, cts, where = c.query(s, sets.client, 4)
     assert rc == 0
     out = c.eval(rlk, cts, Ts)
-    assert c.last_counts == (c.ell * c.mu, c.mu * int(math.log2(h)))
+    assert c.last_counts == (c.ell * c.mu, c.mu * int(math.log2(h)))  # Thm 1 with log2 h products
     slots, bud = c.decrypt(s, out)
     assert bud > 0
     server = set(int(x) for x in sets.server)

@@ -33,6 +33,9 @@ METRIC = "server eval ms at 1024 x 2^20 items; ct-mult+relin/s; NTT % of HBM roo
 WL = dict(N=8192, prime_bits=[55, 55, 54, 54], h=4, ell=600, lambda_bar=32, mu=526, m=1024, n=1 << 20, planted=102)
 # small case of the same kernels for profiler captures (5.5 GB of resident plaintexts, > L2)
 WL_SMALL = dict(WL, mu=35, n=1 << 14)
+# large configuration: the 468 GB plaintext table is regenerated per layer chunk
+WL_LARGE = dict(N=16384, prime_bits=[55] * 6 + [54] * 2, h=8, ell=128, lambda_bar=40, mu=3487, m=4096, n=1 << 24,
+                planted=41)
 HASH_KEY, KEY_SEED, ENC_SEED = 0x5EED, 3, 4
 WORKLOAD_NAME = ("paper-shaped PSI: N=8192 bins, t=65537, q=4 RNS primes (55,55,54,54 bits), CW code ell=600 h=4, "
                  "mu=526 layers, 1024 client x 2^20 server uniform 64-bit items, 102 planted")
@@ -235,7 +238,7 @@ def run_ours(args):
     mac_launch_ms = mac_ms / mac_launches
     achieved = mac_bytes_eval / mac_launches_per_eval / (mac_launch_ms * 1e-3) / 1e9
     peak, peak_kind = measured_peaks()
-    traffic = stored_traffic()
+    traffic = stored_traffic() if args.case == "paper" else None
 
     # end to end through the C ABI with host buffers (pinned), copies inside the timed region
     for _ in range(2):
@@ -246,6 +249,20 @@ def run_ours(args):
         ctx.eval(sid, cts_pinned, out=out_pinned)
         e2e.append((time.perf_counter() - t) * 1e3)
     e2e_ms = statistics.median(e2e)
+
+    if args.case == "large":
+        line = {"metric": METRIC, "value": round(ms, 3), "unit": "ms", "n_gpus": args.gpus, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": round(ms, 3), "higher_is_better": False, "scaling": "weak",
+                "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+                "config": {"workload": WORKLOAD_NAME, "l2": "inputs larger than L2 (plaintext chunks of 4.3 GB)"},
+                "correct": correct, "noise_budget_bits": round(budget, 2),
+                "offline_server_load_ms": round(offline_ms, 1),
+                "kernel_ms_per_step": {name: round(v[1] / psteps, 3) for name, v in prof.items() if v[0]},
+                "gpu_launches": int(launches), "clocks": clk}
+        if rank == 0:
+            print(json.dumps(line), flush=True)
+        ctx.close()
+        return 0
 
     # batched form: 4 requests on the same server set in one pepsi_eval_batch call,
     # against 4 sequential pepsi_eval calls (same outputs)
@@ -391,13 +408,20 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--case", choices=["paper", "small"], default="paper",
-                    help="small: the same kernels on 2^14 server items (mu=35), for profiler captures")
+    ap.add_argument("--case", choices=["paper", "small", "large"], default="paper",
+                    help="small: the same kernels on 2^14 server items (mu=35), for profiler captures; "
+                         "large: N=16384, 8 primes, h=8, 4096 x 2^24 items, streamed plaintexts")
     args = ap.parse_args()
+    global WORKLOAD_NAME
     if args.case == "small":
-        global WORKLOAD_NAME
         WL.update(WL_SMALL)
         WORKLOAD_NAME = WORKLOAD_NAME.replace("mu=526", "mu=35").replace("2^20", "2^14") + " (profiling case)"
+        args.no_cpu_baseline = True
+    elif args.case == "large":
+        WL.update(WL_LARGE)
+        WORKLOAD_NAME = ("large PSI: N=16384 bins, t=65537, q=8 RNS primes (55x6, 54x2 bits), CW code ell=128 h=8, "
+                         "mu=3487 layers, 4096 client x 2^24 server uniform 64-bit items, 41 planted, plaintexts "
+                         "regenerated per layer chunk")
         args.no_cpu_baseline = True
     if args.warmup < 3:
         args.warmup = 3

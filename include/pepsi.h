@@ -69,8 +69,10 @@ typedef struct {
   uint32_t num_hashes;     /* cuckoo / simple hash functions: must be 3 */
   uint32_t mu;             /* server maximum bin load; 0 -> bound rule */
   uint64_t hash_key;       /* public seed of H_0..H_3 */
-  uint64_t resident_bytes; /* 0: keep server plaintexts resident when they fit in
-                              60% of free HBM; UINT64_MAX: never; else a byte cap */
+  uint64_t resident_bytes; /* HBM budget for resident server plaintexts: the longest
+                              prefix of layers that fits stays resident, the rest is
+                              regenerated per chunk at evaluation.  0: 60% of free
+                              HBM at load time; UINT64_MAX: none; else a byte cap */
 } pepsi_params;
 
 /* Derived values of a context (for callers and tests). */
@@ -99,8 +101,9 @@ int pepsi_get_info(const pepsi_ctx* ctx, pepsi_info* info);
  * H_0 to lambda bits, permutation-based hashing into each of the three
  * bins of every item, de-duplication of equal x_L inside a bin, stable
  * layer order, dummies up to mu; then the NTT-form server plaintexts
- * pt_s[layer][j] are generated on the device (resident when the budget
- * allows, otherwise regenerated per layer chunk at evaluation time).
+ * pt_s[layer][j] are generated on the device: the layers that fit the
+ * resident_bytes budget stay resident, the others are regenerated per
+ * layer chunk at evaluation time.
  * items: host array of n 64-bit items.  *set_id receives the handle.
  * Errors: PEPSI_E_BIN_OVERFLOW, PEPSI_E_NOMEM, PEPSI_E_PARAM, PEPSI_E_CUDA. */
 int pepsi_server_load(pepsi_ctx* ctx, const uint64_t* items, size_t n, int* set_id);

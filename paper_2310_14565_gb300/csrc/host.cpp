@@ -9,7 +9,7 @@
 #include <algorithm>
 #include <cmath>
 #include <map>
-#include <unordered_set>
+#include <thread>
 
 namespace hostmath {
 
@@ -314,28 +314,76 @@ int cuckoo(const Hasher& H, const u64* items, size_t m, std::vector<u64>& table,
   return 0;
 }
 
+// run f(lo, hi) over [0, count) split across the host's cores
+template <class F>
+static void parallel_ranges(size_t count, F f) {
+  const size_t nt = std::max<size_t>(1, std::min<size_t>(std::thread::hardware_concurrency(), 64));
+  if (nt == 1 || count < 4096) {
+    f((size_t)0, count);
+    return;
+  }
+  std::vector<std::thread> th;
+  for (size_t t = 0; t < nt; ++t) {
+    const size_t lo = count * t / nt, hi = count * (t + 1) / nt;
+    th.emplace_back([=] { f(lo, hi); });
+  }
+  for (auto& x : th) x.join();
+}
+
 int simple_hash(const Hasher& H, const u64* items, size_t n, u32 mu, std::vector<u64>& T, u32* max_load) {
   const u32 b = 1u << H.logb;
-  std::vector<std::vector<u64>> bin(b);
-  std::vector<std::unordered_set<u64>> seen(b);
+  std::vector<u64> ixl(n);
+  std::vector<u32> ibin(3 * n);
+  parallel_ranges(n, [&](size_t lo, size_t hi) {
+    for (size_t u = lo; u < hi; ++u) H(items[u], &ixl[u], &ibin[3 * u]);
+  });
+  // arrivals (bin, x_L) in order: item by item, each distinct bin of the item once
+  std::vector<u32> abin;
+  std::vector<u64> axl;
+  abin.reserve(3 * n);
+  axl.reserve(3 * n);
   for (size_t u = 0; u < n; ++u) {
-    u64 xl;
-    u32 bs[3];
-    H(items[u], &xl, bs);
+    const u64 xl = ixl[u];
+    const u32* bs = &ibin[3 * u];
     for (int i = 0; i < 3; ++i) {
       if ((i > 0 && bs[i] == bs[0]) || (i > 1 && bs[i] == bs[1])) continue;
-      if (!seen[bs[i]].insert(xl).second) continue;
-      bin[bs[i]].push_back(xl);
+      abin.push_back(bs[i]);
+      axl.push_back(xl);
     }
   }
-  u32 mx = 0;
-  for (u32 i = 0; i < b; ++i) mx = std::max<u32>(mx, (u32)bin[i].size());
-  if (max_load) *max_load = mx;
-  if (mx > mu) return PEPSI_E_BIN_OVERFLOW;
+  // stable counting sort by bin keeps the arrival order inside each bin
+  std::vector<size_t> off(b + 1, 0);
+  for (u32 x : abin) ++off[x + 1];
+  for (u32 i = 0; i < b; ++i) off[i + 1] += off[i];
+  std::vector<size_t> fill(off.begin(), off.end() - 1);
+  std::vector<u64> vals(abin.size());
+  for (size_t e = 0; e < abin.size(); ++e) vals[fill[abin[e]]++] = axl[e];
+  // per bin: first arrival of each x_L kept (sorting (x_L, arrival) pairs)
   T.assign((size_t)mu * b, PEPSI_DUMMY);
-  for (u32 i = 0; i < b; ++i)
-    for (size_t l = 0; l < bin[i].size(); ++l) T[l * b + i] = bin[i][l];
-  return 0;
+  std::vector<u32> load(b, 0);
+  parallel_ranges(b, [&](size_t blo, size_t bhi) {
+    std::vector<std::pair<u64, u32>> tmp;
+    std::vector<char> dup;
+    for (size_t bin = blo; bin < bhi; ++bin) {
+      const size_t s0 = off[bin], len = off[bin + 1] - s0;
+      tmp.resize(len);
+      dup.assign(len, 0);
+      for (size_t r = 0; r < len; ++r) tmp[r] = {vals[s0 + r], (u32)r};
+      std::sort(tmp.begin(), tmp.end());
+      for (size_t r = 1; r < len; ++r)
+        if (tmp[r].first == tmp[r - 1].first) dup[tmp[r].second] = 1;
+      u32 layer = 0;
+      for (size_t r = 0; r < len; ++r) {
+        if (dup[r]) continue;
+        if (layer < mu) T[(size_t)layer * b + bin] = vals[s0 + r];
+        ++layer;
+      }
+      load[bin] = layer;
+    }
+  });
+  const u32 mx = *std::max_element(load.begin(), load.end());
+  if (max_load) *max_load = mx;
+  return mx > mu ? PEPSI_E_BIN_OVERFLOW : 0;
 }
 
 }  // namespace hostmath

@@ -34,7 +34,8 @@ struct ServerSet {
   std::vector<u64> hT;          // [mu][N] host copy of T_s
   u64* dT = nullptr;            // [mu][N]
   uint16_t* dpos = nullptr;     // [mu][N][h]
-  u64* dP = nullptr;            // [mu][ell][k][N] resident plaintexts or null
+  u64* dP = nullptr;            // [mu_res][ell][k][N] resident plaintexts (a prefix of the layers) or null
+  u32 mu_res = 0;               // layers [0, mu_res) resident, the rest regenerated per chunk
 };
 
 }  // namespace
@@ -93,10 +94,13 @@ enum ConstSlot { CS_M3, CS_M7, CS_P12, CS_P16, CS_ZINV, CS_D_TM1, CS_D_2, CS_D_6
   } while (0)
 
 thread_local std::string g_last_error = "no error";
+thread_local std::string g_detail;  // names the failing step for the next error report
 
 int cuda_status(cudaError_t e) {
   if (e == cudaSuccess) return PEPSI_OK;
   g_last_error = std::string(cudaGetErrorName(e)) + ": " + cudaGetErrorString(e);
+  if (!g_detail.empty()) g_last_error += " (" + g_detail + ")";
+  g_detail.clear();
   if (e == cudaErrorMemoryAllocation) return PEPSI_E_NOMEM;
   return PEPSI_E_CUDA;
 }
@@ -319,6 +323,13 @@ bool take_error_flag(pepsi_ctx* c) {
   return v != 0;
 }
 
+// Name the failing step when a multiply-accumulate could not be launched.
+cudaError_t mac_status(cudaError_t e) {
+  if (e == cudaErrorInvalidValue)
+    g_detail = "multiply-accumulate: the TMA tensor maps of the plaintext / request tiles could not be encoded";
+  return e;
+}
+
 // Copy `bytes` between caller and device buffers through the stream.
 cudaError_t copy_any(void* dst, const void* src, size_t bytes, cudaStream_t st) {
   return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, st);
@@ -364,32 +375,36 @@ int eval_core(pepsi_ctx* c, int set_id, const u64* cts, u32 layer0, u32 nl, int 
   const size_t k = c->k, N = c->N;
   const size_t kN = k * N, ct2 = 2 * kN, ct3 = 3 * kN;
   const int Lc = std::max(1, std::min<int>(c->chunk, (int)nl));
+  const u32 end = layer0 + nl, res_end = std::min(end, S.mu_res);
   EvalBufs b;
-  cudaError_t e = eval_bufs(c, Lc, S.dP == nullptr, &b);
+  cudaError_t e = eval_bufs(c, Lc, res_end < end, &b);
   if (e != cudaSuccess) return cuda_status(e);
   CKS(prepare_request(c, cts, b.C, st));
-  // a5 with a resident table: one multiply-accumulate launch over all layers,
-  // so the request is read from HBM once
+  // a5 on the resident layers: one multiply-accumulate launch over all of
+  // them, so the request is read from HBM once
   u64* Hall = nullptr;
-  if (S.dP) {
-    Hall = (u64*)scratch(c, S_HALL, (size_t)nl * ct2 * 8, &e);
+  if (res_end > layer0) {
+    Hall = (u64*)scratch(c, S_HALL, (size_t)(res_end - layer0) * ct2 * 8, &e);
     if (!Hall) return cuda_status(e);
     Prof p(c, PC_MAC, st);
-    CKS(launch_mac(c->V, b.C, S.dP + (size_t)layer0 * c->ell * kN, Hall, c->ell, (int)nl, c->mac_fold, c->d_err,
-                  st));
+    CKS(mac_status(launch_mac(c->V, b.C, S.dP + (size_t)layer0 * c->ell * kN, Hall, c->ell, (int)(res_end - layer0),
+                              c->mac_fold, c->d_err, st)));
   }
   bool first = true;
-  for (u32 l0 = layer0; l0 < layer0 + nl; l0 += Lc) {
-    const int L = (int)std::min<u32>(Lc, layer0 + nl - l0);
-    if (Hall) {
+  u64* const Hchunk = b.H;  // h' of a regenerated chunk (Lc layers)
+  for (u32 l0 = layer0; l0 < end;) {
+    int L = (int)std::min<u32>(Lc, end - l0);
+    if (l0 < res_end) {
+      L = (int)std::min<u32>(L, res_end - l0);
       b.H = Hall + (size_t)(l0 - layer0) * ct2;
     } else {
+      b.H = Hchunk;
       {
         Prof p(c, PC_PTGEN, st);
         launch_ptgen(c->V, S.dpos + (size_t)l0 * N * c->h, L, c->ell, c->h, b.Pc, st);
       }
-      Prof p(c, PC_MAC, st);  // a5: fused ct x pt multiply-accumulate on the regenerated chunk
-      CKS(launch_mac(c->V, b.C, b.Pc, b.H, c->ell, L, c->mac_fold, c->d_err, st));
+      Prof p(c, PC_MAC, st);  // a5 on a regenerated chunk
+      CKS(mac_status(launch_mac(c->V, b.C, b.Pc, b.H, c->ell, L, c->mac_fold, c->d_err, st)));
     }
     eq_circuit(c, b, L, st);  // a6
     // b.Hc holds h' in coefficient form after the circuit
@@ -400,6 +415,7 @@ int eval_core(pepsi_ctx* c, int set_id, const u64* cts, u32 layer0, u32 nl, int 
       launch_accum(c->V, b.D, L, b.acc, first, st);
     }
     first = false;
+    l0 += L;
   }
   if (out_ct) CKS(finish_request(c, b, b.acc, mode, mask_seed, out_ct, st));
   e = cudaGetLastError();
@@ -462,46 +478,50 @@ int eval_batch_core(pepsi_ctx* c, int nq, const int* set_ids, const u64* const* 
     const std::vector<int>& grp = groups[gi];
     const int G = (int)grp.size();
     ServerSet& S = c->sets[set_ids[grp[0]]];
-    const u32 mu = S.mu;
+    const u32 mu = S.mu, mres = S.mu_res;
     const int Lc = std::max(1, std::min<int>(c->chunk, (int)mu));
     EvalBufs b;
-    e = eval_bufs(c, Lc, S.dP == nullptr, &b);
+    e = eval_bufs(c, Lc, mres < mu, &b);
     if (e != cudaSuccess) return cuda_status(e);
-    const size_t hq = (size_t)(S.dP ? mu : Lc) * ct2;
+    const size_t hq = (size_t)std::max<u32>(mres, (u32)Lc) * ct2;
     u64* CB = (u64*)scratch(c, slot ? S_CB2 : S_CB, (size_t)PEPSI_MAC_MAX_REQUESTS * cwords * 8, &e);
     u64* HB = (u64*)scratch(c, slot ? S_HB2 : S_HB, (size_t)PEPSI_MAC_MAX_REQUESTS * hq * 8, &e);
     u64* ACC = (u64*)scratch(c, S_ACCB, (size_t)PEPSI_MAC_MAX_REQUESTS * ct3 * 8, &e);
     if (!CB || !HB || !ACC) return cuda_status(e);
-    if (S.dP) {
-      // requests and multiply-accumulate of this group on the auxiliary stream, once the
-      // circuits that last used this slot's buffers are done
+    if (mres) {
+      // requests and multiply-accumulate over the resident layers on the auxiliary
+      // stream, once the circuits that last used this slot's buffers are done
       CKS(cudaStreamWaitEvent(ax, circ_done[slot], 0));
       for (int g = 0; g < G; ++g) CKS(prepare_request(c, cts[grp[g]], CB + (size_t)g * cwords, ax));
       {
         Prof p(c, PC_MAC, ax);
-        CKS(launch_mac_multi(c->V, CB, G, S.dP, HB, hq, c->ell, (int)mu, c->mac_fold, c->d_err, ax));
+        CKS(mac_status(launch_mac_multi(c->V, CB, G, S.dP, HB, hq, c->ell, (int)mres, c->mac_fold, c->d_err, ax)));
       }
       CKS(cudaEventRecord(mac_done[slot], ax));
       CKS(cudaStreamWaitEvent(st, mac_done[slot], 0));
     } else {
       for (int g = 0; g < G; ++g) CKS(prepare_request(c, cts[grp[g]], CB + (size_t)g * cwords, st));
     }
-    for (u32 l0 = 0; l0 < mu; l0 += Lc) {
-      const int L = (int)std::min<u32>(Lc, mu - l0);
-      if (!S.dP) {
+    for (u32 l0 = 0; l0 < mu;) {
+      int L = (int)std::min<u32>(Lc, mu - l0);
+      const bool res = l0 < mres;
+      if (res) {
+        L = (int)std::min<u32>(L, mres - l0);
+      } else {
         {
           Prof p(c, PC_PTGEN, st);
           launch_ptgen(c->V, S.dpos + (size_t)l0 * N * c->h, L, c->ell, c->h, b.Pc, st);
         }
         Prof p(c, PC_MAC, st);
-        CKS(launch_mac_multi(c->V, CB, G, b.Pc, HB, hq, c->ell, L, c->mac_fold, c->d_err, st));
+        CKS(mac_status(launch_mac_multi(c->V, CB, G, b.Pc, HB, hq, c->ell, L, c->mac_fold, c->d_err, st)));
       }
       for (int g = 0; g < G; ++g) {
-        b.H = HB + (size_t)g * hq + (S.dP ? (size_t)l0 * ct2 : 0);
+        b.H = HB + (size_t)g * hq + (res ? (size_t)l0 * ct2 : 0);
         eq_circuit(c, b, L, st);
         Prof p(c, PC_POINTWISE, st);
         launch_accum(c->V, b.D, L, ACC + (size_t)g * ct3, l0 == 0, st);
       }
+      l0 += L;
     }
     for (int g = 0; g < G; ++g) {
       const int i = grp[g];
@@ -841,21 +861,23 @@ int pepsi_server_load(pepsi_ctx* c, const uint64_t* items, size_t n, int* set_id
     Prof p(c, PC_PTGEN, c->stream);
     launch_cw_unrank(S.dT, (size_t)mu * N, c->d_binom, c->ell, c->h, S.dpos, c->stream);
   }
-  // resident NTT-form plaintexts when the budget allows
-  const size_t pbytes = (size_t)mu * c->ell * k * N * 8;
+  // resident NTT-form plaintexts: the longest prefix of layers the budget holds
+  const size_t per_layer = (size_t)c->ell * k * N * 8;
   size_t freeb = 0, totalb = 0;
   cudaMemGetInfo(&freeb, &totalb);
-  u64 cap = c->prm.resident_bytes;
-  bool resident = cap == 0 ? pbytes <= (size_t)(0.6 * (double)freeb) : (cap != UINT64_MAX && pbytes <= cap);
-  if (resident) {
-    e = cudaMalloc((void**)&S.dP, pbytes);
+  const u64 cap = c->prm.resident_bytes;
+  const size_t budget = cap == 0 ? (size_t)(0.6 * (double)freeb) : (cap == UINT64_MAX ? 0 : (size_t)cap);
+  S.mu_res = (u32)std::min<size_t>(mu, budget / per_layer);
+  if (S.mu_res) {
+    e = cudaMalloc((void**)&S.dP, (size_t)S.mu_res * per_layer);
     if (e != cudaSuccess) {
       cudaGetLastError();
       S.dP = nullptr;
+      S.mu_res = 0;
     } else {
       const int G = 64;  // layers per launch
-      for (u32 l0 = 0; l0 < mu; l0 += G) {
-        const int L = (int)std::min<u32>(G, mu - l0);
+      for (u32 l0 = 0; l0 < S.mu_res; l0 += G) {
+        const int L = (int)std::min<u32>(G, S.mu_res - l0);
         Prof p(c, PC_PTGEN, c->stream);
         launch_ptgen(c->V, S.dpos + (size_t)l0 * N * c->h, L, c->ell, c->h, S.dP + (size_t)l0 * c->ell * k * N,
                      c->stream);
@@ -890,7 +912,7 @@ int pepsi_server_plaintexts(pepsi_ctx* c, int set_id, uint32_t layer0, uint32_t 
   cudaError_t e = cudaSuccess;
   u64* tmp = (u64*)scratch(c, S_PC, (size_t)nl * per * 8, &e);
   if (!tmp) return cuda_status(e);
-  if (S.dP) {
+  if ((u64)layer0 + nl <= S.mu_res) {
     CKS(cudaMemcpyAsync(tmp, S.dP + (size_t)layer0 * per, (size_t)nl * per * 8, cudaMemcpyDeviceToDevice, st));
   } else {
     Prof p(c, PC_PTGEN, st);

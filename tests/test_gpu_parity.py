@@ -11,7 +11,7 @@ import os
 import numpy as np
 import pytest
 
-from gpu_helpers import T, brute_indicator, pair, to_dev, to_host, torch_cuda
+from gpu_helpers import T, brute_indicator, hashed_indicator, pair, to_dev, to_host, torch_cuda
 
 pytestmark = pytest.mark.gpu
 
@@ -168,7 +168,10 @@ def test_eval_matches_oracle_both_modes(h, bits, lb, N):
         assert np.array_equal(gslots, oslots)
         assert abs(gb - ob) < 1e-9 and gb > 0
         if mode == 0:
-            assert np.array_equal(gslots, brute_indicator(sets.client, sets.server, where, N))
+            # exact in the hashed domain; contains every true member
+            assert np.array_equal(gslots, hashed_indicator(sets.client, sets.server, where, N, lb))
+            true = brute_indicator(sets.client, sets.server, where, N)
+            assert np.all(gslots >= true)
         else:
             assert int(gslots.astype(np.int64).sum()) % T == len(sets.planted)
 
@@ -295,3 +298,29 @@ def test_eval_batch_matches_single_calls_and_oracle(resident):
         assert np.array_equal(outs[i], oc.eval(rlk, cts[i], T_, mode=modes[i], mask_seed=seeds[i])), i
     slots, b = gc.decrypt(outs[0])
     assert b > 0 and int(slots.sum()) >= 3
+
+
+def test_partially_resident_table():
+    """A budget holding only some layers: the resident prefix and the
+    regenerated rest give the words of the fully resident table."""
+    import paper_2310_14565_gb300 as pepsi
+
+    oc, gc, s, rlk, sets, Ts, cts, where, sid = _psi_case(64, PAPER, 4, 10, mu=7, m=20, n=70, planted=4, chunk=3)
+    mu = Ts.shape[0]
+    per_layer = gc.ell * gc.k * 64 * 8
+    os.environ["PEPSI_CHUNK"] = "3"
+    try:
+        g2 = pepsi.Context(N=64, t=T, prime_bits=PAPER, h=4, lambda_bar=10, mu=mu, hash_key=0x5EED, key_seed=3,
+                           resident_bytes=per_layer * 4)  # 4 of mu layers resident
+    finally:
+        os.environ.pop("PEPSI_CHUNK", None)
+    sid2 = g2.server_load(sets.server)
+    want = oc.eval(rlk, cts, Ts)
+    assert np.array_equal(g2.eval(sid2, cts), want)
+    _, ge = g2.eval_layers(sid2, cts, 2, 4)  # straddles the resident boundary
+    _, _, de = oc.eval(rlk, cts, Ts, debug=True)
+    assert np.array_equal(ge, de[2:6])
+    outs = g2.eval_batch([sid2, sid2], [cts, cts])
+    assert np.array_equal(outs[0], want) and np.array_equal(outs[1], want)
+    P = g2.server_plaintexts(sid2, 3, 2)
+    assert np.array_equal(P[1, 0], oc.server_plaintext(Ts, 4, 0))

@@ -159,6 +159,7 @@ def test_eval_layers_match_oracle(h, bits, lb):
 def test_eval_matches_oracle_both_modes(h, bits, lb, N):
     oc, gc, s, rlk, sets, Ts, cts, where, sid = _psi_case(N, bits, h, lb, mu=6, m=min(20, N // 2), n=70,
                                                           planted=4, chunk=4)
+    hashed = hashed_indicator(sets.client, sets.server, where, N, lb)
     for mode in (0, 1):
         want = oc.eval(rlk, cts, Ts, mode=mode, mask_seed=5)
         got = gc.eval(sid, cts, mode=mode, mask_seed=5)
@@ -169,11 +170,11 @@ def test_eval_matches_oracle_both_modes(h, bits, lb, N):
         assert abs(gb - ob) < 1e-9 and gb > 0
         if mode == 0:
             # exact in the hashed domain; contains every true member
-            assert np.array_equal(gslots, hashed_indicator(sets.client, sets.server, where, N, lb))
+            assert np.array_equal(gslots, hashed)
             true = brute_indicator(sets.client, sets.server, where, N)
             assert np.all(gslots >= true)
         else:
-            assert int(gslots.astype(np.int64).sum()) % T == len(sets.planted)
+            assert int(gslots.astype(np.int64).sum()) % T == int(hashed.sum())
 
 
 def test_eval_device_buffers_and_stream():

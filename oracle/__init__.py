@@ -112,9 +112,10 @@ def lib():
         L.or_relin.argtypes = [C.c_void_p, u64p, u64p, u64p]
         L.or_server_plaintext.argtypes = [C.c_void_p, u64p, C.c_uint32, C.c_uint32, C.c_uint32, C.c_uint32, u64p]
         L.or_query_plaintexts.argtypes = [C.c_void_p, u64p, C.c_uint32, C.c_uint32, u32p]
+        L.or_ct_mult_sum.argtypes = [C.c_void_p, u64p, u64p, C.c_uint32, u64p]
         L.or_eval.argtypes = [C.c_void_p, u64p, u64p, C.c_uint32, C.c_uint32, u64p, C.c_uint32,
-                              C.c_uint32, C.c_uint32, C.c_int, C.c_uint64, u64p, C.c_void_p,
-                              C.c_void_p, u64p]
+                              C.c_uint32, C.c_uint32, C.c_int, C.c_uint64, C.c_uint32, u64p, C.c_void_p,
+                              C.c_void_p, C.c_void_p, u64p]
         L.or_set_threads.argtypes = [C.c_int]
         L.or_get_threads.restype = C.c_int
         _lib = L
@@ -349,6 +350,16 @@ class Ctx:
         assert rc == 0
         return out
 
+    def ct_mult_sum(self, a, b):
+        """round(t/Q * sum_i a_i (x) b_i) mod Q with one rounding; a, b:
+        [n][2][k][N]."""
+        a = np.ascontiguousarray(a, np.uint64)
+        b = np.ascontiguousarray(b, np.uint64)
+        out = np.zeros((3, self.k, self.N), np.uint64)
+        rc = lib().or_ct_mult_sum(self._p, a, b, a.shape[0], out)
+        assert rc == 0
+        return out
+
     def relin(self, rlk, ct3):
         out = np.zeros((2, self.k, self.N), np.uint64)
         lib().or_relin(self._p, np.ascontiguousarray(rlk, np.uint64), np.ascontiguousarray(ct3, np.uint64), out)
@@ -380,22 +391,31 @@ class Ctx:
         m = self.query_plaintexts(table)
         return 0, self.encrypt(s, m, enc_seed), where
 
-    def eval(self, rlk, cts, T, mode=0, mask_seed=0, layer0=0, nlayers=None, debug=False):
+    def eval(self, rlk, cts, T, mode=0, mask_seed=0, layer0=0, nlayers=None, debug=False, group=1, acc=False):
         """Alg 2 over layers [layer0, layer0+nlayers).  Returns the result
-        ciphertext [2][k][N] and, with debug, per-layer h' and E words."""
+        ciphertext [2][k][N] and, with debug, per-layer h' and E words (E
+        only when group <= 1); with acc, also the layer sum before
+        relinearisation [3][k][N].  group > 1 rounds the last product of
+        runs of `group` consecutive layers once (lazy rescaling)."""
         mu = T.shape[0]
         nl = mu - layer0 if nlayers is None else nlayers
+        lazy = group > 1 and self.h > 1
         out = np.zeros((2, self.k, self.N), np.uint64)
         counts = np.zeros(2, np.uint64)
         dh = np.zeros((nl, 2, self.k, self.N), np.uint64) if debug else None
-        de = np.zeros((nl, 3, self.k, self.N), np.uint64) if debug else None
+        de = np.zeros((nl, 3, self.k, self.N), np.uint64) if debug and not lazy else None
+        da = np.zeros((3, self.k, self.N), np.uint64) if acc else None
         rc = lib().or_eval(self._p, np.ascontiguousarray(rlk, np.uint64), np.ascontiguousarray(cts, np.uint64),
                            self.ell, self.h, np.ascontiguousarray(T, np.uint64), mu, layer0, nl, mode, mask_seed,
-                           out, dh.ctypes.data if debug else None, de.ctypes.data if debug else None, counts)
+                           group, out, dh.ctypes.data if debug else None,
+                           de.ctypes.data if de is not None else None, da.ctypes.data if acc else None, counts)
         if rc:
             raise RuntimeError("oracle eval failed: %d" % rc)
         self.last_counts = (int(counts[0]), int(counts[1]))
-        return (out, dh, de) if debug else out
+        res = (out, dh, de) if debug else (out,)
+        if acc:
+            res = res + (da,)
+        return res if len(res) > 1 else res[0]
 
 
 def set_threads(n: int):

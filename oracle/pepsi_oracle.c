@@ -40,6 +40,7 @@ typedef unsigned __int128 u128;
 #define OR_MAXA 24   /* auxiliary primes for exact integer products */
 #define BNL 48       /* 32-bit limbs per big integer: 1536 bits */
 #define OR_DUMMY UINT64_MAX
+#define OR_MAX_GROUP 65536 /* most layers whose rounding may be deferred to one */
 
 enum { OR_OK = 0, OR_E_PARAM = 1, OR_E_BIN_OVERFLOW = 2, OR_E_CUCKOO_FAIL = 3, OR_E_NOMEM = 4 };
 
@@ -462,9 +463,10 @@ or_ctx* or_create(u32 N, u64 t, u32 k, const unsigned char* bits) {
   bn_divmod(&c->Qhalf, NULL, &c->Qhalf, &(bn){.d = {2}, .n = 1});
   for (u32 i = 0; i < k; i++)
     for (u32 j = 0; j < k; j++) c->invq[i * k + j] = (i == j) ? 1 : invmod(c->q[j] % c->q[i], c->q[i]);
-  /* auxiliary primes: product must exceed 4 * N * Q^2 (two products of
-   * centred values summed, both signs) */
-  double need = log2((double)N) + 2.0 * bn_log2(&c->Q) + 3.0, have = 0;
+  /* auxiliary primes: product must exceed 4 * G * N * Q^2 (two products of
+   * centred values summed, both signs, over up to G = OR_MAX_GROUP layers
+   * when the rounding is deferred to the group) */
+  double need = log2((double)N) + 2.0 * bn_log2(&c->Q) + 3.0 + log2((double)OR_MAX_GROUP), have = 0;
   c->na = 0;
   while (have < need) {
     if (c->na >= OR_MAXA) { or_free(c); return NULL; }
@@ -867,12 +869,15 @@ void or_ct_add_const(const or_ctx* c, u64* ct, i64 v) {
  * with a, b the centred lifts in (-Q/2, Q/2], then reduced mod Q.  The
  * integer products are computed exactly: residues mod auxiliary NTT primes
  * whose product exceeds the bound, CRT back to big integers. */
-int or_ct_mult(const or_ctx* c, const u64* a, const u64* b, u64* out) {
+
+/* The exact integer tensor of a and b as residues mod the auxiliary
+ * primes, added into T[3][na][N] (T starts at zero for a single product). */
+static int ct_tensor_aux(const or_ctx* c, const u64* a, const u64* b, u64* T) {
   u32 N = c->N, k = c->k, na = c->na;
   u64* A = (u64*)malloc(sizeof(u64) * 4 * na * N); /* [a0,a1,b0,b1][aux][N] */
-  u64* T = (u64*)malloc(sizeof(u64) * 3 * na * N);
   u64* tmp = (u64*)malloc(sizeof(u64) * N);
-  if (!A || !T || !tmp) { free(A); free(T); free(tmp); return OR_E_NOMEM; }
+  u64* prod = (u64*)malloc(sizeof(u64) * N);
+  if (!A || !tmp || !prod) { free(A); free(tmp); free(prod); return OR_E_NOMEM; }
   const u64* src[4] = {a, a + (u64)k * N, b, b + (u64)k * N};
   u64 x[OR_MAXK];
   for (u32 s = 0; s < 4; s++)
@@ -882,19 +887,26 @@ int or_ct_mult(const or_ctx* c, const u64* a, const u64* b, u64* out) {
       lift_q(c, x, &X);
       for (u32 j = 0; j < na; j++) A[((u64)s * na + j) * N + n] = sbn_mod_u64(&X, c->qa[j]);
     }
+  /* (component, index of the a factor, index of the b factor):
+   * d0 = a0 b0, d1 = a0 b1 + a1 b0, d2 = a1 b1 */
+  static const int terms[4][3] = {{0, 0, 2}, {1, 0, 3}, {1, 1, 2}, {2, 1, 3}};
   for (u32 j = 0; j < na; j++) {
     u64 qa = c->qa[j];
-    u64 *a0 = A + ((u64)0 * na + j) * N, *a1 = A + ((u64)1 * na + j) * N;
-    u64 *b0 = A + ((u64)2 * na + j) * N, *b1 = A + ((u64)3 * na + j) * N;
-    u64 *t0 = T + ((u64)0 * na + j) * N, *t1 = T + ((u64)1 * na + j) * N, *t2 = T + ((u64)2 * na + j) * N;
-    ring_mul(a0, b0, t0, N, &c->ta[j], tmp);
-    ring_mul(a1, b1, t2, N, &c->ta[j], tmp);
-    ring_mul(a0, b1, t1, N, &c->ta[j], tmp);
-    u64* t1b = (u64*)malloc(sizeof(u64) * N);
-    ring_mul(a1, b0, t1b, N, &c->ta[j], tmp);
-    for (u32 n = 0; n < N; n++) t1[n] = addmod(t1[n], t1b[n], qa);
-    free(t1b);
+    for (int ti = 0; ti < 4; ti++) {
+      const u64* x0 = A + ((u64)terms[ti][1] * na + j) * N;
+      const u64* y0 = A + ((u64)terms[ti][2] * na + j) * N;
+      u64* dst = T + ((u64)terms[ti][0] * na + j) * N;
+      ring_mul(x0, y0, prod, N, &c->ta[j], tmp);
+      for (u32 n = 0; n < N; n++) dst[n] = addmod(dst[n], prod[n], qa);
+    }
   }
+  free(A); free(tmp); free(prod);
+  return 0;
+}
+/* out[3][k][N] = round(t * X / Q) mod Q for the integers X whose residues
+ * mod the auxiliary primes are T[3][na][N], centred in (-PA/2, PA/2]. */
+static void ct_round_aux(const or_ctx* c, const u64* T, u64* out) {
+  u32 N = c->N, k = c->k, na = c->na;
   u64 xa[OR_MAXA];
   sbn half = {c->Qhalf, 0};
   for (u32 comp = 0; comp < 3; comp++)
@@ -910,8 +922,28 @@ int or_ct_mult(const or_ctx* c, const u64* a, const u64* b, u64* out) {
       sbn_floordiv(&y, &num, &c->Q); /* round(t*X/Q), Q odd */
       for (u32 p = 0; p < k; p++) out[((u64)comp * k + p) * N + n] = sbn_mod_u64(&y, c->q[p]);
     }
-  free(A); free(T); free(tmp);
-  return 0;
+}
+int or_ct_mult(const or_ctx* c, const u64* a, const u64* b, u64* out) {
+  u64* T = (u64*)calloc((u64)3 * c->na * c->N, sizeof(u64));
+  if (!T) return OR_E_NOMEM;
+  int rc = ct_tensor_aux(c, a, b, T);
+  if (!rc) ct_round_aux(c, T, out);
+  free(T);
+  return rc;
+}
+/* Deferred rounding over n products (lazy rescaling of a sum of products):
+ * out = round(t/Q * sum_i a_i (x) b_i) mod Q, one rounding of the sum of
+ * the exact integer tensors.  a, b: [n][2][k][N]; 1 <= n <= OR_MAX_GROUP. */
+int or_ct_mult_sum(const or_ctx* c, const u64* a, const u64* b, u32 n, u64* out) {
+  if (n == 0 || n > OR_MAX_GROUP) return OR_E_PARAM;
+  u64 ct2 = 2ULL * c->k * c->N;
+  u64* T = (u64*)calloc((u64)3 * c->na * c->N, sizeof(u64));
+  if (!T) return OR_E_NOMEM;
+  int rc = 0;
+  for (u32 i = 0; i < n && !rc; i++) rc = ct_tensor_aux(c, a + i * ct2, b + i * ct2, T);
+  if (!rc) ct_round_aux(c, T, out);
+  free(T);
+  return rc;
 }
 /* Relinearisation with RNS digits (no special prime): d_i = [d2]_{q_i} in
  * [0, q_i); (c0, c1) = (d0, d1) + sum_i d_i * rlk_i. */
@@ -988,15 +1020,19 @@ void or_query_plaintexts(const or_ctx* c, const u64* Tc, u32 ell, u32 h, u32* m)
  *   h=8: u = R(Mult(h',h')) - 7h';  w = R(Mult(u,u));
  *        E = Mult(w + 12u, w + 16u + 60)
  * which equal prod_{i<h}(h' - i); the factor 1/h! is applied once after the
- * sum over layers.  E is left without relinearisation. */
-static int eq_circuit(const or_ctx* c, const u64* rlk, u32 h, const u64* hp /*[2][k][N]*/, u64* E /*[3][k][N]*/, u32* nmult) {
+ * sum over layers.  E is left without relinearisation.
+ * With Xaux non-NULL (h >= 2) the last Mult is not rounded: the exact
+ * integer tensor of its operands is added into Xaux[3][na][N] (residues
+ * mod the auxiliary primes) instead, and E is not written. */
+static int eq_circuit(const or_ctx* c, const u64* rlk, u32 h, const u64* hp /*[2][k][N]*/, u64* E /*[3][k][N]*/,
+                      u64* Xaux, u32* nmult) {
   u32 N = c->N, k = c->k;
   u64 ct2 = 2ULL * k * N, ct3 = 3ULL * k * N;
   u64* buf = (u64*)calloc(8 * ct3, sizeof(u64));
   if (!buf) return OR_E_NOMEM;
   u64 *t3 = buf, *u = buf + ct3, *w = buf + 2 * ct3, *x = buf + 3 * ct3, *y = buf + 4 * ct3;
   int rc = 0;
-  memset(E, 0, sizeof(u64) * ct3);
+  if (E) memset(E, 0, sizeof(u64) * ct3);
   switch (h) {
     case 1:
       memcpy(E, hp, sizeof(u64) * ct2);
@@ -1004,7 +1040,7 @@ static int eq_circuit(const or_ctx* c, const u64* rlk, u32 h, const u64* hp /*[2
     case 2:
       memcpy(x, hp, sizeof(u64) * ct2);
       or_ct_add_const(c, x, -1);
-      rc = or_ct_mult(c, hp, x, E); (*nmult)++;
+      rc = Xaux ? ct_tensor_aux(c, hp, x, Xaux) : or_ct_mult(c, hp, x, E); (*nmult)++;
       break;
     case 4:
       rc = or_ct_mult(c, hp, hp, t3); (*nmult)++;
@@ -1012,7 +1048,7 @@ static int eq_circuit(const or_ctx* c, const u64* rlk, u32 h, const u64* hp /*[2
       or_ct_axpy(c, u, -3, hp, 2, u);
       memcpy(x, u, sizeof(u64) * ct2);
       or_ct_add_const(c, x, 2);
-      rc |= or_ct_mult(c, u, x, E); (*nmult)++;
+      rc |= Xaux ? ct_tensor_aux(c, u, x, Xaux) : or_ct_mult(c, u, x, E); (*nmult)++;
       break;
     case 8:
       rc = or_ct_mult(c, hp, hp, t3); (*nmult)++;
@@ -1023,7 +1059,7 @@ static int eq_circuit(const or_ctx* c, const u64* rlk, u32 h, const u64* hp /*[2
       or_ct_axpy(c, w, 12, u, 2, x);
       or_ct_axpy(c, w, 16, u, 2, y);
       or_ct_add_const(c, y, 60);
-      rc |= or_ct_mult(c, x, y, E); (*nmult)++;
+      rc |= Xaux ? ct_tensor_aux(c, x, y, Xaux) : or_ct_mult(c, x, y, E); (*nmult)++;
       break;
     default:
       rc = OR_E_PARAM;
@@ -1048,21 +1084,32 @@ static i64 inv_hfact(const or_ctx* c, u32 h) {
  *   with r uniform in Z_t^N, r_{N-1} = -sum of the others.
  * cts: [ell][2][k][N] coefficient form.  T: server table [mu][N].
  * dbg_h: [nl][2][k][N] h' (coefficient form), dbg_e: [nl][3][k][N] E.
+ * dbg_acc: [3][k][N] the layer sum A before relinearisation.
  * counts (optional): [0] plaintext mults, [1] ciphertext mults.
+ * group: rounding of the last Mult of each layer.  group <= 1 rounds every
+ * layer (E_{i'} as above).  group = G > 1 (lazy rescaling, h >= 2) splits
+ * the layers, from layer0 on, into runs of G consecutive layers; the exact
+ * integer tensors of a run's last Mults are summed and rounded once,
+ * round(t/Q * sum X_{i'}), and the runs' results are summed mod Q into A.
+ * Per-layer E words do not exist then, so dbg_e must be NULL.
  * The plaintext-times-ciphertext sums are accumulated in the NTT domain
  * and transformed back once per layer (the inverse NTT is linear). */
 int or_eval(const or_ctx* c, const u64* rlk, const u64* cts, u32 ell, u32 h, const u64* T, u32 mu, u32 layer0,
-            u32 nl, int mode, u64 mask_seed, u64* out, u64* dbg_h, u64* dbg_e, u64* counts) {
+            u32 nl, int mode, u64 mask_seed, u32 group, u64* out, u64* dbg_h, u64* dbg_e, u64* dbg_acc,
+            u64* counts) {
   u32 N = c->N, k = c->k;
   if (layer0 + nl > mu || (h != 1 && h != 2 && h != 4 && h != 8)) return OR_E_PARAM;
-  u64 ct2 = 2ULL * k * N, ct3 = 3ULL * k * N;
+  if (group > OR_MAX_GROUP) return OR_E_PARAM;
+  const int lazy = group > 1 && h > 1;
+  if (lazy && dbg_e) return OR_E_PARAM;
+  u64 ct2 = 2ULL * k * N, ct3 = 3ULL * k * N, ctx = 3ULL * c->na * N;
   /* query ciphertexts to NTT form */
   u64* CN = (u64*)malloc(sizeof(u64) * ell * ct2);
   if (!CN) return OR_E_NOMEM;
   memcpy(CN, cts, sizeof(u64) * ell * ct2);
 #pragma omp parallel for schedule(dynamic)
   for (long jj = 0; jj < (long)ell * 2 * k; jj++) ntt_fwd(CN + (u64)jj * N, N, &c->tq[jj % k]);
-  u64* Eall = (u64*)calloc((u64)(nl ? nl : 1) * ct3, sizeof(u64));
+  u64* Eall = (u64*)calloc((u64)(nl ? nl : 1) * (lazy ? ctx : ct3), sizeof(u64)); /* E, or X when lazy */
   u64 pm = 0, mm = 0;
   int rc = 0;
 #pragma omp parallel for schedule(dynamic) reduction(+ : pm, mm) reduction(| : rc)
@@ -1097,7 +1144,10 @@ int or_eval(const or_ctx* c, const u64* rlk, const u64* cts, u32 ell, u32 h, con
         ntt_inv(hrow, N, &c->tq[p]);
       }
     if (dbg_h) memcpy(dbg_h + (u64)li * ct2, hp, sizeof(u64) * ct2);
-    rc |= eq_circuit(c, rlk, h, hp, Eall + (u64)li * ct3, &nm);
+    if (lazy)
+      rc |= eq_circuit(c, rlk, h, hp, NULL, Eall + (u64)li * ctx, &nm);
+    else
+      rc |= eq_circuit(c, rlk, h, hp, Eall + (u64)li * ct3, NULL, &nm);
     mm += nm;
     if (dbg_e) memcpy(dbg_e + (u64)li * ct3, Eall + (u64)li * ct3, sizeof(u64) * ct3);
     free(acc); free(pt); free(hp); free(sl); free(mt); free(pos);
@@ -1105,13 +1155,39 @@ int or_eval(const or_ctx* c, const u64* rlk, const u64* cts, u32 ell, u32 h, con
   if (rc) { free(CN); free(Eall); return rc; }
   /* A = sum over layers (mod Q) */
   u64* A = (u64*)calloc(ct3, sizeof(u64));
-  for (u32 li = 0; li < nl; li++)
-    for (u32 comp = 0; comp < 3; comp++)
-      for (u32 p = 0; p < k; p++)
-        for (u32 n = 0; n < N; n++) {
-          u64 i = ((u64)comp * k + p) * N + n;
-          A[i] = addmod(A[i], Eall[(u64)li * ct3 + i], c->q[p]);
-        }
+  if (lazy) {
+    /* each run of `group` layers: sum the exact tensors, round once */
+    u64* Xg = (u64*)malloc(sizeof(u64) * ctx);
+    u64* Eg = (u64*)malloc(sizeof(u64) * ct3);
+    for (u32 g0 = 0; g0 < nl; g0 += group) {
+      u32 g1 = g0 + group < nl ? g0 + group : nl;
+      memset(Xg, 0, sizeof(u64) * ctx);
+      for (u32 li = g0; li < g1; li++)
+        for (u32 comp = 0; comp < 3; comp++)
+          for (u32 j = 0; j < c->na; j++)
+            for (u32 n = 0; n < N; n++) {
+              u64 i = ((u64)comp * c->na + j) * N + n;
+              Xg[i] = addmod(Xg[i], Eall[(u64)li * ctx + i], c->qa[j]);
+            }
+      ct_round_aux(c, Xg, Eg);
+      for (u32 comp = 0; comp < 3; comp++)
+        for (u32 p = 0; p < k; p++)
+          for (u32 n = 0; n < N; n++) {
+            u64 i = ((u64)comp * k + p) * N + n;
+            A[i] = addmod(A[i], Eg[i], c->q[p]);
+          }
+    }
+    free(Xg); free(Eg);
+  } else {
+    for (u32 li = 0; li < nl; li++)
+      for (u32 comp = 0; comp < 3; comp++)
+        for (u32 p = 0; p < k; p++)
+          for (u32 n = 0; n < N; n++) {
+            u64 i = ((u64)comp * k + p) * N + n;
+            A[i] = addmod(A[i], Eall[(u64)li * ct3 + i], c->q[p]);
+          }
+  }
+  if (dbg_acc) memcpy(dbg_acc, A, sizeof(u64) * ct3);
   or_relin(c, rlk, A, out);
   or_ct_scale(c, out, inv_hfact(c, h), 2);
   if (mode == 1) {

@@ -464,3 +464,100 @@ def test_psi_matches_brute_force(oracle_mod, h, bits, lb):
     slots_c, _ = c.decrypt(s, out_c)
     assert int(slots_c.astype(np.int64).sum()) % T == len(sets.planted)
     assert not (slots_c == want).all()  # masked: individual slots hide the indicator
+
+
+# ------------------------------------------------- deferred (lazy) rounding
+def test_mult_sum_words_against_big_integer_schoolbook(oracle_mod):
+    # one rounding of a sum of products: round(t/Q * sum_i a~_i (x) b~_i),
+    # exact integers, centred lifts
+    c = oracle_mod.Ctx(N=8, t=T, prime_bits=[36, 37], h=1, lambda_bar=3)
+    s, _ = c.keygen(5)
+    rng = np.random.default_rng(7)
+    n = 3
+    ca = np.stack([c.encrypt(s, c.encode(rand_slots(rng, 8)), 10 + i)[0] for i in range(n)])
+    cb = np.stack([c.encrypt(s, c.encode(rand_slots(rng, 8)), 20 + i)[0] for i in range(n)])
+    Q, N = c.Q, c.N
+
+    def lift(ct, comp):
+        v = [int(sympy_crt(c.q, [int(ct[comp, p, m]) for p in range(c.k)])[0]) for m in range(N)]
+        return [x - Q if x > Q // 2 else x for x in v]
+
+    X = [[0] * N for _ in range(3)]
+    for i in range(n):
+        a0, a1, b0, b1 = lift(ca[i], 0), lift(ca[i], 1), lift(cb[i], 0), lift(cb[i], 1)
+        terms = (negacyclic_schoolbook(a0, b0, N),
+                 [u + v for u, v in zip(negacyclic_schoolbook(a0, b1, N), negacyclic_schoolbook(a1, b0, N))],
+                 negacyclic_schoolbook(a1, b1, N))
+        for comp in range(3):
+            X[comp] = [u + v for u, v in zip(X[comp], terms[comp])]
+    got = c.ct_mult_sum(ca, cb)
+    for comp in range(3):
+        for m in range(N):
+            y = (T * X[comp][m] + (Q - 1) // 2) // Q
+            for p, q in enumerate(c.q):
+                assert int(got[comp, p, m]) == y % q
+    # a single product is the ordinary multiplication
+    assert np.array_equal(c.ct_mult_sum(ca[:1], cb[:1]), c.ct_mult(ca[0], cb[0]))
+
+
+def _lazy_case(oracle_mod, h, bits, lb):
+    from paper_2310_14565_gb300.workload import make_sets
+
+    N = 64
+    sets = make_sets(24, 150, 7, bits=32, seed_items=h, seed_plant=h + 1)
+    load = oracle_mod.simple_hash(99, lb, 6, sets.server, 1000)[2]
+    c = oracle_mod.Ctx(N=N, t=T, prime_bits=bits, h=h, lambda_bar=lb, hash_key=99, mu=max(7, load))
+    s, rlk = c.keygen(3)
+    rc, Ts, _ = c.server_table(sets.server)
+    assert rc == 0
+    rc, cts, where = c.query(s, sets.client, 4)
+    assert rc == 0
+    return c, s, rlk, sets, Ts, cts, where
+
+
+@pytest.mark.parametrize("h,bits,lb", [(2, [36, 36, 37], 10), (4, [55, 55, 54, 54], 12), (8, [55] * 6 + [54] * 2, 14)])
+def test_lazy_rescale_bounded_rounding_difference(oracle_mod, h, bits, lb):
+    # Sum_l round(y_l) and round(Sum_l y_l) differ by at most (G + 1)/2 per
+    # run of G layers, so the layer sums before relinearisation differ by at
+    # most (nl + runs)/2 per coefficient; a one-layer run is the canonical
+    # rounding itself
+    c, s, rlk, sets, Ts, cts, where = _lazy_case(oracle_mod, h, bits, lb)
+    mu = Ts.shape[0]
+    out1, A1 = c.eval(rlk, cts, Ts, acc=True)
+    for group in (2, 3, mu):
+        outg, Ag = c.eval(rlk, cts, Ts, group=group, acc=True)
+        runs = -(-mu // group)
+        bound = (mu + runs) // 2
+        for comp in range(3):
+            for m in range(c.N):
+                d = int(sympy_crt(c.q, [(int(Ag[comp, p, m]) - int(A1[comp, p, m])) % q
+                                        for p, q in enumerate(c.q)])[0])
+                d = d - c.Q if d > c.Q // 2 else d
+                assert abs(d) <= bound
+        assert not np.array_equal(Ag, A1)  # the words do change
+    o1 = c.eval(rlk, cts, Ts, layer0=2, nlayers=1)
+    assert np.array_equal(c.eval(rlk, cts, Ts, layer0=2, nlayers=1, group=4), o1)
+
+
+@pytest.mark.parametrize("h,bits,lb", [(2, [36, 36, 37], 10), (4, [55, 55, 54, 54], 12), (8, [55] * 6 + [54] * 2, 14)])
+def test_lazy_rescale_psi_matches_hashed_brute_force(oracle_mod, h, bits, lb):
+    c, s, rlk, sets, Ts, cts, where = _lazy_case(oracle_mod, h, bits, lb)
+    mu = Ts.shape[0]
+    srv = {}
+    for y in sets.server:
+        yl, bins = oracle_mod.hash_item(99, lb, 6, y)
+        for b in bins:
+            srv.setdefault(b, set()).add(yl)
+    hashed = np.zeros(c.N, np.uint32)
+    for u, x in enumerate(sets.client):
+        xl, _ = oracle_mod.hash_item(99, lb, 6, x)
+        hashed[where[u]] = int(xl in srv.get(int(where[u]), set()))
+    budgets = []
+    for group in (3, mu):
+        slots, bud = c.decrypt(s, c.eval(rlk, cts, Ts, group=group))
+        assert bud > 0 and (slots == hashed).all()
+        budgets.append(bud)
+        slots_c, _ = c.decrypt(s, c.eval(rlk, cts, Ts, mode=1, mask_seed=5, group=group))
+        assert int(slots_c.astype(np.int64).sum()) % T == int(hashed.sum())
+    _, b1 = c.decrypt(s, c.eval(rlk, cts, Ts))
+    assert budgets[-1] >= b1 - 1.0  # fewer roundings: no worse noise

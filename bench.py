@@ -8,7 +8,10 @@ h = 4, mu = 526 server layers; 1024 client items against 2^20 server items
 
 One step = one pepsi_eval (Algorithm 2 with the equality circuit of
 Algorithm 1) from device-resident request ciphertexts to a device-resident
-result ciphertext.  The resident server plaintext table (82.7 GB) is read in
+result ciphertext.  By default the last ciphertext products of all layers
+are rounded once (lazy rescaling, --rescale all); --rescale layer rounds
+every layer's product (textbook FV words).  Both are exact and decrypt to
+the same result; the line reports the other mode's time too.  The resident server plaintext table (82.7 GB) is read in
 full by every step, so the inputs of a step are larger than L2.
 
 Prints one JSON line.  --impl reference times the CPU oracle instead (the
@@ -40,6 +43,8 @@ HASH_KEY, KEY_SEED, ENC_SEED = 0x5EED, 3, 4
 WORKLOAD_NAME = ("paper-shaped PSI: N=8192 bins, t=65537, q=4 RNS primes (55,55,54,54 bits), CW code ell=600 h=4, "
                  "mu=526 layers, 1024 client x 2^20 server uniform 64-bit items, 102 planted")
 L2_NOTE = "inputs larger than L2: the 82.7 GB resident plaintext table is streamed from HBM every step"
+RESCALE_NOTE = {"all": "lazy: last ciphertext products of all layers summed exactly, rounded once",
+                "layer": "per layer: every ciphertext product rounded (textbook FV)"}
 
 
 def measured_peaks():
@@ -108,21 +113,24 @@ def oracle_setup():
     return oracle, oc, rlk, cts, Ts
 
 
-def oracle_sample(oracle, oc, rlk, cts, Ts, layers, layer0=0):
+RESCALE = {"all": 0xFFFFFFFF, "layer": 1}
+
+
+def oracle_sample(oracle, oc, rlk, cts, Ts, layers, layer0=0, lazy=True):
     t = time.perf_counter()
-    oc.eval(rlk, cts, Ts, layer0=layer0, nlayers=layers)
+    oc.eval(rlk, cts, Ts, layer0=layer0, nlayers=layers, group=max(1, layers) if lazy else 1)
     return (time.perf_counter() - t) * 1e3
 
 
-def cpu_baseline():
+def cpu_baseline(lazy):
     """The oracle as it stands on the host cores, on a bounded sample: the
     fixed part (request NTT, final relinearisation) plus a layer sample,
-    scaled to the workload's 526 layers."""
+    scaled to the workload's 526 layers, in the rounding mode of the run."""
     oracle, oc, rlk, cts, Ts = oracle_setup()
     cores = oracle.get_threads()
     layers = max(2, 2 * cores)
-    fixed = oracle_sample(oracle, oc, rlk, cts, Ts, 0)
-    total = oracle_sample(oracle, oc, rlk, cts, Ts, layers)
+    fixed = oracle_sample(oracle, oc, rlk, cts, Ts, 0, lazy=lazy)
+    total = oracle_sample(oracle, oc, rlk, cts, Ts, layers, lazy=lazy)
     est = fixed + (total - fixed) * WL["mu"] / layers
     return {"value": round(est, 1), "unit": "ms", "cores": cores, "kind": "oracle",
             "sample": "request NTT + relin/scale (%.0f ms) and %d of 526 layers (%.0f ms), layer part scaled to 526"
@@ -138,8 +146,9 @@ def run_reference(args):
     fixed = oracle_sample(oracle, oc, rlk, cts, Ts, 0)
     layers = max(1, cores)
     times = []
+    lazy = args.rescale == "all"
     for i in range(args.warmup + args.steps):
-        t = oracle_sample(oracle, oc, rlk, cts, Ts, layers, layer0=(i * layers) % (WL["mu"] - layers))
+        t = oracle_sample(oracle, oc, rlk, cts, Ts, layers, layer0=(i * layers) % (WL["mu"] - layers), lazy=lazy)
         if i >= args.warmup:
             times.append(t)
     per = statistics.median(times)
@@ -148,7 +157,7 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": round(est, 1), "unit": "ms", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(per, 1), "higher_is_better": False,
         "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-        "config": {"workload": WORKLOAD_NAME, "l2": "CPU run"},
+        "config": {"workload": WORKLOAD_NAME, "l2": "CPU run", "rescale": RESCALE_NOTE[args.rescale]},
         "cpu_baseline": {"value": round(est, 1), "unit": "ms", "cores": cores, "kind": "oracle",
                          "sample": "each step: request NTT + %d of 526 layers; value scales the layer part to 526"
                                    % layers},
@@ -175,8 +184,12 @@ def run_ours(args):
     if not os.path.exists(pepsi.LIB_PATH):
         _build.build()
     N, k = WL["N"], len(WL["prime_bits"])
+    # the auxiliary base is sized for one rounding over all layers; the
+    # rounding mode of each evaluation is then a context setting
     ctx = pepsi.Context(N=N, t=65537, prime_bits=WL["prime_bits"], h=WL["h"], ell=WL["ell"],
-                        lambda_bar=WL["lambda_bar"], mu=WL["mu"], hash_key=HASH_KEY, key_seed=KEY_SEED)
+                        lambda_bar=WL["lambda_bar"], mu=WL["mu"], hash_key=HASH_KEY, key_seed=KEY_SEED,
+                        rescale_group=RESCALE["all"])
+    ctx.set_rescale_group(RESCALE[args.rescale])
     sets = make_sets(WL["m"], WL["n"], WL["planted"], bits=64)
     t0 = time.perf_counter()
     sid = ctx.server_load(sets.server)
@@ -250,11 +263,30 @@ def run_ours(args):
         e2e.append((time.perf_counter() - t) * 1e3)
     e2e_ms = statistics.median(e2e)
 
+    # the other rounding mode on the same context and table (same outputs after decryption)
+    other = "layer" if args.rescale == "all" else "all"
+    ctx.set_rescale_group(RESCALE[other])
+    for _ in range(2):
+        step()
+    oslots, obudget = ctx.decrypt(out_dev)
+    osteps = max(3, min(args.steps, 10))
+    e0.record(stream)
+    for _ in range(osteps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    other_line = {"rescale": RESCALE_NOTE[other], "ms_per_step": round(e0.elapsed_time(e1) / osteps, 3),
+                  "noise_budget_bits": round(obudget, 2),
+                  "same_decryption": bool((oslots == slots).all()), "steps": osteps}
+    ctx.set_rescale_group(RESCALE[args.rescale])
+
     if args.case == "large":
         line = {"metric": METRIC, "value": round(ms, 3), "unit": "ms", "n_gpus": args.gpus, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": round(ms, 3), "higher_is_better": False, "scaling": "weak",
                 "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-                "config": {"workload": WORKLOAD_NAME, "l2": "inputs larger than L2 (plaintext chunks of 4.3 GB)"},
+                "config": {"workload": WORKLOAD_NAME, "l2": "inputs larger than L2 (plaintext chunks of 4.3 GB)",
+                           "rescale": RESCALE_NOTE[args.rescale]},
+                "other_rounding": other_line,
                 "correct": correct, "noise_budget_bits": round(budget, 2),
                 "offline_server_load_ms": round(offline_ms, 1),
                 "kernel_ms_per_step": {name: round(v[1] / psteps, 3) for name, v in prof.items() if v[0]},
@@ -348,7 +380,9 @@ def run_ours(args):
         "warmup": args.warmup, "ms_per_step": round(ms, 3), "higher_is_better": False, "scaling": "weak",
         "vs_baseline": None, "dtype": "u64", "data": "synthetic",
         "config": {"workload": WORKLOAD_NAME, "l2": L2_NOTE, "parallelism": "replicas" if ws > 1 else "1 GPU",
-                   "resident_plaintexts_gb": round(mu * ell * k * N * 8 / 1e9, 1)},
+                   "resident_plaintexts_gb": round(mu * ell * k * N * 8 / 1e9, 1),
+                   "rescale": RESCALE_NOTE[args.rescale]},
+        "other_rounding": other_line,
         "correct": correct, "noise_budget_bits": round(budget, 2),
         "offline_server_load_ms": round(offline_ms, 1),
         "ct_mult_relin_per_s": round(mult_per_s, 1),
@@ -367,7 +401,7 @@ def run_ours(args):
         "clocks": clk,
     }
     if rank == 0 and args.gpus == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline()
+        line["cpu_baseline"] = cpu_baseline(args.rescale == "all")
     if rank == 0:
         print(json.dumps(line), flush=True)
     ctx.close()
@@ -408,6 +442,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--rescale", choices=["all", "layer"], default="all",
+                    help="all: one rounding of the layers' last products per evaluation (lazy rescaling); "
+                         "layer: every product rounded (textbook FV words)")
     ap.add_argument("--case", choices=["paper", "small", "large"], default="paper",
                     help="small: the same kernels on 2^14 server items (mu=35), for profiler captures; "
                          "large: N=16384, 8 primes, h=8, 4096 x 2^24 items, streamed plaintexts")

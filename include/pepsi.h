@@ -55,6 +55,9 @@ enum {
   PEPSI_MODE_CARDINALITY = 1 /* Algorithm 5 with val_s = 1: masked, slots sum to |X cap Y| */
 };
 
+/* pepsi_params.rescale_group: one rounding for all layers of an evaluation. */
+#define PEPSI_RESCALE_ALL 0xFFFFFFFFu
+
 typedef struct pepsi_ctx pepsi_ctx; /* opaque */
 
 /* Parameters (Table 2 notation).  Zero means "derive". */
@@ -73,6 +76,19 @@ typedef struct {
                               prefix of layers that fits stays resident, the rest is
                               regenerated per chunk at evaluation.  0: 60% of free
                               HBM at load time; UINT64_MAX: none; else a byte cap */
+  uint32_t rescale_group;  /* rounding of the last ciphertext product of each layer in
+                              pepsi_eval / pepsi_eval_batch.  0 or 1: every layer's product
+                              is rounded, round(t/Q * X), as in textbook FV multiplication.
+                              G > 1 (lazy rescaling): the exact integer products of runs of
+                              G consecutive layers (from the first evaluated layer) are
+                              summed in the auxiliary base and each run is rounded once,
+                              round(t/Q * sum X); the result decrypts the same, its words
+                              differ, and each run saves the inverse transforms and the
+                              rounding of G - 1 products.  PEPSI_RESCALE_ALL: one run per
+                              evaluation.  The auxiliary base is sized at setup for runs of
+                              up to pepsi_info.rescale_cap layers (G itself; for
+                              PEPSI_RESCALE_ALL mu, or 65536 when mu = 0); longer runs are
+                              cut at the cap.  pepsi_eval_layers always rounds per layer. */
 } pepsi_params;
 
 /* Derived values of a context (for callers and tests). */
@@ -84,6 +100,8 @@ typedef struct {
   uint64_t psi_t;       /* minimal primitive 2N-th root mod t */
   uint64_t b_primes[12];/* auxiliary base B used for exact multiplication */
   double log2_q;
+  uint32_t rescale_group;/* rescale_group as given (0 and 1 both mean per layer) */
+  uint32_t rescale_cap;  /* most layers one rounding may cover (1: per-layer rounding only) */
 } pepsi_info;
 
 /* Setup (Section 4, parameters of Tables 2-3): derives ell (Eq. 1), the
@@ -96,6 +114,13 @@ int pepsi_setup(const pepsi_params* params, uint64_t key_seed, pepsi_ctx** out);
 
 /* Fill *info with the context's derived parameters. */
 int pepsi_get_info(const pepsi_ctx* ctx, pepsi_info* info);
+
+/* Set the rounding run length of later evaluations on this context, with
+ * the meaning of pepsi_params.rescale_group (1: per-layer rounding; G > 1
+ * or PEPSI_RESCALE_ALL: lazy rescaling).  Runs stay cut at the
+ * rescale_cap fixed at setup, so every value is accepted and the result
+ * stays exact.  Errors: PEPSI_E_PARAM for a null context. */
+int pepsi_set_rescale_group(pepsi_ctx* ctx, uint32_t rescale_group);
 
 /* Server preprocessing, offline (Section 4.1 and App. Alg 7, server side):
  * H_0 to lambda bits, permutation-based hashing into each of the three

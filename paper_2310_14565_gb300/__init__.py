@@ -40,6 +40,7 @@ class Params(C.Structure):
         ("N", C.c_uint32), ("t", C.c_uint64), ("k", C.c_uint32), ("prime_bits", C.c_uint8 * 8),
         ("h", C.c_uint32), ("ell", C.c_uint32), ("lambda_bar", C.c_uint32), ("num_hashes", C.c_uint32),
         ("mu", C.c_uint32), ("hash_key", C.c_uint64), ("resident_bytes", C.c_uint64),
+        ("rescale_group", C.c_uint32),
     ]
 
 
@@ -48,14 +49,17 @@ class Info(C.Structure):
         ("N", C.c_uint32), ("k", C.c_uint32), ("kb", C.c_uint32), ("ell", C.c_uint32), ("h", C.c_uint32),
         ("mu", C.c_uint32), ("lambda_bar", C.c_uint32), ("logb", C.c_uint32), ("t", C.c_uint64),
         ("q", C.c_uint64 * 8), ("psi", C.c_uint64 * 8), ("psi_t", C.c_uint64), ("b_primes", C.c_uint64 * 12),
-        ("log2_q", C.c_double),
+        ("log2_q", C.c_double), ("rescale_group", C.c_uint32), ("rescale_cap", C.c_uint32),
     ]
 
+
+RESCALE_ALL = 0xFFFFFFFF
 
 SYMBOLS = {
     # name: (restype, argtypes)
     "pepsi_setup": (C.c_int, [C.POINTER(Params), C.c_uint64, C.POINTER(C.c_void_p)]),
     "pepsi_get_info": (C.c_int, [C.c_void_p, C.POINTER(Info)]),
+    "pepsi_set_rescale_group": (C.c_int, [C.c_void_p, C.c_uint32]),
     "pepsi_server_load": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t, C.POINTER(C.c_int)]),
     "pepsi_server_table": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p]),
     "pepsi_server_plaintexts": (C.c_int, [C.c_void_p, C.c_int, C.c_uint32, C.c_uint32, C.c_void_p, C.c_void_p]),
@@ -151,13 +155,13 @@ class Context:
     """One parameter set with its keys, server sets and scratch (pepsi_ctx)."""
 
     def __init__(self, N, t=65537, prime_bits=(36, 36, 37), h=2, ell=0, lambda_bar=16, mu=0, hash_key=0,
-                 key_seed=3, resident_bytes=0):
+                 key_seed=3, resident_bytes=0, rescale_group=0):
         p = Params()
         p.N, p.t, p.k = N, t, len(prime_bits)
         for i, b in enumerate(prime_bits):
             p.prime_bits[i] = b
         p.h, p.ell, p.lambda_bar, p.num_hashes, p.mu = h, ell, lambda_bar, 3, mu
-        p.hash_key, p.resident_bytes = hash_key, resident_bytes
+        p.hash_key, p.resident_bytes, p.rescale_group = hash_key, resident_bytes, rescale_group
         self._h = C.c_void_p()
         _check(lib().pepsi_setup(C.byref(p), key_seed, C.byref(self._h)), "pepsi_setup")
         info = Info()
@@ -168,6 +172,7 @@ class Context:
         self.psi = [int(info.psi[i]) for i in range(self.k)]
         self.psi_t = int(info.psi_t)
         self.b_primes = [int(info.b_primes[i]) for i in range(min(self.kb, 12))]
+        self.rescale_cap = int(info.rescale_cap)
         self.mu = {}
 
     def close(self):
@@ -184,6 +189,11 @@ class Context:
     # ---- shapes
     def ct_words(self, comps=2):
         return comps * self.k * self.N
+
+    def set_rescale_group(self, group):
+        """Rounding run length of later evaluations (1: per layer;
+        RESCALE_ALL: one rounding per evaluation), cut at rescale_cap."""
+        _check(lib().pepsi_set_rescale_group(self._h, int(group)), "pepsi_set_rescale_group")
 
     # ---- server side
     def server_load(self, items):

@@ -671,6 +671,60 @@ __global__ void k_tensor(DevView V, const u64* __restrict__ AQ, const u64* __res
   o[(size_t)2 * np * rs] = d2;
 }
 
+// Lazy rescaling: X[c][pi][n] (+)= sum over layers l < L of component c of
+// the tensor of (A_l, B_l), in NTT form over Q u B.  The products of each
+// (prime, point) are summed in 128 bits and reduced once per 16 layers
+// (32 products below 2^122 each stay below 2^127), so the sum is exact mod
+// every prime; the integer it represents is the sum of the layers' exact
+// integer tensors as long as B holds it (sized at setup).
+__global__ void k_tensor_sum(DevView V, const u64* __restrict__ AQ, const u64* __restrict__ AB,
+                             const u64* __restrict__ BQ, const u64* __restrict__ BB, const u64* __restrict__ cstQ,
+                             const u64* __restrict__ side, u64* __restrict__ X, int L, int square, int init) {
+  const int N = V.N, k = V.k, kb = V.kb, np = k + kb;
+  const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;  // over np*N
+  if (idx >= (size_t)np * N) return;
+  const int n = (int)(idx % N);
+  const int pi = (int)(idx / N);
+  const DevPrime pr = V.pr[pi];
+  const bool inQ = pi < k;
+  const int kk = inQ ? k : kb, pp = inQ ? pi : pi - k;
+  const u64* A = inQ ? AQ : AB;
+  const u64* Bp = inQ ? BQ : BB;
+  const u64 cq = (inQ && cstQ) ? cstQ[pi] : 0;
+  const size_t cs = (size_t)kk * N;  // component stride of the operands
+  u64 s0l = 0, s0h = 0, s1l = 0, s1h = 0, s2l = 0, s2h = 0;
+  for (int l = 0; l < L; ++l) {
+    const size_t o0 = ((size_t)l * 2 * kk + pp) * N + n;
+    const u64 a0 = A[o0], a1 = A[o0 + cs];
+    u64 b0 = a0, b1 = a1;
+    if (!square) {
+      b0 = Bp[o0];
+      b1 = Bp[o0 + cs];
+      if (inQ) {
+        b0 = addmod(b0, cq, pr.q);
+      } else if (side) {
+        b0 = addmod(b0, side[(size_t)l * kb + pp], pr.q);
+      }
+    }
+    mac128(s0l, s0h, a0, b0);
+    mac128(s1l, s1h, a0, b1);
+    mac128(s1l, s1h, a1, b0);
+    mac128(s2l, s2h, a1, b1);
+    if ((l & 15) == 15) {
+      s0l = barrett128(s0h, s0l, pr.q, pr.bhi, pr.blo);
+      s1l = barrett128(s1h, s1l, pr.q, pr.bhi, pr.blo);
+      s2l = barrett128(s2h, s2l, pr.q, pr.bhi, pr.blo);
+      s0h = s1h = s2h = 0;
+    }
+  }
+  u64 d[3] = {barrett128(s0h, s0l, pr.q, pr.bhi, pr.blo), barrett128(s1h, s1l, pr.q, pr.bhi, pr.blo),
+              barrett128(s2h, s2l, pr.q, pr.bhi, pr.blo)};
+  u64* o = X + (size_t)pi * N + n;
+  const size_t os = (size_t)np * N;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) o[c * os] = init ? d[c] : addmod(d[c], o[c * os], pr.q);
+}
+
 // ------------------------------------------------------ scale and round
 // y = round(t x / Q) exactly: z = t x + (Q-1)/2, [z]_Q from the Q residues
 // by Garner, y = (z - [z]_Q) / Q computed in B, y centred in B and mapped
@@ -1125,6 +1179,13 @@ void launch_tensor(const DevView& V, const u64* AQ, const u64* AB, const u64* BQ
   const size_t total = (size_t)L * (V.k + V.kb) * V.N;
   if (!total) return;
   k_tensor<<<grid_for(total, 256), 256, 0, st>>>(V, AQ, AB, BQ, BB, cstQ, side, T3, L, square ? 1 : 0);
+}
+
+void launch_tensor_sum(const DevView& V, const u64* AQ, const u64* AB, const u64* BQ, const u64* BB,
+                       const u64* cstQ, const u64* side, u64* X, int L, bool square, bool init, cudaStream_t st) {
+  const size_t total = (size_t)(V.k + V.kb) * V.N;
+  k_tensor_sum<<<grid_for(total, 128), 128, 0, st>>>(V, AQ, AB, BQ, BB, cstQ, side, X, L, square ? 1 : 0,
+                                                      init ? 1 : 0);
 }
 
 void launch_scale_round(const DevView& V, const u64* T3, u64* D, int L, cudaStream_t st) {

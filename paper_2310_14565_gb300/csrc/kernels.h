@@ -42,6 +42,9 @@ void launch_tensor(const DevView& V, const u64* AQ, const u64* AB, const u64* BQ
                    const u64* side, u64* T3, int L, bool square, cudaStream_t st);
 
 // Exact round(t x / Q) from Q u B residues (coefficient form) -> D[L][3][k][N] mod Q.
+// X[3][k+kb][N] (+)= sum over L layers of the tensor of (A, B) (NTT form over Q u B)
+void launch_tensor_sum(const DevView& V, const u64* AQ, const u64* AB, const u64* BQ, const u64* BB,
+                       const u64* cstQ, const u64* side, u64* X, int L, bool square, bool init, cudaStream_t st);
 void launch_scale_round(const DevView& V, const u64* T3, u64* D, int L, cudaStream_t st);
 
 // RNS-digit relinearisation: D[L][3][k][N] coefficient form, rlk[k][2][k][N] NTT form

@@ -67,6 +67,7 @@ struct pepsi_ctx {
   // scratch, grown on demand
   std::vector<DevBuf> scratch;
   int chunk = 32;
+  u32 rescale_cap = 1;  // most layers one rounding of the last products may cover
   // profiling
   bool prof = false;
   std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> prof_ev;
@@ -268,12 +269,43 @@ cudaError_t eval_bufs(pepsi_ctx* c, int Lc, bool need_pc, EvalBufs* b) {
   return e;
 }
 
-// Arith-CW-Eq (Algorithm 1) on L layers whose h' is in H (NTT form):
-// D <- prod_{i<h}(h' - i) as un-relinearised 3-component ciphertexts
-// (coefficient form); Hc <- h' in coefficient form.
-void eq_circuit(pepsi_ctx* c, EvalBufs& b, int L, cudaStream_t st) {
+// Operands of the last ciphertext product of the equality circuit, for L
+// layers: Q parts in NTT form, B parts in NTT form, the constant added to
+// the second operand's component 0 (Q residues, and its B extension per
+// layer in `side`), and whether both operands are the same.
+struct LastMult {
+  const u64 *AQ = nullptr, *AB = nullptr, *BQ = nullptr, *BB = nullptr, *cQ = nullptr, *side = nullptr;
+  bool square = false;
+  // the same operands from layer `l` of the chunk on
+  LastMult at(const pepsi_ctx* c, int l) const {
+    const size_t qs = (size_t)l * 2 * c->k * c->N, bs = (size_t)l * 2 * c->kb * c->N;
+    LastMult m = *this;
+    m.AQ += qs;
+    m.AB += bs;
+    m.BQ += qs;
+    m.BB += bs;
+    if (m.side) m.side += (size_t)l * c->kb;
+    return m;
+  }
+};
+
+// Arith-CW-Eq (Algorithm 1) on L layers whose h' is in H (NTT form), up to
+// its last ciphertext product, whose operands are returned (h >= 2).  For
+// h = 1 there is no product: D <- h' directly.  Hc <- h' in coefficient form.
+LastMult eq_circuit_front(pepsi_ctx* c, EvalBufs& b, int L, cudaStream_t st) {
   const size_t k = c->k, N = c->N;
   const size_t ct2 = 2 * k * N;
+  LastMult m;
+  auto last = [&](const u64* AQ, const u64* AB, const u64* BQ, const u64* BB, const u64* cQ, const u64* side,
+                  bool square) {
+    m.AQ = AQ;
+    m.AB = AB;
+    m.BQ = BQ;
+    m.BB = BB;
+    m.cQ = cQ;
+    m.side = side;
+    m.square = square;
+  };
   switch (c->h) {
     case 1: {
       ntt(c, false, b.H, b.Hc, (size_t)L * 2, c->k, 0, k * N, k * N, st);
@@ -285,7 +317,7 @@ void eq_circuit(pepsi_ctx* c, EvalBufs& b, int L, cudaStream_t st) {
     }
     case 2: {  // E = Mult(h', h' - 1)
       extend(c, b.H, b.Hc, b.XB, L, cst(c, CS_D_TM1), b.side, st);
-      mult_tail(c, b.H, b.XB, b.H, b.XB, cst(c, CS_D_TM1), b.side, false, b.T3, b.D, L, st);
+      last(b.H, b.XB, b.H, b.XB, cst(c, CS_D_TM1), b.side, false);
       break;
     }
     case 4: {  // u = R(h'^2) - 3h';  E = Mult(u, u + 2)
@@ -294,7 +326,7 @@ void eq_circuit(pepsi_ctx* c, EvalBufs& b, int L, cudaStream_t st) {
       relin(c, b.D, b.R, L, st);
       axpy(c, b.R, cst(c, CS_M3), b.H, b.U, (size_t)L * 2, st);
       extend(c, b.U, b.X, b.YB, L, cst(c, CS_D_2), b.side, st);
-      mult_tail(c, b.U, b.YB, b.U, b.YB, cst(c, CS_D_2), b.side, false, b.T3, b.D, L, st);
+      last(b.U, b.YB, b.U, b.YB, cst(c, CS_D_2), b.side, false);
       break;
     }
     case 8: {  // u = R(h'^2) - 7h'; w = R(u^2); E = Mult(w + 12u, w + 16u + 60)
@@ -309,10 +341,69 @@ void eq_circuit(pepsi_ctx* c, EvalBufs& b, int L, cudaStream_t st) {
       axpy(c, b.W, cst(c, CS_P16), b.U, b.Y, (size_t)L * 2, st);
       extend(c, b.X, b.R, b.XB, L, nullptr, nullptr, st);
       extend(c, b.Y, b.U, b.YB, L, cst(c, CS_D_60), b.side, st);
-      mult_tail(c, b.X, b.XB, b.Y, b.YB, cst(c, CS_D_60), b.side, false, b.T3, b.D, L, st);
+      last(b.X, b.XB, b.Y, b.YB, cst(c, CS_D_60), b.side, false);
       break;
     }
   }
+  return m;
+}
+
+// The whole circuit with per-layer rounding: D <- prod_{i<h}(h' - i) as
+// un-relinearised 3-component ciphertexts (coefficient form).
+void eq_circuit(pepsi_ctx* c, EvalBufs& b, int L, cudaStream_t st) {
+  const LastMult m = eq_circuit_front(c, b, L, st);
+  if (m.AQ) mult_tail(c, m.AQ, m.AB, m.BQ, m.BB, m.cQ, m.side, m.square, b.T3, b.D, L, st);
+}
+
+// Lazy rescaling state of one request: runs of G layers (counted from the
+// first evaluated layer) share one rounding.  X holds the running sum of
+// the run's exact products (NTT form over Q u B), acc the mod-Q layer sum.
+struct LazyRun {
+  u64* X;
+  u64* acc;
+  u32 G;
+  u32 pos = 0;           // layers consumed so far
+  bool acc_init = true;  // acc not yet written
+};
+
+// Round the completed run in X into acc: inverse NTT over Q u B, exact
+// round(t x / Q), accumulate (D serves as one layer of scratch).
+void lazy_flush(pepsi_ctx* c, EvalBufs& b, LazyRun& r, cudaStream_t st) {
+  const int np = c->k + c->kb;
+  const size_t npN = (size_t)np * c->N;
+  ntt(c, false, r.X, r.X, 3, np, 0, npN, npN, st);
+  {
+    Prof p(c, PC_SCALE, st);
+    launch_scale_round(c->V, r.X, b.D, 1, st);
+  }
+  Prof p(c, PC_POINTWISE, st);
+  launch_accum(c->V, b.D, 1, r.acc, r.acc_init, st);
+  r.acc_init = false;
+}
+
+// Add the last products of the chunk's L layers to the run sums, rounding
+// each run as it completes (and the final partial run when `end`).
+void lazy_chunk(pepsi_ctx* c, EvalBufs& b, const LastMult& m, int L, bool end, LazyRun& r, cudaStream_t st) {
+  for (int done = 0; done < L;) {
+    const u32 in_run = r.pos % r.G;
+    const int take = (int)std::min<u32>((u32)(L - done), r.G - in_run);
+    {
+      const LastMult mm = m.at(c, done);
+      Prof p(c, PC_TENSOR, st);
+      launch_tensor_sum(c->V, mm.AQ, mm.AB, mm.BQ, mm.BB, mm.cQ, mm.side, r.X, take, mm.square, in_run == 0, st);
+    }
+    done += take;
+    r.pos += take;
+    if (r.pos % r.G == 0 || (end && done == L)) lazy_flush(c, b, r, st);
+  }
+}
+
+// Run length of the lazy rescaling for an evaluation of nl layers (1: per
+// layer rounding).
+u32 rescale_run(const pepsi_ctx* c, u32 nl) {
+  const u32 g = c->prm.rescale_group;
+  if (g <= 1 || c->h == 1) return 1;
+  return std::max<u32>(1, std::min<u32>(g == PEPSI_RESCALE_ALL ? nl : g, c->rescale_cap));
 }
 
 // Read and clear the device error flag (the stream must be synchronised).
@@ -365,6 +456,9 @@ cudaError_t finish_request(pepsi_ctx* c, EvalBufs& b, const u64* acc, int mode, 
   return copy_any(out, b.out, 2 * kN * 8, st);
 }
 
+// scratch id of the lazy-rescaling run sum of a single request
+constexpr int kScratchAccX = 46;
+
 // Core of pepsi_eval / pepsi_eval_layers.
 int eval_core(pepsi_ctx* c, int set_id, const u64* cts, u32 layer0, u32 nl, int mode, u64 mask_seed, u64* out_ct,
               u64* h_out, u64* e_out, cudaStream_t st) {
@@ -379,6 +473,15 @@ int eval_core(pepsi_ctx* c, int set_id, const u64* cts, u32 layer0, u32 nl, int 
   EvalBufs b;
   cudaError_t e = eval_bufs(c, Lc, res_end < end, &b);
   if (e != cudaSuccess) return cuda_status(e);
+  // per-layer E words are only defined with per-layer rounding
+  const u32 G = e_out ? 1 : rescale_run(c, nl);
+  LazyRun lr{};
+  if (G > 1) {
+    lr.X = (u64*)scratch(c, kScratchAccX, (size_t)3 * (c->k + c->kb) * N * 8, &e);
+    if (!lr.X) return cuda_status(e);
+    lr.acc = b.acc;
+    lr.G = G;
+  }
   CKS(prepare_request(c, cts, b.C, st));
   // a5 on the resident layers: one multiply-accumulate launch over all of
   // them, so the request is read from HBM once
@@ -406,14 +509,17 @@ int eval_core(pepsi_ctx* c, int set_id, const u64* cts, u32 layer0, u32 nl, int 
       Prof p(c, PC_MAC, st);  // a5 on a regenerated chunk
       CKS(mac_status(launch_mac(c->V, b.C, b.Pc, b.H, c->ell, L, c->mac_fold, c->d_err, st)));
     }
-    eq_circuit(c, b, L, st);  // a6
-    // b.Hc holds h' in coefficient form after the circuit
-    if (h_out) CKS(copy_any(h_out + (size_t)(l0 - layer0) * ct2, b.Hc, (size_t)L * ct2 * 8, st));
-    if (e_out) CKS(copy_any(e_out + (size_t)(l0 - layer0) * ct3, b.D, (size_t)L * ct3 * 8, st));
-    {
+    if (G > 1) {  // a6 + a7 with lazy rescaling
+      const LastMult m = eq_circuit_front(c, b, L, st);
+      lazy_chunk(c, b, m, L, l0 + L == end, lr, st);
+    } else {
+      eq_circuit(c, b, L, st);  // a6
+      if (e_out) CKS(copy_any(e_out + (size_t)(l0 - layer0) * ct3, b.D, (size_t)L * ct3 * 8, st));
       Prof p(c, PC_POINTWISE, st);  // a7: layer accumulation
       launch_accum(c->V, b.D, L, b.acc, first, st);
     }
+    // b.Hc holds h' in coefficient form after the circuit
+    if (h_out) CKS(copy_any(h_out + (size_t)(l0 - layer0) * ct2, b.Hc, (size_t)L * ct2 * 8, st));
     first = false;
     l0 += L;
   }
@@ -438,7 +544,7 @@ int eval_core(pepsi_ctx* c, int set_id, const u64* cts, u32 layer0, u32 nl, int 
 // the context's second stream while the circuits of the current group run
 // on the call's stream (double-buffered requests and h'), so the
 // HBM-bound stream of plaintexts overlaps the compute-bound circuits.
-enum { S_CB = 41, S_HB = 42, S_ACCB = 43, S_CB2 = 44, S_HB2 = 45 };
+enum { S_CB = 41, S_HB = 42, S_ACCB = 43, S_CB2 = 44, S_HB2 = 45, S_ACCXB = 47 };
 int eval_batch_core(pepsi_ctx* c, int nq, const int* set_ids, const u64* const* cts, const int* modes,
                     const u64* mask_seeds, u64* const* outs, cudaStream_t st) {
   const size_t k = c->k, N = c->N, kN = k * N, ct2 = 2 * kN, ct3 = 3 * kN;
@@ -488,6 +594,18 @@ int eval_batch_core(pepsi_ctx* c, int nq, const int* set_ids, const u64* const* 
     u64* HB = (u64*)scratch(c, slot ? S_HB2 : S_HB, (size_t)PEPSI_MAC_MAX_REQUESTS * hq * 8, &e);
     u64* ACC = (u64*)scratch(c, S_ACCB, (size_t)PEPSI_MAC_MAX_REQUESTS * ct3 * 8, &e);
     if (!CB || !HB || !ACC) return cuda_status(e);
+    const u32 RG = rescale_run(c, mu);
+    const size_t xw = (size_t)3 * (c->k + c->kb) * N;
+    LazyRun lr[PEPSI_MAC_MAX_REQUESTS];
+    if (RG > 1) {
+      u64* ACCX = (u64*)scratch(c, S_ACCXB, (size_t)PEPSI_MAC_MAX_REQUESTS * xw * 8, &e);
+      if (!ACCX) return cuda_status(e);
+      for (int g = 0; g < G; ++g) {
+        lr[g].X = ACCX + (size_t)g * xw;
+        lr[g].acc = ACC + (size_t)g * ct3;
+        lr[g].G = RG;
+      }
+    }
     if (mres) {
       // requests and multiply-accumulate over the resident layers on the auxiliary
       // stream, once the circuits that last used this slot's buffers are done
@@ -517,6 +635,11 @@ int eval_batch_core(pepsi_ctx* c, int nq, const int* set_ids, const u64* const* 
       }
       for (int g = 0; g < G; ++g) {
         b.H = HB + (size_t)g * hq + (res ? (size_t)l0 * ct2 : 0);
+        if (RG > 1) {
+          const LastMult m = eq_circuit_front(c, b, L, st);
+          lazy_chunk(c, b, m, L, l0 + L == mu, lr[g], st);
+          continue;
+        }
         eq_circuit(c, b, L, st);
         Prof p(c, PC_POINTWISE, st);
         launch_accum(c->V, b.D, L, ACC + (size_t)g * ct3, l0 == 0, st);
@@ -696,8 +819,14 @@ int pepsi_setup(const pepsi_params* params, uint64_t key_seed, pepsi_ctx** out) 
       return PEPSI_E_PARAM;
     }
   }
-  // auxiliary base B: 61-bit primes with log2 B >= log2(t N Q) + 3
-  const double needB = std::log2((double)c->t) + c->logN + lq + 3.0;
+  // lazy rescaling: runs of up to rescale_cap layers share one rounding
+  {
+    const u32 g = params->rescale_group;
+    c->rescale_cap = g <= 1 ? 1 : g != PEPSI_RESCALE_ALL ? g : params->mu ? params->mu : 65536u;
+  }
+  // auxiliary base B: 61-bit primes with log2 B >= log2(t N Q G) + 3, G the
+  // longest run of layers whose exact products are summed before rounding
+  const double needB = std::log2((double)c->t) + c->logN + lq + std::ceil(std::log2((double)c->rescale_cap)) + 3.0;
   double haveB = 0;
   std::vector<u64> taken = c->Q;
   while (haveB < needB) {
@@ -836,6 +965,14 @@ int pepsi_get_info(const pepsi_ctx* c, pepsi_info* info) {
   for (int j = 0; j < c->kb && j < 12; ++j) info->b_primes[j] = c->B[j];
   info->psi_t = c->psi_t;
   info->log2_q = c->log2q;
+  info->rescale_group = c->prm.rescale_group;
+  info->rescale_cap = c->rescale_cap;
+  return PEPSI_OK;
+}
+
+int pepsi_set_rescale_group(pepsi_ctx* c, uint32_t rescale_group) {
+  if (!c) return PEPSI_E_PARAM;
+  c->prm.rescale_group = rescale_group;
   return PEPSI_OK;
 }
 

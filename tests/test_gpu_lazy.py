@@ -1,0 +1,127 @@
+"""Lazy rescaling (pepsi_params.rescale_group) against the oracle's deferred
+rounding, word for word through the C ABI: the last products of runs of G
+consecutive layers are summed exactly and rounded once.  Runs cross layer
+chunks (chunk 4, runs of 3), the resident / regenerated boundary, and the
+requests of a batch; the per-layer debug path keeps per-layer rounding."""
+import math
+import os
+
+import numpy as np
+import pytest
+
+from gpu_helpers import T, brute_indicator, hashed_indicator, pair, torch_cuda
+
+pytestmark = pytest.mark.gpu
+
+TOY = [36, 36, 37]
+PAPER = [55, 55, 54, 54]
+LARGE = [55] * 6 + [54] * 2
+ALL = 0xFFFFFFFF
+
+
+@pytest.fixture(autouse=True)
+def _cuda():
+    torch_cuda()
+
+
+def _case(N, bits, h, lb, group, chunk=4, resident_bytes=0, m=20, n=70, planted=4, seed=5, mu_min=7):
+    import oracle
+    from paper_2310_14565_gb300.workload import make_sets
+
+    sets = make_sets(m, n, planted, bits=32, seed_items=seed, seed_plant=seed + 1)
+    load = oracle.simple_hash(0x5EED, lb, int(math.log2(N)), sets.server, 10 * n + 1)[2]
+    mu = max(mu_min, load)
+    os.environ["PEPSI_CHUNK"] = str(chunk)
+    try:
+        oc, gc, s, rlk = pair(N, bits, h, lb, mu=mu, resident_bytes=resident_bytes, rescale_group=group)
+    finally:
+        os.environ.pop("PEPSI_CHUNK", None)
+    rc, Ts, _ = oc.server_table(sets.server)
+    assert rc == 0
+    sid = gc.server_load(sets.server)
+    cts, where = gc.query(sets.client, 4)
+    return oc, gc, s, rlk, sets, Ts, cts, where, sid, mu
+
+
+def _run(group, mu, cap):
+    g = mu if group == ALL else group
+    return min(g, cap)
+
+
+@pytest.mark.parametrize("group", [3, ALL])
+@pytest.mark.parametrize("h,bits,lb", [(2, TOY, 8), (4, PAPER, 10), (8, LARGE, 12)])
+def test_lazy_eval_matches_oracle(h, bits, lb, group):
+    oc, gc, s, rlk, sets, Ts, cts, where, sid, mu = _case(64, bits, h, lb, group)
+    assert gc.rescale_cap == (3 if group == 3 else mu)
+    G = _run(group, mu, gc.rescale_cap)
+    hashed = hashed_indicator(sets.client, sets.server, where, 64, lb)
+    for mode in (0, 1):
+        want = oc.eval(rlk, cts, Ts, mode=mode, mask_seed=5, group=G)
+        got = gc.eval(sid, cts, mode=mode, mask_seed=5)
+        assert np.array_equal(got, want), mode
+        slots, b = gc.decrypt(got)
+        assert b > 0
+        if mode == 0:
+            assert np.array_equal(slots, hashed)
+        else:
+            assert int(slots.astype(np.int64).sum()) % T == int(hashed.sum())
+
+
+def test_lazy_run_longer_than_cap_is_cut():
+    """rescale_group = 5 with setup cap 5, then ALL: runs stay at 5 layers."""
+    oc, gc, s, rlk, sets, Ts, cts, where, sid, mu = _case(64, PAPER, 4, 10, 5, chunk=3, mu_min=12)
+    assert gc.rescale_cap == 5 and mu > 5
+    want = oc.eval(rlk, cts, Ts, group=5)
+    assert np.array_equal(gc.eval(sid, cts), want)
+    gc.set_rescale_group(ALL)
+    assert np.array_equal(gc.eval(sid, cts), want)
+    gc.set_rescale_group(2)
+    assert np.array_equal(gc.eval(sid, cts), oc.eval(rlk, cts, Ts, group=2))
+    gc.set_rescale_group(1)
+    assert np.array_equal(gc.eval(sid, cts), oc.eval(rlk, cts, Ts))
+
+
+@pytest.mark.parametrize("resident_layers", [0, 4])
+def test_lazy_streamed_and_partially_resident(resident_layers):
+    N, bits, h, lb = 64, PAPER, 4, 10
+    per_layer = None
+    import paper_2310_14565_gb300 as pepsi
+
+    probe = pepsi.Context(N=N, prime_bits=bits, h=h, lambda_bar=lb, mu=8)
+    per_layer = probe.ell * probe.k * N * 8
+    del probe
+    budget = (1 << 64) - 1 if resident_layers == 0 else resident_layers * per_layer
+    oc, gc, s, rlk, sets, Ts, cts, where, sid, mu = _case(N, bits, h, lb, 3, chunk=3, resident_bytes=budget)
+    assert mu > resident_layers + 2
+    want = oc.eval(rlk, cts, Ts, group=3)
+    assert np.array_equal(gc.eval(sid, cts), want)
+
+
+def test_lazy_batch_matches_single_and_oracle():
+    oc, gc, s, rlk, sets, Ts, cts, where, sid, mu = _case(64, PAPER, 4, 10, ALL, chunk=3)
+    cts2, _ = gc.query(sets.client[::-1].copy(), 9)
+    outs = gc.eval_batch([sid, sid, sid], [cts, cts2, cts], [0, 1, 0], [5, 6, 7])
+    assert np.array_equal(outs[0], gc.eval(sid, cts))
+    assert np.array_equal(outs[1], gc.eval(sid, cts2, mode=1, mask_seed=6))
+    assert np.array_equal(outs[2], outs[0])
+    assert np.array_equal(outs[0], oc.eval(rlk, cts, Ts, group=mu))
+    assert np.array_equal(outs[1], oc.eval(rlk, cts2, Ts, mode=1, mask_seed=6, group=mu))
+
+
+def test_lazy_context_eval_layers_rounds_per_layer():
+    oc, gc, s, rlk, sets, Ts, cts, where, sid, mu = _case(64, LARGE, 8, 12, ALL)
+    _, dh, de = oc.eval(rlk, cts, Ts, layer0=1, nlayers=3, debug=True)
+    gh, ge = gc.eval_layers(sid, cts, 1, 3)
+    assert np.array_equal(gh, dh) and np.array_equal(ge, de)
+
+
+def test_lazy_toy_size_full_parity():
+    """N = 4096, three primes, h = 2, ell = 363, one rounding for all layers."""
+    oc, gc, s, rlk, sets, Ts, cts, where, sid, mu = _case(4096, TOY, 2, 16, ALL, chunk=32, m=64, n=1024,
+                                                          planted=16, seed=1, mu_min=16)
+    want = oc.eval(rlk, cts, Ts, group=mu)
+    got = gc.eval(sid, cts)
+    assert np.array_equal(got, want)
+    slots, b = gc.decrypt(got)
+    assert b > 0
+    assert np.array_equal(slots, brute_indicator(sets.client, sets.server, where, 4096))

@@ -119,7 +119,7 @@ def test_ct_mult_and_relin_match_oracle(N, bits):
 
 
 # -------------------------------------------------------------- evaluation
-def _psi_case(N, bits, h, lb, mu, m, n, planted, chunk=None, seed=5):
+def _psi_case(N, bits, h, lb, mu, m, n, planted, chunk=None, seed=5, **ctx_kw):
     """A PSI instance; mu is raised to the actual maximum bin load."""
     import oracle
     from paper_2310_14565_gb300.workload import make_sets
@@ -130,7 +130,7 @@ def _psi_case(N, bits, h, lb, mu, m, n, planted, chunk=None, seed=5):
     if chunk:
         os.environ["PEPSI_CHUNK"] = str(chunk)
     try:
-        oc, gc, s, rlk = pair(N, bits, h, lb, mu=mu)
+        oc, gc, s, rlk = pair(N, bits, h, lb, mu=mu, **ctx_kw)
     finally:
         os.environ.pop("PEPSI_CHUNK", None)
     rc, Ts, _ = oc.server_table(sets.server)

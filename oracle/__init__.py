@@ -112,8 +112,10 @@ def lib():
         L.or_relin.argtypes = [C.c_void_p, u64p, u64p, u64p]
         L.or_server_plaintext.argtypes = [C.c_void_p, u64p, C.c_uint32, C.c_uint32, C.c_uint32, C.c_uint32, u64p]
         L.or_query_plaintexts.argtypes = [C.c_void_p, u64p, C.c_uint32, C.c_uint32, u32p]
-        L.or_ct_mult_sum.argtypes = [C.c_void_p, u64p, u64p, C.c_uint32, u64p]
-        L.or_eval.argtypes = [C.c_void_p, u64p, u64p, C.c_uint32, C.c_uint32, u64p, C.c_uint32,
+        L.or_ct_mult_sum.argtypes = [C.c_void_p, u64p, u64p, C.c_void_p, C.c_uint32, u64p]
+        L.or_simple_hash_values.argtypes = [C.c_uint64, C.c_uint32, C.c_uint32, u64p, u32p, C.c_uint64,
+                                            C.c_uint32, u64p, u32p, C.POINTER(C.c_uint32)]
+        L.or_eval.argtypes = [C.c_void_p, u64p, u64p, C.c_uint32, C.c_uint32, u64p, C.c_void_p, C.c_uint32,
                               C.c_uint32, C.c_uint32, C.c_int, C.c_uint64, C.c_uint32, u64p, C.c_void_p,
                               C.c_void_p, C.c_void_p, u64p]
         L.or_set_threads.argtypes = [C.c_int]
@@ -234,6 +236,19 @@ PAPER_MU = {  # (n, b) -> mu, Tables 5, 6 and 7
 }
 
 
+def simple_hash_values(hash_key, lambda_bar, logb, items, values, mu):
+    """Server table plus the value of the item stored at each (layer, bin)."""
+    items = np.ascontiguousarray(items, dtype=np.uint64)
+    values = np.ascontiguousarray(values, dtype=np.uint32)
+    T = np.zeros((mu, 1 << logb), dtype=np.uint64)
+    V = np.zeros((mu, 1 << logb), dtype=np.uint32)
+    load = C.c_uint32(0)
+    rc = lib().or_simple_hash_values(hash_key, lambda_bar, logb, items if len(items) else np.zeros(1, np.uint64),
+                                     values if len(values) else np.zeros(1, np.uint32), len(items), mu, T, V,
+                                     C.byref(load))
+    return rc, T, V, int(load.value)
+
+
 def mu_bound(n: int, b: int) -> int:
     """Server maximum bin load: the paper's value for its own (n, b) pairs,
     else smallest mu with b * P[Binomial(3n, 1/b) > mu] <= 2^-40."""
@@ -350,13 +365,15 @@ class Ctx:
         assert rc == 0
         return out
 
-    def ct_mult_sum(self, a, b):
-        """round(t/Q * sum_i a_i (x) b_i) mod Q with one rounding; a, b:
-        [n][2][k][N]."""
+    def ct_mult_sum(self, a, b, v=None):
+        """round(t/Q * sum_i v_i (x) a_i (x) b_i) mod Q with one rounding;
+        a, b: [n][2][k][N]; v: [n][N] plaintext coefficients in [0, t)
+        (centred lift) or None."""
         a = np.ascontiguousarray(a, np.uint64)
         b = np.ascontiguousarray(b, np.uint64)
+        vv = None if v is None else np.ascontiguousarray(v, np.uint32)
         out = np.zeros((3, self.k, self.N), np.uint64)
-        rc = lib().or_ct_mult_sum(self._p, a, b, a.shape[0], out)
+        rc = lib().or_ct_mult_sum(self._p, a, b, None if vv is None else vv.ctypes.data, a.shape[0], out)
         assert rc == 0
         return out
 
@@ -371,6 +388,10 @@ class Ctx:
 
     def server_table(self, items, mu=None):
         return simple_hash(self.hash_key, self.lambda_bar, self.logb, items, mu or self.mu)
+
+    def server_table_values(self, items, values, mu=None):
+        """(rc, T [mu][N], V [mu][N] values of the stored items, max load)."""
+        return simple_hash_values(self.hash_key, self.lambda_bar, self.logb, items, values, mu or self.mu)
 
     def server_plaintext(self, T, layer, j):
         out = np.zeros((self.k, self.N), np.uint64)
@@ -391,12 +412,14 @@ class Ctx:
         m = self.query_plaintexts(table)
         return 0, self.encrypt(s, m, enc_seed), where
 
-    def eval(self, rlk, cts, T, mode=0, mask_seed=0, layer0=0, nlayers=None, debug=False, group=1, acc=False):
+    def eval(self, rlk, cts, T, mode=0, mask_seed=0, layer0=0, nlayers=None, debug=False, group=1, acc=False,
+             V=None):
         """Alg 2 over layers [layer0, layer0+nlayers).  Returns the result
         ciphertext [2][k][N] and, with debug, per-layer h' and E words (E
         only when group <= 1); with acc, also the layer sum before
         relinearisation [3][k][N].  group > 1 rounds the last product of
-        runs of `group` consecutive layers once (lazy rescaling)."""
+        runs of `group` consecutive layers once (lazy rescaling).  Modes 2
+        (labelled PSI) and 3 (PSI-Sum) need the value table V [mu][N]."""
         mu = T.shape[0]
         nl = mu - layer0 if nlayers is None else nlayers
         lazy = group > 1 and self.h > 1
@@ -406,8 +429,9 @@ class Ctx:
         de = np.zeros((nl, 3, self.k, self.N), np.uint64) if debug and not lazy else None
         da = np.zeros((3, self.k, self.N), np.uint64) if acc else None
         rc = lib().or_eval(self._p, np.ascontiguousarray(rlk, np.uint64), np.ascontiguousarray(cts, np.uint64),
-                           self.ell, self.h, np.ascontiguousarray(T, np.uint64), mu, layer0, nl, mode, mask_seed,
-                           group, out, dh.ctypes.data if debug else None,
+                           self.ell, self.h, np.ascontiguousarray(T, np.uint64),
+                           None if V is None else np.ascontiguousarray(V, np.uint32).ctypes.data, mu, layer0, nl,
+                           mode, mask_seed, group, out, dh.ctypes.data if debug else None,
                            de.ctypes.data if de is not None else None, da.ctypes.data if acc else None, counts)
         if rc:
             raise RuntimeError("oracle eval failed: %d" % rc)

@@ -465,8 +465,10 @@ or_ctx* or_create(u32 N, u64 t, u32 k, const unsigned char* bits) {
     for (u32 j = 0; j < k; j++) c->invq[i * k + j] = (i == j) ? 1 : invmod(c->q[j] % c->q[i], c->q[i]);
   /* auxiliary primes: product must exceed 4 * G * N * Q^2 (two products of
    * centred values summed, both signs, over up to G = OR_MAX_GROUP layers
-   * when the rounding is deferred to the group) */
-  double need = log2((double)N) + 2.0 * bn_log2(&c->Q) + 3.0 + log2((double)OR_MAX_GROUP), have = 0;
+   * when the rounding is deferred to the group), times N * t / 2 for the
+   * product with a value plaintext (centred coefficients, |v| <= t/2) */
+  double need = log2((double)N) + 2.0 * bn_log2(&c->Q) + 3.0 + log2((double)OR_MAX_GROUP) +
+                log2((double)N * (double)t), have = 0;
   c->na = 0;
   while (have < need) {
     if (c->na >= OR_MAXA) { or_free(c); return NULL; }
@@ -633,11 +635,21 @@ static int cmp_arrival(const void* a, const void* b) {
   if (x->xl != y->xl) return x->xl < y->xl ? -1 : 1;
   return x->pos < y->pos ? -1 : (x->pos > y->pos);
 }
+int or_simple_hash_values(u64 hash_key, u32 lambda_bar, u32 logb, const u64* items, const u32* values, u64 n,
+                          u32 mu, u64* T, u32* V, u32* max_load);
 int or_simple_hash(u64 hash_key, u32 lambda_bar, u32 logb, const u64* items, u64 n, u32 mu, u64* T, u32* max_load) {
+  return or_simple_hash_values(hash_key, lambda_bar, logb, items, NULL, n, mu, T, NULL, max_load);
+}
+/* The same table plus V[mu][b]: the value of the item stored at each
+ * (layer, bin) (labelled PSI / PSI-Sum, Algorithms 4-5), 0 for dummies.
+ * values may be NULL (then V is all zero); V may be NULL. */
+int or_simple_hash_values(u64 hash_key, u32 lambda_bar, u32 logb, const u64* items, const u32* values, u64 n,
+                          u32 mu, u64* T, u32* V, u32* max_load) {
   u32 b = 1u << logb;
   u64 cap = 3 * n + 1;
   u32* abin = (u32*)malloc(sizeof(u32) * cap);
   u64* axl = (u64*)malloc(sizeof(u64) * cap);
+  u64* aown = (u64*)malloc(sizeof(u64) * cap); /* item of each arrival */
   u64 na = 0;
   for (u64 u = 0; u < n; u++) {
     u64 xL;
@@ -649,6 +661,7 @@ int or_simple_hash(u64 hash_key, u32 lambda_bar, u32 logb, const u64* items, u64
       if (dup_bin) continue;
       abin[na] = bins[i];
       axl[na] = xL;
+      aown[na] = u;
       na++;
     }
   }
@@ -661,6 +674,7 @@ int or_simple_hash(u64 hash_key, u32 lambda_bar, u32 logb, const u64* items, u64
   u64* order = (u64*)malloc(sizeof(u64) * (na ? na : 1));
   for (u64 e = 0; e < na; e++) order[fill[abin[e]]++] = e;
   for (u64 i = 0; i < (u64)mu * b; i++) T[i] = OR_DUMMY;
+  if (V) memset(V, 0, sizeof(u32) * (u64)mu * b);
   u32 mx = 0;
   or_arrival* tmp = (or_arrival*)malloc(sizeof(or_arrival) * (na ? na : 1));
   char* dup = (char*)calloc(na ? na : 1, 1);
@@ -676,13 +690,16 @@ int or_simple_hash(u64 hash_key, u32 lambda_bar, u32 logb, const u64* items, u64
     u32 layer = 0;
     for (u64 r = 0; r < len; r++) {
       if (dup[s0 + r]) continue;
-      if (layer < mu) T[(u64)layer * b + bin] = axl[order[s0 + r]];
+      if (layer < mu) {
+        T[(u64)layer * b + bin] = axl[order[s0 + r]];
+        if (V && values) V[(u64)layer * b + bin] = values[aown[order[s0 + r]]];
+      }
       layer++;
     }
     if (layer > mx) mx = layer;
   }
   if (max_load) *max_load = mx;
-  free(abin); free(axl); free(start); free(fill); free(order); free(tmp); free(dup);
+  free(abin); free(axl); free(aown); free(start); free(fill); free(order); free(tmp); free(dup);
   return mx > mu ? OR_E_BIN_OVERFLOW : OR_OK;
 }
 
@@ -923,6 +940,22 @@ static void ct_round_aux(const or_ctx* c, const u64* T, u64* out) {
       for (u32 p = 0; p < k; p++) out[((u64)comp * k + p) * N + n] = sbn_mod_u64(&y, c->q[p]);
     }
 }
+/* X[3][na][N] <- X (x) v for the plaintext v (coefficients in [0, t),
+ * centred lift), exactly over the integers (residues mod the aux primes). */
+static void aux_mul_plain(const or_ctx* c, u64* X, const u32* v) {
+  u32 N = c->N, na = c->na;
+  u64 *vl = (u64*)malloc(sizeof(u64) * N), *prod = (u64*)malloc(sizeof(u64) * N), *tmp = (u64*)malloc(sizeof(u64) * N);
+  for (u32 j = 0; j < na; j++) {
+    u64 qa = c->qa[j];
+    for (u32 n = 0; n < N; n++) vl[n] = v[n] <= c->t / 2 ? v[n] : qa - (c->t - v[n]);
+    for (u32 comp = 0; comp < 3; comp++) {
+      u64* x = X + ((u64)comp * na + j) * N;
+      ring_mul(x, vl, prod, N, &c->ta[j], tmp);
+      memcpy(x, prod, sizeof(u64) * N);
+    }
+  }
+  free(vl); free(prod); free(tmp);
+}
 int or_ct_mult(const or_ctx* c, const u64* a, const u64* b, u64* out) {
   u64* T = (u64*)calloc((u64)3 * c->na * c->N, sizeof(u64));
   if (!T) return OR_E_NOMEM;
@@ -932,17 +965,30 @@ int or_ct_mult(const or_ctx* c, const u64* a, const u64* b, u64* out) {
   return rc;
 }
 /* Deferred rounding over n products (lazy rescaling of a sum of products):
- * out = round(t/Q * sum_i a_i (x) b_i) mod Q, one rounding of the sum of
- * the exact integer tensors.  a, b: [n][2][k][N]; 1 <= n <= OR_MAX_GROUP. */
-int or_ct_mult_sum(const or_ctx* c, const u64* a, const u64* b, u32 n, u64* out) {
+ * out = round(t/Q * sum_i v_i (x) a_i (x) b_i) mod Q, one rounding of the
+ * sum of the exact integer tensors, each times the centred lift of the
+ * plaintext v_i[N] (coefficients in [0, t)) when v is not NULL.
+ * a, b: [n][2][k][N]; v: [n][N] or NULL; 1 <= n <= OR_MAX_GROUP. */
+int or_ct_mult_sum(const or_ctx* c, const u64* a, const u64* b, const u32* v, u32 n, u64* out) {
   if (n == 0 || n > OR_MAX_GROUP) return OR_E_PARAM;
-  u64 ct2 = 2ULL * c->k * c->N;
-  u64* T = (u64*)calloc((u64)3 * c->na * c->N, sizeof(u64));
-  if (!T) return OR_E_NOMEM;
+  u64 ct2 = 2ULL * c->k * c->N, tx = 3ULL * c->na * c->N;
+  u64* T = (u64*)calloc(tx, sizeof(u64));
+  u64* X = (u64*)malloc(sizeof(u64) * tx);
+  if (!T || !X) { free(T); free(X); return OR_E_NOMEM; }
   int rc = 0;
-  for (u32 i = 0; i < n && !rc; i++) rc = ct_tensor_aux(c, a + i * ct2, b + i * ct2, T);
+  for (u32 i = 0; i < n && !rc; i++) {
+    memset(X, 0, sizeof(u64) * tx);
+    rc = ct_tensor_aux(c, a + i * ct2, b + i * ct2, X);
+    if (v) aux_mul_plain(c, X, v + (u64)i * c->N);
+    for (u32 comp = 0; comp < 3; comp++)
+      for (u32 j = 0; j < c->na; j++)
+        for (u32 m = 0; m < c->N; m++) {
+          u64 e = ((u64)comp * c->na + j) * c->N + m;
+          T[e] = addmod(T[e], X[e], c->qa[j]);
+        }
+  }
   if (!rc) ct_round_aux(c, T, out);
-  free(T);
+  free(T); free(X);
   return rc;
 }
 /* Relinearisation with RNS digits (no special prime): d_i = [d2]_{q_i} in
@@ -1082,6 +1128,10 @@ static i64 inv_hfact(const or_ctx* c, u32 h) {
  *   A = sum_{i'} E_{i'};  ct = (h!)^-1 * R(A);
  *   mode 1 (cardinality, Alg 5 with val = 1): ct += (round(Q*Encode(r)/t), 0)
  *   with r uniform in Z_t^N, r_{N-1} = -sum of the others.
+ *   mode 2 (labelled PSI, Alg 4): A = sum_{i'} val_s[i'] * E_{i'}, where
+ *   val_s[i'] = Encode(V[i'][.]) (centred lift) holds the value of the
+ *   item stored in each bin of layer i'.
+ *   mode 3 (PSI-Sum, Alg 5): as mode 2, plus the mask of mode 1.
  * cts: [ell][2][k][N] coefficient form.  T: server table [mu][N].
  * dbg_h: [nl][2][k][N] h' (coefficient form), dbg_e: [nl][3][k][N] E.
  * dbg_acc: [3][k][N] the layer sum A before relinearisation.
@@ -1091,14 +1141,20 @@ static i64 inv_hfact(const or_ctx* c, u32 h) {
  * the layers, from layer0 on, into runs of G consecutive layers; the exact
  * integer tensors of a run's last Mults are summed and rounded once,
  * round(t/Q * sum X_{i'}), and the runs' results are summed mod Q into A.
- * Per-layer E words do not exist then, so dbg_e must be NULL.
+ * Per-layer E words do not exist then, so dbg_e must be NULL.  In modes 2
+ * and 3 a run sums val_s[i'] (x) X_{i'} (the value product taken before
+ * the run's rounding); with group <= 1 val_s[i'] multiplies the rounded
+ * E_{i'}, as Algorithms 4-5 write it.
  * The plaintext-times-ciphertext sums are accumulated in the NTT domain
  * and transformed back once per layer (the inverse NTT is linear). */
-int or_eval(const or_ctx* c, const u64* rlk, const u64* cts, u32 ell, u32 h, const u64* T, u32 mu, u32 layer0,
-            u32 nl, int mode, u64 mask_seed, u32 group, u64* out, u64* dbg_h, u64* dbg_e, u64* dbg_acc,
-            u64* counts) {
+int or_eval(const or_ctx* c, const u64* rlk, const u64* cts, u32 ell, u32 h, const u64* T, const u32* V, u32 mu,
+            u32 layer0, u32 nl, int mode, u64 mask_seed, u32 group, u64* out, u64* dbg_h, u64* dbg_e,
+            u64* dbg_acc, u64* counts) {
   u32 N = c->N, k = c->k;
   if (layer0 + nl > mu || (h != 1 && h != 2 && h != 4 && h != 8)) return OR_E_PARAM;
+  if (mode < 0 || mode > 3) return OR_E_PARAM;
+  const int valued = mode >= 2;
+  if (valued && !V) return OR_E_PARAM;
   if (group > OR_MAX_GROUP) return OR_E_PARAM;
   const int lazy = group > 1 && h > 1;
   if (lazy && dbg_e) return OR_E_PARAM;
@@ -1148,6 +1204,24 @@ int or_eval(const or_ctx* c, const u64* rlk, const u64* cts, u32 ell, u32 h, con
       rc |= eq_circuit(c, rlk, h, hp, NULL, Eall + (u64)li * ctx, &nm);
     else
       rc |= eq_circuit(c, rlk, h, hp, Eall + (u64)li * ct3, NULL, &nm);
+    if (valued) { /* val_s[layer] (Alg 4 / 5) */
+      or_encode(c, V + (u64)layer * N, mt);
+      if (lazy) {
+        aux_mul_plain(c, Eall + (u64)li * ctx, mt);
+      } else {
+        u64* E = Eall + (u64)li * ct3;
+        u64* pl = (u64*)malloc(sizeof(u64) * k * N);
+        u64 *prod = (u64*)malloc(sizeof(u64) * N), *tmp = (u64*)malloc(sizeof(u64) * N);
+        or_pt_lift(c, mt, pl);
+        for (u32 comp = 0; comp < 3; comp++)
+          for (u32 p = 0; p < k; p++) {
+            u64* e = E + ((u64)comp * k + p) * N;
+            ring_mul(e, pl + (u64)p * N, prod, N, &c->tq[p], tmp);
+            memcpy(e, prod, sizeof(u64) * N);
+          }
+        free(pl); free(prod); free(tmp);
+      }
+    }
     mm += nm;
     if (dbg_e) memcpy(dbg_e + (u64)li * ct3, Eall + (u64)li * ct3, sizeof(u64) * ct3);
     free(acc); free(pt); free(hp); free(sl); free(mt); free(pos);
@@ -1190,7 +1264,7 @@ int or_eval(const or_ctx* c, const u64* rlk, const u64* cts, u32 ell, u32 h, con
   if (dbg_acc) memcpy(dbg_acc, A, sizeof(u64) * ct3);
   or_relin(c, rlk, A, out);
   or_ct_scale(c, out, inv_hfact(c, h), 2);
-  if (mode == 1) {
+  if (mode == 1 || mode == 3) {
     u32 *r = (u32*)malloc(sizeof(u32) * N), *mr = (u32*)malloc(sizeof(u32) * N);
     u64 sum = 0;
     for (u32 s = 0; s + 1 < N; s++) {

@@ -561,3 +561,102 @@ def test_lazy_rescale_psi_matches_hashed_brute_force(oracle_mod, h, bits, lb):
         assert int(slots_c.astype(np.int64).sum()) % T == int(hashed.sum())
     _, b1 = c.decrypt(s, c.eval(rlk, cts, Ts))
     assert budgets[-1] >= b1 - 1.0  # fewer roundings: no worse noise
+
+
+# ------------------------------------------- labelled PSI and PSI-Sum
+def test_mult_sum_with_values_against_big_integer_schoolbook(oracle_mod):
+    # round(t/Q * sum_i v~_i (x) a~_i (x) b~_i), v~ the centred lift of a
+    # plaintext, exact integers
+    c = oracle_mod.Ctx(N=8, t=T, prime_bits=[36, 37], h=1, lambda_bar=3)
+    s, _ = c.keygen(5)
+    rng = np.random.default_rng(8)
+    n = 2
+    ca = np.stack([c.encrypt(s, c.encode(rand_slots(rng, 8)), 30 + i)[0] for i in range(n)])
+    cb = np.stack([c.encrypt(s, c.encode(rand_slots(rng, 8)), 40 + i)[0] for i in range(n)])
+    v = rng.integers(0, T, size=(n, 8)).astype(np.uint32)
+    Q, N = c.Q, c.N
+
+    def lift(ct, comp):
+        w = [int(sympy_crt(c.q, [int(ct[comp, p, m]) for p in range(c.k)])[0]) for m in range(N)]
+        return [x - Q if x > Q // 2 else x for x in w]
+
+    X = [[0] * N for _ in range(3)]
+    for i in range(n):
+        a0, a1, b0, b1 = lift(ca[i], 0), lift(ca[i], 1), lift(cb[i], 0), lift(cb[i], 1)
+        vi = [int(x) if x <= T // 2 else int(x) - T for x in v[i]]
+        terms = (negacyclic_schoolbook(a0, b0, N),
+                 [u + w for u, w in zip(negacyclic_schoolbook(a0, b1, N), negacyclic_schoolbook(a1, b0, N))],
+                 negacyclic_schoolbook(a1, b1, N))
+        for comp in range(3):
+            X[comp] = [u + w for u, w in zip(X[comp], negacyclic_schoolbook(terms[comp], vi, N))]
+    got = c.ct_mult_sum(ca, cb, v)
+    for comp in range(3):
+        for m in range(N):
+            y = (T * X[comp][m] + (Q - 1) // 2) // Q
+            for p, q in enumerate(c.q):
+                assert int(got[comp, p, m]) == y % q
+
+
+def test_value_table_brute_force(oracle_mod):
+    from paper_2310_14565_gb300.workload import make_sets
+
+    lb, logb = 6, 4
+    items = make_sets(4, 90, 2, bits=32, seed_items=3, seed_plant=4).server
+    values = (np.arange(len(items), dtype=np.uint32) * 7919 + 1) % T
+    rc, Tt, V, load = oracle_mod.simple_hash_values(7, lb, logb, items, values, 40)
+    assert rc == 0
+    rc2, T2, _ = oracle_mod.simple_hash(7, lb, logb, items, 40)
+    assert np.array_equal(Tt, T2)
+    hashed = [oracle_mod.hash_item(7, lb, logb, int(x)) for x in items]
+    for layer in range(Tt.shape[0]):
+        for b in range(1 << logb):
+            if Tt[layer, b] == oracle_mod.DUMMY:
+                assert V[layer, b] == 0
+                continue
+            # the first item (input order) with this x_L among those mapping to bin b
+            owner = next(u for u, (xl, bins) in enumerate(hashed) if xl == int(Tt[layer, b]) and b in bins)
+            assert V[layer, b] == values[owner]
+
+
+def _valued_case(oracle_mod, h, bits, lb, seed):
+    from paper_2310_14565_gb300.workload import make_sets
+
+    N = 64
+    sets = make_sets(24, 150, 7, bits=32, seed_items=seed, seed_plant=seed + 1)
+    values = np.random.default_rng(seed).integers(1, T, size=150).astype(np.uint32)
+    load = oracle_mod.simple_hash(99, lb, 6, sets.server, 1000)[2]
+    c = oracle_mod.Ctx(N=N, t=T, prime_bits=bits, h=h, lambda_bar=lb, hash_key=99, mu=max(7, load))
+    s, rlk = c.keygen(3)
+    rc, Ts, V, _ = c.server_table_values(sets.server, values)
+    assert rc == 0
+    rc, cts, where = c.query(s, sets.client, 4)
+    assert rc == 0
+    # expected label per client slot: the value stored with the matching x_L in its bin (hashed domain)
+    labels = np.zeros(N, np.uint32)
+    for u, x in enumerate(sets.client):
+        xl, _ = oracle_mod.hash_item(99, lb, 6, x)
+        col = Ts[:, where[u]]
+        hit = np.nonzero(col == xl)[0]
+        if hit.size:
+            labels[where[u]] = V[hit[0], where[u]]
+    return c, s, rlk, sets, Ts, V, cts, where, labels
+
+
+@pytest.mark.parametrize("h,bits,lb", [(1, [36, 37], 8), (2, [36, 36, 37], 10), (4, [55, 55, 54, 54], 12),
+                                       (8, [55] * 6 + [54] * 2, 14)])
+def test_labelled_psi_and_psi_sum(oracle_mod, h, bits, lb):
+    c, s, rlk, sets, Ts, V, cts, where, labels = _valued_case(oracle_mod, h, bits, lb, seed=h + 20)
+    assert int((labels != 0).sum()) >= len(sets.planted)
+    for group in (1, Ts.shape[0]):
+        out = c.eval(rlk, cts, Ts, mode=2, V=V, group=group)
+        slots, bud = c.decrypt(s, out)
+        assert bud > 0 and np.array_equal(slots, labels), group  # Algorithm 4
+        outs = c.eval(rlk, cts, Ts, mode=3, mask_seed=5, V=V, group=group)
+        ss, bud = c.decrypt(s, outs)
+        assert bud > 0
+        assert int(ss.astype(np.int64).sum()) % T == int(labels.astype(np.int64).sum()) % T  # Algorithm 5
+        assert not np.array_equal(ss, labels)  # masked
+    # values all 1: the labelled result is the indicator
+    ones = (V != 0).astype(np.uint32)
+    ind = c.decrypt(s, c.eval(rlk, cts, Ts))[0]
+    assert np.array_equal(c.decrypt(s, c.eval(rlk, cts, Ts, mode=2, V=ones))[0], ind)

@@ -51,8 +51,12 @@ enum {
 
 /* Evaluation modes. */
 enum {
-  PEPSI_MODE_INDICATOR = 0,  /* Algorithm 2: encrypted per-bin indicator */
-  PEPSI_MODE_CARDINALITY = 1 /* Algorithm 5 with val_s = 1: masked, slots sum to |X cap Y| */
+  PEPSI_MODE_INDICATOR = 0,   /* Algorithm 2: encrypted per-bin indicator */
+  PEPSI_MODE_CARDINALITY = 1, /* Algorithm 5 with val_s = 1: masked, slots sum to |X cap Y| */
+  PEPSI_MODE_LABELS = 2,      /* Algorithm 4: slot of a matched client item = the server item's value
+                                 (0 otherwise); needs a set loaded with values */
+  PEPSI_MODE_SUM = 3          /* Algorithm 5: masked, slots sum to the matched items' values mod t;
+                                 needs a set loaded with values */
 };
 
 /* pepsi_params.rescale_group: one rounding for all layers of an evaluation. */
@@ -89,6 +93,9 @@ typedef struct {
                               up to pepsi_info.rescale_cap layers (G itself; for
                               PEPSI_RESCALE_ALL mu, or 65536 when mu = 0); longer runs are
                               cut at the cap.  pepsi_eval_layers always rounds per layer. */
+  uint32_t server_values;  /* nonzero: the auxiliary base also holds the value products of
+                              the LABELS and SUM modes under lazy rescaling (log2(N t / 2)
+                              more bits); with 0 those modes round per layer */
 } pepsi_params;
 
 /* Derived values of a context (for callers and tests). */
@@ -133,6 +140,19 @@ int pepsi_set_rescale_group(pepsi_ctx* ctx, uint32_t rescale_group);
  * Errors: PEPSI_E_BIN_OVERFLOW, PEPSI_E_NOMEM, PEPSI_E_PARAM, PEPSI_E_CUDA. */
 int pepsi_server_load(pepsi_ctx* ctx, const uint64_t* items, size_t n, int* set_id);
 
+/* Server preprocessing with a value per item, for labelled PSI (Algorithm
+ * 4) and PSI-Sum (Algorithm 5): as pepsi_server_load, and the value of the
+ * item stored at each (layer, bin) (0 for dummies; of an x_L stored twice
+ * in a bin, the first item's) becomes the value plaintext val_s[layer],
+ * kept resident in NTT form over the ciphertext and auxiliary primes.
+ * values: host array of n values in [0, t).  Errors: as pepsi_server_load;
+ * PEPSI_E_PARAM for a value >= t. */
+int pepsi_server_load_values(pepsi_ctx* ctx, const uint64_t* items, const uint32_t* values, size_t n,
+                             int* set_id);
+
+/* Copy the value table of a set loaded with values: out[mu][N] (host). */
+int pepsi_server_values(pepsi_ctx* ctx, int set_id, uint32_t* out);
+
 /* Copy the raw server table T_s of a set: out[mu][N] (host), entries are
  * x_L values or UINT64_MAX for dummies. */
 int pepsi_server_table(pepsi_ctx* ctx, int set_id, uint64_t* out);
@@ -154,7 +174,10 @@ int pepsi_query(pepsi_ctx* ctx, const uint64_t* items, size_t m, uint64_t enc_se
 /* Server computation (Algorithm 2; mode CARDINALITY adds Algorithm 5's
  * zero-sum mask drawn from mask_seed): for every layer i',
  * h' = sum_j ct_c[j] x pt_s[i'][j], e = prod_{i<h}(h' - i), summed over
- * layers, relinearised and multiplied by (h!)^-1 mod t.
+ * layers, relinearised and multiplied by (h!)^-1 mod t.  Modes LABELS and
+ * SUM weight layer i' by its value plaintext val_s[i'] (Algorithms 4-5):
+ * with per-layer rounding val_s[i'] multiplies the rounded e; with lazy
+ * rescaling it multiplies the exact product before the run's rounding.
  * cts: [ell][2][k][N] coefficient form, host or device.
  * out_ct: [2][k][N] coefficient form, host or device.
  * Errors: PEPSI_E_PARAM (bad set/mode), PEPSI_E_NOMEM, PEPSI_E_CUDA. */

@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(_HERE, "libpepsi_gb300.so")
 _lib = None
 
 OK, E_PARAM, E_BIN_OVERFLOW, E_CUCKOO_FAIL, E_NOMEM, E_CUDA, E_TIMEOUT, E_NOISE = range(8)
-MODE_INDICATOR, MODE_CARDINALITY = 0, 1
+MODE_INDICATOR, MODE_CARDINALITY, MODE_LABELS, MODE_SUM = 0, 1, 2, 3
 DUMMY = 0xFFFFFFFFFFFFFFFF
 
 
@@ -40,7 +40,7 @@ class Params(C.Structure):
         ("N", C.c_uint32), ("t", C.c_uint64), ("k", C.c_uint32), ("prime_bits", C.c_uint8 * 8),
         ("h", C.c_uint32), ("ell", C.c_uint32), ("lambda_bar", C.c_uint32), ("num_hashes", C.c_uint32),
         ("mu", C.c_uint32), ("hash_key", C.c_uint64), ("resident_bytes", C.c_uint64),
-        ("rescale_group", C.c_uint32),
+        ("rescale_group", C.c_uint32), ("server_values", C.c_uint32),
     ]
 
 
@@ -62,6 +62,8 @@ SYMBOLS = {
     "pepsi_set_rescale_group": (C.c_int, [C.c_void_p, C.c_uint32]),
     "pepsi_server_load": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t, C.POINTER(C.c_int)]),
     "pepsi_server_table": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p]),
+    "pepsi_server_load_values": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_size_t, C.POINTER(C.c_int)]),
+    "pepsi_server_values": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p]),
     "pepsi_server_plaintexts": (C.c_int, [C.c_void_p, C.c_int, C.c_uint32, C.c_uint32, C.c_void_p, C.c_void_p]),
     "pepsi_query": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t, C.c_uint64, C.c_void_p, C.c_void_p, C.c_void_p]),
     "pepsi_eval": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.c_uint64, C.c_void_p, C.c_void_p]),
@@ -155,13 +157,14 @@ class Context:
     """One parameter set with its keys, server sets and scratch (pepsi_ctx)."""
 
     def __init__(self, N, t=65537, prime_bits=(36, 36, 37), h=2, ell=0, lambda_bar=16, mu=0, hash_key=0,
-                 key_seed=3, resident_bytes=0, rescale_group=0):
+                 key_seed=3, resident_bytes=0, rescale_group=0, server_values=0):
         p = Params()
         p.N, p.t, p.k = N, t, len(prime_bits)
         for i, b in enumerate(prime_bits):
             p.prime_bits[i] = b
         p.h, p.ell, p.lambda_bar, p.num_hashes, p.mu = h, ell, lambda_bar, 3, mu
         p.hash_key, p.resident_bytes, p.rescale_group = hash_key, resident_bytes, rescale_group
+        p.server_values = server_values
         self._h = C.c_void_p()
         _check(lib().pepsi_setup(C.byref(p), key_seed, C.byref(self._h)), "pepsi_setup")
         info = Info()
@@ -202,6 +205,23 @@ class Context:
         _check(lib().pepsi_server_load(self._h, _ptr(items) if items.size else None, items.size, C.byref(sid)),
                "pepsi_server_load")
         return sid.value
+
+    def server_load_values(self, items, values):
+        """Server set with a value in [0, t) per item (labelled PSI / PSI-Sum)."""
+        items = np.ascontiguousarray(items, dtype=np.uint64)
+        values = np.ascontiguousarray(values, dtype=np.uint32)
+        if values.shape != items.shape:
+            raise ValueError("one value per item")
+        sid = C.c_int(-1)
+        _check(lib().pepsi_server_load_values(self._h, _ptr(items) if items.size else None,
+                                              _ptr(values) if values.size else None, items.size, C.byref(sid)),
+               "pepsi_server_load_values")
+        return sid.value
+
+    def server_values(self, set_id, mu):
+        out = np.zeros((mu, self.N), dtype=np.uint32)
+        _check(lib().pepsi_server_values(self._h, set_id, _ptr(out)), "pepsi_server_values")
+        return out
 
     def server_table(self, set_id, mu):
         out = np.zeros((mu, self.N), dtype=np.uint64)

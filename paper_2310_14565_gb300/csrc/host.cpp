@@ -330,7 +330,8 @@ static void parallel_ranges(size_t count, F f) {
   for (auto& x : th) x.join();
 }
 
-int simple_hash(const Hasher& H, const u64* items, size_t n, u32 mu, std::vector<u64>& T, u32* max_load) {
+int simple_hash(const Hasher& H, const u64* items, size_t n, u32 mu, std::vector<u64>& T, u32* max_load,
+                const uint32_t* values, std::vector<uint32_t>* V) {
   const u32 b = 1u << H.logb;
   std::vector<u64> ixl(n);
   std::vector<u32> ibin(3 * n);
@@ -338,10 +339,11 @@ int simple_hash(const Hasher& H, const u64* items, size_t n, u32 mu, std::vector
     for (size_t u = lo; u < hi; ++u) H(items[u], &ixl[u], &ibin[3 * u]);
   });
   // arrivals (bin, x_L) in order: item by item, each distinct bin of the item once
-  std::vector<u32> abin;
+  std::vector<u32> abin, aown;  // bin and item of each arrival
   std::vector<u64> axl;
   abin.reserve(3 * n);
   axl.reserve(3 * n);
+  if (V) aown.reserve(3 * n);
   for (size_t u = 0; u < n; ++u) {
     const u64 xl = ixl[u];
     const u32* bs = &ibin[3 * u];
@@ -349,6 +351,7 @@ int simple_hash(const Hasher& H, const u64* items, size_t n, u32 mu, std::vector
       if ((i > 0 && bs[i] == bs[0]) || (i > 1 && bs[i] == bs[1])) continue;
       abin.push_back(bs[i]);
       axl.push_back(xl);
+      if (V) aown.push_back((u32)u);
     }
   }
   // stable counting sort by bin keeps the arrival order inside each bin
@@ -357,9 +360,15 @@ int simple_hash(const Hasher& H, const u64* items, size_t n, u32 mu, std::vector
   for (u32 i = 0; i < b; ++i) off[i + 1] += off[i];
   std::vector<size_t> fill(off.begin(), off.end() - 1);
   std::vector<u64> vals(abin.size());
-  for (size_t e = 0; e < abin.size(); ++e) vals[fill[abin[e]]++] = axl[e];
+  std::vector<u32> owners(V ? abin.size() : 0);
+  for (size_t e = 0; e < abin.size(); ++e) {
+    const size_t at = fill[abin[e]]++;
+    vals[at] = axl[e];
+    if (V) owners[at] = aown[e];
+  }
   // per bin: first arrival of each x_L kept (sorting (x_L, arrival) pairs)
   T.assign((size_t)mu * b, PEPSI_DUMMY);
+  if (V) V->assign((size_t)mu * b, 0u);
   std::vector<u32> load(b, 0);
   parallel_ranges(b, [&](size_t blo, size_t bhi) {
     std::vector<std::pair<u64, u32>> tmp;
@@ -375,7 +384,10 @@ int simple_hash(const Hasher& H, const u64* items, size_t n, u32 mu, std::vector
       u32 layer = 0;
       for (size_t r = 0; r < len; ++r) {
         if (dup[r]) continue;
-        if (layer < mu) T[(size_t)layer * b + bin] = vals[s0 + r];
+        if (layer < mu) {
+          T[(size_t)layer * b + bin] = vals[s0 + r];
+          if (V) (*V)[(size_t)layer * b + bin] = values[owners[s0 + r]];
+        }
         ++layer;
       }
       load[bin] = layer;

@@ -42,7 +42,10 @@ struct Hasher {
 };
 // client cuckoo hashing without stash; returns 0 or PEPSI_E_CUCKOO_FAIL
 int cuckoo(const Hasher& H, const u64* items, size_t m, std::vector<u64>& table, std::vector<int32_t>& where);
-// server simple hashing; T[mu][b]; returns 0 or PEPSI_E_BIN_OVERFLOW
-int simple_hash(const Hasher& H, const u64* items, size_t n, u32 mu, std::vector<u64>& T, u32* max_load);
+// Server simple hashing: T[mu][b] (x_L or PEPSI_DUMMY); with values, also
+// V[mu][b], the value of the item stored at each (layer, bin), 0 for
+// dummies.  Returns 0 or PEPSI_E_BIN_OVERFLOW.
+int simple_hash(const Hasher& H, const u64* items, size_t n, u32 mu, std::vector<u64>& T, u32* max_load,
+                const uint32_t* values = nullptr, std::vector<uint32_t>* V = nullptr);
 
 }  // namespace hostmath

@@ -126,6 +126,37 @@ __global__ void __launch_bounds__(NTT_MAX_THREADS, 2) k_ptgen(DevView V, const u
   }
 }
 
+// Value plaintexts of labelled PSI / PSI-Sum (Algorithms 4-5): for layer
+// l (one block each), slots V[l][.] -> Encode (inverse NTT mod t, slot s at
+// position brev(s)) -> centred lift -> forward NTT for every prime of
+// Q u B.  Out VP[l][k+kb][N] (plain residues, not the split format).
+__global__ void __launch_bounds__(NTT_MAX_THREADS, 2) k_valgen(DevView V, const u32* __restrict__ vals, u64* VP) {
+  extern __shared__ u64 sm[];
+  const int N = V.N, np = V.k + V.kb;
+  u64* poly = sm;                              // N u64
+  u32* mbuf = reinterpret_cast<u32*>(sm + N);  // N u32
+  const int l = blockIdx.x;
+  const u32* row = vals + (size_t)l * N;
+  for (int i = threadIdx.x; i < N; i += blockDim.x) poly[nsw(i)] = row[brev_bits(i, V.logN)];
+  __syncthreads();
+  ntt_inv_view(poly, V, V.tidx);
+  for (int i = threadIdx.x; i < N; i += blockDim.x) mbuf[i] = (u32)poly[nsw(i)];
+  __syncthreads();
+  const u64 t = V.pr[V.tidx].q, thalf = t >> 1;
+  for (int p = 0; p < np; ++p) {
+    const u64 q = V.pr[p].q;
+    for (int i = threadIdx.x; i < N; i += blockDim.x) {
+      const u64 m = mbuf[i];
+      poly[nsw(i)] = m <= thalf ? m : q - (t - m);
+    }
+    __syncthreads();
+    ntt_fwd_view(poly, V, p);
+    u64* out = VP + ((size_t)l * np + p) * N;
+    for (int i = threadIdx.x; i < N; i += blockDim.x) out[i] = poly[nsw(i)];
+    __syncthreads();
+  }
+}
+
 // ------------------------------------------------------- fused MAC (K4)
 // h'[l] = sum_j C[j] * P[l][j] pointwise in the NTT domain, for both
 // ciphertext components.  A block owns TN consecutive (prime, point) words
@@ -672,14 +703,17 @@ __global__ void k_tensor(DevView V, const u64* __restrict__ AQ, const u64* __res
 }
 
 // Lazy rescaling: X[c][pi][n] (+)= sum over layers l < L of component c of
-// the tensor of (A_l, B_l), in NTT form over Q u B.  The products of each
-// (prime, point) are summed in 128 bits and reduced once per 16 layers
-// (32 products below 2^122 each stay below 2^127), so the sum is exact mod
-// every prime; the integer it represents is the sum of the layers' exact
-// integer tensors as long as B holds it (sized at setup).
+// the tensor of (A_l, B_l), in NTT form over Q u B, each layer's tensor
+// times its value plaintext VP[l][pi][n] when VP is given (labelled PSI /
+// PSI-Sum).  The products of each (prime, point) are summed in 128 bits
+// and reduced once per 16 layers (at most 32 products below 2^122 each
+// stay below 2^127), so the sum is exact mod every prime; the integer it
+// represents is the sum of the layers' exact integer tensors (times the
+// values) as long as B holds it (sized at setup).
 __global__ void k_tensor_sum(DevView V, const u64* __restrict__ AQ, const u64* __restrict__ AB,
                              const u64* __restrict__ BQ, const u64* __restrict__ BB, const u64* __restrict__ cstQ,
-                             const u64* __restrict__ side, u64* __restrict__ X, int L, int square, int init) {
+                             const u64* __restrict__ side, const u64* __restrict__ VP, u64* __restrict__ X, int L,
+                             int square, int init) {
   const int N = V.N, k = V.k, kb = V.kb, np = k + kb;
   const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;  // over np*N
   if (idx >= (size_t)np * N) return;
@@ -706,10 +740,20 @@ __global__ void k_tensor_sum(DevView V, const u64* __restrict__ AQ, const u64* _
         b0 = addmod(b0, side[(size_t)l * kb + pp], pr.q);
       }
     }
-    mac128(s0l, s0h, a0, b0);
-    mac128(s1l, s1h, a0, b1);
-    mac128(s1l, s1h, a1, b0);
-    mac128(s2l, s2h, a1, b1);
+    if (VP) {
+      const u64 v = VP[((size_t)l * np + pi) * N + n];
+      u64 lo = 0, hi = 0;
+      mac128(lo, hi, a0, b1);
+      mac128(lo, hi, a1, b0);
+      mac128(s0l, s0h, mulmod(a0, b0, pr), v);
+      mac128(s1l, s1h, barrett128(hi, lo, pr.q, pr.bhi, pr.blo), v);
+      mac128(s2l, s2h, mulmod(a1, b1, pr), v);
+    } else {
+      mac128(s0l, s0h, a0, b0);
+      mac128(s1l, s1h, a0, b1);
+      mac128(s1l, s1h, a1, b0);
+      mac128(s2l, s2h, a1, b1);
+    }
     if ((l & 15) == 15) {
       s0l = barrett128(s0h, s0l, pr.q, pr.bhi, pr.blo);
       s1l = barrett128(s1h, s1l, pr.q, pr.bhi, pr.blo);
@@ -1182,10 +1226,45 @@ void launch_tensor(const DevView& V, const u64* AQ, const u64* AB, const u64* BQ
 }
 
 void launch_tensor_sum(const DevView& V, const u64* AQ, const u64* AB, const u64* BQ, const u64* BB,
-                       const u64* cstQ, const u64* side, u64* X, int L, bool square, bool init, cudaStream_t st) {
+                       const u64* cstQ, const u64* side, const u64* VP, u64* X, int L, bool square, bool init,
+                       cudaStream_t st) {
   const size_t total = (size_t)(V.k + V.kb) * V.N;
-  k_tensor_sum<<<grid_for(total, 128), 128, 0, st>>>(V, AQ, AB, BQ, BB, cstQ, side, X, L, square ? 1 : 0,
+  k_tensor_sum<<<grid_for(total, 128), 128, 0, st>>>(V, AQ, AB, BQ, BB, cstQ, side, VP, X, L, square ? 1 : 0,
                                                       init ? 1 : 0);
+}
+
+void launch_valgen(const DevView& V, const u32* vals, int L, u64* VP, cudaStream_t st) {
+  if (L <= 0) return;
+  k_valgen<<<L, ntt_threads(V.N), (size_t)V.N * 12, st>>>(V, vals, VP);
+}
+
+// Value-weighted layer sum with per-layer rounding: acc[c][p][n] (+)=
+// sum_{l<L} D_l[c][p][n] * VP_l[p][n] mod q_p, D in NTT form over Q.  One
+// product below 2^122 per layer; the 128-bit sums are reduced every 32.
+__global__ void k_accum_val(DevView V, const u64* __restrict__ D, const u64* __restrict__ VP, int L, u64* acc,
+                            int init) {
+  const int N = V.N, k = V.k, np = V.k + V.kb;
+  const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;  // over 3*k*N
+  if (idx >= (size_t)3 * k * N) return;
+  const int n = (int)(idx % N);
+  const int p = (int)((idx / N) % k);
+  const int c = (int)(idx / ((size_t)k * N));
+  const DevPrime pr = V.pr[p];
+  u64 lo = 0, hi = 0;
+  for (int l = 0; l < L; ++l) {
+    mac128(lo, hi, D[(((size_t)l * 3 + c) * k + p) * N + n], VP[((size_t)l * np + p) * N + n]);
+    if ((l & 31) == 31) {
+      lo = barrett128(hi, lo, pr.q, pr.bhi, pr.blo);
+      hi = 0;
+    }
+  }
+  const u64 r = barrett128(hi, lo, pr.q, pr.bhi, pr.blo);
+  acc[idx] = init ? r : addmod(r, acc[idx], pr.q);
+}
+
+void launch_accum_val(const DevView& V, const u64* D, const u64* VP, int L, u64* acc, bool init, cudaStream_t st) {
+  const size_t total = (size_t)3 * V.k * V.N;
+  k_accum_val<<<grid_for(total, 256), 256, 0, st>>>(V, D, VP, L, acc, init ? 1 : 0);
 }
 
 void launch_scale_round(const DevView& V, const u64* T3, u64* D, int L, cudaStream_t st) {
@@ -1257,6 +1336,7 @@ cudaError_t kernels_init(int N) {
   set((const void*)k_ntt<true>);
   set((const void*)k_ntt<false>);
   set((const void*)k_ptgen);
+  set((const void*)k_valgen);
   set((const void*)k_mac);
   set((const void*)k_mac_multi<1>);
   set((const void*)k_mac_multi<2>);

@@ -42,9 +42,16 @@ void launch_tensor(const DevView& V, const u64* AQ, const u64* AB, const u64* BQ
                    const u64* side, u64* T3, int L, bool square, cudaStream_t st);
 
 // Exact round(t x / Q) from Q u B residues (coefficient form) -> D[L][3][k][N] mod Q.
-// X[3][k+kb][N] (+)= sum over L layers of the tensor of (A, B) (NTT form over Q u B)
+// X[3][k+kb][N] (+)= sum over L layers of the tensor of (A, B) (NTT form over
+// Q u B), each times the layer's value plaintext VP[l][k+kb][N] when VP is
+// not null
 void launch_tensor_sum(const DevView& V, const u64* AQ, const u64* AB, const u64* BQ, const u64* BB,
-                       const u64* cstQ, const u64* side, u64* X, int L, bool square, bool init, cudaStream_t st);
+                       const u64* cstQ, const u64* side, const u64* VP, u64* X, int L, bool square, bool init,
+                       cudaStream_t st);
+// Value plaintexts VP[L][k+kb][N] (NTT form) of the value rows vals[L][N]
+void launch_valgen(const DevView& V, const u32* vals, int L, u64* VP, cudaStream_t st);
+// acc[3][k][N] (+)= sum over L layers of D_l (NTT form over Q) times VP_l
+void launch_accum_val(const DevView& V, const u64* D, const u64* VP, int L, u64* acc, bool init, cudaStream_t st);
 void launch_scale_round(const DevView& V, const u64* T3, u64* D, int L, cudaStream_t st);
 
 // RNS-digit relinearisation: D[L][3][k][N] coefficient form, rlk[k][2][k][N] NTT form

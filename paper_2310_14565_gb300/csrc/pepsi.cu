@@ -36,6 +36,9 @@ struct ServerSet {
   uint16_t* dpos = nullptr;     // [mu][N][h]
   u64* dP = nullptr;            // [mu_res][ell][k][N] resident plaintexts (a prefix of the layers) or null
   u32 mu_res = 0;               // layers [0, mu_res) resident, the rest regenerated per chunk
+  bool has_values = false;      // loaded with values (labelled PSI / PSI-Sum)
+  std::vector<uint32_t> hV;     // [mu][N] host copy of the value table
+  u64* dVP = nullptr;           // [mu][k+kb][N] value plaintexts val_s, NTT form over Q u B
 };
 
 }  // namespace
@@ -67,7 +70,8 @@ struct pepsi_ctx {
   // scratch, grown on demand
   std::vector<DevBuf> scratch;
   int chunk = 32;
-  u32 rescale_cap = 1;  // most layers one rounding of the last products may cover
+  u32 rescale_cap = 1;      // most layers one rounding of the last products may cover
+  bool value_margin = false;  // B also holds the value products under lazy rescaling
   // profiling
   bool prof = false;
   std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> prof_ev;
@@ -383,14 +387,18 @@ void lazy_flush(pepsi_ctx* c, EvalBufs& b, LazyRun& r, cudaStream_t st) {
 
 // Add the last products of the chunk's L layers to the run sums, rounding
 // each run as it completes (and the final partial run when `end`).
-void lazy_chunk(pepsi_ctx* c, EvalBufs& b, const LastMult& m, int L, bool end, LazyRun& r, cudaStream_t st) {
+// VP: value plaintexts of the chunk's layers [L][k+kb][N], or null.
+void lazy_chunk(pepsi_ctx* c, EvalBufs& b, const LastMult& m, const u64* VP, int L, bool end, LazyRun& r,
+                cudaStream_t st) {
+  const size_t vstride = (size_t)(c->k + c->kb) * c->N;
   for (int done = 0; done < L;) {
     const u32 in_run = r.pos % r.G;
     const int take = (int)std::min<u32>((u32)(L - done), r.G - in_run);
     {
       const LastMult mm = m.at(c, done);
       Prof p(c, PC_TENSOR, st);
-      launch_tensor_sum(c->V, mm.AQ, mm.AB, mm.BQ, mm.BB, mm.cQ, mm.side, r.X, take, mm.square, in_run == 0, st);
+      launch_tensor_sum(c->V, mm.AQ, mm.AB, mm.BQ, mm.BB, mm.cQ, mm.side, VP ? VP + (size_t)done * vstride : nullptr,
+                        r.X, take, mm.square, in_run == 0, st);
     }
     done += take;
     r.pos += take;
@@ -398,11 +406,12 @@ void lazy_chunk(pepsi_ctx* c, EvalBufs& b, const LastMult& m, int L, bool end, L
   }
 }
 
-// Run length of the lazy rescaling for an evaluation of nl layers (1: per
-// layer rounding).
-u32 rescale_run(const pepsi_ctx* c, u32 nl) {
+// Run length of the lazy rescaling for an evaluation of nl layers in `mode`
+// (1: per layer rounding; also for the value modes when B lacks the room).
+u32 rescale_run(const pepsi_ctx* c, u32 nl, int mode) {
   const u32 g = c->prm.rescale_group;
   if (g <= 1 || c->h == 1) return 1;
+  if (mode >= PEPSI_MODE_LABELS && !c->value_margin) return 1;
   return std::max<u32>(1, std::min<u32>(g == PEPSI_RESCALE_ALL ? nl : g, c->rescale_cap));
 }
 
@@ -443,13 +452,14 @@ cudaError_t prepare_request(pepsi_ctx* c, const u64* cts, u64* C, cudaStream_t s
 
 // a7 output: ct = (h!)^-1 * R(A) to coefficient form, plus the mask of
 // Algorithm 5 in cardinality mode, copied to out (host or device).
-cudaError_t finish_request(pepsi_ctx* c, EvalBufs& b, const u64* acc, int mode, u64 mask_seed, u64* out,
+cudaError_t finish_request(pepsi_ctx* c, EvalBufs& b, u64* acc, bool acc_ntt, int mode, u64 mask_seed, u64* out,
                            cudaStream_t st) {
   const size_t kN = (size_t)c->k * c->N;
+  if (acc_ntt) ntt(c, false, acc, acc, 3, c->k, 0, kN, kN, st);  // value-weighted sum, NTT form
   relin(c, acc, b.R, 1, st);
   axpy(c, b.zero, cst(c, CS_ZINV), b.R, b.R, 2, st);
   ntt(c, false, b.R, b.out, 2, c->k, 0, kN, kN, st);
-  if (mode == PEPSI_MODE_CARDINALITY) {
+  if (mode == PEPSI_MODE_CARDINALITY || mode == PEPSI_MODE_SUM) {
     Prof p(c, PC_CLIENT, st);
     launch_mask(c->V, mask_seed, b.out, st);
   }
@@ -465,8 +475,11 @@ int eval_core(pepsi_ctx* c, int set_id, const u64* cts, u32 layer0, u32 nl, int 
   if (set_id < 0 || set_id >= (int)c->sets.size() || !c->sets[set_id].live) return PEPSI_E_PARAM;
   ServerSet& S = c->sets[set_id];
   if ((u64)layer0 + nl > S.mu || !cts) return PEPSI_E_PARAM;
-  if (mode != PEPSI_MODE_INDICATOR && mode != PEPSI_MODE_CARDINALITY) return PEPSI_E_PARAM;
+  if (mode < PEPSI_MODE_INDICATOR || mode > PEPSI_MODE_SUM) return PEPSI_E_PARAM;
+  const bool valued = mode >= PEPSI_MODE_LABELS;
+  if (valued && !S.has_values) return PEPSI_E_PARAM;
   const size_t k = c->k, N = c->N;
+  const size_t vstride = (size_t)(c->k + c->kb) * N;  // value plaintext words per layer
   const size_t kN = k * N, ct2 = 2 * kN, ct3 = 3 * kN;
   const int Lc = std::max(1, std::min<int>(c->chunk, (int)nl));
   const u32 end = layer0 + nl, res_end = std::min(end, S.mu_res);
@@ -474,7 +487,7 @@ int eval_core(pepsi_ctx* c, int set_id, const u64* cts, u32 layer0, u32 nl, int 
   cudaError_t e = eval_bufs(c, Lc, res_end < end, &b);
   if (e != cudaSuccess) return cuda_status(e);
   // per-layer E words are only defined with per-layer rounding
-  const u32 G = e_out ? 1 : rescale_run(c, nl);
+  const u32 G = e_out ? 1 : rescale_run(c, nl, mode);
   LazyRun lr{};
   if (G > 1) {
     lr.X = (u64*)scratch(c, kScratchAccX, (size_t)3 * (c->k + c->kb) * N * 8, &e);
@@ -509,21 +522,28 @@ int eval_core(pepsi_ctx* c, int set_id, const u64* cts, u32 layer0, u32 nl, int 
       Prof p(c, PC_MAC, st);  // a5 on a regenerated chunk
       CKS(mac_status(launch_mac(c->V, b.C, b.Pc, b.H, c->ell, L, c->mac_fold, c->d_err, st)));
     }
+    const u64* VP = valued ? S.dVP + (size_t)l0 * vstride : nullptr;
     if (G > 1) {  // a6 + a7 with lazy rescaling
       const LastMult m = eq_circuit_front(c, b, L, st);
-      lazy_chunk(c, b, m, L, l0 + L == end, lr, st);
+      lazy_chunk(c, b, m, VP, L, l0 + L == end, lr, st);
     } else {
       eq_circuit(c, b, L, st);  // a6
       if (e_out) CKS(copy_any(e_out + (size_t)(l0 - layer0) * ct3, b.D, (size_t)L * ct3 * 8, st));
-      Prof p(c, PC_POINTWISE, st);  // a7: layer accumulation
-      launch_accum(c->V, b.D, L, b.acc, first, st);
+      if (valued) {  // a7, Algorithms 4-5: sum of val_s[i'] * E_{i'} in NTT form
+        ntt(c, true, b.D, b.D, (size_t)L * 3, c->k, 0, k * N, k * N, st);
+        Prof p(c, PC_POINTWISE, st);
+        launch_accum_val(c->V, b.D, VP, L, b.acc, first, st);
+      } else {
+        Prof p(c, PC_POINTWISE, st);  // a7: layer accumulation
+        launch_accum(c->V, b.D, L, b.acc, first, st);
+      }
     }
     // b.Hc holds h' in coefficient form after the circuit
     if (h_out) CKS(copy_any(h_out + (size_t)(l0 - layer0) * ct2, b.Hc, (size_t)L * ct2 * 8, st));
     first = false;
     l0 += L;
   }
-  if (out_ct) CKS(finish_request(c, b, b.acc, mode, mask_seed, out_ct, st));
+  if (out_ct) CKS(finish_request(c, b, b.acc, valued && G == 1, mode, mask_seed, out_ct, st));
   e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_status(e);
   if (!is_device_ptr(out_ct ? (const void*)out_ct : (const void*)b.out) || (h_out && !is_device_ptr(h_out)) ||
@@ -553,7 +573,8 @@ int eval_batch_core(pepsi_ctx* c, int nq, const int* set_ids, const u64* const* 
     if (set_ids[i] < 0 || set_ids[i] >= (int)c->sets.size() || !c->sets[set_ids[i]].live || !cts[i] || !outs[i])
       return PEPSI_E_PARAM;
     const int mode = modes ? modes[i] : PEPSI_MODE_INDICATOR;
-    if (mode != PEPSI_MODE_INDICATOR && mode != PEPSI_MODE_CARDINALITY) return PEPSI_E_PARAM;
+    if (mode < PEPSI_MODE_INDICATOR || mode > PEPSI_MODE_SUM) return PEPSI_E_PARAM;
+    if (mode >= PEPSI_MODE_LABELS && !c->sets[set_ids[i]].has_values) return PEPSI_E_PARAM;
   }
   // groups of requests on the same set, in order of first appearance
   std::vector<std::vector<int>> groups;
@@ -594,16 +615,19 @@ int eval_batch_core(pepsi_ctx* c, int nq, const int* set_ids, const u64* const* 
     u64* HB = (u64*)scratch(c, slot ? S_HB2 : S_HB, (size_t)PEPSI_MAC_MAX_REQUESTS * hq * 8, &e);
     u64* ACC = (u64*)scratch(c, S_ACCB, (size_t)PEPSI_MAC_MAX_REQUESTS * ct3 * 8, &e);
     if (!CB || !HB || !ACC) return cuda_status(e);
-    const u32 RG = rescale_run(c, mu);
-    const size_t xw = (size_t)3 * (c->k + c->kb) * N;
+    // per request: its mode, value plaintexts and rounding run length
+    const size_t xw = (size_t)3 * (c->k + c->kb) * N, vstride = (size_t)(c->k + c->kb) * N;
+    int gmode[PEPSI_MAC_MAX_REQUESTS];
     LazyRun lr[PEPSI_MAC_MAX_REQUESTS];
-    if (RG > 1) {
-      u64* ACCX = (u64*)scratch(c, S_ACCXB, (size_t)PEPSI_MAC_MAX_REQUESTS * xw * 8, &e);
-      if (!ACCX) return cuda_status(e);
-      for (int g = 0; g < G; ++g) {
+    u64* ACCX = nullptr;
+    for (int g = 0; g < G; ++g) {
+      gmode[g] = modes ? modes[grp[g]] : PEPSI_MODE_INDICATOR;
+      lr[g].G = rescale_run(c, mu, gmode[g]);
+      lr[g].acc = ACC + (size_t)g * ct3;
+      if (lr[g].G > 1) {
+        if (!ACCX) ACCX = (u64*)scratch(c, S_ACCXB, (size_t)PEPSI_MAC_MAX_REQUESTS * xw * 8, &e);
+        if (!ACCX) return cuda_status(e);
         lr[g].X = ACCX + (size_t)g * xw;
-        lr[g].acc = ACC + (size_t)g * ct3;
-        lr[g].G = RG;
       }
     }
     if (mres) {
@@ -635,20 +659,27 @@ int eval_batch_core(pepsi_ctx* c, int nq, const int* set_ids, const u64* const* 
       }
       for (int g = 0; g < G; ++g) {
         b.H = HB + (size_t)g * hq + (res ? (size_t)l0 * ct2 : 0);
-        if (RG > 1) {
+        const u64* VP = gmode[g] >= PEPSI_MODE_LABELS ? S.dVP + (size_t)l0 * vstride : nullptr;
+        if (lr[g].G > 1) {
           const LastMult m = eq_circuit_front(c, b, L, st);
-          lazy_chunk(c, b, m, L, l0 + L == mu, lr[g], st);
+          lazy_chunk(c, b, m, VP, L, l0 + L == mu, lr[g], st);
           continue;
         }
         eq_circuit(c, b, L, st);
-        Prof p(c, PC_POINTWISE, st);
-        launch_accum(c->V, b.D, L, ACC + (size_t)g * ct3, l0 == 0, st);
+        if (VP) {
+          ntt(c, true, b.D, b.D, (size_t)L * 3, c->k, 0, kN, kN, st);
+          Prof p(c, PC_POINTWISE, st);
+          launch_accum_val(c->V, b.D, VP, L, ACC + (size_t)g * ct3, l0 == 0, st);
+        } else {
+          Prof p(c, PC_POINTWISE, st);
+          launch_accum(c->V, b.D, L, ACC + (size_t)g * ct3, l0 == 0, st);
+        }
       }
       l0 += L;
     }
     for (int g = 0; g < G; ++g) {
       const int i = grp[g];
-      CKS(finish_request(c, b, ACC + (size_t)g * ct3, modes ? modes[i] : PEPSI_MODE_INDICATOR,
+      CKS(finish_request(c, b, ACC + (size_t)g * ct3, gmode[g] >= PEPSI_MODE_LABELS && lr[g].G == 1, gmode[g],
                          mask_seeds ? mask_seeds[i] : 0, outs[i], st));
       any_host |= !is_device_ptr(outs[i]);
     }
@@ -694,6 +725,7 @@ void free_set(ServerSet& S) {
   cudaFree(S.dT);
   cudaFree(S.dpos);
   cudaFree(S.dP);
+  cudaFree(S.dVP);
   S = ServerSet{};
 }
 
@@ -826,7 +858,11 @@ int pepsi_setup(const pepsi_params* params, uint64_t key_seed, pepsi_ctx** out) 
   }
   // auxiliary base B: 61-bit primes with log2 B >= log2(t N Q G) + 3, G the
   // longest run of layers whose exact products are summed before rounding
-  const double needB = std::log2((double)c->t) + c->logN + lq + std::ceil(std::log2((double)c->rescale_cap)) + 3.0;
+  // (and, for the value modes, N t / 2 times more: the product with a value
+  // plaintext of centred coefficients)
+  c->value_margin = params->server_values != 0 && c->rescale_cap > 1;
+  const double needB = std::log2((double)c->t) + c->logN + lq + std::ceil(std::log2((double)c->rescale_cap)) + 3.0 +
+                       (c->value_margin ? std::ceil(c->logN + std::log2((double)c->t) - 1.0) : 0.0);
   double haveB = 0;
   std::vector<u64> taken = c->Q;
   while (haveB < needB) {
@@ -976,14 +1012,20 @@ int pepsi_set_rescale_group(pepsi_ctx* c, uint32_t rescale_group) {
   return PEPSI_OK;
 }
 
-int pepsi_server_load(pepsi_ctx* c, const uint64_t* items, size_t n, int* set_id) {
-  if (!c || (!items && n) || !set_id) return PEPSI_E_PARAM;
+namespace {
+// with_values: the set carries values[n] (labelled PSI / PSI-Sum)
+int server_load_impl(pepsi_ctx* c, const uint64_t* items, bool with_values, const uint32_t* values, size_t n,
+                     int* set_id) {
+  if (!c || (!items && n) || !set_id || (with_values && !values && n)) return PEPSI_E_PARAM;
+  if (with_values)
+    for (size_t i = 0; i < n; ++i)
+      if (values[i] >= c->t) return PEPSI_E_PARAM;
   hostmath::Hasher H(c->prm.hash_key, c->prm.lambda_bar, c->logN);
   u32 mu = c->prm.mu ? c->prm.mu : hostmath::mu_rule(n, c->N);
   ServerSet S;
   S.mu = mu;
   u32 maxload = 0;
-  int rc = hostmath::simple_hash(H, items, n, mu, S.hT, &maxload);
+  int rc = hostmath::simple_hash(H, items, n, mu, S.hT, &maxload, values, with_values ? &S.hV : nullptr);
   if (rc) return rc;
   const size_t N = c->N, k = c->k;
   const size_t tbytes = (size_t)mu * N * 8;
@@ -997,6 +1039,23 @@ int pepsi_server_load(pepsi_ctx* c, const uint64_t* items, size_t n, int* set_id
   {
     Prof p(c, PC_PTGEN, c->stream);
     launch_cw_unrank(S.dT, (size_t)mu * N, c->d_binom, c->ell, c->h, S.dpos, c->stream);
+  }
+  if (with_values) {  // value plaintexts val_s[layer] (Algorithms 4-5), NTT form over Q u B
+    S.has_values = true;
+    u32* dv = nullptr;
+    e = upload((void**)&dv, S.hV.data(), (size_t)mu * N * sizeof(u32));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&S.dVP, (size_t)mu * (c->k + c->kb) * N * 8);
+    if (e == cudaSuccess) {
+      Prof p(c, PC_PTGEN, c->stream);
+      launch_valgen(c->V, dv, (int)mu, S.dVP, c->stream);
+      e = cudaStreamSynchronize(c->stream);
+    }
+    cudaFree(dv);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      free_set(S);
+      return cuda_status(e);
+    }
   }
   // resident NTT-form plaintexts: the longest prefix of layers the budget holds
   const size_t per_layer = (size_t)c->ell * k * N * 8;
@@ -1031,6 +1090,23 @@ int pepsi_server_load(pepsi_ctx* c, const uint64_t* items, size_t n, int* set_id
   S.live = true;
   c->sets.push_back(std::move(S));
   *set_id = (int)c->sets.size() - 1;
+  return PEPSI_OK;
+}
+}  // namespace
+
+int pepsi_server_load(pepsi_ctx* c, const uint64_t* items, size_t n, int* set_id) {
+  return server_load_impl(c, items, false, nullptr, n, set_id);
+}
+
+int pepsi_server_load_values(pepsi_ctx* c, const uint64_t* items, const uint32_t* values, size_t n, int* set_id) {
+  return server_load_impl(c, items, true, values, n, set_id);
+}
+
+int pepsi_server_values(pepsi_ctx* c, int set_id, uint32_t* out) {
+  if (!c || !out || set_id < 0 || set_id >= (int)c->sets.size() || !c->sets[set_id].live ||
+      !c->sets[set_id].has_values)
+    return PEPSI_E_PARAM;
+  memcpy(out, c->sets[set_id].hV.data(), c->sets[set_id].hV.size() * sizeof(uint32_t));
   return PEPSI_OK;
 }
 

@@ -63,6 +63,26 @@ def test_paper_result_decrypts_to_intersection(paper_case):
     assert int(cs.astype(np.int64).sum()) % 65537 == 102
 
 
+def test_paper_labels_and_sum(paper_case):
+    """Labelled PSI and PSI-Sum at the paper size: a second set, the same
+    2^20 items with a value each; the labelled result decrypts to the value
+    of every planted item at its bin and zero elsewhere, the masked sum to
+    their total mod t."""
+    oc, gc, s, rlk, sets, sid, Ts, cts, where = paper_case
+    values = (np.arange(1 << 20, dtype=np.uint64) * 7919 % 65536 + 1).astype(np.uint32)
+    vid = gc.server_load_values(sets.server, values)
+    assert np.array_equal(gc.server_table(vid, 526), Ts)
+    val_of = dict(zip(sets.server.tolist(), values.tolist()))
+    want = np.zeros(8192, np.uint32)
+    for u, x in enumerate(sets.client.tolist()):
+        if x in val_of:
+            want[where[u]] = val_of[x]
+    slots, budget = gc.decrypt(gc.eval(vid, cts, mode=2))
+    assert budget > 0 and np.array_equal(slots, want)
+    ss, budget = gc.decrypt(gc.eval(vid, cts, mode=3, mask_seed=9))
+    assert budget > 0 and int(ss.astype(np.int64).sum()) % 65537 == int(want.astype(np.int64).sum()) % 65537
+
+
 LARGE = [55] * 6 + [54] * 2
 
 

@@ -103,6 +103,8 @@ def lib():
         L.or_keygen.argtypes = [C.c_void_p, C.c_uint64, i8p, u64p]
         L.or_encrypt.argtypes = [C.c_void_p, i8p, u32p, C.c_uint32, C.c_uint64, u64p]
         L.or_decrypt.argtypes = [C.c_void_p, i8p, u64p, u32p, C.POINTER(C.c_double)]
+        L.or_decrypt_primes.argtypes = [C.c_void_p, i8p, u64p, C.c_uint32, u32p, C.POINTER(C.c_double)]
+        L.or_mod_switch.argtypes = [C.c_void_p, u64p, C.c_uint32, u64p]
         L.or_pt_lift.argtypes = [C.c_void_p, u32p, u64p]
         L.or_ct_mul_pt.argtypes = [C.c_void_p, u64p, u32p, u64p]
         L.or_ct_axpy.argtypes = [C.c_void_p, u64p, C.c_int64, u64p, C.c_uint32, u64p]
@@ -331,11 +333,21 @@ class Ctx:
         return cts
 
     def decrypt(self, s, ct):
+        """Slots and noise budget of a ciphertext [2][r][N] over the first r
+        primes (r = k, or fewer after modulus switching)."""
         ct = np.ascontiguousarray(ct, dtype=np.uint64)
         slots = np.zeros(self.N, np.uint32)
         b = C.c_double(0)
-        lib().or_decrypt(self._p, np.ascontiguousarray(s, np.int8), ct, slots, C.byref(b))
+        rc = lib().or_decrypt_primes(self._p, np.ascontiguousarray(s, np.int8), ct, ct.shape[-2], slots, C.byref(b))
+        assert rc == 0
         return slots, b.value
+
+    def mod_switch(self, ct, r):
+        """round(c~ * Q_r / Q) to the first r primes: [2][k][N] -> [2][r][N]."""
+        out = np.zeros((2, r, self.N), np.uint64)
+        rc = lib().or_mod_switch(self._p, np.ascontiguousarray(ct, np.uint64), r, out)
+        assert rc == 0
+        return out
 
     # ---- homomorphic primitives
     def pt_lift(self, m):

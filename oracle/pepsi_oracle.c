@@ -788,43 +788,93 @@ int or_encrypt(const or_ctx* c, const int8_t* s, const u32* m, u32 count, u64 se
 /* FV decryption: z = [c0 + c1*s]_Q (centred), m = [round(t*z/Q)]_t, then
  * slots.  Noise budget = log2(Q) - log2(2*max|[t*z]_Q|) (centred), which is
  * positive exactly when decryption is correct. */
-int or_decrypt(const or_ctx* c, const int8_t* s, const u64* ct, u32* slots, double* budget) {
-  u32 N = c->N, k = c->k;
-  u64* z = (u64*)malloc(sizeof(u64) * N * k);
+/* Decryption of a ciphertext over the first r primes, modulus
+ * Q_r = q_0 ... q_{r-1} (r = k: the full modulus; r < k: a response after
+ * modulus switching): z = [c0 + c1 s]_{Q_r} centred, m = [round(t z / Q_r)]_t,
+ * slots = Decode(m); budget = log2 Q_r - 1 - log2 max |[t z]_{Q_r}| (centred),
+ * positive exactly when the decryption is correct. */
+int or_decrypt_primes(const or_ctx* c, const int8_t* s, const u64* ct, u32 r, u32* slots, double* budget) {
+  u32 N = c->N;
+  if (r == 0 || r > c->k) return OR_E_PARAM;
+  u64* z = (u64*)malloc(sizeof(u64) * N * r);
   u64 *sq = (u64*)malloc(sizeof(u64) * N), *tmp = (u64*)malloc(sizeof(u64) * N), *prod = (u64*)malloc(sizeof(u64) * N);
-  for (u32 p = 0; p < k; p++) {
+  for (u32 p = 0; p < r; p++) {
     u64 q = c->q[p];
     for (u32 n = 0; n < N; n++) sq[n] = smod(s[n], q);
-    ring_mul(ct + ((u64)1 * k + p) * N, sq, prod, N, &c->tq[p], tmp);
-    for (u32 n = 0; n < N; n++) z[(u64)n * k + p] = addmod(ct[(u64)p * N + n], prod[n], q);
+    ring_mul(ct + ((u64)1 * r + p) * N, sq, prod, N, &c->tq[p], tmp);
+    for (u32 n = 0; n < N; n++) z[(u64)n * r + p] = addmod(ct[(u64)p * N + n], prod[n], q);
   }
+  /* Q_r, (Q_r - 1)/2 and the Garner inverses of the first r primes */
+  bn Qr, Qrh, one;
+  bn_set_u64(&Qr, 1);
+  for (u32 p = 0; p < r; p++) bn_mul_u64(&Qr, &Qr, c->q[p]);
+  bn_set_u64(&one, 1);
+  bn_sub(&Qrh, &Qr, &one);
+  bn_divmod(&Qrh, NULL, &Qrh, &(bn){.d = {2}, .n = 1});
+  u64 inv[OR_MAXK * OR_MAXK];
+  for (u32 i = 0; i < r; i++)
+    for (u32 j = 0; j < r; j++) inv[i * r + j] = (i == j) ? 1 : invmod(c->q[j] % c->q[i], c->q[i]);
   u32* mm = (u32*)malloc(sizeof(u32) * N);
   bn maxr;
   bn_zero(&maxr);
   for (u32 n = 0; n < N; n++) {
     sbn Z, num, y;
-    lift_q(c, z + (u64)n * k, &Z);
-    /* m = round(t*Z/Q) mod t */
+    crt_garner(z + (u64)n * r, c->q, r, inv, &Z.m);
+    Z.neg = 0;
+    if (bn_cmp(&Z.m, &Qrh) > 0) { bn_sub(&Z.m, &Qr, &Z.m); Z.neg = 1; }
+    /* m = round(t*Z/Q_r) mod t */
     bn_mul_u64(&num.m, &Z.m, c->t);
     num.neg = Z.neg && num.m.n;
-    sbn half = {c->Qhalf, 0};
+    sbn half = {Qrh, 0};
     sbn_add(&num, &num, &half);
-    sbn_floordiv(&y, &num, &c->Q);
+    sbn_floordiv(&y, &num, &Qr);
     mm[n] = (u32)sbn_mod_u64(&y, c->t);
-    /* r = [t*Z]_Q centred */
-    bn tz, r;
+    /* [t*Z]_{Q_r} centred */
+    bn tz, rr;
     bn_mul_u64(&tz, &Z.m, c->t);
-    bn_divmod(NULL, &r, &tz, &c->Q);
-    if (Z.neg && r.n) bn_sub(&r, &c->Q, &r); /* t*Z mod Q for negative Z */
-    if (bn_cmp(&r, &c->Qhalf) > 0) bn_sub(&r, &c->Q, &r);
-    if (bn_cmp(&r, &maxr) > 0) maxr = r;
+    bn_divmod(NULL, &rr, &tz, &Qr);
+    if (Z.neg && rr.n) bn_sub(&rr, &Qr, &rr); /* t*Z mod Q_r for negative Z */
+    if (bn_cmp(&rr, &Qrh) > 0) bn_sub(&rr, &Qr, &rr);
+    if (bn_cmp(&rr, &maxr) > 0) maxr = rr;
   }
   or_decode(c, mm, slots);
   if (budget) {
     if (maxr.n == 0) *budget = INFINITY;
-    else *budget = bn_log2(&c->Q) - 1.0 - bn_log2(&maxr);
+    else *budget = bn_log2(&Qr) - 1.0 - bn_log2(&maxr);
   }
   free(z); free(sq); free(tmp); free(prod); free(mm);
+  return 0;
+}
+int or_decrypt(const or_ctx* c, const int8_t* s, const u64* ct, u32* slots, double* budget) {
+  return or_decrypt_primes(c, s, ct, c->k, slots, budget);
+}
+
+/* Modulus switching of a ciphertext to the first r primes (the response of
+ * the server computation): each coefficient's centred lift c~ in
+ * (-Q/2, Q/2] becomes round(c~ * Q_r / Q) = round(c~ / Q'), Q' = Q / Q_r
+ * (odd, so there are no ties), reduced mod q_0 .. q_{r-1}.
+ * ct: [2][k][N], out: [2][r][N], 1 <= r <= k. */
+int or_mod_switch(const or_ctx* c, const u64* ct, u32 r, u64* out) {
+  u32 N = c->N, k = c->k;
+  if (r == 0 || r > k) return OR_E_PARAM;
+  bn Qd, Qdh, one;
+  bn_set_u64(&Qd, 1);
+  for (u32 p = r; p < k; p++) bn_mul_u64(&Qd, &Qd, c->q[p]);
+  bn_set_u64(&one, 1);
+  bn_sub(&Qdh, &Qd, &one);
+  bn_divmod(&Qdh, NULL, &Qdh, &(bn){.d = {2}, .n = 1});
+  sbn half = {Qdh, 0};
+  u64 x[OR_MAXK];
+  for (u32 comp = 0; comp < 2; comp++)
+    for (u32 n = 0; n < N; n++) {
+      sbn X, num, y;
+      for (u32 p = 0; p < k; p++) x[p] = ct[((u64)comp * k + p) * N + n];
+      lift_q(c, x, &X);
+      num = X;
+      sbn_add(&num, &num, &half);
+      sbn_floordiv(&y, &num, &Qd);
+      for (u32 p = 0; p < r; p++) out[((u64)comp * r + p) * N + n] = sbn_mod_u64(&y, c->q[p]);
+    }
   return 0;
 }
 

@@ -660,3 +660,58 @@ def test_labelled_psi_and_psi_sum(oracle_mod, h, bits, lb):
     ones = (V != 0).astype(np.uint32)
     ind = c.decrypt(s, c.eval(rlk, cts, Ts))[0]
     assert np.array_equal(c.decrypt(s, c.eval(rlk, cts, Ts, mode=2, V=ones))[0], ind)
+
+
+# ------------------------------------------- response modulus switching
+def test_mod_switch_words_against_big_integers(oracle_mod):
+    # round(c~ * Q_r / Q) of the centred lift, exact integers
+    c = oracle_mod.Ctx(N=8, t=T, prime_bits=[36, 36, 37], h=1, lambda_bar=3)
+    s, _ = c.keygen(5)
+    rng = np.random.default_rng(9)
+    ct = c.encrypt(s, c.encode(rand_slots(rng, 8)), 3)[0]
+    Q = c.Q
+    for r in (1, 2, 3):
+        Qr = math.prod(c.q[:r])
+        got = c.mod_switch(ct, r)
+        for comp in range(2):
+            for m in range(8):
+                x = int(sympy_crt(c.q, [int(ct[comp, p, m]) for p in range(c.k)])[0])
+                x = x - Q if x > Q // 2 else x
+                num = x * Qr
+                y = (2 * num + Q) // (2 * Q)  # round(num / Q), Q odd: no ties
+                for p in range(r):
+                    assert int(got[comp, p, m]) == y % c.q[p]
+    assert np.array_equal(c.mod_switch(ct, 3), ct)
+
+
+@pytest.mark.parametrize("bits", [[36, 36, 37], [55, 55, 54, 54]])
+def test_mod_switch_preserves_decryption(oracle_mod, bits):
+    c = oracle_mod.Ctx(N=64, t=T, prime_bits=bits, h=1, lambda_bar=6)
+    s, rlk = c.keygen(2)
+    rng = np.random.default_rng(10)
+    a, b = rand_slots(rng, 64), rand_slots(rng, 64)
+    cts = c.encrypt(s, np.stack([c.encode(a), c.encode(b)]), 4)
+    prod = c.relin(rlk, c.ct_mult(cts[0], cts[1]))  # a noisier ciphertext too
+    want = a.astype(np.int64) * b % T
+    for ct, slots in ((cts[0], a), (prod, want)):
+        full, b_full = c.decrypt(s, ct)
+        for r in range(1, c.k + 1):
+            sw = c.mod_switch(ct, r)
+            got, bud = c.decrypt(s, sw)
+            assert bud > 0 and np.array_equal(got, slots) and np.array_equal(got, full)
+            # c' = c Q_r / Q + eps with |eps| <= 1/2 per coefficient, so
+            # |[t z']_{Q_r}| <= |[t z]_Q| Q_r / Q + t (1 + |s|_1) / 2
+            lq, lqr = math.log2(c.Q), sum(math.log2(q) for q in c.q[:r])
+            e_full = 2.0 ** (lq - 1 - b_full)
+            bound = lqr - 1 - math.log2(e_full * 2.0 ** (lqr - lq) + T * (1 + int(np.abs(s).sum())) / 2)
+            assert bud >= bound - 1e-6 or r == c.k
+
+
+@pytest.mark.parametrize("h,bits,lb", [(4, [55, 55, 54, 54], 12), (8, [55] * 6 + [54] * 2, 14)])
+def test_psi_response_switched_to_one_prime(oracle_mod, h, bits, lb):
+    c, s, rlk, sets, Ts, cts, where = _lazy_case(oracle_mod, h, bits, lb)
+    out = c.eval(rlk, cts, Ts)
+    full, _ = c.decrypt(s, out)
+    for r in (1, 2):
+        slots, bud = c.decrypt(s, c.mod_switch(out, r))
+        assert bud > 0 and np.array_equal(slots, full)

@@ -96,6 +96,10 @@ typedef struct {
   uint32_t server_values;  /* nonzero: the auxiliary base also holds the value products of
                               the LABELS and SUM modes under lazy rescaling (log2(N t / 2)
                               more bits); with 0 those modes round per layer */
+  uint32_t response_primes;/* primes r of the evaluation's response: pepsi_eval and
+                              pepsi_eval_batch switch the result to q_0..q_{r-1}
+                              (pepsi_mod_switch), out_ct [2][r][N]; 0 = k, no switching.
+                              r = 1 gives the one-prime response (2 N 8 bytes) */
 } pepsi_params;
 
 /* Derived values of a context (for callers and tests). */
@@ -109,6 +113,7 @@ typedef struct {
   double log2_q;
   uint32_t rescale_group;/* rescale_group as given (0 and 1 both mean per layer) */
   uint32_t rescale_cap;  /* most layers one rounding may cover (1: per-layer rounding only) */
+  uint32_t response_primes; /* primes of the evaluation's response (k: not switched) */
 } pepsi_info;
 
 /* Setup (Section 4, parameters of Tables 2-3): derives ell (Eq. 1), the
@@ -179,7 +184,8 @@ int pepsi_query(pepsi_ctx* ctx, const uint64_t* items, size_t m, uint64_t enc_se
  * with per-layer rounding val_s[i'] multiplies the rounded e; with lazy
  * rescaling it multiplies the exact product before the run's rounding.
  * cts: [ell][2][k][N] coefficient form, host or device.
- * out_ct: [2][k][N] coefficient form, host or device.
+ * out_ct: [2][r][N] coefficient form, host or device, r =
+ * pepsi_info.response_primes (k unless the response is switched).
  * Errors: PEPSI_E_PARAM (bad set/mode), PEPSI_E_NOMEM, PEPSI_E_CUDA. */
 int pepsi_eval(pepsi_ctx* ctx, int set_id, const uint64_t* cts, int mode, uint64_t mask_seed, uint64_t* out_ct,
                void* stream);
@@ -208,6 +214,24 @@ int pepsi_eval_layers(pepsi_ctx* ctx, int set_id, const uint64_t* cts, uint32_t 
  * Returns PEPSI_E_NOISE when the budget is not positive (slots are still
  * written). */
 int pepsi_decrypt(pepsi_ctx* ctx, const uint64_t* ct, uint32_t* slots, double* noise_budget_bits);
+
+/* The same over the first nprimes primes, modulus Q_r = q_0..q_{r-1}
+ * (r = nprimes, 1..k): for a response switched by pepsi_mod_switch or
+ * pepsi_params.response_primes.  ct: [2][r][N] (host or device); the budget
+ * is log2(Q_r) - log2(2 max|[t z]_{Q_r}|).  Errors as pepsi_decrypt, and
+ * PEPSI_E_PARAM for r outside 1..k. */
+int pepsi_decrypt_primes(pepsi_ctx* ctx, const uint64_t* ct, uint32_t nprimes, uint32_t* slots,
+                         double* noise_budget_bits);
+
+/* Modulus switching of n ciphertexts to the first nprimes primes (the
+ * server's response, whose size Section 7 reports as one ciphertext at one
+ * prime): each coefficient's centred lift c~ in (-Q/2, Q/2] becomes
+ * round(c~ q_0..q_{r-1} / Q) mod q_i, exact (Garner over the dropped
+ * primes; Q / Q_r is odd, so there are no ties).  Decryption is preserved
+ * while t (1 + |s|_1) / 2 plus the scaled noise stays below Q_r / 2.
+ * ct: [n][2][k][N], out: [n][2][r][N], coefficient form, host or device;
+ * r = k copies.  Errors: PEPSI_E_PARAM, PEPSI_E_CUDA. */
+int pepsi_mod_switch(pepsi_ctx* ctx, const uint64_t* ct, size_t n, uint32_t nprimes, uint64_t* out, void* stream);
 
 /* Forward (inverse = 0) or inverse negacyclic NTT over the ciphertext
  * primes, in place: polys[count][k][N], device memory.  Forward maps

@@ -40,7 +40,7 @@ class Params(C.Structure):
         ("N", C.c_uint32), ("t", C.c_uint64), ("k", C.c_uint32), ("prime_bits", C.c_uint8 * 8),
         ("h", C.c_uint32), ("ell", C.c_uint32), ("lambda_bar", C.c_uint32), ("num_hashes", C.c_uint32),
         ("mu", C.c_uint32), ("hash_key", C.c_uint64), ("resident_bytes", C.c_uint64),
-        ("rescale_group", C.c_uint32), ("server_values", C.c_uint32),
+        ("rescale_group", C.c_uint32), ("server_values", C.c_uint32), ("response_primes", C.c_uint32),
     ]
 
 
@@ -50,6 +50,7 @@ class Info(C.Structure):
         ("mu", C.c_uint32), ("lambda_bar", C.c_uint32), ("logb", C.c_uint32), ("t", C.c_uint64),
         ("q", C.c_uint64 * 8), ("psi", C.c_uint64 * 8), ("psi_t", C.c_uint64), ("b_primes", C.c_uint64 * 12),
         ("log2_q", C.c_double), ("rescale_group", C.c_uint32), ("rescale_cap", C.c_uint32),
+        ("response_primes", C.c_uint32),
     ]
 
 
@@ -72,6 +73,8 @@ SYMBOLS = {
     "pepsi_eval_layers": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_uint32, C.c_uint32, C.c_void_p,
                                     C.c_void_p, C.c_void_p]),
     "pepsi_decrypt": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(C.c_double)]),
+    "pepsi_decrypt_primes": (C.c_int, [C.c_void_p, C.c_void_p, C.c_uint32, C.c_void_p, C.POINTER(C.c_double)]),
+    "pepsi_mod_switch": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t, C.c_uint32, C.c_void_p, C.c_void_p]),
     "pepsi_ntt": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t, C.c_int, C.c_void_p]),
     "pepsi_ct_mult": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_size_t, C.c_int, C.c_void_p, C.c_void_p]),
     "pepsi_relin": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p]),
@@ -157,14 +160,14 @@ class Context:
     """One parameter set with its keys, server sets and scratch (pepsi_ctx)."""
 
     def __init__(self, N, t=65537, prime_bits=(36, 36, 37), h=2, ell=0, lambda_bar=16, mu=0, hash_key=0,
-                 key_seed=3, resident_bytes=0, rescale_group=0, server_values=0):
+                 key_seed=3, resident_bytes=0, rescale_group=0, server_values=0, response_primes=0):
         p = Params()
         p.N, p.t, p.k = N, t, len(prime_bits)
         for i, b in enumerate(prime_bits):
             p.prime_bits[i] = b
         p.h, p.ell, p.lambda_bar, p.num_hashes, p.mu = h, ell, lambda_bar, 3, mu
         p.hash_key, p.resident_bytes, p.rescale_group = hash_key, resident_bytes, rescale_group
-        p.server_values = server_values
+        p.server_values, p.response_primes = server_values, response_primes
         self._h = C.c_void_p()
         _check(lib().pepsi_setup(C.byref(p), key_seed, C.byref(self._h)), "pepsi_setup")
         info = Info()
@@ -176,6 +179,7 @@ class Context:
         self.psi_t = int(info.psi_t)
         self.b_primes = [int(info.b_primes[i]) for i in range(min(self.kb, 12))]
         self.rescale_cap = int(info.rescale_cap)
+        self.response_primes = int(info.response_primes)
         self.mu = {}
 
     def close(self):
@@ -246,18 +250,32 @@ class Context:
         return out, where[: items.size]
 
     def decrypt(self, ct):
+        """Slots and noise budget of a ciphertext [2][r][N] over the first r
+        primes (r = k, or fewer for a switched response)."""
         ct = np.ascontiguousarray(ct, dtype=np.uint64) if isinstance(ct, np.ndarray) else ct
+        r = int(ct.shape[-2])
         slots = np.zeros(self.N, dtype=np.uint32)
         b = C.c_double(0)
-        rc = lib().pepsi_decrypt(self._h, _ptr(ct), _ptr(slots), C.byref(b))
+        rc = lib().pepsi_decrypt_primes(self._h, _ptr(ct), r, _ptr(slots), C.byref(b))
         if rc not in (OK, E_NOISE):
-            raise PepsiError(rc, "pepsi_decrypt")
+            raise PepsiError(rc, "pepsi_decrypt_primes")
         return slots, b.value
+
+    def mod_switch(self, cts, r, out=None, stream=None):
+        """round(c~ Q_r / Q): [n][2][k][N] (or [2][k][N]) -> [n][2][r][N]."""
+        single = len(cts.shape) == 3
+        n = 1 if single else int(cts.shape[0])
+        if out is None:
+            out = np.zeros(((2, r, self.N) if single else (n, 2, r, self.N)), dtype=np.uint64)
+            if isinstance(cts, np.ndarray):
+                cts = np.ascontiguousarray(cts, dtype=np.uint64)
+        _check(lib().pepsi_mod_switch(self._h, _ptr(cts), n, r, _ptr(out), _stream(stream)), "pepsi_mod_switch")
+        return out
 
     # ---- evaluation
     def eval(self, set_id, cts, mode=MODE_INDICATOR, mask_seed=0, out=None, stream=None):
         if out is None:
-            out = np.zeros((2, self.k, self.N), dtype=np.uint64)
+            out = np.zeros((2, self.response_primes, self.N), dtype=np.uint64)
         _check(lib().pepsi_eval(self._h, set_id, _ptr(cts), mode, mask_seed, _ptr(out), _stream(stream)),
                "pepsi_eval")
         return out
@@ -266,7 +284,7 @@ class Context:
         """pepsi_eval_batch: one output ciphertext per request."""
         nq = len(cts_list)
         if outs is None:
-            outs = [np.zeros((2, self.k, self.N), dtype=np.uint64) for _ in range(nq)]
+            outs = [np.zeros((2, self.response_primes, self.N), dtype=np.uint64) for _ in range(nq)]
         sid = (C.c_int * nq)(*set_ids)
         cp = (C.c_void_p * nq)(*[_ptr(x) for x in cts_list])
         op = (C.c_void_p * nq)(*[_ptr(x) for x in outs])

@@ -1055,6 +1055,41 @@ __global__ void __launch_bounds__(NTT_MAX_THREADS, 2) k_dec_slots(DevView V, con
   for (int s = threadIdx.x; s < N; s += blockDim.x) slots[s] = (u32)sm[nsw(brev_bits(s, V.logN))];
 }
 
+// Modulus switching of the response to the first r primes: per
+// coefficient, with z = c + (Q'-1)/2, [z]_{Q'} from Garner over the dropped
+// primes, y = (z - [z]_{Q'}) / Q' mod q_i = round(c~ / Q') for any
+// representative c of the residue class mod Q (Q' odd, no ties).
+__global__ void k_modswitch(const __grid_constant__ ModSwitchArgs M, DevView V, const u64* __restrict__ in,
+                            u64* __restrict__ out, size_t n) {
+  const int N = V.N, k = M.k, r = M.r, m = k - r;
+  const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;  // over n*2*N
+  if (idx >= n * 2 * N) return;
+  const int x = (int)(idx % N);
+  const size_t cc = idx / N;  // ciphertext * 2 + component
+  const u64* src = in + cc * k * N + x;
+  u64 v[PEPSI_MAXQ];
+#pragma unroll
+  for (int j = 0; j < PEPSI_MAXQ; ++j) {
+    if (j < m) {
+      const DevPrime d = V.pr[r + j];
+      u64 z = addmod(src[(size_t)(r + j) * N], M.h[r + j], d.q);
+#pragma unroll
+      for (int l = 0; l < PEPSI_MAXQ; ++l)
+        if (l < j) z = mulmod(submod(z, barrett64(v[l], d), d.q), M.ginv[j][l], d);
+      v[j] = z;
+    }
+  }
+  u64* dst = out + cc * r * N + x;
+  for (int i = 0; i < r; ++i) {
+    const DevPrime qi = V.pr[i];
+    u64 S = 0;
+#pragma unroll
+    for (int j = 0; j < PEPSI_MAXQ; ++j)
+      if (j < m) S = addmod(S, mulmod(barrett64(v[j], qi), M.pw[i][j], qi), qi.q);
+    dst[(size_t)i * N] = mulmod(submod(addmod(src[(size_t)i * N], M.h[i], qi.q), S, qi.q), M.qdinv[i], qi);
+  }
+}
+
 // Cardinality mask (Algorithm 5): r_s uniform in Z_t for s < N-1,
 // r_{N-1} = -sum; c0 += round(Q Encode(r) / t).  One block.
 __global__ void __launch_bounds__(NTT_MAX_THREADS, 2) k_mask(DevView V, u64 seed, u64* ct) {
@@ -1304,6 +1339,12 @@ void launch_keygen(const DevView& V, u64 seed, int8_t* s, u64* s_ntt, u64* rlk, 
   k_keygen_s<<<grid_for(V.N, 256), 256, 0, st>>>(V, seed, s);
   k_keygen_sntt<<<V.k, ntt_threads(V.N), (size_t)V.N * 8, st>>>(V, s, s_ntt);
   k_keygen_rlk<<<V.k * V.k, ntt_threads(V.N), (size_t)V.N * 8, st>>>(V, seed, s_ntt, rlk);
+}
+
+void launch_modswitch(const DevView& V, const ModSwitchArgs& M, const u64* in, u64* out, size_t n, cudaStream_t st) {
+  const size_t total = n * 2 * V.N;
+  if (!total) return;
+  k_modswitch<<<grid_for(total, 256), 256, 0, st>>>(M, V, in, out, n);
 }
 
 void launch_decrypt(const DevView& V, const u64* ct, const u64* s_ntt, u64* zbuf, u32* mbuf, u32* slots,

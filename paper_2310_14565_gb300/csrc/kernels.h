@@ -48,6 +48,17 @@ void launch_tensor(const DevView& V, const u64* AQ, const u64* AB, const u64* BQ
 void launch_tensor_sum(const DevView& V, const u64* AQ, const u64* AB, const u64* BQ, const u64* BB,
                        const u64* cstQ, const u64* side, const u64* VP, u64* X, int L, bool square, bool init,
                        cudaStream_t st);
+// Constants of modulus switching from Q = q_0..q_{k-1} to Q_r = q_0..q_{r-1}
+// (Q' = q_r..q_{k-1} dropped), computed on the host for each r.
+struct ModSwitchArgs {
+  int k = 0, r = 0;
+  u64 h[PEPSI_MAXQ];                    // (Q' - 1)/2 mod q_p, every p
+  u64 ginv[PEPSI_MAXQ][PEPSI_MAXQ];     // Garner over Q': d_l^-1 mod d_j (l < j), d_j = q_{r+j}
+  u64 pw[PEPSI_MAXQ][PEPSI_MAXQ];       // prod_{l<j} d_l mod q_i, kept i
+  u64 qdinv[PEPSI_MAXQ];                // Q'^-1 mod q_i, kept i
+};
+// out[n][2][r][N] = round(c~ Q_r / Q) of in[n][2][k][N] (coefficient form)
+void launch_modswitch(const DevView& V, const ModSwitchArgs& M, const u64* in, u64* out, size_t n, cudaStream_t st);
 // Value plaintexts VP[L][k+kb][N] (NTT form) of the value rows vals[L][N]
 void launch_valgen(const DevView& V, const u32* vals, int L, u64* VP, cudaStream_t st);
 // acc[3][k][N] (+)= sum over L layers of D_l (NTT form over Q) times VP_l

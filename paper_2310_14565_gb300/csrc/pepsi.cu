@@ -7,6 +7,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <memory>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -72,6 +73,11 @@ struct pepsi_ctx {
   int chunk = 32;
   u32 rescale_cap = 1;      // most layers one rounding of the last products may cover
   bool value_margin = false;  // B also holds the value products under lazy rescaling
+  int resp = 0;               // primes of the evaluation's response (k: no switching)
+  // per prime count r < k: modulus-switching constants and the RNS
+  // constants of Q_r for decryption, built on first use
+  std::unique_ptr<ModSwitchArgs> ms_args[PEPSI_MAXQ + 1];
+  std::unique_ptr<RnsArgs> sub_args[PEPSI_MAXQ + 1];
   // profiling
   bool prof = false;
   std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> prof_ev;
@@ -450,8 +456,54 @@ cudaError_t prepare_request(pepsi_ctx* c, const u64* cts, u64* C, cudaStream_t s
   return cudaSuccess;
 }
 
+// Constants of modulus switching to the first r < k primes (host math):
+// Garner over the dropped primes d_j = q_{r+j}, their prefix products and
+// Q'^-1 mod the kept primes, (Q'-1)/2 mod every prime.
+const ModSwitchArgs& ms_args(pepsi_ctx* c, int r) {
+  if (!c->ms_args[r]) {
+    auto M = std::make_unique<ModSwitchArgs>();
+    M->k = c->k;
+    M->r = r;
+    const int m = c->k - r;
+    for (int p = 0; p < c->k; ++p) {  // (Q'-1)/2 mod q_p: Q' is odd, so (Q'-1)/2 = (Q' - 1) * 2^-1
+      const u64 q = c->Q[p];
+      u64 qd = 1;
+      for (int j = 0; j < m; ++j) qd = hostmath::mulmod(qd, c->Q[r + j] % q, q);
+      M->h[p] = hostmath::mulmod((qd + q - 1) % q, (q + 1) / 2, q);
+    }
+    for (int j = 0; j < m; ++j)
+      for (int l = 0; l < j; ++l) M->ginv[j][l] = hostmath::invmod(c->Q[r + l] % c->Q[r + j], c->Q[r + j]);
+    for (int i = 0; i < r; ++i) {
+      const u64 q = c->Q[i];
+      u64 w = 1;
+      for (int j = 0; j < m; ++j) {
+        M->pw[i][j] = w;
+        w = hostmath::mulmod(w, c->Q[r + j] % q, q);
+      }
+      M->qdinv[i] = hostmath::invmod(w, q);
+    }
+    c->ms_args[r] = std::move(M);
+  }
+  return *c->ms_args[r];
+}
+
+// RNS constants of the modulus Q_r = q_0..q_{r-1} (decryption over Q_r).
+const RnsArgs& sub_args(pepsi_ctx* c, int r) {
+  if (r == c->k) return c->rargs;
+  if (!c->sub_args[r]) {
+    auto A = std::make_unique<RnsArgs>(c->rargs);
+    std::vector<u64> Qr(c->Q.begin(), c->Q.begin() + r);
+    for (int j = 0; j < c->kb; ++j) A->pr[r + j] = c->rargs.pr[c->k + j];
+    hostmath::rns_constants(Qr, c->B, c->t, &A->rc);
+    A->k = r;
+    c->sub_args[r] = std::move(A);
+  }
+  return *c->sub_args[r];
+}
+
 // a7 output: ct = (h!)^-1 * R(A) to coefficient form, plus the mask of
-// Algorithm 5 in cardinality mode, copied to out (host or device).
+// Algorithm 5 in cardinality mode, switched to the response primes, copied
+// to out (host or device).
 cudaError_t finish_request(pepsi_ctx* c, EvalBufs& b, u64* acc, bool acc_ntt, int mode, u64 mask_seed, u64* out,
                            cudaStream_t st) {
   const size_t kN = (size_t)c->k * c->N;
@@ -462,6 +514,13 @@ cudaError_t finish_request(pepsi_ctx* c, EvalBufs& b, u64* acc, bool acc_ntt, in
   if (mode == PEPSI_MODE_CARDINALITY || mode == PEPSI_MODE_SUM) {
     Prof p(c, PC_CLIENT, st);
     launch_mask(c->V, mask_seed, b.out, st);
+  }
+  if (c->resp < c->k) {  // response modulus switching (b.R is free after the relinearisation)
+    {
+      Prof p(c, PC_CLIENT, st);
+      launch_modswitch(c->V, ms_args(c, c->resp), b.out, b.R, 1, st);
+    }
+    return copy_any(out, b.R, 2 * (size_t)c->resp * c->N * 8, st);
   }
   return copy_any(out, b.out, 2 * kN * 8, st);
 }
@@ -851,6 +910,11 @@ int pepsi_setup(const pepsi_params* params, uint64_t key_seed, pepsi_ctx** out) 
       return PEPSI_E_PARAM;
     }
   }
+  if (params->response_primes > (u32)c->k) {
+    delete c;
+    return PEPSI_E_PARAM;
+  }
+  c->resp = params->response_primes ? (int)params->response_primes : c->k;
   // lazy rescaling: runs of up to rescale_cap layers share one rounding
   {
     const u32 g = params->rescale_group;
@@ -1003,6 +1067,7 @@ int pepsi_get_info(const pepsi_ctx* c, pepsi_info* info) {
   info->log2_q = c->log2q;
   info->rescale_group = c->prm.rescale_group;
   info->rescale_cap = c->rescale_cap;
+  info->response_primes = (uint32_t)c->resp;
   return PEPSI_OK;
 }
 
@@ -1192,21 +1257,28 @@ int pepsi_eval_layers(pepsi_ctx* c, int set_id, const uint64_t* cts, uint32_t la
   return eval_core(c, set_id, cts, layer0, nl, PEPSI_MODE_INDICATOR, 0, nullptr, h_out, e_out, pick(c, stream));
 }
 
-int pepsi_decrypt(pepsi_ctx* c, const uint64_t* ct, uint32_t* slots, double* noise_budget_bits) {
-  if (!c || !ct || !slots) return PEPSI_E_PARAM;
+int pepsi_decrypt_primes(pepsi_ctx* c, const uint64_t* ct, uint32_t nprimes, uint32_t* slots,
+                         double* noise_budget_bits) {
+  if (!c || !ct || !slots || nprimes == 0 || nprimes > (uint32_t)c->k) return PEPSI_E_PARAM;
+  const int r = (int)nprimes;
   cudaStream_t st = c->stream;
   cudaError_t e = cudaSuccess;
-  const size_t N = c->N, ct2 = 2 * (size_t)c->k * N;
+  const size_t N = c->N, ct2 = 2 * (size_t)r * N;
   u64* din = (u64*)scratch(c, S_IN, ct2 * 8, &e);
-  u64* z = (u64*)scratch(c, S_DEC_Z, (size_t)c->k * N * 8, &e);
+  u64* z = (u64*)scratch(c, S_DEC_Z, (size_t)r * N * 8, &e);
   u32* m = (u32*)scratch(c, S_DEC_M, N * 4, &e);
   u32* sl = (u32*)scratch(c, S_DEC_SLOTS, N * 4, &e);
   unsigned long long* mx = (unsigned long long*)scratch(c, S_DEC_MAX, 8, &e);
   if (!din || !z || !m || !sl || !mx) return cuda_status(e);
   CKS(copy_any(din, ct, ct2 * 8, st));
+  // the same tables, viewed as the first r primes, with the constants of Q_r
+  const RnsArgs& A = sub_args(c, r);
+  DevView Vr = c->V;
+  Vr.k = r;
+  Vr.host_args = &A;
   {
     Prof p(c, PC_CLIENT, st, 3);
-    launch_decrypt(c->V, din, c->d_s_ntt, z, m, sl, mx, st);
+    launch_decrypt(Vr, din, c->d_s_ntt, z, m, sl, mx, st);
   }
   unsigned long long bits = 0;
   CKS(cudaMemcpyAsync(slots, sl, N * 4, cudaMemcpyDeviceToHost, st));
@@ -1215,11 +1287,55 @@ int pepsi_decrypt(pepsi_ctx* c, const uint64_t* ct, uint32_t* slots, double* noi
   if (e == cudaSuccess) e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_status(e);
   if (c->prof) prof_collect(c);
-  double maxr;
+  double maxr, log2qr = 0;
   memcpy(&maxr, &bits, 8);
-  const double budget = maxr > 0 ? c->log2q - 1.0 - std::log2(maxr) : INFINITY;
+  for (int i = 0; i < r; ++i) log2qr += std::log2((double)c->Q[i]);
+  const double budget = maxr > 0 ? log2qr - 1.0 - std::log2(maxr) : INFINITY;
   if (noise_budget_bits) *noise_budget_bits = budget;
   return budget > 0 ? PEPSI_OK : PEPSI_E_NOISE;
+}
+
+int pepsi_decrypt(pepsi_ctx* c, const uint64_t* ct, uint32_t* slots, double* noise_budget_bits) {
+  if (!c) return PEPSI_E_PARAM;
+  return pepsi_decrypt_primes(c, ct, (uint32_t)c->k, slots, noise_budget_bits);
+}
+
+int pepsi_mod_switch(pepsi_ctx* c, const uint64_t* ct, size_t n, uint32_t nprimes, uint64_t* out, void* stream) {
+  if (!c || !ct || !out || nprimes == 0 || nprimes > (uint32_t)c->k) return PEPSI_E_PARAM;
+  if (!n) return PEPSI_OK;
+  cudaStream_t st = pick(c, stream);
+  const size_t N = c->N, r = nprimes;
+  const size_t in_w = n * 2 * c->k * N, out_w = n * 2 * r * N;
+  if ((int)r == c->k) {
+    CKS(copy_any(out, ct, in_w * 8, st));
+  } else {
+    cudaError_t e = cudaSuccess;
+    const bool din = is_device_ptr(ct), dout = is_device_ptr(out);
+    const u64* src = ct;
+    u64* dst = out;
+    if (!din) {
+      u64* b = (u64*)scratch(c, S_CT, in_w * 8, &e);
+      if (!b) return cuda_status(e);
+      CKS(copy_any(b, ct, in_w * 8, st));
+      src = b;
+    }
+    if (!dout) {
+      dst = (u64*)scratch(c, S_TC, out_w * 8, &e);
+      if (!dst) return cuda_status(e);
+    }
+    {
+      Prof p(c, PC_CLIENT, st);
+      launch_modswitch(c->V, ms_args(c, (int)r), src, dst, n, st);
+    }
+    if (!dout) CKS(copy_any(out, dst, out_w * 8, st));
+  }
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_status(e);
+  if (!is_device_ptr(out)) {
+    e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_status(e);
+  }
+  return PEPSI_OK;
 }
 
 int pepsi_ntt(pepsi_ctx* c, uint64_t* polys, size_t count, int inverse, void* stream) {

@@ -58,6 +58,11 @@ def test_paper_result_decrypts_to_intersection(paper_case):
     assert int(slots.sum()) == 102
     oslots, obudget = oc.decrypt(s, out)
     assert np.array_equal(oslots, slots) and abs(obudget - budget) < 1e-9
+    # the one-prime response (about 0.11 MB) decrypts the same
+    sw = gc.mod_switch(out, 1)
+    assert np.array_equal(sw, oc.mod_switch(out, 1))
+    sws, swb = gc.decrypt(sw)
+    assert swb > 0 and np.array_equal(sws, slots)
     card = gc.eval(sid, cts, mode=1, mask_seed=5)
     cs, _ = gc.decrypt(card)
     assert int(cs.astype(np.int64).sum()) % 65537 == 102

@@ -124,6 +124,20 @@ typedef struct {
  * pepsi_destroy().  Errors: PEPSI_E_PARAM, PEPSI_E_NOMEM, PEPSI_E_CUDA. */
 int pepsi_setup(const pepsi_params* params, uint64_t key_seed, pepsi_ctx** out);
 
+/* Parameter selection, host only (Section 6.1).  Request size of a query:
+ * ceil(bins / N) * ell * N * log2 q bits, with ell = Eq. 1 (the smallest
+ * code length with C(ell, h) >= 2^lambda_bar) and (log2 N, log2 q) the
+ * smallest parameter set for Hamming weight h (Table 3: h = 1, 2, 3-4,
+ * 5-8, 9-16, 17-32, 33-64).  ell, log2_n, log2_q may be NULL.  Errors:
+ * PEPSI_E_PARAM for h outside 1..64, lambda_bar outside 1..62, bins = 0. */
+int pepsi_request_bits(uint32_t lambda_bar, uint32_t h, uint64_t bins, double* bits, uint64_t* ell,
+                       uint32_t* log2_n, uint32_t* log2_q);
+
+/* The communication-optimal Hamming weight (Section 6.1): the h in
+ * 1..h_max minimising pepsi_request_bits, a tie going to the smaller h
+ * (less computation).  Host only.  Errors: PEPSI_E_PARAM. */
+int pepsi_comm_optimal_h(uint32_t lambda_bar, uint64_t bins, uint32_t h_max, uint32_t* h);
+
 /* Fill *info with the context's derived parameters. */
 int pepsi_get_info(const pepsi_ctx* ctx, pepsi_info* info);
 

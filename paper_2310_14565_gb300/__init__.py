@@ -61,6 +61,9 @@ SYMBOLS = {
     "pepsi_setup": (C.c_int, [C.POINTER(Params), C.c_uint64, C.POINTER(C.c_void_p)]),
     "pepsi_get_info": (C.c_int, [C.c_void_p, C.POINTER(Info)]),
     "pepsi_set_rescale_group": (C.c_int, [C.c_void_p, C.c_uint32]),
+    "pepsi_request_bits": (C.c_int, [C.c_uint32, C.c_uint32, C.c_uint64, C.POINTER(C.c_double),
+                                     C.POINTER(C.c_uint64), C.POINTER(C.c_uint32), C.POINTER(C.c_uint32)]),
+    "pepsi_comm_optimal_h": (C.c_int, [C.c_uint32, C.c_uint64, C.c_uint32, C.POINTER(C.c_uint32)]),
     "pepsi_server_load": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t, C.POINTER(C.c_int)]),
     "pepsi_server_table": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p]),
     "pepsi_server_load_values": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_size_t, C.POINTER(C.c_int)]),
@@ -147,6 +150,21 @@ def _stream(s):
 def _check(rc, what):
     if rc != OK:
         raise PepsiError(rc, what)
+
+
+def request_bits(lambda_bar, h, bins):
+    """Request size model of Section 6.1: (bits, ell, log2 N, log2 q)."""
+    b, l, ln, lq = C.c_double(0), C.c_uint64(0), C.c_uint32(0), C.c_uint32(0)
+    _check(lib().pepsi_request_bits(lambda_bar, h, bins, C.byref(b), C.byref(l), C.byref(ln), C.byref(lq)),
+           "pepsi_request_bits")
+    return b.value, int(l.value), int(ln.value), int(lq.value)
+
+
+def comm_optimal_h(lambda_bar, bins, h_max=64):
+    """Hamming weight minimising the request size (ties to the smaller h)."""
+    h = C.c_uint32(0)
+    _check(lib().pepsi_comm_optimal_h(lambda_bar, bins, h_max, C.byref(h)), "pepsi_comm_optimal_h")
+    return int(h.value)
 
 
 def int_peak(wide=True):

@@ -399,3 +399,36 @@ int simple_hash(const Hasher& H, const u64* items, size_t n, u32 mu, std::vector
 }
 
 }  // namespace hostmath
+
+namespace hostmath {
+
+// Table 3: the smallest (log2 N, log2 q) for each range of Hamming weights.
+bool table3(u32 h, u32* log2n, u32* log2q) {
+  static const u32 rows[][4] = {{1, 1, 12, 72},   {2, 2, 13, 144},   {3, 4, 13, 168},  {5, 8, 13, 204},
+                                {9, 16, 14, 240}, {17, 32, 14, 276}, {33, 64, 14, 312}};
+  for (const auto& r : rows)
+    if (h >= r[0] && h <= r[1]) {
+      *log2n = r[2];
+      *log2q = r[3];
+      return true;
+    }
+  return false;
+}
+
+// Eq. 1 without a cap on ell: the smallest ell with C(ell, h) >= 2^lambda_bar
+// (C(ell, h) grows with ell, so a binary search over [h, h + 2^lambda_bar]).
+u64 code_length_any(u32 lambda_bar, u32 h) {
+  if (h == 0 || lambda_bar > 62) return 0;
+  const u64 need = 1ull << lambda_bar;
+  u64 lo = h, hi = (u64)h + need;
+  while (lo < hi) {
+    const u64 mid = lo + (hi - lo) / 2;
+    if (binom_sat(mid, h) >= need)
+      hi = mid;
+    else
+      lo = mid + 1;
+  }
+  return lo;
+}
+
+}  // namespace hostmath

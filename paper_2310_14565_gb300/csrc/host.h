@@ -28,6 +28,10 @@ void delta(const std::vector<u64>& Qp, u64 t, u64 v, u64* out);
 
 // Eq. 1
 u32 code_length(u32 lambda_bar, u32 h);
+// Eq. 1 for any ell (binary search), 0 for unsupported arguments
+u64 code_length_any(u32 lambda_bar, u32 h);
+// Table 3: (log2 N, log2 q) for Hamming weight h in 1..64
+bool table3(u32 h, u32* log2n, u32* log2q);
 u64 binom_sat(u64 n, u64 r);
 // server bin bound: the paper's values for its (n, b) pairs, else the
 // smallest mu with b * P[Binomial(3n, 1/b) > mu] <= 2^-40

@@ -1071,6 +1071,39 @@ int pepsi_get_info(const pepsi_ctx* c, pepsi_info* info) {
   return PEPSI_OK;
 }
 
+int pepsi_request_bits(uint32_t lambda_bar, uint32_t h, uint64_t bins, double* bits, uint64_t* ell,
+                       uint32_t* log2_n, uint32_t* log2_q) {
+  u32 ln = 0, lq = 0;
+  if (!bits || bins == 0 || lambda_bar == 0 || lambda_bar > 62 || !hostmath::table3(h, &ln, &lq))
+    return PEPSI_E_PARAM;
+  const u64 l = hostmath::code_length_any(lambda_bar, h);
+  if (!l) return PEPSI_E_PARAM;
+  const u64 N = 1ull << ln;
+  const u64 blocks = (bins + N - 1) / N;
+  *bits = (double)blocks * (double)l * (double)N * (double)lq;
+  if (ell) *ell = l;
+  if (log2_n) *log2_n = ln;
+  if (log2_q) *log2_q = lq;
+  return PEPSI_OK;
+}
+
+int pepsi_comm_optimal_h(uint32_t lambda_bar, uint64_t bins, uint32_t h_max, uint32_t* h) {
+  if (!h || h_max == 0 || h_max > 64) return PEPSI_E_PARAM;
+  double best = 0;
+  u32 arg = 0;
+  for (u32 w = 1; w <= h_max; ++w) {
+    double b = 0;
+    const int rc = pepsi_request_bits(lambda_bar, w, bins, &b, nullptr, nullptr, nullptr);
+    if (rc) return rc;
+    if (!arg || b < best) {  // strict: a tie keeps the smaller weight
+      best = b;
+      arg = w;
+    }
+  }
+  *h = arg;
+  return PEPSI_OK;
+}
+
 int pepsi_set_rescale_group(pepsi_ctx* c, uint32_t rescale_group) {
   if (!c) return PEPSI_E_PARAM;
   c->prm.rescale_group = rescale_group;

@@ -415,6 +415,81 @@ def run_ours(args):
     return 0
 
 
+def run_sweep_h(args):
+    """GPU counterpart of the paper's Figure 5 (Section 6.2): runtime of the
+    server computation for one client batch against one server batch
+    (gamma = mu = 1) as a function of the Hamming weight h, for effective
+    bitlengths 16, 32, 48.  (N, q) per Table 3 with q split evenly into
+    primes of at most 60 bits, ell by Eq. 1; h in {1, 2, 4, 8} (the weights
+    of the equality circuit); pairs whose code length exceeds the library's
+    65535 (16-bit codeword positions) are skipped.  Also the communication-optimal h of the request model."""
+    import torch
+
+    import paper_2310_14565_gb300 as pepsi
+    from paper_2310_14565_gb300 import build as _build
+    from paper_2310_14565_gb300.workload import make_sets
+
+    if not os.path.exists(pepsi.LIB_PATH):
+        _build.build()
+    torch.cuda.set_device(0)
+    rows = []
+    for lb in (16, 32, 48):
+        for h in (1, 2, 4, 8):
+            bits, ell, ln, lq = pepsi.request_bits(lb, h, 4096)
+            row = {"lambda_bar": lb, "h": h, "ell": ell, "log2_n": ln, "log2_q": lq,
+                   "request_mb": round(bits / 8e6, 3)}
+            if ell > 65535:
+                row["skipped"] = "code length above 65535"
+                rows.append(row)
+                continue
+            N = 1 << ln
+            k = -(-lq // 60)
+            prime_bits = [lq // k + (1 if i < lq % k else 0) for i in range(k)]
+            ctx = pepsi.Context(N=N, t=65537, prime_bits=prime_bits, h=h, ell=ell, lambda_bar=lb, mu=1,
+                                hash_key=HASH_KEY, key_seed=KEY_SEED)
+            for seed in range(100, 150):  # mu = 1: redraw until no two server items share a bin
+                sets = make_sets(N // 2, 8, 4, bits=64, seed_items=seed, seed_plant=seed + 1)
+                try:
+                    sid = ctx.server_load(sets.server)
+                    break
+                except pepsi.PepsiError as err:
+                    if err.code != pepsi.E_BIN_OVERFLOW:
+                        raise
+            cts_np, where = ctx.query(sets.client, ENC_SEED)
+            cts = torch.from_numpy(cts_np.view("int64")).cuda()
+            out = torch.empty((2, k, N), dtype=torch.int64, device="cuda")
+            stream = torch.cuda.current_stream()
+            for _ in range(3):
+                ctx.eval(sid, cts, out=out)
+            torch.cuda.synchronize()
+            slots, budget = ctx.decrypt(out)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            reps = 10
+            e0.record(stream)
+            for _ in range(reps):
+                ctx.eval(sid, cts, out=out)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            row.update({"prime_bits": prime_bits, "ms": round(e0.elapsed_time(e1) / reps, 3),
+                        "noise_budget_bits": round(budget, 2), "correct": bool(int(slots.sum()) == 4 and budget > 0)})
+            rows.append(row)
+            ctx.close()
+            del cts, out
+    comp = {}
+    for lb in (16, 32, 48):
+        done = [r for r in rows if r["lambda_bar"] == lb and r.get("correct")]
+        comp[lb] = min(done, key=lambda r: (r["ms"], r["h"]))["h"] if done else None
+    line = {"metric": "server computation ms per (client batch, server batch) vs Hamming weight (Figure 5 on GB300)",
+            "unit": "ms", "data": "synthetic", "n_gpus": 1,
+            "config": {"workload": "gamma = mu = 1, b = N bins, N and q per Table 3, m = N/2 client items, "
+                                   "8 server items (4 shared), per-layer rounding"},
+            "rows": rows, "comp_optimal_h_of_1_2_4_8": comp,
+            "comm_optimal_h": {lb: pepsi.comm_optimal_h(lb, 4096) for lb in (16, 32, 48)},
+            "paper_comp_optimal_h": {"16": 4, "32": 8, "48": 8, "cite": "Figure 5 caption (CPU, SEAL, one thread)"}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def stored_traffic():
     """DRAM bytes per k_mac launch from the committed ncu summary, if it was
     taken on the current kernel source (else None)."""
@@ -450,7 +525,7 @@ def main():
     ap.add_argument("--rescale", choices=["all", "layer"], default="all",
                     help="all: one rounding of the layers' last products per evaluation (lazy rescaling); "
                          "layer: every product rounded (textbook FV words)")
-    ap.add_argument("--case", choices=["paper", "small", "large"], default="paper",
+    ap.add_argument("--case", choices=["paper", "small", "large", "sweep-h"], default="paper",
                     help="small: the same kernels on 2^14 server items (mu=35), for profiler captures; "
                          "large: N=16384, 8 primes, h=8, 4096 x 2^24 items, streamed plaintexts")
     args = ap.parse_args()
@@ -467,6 +542,8 @@ def main():
         args.no_cpu_baseline = True
     if args.warmup < 3:
         args.warmup = 3
+    if args.case == "sweep-h":
+        return run_sweep_h(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

@@ -325,3 +325,18 @@ def test_partially_resident_table():
     assert np.array_equal(outs[0], want) and np.array_equal(outs[1], want)
     P = g2.server_plaintexts(sid2, 3, 2)
     assert np.array_equal(P[1, 0], oc.server_plaintext(Ts, 4, 0))
+
+
+@pytest.mark.parametrize("h,bits,N", [(1, [36, 36], 64), (2, [48, 48, 48], 64), (4, [56, 56, 56], 64),
+                                      (8, [51, 51, 51, 51], 64)])
+def test_table3_prime_sets_match_oracle(h, bits, N):
+    """The prime splits of Table 3's coefficient moduli (72, 144, 168, 204
+    bits) used by the Hamming-weight sweep: words equal to the oracle."""
+    oc, gc, s, rlk, sets, Ts, cts, where, sid = _psi_case(N, bits, h, 12, mu=3, m=min(20, N // 2), n=40,
+                                                          planted=3, chunk=2)
+    want = oc.eval(rlk, cts, Ts)
+    got = gc.eval(sid, cts)
+    assert np.array_equal(got, want)
+    slots, b = gc.decrypt(got)
+    assert b > 0
+    assert np.array_equal(slots, hashed_indicator(sets.client, sets.server, where, N, 12))

@@ -289,6 +289,15 @@ int pepsi_relin_noalloc(pepsi_ctx* ctx, const uint64_t* in, size_t n, uint64_t* 
  * in coefficient form rlk[k][2][k][N] (host); either may be NULL. */
 int pepsi_export_keys(pepsi_ctx* ctx, int8_t* s, uint64_t* rlk);
 
+/* Test of the bounded device waits (no counterpart in the paper): one
+ * block waits on an mbarrier with the helper every multiply-accumulate
+ * uses.  arrive = 1: the barrier completes and the call returns PEPSI_OK.
+ * arrive = 0: nothing completes it, the wait gives up after about one
+ * second, the kernel sets the context's error word and returns, and the
+ * call returns PEPSI_E_TIMEOUT; the context stays usable (the error word
+ * is cleared).  Synchronises the context's stream. */
+int pepsi_wait_probe(pepsi_ctx* ctx, int arrive);
+
 /* Measurement helper (no paper counterpart): the integer-pipe throughput of
  * the multiply forms the kernels use, measured on the current device with
  * independent chains on every SM.  wide = 1: 32x32->64 multiply-adds

@@ -61,6 +61,7 @@ SYMBOLS = {
     "pepsi_setup": (C.c_int, [C.POINTER(Params), C.c_uint64, C.POINTER(C.c_void_p)]),
     "pepsi_get_info": (C.c_int, [C.c_void_p, C.POINTER(Info)]),
     "pepsi_set_rescale_group": (C.c_int, [C.c_void_p, C.c_uint32]),
+    "pepsi_wait_probe": (C.c_int, [C.c_void_p, C.c_int]),
     "pepsi_request_bits": (C.c_int, [C.c_uint32, C.c_uint32, C.c_uint64, C.POINTER(C.c_double),
                                      C.POINTER(C.c_uint64), C.POINTER(C.c_uint32), C.POINTER(C.c_uint32)]),
     "pepsi_comm_optimal_h": (C.c_int, [C.c_uint32, C.c_uint64, C.c_uint32, C.POINTER(C.c_uint32)]),
@@ -214,6 +215,11 @@ class Context:
     # ---- shapes
     def ct_words(self, comps=2):
         return comps * self.k * self.N
+
+    def wait_probe(self, arrive):
+        """Status code of the bounded-wait test (OK, or E_TIMEOUT when
+        nothing completes the barrier)."""
+        return lib().pepsi_wait_probe(self._h, int(arrive))
 
     def set_rescale_group(self, group):
         """Rounding run length of later evaluations (1: per layer;

@@ -57,6 +57,8 @@ struct ModSwitchArgs {
   u64 pw[PEPSI_MAXQ][PEPSI_MAXQ];       // prod_{l<j} d_l mod q_i, kept i
   u64 qdinv[PEPSI_MAXQ];                // Q'^-1 mod q_i, kept i
 };
+// bounded-wait test: *err = 1 after about one second unless arrive != 0
+void launch_wait_probe(int arrive, int* err, cudaStream_t st);
 // out[n][2][r][N] = round(c~ Q_r / Q) of in[n][2][k][N] (coefficient form)
 void launch_modswitch(const DevView& V, const ModSwitchArgs& M, const u64* in, u64* out, size_t n, cudaStream_t st);
 // Value plaintexts VP[L][k+kb][N] (NTT form) of the value rows vals[L][N]

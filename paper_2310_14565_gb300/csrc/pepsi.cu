@@ -1474,6 +1474,15 @@ int pepsi_export_keys(pepsi_ctx* c, int8_t* s, uint64_t* rlk) {
   return cuda_status(cudaStreamSynchronize(st));
 }
 
+int pepsi_wait_probe(pepsi_ctx* c, int arrive) {
+  if (!c) return PEPSI_E_PARAM;
+  launch_wait_probe(arrive, c->d_err, c->stream);
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  if (e == cudaSuccess) e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_status(e);
+  return take_error_flag(c) ? PEPSI_E_TIMEOUT : PEPSI_OK;
+}
+
 int pepsi_int_peak(int wide, double* ops_per_s) {
   if (!ops_per_s) return PEPSI_E_PARAM;
   *ops_per_s = measure_int_peak(wide);

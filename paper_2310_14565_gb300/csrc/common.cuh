@@ -73,8 +73,8 @@ struct RnsArgs {
 struct DevView {
   int N, logN, k, kb, tidx;  // tidx: index of t among the moduli (= k + kb)
   const DevPrime* pr;        // [k + kb + 1]
-  const u64 *tw, *tws;       // [np][N] psi^brev(i) and Shoup companion
-  const u64 *itw, *itws;     // [np][N] psi^-brev(i) and Shoup companion
+  const ulonglong2* twp;     // [np][N] (psi^brev(i), its Shoup companion)
+  const ulonglong2* itwp;    // [np][N] (psi^-brev(i), its Shoup companion)
   const RnsConst* rc;
   const RnsArgs* host_args;  // host copy for by-value launches (not dereferenced on the device)
 };

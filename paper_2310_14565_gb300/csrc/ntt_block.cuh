@@ -25,20 +25,10 @@ __device__ __forceinline__ int nsw(int x) { return x ^ ((x >> 4) & 15); }
 
 namespace nttd {
 
-// Phase sizes for log2 N stages: 3-stage phases, then the remainder.
-__device__ __forceinline__ int phase_plan(int logN, int* r) {
-  int n = 0, rest = logN;
-  while (rest >= 3) {
-    r[n++] = 3;
-    rest -= 3;
-  }
-  if (rest) r[n++] = rest;
-  return n;
-}
-
+// Twiddles come as (w, Shoup companion) pairs, one 16-byte load each.
 template <int RR>
-__device__ __forceinline__ void fwd_phase(u64* a, int N, int logN, int s0, u64 q, const u64* __restrict__ tw,
-                                          const u64* __restrict__ tws, bool last) {
+__device__ __forceinline__ void fwd_phase(u64* a, int N, int logN, int s0, u64 q, const ulonglong2* __restrict__ tw,
+                                          bool last) {
   constexpr int E = 1 << RR;
   const int slog = logN - s0 - RR;  // log2 of the element stride inside a group
   const int groups = N >> RR;
@@ -56,16 +46,13 @@ __device__ __forceinline__ void fwd_phase(u64* a, int N, int logN, int s0, u64 q
       // butterfly i splits into a group part and i >> (RR - ss): stage ss of
       // the phase needs only 2^ss distinct twiddles
       const int tbase = (1 << s) + (base >> (logN - s));
-      u64 Wt[1 << (RR - 1)], Wst[1 << (RR - 1)];
+      ulonglong2 Wt[1 << (RR - 1)];
 #pragma unroll
-      for (int d = 0; d < (1 << ss); ++d) {
-        Wt[d] = __ldg(tw + tbase + d);
-        Wst[d] = __ldg(tws + tbase + d);
-      }
+      for (int d = 0; d < (1 << ss); ++d) Wt[d] = __ldg(tw + tbase + d);
 #pragma unroll
       for (int i = 0; i < E; ++i) {
         if ((i & half) == 0) {
-          const u64 W = Wt[i >> (RR - ss)], Ws = Wst[i >> (RR - ss)];
+          const u64 W = Wt[i >> (RR - ss)].x, Ws = Wt[i >> (RR - ss)].y;
           u64 U = x[i];
           U = U >= q2 ? U - q2 : U;
           const u64 T = shoup_lazy(x[i + half], W, Ws, q);
@@ -88,8 +75,8 @@ __device__ __forceinline__ void fwd_phase(u64* a, int N, int logN, int s0, u64 q
 }
 
 template <int RR>
-__device__ __forceinline__ void inv_phase(u64* a, int N, int logN, int s0, u64 q, const u64* __restrict__ itw,
-                                          const u64* __restrict__ itws, bool last, u64 ninv, u64 ninvs) {
+__device__ __forceinline__ void inv_phase(u64* a, int N, int logN, int s0, u64 q, const ulonglong2* __restrict__ itw,
+                                          bool last, u64 ninv, u64 ninvs) {
   constexpr int E = 1 << RR;
   const int slog = logN - s0 - RR;
   const int groups = N >> RR;
@@ -104,16 +91,13 @@ __device__ __forceinline__ void inv_phase(u64* a, int N, int logN, int s0, u64 q
       const int s = s0 + ss;
       const int half = 1 << (RR - 1 - ss);
       const int tbase = (1 << s) + (base >> (logN - s));
-      u64 Wt[1 << (RR - 1)], Wst[1 << (RR - 1)];
+      ulonglong2 Wt[1 << (RR - 1)];
 #pragma unroll
-      for (int d = 0; d < (1 << ss); ++d) {
-        Wt[d] = __ldg(itw + tbase + d);
-        Wst[d] = __ldg(itws + tbase + d);
-      }
+      for (int d = 0; d < (1 << ss); ++d) Wt[d] = __ldg(itw + tbase + d);
 #pragma unroll
       for (int i = 0; i < E; ++i) {
         if ((i & half) == 0) {
-          const u64 W = Wt[i >> (RR - ss)], Ws = Wst[i >> (RR - ss)];
+          const u64 W = Wt[i >> (RR - ss)].x, Ws = Wt[i >> (RR - ss)].y;
           const u64 U = x[i], V = x[i + half];
           u64 S = U + V;
           S = S >= q2 ? S - q2 : S;
@@ -136,48 +120,39 @@ __device__ __forceinline__ void inv_phase(u64* a, int N, int logN, int s0, u64 q
 
 }  // namespace nttd
 
-// a[0..N) in [0, 4q) on entry, [0, q) on exit.
-__device__ __forceinline__ void ntt_fwd_block(u64* a, int N, int logN, u64 q, const u64* __restrict__ tw,
-                                              const u64* __restrict__ tws) {
-  int r[16];
-  const int np = nttd::phase_plan(logN, r);
+// a[0..N) in [0, 4q) on entry, [0, q) on exit.  Phases of three stages
+// from stage 0, then the remaining one or two.
+__device__ __forceinline__ void ntt_fwd_block(u64* a, int N, int logN, u64 q, const ulonglong2* __restrict__ tw) {
   int s0 = 0;
-  for (int p = 0; p < np; ++p) {
-    const bool last = p == np - 1;
-    switch (r[p]) {
-      case 3: nttd::fwd_phase<3>(a, N, logN, s0, q, tw, tws, last); break;
-      case 2: nttd::fwd_phase<2>(a, N, logN, s0, q, tw, tws, last); break;
-      default: nttd::fwd_phase<1>(a, N, logN, s0, q, tw, tws, last); break;
-    }
-    s0 += r[p];
+  for (; s0 + 3 <= logN; s0 += 3) {
+    nttd::fwd_phase<3>(a, N, logN, s0, q, tw, s0 + 3 == logN);
     __syncthreads();
   }
+  const int rem = logN - s0;
+  if (rem == 2) nttd::fwd_phase<2>(a, N, logN, s0, q, tw, true);
+  if (rem == 1) nttd::fwd_phase<1>(a, N, logN, s0, q, tw, true);
+  if (rem) __syncthreads();
 }
 
-// a[0..N) in [0, 2q) on entry, [0, q) on exit.
-__device__ __forceinline__ void ntt_inv_block(u64* a, int N, int logN, u64 q, const u64* __restrict__ itw,
-                                              const u64* __restrict__ itws, u64 ninv, u64 ninvs) {
-  int r[16];
-  const int np = nttd::phase_plan(logN, r);
-  int s0 = logN;
-  for (int p = np - 1; p >= 0; --p) {
-    s0 -= r[p];
-    const bool last = p == 0;
-    switch (r[p]) {
-      case 3: nttd::inv_phase<3>(a, N, logN, s0, q, itw, itws, last, ninv, ninvs); break;
-      case 2: nttd::inv_phase<2>(a, N, logN, s0, q, itw, itws, last, ninv, ninvs); break;
-      default: nttd::inv_phase<1>(a, N, logN, s0, q, itw, itws, last, ninv, ninvs); break;
-    }
+// a[0..N) in [0, 2q) on entry, [0, q) on exit.  The forward phases in
+// reverse order: the remainder first, then three stages at a time.
+__device__ __forceinline__ void ntt_inv_block(u64* a, int N, int logN, u64 q, const ulonglong2* __restrict__ itw,
+                                              u64 ninv, u64 ninvs) {
+  const int rem = logN % 3;
+  int s0 = logN - rem;
+  if (rem == 2) nttd::inv_phase<2>(a, N, logN, s0, q, itw, s0 == 0, ninv, ninvs);
+  if (rem == 1) nttd::inv_phase<1>(a, N, logN, s0, q, itw, s0 == 0, ninv, ninvs);
+  if (rem) __syncthreads();
+  for (s0 -= 3; s0 >= 0; s0 -= 3) {
+    nttd::inv_phase<3>(a, N, logN, s0, q, itw, s0 == 0, ninv, ninvs);
     __syncthreads();
   }
 }
 
 __device__ __forceinline__ void ntt_fwd_view(u64* a, const DevView& V, int pi) {
-  const size_t off = (size_t)pi * V.N;
-  ntt_fwd_block(a, V.N, V.logN, V.pr[pi].q, V.tw + off, V.tws + off);
+  ntt_fwd_block(a, V.N, V.logN, V.pr[pi].q, V.twp + (size_t)pi * V.N);
 }
 __device__ __forceinline__ void ntt_inv_view(u64* a, const DevView& V, int pi) {
-  const size_t off = (size_t)pi * V.N;
   const DevPrime P = V.pr[pi];
-  ntt_inv_block(a, V.N, V.logN, P.q, V.itw + off, V.itws + off, P.ninv, P.ninvs);
+  ntt_inv_block(a, V.N, V.logN, P.q, V.itwp + (size_t)pi * V.N, P.ninv, P.ninvs);
 }

@@ -58,7 +58,7 @@ struct pepsi_ctx {
   cudaEvent_t aux_ev[4] = {};
   // device tables and keys
   DevPrime* d_pr = nullptr;
-  u64 *d_tw = nullptr, *d_tws = nullptr, *d_itw = nullptr, *d_itws = nullptr;
+  ulonglong2 *d_twp = nullptr, *d_itwp = nullptr;  // twiddles interleaved with their Shoup companions
   RnsConst* d_rc = nullptr;
   u64* d_binom = nullptr;
   int8_t* d_s = nullptr;
@@ -853,10 +853,8 @@ void pepsi_destroy(pepsi_ctx* c) {
     cudaEventDestroy(pe.second.second);
   }
   cudaFree(c->d_pr);
-  cudaFree(c->d_tw);
-  cudaFree(c->d_tws);
-  cudaFree(c->d_itw);
-  cudaFree(c->d_itws);
+  cudaFree(c->d_twp);
+  cudaFree(c->d_itwp);
   cudaFree(c->d_rc);
   cudaFree(c->d_binom);
   cudaFree(c->d_s);
@@ -998,10 +996,15 @@ int pepsi_setup(const pepsi_params* params, uint64_t key_seed, pepsi_ctx** out) 
   cudaError_t e = cudaStreamCreate(&c->stream);
   if (e == cudaSuccess) e = kernels_init(c->N);
   if (e == cudaSuccess) e = upload((void**)&c->d_pr, pr.data(), pr.size() * sizeof(DevPrime));
-  if (e == cudaSuccess) e = upload((void**)&c->d_tw, tw.data(), tw.size() * 8);
-  if (e == cudaSuccess) e = upload((void**)&c->d_tws, tws.data(), tws.size() * 8);
-  if (e == cudaSuccess) e = upload((void**)&c->d_itw, itw.data(), itw.size() * 8);
-  if (e == cudaSuccess) e = upload((void**)&c->d_itws, itws.data(), itws.size() * 8);
+  {  // (twiddle, Shoup companion) pairs: one 16-byte load per butterfly group
+    std::vector<ulonglong2> twp(tw.size()), itwp(tw.size());
+    for (size_t i = 0; i < tw.size(); ++i) {
+      twp[i] = make_ulonglong2(tw[i], tws[i]);
+      itwp[i] = make_ulonglong2(itw[i], itws[i]);
+    }
+    if (e == cudaSuccess) e = upload((void**)&c->d_twp, twp.data(), twp.size() * sizeof(ulonglong2));
+    if (e == cudaSuccess) e = upload((void**)&c->d_itwp, itwp.data(), itwp.size() * sizeof(ulonglong2));
+  }
   if (e == cudaSuccess) e = upload((void**)&c->d_rc, &rcst, sizeof(rcst));
   if (e == cudaSuccess) e = upload((void**)&c->d_binom, binom.data(), binom.size() * 8);
   if (e == cudaSuccess) e = upload((void**)&c->d_consts, consts.data(), consts.size() * 8);
@@ -1021,10 +1024,8 @@ int pepsi_setup(const pepsi_params* params, uint64_t key_seed, pepsi_ctx** out) 
   c->V.kb = c->kb;
   c->V.tidx = c->k + c->kb;
   c->V.pr = c->d_pr;
-  c->V.tw = c->d_tw;
-  c->V.tws = c->d_tws;
-  c->V.itw = c->d_itw;
-  c->V.itws = c->d_itws;
+  c->V.twp = c->d_twp;
+  c->V.itwp = c->d_itwp;
   c->V.rc = c->d_rc;
   for (int i = 0; i < c->k + c->kb; ++i) c->rargs.pr[i] = pr[i];
   c->rargs.rc = rcst;

@@ -36,9 +36,9 @@ __global__ void __launch_bounds__(NTT_MAX_THREADS, 2) k_ntt(DevView V, const u64
   for (int x = threadIdx.x; x < N; x += blockDim.x) sm[nsw(x)] = s[x];
   __syncthreads();
   if (FWD)
-    ntt_fwd_view(sm, V, p0 + pl);
+    ntt_fwd_fast(sm, V, p0 + pl);
   else
-    ntt_inv_view(sm, V, p0 + pl);
+    ntt_inv_fast(sm, V, p0 + pl);
   for (int x = threadIdx.x; x < N; x += blockDim.x) d[x] = sm[nsw(x)];
 }
 
@@ -107,7 +107,7 @@ __global__ void __launch_bounds__(NTT_MAX_THREADS, 2) k_ptgen(DevView V, const u
       poly[nsw(i)] = (bits[jj * words + (s >> 5)] >> (s & 31)) & 1u;
     }
     __syncthreads();
-    ntt_inv_view(poly, V, V.tidx);
+    ntt_inv_fast(poly, V, V.tidx);
     for (int i = threadIdx.x; i < N; i += blockDim.x) mbuf[i] = (u32)poly[nsw(i)];
     __syncthreads();
     for (int p = 0; p < k; ++p) {
@@ -117,7 +117,7 @@ __global__ void __launch_bounds__(NTT_MAX_THREADS, 2) k_ptgen(DevView V, const u
         poly[nsw(i)] = m <= thalf ? m : q - (t - m);
       }
       __syncthreads();
-      ntt_fwd_view(poly, V, p);
+      ntt_fwd_fast(poly, V, p);
       u64* out = P + (((size_t)l * ell + j) * k + p) * N;
       const u64 sp = V.pr[p].split;
       for (int i = threadIdx.x; i < N; i += blockDim.x) out[i] = to_split(poly[nsw(i)], sp);
@@ -850,7 +850,7 @@ __global__ void __launch_bounds__(NTT_MAX_THREADS, 2) k_relin_ntt(DevView V, con
     sm[nsw(x)] = w >= pj.q ? barrett64(w, pj) : w;
   }
   __syncthreads();
-  ntt_fwd_view(sm, V, j);
+  ntt_fwd_fast(sm, V, j);
   u64* out = DG + r * N;
   for (int x = threadIdx.x; x < N; x += blockDim.x) out[x] = sm[nsw(x)];
 }

@@ -156,3 +156,64 @@ __device__ __forceinline__ void ntt_inv_view(u64* a, const DevView& V, int pi) {
   const DevPrime P = V.pr[pi];
   ntt_inv_block(a, V.N, V.logN, P.q, V.itwp + (size_t)pi * V.N, P.ninv, P.ninvs);
 }
+
+// The same transforms with log2 N fixed at compile time: the phase bounds,
+// strides and shift amounts become constants.
+template <int LOGN>
+__device__ __forceinline__ void ntt_fwd_fixed(u64* a, u64 q, const ulonglong2* __restrict__ tw) {
+  constexpr int N = 1 << LOGN, REM = LOGN % 3;
+#pragma unroll
+  for (int s0 = 0; s0 + 3 <= LOGN; s0 += 3) {
+    nttd::fwd_phase<3>(a, N, LOGN, s0, q, tw, s0 + 3 == LOGN);
+    __syncthreads();
+  }
+  if constexpr (REM == 2) {
+    nttd::fwd_phase<2>(a, N, LOGN, LOGN - 2, q, tw, true);
+    __syncthreads();
+  }
+  if constexpr (REM == 1) {
+    nttd::fwd_phase<1>(a, N, LOGN, LOGN - 1, q, tw, true);
+    __syncthreads();
+  }
+}
+template <int LOGN>
+__device__ __forceinline__ void ntt_inv_fixed(u64* a, u64 q, const ulonglong2* __restrict__ itw, u64 ninv,
+                                              u64 ninvs) {
+  constexpr int N = 1 << LOGN, REM = LOGN % 3, TOP = LOGN - REM;
+  if constexpr (REM == 2) {
+    nttd::inv_phase<2>(a, N, LOGN, TOP, q, itw, TOP == 0, ninv, ninvs);
+    __syncthreads();
+  }
+  if constexpr (REM == 1) {
+    nttd::inv_phase<1>(a, N, LOGN, TOP, q, itw, TOP == 0, ninv, ninvs);
+    __syncthreads();
+  }
+#pragma unroll
+  for (int s0 = TOP - 3; s0 >= 0; s0 -= 3) {
+    nttd::inv_phase<3>(a, N, LOGN, s0, q, itw, s0 == 0, ninv, ninvs);
+    __syncthreads();
+  }
+}
+
+// ntt_fwd_view / ntt_inv_view with the ring sizes of the workloads
+// (N = 4096, 8192, 16384) compiled for their fixed size.
+__device__ __forceinline__ void ntt_fwd_fast(u64* a, const DevView& V, int pi) {
+  const ulonglong2* tw = V.twp + (size_t)pi * V.N;
+  const u64 q = V.pr[pi].q;
+  switch (V.logN) {
+    case 12: ntt_fwd_fixed<12>(a, q, tw); break;
+    case 13: ntt_fwd_fixed<13>(a, q, tw); break;
+    case 14: ntt_fwd_fixed<14>(a, q, tw); break;
+    default: ntt_fwd_block(a, V.N, V.logN, q, tw); break;
+  }
+}
+__device__ __forceinline__ void ntt_inv_fast(u64* a, const DevView& V, int pi) {
+  const ulonglong2* itw = V.itwp + (size_t)pi * V.N;
+  const DevPrime P = V.pr[pi];
+  switch (V.logN) {
+    case 12: ntt_inv_fixed<12>(a, P.q, itw, P.ninv, P.ninvs); break;
+    case 13: ntt_inv_fixed<13>(a, P.q, itw, P.ninv, P.ninvs); break;
+    case 14: ntt_inv_fixed<14>(a, P.q, itw, P.ninv, P.ninvs); break;
+    default: ntt_inv_block(a, V.N, V.logN, P.q, itw, P.ninv, P.ninvs); break;
+  }
+}

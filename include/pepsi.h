@@ -100,6 +100,12 @@ typedef struct {
                               pepsi_eval_batch switch the result to q_0..q_{r-1}
                               (pepsi_mod_switch), out_ct [2][r][N]; 0 = k, no switching.
                               r = 1 gives the one-prime response (2 N 8 bytes) */
+  uint32_t bins;           /* number of bins b: 0 = N; else a power of two N * B, B <= 1024.
+                              The b bins form B blocks of N slots (Section 4: ceil(b/N)
+                              ciphertexts per code bit): the request holds B * ell
+                              ciphertexts [B][ell][2][k][N], every server layer one block of
+                              plaintexts per request block, and the response B ciphertexts
+                              [B][2][r][N], block j answering bins j*N .. j*N + N - 1 */
 } pepsi_params;
 
 /* Derived values of a context (for callers and tests). */
@@ -114,6 +120,7 @@ typedef struct {
   uint32_t rescale_group;/* rescale_group as given (0 and 1 both mean per layer) */
   uint32_t rescale_cap;  /* most layers one rounding may cover (1: per-layer rounding only) */
   uint32_t response_primes; /* primes of the evaluation's response (k: not switched) */
+  uint32_t bins, blocks;     /* b = blocks * N bins */
 } pepsi_info;
 
 /* Setup (Section 4, parameters of Tables 2-3): derives ell (Eq. 1), the
@@ -169,22 +176,23 @@ int pepsi_server_load(pepsi_ctx* ctx, const uint64_t* items, size_t n, int* set_
 int pepsi_server_load_values(pepsi_ctx* ctx, const uint64_t* items, const uint32_t* values, size_t n,
                              int* set_id);
 
-/* Copy the value table of a set loaded with values: out[mu][N] (host). */
+/* Copy the value table of a set loaded with values: out[mu][b] (host). */
 int pepsi_server_values(pepsi_ctx* ctx, int set_id, uint32_t* out);
 
-/* Copy the raw server table T_s of a set: out[mu][N] (host), entries are
+/* Copy the raw server table T_s of a set: out[mu][b] (host, b bins), entries are
  * x_L values or UINT64_MAX for dummies. */
 int pepsi_server_table(pepsi_ctx* ctx, int set_id, uint64_t* out);
 
 /* Copy server plaintexts pt_s[layer][j] for layers [layer0, layer0+nl) in
- * NTT form (value at psi^(2 brev(i)+1) in slot i): out[nl][ell][k][N],
+ * NTT form (value at psi^(2 brev(i)+1) in slot i): out[B][nl][ell][k][N] (B blocks),
  * host or device. */
 int pepsi_server_plaintexts(pepsi_ctx* ctx, int set_id, uint32_t layer0, uint32_t nl, uint64_t* out,
                             void* stream);
 
 /* Client request (App. Alg 7, client side): cuckoo hashing without stash
  * (3 hashes, eviction bound 1000), CW-Encode, batching, symmetric FV
- * encryption under s with randomness from enc_seed.  cts: [ell][2][k][N]
+ * encryption under s with randomness from enc_seed (ciphertext i of the
+ * request draws from stream index i).  cts: [B][ell][2][k][N]
  * coefficient form (host or device).  bin_of_item: host int32[m], the bin
  * that holds each item.  Errors: PEPSI_E_CUCKOO_FAIL, PEPSI_E_PARAM. */
 int pepsi_query(pepsi_ctx* ctx, const uint64_t* items, size_t m, uint64_t enc_seed, uint64_t* cts,
@@ -197,9 +205,11 @@ int pepsi_query(pepsi_ctx* ctx, const uint64_t* items, size_t m, uint64_t enc_se
  * SUM weight layer i' by its value plaintext val_s[i'] (Algorithms 4-5):
  * with per-layer rounding val_s[i'] multiplies the rounded e; with lazy
  * rescaling it multiplies the exact product before the run's rounding.
- * cts: [ell][2][k][N] coefficient form, host or device.
- * out_ct: [2][r][N] coefficient form, host or device, r =
- * pepsi_info.response_primes (k unless the response is switched).
+ * cts: [B][ell][2][k][N] coefficient form, host or device.
+ * out_ct: [B][2][r][N] coefficient form, host or device, with B blocks and
+ * r = pepsi_info.response_primes (k unless the response is switched);
+ * block j of the response answers request block j, its mask drawn from
+ * mask_seed + j.
  * Errors: PEPSI_E_PARAM (bad set/mode), PEPSI_E_NOMEM, PEPSI_E_CUDA. */
 int pepsi_eval(pepsi_ctx* ctx, int set_id, const uint64_t* cts, int mode, uint64_t mask_seed, uint64_t* out_ct,
                void* stream);
@@ -210,14 +220,14 @@ int pepsi_eval(pepsi_ctx* ctx, int set_id, const uint64_t* cts, int mode, uint64
  * Requests on the same set are processed in groups of up to 2 whose
  * multiply-accumulate reads the server plaintexts once for the whole group
  * (or generates each plaintext chunk once, when the table is not
- * resident).  cts[i]: [ell][2][k][N], out_cts[i]: [2][k][N], each host or
+ * resident).  cts[i]: [B][ell][2][k][N], out_cts[i]: [B][2][r][N], each host or
  * device.  Errors as pepsi_eval. */
 int pepsi_eval_batch(pepsi_ctx* ctx, int nq, const int* set_ids, const uint64_t* const* cts, const int* modes,
                      const uint64_t* mask_seeds, uint64_t* const* out_cts, void* stream);
 
 /* The same pipeline on layers [layer0, layer0+nl) only, returning the
- * per-layer intermediate words: h_out[nl][2][k][N] (h', coefficient form)
- * and e_out[nl][3][k][N] (the un-relinearised equality ciphertexts), host
+ * per-layer intermediate words: h_out[B][nl][2][k][N] (h', coefficient form)
+ * and e_out[B][nl][3][k][N] (the un-relinearised equality ciphertexts), host
  * or device; either may be NULL.  For sampled parity checks. */
 int pepsi_eval_layers(pepsi_ctx* ctx, int set_id, const uint64_t* cts, uint32_t layer0, uint32_t nl,
                       uint64_t* h_out, uint64_t* e_out, void* stream);

@@ -268,15 +268,18 @@ class Ctx:
     """One BFV parameter set (N, t, prime bit sizes) plus PEPSI's code and
     hashing parameters."""
 
-    def __init__(self, N, t, prime_bits, h=2, ell=0, lambda_bar=16, mu=0, hash_key=0, n_server=None):
+    def __init__(self, N, t, prime_bits, h=2, ell=0, lambda_bar=16, mu=0, hash_key=0, n_server=None, bins=0):
         self.N, self.t, self.h = int(N), int(t), int(h)
         self.prime_bits = list(prime_bits)
         self.k = len(self.prime_bits)
         self.lambda_bar = int(lambda_bar)
         self.ell = int(ell) if ell else code_length(lambda_bar, h)
-        self.logb = int(math.log2(N))
+        # b bins in B = b / N blocks of N slots (Section 4: ceil(b/N) ciphertexts per code bit)
+        self.bins = int(bins) if bins else self.N
+        self.blocks = self.bins // self.N
+        self.logb = int(math.log2(self.bins))
         self.hash_key = int(hash_key)
-        self.mu = int(mu) if mu else (mu_bound(n_server, N) if n_server else 0)
+        self.mu = int(mu) if mu else (mu_bound(n_server, self.bins) if n_server else 0)
         bits = np.array(self.prime_bits, dtype=np.uint8)
         self._p = lib().or_create(self.N, self.t, self.k, bits)
         if not self._p:
@@ -416,13 +419,18 @@ class Ctx:
         return m
 
     def query(self, s, items, enc_seed):
-        """Client side: cuckoo -> CW bit planes -> encode -> encrypt.
-        Returns (rc, cts [ell][2][k][N], bin_of_item)."""
+        """Client side: cuckoo into the b bins -> CW bit planes of each block
+        of N bins -> encode -> encrypt (ciphertext i of the request from
+        stream index i).  Returns (rc, cts [ell][2][k][N], or
+        [B][ell][2][k][N] for B > 1 blocks, bin_of_item)."""
         rc, table, where = self.cuckoo(items)
         if rc:
             return rc, None, where
-        m = self.query_plaintexts(table)
-        return 0, self.encrypt(s, m, enc_seed), where
+        m = np.concatenate([self.query_plaintexts(table[b * self.N:(b + 1) * self.N]) for b in range(self.blocks)])
+        cts = self.encrypt(s, m, enc_seed)
+        if self.blocks > 1:
+            cts = cts.reshape(self.blocks, self.ell, 2, self.k, self.N)
+        return 0, cts, where
 
     def eval(self, rlk, cts, T, mode=0, mask_seed=0, layer0=0, nlayers=None, debug=False, group=1, acc=False,
              V=None):
@@ -440,9 +448,10 @@ class Ctx:
         dh = np.zeros((nl, 2, self.k, self.N), np.uint64) if debug else None
         de = np.zeros((nl, 3, self.k, self.N), np.uint64) if debug and not lazy else None
         da = np.zeros((3, self.k, self.N), np.uint64) if acc else None
+        Vc = None if V is None else np.ascontiguousarray(V, np.uint32)  # kept alive across the call
         rc = lib().or_eval(self._p, np.ascontiguousarray(rlk, np.uint64), np.ascontiguousarray(cts, np.uint64),
                            self.ell, self.h, np.ascontiguousarray(T, np.uint64),
-                           None if V is None else np.ascontiguousarray(V, np.uint32).ctypes.data, mu, layer0, nl,
+                           None if Vc is None else Vc.ctypes.data, mu, layer0, nl,
                            mode, mask_seed, group, out, dh.ctypes.data if debug else None,
                            de.ctypes.data if de is not None else None, da.ctypes.data if acc else None, counts)
         if rc:

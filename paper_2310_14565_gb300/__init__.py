@@ -41,6 +41,7 @@ class Params(C.Structure):
         ("h", C.c_uint32), ("ell", C.c_uint32), ("lambda_bar", C.c_uint32), ("num_hashes", C.c_uint32),
         ("mu", C.c_uint32), ("hash_key", C.c_uint64), ("resident_bytes", C.c_uint64),
         ("rescale_group", C.c_uint32), ("server_values", C.c_uint32), ("response_primes", C.c_uint32),
+        ("bins", C.c_uint32),
     ]
 
 
@@ -50,7 +51,7 @@ class Info(C.Structure):
         ("mu", C.c_uint32), ("lambda_bar", C.c_uint32), ("logb", C.c_uint32), ("t", C.c_uint64),
         ("q", C.c_uint64 * 8), ("psi", C.c_uint64 * 8), ("psi_t", C.c_uint64), ("b_primes", C.c_uint64 * 12),
         ("log2_q", C.c_double), ("rescale_group", C.c_uint32), ("rescale_cap", C.c_uint32),
-        ("response_primes", C.c_uint32),
+        ("response_primes", C.c_uint32), ("bins", C.c_uint32), ("blocks", C.c_uint32),
     ]
 
 
@@ -179,14 +180,14 @@ class Context:
     """One parameter set with its keys, server sets and scratch (pepsi_ctx)."""
 
     def __init__(self, N, t=65537, prime_bits=(36, 36, 37), h=2, ell=0, lambda_bar=16, mu=0, hash_key=0,
-                 key_seed=3, resident_bytes=0, rescale_group=0, server_values=0, response_primes=0):
+                 key_seed=3, resident_bytes=0, rescale_group=0, server_values=0, response_primes=0, bins=0):
         p = Params()
         p.N, p.t, p.k = N, t, len(prime_bits)
         for i, b in enumerate(prime_bits):
             p.prime_bits[i] = b
         p.h, p.ell, p.lambda_bar, p.num_hashes, p.mu = h, ell, lambda_bar, 3, mu
         p.hash_key, p.resident_bytes, p.rescale_group = hash_key, resident_bytes, rescale_group
-        p.server_values, p.response_primes = server_values, response_primes
+        p.server_values, p.response_primes, p.bins = server_values, response_primes, bins
         self._h = C.c_void_p()
         _check(lib().pepsi_setup(C.byref(p), key_seed, C.byref(self._h)), "pepsi_setup")
         info = Info()
@@ -199,6 +200,7 @@ class Context:
         self.b_primes = [int(info.b_primes[i]) for i in range(min(self.kb, 12))]
         self.rescale_cap = int(info.rescale_cap)
         self.response_primes = int(info.response_primes)
+        self.bins, self.blocks = int(info.bins), int(info.blocks)
         self.mu = {}
 
     def close(self):
@@ -246,19 +248,23 @@ class Context:
                "pepsi_server_load_values")
         return sid.value
 
+    def _blocked(self, shape):
+        """Array shape with a leading block dimension when b > N."""
+        return (self.blocks,) + tuple(shape) if self.blocks > 1 else tuple(shape)
+
     def server_values(self, set_id, mu):
-        out = np.zeros((mu, self.N), dtype=np.uint32)
+        out = np.zeros((mu, self.bins), dtype=np.uint32)
         _check(lib().pepsi_server_values(self._h, set_id, _ptr(out)), "pepsi_server_values")
         return out
 
     def server_table(self, set_id, mu):
-        out = np.zeros((mu, self.N), dtype=np.uint64)
+        out = np.zeros((mu, self.bins), dtype=np.uint64)
         _check(lib().pepsi_server_table(self._h, set_id, _ptr(out)), "pepsi_server_table")
         return out
 
     def server_plaintexts(self, set_id, layer0, nl, out=None, stream=None):
         if out is None:
-            out = np.zeros((nl, self.ell, self.k, self.N), dtype=np.uint64)
+            out = np.zeros(self._blocked((nl, self.ell, self.k, self.N)), dtype=np.uint64)
         _check(lib().pepsi_server_plaintexts(self._h, set_id, layer0, nl, _ptr(out), _stream(stream)),
                "pepsi_server_plaintexts")
         return out
@@ -267,7 +273,7 @@ class Context:
     def query(self, items, enc_seed, out=None, stream=None):
         items = np.ascontiguousarray(items, dtype=np.uint64)
         if out is None:
-            out = np.zeros((self.ell, 2, self.k, self.N), dtype=np.uint64)
+            out = np.zeros(self._blocked((self.ell, 2, self.k, self.N)), dtype=np.uint64)
         where = np.full(max(items.size, 1), -1, dtype=np.int32)
         _check(lib().pepsi_query(self._h, _ptr(items) if items.size else None, items.size, enc_seed, _ptr(out),
                                  _ptr(where), _stream(stream)), "pepsi_query")
@@ -275,7 +281,12 @@ class Context:
 
     def decrypt(self, ct):
         """Slots and noise budget of a ciphertext [2][r][N] over the first r
-        primes (r = k, or fewer for a switched response)."""
+        primes (r = k, or fewer for a switched response).  A response of B
+        blocks [B][2][r][N] gives the B*N slots in bin order and the
+        smallest budget."""
+        if len(ct.shape) == 4:
+            parts = [self.decrypt(ct[i]) for i in range(int(ct.shape[0]))]
+            return np.concatenate([p[0] for p in parts]), min(p[1] for p in parts)
         ct = np.ascontiguousarray(ct, dtype=np.uint64) if isinstance(ct, np.ndarray) else ct
         r = int(ct.shape[-2])
         slots = np.zeros(self.N, dtype=np.uint32)
@@ -299,7 +310,7 @@ class Context:
     # ---- evaluation
     def eval(self, set_id, cts, mode=MODE_INDICATOR, mask_seed=0, out=None, stream=None):
         if out is None:
-            out = np.zeros((2, self.response_primes, self.N), dtype=np.uint64)
+            out = np.zeros(self._blocked((2, self.response_primes, self.N)), dtype=np.uint64)
         _check(lib().pepsi_eval(self._h, set_id, _ptr(cts), mode, mask_seed, _ptr(out), _stream(stream)),
                "pepsi_eval")
         return out
@@ -308,7 +319,7 @@ class Context:
         """pepsi_eval_batch: one output ciphertext per request."""
         nq = len(cts_list)
         if outs is None:
-            outs = [np.zeros((2, self.response_primes, self.N), dtype=np.uint64) for _ in range(nq)]
+            outs = [np.zeros(self._blocked((2, self.response_primes, self.N)), dtype=np.uint64) for _ in range(nq)]
         sid = (C.c_int * nq)(*set_ids)
         cp = (C.c_void_p * nq)(*[_ptr(x) for x in cts_list])
         op = (C.c_void_p * nq)(*[_ptr(x) for x in outs])
@@ -318,8 +329,8 @@ class Context:
         return outs
 
     def eval_layers(self, set_id, cts, layer0, nl, want_h=True, want_e=True, stream=None):
-        h = np.zeros((nl, 2, self.k, self.N), dtype=np.uint64) if want_h else None
-        e = np.zeros((nl, 3, self.k, self.N), dtype=np.uint64) if want_e else None
+        h = np.zeros(self._blocked((nl, 2, self.k, self.N)), dtype=np.uint64) if want_h else None
+        e = np.zeros(self._blocked((nl, 3, self.k, self.N)), dtype=np.uint64) if want_e else None
         _check(lib().pepsi_eval_layers(self._h, set_id, _ptr(cts), layer0, nl, _ptr(h), _ptr(e), _stream(stream)),
                "pepsi_eval_layers")
         return h, e

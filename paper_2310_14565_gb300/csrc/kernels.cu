@@ -911,7 +911,7 @@ __device__ __forceinline__ u64 smod_dev(i64 v, u64 q) { return v >= 0 ? (u64)v :
 // Block per ciphertext j: encode bit plane j, then for each prime sample
 // a, compute c0 = e - a s + round(Q m / t), c1 = a (coefficient form).
 __global__ void __launch_bounds__(NTT_MAX_THREADS, 2) k_encrypt(DevView V, const uint16_t* __restrict__ pos, int h, const u64* __restrict__ s_ntt, u64 seed,
-                          u64* cts) {
+                          u64 idx0, u64* cts) {
   extern __shared__ u64 sm[];
   const int N = V.N, k = V.k, j = blockIdx.x;
   u64* poly = sm;
@@ -929,10 +929,10 @@ __global__ void __launch_bounds__(NTT_MAX_THREADS, 2) k_encrypt(DevView V, const
   ntt_inv_view(poly, V, V.tidx);
   for (int i = threadIdx.x; i < N; i += blockDim.x) mbuf[i] = (u32)poly[nsw(i)];
   __syncthreads();
-  const u64 key_e = stream_key(seed, make_stream(STREAM_ENC_E, j, 0));
+  const u64 key_e = stream_key(seed, make_stream(STREAM_ENC_E, idx0 + j, 0));
   for (int p = 0; p < k; ++p) {
     const DevPrime pq = V.pr[p];
-    const u64 key_a = stream_key(seed, make_stream(STREAM_ENC_A, j, p));
+    const u64 key_a = stream_key(seed, make_stream(STREAM_ENC_A, idx0 + j, p));
     u64* c0 = cts + (((size_t)j * 2 + 0) * k + p) * N;
     u64* c1 = cts + (((size_t)j * 2 + 1) * k + p) * N;
     for (int i = threadIdx.x; i < N; i += blockDim.x) {
@@ -1345,10 +1345,10 @@ void launch_accum(const DevView& V, const u64* D, int L, u64* acc, bool init, cu
   k_accum<<<grid_for(total, 256), 256, 0, st>>>(V, D, L, acc, init ? 1 : 0);
 }
 
-void launch_encrypt(const DevView& V, const uint16_t* pos, int ell, int h, const u64* s_ntt, u64 seed, u64* cts,
-                    cudaStream_t st) {
+void launch_encrypt(const DevView& V, const uint16_t* pos, int ell, int h, const u64* s_ntt, u64 seed, u64 idx0,
+                    u64* cts, cudaStream_t st) {
   if (ell <= 0) return;
-  k_encrypt<<<ell, ntt_threads(V.N), (size_t)V.N * 12, st>>>(V, pos, h, s_ntt, seed, cts);
+  k_encrypt<<<ell, ntt_threads(V.N), (size_t)V.N * 12, st>>>(V, pos, h, s_ntt, seed, idx0, cts);
 }
 
 void launch_keygen(const DevView& V, u64 seed, int8_t* s, u64* s_ntt, u64* rlk, cudaStream_t st) {

@@ -79,8 +79,8 @@ void launch_axpy(const DevView& V, const u64* a, const u64* zres, const u64* b, 
 void launch_accum(const DevView& V, const u64* D, int L, u64* acc, bool init, cudaStream_t st);
 
 // Client encryption of ell plaintexts given the client codeword positions pos[N][h].
-void launch_encrypt(const DevView& V, const uint16_t* pos, int ell, int h, const u64* s_ntt, u64 seed, u64* cts,
-                    cudaStream_t st);
+void launch_encrypt(const DevView& V, const uint16_t* pos, int ell, int h, const u64* s_ntt, u64 seed, u64 idx0,
+                    u64* cts, cudaStream_t st);
 
 // Key generation: s (ternary) and its NTT rows; rlk in NTT form.
 void launch_keygen(const DevView& V, u64 seed, int8_t* s, u64* s_ntt, u64* rlk, cudaStream_t st);

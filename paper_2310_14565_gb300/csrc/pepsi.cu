@@ -42,6 +42,18 @@ struct ServerSet {
   u64* dVP = nullptr;           // [mu][k+kb][N] value plaintexts val_s, NTT form over Q u B
 };
 
+// A server set as the caller sees it: its b = B*N bins are B blocks of N
+// slots, each an internal ServerSet (its own layers and plaintexts) that
+// is evaluated against the request's block of the same index.
+struct SetGroup {
+  bool live = false;
+  u32 mu = 0;
+  std::vector<int> blk;       // internal set of each block
+  std::vector<u64> hT;        // [mu][bins] the whole table
+  std::vector<uint32_t> hV;   // [mu][bins] values, when loaded with values
+  bool has_values = false;
+};
+
 }  // namespace
 
 struct pepsi_ctx {
@@ -67,7 +79,9 @@ struct pepsi_ctx {
   u64* d_consts = nullptr; // residues of circuit scalars and constants, [slot][k]
   int* d_err = nullptr;     // set by kernels whose bounded wait expired
   int mac_fold = 1;         // terms between folds of the MAC partial sums
-  std::vector<ServerSet> sets;
+  std::vector<ServerSet> sets;   // internal: one per block of a loaded set
+  std::vector<SetGroup> groups;  // the caller's set ids
+  u32 logb = 0, blocks = 1;      // bins = blocks * N = 2^logb
   // scratch, grown on demand
   std::vector<DevBuf> scratch;
   int chunk = 32;
@@ -908,6 +922,19 @@ int pepsi_setup(const pepsi_params* params, uint64_t key_seed, pepsi_ctx** out) 
       return PEPSI_E_PARAM;
     }
   }
+  {  // bins: B blocks of N slots
+    const u64 bins = params->bins ? params->bins : (u64)c->N;
+    if (bins < (u64)c->N || bins % c->N || (bins & (bins - 1)) || bins / c->N > 1024) {
+      delete c;
+      return PEPSI_E_PARAM;
+    }
+    while ((1ull << c->logb) < bins) ++c->logb;
+    c->blocks = (u32)(bins / c->N);
+    if (params->lambda_bar + c->logb >= 64) {
+      delete c;
+      return PEPSI_E_PARAM;
+    }
+  }
   if (params->response_primes > (u32)c->k) {
     delete c;
     return PEPSI_E_PARAM;
@@ -1069,6 +1096,8 @@ int pepsi_get_info(const pepsi_ctx* c, pepsi_info* info) {
   info->rescale_group = c->prm.rescale_group;
   info->rescale_cap = c->rescale_cap;
   info->response_primes = (uint32_t)c->resp;
+  info->bins = c->blocks * (uint32_t)c->N;
+  info->blocks = c->blocks;
   return PEPSI_OK;
 }
 
@@ -1112,23 +1141,15 @@ int pepsi_set_rescale_group(pepsi_ctx* c, uint32_t rescale_group) {
 }
 
 namespace {
-// with_values: the set carries values[n] (labelled PSI / PSI-Sum)
-int server_load_impl(pepsi_ctx* c, const uint64_t* items, bool with_values, const uint32_t* values, size_t n,
-                     int* set_id) {
-  if (!c || (!items && n) || !set_id || (with_values && !values && n)) return PEPSI_E_PARAM;
-  if (with_values)
-    for (size_t i = 0; i < n; ++i)
-      if (values[i] >= c->t) return PEPSI_E_PARAM;
-  hostmath::Hasher H(c->prm.hash_key, c->prm.lambda_bar, c->logN);
-  u32 mu = c->prm.mu ? c->prm.mu : hostmath::mu_rule(n, c->N);
+// Device side of one block: its table [mu][N] (and values) to codeword
+// positions, value plaintexts, and the resident prefix of mu_res layers of
+// NTT-form plaintexts.
+int load_block(pepsi_ctx* c, std::vector<u64>&& hT, std::vector<uint32_t>* hV, u32 mu, u32 mu_res, int* internal) {
   ServerSet S;
   S.mu = mu;
-  u32 maxload = 0;
-  int rc = hostmath::simple_hash(H, items, n, mu, S.hT, &maxload, values, with_values ? &S.hV : nullptr);
-  if (rc) return rc;
+  S.hT = std::move(hT);
   const size_t N = c->N, k = c->k;
-  const size_t tbytes = (size_t)mu * N * 8;
-  cudaError_t e = upload((void**)&S.dT, S.hT.data(), tbytes);
+  cudaError_t e = upload((void**)&S.dT, S.hT.data(), (size_t)mu * N * 8);
   if (e == cudaSuccess) e = cudaMalloc((void**)&S.dpos, (size_t)mu * N * c->h * sizeof(uint16_t));
   if (e != cudaSuccess) {
     cudaGetLastError();
@@ -1139,8 +1160,9 @@ int server_load_impl(pepsi_ctx* c, const uint64_t* items, bool with_values, cons
     Prof p(c, PC_PTGEN, c->stream);
     launch_cw_unrank(S.dT, (size_t)mu * N, c->d_binom, c->ell, c->h, S.dpos, c->stream);
   }
-  if (with_values) {  // value plaintexts val_s[layer] (Algorithms 4-5), NTT form over Q u B
+  if (hV) {  // value plaintexts val_s[layer] (Algorithms 4-5), NTT form over Q u B
     S.has_values = true;
+    S.hV = std::move(*hV);
     u32* dv = nullptr;
     e = upload((void**)&dv, S.hV.data(), (size_t)mu * N * sizeof(u32));
     if (e == cudaSuccess) e = cudaMalloc((void**)&S.dVP, (size_t)mu * (c->k + c->kb) * N * 8);
@@ -1156,13 +1178,8 @@ int server_load_impl(pepsi_ctx* c, const uint64_t* items, bool with_values, cons
       return cuda_status(e);
     }
   }
-  // resident NTT-form plaintexts: the longest prefix of layers the budget holds
   const size_t per_layer = (size_t)c->ell * k * N * 8;
-  size_t freeb = 0, totalb = 0;
-  cudaMemGetInfo(&freeb, &totalb);
-  const u64 cap = c->prm.resident_bytes;
-  const size_t budget = cap == 0 ? (size_t)(0.6 * (double)freeb) : (cap == UINT64_MAX ? 0 : (size_t)cap);
-  S.mu_res = (u32)std::min<size_t>(mu, budget / per_layer);
+  S.mu_res = mu_res;
   if (S.mu_res) {
     e = cudaMalloc((void**)&S.dP, (size_t)S.mu_res * per_layer);
     if (e != cudaSuccess) {
@@ -1185,11 +1202,66 @@ int server_load_impl(pepsi_ctx* c, const uint64_t* items, bool with_values, cons
     free_set(S);
     return cuda_status(e);
   }
-  if (c->prof) prof_collect(c);
   S.live = true;
   c->sets.push_back(std::move(S));
-  *set_id = (int)c->sets.size() - 1;
+  *internal = (int)c->sets.size() - 1;
   return PEPSI_OK;
+}
+
+// with_values: the set carries values[n] (labelled PSI / PSI-Sum)
+int server_load_impl(pepsi_ctx* c, const uint64_t* items, bool with_values, const uint32_t* values, size_t n,
+                     int* set_id) {
+  if (!c || (!items && n) || !set_id || (with_values && !values && n)) return PEPSI_E_PARAM;
+  if (with_values)
+    for (size_t i = 0; i < n; ++i)
+      if (values[i] >= c->t) return PEPSI_E_PARAM;
+  const size_t N = c->N, bins = (size_t)c->blocks * N;
+  hostmath::Hasher H(c->prm.hash_key, c->prm.lambda_bar, c->logb);
+  const u32 mu = c->prm.mu ? c->prm.mu : hostmath::mu_rule(n, (u32)bins);
+  SetGroup G;
+  G.mu = mu;
+  G.has_values = with_values;
+  u32 maxload = 0;
+  int rc = hostmath::simple_hash(H, items, n, mu, G.hT, &maxload, values, with_values ? &G.hV : nullptr);
+  if (rc) return rc;
+  // resident NTT-form plaintexts: the longest prefix of layers the budget
+  // holds for every block
+  const size_t per_layer = (size_t)c->ell * c->k * N * 8 * c->blocks;
+  size_t freeb = 0, totalb = 0;
+  cudaMemGetInfo(&freeb, &totalb);
+  const u64 cap = c->prm.resident_bytes;
+  const size_t budget = cap == 0 ? (size_t)(0.6 * (double)freeb) : (cap == UINT64_MAX ? 0 : (size_t)cap);
+  const u32 mu_res = (u32)std::min<size_t>(mu, budget / per_layer);
+  for (u32 b = 0; b < c->blocks; ++b) {
+    std::vector<u64> T((size_t)mu * N);
+    std::vector<uint32_t> V(with_values ? (size_t)mu * N : 0);
+    for (u32 l = 0; l < mu; ++l) {
+      memcpy(&T[(size_t)l * N], &G.hT[(size_t)l * bins + (size_t)b * N], N * 8);
+      if (with_values) memcpy(&V[(size_t)l * N], &G.hV[(size_t)l * bins + (size_t)b * N], N * 4);
+    }
+    int id = -1;
+    rc = load_block(c, std::move(T), with_values ? &V : nullptr, mu, mu_res, &id);
+    if (rc) {
+      for (int i : G.blk) free_set(c->sets[i]);
+      return rc;
+    }
+    G.blk.push_back(id);
+  }
+  if (c->prof) prof_collect(c);
+  G.live = true;
+  c->groups.push_back(std::move(G));
+  *set_id = (int)c->groups.size() - 1;
+  return PEPSI_OK;
+}
+
+// Words per block of a request and of a response.
+size_t request_block_words(const pepsi_ctx* c) { return (size_t)c->ell * 2 * c->k * c->N; }
+size_t response_block_words(const pepsi_ctx* c) { return (size_t)2 * c->resp * c->N; }
+
+// The caller's set, or null.
+SetGroup* group(pepsi_ctx* c, int set_id) {
+  if (!c || set_id < 0 || set_id >= (int)c->groups.size() || !c->groups[set_id].live) return nullptr;
+  return &c->groups[set_id];
 }
 }  // namespace
 
@@ -1202,66 +1274,70 @@ int pepsi_server_load_values(pepsi_ctx* c, const uint64_t* items, const uint32_t
 }
 
 int pepsi_server_values(pepsi_ctx* c, int set_id, uint32_t* out) {
-  if (!c || !out || set_id < 0 || set_id >= (int)c->sets.size() || !c->sets[set_id].live ||
-      !c->sets[set_id].has_values)
-    return PEPSI_E_PARAM;
-  memcpy(out, c->sets[set_id].hV.data(), c->sets[set_id].hV.size() * sizeof(uint32_t));
+  SetGroup* G = group(c, set_id);
+  if (!G || !out || !G->has_values) return PEPSI_E_PARAM;
+  memcpy(out, G->hV.data(), G->hV.size() * sizeof(uint32_t));
   return PEPSI_OK;
 }
 
 int pepsi_server_table(pepsi_ctx* c, int set_id, uint64_t* out) {
-  if (!c || !out || set_id < 0 || set_id >= (int)c->sets.size() || !c->sets[set_id].live) return PEPSI_E_PARAM;
-  memcpy(out, c->sets[set_id].hT.data(), c->sets[set_id].hT.size() * 8);
+  SetGroup* G = group(c, set_id);
+  if (!G || !out) return PEPSI_E_PARAM;
+  memcpy(out, G->hT.data(), G->hT.size() * 8);
   return PEPSI_OK;
 }
 
 int pepsi_server_plaintexts(pepsi_ctx* c, int set_id, uint32_t layer0, uint32_t nl, uint64_t* out, void* stream) {
-  if (!c || !out || set_id < 0 || set_id >= (int)c->sets.size() || !c->sets[set_id].live) return PEPSI_E_PARAM;
-  ServerSet& S = c->sets[set_id];
-  if ((u64)layer0 + nl > S.mu) return PEPSI_E_PARAM;
+  SetGroup* G = group(c, set_id);
+  if (!G || !out || (u64)layer0 + nl > G->mu) return PEPSI_E_PARAM;
   cudaStream_t st = pick(c, stream);
   const size_t per = (size_t)c->ell * c->k * c->N;
   cudaError_t e = cudaSuccess;
   u64* tmp = (u64*)scratch(c, S_PC, (size_t)nl * per * 8, &e);
   if (!tmp) return cuda_status(e);
-  if ((u64)layer0 + nl <= S.mu_res) {
-    CKS(cudaMemcpyAsync(tmp, S.dP + (size_t)layer0 * per, (size_t)nl * per * 8, cudaMemcpyDeviceToDevice, st));
-  } else {
-    Prof p(c, PC_PTGEN, st);
-    launch_ptgen(c->V, S.dpos + (size_t)layer0 * c->N * c->h, nl, c->ell, c->h, tmp, st);
+  for (size_t b = 0; b < G->blk.size(); ++b) {
+    ServerSet& S = c->sets[G->blk[b]];
+    if ((u64)layer0 + nl <= S.mu_res) {
+      CKS(cudaMemcpyAsync(tmp, S.dP + (size_t)layer0 * per, (size_t)nl * per * 8, cudaMemcpyDeviceToDevice, st));
+    } else {
+      Prof p(c, PC_PTGEN, st);
+      launch_ptgen(c->V, S.dpos + (size_t)layer0 * c->N * c->h, nl, c->ell, c->h, tmp, st);
+    }
+    launch_split(c->V, tmp, (size_t)nl * c->ell, false, st);  // stored split; returned reduced
+    e = copy_any(out + b * nl * per, tmp, (size_t)nl * per * 8, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_status(e);
   }
-  launch_split(c->V, tmp, (size_t)nl * c->ell, false, st);  // stored split; returned reduced
-  e = copy_any(out, tmp, (size_t)nl * per * 8, st);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-  return cuda_status(e);
+  return PEPSI_OK;
 }
 
 int pepsi_query(pepsi_ctx* c, const uint64_t* items, size_t m, uint64_t enc_seed, uint64_t* cts,
                 int32_t* bin_of_item, void* stream) {
   if (!c || (!items && m) || !cts) return PEPSI_E_PARAM;
   cudaStream_t st = pick(c, stream);
-  hostmath::Hasher H(c->prm.hash_key, c->prm.lambda_bar, c->logN);
-  std::vector<u64> table;
+  hostmath::Hasher H(c->prm.hash_key, c->prm.lambda_bar, c->logb);
+  std::vector<u64> table;  // [bins]
   std::vector<int32_t> where;
   int rc = hostmath::cuckoo(H, items, m, table, where);
   if (rc) return rc;
   if (bin_of_item) memcpy(bin_of_item, where.data(), m * sizeof(int32_t));
   cudaError_t e = cudaSuccess;
-  const size_t N = c->N;
-  u64* dTc = (u64*)scratch(c, S_TC, N * 8, &e);
-  uint16_t* dpos = (uint16_t*)scratch(c, S_POS, N * c->h * sizeof(uint16_t), &e);
-  const size_t words = (size_t)c->ell * 2 * c->k * N;
+  const size_t N = c->N, bins = (size_t)c->blocks * N;
+  u64* dTc = (u64*)scratch(c, S_TC, bins * 8, &e);
+  uint16_t* dpos = (uint16_t*)scratch(c, S_POS, bins * c->h * sizeof(uint16_t), &e);
+  const size_t words = request_block_words(c) * c->blocks;
   const bool dev_out = is_device_ptr(cts);
   u64* dct = dev_out ? cts : (u64*)scratch(c, S_CT, words * 8, &e);
   if (!dTc || !dpos || !dct) return cuda_status(e);
-  CKS(copy_any(dTc, table.data(), N * 8, st));
+  CKS(copy_any(dTc, table.data(), bins * 8, st));
   {
     Prof p(c, PC_CLIENT, st);
-    launch_cw_unrank(dTc, N, c->d_binom, c->ell, c->h, dpos, st);
+    launch_cw_unrank(dTc, bins, c->d_binom, c->ell, c->h, dpos, st);
   }
-  {
+  for (u32 b = 0; b < c->blocks; ++b) {  // block b: ciphertexts b*ell .. b*ell + ell - 1
     Prof p(c, PC_CLIENT, st);
-    launch_encrypt(c->V, dpos, c->ell, c->h, c->d_s_ntt, enc_seed, dct, st);
+    launch_encrypt(c->V, dpos + (size_t)b * N * c->h, c->ell, c->h, c->d_s_ntt, enc_seed, (u64)b * c->ell,
+                   dct + (size_t)b * request_block_words(c), st);
   }
   if (!dev_out) CKS(copy_any(cts, dct, words * 8, st));
   e = cudaStreamSynchronize(st);  // the host cuckoo table must outlive the copy
@@ -1272,23 +1348,54 @@ int pepsi_query(pepsi_ctx* c, const uint64_t* items, size_t m, uint64_t enc_seed
 
 int pepsi_eval(pepsi_ctx* c, int set_id, const uint64_t* cts, int mode, uint64_t mask_seed, uint64_t* out_ct,
                void* stream) {
-  if (!c || !out_ct) return PEPSI_E_PARAM;
-  if (set_id < 0 || set_id >= (int)c->sets.size()) return PEPSI_E_PARAM;
-  return eval_core(c, set_id, cts, 0, c->sets[set_id].mu, mode, mask_seed, out_ct, nullptr, nullptr,
-                   pick(c, stream));
+  SetGroup* G = group(c, set_id);
+  if (!G || !out_ct || !cts) return PEPSI_E_PARAM;
+  cudaStream_t st = pick(c, stream);
+  for (size_t b = 0; b < G->blk.size(); ++b) {  // block b: its request block, mask seed + b
+    const int rc = eval_core(c, G->blk[b], cts + b * request_block_words(c), 0, G->mu, mode, mask_seed + b,
+                             out_ct + b * response_block_words(c), nullptr, nullptr, st);
+    if (rc) return rc;
+  }
+  return PEPSI_OK;
 }
 
 int pepsi_eval_batch(pepsi_ctx* c, int nq, const int* set_ids, const uint64_t* const* cts, const int* modes,
                      const uint64_t* mask_seeds, uint64_t* const* out_cts, void* stream) {
   if (!c || nq < 0 || (nq && (!set_ids || !cts || !out_cts))) return PEPSI_E_PARAM;
   if (!nq) return PEPSI_OK;
-  return eval_batch_core(c, nq, set_ids, cts, modes, mask_seeds, out_cts, pick(c, stream));
+  // one internal request per (request, block)
+  std::vector<int> ids, md;
+  std::vector<const u64*> in;
+  std::vector<u64*> out;
+  std::vector<u64> seeds;
+  for (int i = 0; i < nq; ++i) {
+    SetGroup* G = group(c, set_ids[i]);
+    if (!G || !cts[i] || !out_cts[i]) return PEPSI_E_PARAM;
+    for (size_t b = 0; b < G->blk.size(); ++b) {
+      ids.push_back(G->blk[b]);
+      in.push_back(cts[i] + b * request_block_words(c));
+      out.push_back(out_cts[i] + b * response_block_words(c));
+      md.push_back(modes ? modes[i] : PEPSI_MODE_INDICATOR);
+      seeds.push_back((mask_seeds ? mask_seeds[i] : 0) + b);
+    }
+  }
+  return eval_batch_core(c, (int)ids.size(), ids.data(), in.data(), md.data(), seeds.data(), out.data(),
+                         pick(c, stream));
 }
 
 int pepsi_eval_layers(pepsi_ctx* c, int set_id, const uint64_t* cts, uint32_t layer0, uint32_t nl, uint64_t* h_out,
                       uint64_t* e_out, void* stream) {
-  if (!c || nl == 0) return PEPSI_E_PARAM;
-  return eval_core(c, set_id, cts, layer0, nl, PEPSI_MODE_INDICATOR, 0, nullptr, h_out, e_out, pick(c, stream));
+  SetGroup* G = group(c, set_id);
+  if (!G || nl == 0 || !cts) return PEPSI_E_PARAM;
+  const size_t kN = (size_t)c->k * c->N;
+  cudaStream_t st = pick(c, stream);
+  for (size_t b = 0; b < G->blk.size(); ++b) {
+    const int rc = eval_core(c, G->blk[b], cts + b * request_block_words(c), layer0, nl, PEPSI_MODE_INDICATOR, 0,
+                             nullptr, h_out ? h_out + b * nl * 2 * kN : nullptr,
+                             e_out ? e_out + b * nl * 3 * kN : nullptr, st);
+    if (rc) return rc;
+  }
+  return PEPSI_OK;
 }
 
 int pepsi_decrypt_primes(pepsi_ctx* c, const uint64_t* ct, uint32_t nprimes, uint32_t* slots,

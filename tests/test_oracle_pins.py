@@ -715,3 +715,35 @@ def test_psi_response_switched_to_one_prime(oracle_mod, h, bits, lb):
     for r in (1, 2):
         slots, bud = c.decrypt(s, c.mod_switch(out, r))
         assert bud > 0 and np.array_equal(slots, full)
+
+
+# ----------------------------------------------- more bins than slots
+def test_psi_with_more_bins_than_slots(oracle_mod):
+    # b = 4N bins: four blocks of N slots, each evaluated against its own
+    # block of the server table; the blocks' slots together equal the
+    # hashed-domain brute force over all b bins
+    from paper_2310_14565_gb300.workload import make_sets
+
+    N, B, lb = 64, 4, 10
+    sets = make_sets(150, 300, 9, bits=32, seed_items=61, seed_plant=62)
+    load = oracle_mod.simple_hash(99, lb, 8, sets.server, 1000)[2]
+    c = oracle_mod.Ctx(N=N, t=T, prime_bits=[55, 55, 54, 54], h=4, lambda_bar=lb, hash_key=99, mu=max(5, load),
+                       bins=N * B)
+    s, rlk = c.keygen(3)
+    rc, Ts, _ = c.server_table(sets.server)
+    assert rc == 0 and Ts.shape == (c.mu, N * B)
+    rc, cts, where = c.query(s, sets.client, 4)
+    assert rc == 0 and cts.shape == (B, c.ell, 2, c.k, N)
+    slots = np.concatenate([c.decrypt(s, c.eval(rlk, cts[b], Ts[:, b * N:(b + 1) * N]))[0] for b in range(B)])
+    srv = {}
+    for y in sets.server:
+        yl, bins = oracle_mod.hash_item(99, lb, 8, y)
+        for bb in bins:
+            srv.setdefault(bb, set()).add(yl)
+    want = np.zeros(N * B, np.uint32)
+    for u, x in enumerate(sets.client):
+        xl, _ = oracle_mod.hash_item(99, lb, 8, x)
+        want[where[u]] = int(xl in srv.get(int(where[u]), set()))
+    assert np.array_equal(slots, want) and int(want.sum()) >= 9
+    # more client items than one block holds
+    assert len(sets.client) > N

@@ -136,9 +136,20 @@ def cpu_baseline(lazy):
     fixed = oracle_sample(oracle, oc, rlk, cts, Ts, 0, lazy=lazy)
     total = oracle_sample(oracle, oc, rlk, cts, Ts, layers, lazy=lazy)
     est = fixed + (total - fixed) * WL["mu"] / layers
+    # the same on one core: the fixed part and two layers
+    oracle.set_threads(1)
+    try:
+        fixed1 = oracle_sample(oracle, oc, rlk, cts, Ts, 0, lazy=lazy)
+        total1 = oracle_sample(oracle, oc, rlk, cts, Ts, 2, lazy=lazy)
+    finally:
+        oracle.set_threads(cores)
+    est1 = fixed1 + (total1 - fixed1) * WL["mu"] / 2
     return {"value": round(est, 1), "unit": "ms", "cores": cores, "kind": "oracle",
             "sample": "request NTT + relin/scale (%.0f ms) and %d of 526 layers (%.0f ms), layer part scaled to 526"
-                      % (fixed, layers, total - fixed)}
+                      % (fixed, layers, total - fixed),
+            "one_core": {"value": round(est1, 1), "unit": "ms", "cores": 1,
+                         "sample": "request NTT + relin/scale (%.0f ms) and 2 of 526 layers (%.0f ms), scaled"
+                                   % (fixed1, total1 - fixed1)}}
 
 
 def run_reference(args):

@@ -213,22 +213,6 @@ __device__ __forceinline__ bool mbar_wait_bounded(u32 addr, u32 parity) {
     if (globaltimer_ns() - t0 > 1000000000ull) return false;
   return true;
 }
-// Test of the bounded wait above: one thread waits on an mbarrier that
-// needs one arrival.  With arrive != 0 it arrives first and the wait
-// completes; with arrive == 0 nothing completes the phase, the wait gives
-// up after about one second and the kernel sets *err and returns, as the
-// multiply-accumulate does when its copies never land.
-__global__ void k_wait_probe(int arrive, int* err) {
-  __shared__ __align__(8) u64 bar;
-  const u32 addr = (u32)__cvta_generic_to_shared(&bar);
-  if (threadIdx.x == 0) {
-    mbar_init(addr, 1);
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    if (arrive) mbar_arrive(addr);
-    if (!mbar_wait_bounded(addr, 0)) atomicExch(err, 1);
-  }
-}
-
 __device__ __forceinline__ void tma_load_3d(u32 dst, const CUtensorMap* tm, int c0, int c1, int c2, u32 bar) {
   asm volatile(
       "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(
@@ -1361,6 +1345,22 @@ void launch_modswitch(const DevView& V, const ModSwitchArgs& M, const u64* in, u
   const size_t total = n * 2 * V.N;
   if (!total) return;
   k_modswitch<<<grid_for(total, 256), 256, 0, st>>>(M, V, in, out, n);
+}
+
+// Test of the multiply-accumulate's bounded wait (mbar_wait_bounded): one thread waits on an mbarrier that
+// needs one arrival.  With arrive != 0 it arrives first and the wait
+// completes; with arrive == 0 nothing completes the phase, the wait gives
+// up after about one second and the kernel sets *err and returns, as the
+// multiply-accumulate does when its copies never land.
+__global__ void k_wait_probe(int arrive, int* err) {
+  __shared__ __align__(8) u64 bar;
+  const u32 addr = (u32)__cvta_generic_to_shared(&bar);
+  if (threadIdx.x == 0) {
+    mbar_init(addr, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    if (arrive) mbar_arrive(addr);
+    if (!mbar_wait_bounded(addr, 0)) atomicExch(err, 1);
+  }
 }
 
 void launch_wait_probe(int arrive, int* err, cudaStream_t st) { k_wait_probe<<<1, 32, 0, st>>>(arrive, err); }

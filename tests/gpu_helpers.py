@@ -26,14 +26,15 @@ def to_host(t):
     return t.cpu().numpy().view(np.uint64)
 
 
-def pair(N, bits, h, lambda_bar, mu, ell=0, hash_key=HASH_KEY, key_seed=KEY_SEED, resident_bytes=0, rescale_group=0):
+def pair(N, bits, h, lambda_bar, mu, ell=0, hash_key=HASH_KEY, key_seed=KEY_SEED, resident_bytes=0, rescale_group=0,
+         **ctx_kw):
     import oracle
 
     import paper_2310_14565_gb300 as pepsi
 
     oc = oracle.Ctx(N=N, t=T, prime_bits=bits, h=h, ell=ell, lambda_bar=lambda_bar, mu=mu, hash_key=hash_key)
     gc = pepsi.Context(N=N, t=T, prime_bits=bits, h=h, ell=ell, lambda_bar=lambda_bar, mu=mu, hash_key=hash_key,
-                       key_seed=key_seed, resident_bytes=resident_bytes, rescale_group=rescale_group)
+                       key_seed=key_seed, resident_bytes=resident_bytes, rescale_group=rescale_group, **ctx_kw)
     s, rlk = oc.keygen(key_seed)
     return oc, gc, s, rlk
 

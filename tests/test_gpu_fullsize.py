@@ -1,10 +1,13 @@
 """Parity at the paper-shaped size, in the configuration bench.py times:
 N = 8192, four 54/55-bit primes, t = 65537, h = 4, ell = 600, mu = 526,
 1024 client items against 2^20 server items (102 planted), resident
-server plaintexts.  The oracle checks sampled outputs one by one (the
-server table, the request words, sampled plaintexts, the h' and E words of
-sampled layers); the final result is checked by properties that hold at
-any size (decrypts to the brute-force intersection with positive budget)."""
+server plaintexts, one rounding of the layers' last products per
+evaluation and a one-prime response.  The oracle checks sampled outputs one
+by one (the server table, the request words, sampled plaintexts, the h'
+and E words of sampled layers, the response switch of a full ciphertext);
+the final result is checked by properties that hold at any size (decrypts
+to the brute-force intersection with positive budget, the same as with
+per-layer rounding)."""
 import numpy as np
 import pytest
 
@@ -13,6 +16,7 @@ from gpu_helpers import brute_indicator, pair, torch_cuda
 pytestmark = pytest.mark.gpu
 
 PAPER = [55, 55, 54, 54]
+ALL = 0xFFFFFFFF
 
 
 @pytest.fixture(scope="module")
@@ -20,7 +24,8 @@ def paper_case():
     torch_cuda()
     from paper_2310_14565_gb300.workload import make_sets
 
-    oc, gc, s, rlk = pair(8192, PAPER, 4, 32, mu=526, ell=600)
+    oc, gc, s, rlk = pair(8192, PAPER, 4, 32, mu=526, ell=600, rescale_group=ALL, server_values=1,
+                          response_primes=1)
     sets = make_sets(1024, 1 << 20, 102, bits=64)
     sid = gc.server_load(sets.server)
     rc, Ts, _ = oc.server_table(sets.server)
@@ -51,18 +56,23 @@ def test_paper_sampled_layers(paper_case):
 
 def test_paper_result_decrypts_to_intersection(paper_case):
     oc, gc, s, rlk, sets, sid, Ts, cts, where = paper_case
-    out = gc.eval(sid, cts)
+    out = gc.eval(sid, cts)  # lazy rescaling, one-prime response (2 N words)
+    assert out.shape == (2, 1, 8192)
     slots, budget = gc.decrypt(out)
     assert budget > 0
     assert np.array_equal(slots, brute_indicator(sets.client, sets.server, where, 8192))
     assert int(slots.sum()) == 102
     oslots, obudget = oc.decrypt(s, out)
     assert np.array_equal(oslots, slots) and abs(obudget - budget) < 1e-9
-    # the one-prime response (about 0.11 MB) decrypts the same
-    sw = gc.mod_switch(out, 1)
-    assert np.array_equal(sw, oc.mod_switch(out, 1))
-    sws, swb = gc.decrypt(sw)
-    assert swb > 0 and np.array_equal(sws, slots)
+    # per-layer rounding on the same context and table decrypts the same
+    gc.set_rescale_group(1)
+    try:
+        pslots, pbudget = gc.decrypt(gc.eval(sid, cts))
+    finally:
+        gc.set_rescale_group(ALL)
+    assert pbudget > 0 and np.array_equal(pslots, slots)
+    # the response switch of a full ciphertext, word for word
+    assert np.array_equal(gc.mod_switch(cts[0], 1), oc.mod_switch(cts[0], 1))
     card = gc.eval(sid, cts, mode=1, mask_seed=5)
     cs, _ = gc.decrypt(card)
     assert int(cs.astype(np.int64).sum()) % 65537 == 102
@@ -95,13 +105,15 @@ def test_large_config_streamed_plaintexts():
     """Large configuration: N = 16384, eight primes (438 bits), h = 8,
     ell = 128, mu = 3487, 4096 client items against 2^24 server items (1%
     planted).  The NTT-form plaintexts (468 GB) cannot be resident, so the
-    evaluation regenerates them per layer chunk.  The oracle checks the
-    server table, the request words and one sampled layer's h' and E words;
-    the result decrypts to the brute-force intersection."""
+    evaluation regenerates them per layer chunk.  As bench.py runs it: one
+    rounding of the layers' last products, a one-prime response.  The
+    oracle checks the server table, the request words and one sampled
+    layer's h' and E words; the result decrypts to the brute-force
+    intersection."""
     torch_cuda()
     from paper_2310_14565_gb300.workload import make_sets
 
-    oc, gc, s, rlk = pair(16384, LARGE, 8, 40, mu=3487, ell=128)
+    oc, gc, s, rlk = pair(16384, LARGE, 8, 40, mu=3487, ell=128, rescale_group=ALL, response_primes=1)
     sets = make_sets(4096, 1 << 24, 41, bits=64)
     sid = gc.server_load(sets.server)
     rc, Ts, _ = oc.server_table(sets.server)

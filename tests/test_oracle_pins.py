@@ -747,3 +747,34 @@ def test_psi_with_more_bins_than_slots(oracle_mod):
     assert np.array_equal(slots, want) and int(want.sum()) >= 9
     # more client items than one block holds
     assert len(sets.client) > N
+
+
+# ------------------------------------------- false matches (Lemma 1)
+def test_false_match_rate_follows_the_hashed_collision_model(oracle_mod):
+    # A client item outside the server set matches when a server item of
+    # its bin has the same lambda_bar-bit x_L.  Permutation-based hashing
+    # puts log2 b of the lambda hash bits into the bin, so inside a bin the
+    # x_L of two unrelated items agree with probability 2^-lambda_bar.  Over
+    # seeded trials the false-match count must follow
+    # E = sum over non-member client items of (distinct x_L stored in its
+    # bin) / 2^lambda_bar, within Poisson noise (4 sigma), and be nonzero.
+    from paper_2310_14565_gb300.workload import make_sets
+
+    lb, logb, m, n, trials = 6, 6, 40, 60, 150
+    measured, expected = 0, 0.0
+    for tr in range(trials):
+        sets = make_sets(m, n, 5, bits=32, seed_items=500 + tr, seed_plant=900 + tr)
+        rc, table, where = oracle_mod.cuckoo(7 + tr, lb, logb, sets.client)
+        assert rc == 0
+        rc, Ts, _ = oracle_mod.simple_hash(7 + tr, lb, logb, sets.server, 200)
+        assert rc == 0
+        server = set(int(y) for y in sets.server)
+        for u, x in enumerate(sets.client):
+            if int(x) in server:
+                continue
+            col = Ts[:, where[u]]
+            stored = col[col != oracle_mod.DUMMY]
+            expected += len(set(int(v) for v in stored)) / 2.0 ** lb
+            measured += int(int(table[where[u]]) in set(int(v) for v in stored))
+    assert measured > 0
+    assert abs(measured - expected) <= 4 * math.sqrt(expected) + 1, (measured, expected)

@@ -118,6 +118,22 @@ def strerror(code: int) -> str:
         return "error %d" % code
 
 
+def _need(x, words, what):
+    """Reject a numpy array or torch tensor smaller than `words` 64-bit words
+    (the C ABI takes raw pointers and cannot check); raw integer pointers
+    are the caller's responsibility."""
+    if x is None or isinstance(x, int):
+        return
+    if isinstance(x, np.ndarray):
+        n, item = x.size, x.itemsize
+    elif hasattr(x, "numel"):
+        n, item = int(x.numel()), int(x.element_size())
+    else:
+        return
+    if item != 8 or n < words:
+        raise ValueError("%s: need %d 64-bit words, got %d elements of %d bytes" % (what, words, n, item))
+
+
 def _ptr(x):
     """Address of a numpy array, a torch tensor or an integer (None -> NULL)."""
     if x is None:
@@ -265,6 +281,7 @@ class Context:
     def server_plaintexts(self, set_id, layer0, nl, out=None, stream=None):
         if out is None:
             out = np.zeros(self._blocked((nl, self.ell, self.k, self.N)), dtype=np.uint64)
+        _need(out, self.blocks * nl * self.ell * self.k * self.N, "server_plaintexts out")
         _check(lib().pepsi_server_plaintexts(self._h, set_id, layer0, nl, _ptr(out), _stream(stream)),
                "pepsi_server_plaintexts")
         return out
@@ -274,6 +291,7 @@ class Context:
         items = np.ascontiguousarray(items, dtype=np.uint64)
         if out is None:
             out = np.zeros(self._blocked((self.ell, 2, self.k, self.N)), dtype=np.uint64)
+        _need(out, self._request_words(), "query out")
         where = np.full(max(items.size, 1), -1, dtype=np.int32)
         _check(lib().pepsi_query(self._h, _ptr(items) if items.size else None, items.size, enc_seed, _ptr(out),
                                  _ptr(where), _stream(stream)), "pepsi_query")
@@ -289,6 +307,9 @@ class Context:
             return np.concatenate([p[0] for p in parts]), min(p[1] for p in parts)
         ct = np.ascontiguousarray(ct, dtype=np.uint64) if isinstance(ct, np.ndarray) else ct
         r = int(ct.shape[-2])
+        if int(ct.shape[-1]) != self.N or not 1 <= r <= self.k:
+            raise ValueError("decrypt: a ciphertext is [2][r][N] with 1 <= r <= k")
+        _need(ct, 2 * r * self.N, "decrypt ct")
         slots = np.zeros(self.N, dtype=np.uint32)
         b = C.c_double(0)
         rc = lib().pepsi_decrypt_primes(self._h, _ptr(ct), r, _ptr(slots), C.byref(b))
@@ -304,13 +325,23 @@ class Context:
             out = np.zeros(((2, r, self.N) if single else (n, 2, r, self.N)), dtype=np.uint64)
             if isinstance(cts, np.ndarray):
                 cts = np.ascontiguousarray(cts, dtype=np.uint64)
+        _need(cts, n * 2 * self.k * self.N, "mod_switch cts")
+        _need(out, n * 2 * r * self.N, "mod_switch out")
         _check(lib().pepsi_mod_switch(self._h, _ptr(cts), n, r, _ptr(out), _stream(stream)), "pepsi_mod_switch")
         return out
 
     # ---- evaluation
+    def _request_words(self):
+        return self.blocks * self.ell * 2 * self.k * self.N
+
+    def _response_words(self):
+        return self.blocks * 2 * self.response_primes * self.N
+
     def eval(self, set_id, cts, mode=MODE_INDICATOR, mask_seed=0, out=None, stream=None):
         if out is None:
             out = np.zeros(self._blocked((2, self.response_primes, self.N)), dtype=np.uint64)
+        _need(cts, self._request_words(), "eval cts")
+        _need(out, self._response_words(), "eval out")
         _check(lib().pepsi_eval(self._h, set_id, _ptr(cts), mode, mask_seed, _ptr(out), _stream(stream)),
                "pepsi_eval")
         return out
@@ -320,6 +351,9 @@ class Context:
         nq = len(cts_list)
         if outs is None:
             outs = [np.zeros(self._blocked((2, self.response_primes, self.N)), dtype=np.uint64) for _ in range(nq)]
+        for x, o in zip(cts_list, outs):
+            _need(x, self._request_words(), "eval_batch cts")
+            _need(o, self._response_words(), "eval_batch out")
         sid = (C.c_int * nq)(*set_ids)
         cp = (C.c_void_p * nq)(*[_ptr(x) for x in cts_list])
         op = (C.c_void_p * nq)(*[_ptr(x) for x in outs])
@@ -331,24 +365,34 @@ class Context:
     def eval_layers(self, set_id, cts, layer0, nl, want_h=True, want_e=True, stream=None):
         h = np.zeros(self._blocked((nl, 2, self.k, self.N)), dtype=np.uint64) if want_h else None
         e = np.zeros(self._blocked((nl, 3, self.k, self.N)), dtype=np.uint64) if want_e else None
+        _need(cts, self._request_words(), "eval_layers cts")
         _check(lib().pepsi_eval_layers(self._h, set_id, _ptr(cts), layer0, nl, _ptr(h), _ptr(e), _stream(stream)),
                "pepsi_eval_layers")
         return h, e
 
     # ---- primitives (device buffers)
     def ntt(self, polys, count, inverse=False, stream=None):
+        _need(polys, count * self.k * self.N, "ntt polys")
         _check(lib().pepsi_ntt(self._h, _ptr(polys), count, int(inverse), _stream(stream)), "pepsi_ntt")
 
     def ct_mult(self, a, b, n, out, relin=False, stream=None):
+        ct2 = 2 * self.k * self.N
+        _need(a, n * ct2, "ct_mult a")
+        _need(b, n * ct2, "ct_mult b")
+        _need(out, n * (2 if relin else 3) * self.k * self.N, "ct_mult out")
         _check(lib().pepsi_ct_mult(self._h, _ptr(a), _ptr(b), n, int(relin), _ptr(out), _stream(stream)),
                "pepsi_ct_mult")
 
     def relin(self, ct3, n, out, stream=None):
+        _need(ct3, n * 3 * self.k * self.N, "relin input")
+        _need(out, n * 2 * self.k * self.N, "relin out")
         _check(lib().pepsi_relin(self._h, _ptr(ct3), n, _ptr(out), _stream(stream)), "pepsi_relin")
 
     def relin_noalloc(self, ct3, n, out, stream=None):
         """pepsi_relin without any allocation: scratch in the library's fixed
         16 MiB device array (shared by all calls; do not overlap calls)."""
+        _need(ct3, n * 3 * self.k * self.N, "relin_noalloc input")
+        _need(out, n * 2 * self.k * self.N, "relin_noalloc out")
         rc = lib().pepsi_relin_noalloc(self._h, _ptr(ct3), n, _ptr(out), _stream(stream))
         if rc != OK:
             err = PepsiError(rc, "pepsi_relin_noalloc")

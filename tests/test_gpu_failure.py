@@ -33,3 +33,37 @@ def test_bounded_wait_times_out_and_context_recovers():
     cts, _ = gc.query(sets.client, 4)
     _, Ts, _ = oc.server_table(sets.server)
     assert np.array_equal(gc.eval(sid, cts), oc.eval(rlk, cts, Ts))
+
+
+def test_binding_rejects_malformed_sizes():
+    """Buffers smaller than the documented layouts never reach the C ABI
+    (whose raw pointers cannot be checked), so no kernel reads or writes
+    past them."""
+    torch = torch_cuda()
+    import paper_2310_14565_gb300 as pepsi
+
+    gc = pepsi.Context(N=64, prime_bits=[55, 55, 54, 54], h=4, lambda_bar=10, mu=4)
+    sid = gc.server_load(np.arange(1, 20, dtype=np.uint64))
+    good = np.zeros((gc.ell, 2, 4, 64), np.uint64)
+    short = torch.zeros(gc.ell * 2 * 4 * 64 - 1, dtype=torch.int64, device="cuda")
+    with pytest.raises(ValueError):
+        gc.eval(sid, short)
+    with pytest.raises(ValueError):
+        gc.eval(sid, good, out=np.zeros((2, 4, 63), np.uint64))
+    with pytest.raises(ValueError):
+        gc.eval(sid, good.astype(np.uint32))  # 4-byte words
+    with pytest.raises(ValueError):
+        gc.eval_batch([sid], [short])
+    with pytest.raises(ValueError):
+        gc.decrypt(np.zeros((2, 4, 32), np.uint64))
+    with pytest.raises(ValueError):
+        gc.ntt(torch.zeros(3 * 4 * 64 - 8, dtype=torch.int64, device="cuda"), 3)
+    one = torch.zeros(2 * 4 * 64, dtype=torch.int64, device="cuda")
+    with pytest.raises(ValueError):
+        gc.ct_mult(one, one[:-1], 1, torch.zeros(3 * 4 * 64, dtype=torch.int64, device="cuda"))
+    with pytest.raises(ValueError):
+        gc.ct_mult(one, one, 1, torch.zeros(3 * 4 * 64 - 1, dtype=torch.int64, device="cuda"))
+    with pytest.raises(ValueError):
+        gc.mod_switch(np.zeros((2, 4, 64), np.uint64), 1, out=np.zeros((2, 1, 60), np.uint64))
+    out = gc.eval(sid, gc.query(np.arange(5, 9, dtype=np.uint64), 4)[0])  # well-formed calls still work
+    assert gc.decrypt(out)[1] > 0

@@ -39,6 +39,11 @@ WL_SMALL = dict(WL, mu=35, n=1 << 14)
 # large configuration: the 468 GB plaintext table is regenerated per layer chunk
 WL_LARGE = dict(N=16384, prime_bits=[55] * 6 + [54] * 2, h=8, ell=128, lambda_bar=40, mu=3487, m=4096, n=1 << 24,
                 planted=41)
+# the paper's own parameters for its headline run (Section 7, Table 5): h = 8,
+# ell = 24, effective bitlength 19, b = N = 8192, 32-bit elements; q per
+# Table 3 for h = 5..8 (204 bits, four 51-bit primes)
+WL_PAPER_EXACT = dict(N=8192, prime_bits=[51] * 4, h=8, ell=24, lambda_bar=19, mu=526, m=1024, n=1 << 20,
+                      planted=102, bits=32)
 HASH_KEY, KEY_SEED, ENC_SEED = 0x5EED, 3, 4
 WORKLOAD_NAME = ("paper-shaped PSI: N=8192 bins, t=65537, q=4 RNS primes (55,55,54,54 bits), CW code ell=600 h=4, "
                  "mu=526 layers, 1024 client x 2^20 server uniform 64-bit items, 102 planted")
@@ -205,7 +210,7 @@ def run_ours(args):
                         lambda_bar=WL["lambda_bar"], mu=WL["mu"], hash_key=HASH_KEY, key_seed=KEY_SEED,
                         rescale_group=RESCALE["all"], response_primes=RESPONSE_PRIMES)
     ctx.set_rescale_group(RESCALE[args.rescale])
-    sets = make_sets(WL["m"], WL["n"], WL["planted"], bits=64)
+    sets = make_sets(WL["m"], WL["n"], WL["planted"], bits=WL.get("bits", 64))
     t0 = time.perf_counter()
     sid = ctx.server_load(sets.server)
     offline_ms = (time.perf_counter() - t0) * 1e3
@@ -225,7 +230,10 @@ def run_ours(args):
     torch.cuda.synchronize()
     # correctness of the timed configuration (outside the timed region)
     slots, budget = ctx.decrypt(out_dev)
-    correct = int(slots.sum()) == WL["planted"] and budget > 0
+    # every planted item matches; at a short effective bitlength an H0
+    # collision may add a match (about 0.75 per query at lambda_bar = 19)
+    correct = (int(slots.sum()) == WL["planted"] or (WL["lambda_bar"] < 32 and int(slots.sum()) >= WL["planted"])) \
+        and budget > 0
 
     ctx.profile(False)  # resets the launch counters
     clocks = Clocks(local)
@@ -295,12 +303,15 @@ def run_ours(args):
                   "same_decryption": bool((oslots == slots).all()), "steps": osteps}
     ctx.set_rescale_group(RESCALE[args.rescale])
 
-    if args.case == "large":
+    if args.case in ("large", "paper-exact"):
         line = {"metric": METRIC, "value": round(ms, 3), "unit": "ms", "n_gpus": args.gpus, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": round(ms, 3), "higher_is_better": False, "scaling": "weak",
                 "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-                "config": {"workload": WORKLOAD_NAME, "l2": "inputs larger than L2 (plaintext chunks of 4.3 GB)",
-                           "rescale": RESCALE_NOTE[args.rescale]},
+                "config": {"workload": WORKLOAD_NAME, "rescale": RESCALE_NOTE[args.rescale],
+                           "l2": ("inputs larger than L2 (plaintext chunks of 4.3 GB)" if args.case == "large" else
+                                  "inputs larger than L2: the 3.3 GB resident plaintext table is read every step")},
+                "e2e": {"value": round(e2e_ms, 3), "unit": "ms", "h2d_bytes_per_step": int(cts_np.nbytes),
+                        "d2h_bytes_per_step": int(out_pinned.numel() * 8)},
                 "other_rounding": other_line,
                 "correct": correct, "noise_budget_bits": round(budget, 2),
                 "offline_server_load_ms": round(offline_ms, 1),
@@ -615,7 +626,7 @@ def main():
     ap.add_argument("--rescale", choices=["all", "layer"], default="all",
                     help="all: one rounding of the layers' last products per evaluation (lazy rescaling); "
                          "layer: every product rounded (textbook FV words)")
-    ap.add_argument("--case", choices=["paper", "small", "large", "sweep-h", "serve"], default="paper",
+    ap.add_argument("--case", choices=["paper", "small", "large", "paper-exact", "sweep-h", "serve"], default="paper",
                     help="small: the same kernels on 2^14 server items (mu=35), for profiler captures; "
                          "large: N=16384, 8 primes, h=8, 4096 x 2^24 items, streamed plaintexts")
     args = ap.parse_args()
@@ -623,6 +634,12 @@ def main():
     if args.case == "small":
         WL.update(WL_SMALL)
         WORKLOAD_NAME = WORKLOAD_NAME.replace("mu=526", "mu=35").replace("2^20", "2^14") + " (profiling case)"
+        args.no_cpu_baseline = True
+    elif args.case == "paper-exact":
+        WL.update(WL_PAPER_EXACT)
+        WORKLOAD_NAME = ("the paper's own headline parameters: N=b=8192, t=65537, q=4 RNS primes (51 bits each, "
+                         "204 bits per Table 3), CW code ell=24 h=8, effective bitlength 19, mu=526, 1024 client x "
+                         "2^20 server uniform 32-bit items, 102 planted (paper: 0.83 s online on an unstated CPU)")
         args.no_cpu_baseline = True
     elif args.case == "large":
         WL.update(WL_LARGE)

@@ -23,7 +23,9 @@ inline int ntt_threads(int N) {
 }
 
 // ------------------------------------------------------------------ NTT
-template <bool FWD>
+// SPLIT: store the result in the split operand format of the
+// multiply-accumulate (the request's forward transform).
+template <bool FWD, bool SPLIT = false>
 __global__ void __launch_bounds__(NTT_MAX_THREADS, 2) k_ntt(DevView V, const u64* __restrict__ src, u64* dst, int np, int p0, size_t src_os,
                       size_t dst_os) {
   extern __shared__ u64 sm[];
@@ -39,7 +41,12 @@ __global__ void __launch_bounds__(NTT_MAX_THREADS, 2) k_ntt(DevView V, const u64
     ntt_fwd_fast(sm, V, p0 + pl);
   else
     ntt_inv_fast(sm, V, p0 + pl);
-  for (int x = threadIdx.x; x < N; x += blockDim.x) d[x] = sm[nsw(x)];
+  if (SPLIT) {
+    const u64 sp = V.pr[p0 + pl].split;
+    for (int x = threadIdx.x; x < N; x += blockDim.x) d[x] = to_split(sm[nsw(x)], sp);
+  } else {
+    for (int x = threadIdx.x; x < N; x += blockDim.x) d[x] = sm[nsw(x)];
+  }
 }
 
 // ---------------------------------------------------------- CW unranking
@@ -1130,11 +1137,13 @@ inline unsigned grid_for(size_t total, int threads) { return (unsigned)((total +
 
 // ------------------------------------------------------------ launchers
 void launch_ntt(const DevView& V, bool fwd, const u64* src, u64* dst, size_t outer, int np, int p0, size_t src_os,
-                size_t dst_os, cudaStream_t st) {
+                size_t dst_os, cudaStream_t st, bool split_out) {
   const size_t rows = outer * (size_t)np;
   if (!rows) return;
   const size_t smem = (size_t)V.N * sizeof(u64);
-  if (fwd)
+  if (fwd && split_out)
+    k_ntt<true, true><<<(unsigned)rows, ntt_threads(V.N), smem, st>>>(V, src, dst, np, p0, src_os, dst_os);
+  else if (fwd)
     k_ntt<true><<<(unsigned)rows, ntt_threads(V.N), smem, st>>>(V, src, dst, np, p0, src_os, dst_os);
   else
     k_ntt<false><<<(unsigned)rows, ntt_threads(V.N), smem, st>>>(V, src, dst, np, p0, src_os, dst_os);
@@ -1394,6 +1403,7 @@ cudaError_t kernels_init(int N) {
   };
   set((const void*)k_ntt<true>);
   set((const void*)k_ntt<false>);
+  set((const void*)k_ntt<true, true>);
   set((const void*)k_ptgen);
   set((const void*)k_valgen);
   set((const void*)k_mac);

@@ -7,7 +7,7 @@
 // Batched NTT over rows laid out [outer][np][N]: row r uses prime p0 + (r % np);
 // src and dst may alias (in place).  fwd: coefficient -> evaluation form.
 void launch_ntt(const DevView& V, bool fwd, const u64* src, u64* dst, size_t outer, int np, int p0, size_t src_os,
-                size_t dst_os, cudaStream_t st);
+                size_t dst_os, cudaStream_t st, bool split_out = false);
 
 // CW-Encode of table entries (colex rank -> positions), pos[count][h], dummy -> PEPSI_CW_NONE.
 void launch_cw_unrank(const u64* T, size_t count, const u64* binom, int ell, int h, uint16_t* pos, cudaStream_t st);

@@ -459,14 +459,13 @@ cudaError_t copy_any(void* dst, const void* src, size_t bytes, cudaStream_t st) 
 // operand format of the multiply-accumulate, into C.
 cudaError_t prepare_request(pepsi_ctx* c, const u64* cts, u64* C, cudaStream_t st) {
   const size_t kN = (size_t)c->k * c->N, words = (size_t)c->ell * 2 * kN;
-  if (is_device_ptr(cts)) {
-    ntt(c, true, cts, C, (size_t)c->ell * 2, c->k, 0, kN, kN, st);
-  } else {
+  const u64* src = cts;
+  if (!is_device_ptr(cts)) {
     CK(copy_any(C, cts, words * 8, st));
-    ntt(c, true, C, C, (size_t)c->ell * 2, c->k, 0, kN, kN, st);
+    src = C;
   }
-  Prof p(c, PC_POINTWISE, st);
-  launch_split(c->V, C, (size_t)c->ell * 2, true, st);
+  Prof p(c, PC_NTT, st);  // forward NTT, stored in the split operand format
+  launch_ntt(c->V, true, src, C, (size_t)c->ell * 2, c->k, 0, kN, kN, st, true);
   return cudaSuccess;
 }
 

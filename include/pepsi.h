@@ -214,6 +214,17 @@ int pepsi_query(pepsi_ctx* ctx, const uint64_t* items, size_t m, uint64_t enc_se
 int pepsi_eval(pepsi_ctx* ctx, int set_id, const uint64_t* cts, int mode, uint64_t mask_seed, uint64_t* out_ct,
                void* stream);
 
+/* Autotuning of the evaluation schedule (no counterpart in the paper):
+ * evaluates the request cts ([B][ell][2][k][N], host or device) against
+ * set_id with circuit chunks of 32, 64, 128 and 256 layers (stopping at
+ * the first whose scratch does not fit in memory), times two evaluations
+ * of each with CUDA events on the stream, and keeps the fastest chunk for
+ * later evaluations on this context (*chosen, may be NULL).  Larger chunks
+ * fill the GPU with more blocks per launch.  The
+ * result words do not depend on the chunk.  Synchronises the stream.
+ * Errors: as pepsi_eval. */
+int pepsi_autotune(pepsi_ctx* ctx, int set_id, const uint64_t* cts, void* stream, uint32_t* chosen);
+
 /* Several requests in one call: request i is evaluated against server set
  * set_ids[i] exactly as by pepsi_eval (same output words), with mode
  * modes[i] (NULL: all indicator) and mask seed mask_seeds[i] (NULL: 0).

@@ -62,6 +62,7 @@ SYMBOLS = {
     "pepsi_setup": (C.c_int, [C.POINTER(Params), C.c_uint64, C.POINTER(C.c_void_p)]),
     "pepsi_get_info": (C.c_int, [C.c_void_p, C.POINTER(Info)]),
     "pepsi_set_rescale_group": (C.c_int, [C.c_void_p, C.c_uint32]),
+    "pepsi_autotune": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.POINTER(C.c_uint32)]),
     "pepsi_wait_probe": (C.c_int, [C.c_void_p, C.c_int]),
     "pepsi_request_bits": (C.c_int, [C.c_uint32, C.c_uint32, C.c_uint64, C.POINTER(C.c_double),
                                      C.POINTER(C.c_uint64), C.POINTER(C.c_uint32), C.POINTER(C.c_uint32)]),
@@ -345,6 +346,14 @@ class Context:
         _check(lib().pepsi_eval(self._h, set_id, _ptr(cts), mode, mask_seed, _ptr(out), _stream(stream)),
                "pepsi_eval")
         return out
+
+    def autotune(self, set_id, cts, stream=None):
+        """Time the evaluation at layer chunks of 32..256, keep the fastest;
+        returns the chosen chunk (outputs do not depend on it)."""
+        _need(cts, self._request_words(), "autotune cts")
+        chosen = C.c_uint32(0)
+        _check(lib().pepsi_autotune(self._h, set_id, _ptr(cts), _stream(stream), C.byref(chosen)), "pepsi_autotune")
+        return int(chosen.value)
 
     def eval_batch(self, set_ids, cts_list, modes=None, mask_seeds=None, outs=None, stream=None):
         """pepsi_eval_batch: one output ciphertext per request."""

@@ -84,7 +84,7 @@ struct pepsi_ctx {
   u32 logb = 0, blocks = 1;      // bins = blocks * N = 2^logb
   // scratch, grown on demand
   std::vector<DevBuf> scratch;
-  int chunk = 32;
+  int chunk = 64;  // layers per circuit chunk (pepsi_autotune may change it)
   u32 rescale_cap = 1;      // most layers one rounding of the last products may cover
   bool value_margin = false;  // B also holds the value products under lazy rescaling
   int resp = 0;               // primes of the evaluation's response (k: no switching)
@@ -540,6 +540,8 @@ cudaError_t finish_request(pepsi_ctx* c, EvalBufs& b, u64* acc, bool acc_ntt, in
 
 // scratch id of the lazy-rescaling run sum of a single request
 constexpr int kScratchAccX = 46;
+// scratch id of the autotuner's response buffer
+constexpr int kScratchTune = 48;
 
 // Core of pepsi_eval / pepsi_eval_layers.
 int eval_core(pepsi_ctx* c, int set_id, const u64* cts, u32 layer0, u32 nl, int mode, u64 mask_seed, u64* out_ct,
@@ -1356,6 +1358,52 @@ int pepsi_eval(pepsi_ctx* c, int set_id, const uint64_t* cts, int mode, uint64_t
     if (rc) return rc;
   }
   return PEPSI_OK;
+}
+
+int pepsi_autotune(pepsi_ctx* c, int set_id, const uint64_t* cts, void* stream, uint32_t* chosen) {
+  SetGroup* G = group(c, set_id);
+  if (!G || !cts) return PEPSI_E_PARAM;
+  cudaStream_t st = pick(c, stream);
+  cudaError_t e = cudaSuccess;
+  u64* out = (u64*)scratch(c, kScratchTune, response_block_words(c) * c->blocks * 8, &e);
+  if (!out) return cuda_status(e);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  CKS(cudaEventCreate(&e0));
+  CKS(cudaEventCreate(&e1));
+  const int saved = c->chunk;
+  int best = saved;
+  float best_ms = 0;
+  int rc = PEPSI_OK;
+  for (int chunk : {32, 64, 128, 256}) {
+    c->chunk = chunk;
+    for (int rep = 0; rep < 3 && !rc; ++rep) {  // one warm-up, two timed
+      if (rep == 1) cudaEventRecord(e0, st);
+      rc = pepsi_eval(c, set_id, cts, PEPSI_MODE_INDICATOR, 0, out, st);
+    }
+    if (rc == PEPSI_E_NOMEM && best_ms > 0) {  // this chunk's scratch does not fit: keep the best so far
+      cudaGetLastError();
+      rc = PEPSI_OK;
+      break;
+    }
+    if (rc) break;
+    cudaEventRecord(e1, st);
+    e = cudaEventSynchronize(e1);
+    float ms = 0;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    if (e != cudaSuccess) {
+      rc = cuda_status(e);
+      break;
+    }
+    if (best_ms == 0 || ms < best_ms) {
+      best_ms = ms;
+      best = chunk;
+    }
+  }
+  c->chunk = rc ? saved : best;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (!rc && chosen) *chosen = (uint32_t)best;
+  return rc;
 }
 
 int pepsi_eval_batch(pepsi_ctx* c, int nq, const int* set_ids, const uint64_t* const* cts, const int* modes,

@@ -204,6 +204,8 @@ def run_ours(args):
     if not os.path.exists(pepsi.LIB_PATH):
         _build.build()
     N, k = WL["N"], len(WL["prime_bits"])
+    if args.chunk:
+        os.environ["PEPSI_CHUNK"] = str(args.chunk)
     # the auxiliary base is sized for one rounding over all layers; the
     # rounding mode of each evaluation is then a context setting
     ctx = pepsi.Context(N=N, t=65537, prime_bits=WL["prime_bits"], h=WL["h"], ell=WL["ell"],
@@ -225,8 +227,9 @@ def run_ours(args):
     def step():
         ctx.eval(sid, cts_dev, out=out_dev)
 
-    # the layer-chunk schedule, autotuned on this request (words do not depend on it)
-    chunk = ctx.autotune(sid, cts_dev)
+    # the layer-chunk schedule, autotuned on this request unless --chunk fixes
+    # it (words do not depend on it)
+    chunk = args.chunk if args.chunk else ctx.autotune(sid, cts_dev)
 
     for _ in range(args.warmup):
         step()
@@ -648,6 +651,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--chunk", type=int, default=0,
+                    help="circuit chunk in layers (default: autotuned on the request)")
     ap.add_argument("--rescale", choices=["all", "layer"], default="all",
                     help="all: one rounding of the layers' last products per evaluation (lazy rescaling); "
                          "layer: every product rounded (textbook FV words)")

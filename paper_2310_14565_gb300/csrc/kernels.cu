@@ -260,9 +260,12 @@ __device__ __forceinline__ void fold_into(u64& acc, u64& S0, u64& S1, u64& S2, u
   S0 = S1 = S2 = 0;
 }
 
+// One launch covers the codeword bits [j0, j0 + nj) (nj a multiple of JS
+// unless the range ends at ell); with acc_in it adds to the h' already in
+// H, so a request can be multiplied in pieces as it arrives.
 __global__ void __launch_bounds__(mac::THREADS, 1)
     k_mac(DevView V, const __grid_constant__ CUtensorMap tmP, const __grid_constant__ CUtensorMap tmC,
-          u64* __restrict__ H, int ell, int L, int fold_stages, int* err) {
+          u64* __restrict__ H, int j0, int nj, int L, int fold_stages, int acc_in, int* err) {
   using namespace mac;
   extern __shared__ __align__(128) u64 sm_raw[];
   // 128-byte aligned stage buffers for the tensor copies
@@ -272,7 +275,7 @@ __global__ void __launch_bounds__(mac::THREADS, 1)
   const int nl = min(LB, L - l0);
   const size_t idx0 = (size_t)blockIdx.y * TN;
   const int cnt = (int)min((size_t)TN, kN - idx0);
-  const int nst = (ell + JS - 1) / JS;
+  const int nst = (nj + JS - 1) / JS;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const u32 sbase = (u32)__cvta_generic_to_shared(sm);
   const u32 full0 = sbase + (u32)(NST * STAGE_WORDS * 8), empty0 = full0 + NST * 8;
@@ -303,8 +306,8 @@ __global__ void __launch_bounds__(mac::THREADS, 1)
         const u32 sb = sbase + (u32)(buf * STAGE_WORDS * 8);
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         mbar_expect_tx(bar, (u32)STAGE_WORDS * 8);
-        tma_load_3d(sb, &tmP, (int)idx0, st * JS, l0, bar);
-        tma_load_3d(sb + (u32)P_WORDS * 8, &tmC, (int)idx0, 0, st * JS, bar);
+        tma_load_3d(sb, &tmP, (int)idx0, j0 + st * JS, l0, bar);
+        tma_load_3d(sb + (u32)P_WORDS * 8, &tmC, (int)idx0, 0, j0 + st * JS, bar);
         issued = st + 1;
       }
     }
@@ -320,7 +323,11 @@ __global__ void __launch_bounds__(mac::THREADS, 1)
 #pragma unroll
     for (int l = 0; l < LPT; ++l)
 #pragma unroll
-      for (int c = 0; c < 2; ++c) S0[l][c] = S1[l][c] = S2[l][c] = acc[l][c] = 0;
+      for (int c = 0; c < 2; ++c) {
+        S0[l][c] = S1[l][c] = S2[l][c] = acc[l][c] = 0;
+        const int layer = g * LPT + l;
+        if (acc_in && active && layer < nl) acc[l][c] = H[((size_t)(l0 + layer) * 2 + c) * kN + idx];
+      }
     int since = 0;
     for (int st = 0; st < nst; ++st) {
       const int buf = st % NST;
@@ -1224,8 +1231,11 @@ cudaError_t launch_mac_multi(const DevView& V, const u64* C, int nq, const u64* 
 }
 
 cudaError_t launch_mac(const DevView& V, const u64* C, const u64* P, u64* H, int ell, int L, int fold, int* err,
-                       cudaStream_t st) {
+                       cudaStream_t st, int j0, int nj, bool acc_in) {
   if (L <= 0) return cudaSuccess;
+  if (nj < 0) nj = ell - j0;
+  if (j0 < 0 || nj <= 0 || j0 + nj > ell || (j0 % mac::JS) || (j0 + nj < ell && nj % mac::JS))
+    return cudaErrorInvalidValue;
   const u64 kN = (u64)V.k * V.N;
   CUtensorMap tmP, tmC;
   if (!encode3d(&tmP, P, kN, ell, L, kN, (u64)ell * kN, mac::TN, mac::JS, mac::LB) ||
@@ -1233,7 +1243,7 @@ cudaError_t launch_mac(const DevView& V, const u64* C, const u64* P, u64* H, int
     return cudaErrorInvalidValue;
   const int fold_stages = fold / mac::JS > 0 ? fold / mac::JS : 1;
   dim3 grid((L + mac::LB - 1) / mac::LB, (unsigned)((kN + mac::TN - 1) / mac::TN));
-  k_mac<<<grid, mac::THREADS, mac::SMEM, st>>>(V, tmP, tmC, H, ell, L, fold_stages, err);
+  k_mac<<<grid, mac::THREADS, mac::SMEM, st>>>(V, tmP, tmC, H, j0, nj, L, fold_stages, acc_in ? 1 : 0, err);
   return cudaSuccess;
 }
 

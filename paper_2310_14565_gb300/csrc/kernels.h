@@ -20,7 +20,8 @@ void launch_ptgen(const DevView& V, const uint16_t* pos, int L, int ell, int h, 
 // 64-bit partial sums.  *err is set when a bounded wait for a TMA copy expires.
 // Returns cudaErrorInvalidValue when the tensor maps of the copies cannot be encoded.
 cudaError_t launch_mac(const DevView& V, const u64* C, const u64* P, u64* H, int ell, int L, int fold, int* err,
-                       cudaStream_t st);
+                       cudaStream_t st, int j0 = 0, int nj = -1,
+                       bool acc_in = false);
 
 // The same for nq <= 2 requests sharing the plaintexts: C holds the requests back to back
 // ([nq][ell][2][k][N], split format), H[q] starts at H + q * hq.

@@ -68,6 +68,13 @@ struct pepsi_ctx {
   cudaStream_t stream = nullptr;
   cudaStream_t aux_stream = nullptr;  // overlapped multiply-accumulates of pepsi_eval_batch
   cudaEvent_t aux_ev[4] = {};
+  // host requests: copies of the request pieces, overlapped with the
+  // multiply-accumulate of the pieces already on the device (two pieces:
+  // each further MAC launch costs its pipeline fill, measured to outweigh
+  // the copy it hides)
+  static constexpr int kPieces = 2;
+  cudaStream_t copy_stream = nullptr;
+  cudaEvent_t copy_ready = nullptr, copy_ev[kPieces] = {};
   // device tables and keys
   DevPrime* d_pr = nullptr;
   ulonglong2 *d_twp = nullptr, *d_itwp = nullptr;  // twiddles interleaved with their Shoup companions
@@ -538,6 +545,15 @@ cudaError_t finish_request(pepsi_ctx* c, EvalBufs& b, u64* acc, bool acc_ntt, in
   return copy_any(out, b.out, 2 * kN * 8, st);
 }
 
+// The copy stream of piecewise request uploads and its events, on first use.
+cudaError_t ensure_copy_stream(pepsi_ctx* c) {
+  if (c->copy_stream) return cudaSuccess;
+  CK(cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking));
+  CK(cudaEventCreateWithFlags(&c->copy_ready, cudaEventDisableTiming));
+  for (auto& ev : c->copy_ev) CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+  return cudaSuccess;
+}
+
 // scratch id of the lazy-rescaling run sum of a single request
 constexpr int kScratchAccX = 46;
 // scratch id of the autotuner's response buffer
@@ -569,16 +585,47 @@ int eval_core(pepsi_ctx* c, int set_id, const u64* cts, u32 layer0, u32 nl, int 
     lr.acc = b.acc;
     lr.G = G;
   }
-  CKS(prepare_request(c, cts, b.C, st));
-  // a5 on the resident layers: one multiply-accumulate launch over all of
-  // them, so the request is read from HBM once
+  // A host request with resident layers arrives in pieces of its code bits:
+  // the upload of piece p+1 overlaps the NTT and multiply-accumulate of
+  // piece p, each piece's MAC adding into h' (the MAC is a sum over the
+  // bits).  Otherwise the request is prepared whole.
+  constexpr int npieces = pepsi_ctx::kPieces;
+  const bool pieces = !is_device_ptr(cts) && res_end > layer0 && c->ell >= 4 * npieces;
+  if (!pieces) CKS(prepare_request(c, cts, b.C, st));
+  // a5 on the resident layers: a multiply-accumulate launch over all of
+  // them (one per piece), so the request is read from HBM once
   u64* Hall = nullptr;
   if (res_end > layer0) {
     Hall = (u64*)scratch(c, S_HALL, (size_t)(res_end - layer0) * ct2 * 8, &e);
     if (!Hall) return cuda_status(e);
-    Prof p(c, PC_MAC, st);
-    CKS(mac_status(launch_mac(c->V, b.C, S.dP + (size_t)layer0 * c->ell * kN, Hall, c->ell, (int)(res_end - layer0),
-                              c->mac_fold, c->d_err, st)));
+    const u64* P0 = S.dP + (size_t)layer0 * c->ell * kN;
+    if (pieces) {
+      int jb[pepsi_ctx::kPieces + 1];
+      for (int q = 0; q < npieces; ++q) jb[q] = (c->ell * q / npieces) & ~3;  // multiples of 4 bits
+      jb[npieces] = c->ell;
+      CKS(ensure_copy_stream(c));
+      CKS(cudaEventRecord(c->copy_ready, st));  // earlier work on st no longer reads the request buffer
+      CKS(cudaStreamWaitEvent(c->copy_stream, c->copy_ready, 0));
+      for (int q = 0; q < npieces; ++q) {
+        CKS(cudaMemcpyAsync(b.C + (size_t)jb[q] * ct2, cts + (size_t)jb[q] * ct2,
+                            (size_t)(jb[q + 1] - jb[q]) * ct2 * 8, cudaMemcpyHostToDevice, c->copy_stream));
+        CKS(cudaEventRecord(c->copy_ev[q], c->copy_stream));
+      }
+      for (int q = 0; q < npieces; ++q) {
+        CKS(cudaStreamWaitEvent(st, c->copy_ev[q], 0));
+        {
+          Prof p(c, PC_NTT, st);  // forward NTT of the piece, stored in the split format
+          launch_ntt(c->V, true, b.C + (size_t)jb[q] * ct2, b.C + (size_t)jb[q] * ct2,
+                     (size_t)(jb[q + 1] - jb[q]) * 2, c->k, 0, kN, kN, st, true);
+        }
+        Prof p(c, PC_MAC, st);
+        CKS(mac_status(launch_mac(c->V, b.C, P0, Hall, c->ell, (int)(res_end - layer0), c->mac_fold, c->d_err, st,
+                                  jb[q], jb[q + 1] - jb[q], q > 0)));
+      }
+    } else {
+      Prof p(c, PC_MAC, st);
+      CKS(mac_status(launch_mac(c->V, b.C, P0, Hall, c->ell, (int)(res_end - layer0), c->mac_fold, c->d_err, st)));
+    }
   }
   bool first = true;
   u64* const Hchunk = b.H;  // h' of a regenerated chunk (Lc layers)
@@ -879,6 +926,10 @@ void pepsi_destroy(pepsi_ctx* c) {
   cudaFree(c->d_err);
   if (c->stream) cudaStreamDestroy(c->stream);
   if (c->aux_stream) cudaStreamDestroy(c->aux_stream);
+  if (c->copy_stream) cudaStreamDestroy(c->copy_stream);
+  if (c->copy_ready) cudaEventDestroy(c->copy_ready);
+  for (auto ev : c->copy_ev)
+    if (ev) cudaEventDestroy(ev);
   for (auto ev : c->aux_ev)
     if (ev) cudaEventDestroy(ev);
   delete c;

@@ -8,8 +8,7 @@
  *
  * Every function states the passage it follows.  Where the paper is silent
  * (prime choice, roots, hashing functions, randomness, CW mapping, slot
- * order) the function follows the reading written in its comment; the same
- * readings are listed in the design doc.
+ * order) the function follows the reading written in its comment.
  *
  * Arithmetic is the textbook one: a*b mod q through a 128-bit product and
  * the `%` operator, big integers through schoolbook limbs and bit-serial

@@ -778,3 +778,23 @@ def test_false_match_rate_follows_the_hashed_collision_model(oracle_mod):
             measured += int(int(table[where[u]]) in set(int(v) for v in stored))
     assert measured > 0
     assert abs(measured - expected) <= 4 * math.sqrt(expected) + 1, (measured, expected)
+
+
+def test_relin_words_against_big_integer_schoolbook(oracle_mod):
+    # RNS-digit key switching without a special prime: d_i = [d2]_{q_i} in
+    # [0, q_i), (c0, c1) += sum_i d_i * rlk_i, products in Z_{q_j}[X]/(X^N+1)
+    # recomputed with Python integers
+    c = oracle_mod.Ctx(N=8, t=T, prime_bits=[36, 36, 37], h=1, lambda_bar=3)
+    s, rlk = c.keygen(9)
+    rng = np.random.default_rng(11)
+    ct3 = np.stack([np.stack([rng.integers(0, q, size=8, dtype=np.uint64) for q in c.q]) for _ in range(3)])
+    got = c.relin(rlk, ct3)
+    N = c.N
+    for comp in range(2):
+        for j, qj in enumerate(c.q):
+            acc = [int(x) for x in ct3[comp, j]]
+            for i in range(c.k):
+                digit = [int(x) % qj for x in ct3[2, i]]  # [d2]_{q_i}, then taken mod q_j
+                prod = negacyclic_schoolbook(digit, [int(x) for x in rlk[i, comp, j]], N, qj)
+                acc = [(a + b) % qj for a, b in zip(acc, prod)]
+            assert [int(x) for x in got[comp, j]] == acc

@@ -11,8 +11,8 @@ Algorithm 1) from device-resident request ciphertexts to a device-resident
 result ciphertext.  By default the last ciphertext products of all layers
 are rounded once (lazy rescaling, --rescale all); --rescale layer rounds
 every layer's product (textbook FV words).  Both are exact and decrypt to
-the same result; the line reports the other mode's time too.  The resident server plaintext table (82.7 GB) is read in
-full by every step, so the inputs of a step are larger than L2.
+the same result; the line reports the other mode's time too.  The resident server plaintext table (82.7 GB of
+64-bit words) is read in full by every step, so the inputs of a step are larger than L2.
 
 Prints one JSON line.  --impl reference times the CPU oracle instead (the
 project's plain C reference on the host cores, on a bounded layer sample
@@ -47,7 +47,7 @@ WL_PAPER_EXACT = dict(N=8192, prime_bits=[51] * 4, h=8, ell=24, lambda_bar=19, m
 HASH_KEY, KEY_SEED, ENC_SEED = 0x5EED, 3, 4
 WORKLOAD_NAME = ("paper-shaped PSI: N=8192 bins, t=65537, q=4 RNS primes (55,55,54,54 bits), CW code ell=600 h=4, "
                  "mu=526 layers, 1024 client x 2^20 server uniform 64-bit items, 102 planted")
-L2_NOTE = "inputs larger than L2: the 82.7 GB resident plaintext table is streamed from HBM every step"
+L2_NOTE = "inputs larger than L2: the %.1f GB resident plaintext table is streamed from HBM every step"
 RESCALE_NOTE = {"all": "lazy: last ciphertext products of all layers summed exactly, rounded once",
                 "layer": "per layer: every ciphertext product rounded (textbook FV)"}
 
@@ -210,8 +210,10 @@ def run_ours(args):
     # rounding mode of each evaluation is then a context setting
     ctx = pepsi.Context(N=N, t=65537, prime_bits=WL["prime_bits"], h=WL["h"], ell=WL["ell"],
                         lambda_bar=WL["lambda_bar"], mu=WL["mu"], hash_key=HASH_KEY, key_seed=KEY_SEED,
-                        rescale_group=RESCALE["all"], response_primes=RESPONSE_PRIMES)
+                        rescale_group=RESCALE["all"], response_primes=RESPONSE_PRIMES,
+                        plaintext_bytes=args.plaintext_bytes)
     ctx.set_rescale_group(RESCALE[args.rescale])
+    pbytes = ctx.plaintext_bytes
     sets = make_sets(WL["m"], WL["n"], WL["planted"], bits=WL.get("bits", 64))
     t0 = time.perf_counter()
     sid = ctx.server_load(sets.server)
@@ -273,10 +275,12 @@ def run_ours(args):
     ctx.profile(False)
     mac_launches, mac_ms = prof["mac"]
     mac_launches_per_eval = mac_launches / psteps
-    # algorithmic bytes of the MAC per evaluation: the plaintext table (mu*ell*k*N words),
-    # the request (ell*2*k*N words, read once by each launch) and h' (mu*2*k*N words), 8 bytes each
+    # algorithmic bytes of the MAC per evaluation: the plaintext table (mu*ell*k*N words of
+    # pbytes = 7 or 8 bytes), the request (ell*2*k*N words, read once by each launch) and
+    # h' (mu*2*k*N words), 8 bytes each
     mu, ell = WL["mu"], WL["ell"]
-    mac_bytes_eval = 8 * (mu * ell * k * N + mac_launches_per_eval * ell * 2 * k * N + mu * 2 * k * N)
+    mac_bytes_eval = (pbytes * mu * ell * k * N +
+                      8 * (mac_launches_per_eval * ell * 2 * k * N + mu * 2 * k * N))
     mac_launch_ms = mac_ms / mac_launches
     achieved = mac_bytes_eval / mac_launches_per_eval / (mac_launch_ms * 1e-3) / 1e9
     peak, peak_kind = measured_peaks()
@@ -335,7 +339,9 @@ def run_ours(args):
                 "config": {"workload": WORKLOAD_NAME, "rescale": RESCALE_NOTE[args.rescale],
                            "l2": ("inputs larger than L2 (plaintext chunks of %.1f GB)" % (chunk * 0.134)
                                   if args.case == "large" else
-                                  "inputs larger than L2: the 3.3 GB resident plaintext table is read every step")},
+                                  "inputs larger than L2: the %.1f GB resident plaintext table is read every step"
+                                  % (WL["mu"] * WL["ell"] * k * N * pbytes / 1e9)),
+                           "plaintext_bytes_per_word": pbytes},
                 "e2e": {"value": round(e2e_ms, 3), "unit": "ms", "h2d_bytes_per_step": int(cts_np.nbytes),
                         "d2h_bytes_per_step": int(out_pinned.numel() * 8)},
                 "other_rounding": other_line, "cuda_graph": graph_line, "layer_chunk": chunk,
@@ -431,8 +437,9 @@ def run_ours(args):
         "metric": METRIC, "value": round(ms, 3), "unit": "ms", "n_gpus": args.gpus, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms, 3), "higher_is_better": False, "scaling": "weak",
         "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-        "config": {"workload": WORKLOAD_NAME, "l2": L2_NOTE, "parallelism": "replicas" if ws > 1 else "1 GPU",
-                   "resident_plaintexts_gb": round(mu * ell * k * N * 8 / 1e9, 1),
+        "config": {"workload": WORKLOAD_NAME, "l2": L2_NOTE % (mu * ell * k * N * pbytes / 1e9), "parallelism": "replicas" if ws > 1 else "1 GPU",
+                   "resident_plaintexts_gb": round(mu * ell * k * N * pbytes / 1e9, 1),
+                   "plaintext_bytes_per_word": pbytes,
                    "rescale": RESCALE_NOTE[args.rescale],
                    "response": "switched to one prime (2 x N words)"},
         "other_rounding": other_line,
@@ -651,6 +658,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--plaintext-bytes", type=int, choices=[0, 7, 8], default=0,
+                    help="storage of the resident plaintexts per word (0 = 8: 64-bit words; 7: three planes)")
     ap.add_argument("--chunk", type=int, default=0,
                     help="circuit chunk in layers (default: autotuned on the request)")
     ap.add_argument("--rescale", choices=["all", "layer"], default="all",

@@ -106,6 +106,13 @@ typedef struct {
                               ciphertexts [B][ell][2][k][N], every server layer one block of
                               plaintexts per request block, and the response B ciphertexts
                               [B][2][r][N], block j answering bins j*N .. j*N + N - 1 */
+  uint32_t plaintext_bytes;/* storage of the resident server plaintexts (NTT form), bytes per
+                              word: 0 or 8 = 64-bit words; 7 = the reduced value in three
+                              planes of 4, 2 and 1 bytes (every q_i < 2^56, else PEPSI_E_PARAM):
+                              12.5% more layers stay resident in the same budget, but the
+                              multiply-accumulate runs slower on a fully resident table (its
+                              unpacking costs more than the saved traffic).  Results are the
+                              same either way */
 } pepsi_params;
 
 /* Derived values of a context (for callers and tests). */
@@ -121,6 +128,7 @@ typedef struct {
   uint32_t rescale_cap;  /* most layers one rounding may cover (1: per-layer rounding only) */
   uint32_t response_primes; /* primes of the evaluation's response (k: not switched) */
   uint32_t bins, blocks;     /* b = blocks * N bins */
+  uint32_t plaintext_bytes;  /* 7 or 8: storage of the resident server plaintexts per word */
 } pepsi_info;
 
 /* Setup (Section 4, parameters of Tables 2-3): derives ell (Eq. 1), the

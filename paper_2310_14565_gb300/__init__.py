@@ -41,7 +41,7 @@ class Params(C.Structure):
         ("h", C.c_uint32), ("ell", C.c_uint32), ("lambda_bar", C.c_uint32), ("num_hashes", C.c_uint32),
         ("mu", C.c_uint32), ("hash_key", C.c_uint64), ("resident_bytes", C.c_uint64),
         ("rescale_group", C.c_uint32), ("server_values", C.c_uint32), ("response_primes", C.c_uint32),
-        ("bins", C.c_uint32),
+        ("bins", C.c_uint32), ("plaintext_bytes", C.c_uint32),
     ]
 
 
@@ -52,6 +52,7 @@ class Info(C.Structure):
         ("q", C.c_uint64 * 8), ("psi", C.c_uint64 * 8), ("psi_t", C.c_uint64), ("b_primes", C.c_uint64 * 12),
         ("log2_q", C.c_double), ("rescale_group", C.c_uint32), ("rescale_cap", C.c_uint32),
         ("response_primes", C.c_uint32), ("bins", C.c_uint32), ("blocks", C.c_uint32),
+        ("plaintext_bytes", C.c_uint32),
     ]
 
 
@@ -197,7 +198,7 @@ class Context:
     """One parameter set with its keys, server sets and scratch (pepsi_ctx)."""
 
     def __init__(self, N, t=65537, prime_bits=(36, 36, 37), h=2, ell=0, lambda_bar=16, mu=0, hash_key=0,
-                 key_seed=3, resident_bytes=0, rescale_group=0, server_values=0, response_primes=0, bins=0):
+                 key_seed=3, resident_bytes=0, rescale_group=0, server_values=0, response_primes=0, bins=0, plaintext_bytes=0):
         p = Params()
         p.N, p.t, p.k = N, t, len(prime_bits)
         for i, b in enumerate(prime_bits):
@@ -205,6 +206,7 @@ class Context:
         p.h, p.ell, p.lambda_bar, p.num_hashes, p.mu = h, ell, lambda_bar, 3, mu
         p.hash_key, p.resident_bytes, p.rescale_group = hash_key, resident_bytes, rescale_group
         p.server_values, p.response_primes, p.bins = server_values, response_primes, bins
+        p.plaintext_bytes = plaintext_bytes
         self._h = C.c_void_p()
         _check(lib().pepsi_setup(C.byref(p), key_seed, C.byref(self._h)), "pepsi_setup")
         info = Info()
@@ -218,6 +220,7 @@ class Context:
         self.rescale_cap = int(info.rescale_cap)
         self.response_primes = int(info.response_primes)
         self.bins, self.blocks = int(info.bins), int(info.blocks)
+        self.plaintext_bytes = int(info.plaintext_bytes)
         self.mu = {}
 
     def close(self):

@@ -185,8 +185,21 @@ constexpr int LG = LB / LPT;                    // layer slices per block
 constexpr int CONSUMER_WARPS = (TN / 32) * LG;  // 16
 constexpr int THREADS = (CONSUMER_WARPS + 1) * 32;
 constexpr int P_WORDS = LB * JS * TN, C_WORDS = 2 * JS * TN;
-constexpr int STAGE_WORDS = P_WORDS + C_WORDS;
-constexpr size_t SMEM = (size_t)NST * STAGE_WORDS * 8 + 2 * NST * 8 + 16 + 128;
+// A stage holds the plaintext tile, then the request tile.  The plaintext
+// tile is 8 bytes per word (split operand format), or 7 bytes per word in
+// three planes one after another: bits 0-31, 32-47 and 48-55 of the value.
+template <bool P7>
+__host__ __device__ constexpr int p_bytes() {
+  return P_WORDS * (P7 ? 7 : 8);
+}
+template <bool P7>
+__host__ __device__ constexpr int stage_bytes() {
+  return p_bytes<P7>() + C_WORDS * 8;
+}
+template <bool P7>
+__host__ __device__ constexpr size_t smem() {
+  return (size_t)NST * stage_bytes<P7>() + 2 * NST * 8 + 16 + 128;
+}
 }  // namespace mac
 
 __device__ __forceinline__ u64 globaltimer_ns() {
@@ -231,23 +244,20 @@ __device__ __forceinline__ void tma_load_3d(u32 dst, const CUtensorMap* tm, int 
 __device__ __forceinline__ void mad_wide(u64& acc, u32 a, u32 b) {
   asm("mad.wide.u32 %0, %1, %2, %0;" : "+l"(acc) : "r"(a), "r"(b));
 }
-// S0 + S1 2^s + S2 2^2s reduced mod q back into S0 (S1 = S2 = 0); S0 then
-// restarts below q, which the fold interval leaves room for.
-__device__ __forceinline__ void fold_inplace(u64& S0, u64& S1, u64& S2, u64 s, const DevPrime& pr) {
-  u64 lo = S0, hi = 0;
-  const u64 a = S1 << s;
-  hi += S1 >> (64 - s);
-  lo += a;
-  hi += lo < a;
-  const u64 b = S2 << (2 * s);
-  hi += S2 >> (64 - 2 * s);
-  lo += b;
-  hi += lo < b;
-  S0 = barrett128(hi, lo, pr.q, pr.bhi, pr.blo);
-  S1 = S2 = 0;
+// Karatsuba form of a split product c x = (ch 2^s + cl)(xh 2^s + xl): three
+// wide multiply-adds, S0 += cl xl, S2 += ch xh, SM += (cl + ch)(xl + xh),
+// instead of four.  The middle sum S1 = sum cl xh + ch xl is SM - S0 - S2
+// at the fold, exact mod 2^64: SM may wrap, S0, S1 and S2 stay below 2^64.
+__device__ __forceinline__ void kmac(u64& S0, u64& SM, u64& S2, u32 cl, u32 ch, u32 cs, u32 xl, u32 xh, u32 xs) {
+  mad_wide(S0, cl, xl);
+  mad_wide(S2, ch, xh);
+  mad_wide(SM, cs, xs);
 }
-__device__ __forceinline__ void fold_into(u64& acc, u64& S0, u64& S1, u64& S2, u64 s, const DevPrime& pr) {
-  u64 lo = S0, hi = 0;
+// S0 + (SM - S0 - S2) 2^s + S2 2^2s as a 128-bit value (hi, lo)
+__device__ __forceinline__ void compose(u64 S0, u64 SM, u64 S2, u64 s, u64& hi, u64& lo) {
+  const u64 S1 = SM - S0 - S2;
+  lo = S0;
+  hi = 0;
   const u64 a = S1 << s;
   hi += S1 >> (64 - s);
   lo += a;
@@ -256,20 +266,65 @@ __device__ __forceinline__ void fold_into(u64& acc, u64& S0, u64& S1, u64& S2, u
   hi += S2 >> (64 - 2 * s);
   lo += b;
   hi += lo < b;
+}
+// The sums reduced mod q back into S0 and SM (S2 = 0): both restart at the
+// residue r, so SM - S0 stays the middle term; the fold interval leaves
+// room for r below 2^64.
+__device__ __forceinline__ void fold_inplace(u64& S0, u64& SM, u64& S2, u64 s, const DevPrime& pr) {
+  u64 hi, lo;
+  compose(S0, SM, S2, s, hi, lo);
+  S0 = SM = barrett128(hi, lo, pr.q, pr.bhi, pr.blo);
+  S2 = 0;
+}
+__device__ __forceinline__ void fold_into(u64& acc, u64& S0, u64& SM, u64& S2, u64 s, const DevPrime& pr) {
+  u64 hi, lo;
+  compose(S0, SM, S2, s, hi, lo);
   acc = addmod(acc, barrett128(hi, lo, pr.q, pr.bhi, pr.blo), pr.q);
-  S0 = S1 = S2 = 0;
+  S0 = SM = S2 = 0;
+}
+
+// Plaintext word o of a stage's tile as split operands xl = x mod 2^s,
+// xh = x >> s.  P7: x is put together from its three planes.
+template <bool P7>
+__device__ __forceinline__ void tile_word(const unsigned char* stg, int o, u32 s, u32 lmask, u32& xl, u32& xh) {
+  if constexpr (P7) {
+    const u32 a = reinterpret_cast<const u32*>(stg)[o];
+    const u32 b = reinterpret_cast<const uint16_t*>(stg + mac::P_WORDS * 4)[o];
+    const u32 c = stg[mac::P_WORDS * 6 + o];
+    const u32 hi = __byte_perm(b, c, 0x2410);  // b | c << 16: bits 32-55 of x
+    xl = a & lmask;
+    xh = __funnelshift_r(a, hi, s);
+  } else {
+    const u64 x = reinterpret_cast<const u64*>(stg)[o];
+    xl = (u32)x;
+    xh = (u32)(x >> 32);
+  }
+}
+// The stage's plaintext copies: one tensor copy of the words, or one per plane.
+template <bool P7>
+__device__ __forceinline__ void tma_plain(u32 sb, const CUtensorMap* tmP, const CUtensorMap* tmPb,
+                                          const CUtensorMap* tmPc, int x, int j, int l, u32 bar) {
+  tma_load_3d(sb, tmP, x, j, l, bar);
+  if constexpr (P7) {
+    tma_load_3d(sb + mac::P_WORDS * 4, tmPb, x, j, l, bar);
+    tma_load_3d(sb + mac::P_WORDS * 6, tmPc, x, j, l, bar);
+  }
 }
 
 // One launch covers the codeword bits [j0, j0 + nj) (nj a multiple of JS
 // unless the range ends at ell); with acc_in it adds to the h' already in
 // H, so a request can be multiplied in pieces as it arrives.
+template <bool P7>
 __global__ void __launch_bounds__(mac::THREADS, 1)
-    k_mac(DevView V, const __grid_constant__ CUtensorMap tmP, const __grid_constant__ CUtensorMap tmC,
-          u64* __restrict__ H, int j0, int nj, int L, int fold_stages, int acc_in, int* err) {
+    k_mac(DevView V, const __grid_constant__ CUtensorMap tmP, const __grid_constant__ CUtensorMap tmPb,
+          const __grid_constant__ CUtensorMap tmPc, const __grid_constant__ CUtensorMap tmC, u64* __restrict__ H,
+          int j0, int nj, int L, int fold_stages, int acc_in, int* err) {
   using namespace mac;
+  constexpr int SB = stage_bytes<P7>(), PB = p_bytes<P7>();
   extern __shared__ __align__(128) u64 sm_raw[];
   // 128-byte aligned stage buffers for the tensor copies
-  u64* sm = reinterpret_cast<u64*>((reinterpret_cast<uintptr_t>(sm_raw) + 127) & ~(uintptr_t)127);
+  unsigned char* sm =
+      reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(sm_raw) + 127) & ~(uintptr_t)127);
   const size_t kN = (size_t)V.k * V.N;
   const int l0 = blockIdx.x * LB;
   const int nl = min(LB, L - l0);
@@ -278,8 +333,8 @@ __global__ void __launch_bounds__(mac::THREADS, 1)
   const int nst = (nj + JS - 1) / JS;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const u32 sbase = (u32)__cvta_generic_to_shared(sm);
-  const u32 full0 = sbase + (u32)(NST * STAGE_WORDS * 8), empty0 = full0 + NST * 8;
-  int* abort_flag = reinterpret_cast<int*>(sm + NST * STAGE_WORDS + 2 * NST);
+  const u32 full0 = sbase + (u32)(NST * SB), empty0 = full0 + NST * 8;
+  int* abort_flag = reinterpret_cast<int*>(sm + NST * SB + 2 * NST * 8);
   if (threadIdx.x == 0) {
     for (int b = 0; b < NST; ++b) {
       mbar_init(full0 + 8 * b, 1);
@@ -292,7 +347,7 @@ __global__ void __launch_bounds__(mac::THREADS, 1)
   bool ok = true;
   int issued = 0;  // producer: stages issued
   if (warp == CONSUMER_WARPS) {
-    // ---------------- producer: one thread issues two tensor copies per stage
+    // ---------------- producer: one thread issues the tensor copies of each stage
     if (lane == 0) {
       asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<u64>(&tmP)) : "memory");
       asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<u64>(&tmC)) : "memory");
@@ -303,11 +358,11 @@ __global__ void __launch_bounds__(mac::THREADS, 1)
           break;
         }
         const u32 bar = full0 + 8 * buf;
-        const u32 sb = sbase + (u32)(buf * STAGE_WORDS * 8);
+        const u32 sb = sbase + (u32)(buf * SB);
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        mbar_expect_tx(bar, (u32)STAGE_WORDS * 8);
-        tma_load_3d(sb, &tmP, (int)idx0, j0 + st * JS, l0, bar);
-        tma_load_3d(sb + (u32)P_WORDS * 8, &tmC, (int)idx0, 0, j0 + st * JS, bar);
+        mbar_expect_tx(bar, (u32)SB);
+        tma_plain<P7>(sb, &tmP, &tmPb, &tmPc, (int)idx0, j0 + st * JS, l0, bar);
+        tma_load_3d(sb + (u32)PB, &tmC, (int)idx0, 0, j0 + st * JS, bar);
         issued = st + 1;
       }
     }
@@ -319,12 +374,13 @@ __global__ void __launch_bounds__(mac::THREADS, 1)
     const size_t idx = idx0 + (active ? tp : 0);
     const DevPrime pr = V.pr[idx / V.N];
     const u64 sp = pr.split;
-    u64 S0[LPT][2], S1[LPT][2], S2[LPT][2], acc[LPT][2];
+    const u32 s32 = (u32)sp, lmask = (1u << s32) - 1;
+    u64 S0[LPT][2], SM[LPT][2], S2[LPT][2], acc[LPT][2];
 #pragma unroll
     for (int l = 0; l < LPT; ++l)
 #pragma unroll
       for (int c = 0; c < 2; ++c) {
-        S0[l][c] = S1[l][c] = S2[l][c] = acc[l][c] = 0;
+        S0[l][c] = SM[l][c] = S2[l][c] = acc[l][c] = 0;
         const int layer = g * LPT + l;
         if (acc_in && active && layer < nl) acc[l][c] = H[((size_t)(l0 + layer) * 2 + c) * kN + idx];
       }
@@ -335,24 +391,21 @@ __global__ void __launch_bounds__(mac::THREADS, 1)
         ok = false;
         break;
       }
-      const u64* ps = sm + (size_t)buf * STAGE_WORDS + (size_t)g * LPT * JS * TN + tp;
-      const u64* cs = sm + (size_t)buf * STAGE_WORDS + P_WORDS + tp;
+      const unsigned char* stg = sm + (size_t)buf * SB;
+      const int po = g * LPT * JS * TN + tp;  // word (slice, bit 0, point) of the tile
+      const u64* cs = reinterpret_cast<const u64*>(stg + PB) + tp;
 #pragma unroll
       for (int jj = 0; jj < JS; ++jj) {
         const u64 c0 = cs[(jj * 2) * TN], c1 = cs[(jj * 2 + 1) * TN];
         const u32 c0l = (u32)c0, c0h = (u32)(c0 >> 32), c1l = (u32)c1, c1h = (u32)(c1 >> 32);
+        const u32 c0s = c0l + c0h, c1s = c1l + c1h;
 #pragma unroll
         for (int l = 0; l < LPT; ++l) {
-          const u64 x = ps[(l * JS + jj) * TN];
-          const u32 xl = (u32)x, xh = (u32)(x >> 32);
-          mad_wide(S0[l][0], c0l, xl);
-          mad_wide(S1[l][0], c0l, xh);
-          mad_wide(S1[l][0], c0h, xl);
-          mad_wide(S2[l][0], c0h, xh);
-          mad_wide(S0[l][1], c1l, xl);
-          mad_wide(S1[l][1], c1l, xh);
-          mad_wide(S1[l][1], c1h, xl);
-          mad_wide(S2[l][1], c1h, xh);
+          u32 xl, xh;
+          tile_word<P7>(stg, po + (l * JS + jj) * TN, s32, lmask, xl, xh);
+          const u32 xs = xl + xh;
+          kmac(S0[l][0], SM[l][0], S2[l][0], c0l, c0h, c0s, xl, xh, xs);
+          kmac(S0[l][1], SM[l][1], S2[l][1], c1l, c1h, c1s, xl, xh, xs);
         }
       }
       __syncwarp();
@@ -361,7 +414,7 @@ __global__ void __launch_bounds__(mac::THREADS, 1)
 #pragma unroll
         for (int l = 0; l < LPT; ++l)
 #pragma unroll
-          for (int c = 0; c < 2; ++c) fold_into(acc[l][c], S0[l][c], S1[l][c], S2[l][c], sp, pr);
+          for (int c = 0; c < 2; ++c) fold_into(acc[l][c], S0[l][c], SM[l][c], S2[l][c], sp, pr);
         since = 0;
       }
     }
@@ -370,7 +423,7 @@ __global__ void __launch_bounds__(mac::THREADS, 1)
       for (int l = 0; l < LPT; ++l)
 #pragma unroll
         for (int c = 0; c < 2; ++c) {
-          fold_into(acc[l][c], S0[l][c], S1[l][c], S2[l][c], sp, pr);
+          fold_into(acc[l][c], S0[l][c], SM[l][c], S2[l][c], sp, pr);
           const int layer = g * LPT + l;
           if (layer < nl) H[((size_t)(l0 + layer) * 2 + c) * kN + idx] = acc[l][c];
         }
@@ -399,8 +452,15 @@ constexpr int LG = LB / LPT;
 constexpr int CONSUMER_WARPS = (TN / 32) * LG;  // 16
 constexpr int THREADS = (CONSUMER_WARPS + 1) * 32;
 constexpr int P_WORDS = LB * JS * TN;
-constexpr int STAGE_WORDS = P_WORDS + QMAX * 2 * JS * TN;
-constexpr size_t SMEM = (size_t)NST * STAGE_WORDS * 8 + 2 * NST * 8 + 16 + 128;
+static_assert(P_WORDS == mac::P_WORDS, "the plaintext tile of both kernels has one shape");
+template <bool P7>
+__host__ __device__ constexpr int stage_bytes() {
+  return mac::p_bytes<P7>() + QMAX * 2 * JS * TN * 8;
+}
+template <bool P7>
+__host__ __device__ constexpr size_t smem() {
+  return (size_t)NST * stage_bytes<P7>() + 2 * NST * 8 + 16 + 128;
+}
 }  // namespace macq
 
 __device__ __forceinline__ void tma_load_4d(u32 dst, const CUtensorMap* tm, int c0, int c1, int c2, int c3, u32 bar) {
@@ -411,13 +471,16 @@ __device__ __forceinline__ void tma_load_4d(u32 dst, const CUtensorMap* tm, int 
       : "memory");
 }
 
-template <int QB>
+template <int QB, bool P7>
 __global__ void __launch_bounds__(macq::THREADS, 1)
-    k_mac_multi(DevView V, const __grid_constant__ CUtensorMap tmP, const __grid_constant__ CUtensorMap tmC,
+    k_mac_multi(DevView V, const __grid_constant__ CUtensorMap tmP, const __grid_constant__ CUtensorMap tmPb,
+                const __grid_constant__ CUtensorMap tmPc, const __grid_constant__ CUtensorMap tmC,
                 u64* __restrict__ H, size_t hq, int ell, int L, int fold_stages, int* err) {
   using namespace macq;
+  constexpr int SB = stage_bytes<P7>(), PB = mac::p_bytes<P7>();
   extern __shared__ __align__(128) u64 sm_raw[];
-  u64* sm = reinterpret_cast<u64*>((reinterpret_cast<uintptr_t>(sm_raw) + 127) & ~(uintptr_t)127);
+  unsigned char* sm =
+      reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(sm_raw) + 127) & ~(uintptr_t)127);
   const size_t kN = (size_t)V.k * V.N;
   const int l0 = blockIdx.x * LB;
   const int nl = min(LB, L - l0);
@@ -426,8 +489,8 @@ __global__ void __launch_bounds__(macq::THREADS, 1)
   const int nst = (ell + JS - 1) / JS;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const u32 sbase = (u32)__cvta_generic_to_shared(sm);
-  const u32 full0 = sbase + (u32)(NST * STAGE_WORDS * 8), empty0 = full0 + NST * 8;
-  int* abort_flag = reinterpret_cast<int*>(sm + NST * STAGE_WORDS + 2 * NST);
+  const u32 full0 = sbase + (u32)(NST * SB), empty0 = full0 + NST * 8;
+  int* abort_flag = reinterpret_cast<int*>(sm + NST * SB + 2 * NST * 8);
   if (threadIdx.x == 0) {
     for (int b = 0; b < NST; ++b) {
       mbar_init(full0 + 8 * b, 1);
@@ -443,7 +506,7 @@ __global__ void __launch_bounds__(macq::THREADS, 1)
     if (lane == 0) {
       asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<u64>(&tmP)) : "memory");
       asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<u64>(&tmC)) : "memory");
-      const u32 bytes = (u32)(P_WORDS + QB * 2 * JS * TN) * 8;
+      const u32 bytes = (u32)(PB + QB * 2 * JS * TN * 8);
       for (int st = 0; st < nst; ++st) {
         const int buf = st % NST;
         if (st >= NST && !mbar_wait_bounded(empty0 + 8 * buf, (u32)(((st / NST) - 1) & 1))) {
@@ -451,11 +514,11 @@ __global__ void __launch_bounds__(macq::THREADS, 1)
           break;
         }
         const u32 bar = full0 + 8 * buf;
-        const u32 sb = sbase + (u32)(buf * STAGE_WORDS * 8);
+        const u32 sb = sbase + (u32)(buf * SB);
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         mbar_expect_tx(bar, bytes);
-        tma_load_3d(sb, &tmP, (int)idx0, st * JS, l0, bar);
-        tma_load_4d(sb + (u32)P_WORDS * 8, &tmC, (int)idx0, 0, st * JS, 0, bar);
+        tma_plain<P7>(sb, &tmP, &tmPb, &tmPc, (int)idx0, st * JS, l0, bar);
+        tma_load_4d(sb + (u32)PB, &tmC, (int)idx0, 0, st * JS, 0, bar);
         issued = st + 1;
       }
     }
@@ -466,13 +529,14 @@ __global__ void __launch_bounds__(macq::THREADS, 1)
     const size_t idx = idx0 + (active ? tp : 0);
     const DevPrime pr = V.pr[idx / V.N];
     const u64 sp = pr.split;
-    u64 S0[LPT][QB][2], S1[LPT][QB][2], S2[LPT][QB][2];
+    const u32 s32 = (u32)sp, lmask = (1u << s32) - 1;
+    u64 S0[LPT][QB][2], SM[LPT][QB][2], S2[LPT][QB][2];
 #pragma unroll
     for (int l = 0; l < LPT; ++l)
 #pragma unroll
       for (int q = 0; q < QB; ++q)
 #pragma unroll
-        for (int c = 0; c < 2; ++c) S0[l][q][c] = S1[l][q][c] = S2[l][q][c] = 0;
+        for (int c = 0; c < 2; ++c) S0[l][q][c] = SM[l][q][c] = S2[l][q][c] = 0;
     int since = 0;
     for (int st = 0; st < nst; ++st) {
       const int buf = st % NST;
@@ -480,11 +544,12 @@ __global__ void __launch_bounds__(macq::THREADS, 1)
         ok = false;
         break;
       }
-      const u64* ps = sm + (size_t)buf * STAGE_WORDS + (size_t)g * LPT * JS * TN + tp;
-      const u64* cs = sm + (size_t)buf * STAGE_WORDS + P_WORDS + tp;
+      const unsigned char* stg = sm + (size_t)buf * SB;
+      const int po = g * LPT * JS * TN + tp;  // word (slice, bit 0, point) of the tile
+      const u64* cs = reinterpret_cast<const u64*>(stg + PB) + tp;
 #pragma unroll
       for (int jj = 0; jj < JS; ++jj) {
-        u32 cl[QB][2], ch[QB][2];
+        u32 cl[QB][2], ch[QB][2], csum[QB][2];
 #pragma unroll
         for (int q = 0; q < QB; ++q)
 #pragma unroll
@@ -492,20 +557,18 @@ __global__ void __launch_bounds__(macq::THREADS, 1)
             const u64 w = cs[((q * JS + jj) * 2 + c) * TN];
             cl[q][c] = (u32)w;
             ch[q][c] = (u32)(w >> 32);
+            csum[q][c] = cl[q][c] + ch[q][c];
           }
 #pragma unroll
         for (int l = 0; l < LPT; ++l) {
-          const u64 x = ps[(l * JS + jj) * TN];
-          const u32 xl = (u32)x, xh = (u32)(x >> 32);
+          u32 xl, xh;
+          tile_word<P7>(stg, po + (l * JS + jj) * TN, s32, lmask, xl, xh);
+          const u32 xs = xl + xh;
 #pragma unroll
           for (int q = 0; q < QB; ++q)
 #pragma unroll
-            for (int c = 0; c < 2; ++c) {
-              mad_wide(S0[l][q][c], cl[q][c], xl);
-              mad_wide(S1[l][q][c], cl[q][c], xh);
-              mad_wide(S1[l][q][c], ch[q][c], xl);
-              mad_wide(S2[l][q][c], ch[q][c], xh);
-            }
+            for (int c = 0; c < 2; ++c)
+              kmac(S0[l][q][c], SM[l][q][c], S2[l][q][c], cl[q][c], ch[q][c], csum[q][c], xl, xh, xs);
         }
       }
       __syncwarp();
@@ -516,7 +579,7 @@ __global__ void __launch_bounds__(macq::THREADS, 1)
 #pragma unroll
           for (int q = 0; q < QB; ++q)
 #pragma unroll
-            for (int c = 0; c < 2; ++c) fold_inplace(S0[l][q][c], S1[l][q][c], S2[l][q][c], sp, pr);
+            for (int c = 0; c < 2; ++c) fold_inplace(S0[l][q][c], SM[l][q][c], S2[l][q][c], sp, pr);
         since = 0;
       }
     }
@@ -527,7 +590,7 @@ __global__ void __launch_bounds__(macq::THREADS, 1)
         for (int q = 0; q < QB; ++q)
 #pragma unroll
           for (int c = 0; c < 2; ++c) {
-            fold_inplace(S0[l][q][c], S1[l][q][c], S2[l][q][c], sp, pr);
+            fold_inplace(S0[l][q][c], SM[l][q][c], S2[l][q][c], sp, pr);
             const int layer = g * LPT + l;
             if (layer < nl) H[(size_t)q * hq + ((size_t)(l0 + layer) * 2 + c) * kN + idx] = S0[l][q][c];
           }
@@ -549,6 +612,25 @@ __global__ void k_split(DevView V, u64* x, size_t total, int to) {
   if (i >= total) return;
   const u64 s = V.pr[(i / V.N) % V.k].split;
   x[i] = to ? to_split(x[i], s) : from_split(x[i], s);
+}
+
+// Split-format words of rows [..][k][N] (row r uses prime r % k) to the
+// three planes of the 7-byte format: bits 0-31, 32-47 and 48-55 of each
+// reduced value (every prime below 2^56).
+__global__ void k_pack7(DevView V, const u64* __restrict__ src, size_t count, u32* a, uint16_t* b, uint8_t* c) {
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= count) return;
+  const u64 x = from_split(src[i], V.pr[(i / V.N) % V.k].split);
+  a[i] = (u32)x;
+  b[i] = (uint16_t)(x >> 32);
+  c[i] = (uint8_t)(x >> 48);
+}
+// The reduced values back from the three planes.
+__global__ void k_unpack7(const u32* __restrict__ a, const uint16_t* __restrict__ b, const uint8_t* __restrict__ c,
+                          size_t count, u64* out) {
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= count) return;
+  out[i] = (u64)a[i] | ((u64)b[i] << 32) | ((u64)c[i] << 48);
 }
 
 // ---------------------------------------------------- RNS conversions
@@ -1186,17 +1268,34 @@ PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
   }
   return fn;
 }
-// 3-D tensor of 64-bit words: dims (d0, d1, d2), row strides s1, s2 in words, box (b0, b1, b2)
-bool encode3d(CUtensorMap* tm, const u64* base, u64 d0, u64 d1, u64 d2, u64 s1, u64 s2, u32 b0, u32 b1, u32 b2) {
+// 3-D tensor of elements of esz bytes: dims (d0, d1, d2), row strides s1, s2 in elements, box (b0, b1, b2)
+bool encode3d_t(CUtensorMap* tm, CUtensorMapDataType dt, int esz, const void* base, u64 d0, u64 d1, u64 d2, u64 s1,
+                u64 s2, u32 b0, u32 b1, u32 b2) {
   auto enc = tensor_map_encoder();
   if (!enc) return false;
   const cuuint64_t dims[3] = {d0, d1, d2};
-  const cuuint64_t strides[2] = {s1 * 8, s2 * 8};
+  const cuuint64_t strides[2] = {s1 * esz, s2 * esz};
   const cuuint32_t box[3] = {b0, b1, b2};
   const cuuint32_t estr[3] = {1, 1, 1};
-  return enc(tm, CU_TENSOR_MAP_DATA_TYPE_UINT64, 3, const_cast<u64*>(base), dims, strides, box, estr,
-             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+  return enc(tm, dt, 3, const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+             CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+bool encode3d(CUtensorMap* tm, const u64* base, u64 d0, u64 d1, u64 d2, u64 s1, u64 s2, u32 b0, u32 b1, u32 b2) {
+  return encode3d_t(tm, CU_TENSOR_MAP_DATA_TYPE_UINT64, 8, base, d0, d1, d2, s1, s2, b0, b1, b2);
+}
+// Tensor maps of the plaintext tiles of L layers [L][ell][kN]: tm[0] the words, or
+// tm[0..2] the three planes of the 7-byte format (tm[1], tm[2] copies of tm[0] otherwise).
+bool encode_plain(CUtensorMap tm[3], const PlainTab& P, u64 kN, int ell, int L, u32 tn, u32 js, u32 lb) {
+  const u64 s2 = (u64)ell * kN;
+  if (!P.packed()) {
+    if (!encode3d(&tm[0], P.w, kN, ell, L, kN, s2, tn, js, lb)) return false;
+    tm[1] = tm[2] = tm[0];
+    return true;
+  }
+  return encode3d_t(&tm[0], CU_TENSOR_MAP_DATA_TYPE_UINT32, 4, P.a, kN, ell, L, kN, s2, tn, js, lb) &&
+         encode3d_t(&tm[1], CU_TENSOR_MAP_DATA_TYPE_UINT16, 2, P.b, kN, ell, L, kN, s2, tn, js, lb) &&
+         encode3d_t(&tm[2], CU_TENSOR_MAP_DATA_TYPE_UINT8, 1, P.c, kN, ell, L, kN, s2, tn, js, lb);
 }
 bool encode4d(CUtensorMap* tm, const u64* base, u64 d0, u64 d1, u64 d2, u64 d3, u64 s1, u64 s2, u64 s3, u32 b0,
               u32 b1, u32 b2, u32 b3) {
@@ -1212,39 +1311,64 @@ bool encode4d(CUtensorMap* tm, const u64* base, u64 d0, u64 d1, u64 d2, u64 d3, 
 }
 }  // namespace
 
-cudaError_t launch_mac_multi(const DevView& V, const u64* C, int nq, const u64* P, u64* H, size_t hq, int ell, int L,
-                             int fold, int* err, cudaStream_t st) {
+cudaError_t launch_mac_multi(const DevView& V, const u64* C, int nq, const PlainTab& P, u64* H, size_t hq, int ell,
+                             int L, int fold, int* err, cudaStream_t st) {
   if (L <= 0 || nq <= 0) return cudaSuccess;
   if (nq > macq::QMAX) return cudaErrorInvalidValue;
   const u64 kN = (u64)V.k * V.N;
-  CUtensorMap tmP, tmC;
-  if (!encode3d(&tmP, P, kN, ell, L, kN, (u64)ell * kN, macq::TN, macq::JS, macq::LB) ||
+  CUtensorMap tmP[3], tmC;
+  if (!encode_plain(tmP, P, kN, ell, L, macq::TN, macq::JS, macq::LB) ||
       !encode4d(&tmC, C, kN, 2, ell, nq, kN, 2 * kN, (u64)ell * 2 * kN, macq::TN, 2, macq::JS, nq))
     return cudaErrorInvalidValue;
   const int fold_stages = fold / macq::JS > 0 ? fold / macq::JS : 1;
   dim3 grid((L + macq::LB - 1) / macq::LB, (unsigned)((kN + macq::TN - 1) / macq::TN));
-  if (nq == 1)
-    k_mac_multi<1><<<grid, macq::THREADS, macq::SMEM, st>>>(V, tmP, tmC, H, hq, ell, L, fold_stages, err);
-  else
-    k_mac_multi<2><<<grid, macq::THREADS, macq::SMEM, st>>>(V, tmP, tmC, H, hq, ell, L, fold_stages, err);
+#define PEPSI_MACQ(QB, P7)                                                                                      \
+  k_mac_multi<QB, P7><<<grid, macq::THREADS, macq::smem<P7>(), st>>>(V, tmP[0], tmP[1], tmP[2], tmC, H, hq, ell, L, \
+                                                                      fold_stages, err)
+  if (P.packed()) {
+    if (nq == 1)
+      PEPSI_MACQ(1, true);
+    else
+      PEPSI_MACQ(2, true);
+  } else {
+    if (nq == 1)
+      PEPSI_MACQ(1, false);
+    else
+      PEPSI_MACQ(2, false);
+  }
+#undef PEPSI_MACQ
   return cudaSuccess;
 }
 
-cudaError_t launch_mac(const DevView& V, const u64* C, const u64* P, u64* H, int ell, int L, int fold, int* err,
+cudaError_t launch_mac(const DevView& V, const u64* C, const PlainTab& P, u64* H, int ell, int L, int fold, int* err,
                        cudaStream_t st, int j0, int nj, bool acc_in) {
   if (L <= 0) return cudaSuccess;
   if (nj < 0) nj = ell - j0;
   if (j0 < 0 || nj <= 0 || j0 + nj > ell || (j0 % mac::JS) || (j0 + nj < ell && nj % mac::JS))
     return cudaErrorInvalidValue;
   const u64 kN = (u64)V.k * V.N;
-  CUtensorMap tmP, tmC;
-  if (!encode3d(&tmP, P, kN, ell, L, kN, (u64)ell * kN, mac::TN, mac::JS, mac::LB) ||
+  CUtensorMap tmP[3], tmC;
+  if (!encode_plain(tmP, P, kN, ell, L, mac::TN, mac::JS, mac::LB) ||
       !encode3d(&tmC, C, kN, 2, ell, kN, 2 * kN, mac::TN, 2, mac::JS))
     return cudaErrorInvalidValue;
   const int fold_stages = fold / mac::JS > 0 ? fold / mac::JS : 1;
   dim3 grid((L + mac::LB - 1) / mac::LB, (unsigned)((kN + mac::TN - 1) / mac::TN));
-  k_mac<<<grid, mac::THREADS, mac::SMEM, st>>>(V, tmP, tmC, H, j0, nj, L, fold_stages, acc_in ? 1 : 0, err);
+  if (P.packed())
+    k_mac<true><<<grid, mac::THREADS, mac::smem<true>(), st>>>(V, tmP[0], tmP[1], tmP[2], tmC, H, j0, nj, L,
+                                                               fold_stages, acc_in ? 1 : 0, err);
+  else
+    k_mac<false><<<grid, mac::THREADS, mac::smem<false>(), st>>>(V, tmP[0], tmP[1], tmP[2], tmC, H, j0, nj, L,
+                                                                 fold_stages, acc_in ? 1 : 0, err);
   return cudaSuccess;
+}
+
+void launch_pack7(const DevView& V, const u64* src, size_t count, u32* a, uint16_t* b, uint8_t* c, cudaStream_t st) {
+  if (!count) return;
+  k_pack7<<<grid_for(count, 256), 256, 0, st>>>(V, src, count, a, b, c);
+}
+void launch_unpack7(const u32* a, const uint16_t* b, const uint8_t* c, size_t count, u64* out, cudaStream_t st) {
+  if (!count) return;
+  k_unpack7<<<grid_for(count, 256), 256, 0, st>>>(a, b, c, count, out);
 }
 
 void launch_split(const DevView& V, u64* x, size_t groups, bool to, cudaStream_t st) {
@@ -1416,9 +1540,12 @@ cudaError_t kernels_init(int N) {
   set((const void*)k_ntt<true, true>);
   set((const void*)k_ptgen);
   set((const void*)k_valgen);
-  set((const void*)k_mac);
-  set((const void*)k_mac_multi<1>);
-  set((const void*)k_mac_multi<2>);
+  set((const void*)k_mac<false>);
+  set((const void*)k_mac<true>);
+  set((const void*)k_mac_multi<1, false>);
+  set((const void*)k_mac_multi<2, false>);
+  set((const void*)k_mac_multi<1, true>);
+  set((const void*)k_mac_multi<2, true>);
   set((const void*)k_relin_ntt);
   set((const void*)k_encrypt);
   set((const void*)k_keygen_sntt);

@@ -15,18 +15,50 @@ void launch_cw_unrank(const u64* T, size_t count, const u64* binom, int ell, int
 // Server plaintexts pt_s[l][j] in NTT form for L layers: P[L][ell][k][N], split operand format.
 void launch_ptgen(const DevView& V, const uint16_t* pos, int L, int ell, int h, u64* P, cudaStream_t st);
 
+// Plaintexts of L layers [L][ell][k][N]: either 64-bit words in the split
+// operand format (w), or 7-byte words of the reduced values in three planes of
+// the same shape (a: bits 0-31, b: bits 32-47, c: bits 48-55; every prime below
+// 2^56).  Each base is 16-byte aligned.
+struct PlainTab {
+  const u64* w = nullptr;
+  const u32* a = nullptr;
+  const uint16_t* b = nullptr;
+  const uint8_t* c = nullptr;
+  bool packed() const { return a != nullptr; }
+  // the table from word `off` on (a whole number of layers)
+  PlainTab at(size_t off) const {
+    PlainTab r;
+    if (packed()) {
+      r.a = a + off;
+      r.b = b + off;
+      r.c = c + off;
+    } else {
+      r.w = w + off;
+    }
+    return r;
+  }
+};
+inline PlainTab plain_words(const u64* w) {
+  PlainTab r;
+  r.w = w;
+  return r;
+}
+
 // Fused ct x pt multiply-accumulate: H[l][c][p][n] = sum_j C[j][c][p][n] * P[l][j][p][n] mod q_p.
-// C and P in the split operand format, H reduced.  fold: terms between folds of the
+// C in the split operand format, H reduced.  fold: terms between folds of the
 // 64-bit partial sums.  *err is set when a bounded wait for a TMA copy expires.
 // Returns cudaErrorInvalidValue when the tensor maps of the copies cannot be encoded.
-cudaError_t launch_mac(const DevView& V, const u64* C, const u64* P, u64* H, int ell, int L, int fold, int* err,
-                       cudaStream_t st, int j0 = 0, int nj = -1,
-                       bool acc_in = false);
+cudaError_t launch_mac(const DevView& V, const u64* C, const PlainTab& P, u64* H, int ell, int L, int fold, int* err,
+                       cudaStream_t st, int j0 = 0, int nj = -1, bool acc_in = false);
 
 // The same for nq <= 2 requests sharing the plaintexts: C holds the requests back to back
 // ([nq][ell][2][k][N], split format), H[q] starts at H + q * hq.
-cudaError_t launch_mac_multi(const DevView& V, const u64* C, int nq, const u64* P, u64* H, size_t hq, int ell, int L,
-                             int fold, int* err, cudaStream_t st);
+cudaError_t launch_mac_multi(const DevView& V, const u64* C, int nq, const PlainTab& P, u64* H, size_t hq, int ell,
+                             int L, int fold, int* err, cudaStream_t st);
+// count split-format words (rows [..][k][N]) to the three planes of the 7-byte format, and back
+// (reduced values)
+void launch_pack7(const DevView& V, const u64* src, size_t count, u32* a, uint16_t* b, uint8_t* c, cudaStream_t st);
+void launch_unpack7(const u32* a, const uint16_t* b, const uint8_t* c, size_t count, u64* out, cudaStream_t st);
 constexpr int PEPSI_MAC_MAX_REQUESTS = 2;
 
 // In-place conversion of groups of k rows to (to = true) or from the split operand format.

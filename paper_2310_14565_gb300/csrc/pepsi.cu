@@ -35,11 +35,25 @@ struct ServerSet {
   std::vector<u64> hT;          // [mu][N] host copy of T_s
   u64* dT = nullptr;            // [mu][N]
   uint16_t* dpos = nullptr;     // [mu][N][h]
-  u64* dP = nullptr;            // [mu_res][ell][k][N] resident plaintexts (a prefix of the layers) or null
+  // resident plaintexts of a prefix of the layers, [mu_res][ell][k][N]: one
+  // device array holding either 64-bit words in the split operand format, or
+  // (p7) the three planes of the 7-byte format one after another
+  void* dP = nullptr;
+  bool p7 = false;
   u32 mu_res = 0;               // layers [0, mu_res) resident, the rest regenerated per chunk
   bool has_values = false;      // loaded with values (labelled PSI / PSI-Sum)
   std::vector<uint32_t> hV;     // [mu][N] host copy of the value table
   u64* dVP = nullptr;           // [mu][k+kb][N] value plaintexts val_s, NTT form over Q u B
+  // the resident plaintexts as a table for the multiply-accumulate, from layer l0
+  PlainTab plain(size_t kN, int ell, u32 l0 = 0) const {
+    const size_t words = (size_t)mu_res * ell * kN, off = (size_t)l0 * ell * kN;
+    if (!p7) return plain_words(static_cast<const u64*>(dP)).at(off);
+    PlainTab t;
+    t.a = static_cast<const u32*>(dP);
+    t.b = reinterpret_cast<const uint16_t*>(t.a + words);
+    t.c = reinterpret_cast<const uint8_t*>(t.b + words);
+    return t.at(off);
+  }
 };
 
 // A server set as the caller sees it: its b = B*N bins are B blocks of N
@@ -95,6 +109,7 @@ struct pepsi_ctx {
   u32 rescale_cap = 1;      // most layers one rounding of the last products may cover
   bool value_margin = false;  // B also holds the value products under lazy rescaling
   int resp = 0;               // primes of the evaluation's response (k: no switching)
+  bool p7 = false;            // resident plaintexts in the 7-byte format
   // per prime count r < k: modulus-switching constants and the RNS
   // constants of Q_r for decryption, built on first use
   std::unique_ptr<ModSwitchArgs> ms_args[PEPSI_MAXQ + 1];
@@ -598,7 +613,7 @@ int eval_core(pepsi_ctx* c, int set_id, const u64* cts, u32 layer0, u32 nl, int 
   if (res_end > layer0) {
     Hall = (u64*)scratch(c, S_HALL, (size_t)(res_end - layer0) * ct2 * 8, &e);
     if (!Hall) return cuda_status(e);
-    const u64* P0 = S.dP + (size_t)layer0 * c->ell * kN;
+    const PlainTab P0 = S.plain(kN, c->ell, layer0);
     if (pieces) {
       int jb[pepsi_ctx::kPieces + 1];
       for (int q = 0; q < npieces; ++q) jb[q] = (c->ell * q / npieces) & ~3;  // multiples of 4 bits
@@ -641,7 +656,7 @@ int eval_core(pepsi_ctx* c, int set_id, const u64* cts, u32 layer0, u32 nl, int 
         launch_ptgen(c->V, S.dpos + (size_t)l0 * N * c->h, L, c->ell, c->h, b.Pc, st);
       }
       Prof p(c, PC_MAC, st);  // a5 on a regenerated chunk
-      CKS(mac_status(launch_mac(c->V, b.C, b.Pc, b.H, c->ell, L, c->mac_fold, c->d_err, st)));
+      CKS(mac_status(launch_mac(c->V, b.C, plain_words(b.Pc), b.H, c->ell, L, c->mac_fold, c->d_err, st)));
     }
     const u64* VP = valued ? S.dVP + (size_t)l0 * vstride : nullptr;
     if (G > 1) {  // a6 + a7 with lazy rescaling
@@ -758,7 +773,7 @@ int eval_batch_core(pepsi_ctx* c, int nq, const int* set_ids, const u64* const* 
       for (int g = 0; g < G; ++g) CKS(prepare_request(c, cts[grp[g]], CB + (size_t)g * cwords, ax));
       {
         Prof p(c, PC_MAC, ax);
-        CKS(mac_status(launch_mac_multi(c->V, CB, G, S.dP, HB, hq, c->ell, (int)mres, c->mac_fold, c->d_err, ax)));
+        CKS(mac_status(launch_mac_multi(c->V, CB, G, S.plain(kN, c->ell), HB, hq, c->ell, (int)mres, c->mac_fold, c->d_err, ax)));
       }
       CKS(cudaEventRecord(mac_done[slot], ax));
       CKS(cudaStreamWaitEvent(st, mac_done[slot], 0));
@@ -776,7 +791,7 @@ int eval_batch_core(pepsi_ctx* c, int nq, const int* set_ids, const u64* const* 
           launch_ptgen(c->V, S.dpos + (size_t)l0 * N * c->h, L, c->ell, c->h, b.Pc, st);
         }
         Prof p(c, PC_MAC, st);
-        CKS(mac_status(launch_mac_multi(c->V, CB, G, b.Pc, HB, hq, c->ell, L, c->mac_fold, c->d_err, st)));
+        CKS(mac_status(launch_mac_multi(c->V, CB, G, plain_words(b.Pc), HB, hq, c->ell, L, c->mac_fold, c->d_err, st)));
       }
       for (int g = 0; g < G; ++g) {
         b.H = HB + (size_t)g * hq + (res ? (size_t)l0 * ct2 : 0);
@@ -992,6 +1007,17 @@ int pepsi_setup(const pepsi_params* params, uint64_t key_seed, pepsi_ctx** out) 
     return PEPSI_E_PARAM;
   }
   c->resp = params->response_primes ? (int)params->response_primes : c->k;
+  // resident plaintexts in 7 bytes per word on request (every q_i < 2^56)
+  {
+    bool fits = true;
+    for (u64 q : c->Q) fits = fits && q < (1ull << 56);
+    const u32 pb = params->plaintext_bytes;
+    if ((pb != 0 && pb != 7 && pb != 8) || (pb == 7 && !fits)) {
+      delete c;
+      return PEPSI_E_PARAM;
+    }
+    c->p7 = pb == 7;
+  }
   // lazy rescaling: runs of up to rescale_cap layers share one rounding
   {
     const u32 g = params->rescale_group;
@@ -1017,8 +1043,10 @@ int pepsi_setup(const pepsi_params* params, uint64_t key_seed, pepsi_ctx** out) 
     haveB += std::log2((double)p);
   }
   c->kb = (int)c->B.size();
-  // MAC partial sums: a 32x32-bit product term is below 2^max(bits+1, 2s);
-  // 2^(63 - that) terms fit in 64 bits
+  // MAC partial sums (Karatsuba form, S0 = sum cl xl, S2 = sum ch xh and
+  // the middle term S1 = sum cl xh + ch xl recovered from SM mod 2^64, so SM
+  // itself may wrap): a term of S0, S1 or S2 is below 2^max(bits+1, 2s), and
+  // 2^(63 - that) terms plus the residue a fold leaves fit in 64 bits
   {
     int worst = 0;
     for (u64 q : c->Q) {
@@ -1150,6 +1178,7 @@ int pepsi_get_info(const pepsi_ctx* c, pepsi_info* info) {
   info->response_primes = (uint32_t)c->resp;
   info->bins = c->blocks * (uint32_t)c->N;
   info->blocks = c->blocks;
+  info->plaintext_bytes = c->p7 ? 7 : 8;
   return PEPSI_OK;
 }
 
@@ -1230,22 +1259,42 @@ int load_block(pepsi_ctx* c, std::vector<u64>&& hT, std::vector<uint32_t>* hV, u
       return cuda_status(e);
     }
   }
-  const size_t per_layer = (size_t)c->ell * k * N * 8;
+  const size_t per_layer = (size_t)c->ell * k * N;  // plaintext words of a layer
   S.mu_res = mu_res;
   if (S.mu_res) {
-    e = cudaMalloc((void**)&S.dP, (size_t)S.mu_res * per_layer);
+    u64* tmp = nullptr;  // split-format words of a few layers, before packing
+    int G = 64;          // layers per generation launch
+    e = cudaMalloc(&S.dP, (size_t)S.mu_res * per_layer * (c->p7 ? 7 : 8));
+    if (e == cudaSuccess && c->p7) {
+      G = (int)std::max<size_t>(1, std::min<size_t>(64, ((size_t)1 << 30) / (per_layer * 8)));
+      e = cudaMalloc((void**)&tmp, (size_t)G * per_layer * 8);
+    }
     if (e != cudaSuccess) {
       cudaGetLastError();
+      cudaFree(S.dP);
       S.dP = nullptr;
       S.mu_res = 0;
     } else {
-      const int G = 64;  // layers per launch
+      S.p7 = c->p7;
+      const PlainTab T = S.plain(k * N, c->ell);
       for (u32 l0 = 0; l0 < S.mu_res; l0 += G) {
         const int L = (int)std::min<u32>(G, S.mu_res - l0);
+        const size_t off = (size_t)l0 * per_layer;
         Prof p(c, PC_PTGEN, c->stream);
-        launch_ptgen(c->V, S.dpos + (size_t)l0 * N * c->h, L, c->ell, c->h, S.dP + (size_t)l0 * c->ell * k * N,
-                     c->stream);
+        if (!S.p7) {
+          launch_ptgen(c->V, S.dpos + (size_t)l0 * N * c->h, L, c->ell, c->h, static_cast<u64*>(S.dP) + off,
+                       c->stream);
+        } else {
+          launch_ptgen(c->V, S.dpos + (size_t)l0 * N * c->h, L, c->ell, c->h, tmp, c->stream);
+          launch_pack7(c->V, tmp, (size_t)L * per_layer, const_cast<u32*>(T.a) + off,
+                       const_cast<uint16_t*>(T.b) + off, const_cast<uint8_t*>(T.c) + off, c->stream);
+        }
       }
+    }
+    if (tmp) {
+      const cudaError_t e2 = cudaStreamSynchronize(c->stream);
+      cudaFree(tmp);
+      if (e2 != cudaSuccess) e = e2;
     }
   }
   e = cudaStreamSynchronize(c->stream);
@@ -1278,7 +1327,7 @@ int server_load_impl(pepsi_ctx* c, const uint64_t* items, bool with_values, cons
   if (rc) return rc;
   // resident NTT-form plaintexts: the longest prefix of layers the budget
   // holds for every block
-  const size_t per_layer = (size_t)c->ell * c->k * N * 8 * c->blocks;
+  const size_t per_layer = (size_t)c->ell * c->k * N * (c->p7 ? 7 : 8) * c->blocks;
   size_t freeb = 0, totalb = 0;
   cudaMemGetInfo(&freeb, &totalb);
   const u64 cap = c->prm.resident_bytes;
@@ -1349,13 +1398,19 @@ int pepsi_server_plaintexts(pepsi_ctx* c, int set_id, uint32_t layer0, uint32_t 
   if (!tmp) return cuda_status(e);
   for (size_t b = 0; b < G->blk.size(); ++b) {
     ServerSet& S = c->sets[G->blk[b]];
-    if ((u64)layer0 + nl <= S.mu_res) {
-      CKS(cudaMemcpyAsync(tmp, S.dP + (size_t)layer0 * per, (size_t)nl * per * 8, cudaMemcpyDeviceToDevice, st));
+    if ((u64)layer0 + nl <= S.mu_res && S.p7) {  // the stored planes, put back together
+      const PlainTab T = S.plain((size_t)c->k * c->N, c->ell, layer0);
+      launch_unpack7(T.a, T.b, T.c, (size_t)nl * per, tmp, st);
     } else {
-      Prof p(c, PC_PTGEN, st);
-      launch_ptgen(c->V, S.dpos + (size_t)layer0 * c->N * c->h, nl, c->ell, c->h, tmp, st);
+      if ((u64)layer0 + nl <= S.mu_res) {
+        CKS(cudaMemcpyAsync(tmp, static_cast<const u64*>(S.dP) + (size_t)layer0 * per, (size_t)nl * per * 8,
+                            cudaMemcpyDeviceToDevice, st));
+      } else {
+        Prof p(c, PC_PTGEN, st);
+        launch_ptgen(c->V, S.dpos + (size_t)layer0 * c->N * c->h, nl, c->ell, c->h, tmp, st);
+      }
+      launch_split(c->V, tmp, (size_t)nl * c->ell, false, st);  // stored split; returned reduced
     }
-    launch_split(c->V, tmp, (size_t)nl * c->ell, false, st);  // stored split; returned reduced
     e = copy_any(out + b * nl * per, tmp, (size_t)nl * per * 8, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return cuda_status(e);

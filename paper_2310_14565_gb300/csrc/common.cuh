@@ -24,11 +24,12 @@ typedef int64_t i64;
 #define PEPSI_DUMMY 0xFFFFFFFFFFFFFFFFull
 #define PEPSI_CW_NONE 0xFFFFu
 
-// One modulus: value, Barrett constant floor(2^128/q) = bhi:blo, N^-1 (Shoup),
-// and the split point s = ceil(bits(q)/2) of the split operand format
-// (hi << 32 | lo with x = hi 2^s + lo) used by the multiply-accumulate.
+// One modulus q of n = bits(q) bits (n <= 61): N^-1 (Shoup); the split point
+// s = ceil(n/2) of the split operand format (hi << 32 | lo with x = hi 2^s +
+// lo) used by the multiply-accumulate; and the reduction constants
+// mu = floor(2^(n+63)/q), m64 = floor(2^64/q), c64 = 2^64 mod q (Shoup).
 struct DevPrime {
-  u64 q, bhi, blo, ninv, ninvs, split;
+  u64 q, ninv, ninvs, split, nbits, mu, m64, c64, c64s;
 };
 __host__ __device__ __forceinline__ u64 to_split(u64 x, u64 s) { return ((x >> s) << 32) | (x & ((1ull << s) - 1)); }
 __host__ __device__ __forceinline__ u64 from_split(u64 w, u64 s) { return ((w >> 32) << s) | (w & 0xFFFFFFFFull); }
@@ -88,25 +89,33 @@ __device__ __forceinline__ u64 shoup(u64 x, u64 w, u64 ws, u64 q) {
   u64 r = shoup_lazy(x, w, ws, q);
   return r >= q ? r - q : r;
 }
-// (hi:lo) mod q for any 128-bit value, q < 2^62.
-__device__ __forceinline__ u64 barrett128(u64 hi, u64 lo, u64 q, u64 bhi, u64 blo) {
-  u64 t = __umul64hi(lo, blo);
-  u64 a_lo = lo * bhi, a_hi = __umul64hi(lo, bhi);
-  u64 b_lo = hi * blo, b_hi = __umul64hi(hi, blo);
-  u64 s = a_lo + b_lo;
-  u64 c = s < a_lo;
-  u64 s2 = s + t;
-  c += s2 < s;
-  u64 qhat = hi * bhi + a_hi + b_hi + c;  // floor(x * m / 2^128) - (0..3), mod 2^64
-  u64 r = lo - qhat * q;
-  r = r >= q ? r - q : r;
-  r = r >= q ? r - q : r;
-  r = r >= q ? r - q : r;
-  return r;
+// x mod q for any 64-bit x: one-word Barrett, floor(x m64 / 2^64) is short
+// of floor(x/q) by at most 1.
+__device__ __forceinline__ u64 barrett64(u64 x, const DevPrime& p) {
+  const u64 r = x - __umul64hi(x, p.m64) * p.q;  // [0, 2q)
+  return r >= p.q ? r - p.q : r;
 }
-__device__ __forceinline__ u64 barrett64(u64 x, const DevPrime& p) { return barrett128(0, x, p.q, p.bhi, p.blo); }
+// (hi:lo) mod q for any 128-bit value: hi 2^64 = hi c64 (mod q) by Shoup
+// and lo by one-word Barrett, each in [0, 2q), then their sum reduced.
+__device__ __forceinline__ u64 reduce128(u64 hi, u64 lo, const DevPrime& p) {
+  const u64 a = shoup_lazy(hi, p.c64, p.c64s, p.q);
+  const u64 b = lo - __umul64hi(lo, p.m64) * p.q;
+  const u64 q2 = 2 * p.q;
+  u64 r = a + b;  // [0, 4q)
+  r = r >= q2 ? r - q2 : r;
+  return r >= p.q ? r - p.q : r;
+}
+// a b mod q for a, b < 2^n (Barrett 1973, one constant): x = a b < 2^2n,
+// x1 = floor(x / 2^(n-1)) < 2^(n+1), and floor(x1 mu / 2^64) is short of
+// floor(x/q) by at most 2 (the dropped fractions are below 1/4 and 1).
 __device__ __forceinline__ u64 mulmod(u64 a, u64 b, const DevPrime& p) {
-  return barrett128(__umul64hi(a, b), a * b, p.q, p.bhi, p.blo);
+  const u64 lo = a * b, hi = __umul64hi(a, b);
+  const int n = (int)p.nbits;
+  const u64 x1 = (hi << (65 - n)) | (lo >> (n - 1));
+  u64 r = lo - __umul64hi(x1, p.mu) * p.q;  // [0, 3q)
+  const u64 q2 = 2 * p.q;
+  r = r >= q2 ? r - q2 : r;
+  return r >= p.q ? r - p.q : r;
 }
 __device__ __forceinline__ u64 addmod(u64 a, u64 b, u64 q) {
   u64 s = a + b;

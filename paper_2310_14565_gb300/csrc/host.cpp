@@ -95,13 +95,15 @@ u64 shoup_of(u64 w, u64 q) { return (u64)(((u128)w << 64) / q); }
 DevPrime make_prime(u64 q, u32 N) {
   DevPrime p;
   p.q = q;
-  u128 m = ~(u128)0 / q;  // floor((2^128 - 1) / q) = floor(2^128 / q) for odd q > 1
-  p.bhi = (u64)(m >> 64);
-  p.blo = (u64)m;
   p.ninv = invmod(N % q, q);
   p.ninvs = shoup_of(p.ninv, q);
-  int bits = 64 - __builtin_clzll(q);
+  const int bits = 64 - __builtin_clzll(q);
   p.split = (u64)((bits + 1) / 2);
+  p.nbits = (u64)bits;
+  p.mu = (u64)(((u128)1 << (bits + 63)) / q);  // < 2^64: q > 2^(bits-1)
+  p.m64 = (u64)(((u128)1 << 64) / q);
+  p.c64 = (u64)(((u128)1 << 64) % q);
+  p.c64s = shoup_of(p.c64, q);
   return p;
 }
 

@@ -273,13 +273,13 @@ __device__ __forceinline__ void compose(u64 S0, u64 SM, u64 S2, u64 s, u64& hi, 
 __device__ __forceinline__ void fold_inplace(u64& S0, u64& SM, u64& S2, u64 s, const DevPrime& pr) {
   u64 hi, lo;
   compose(S0, SM, S2, s, hi, lo);
-  S0 = SM = barrett128(hi, lo, pr.q, pr.bhi, pr.blo);
+  S0 = SM = reduce128(hi, lo, pr);
   S2 = 0;
 }
 __device__ __forceinline__ void fold_into(u64& acc, u64& S0, u64& SM, u64& S2, u64 s, const DevPrime& pr) {
   u64 hi, lo;
   compose(S0, SM, S2, s, hi, lo);
-  acc = addmod(acc, barrett128(hi, lo, pr.q, pr.bhi, pr.blo), pr.q);
+  acc = addmod(acc, reduce128(hi, lo, pr), pr.q);
   S0 = SM = S2 = 0;
 }
 
@@ -704,7 +704,7 @@ __device__ __forceinline__ u64 q_digits_mod_b(const RnsArgs& A, const u64* v, bo
 #pragma unroll
   for (int l = 0; l < M; ++l)
     if (K || l < A.k) mac128(lo, hi, v[l], A.rc.pqb[j][l]);
-  const u64 r = barrett128(hi, lo, pb.q, pb.bhi, pb.blo);
+  const u64 r = reduce128(hi, lo, pb);
   return neg ? submod(r, A.rc.qmodb[j], pb.q) : r;
 }
 
@@ -788,7 +788,7 @@ __global__ void k_tensor(DevView V, const u64* __restrict__ AQ, const u64* __res
     u64 lo = 0, hi = 0;
     mac128(lo, hi, a0, b1);
     mac128(lo, hi, a1, b0);
-    d1 = barrett128(hi, lo, pr.q, pr.bhi, pr.blo);
+    d1 = reduce128(hi, lo, pr);
     d2 = mulmod(a1, b1, pr);
   }
   const size_t rs = (size_t)N;
@@ -842,7 +842,7 @@ __global__ void k_tensor_sum(DevView V, const u64* __restrict__ AQ, const u64* _
       mac128(lo, hi, a0, b1);
       mac128(lo, hi, a1, b0);
       mac128(s0l, s0h, mulmod(a0, b0, pr), v);
-      mac128(s1l, s1h, barrett128(hi, lo, pr.q, pr.bhi, pr.blo), v);
+      mac128(s1l, s1h, reduce128(hi, lo, pr), v);
       mac128(s2l, s2h, mulmod(a1, b1, pr), v);
     } else {
       mac128(s0l, s0h, a0, b0);
@@ -851,14 +851,14 @@ __global__ void k_tensor_sum(DevView V, const u64* __restrict__ AQ, const u64* _
       mac128(s2l, s2h, a1, b1);
     }
     if ((l & 15) == 15) {
-      s0l = barrett128(s0h, s0l, pr.q, pr.bhi, pr.blo);
-      s1l = barrett128(s1h, s1l, pr.q, pr.bhi, pr.blo);
-      s2l = barrett128(s2h, s2l, pr.q, pr.bhi, pr.blo);
+      s0l = reduce128(s0h, s0l, pr);
+      s1l = reduce128(s1h, s1l, pr);
+      s2l = reduce128(s2h, s2l, pr);
       s0h = s1h = s2h = 0;
     }
   }
-  u64 d[3] = {barrett128(s0h, s0l, pr.q, pr.bhi, pr.blo), barrett128(s1h, s1l, pr.q, pr.bhi, pr.blo),
-              barrett128(s2h, s2l, pr.q, pr.bhi, pr.blo)};
+  u64 d[3] = {reduce128(s0h, s0l, pr), reduce128(s1h, s1l, pr),
+              reduce128(s2h, s2l, pr)};
   u64* o = X + (size_t)pi * N + n;
   const size_t os = (size_t)np * N;
 #pragma unroll
@@ -907,7 +907,7 @@ __global__ void k_scale_round(const __grid_constant__ RnsArgs A, const u64* __re
 #pragma unroll
       for (int j = 0; j < MB; ++j)
         if (KB || j < kb) mac128(lo, hi, u[j], A.rc.pbq[i][j]);
-      const u64 r = barrett128(hi, lo, pq.q, pq.bhi, pq.blo);
+      const u64 r = reduce128(hi, lo, pq);
       out[(size_t)i * N] = neg ? submod(r, A.rc.bmodq[i], pq.q) : r;
     }
 }
@@ -954,8 +954,8 @@ __global__ void k_relin_mac(DevView V, const u64* __restrict__ DG, const u64* __
     mac128(lo1, hi1, d, __ldg(rlk + (((size_t)i * 2 + 1) * k + j) * N + n));
   }
   u64* o = R + ((l * 2) * k + j) * N + n;
-  o[0] = barrett128(hi0, lo0, pj.q, pj.bhi, pj.blo);
-  o[(size_t)k * N] = barrett128(hi1, lo1, pj.q, pj.bhi, pj.blo);
+  o[0] = reduce128(hi0, lo0, pj);
+  o[(size_t)k * N] = reduce128(hi1, lo1, pj);
 }
 
 // ------------------------------------------------------------ pointwise
@@ -1432,11 +1432,11 @@ __global__ void k_accum_val(DevView V, const u64* __restrict__ D, const u64* __r
   for (int l = 0; l < L; ++l) {
     mac128(lo, hi, D[(((size_t)l * 3 + c) * k + p) * N + n], VP[((size_t)l * np + p) * N + n]);
     if ((l & 31) == 31) {
-      lo = barrett128(hi, lo, pr.q, pr.bhi, pr.blo);
+      lo = reduce128(hi, lo, pr);
       hi = 0;
     }
   }
-  const u64 r = barrett128(hi, lo, pr.q, pr.bhi, pr.blo);
+  const u64 r = reduce128(hi, lo, pr);
   acc[idx] = init ? r : addmod(r, acc[idx], pr.q);
 }
 

@@ -25,50 +25,99 @@ __device__ __forceinline__ int nsw(int x) { return x ^ ((x >> 4) & 15); }
 
 namespace nttd {
 
+// Forward stages [s0, s0 + RR) on one group of 2^RR elements held in
+// registers, element i of the group at base + i * 2^(logN - s0 - RR).
 // Twiddles come as (w, Shoup companion) pairs, one 16-byte load each.
+template <int RR>
+__device__ __forceinline__ void fwd_group(u64 (&x)[1 << RR], int base, int logN, int s0, u64 q,
+                                          const ulonglong2* __restrict__ tw) {
+  constexpr int E = 1 << RR;
+  const u64 q2 = 2 * q;
+#pragma unroll
+  for (int ss = 0; ss < RR; ++ss) {
+    const int s = s0 + ss;
+    const int half = 1 << (RR - 1 - ss);
+    // base has zero bits where i * stride lands, so the twiddle index of
+    // butterfly i splits into a group part and i >> (RR - ss): stage ss of
+    // the phase needs only 2^ss distinct twiddles
+    const int tbase = (1 << s) + (base >> (logN - s));
+    ulonglong2 Wt[1 << (RR - 1)];
+#pragma unroll
+    for (int d = 0; d < (1 << ss); ++d) Wt[d] = __ldg(tw + tbase + d);
+#pragma unroll
+    for (int i = 0; i < E; ++i) {
+      if ((i & half) == 0) {
+        const u64 W = Wt[i >> (RR - ss)].x, Ws = Wt[i >> (RR - ss)].y;
+        u64 U = x[i];
+        U = U >= q2 ? U - q2 : U;
+        const u64 T = shoup_lazy(x[i + half], W, Ws, q);
+        x[i] = U + T;
+        x[i + half] = U + q2 - T;
+      }
+    }
+  }
+}
+// [0, 4q) -> [0, q)
+template <int E>
+__device__ __forceinline__ void fwd_final(u64 (&x)[E], u64 q) {
+  const u64 q2 = 2 * q;
+#pragma unroll
+  for (int i = 0; i < E; ++i) {
+    u64 v = x[i];
+    v = v >= q2 ? v - q2 : v;
+    x[i] = v >= q ? v - q : v;
+  }
+}
+// Inverse (Gentleman-Sande) stages s0 + RR - 1 down to s0 on one group.
+template <int RR>
+__device__ __forceinline__ void inv_group(u64 (&x)[1 << RR], int base, int logN, int s0, u64 q,
+                                          const ulonglong2* __restrict__ itw) {
+  constexpr int E = 1 << RR;
+  const u64 q2 = 2 * q;
+#pragma unroll
+  for (int ss = RR - 1; ss >= 0; --ss) {
+    const int s = s0 + ss;
+    const int half = 1 << (RR - 1 - ss);
+    const int tbase = (1 << s) + (base >> (logN - s));
+    ulonglong2 Wt[1 << (RR - 1)];
+#pragma unroll
+    for (int d = 0; d < (1 << ss); ++d) Wt[d] = __ldg(itw + tbase + d);
+#pragma unroll
+    for (int i = 0; i < E; ++i) {
+      if ((i & half) == 0) {
+        const u64 W = Wt[i >> (RR - ss)].x, Ws = Wt[i >> (RR - ss)].y;
+        const u64 U = x[i], V = x[i + half];
+        u64 S = U + V;
+        S = S >= q2 ? S - q2 : S;
+        x[i] = S;
+        x[i + half] = shoup_lazy(U + q2 - V, W, Ws, q);
+      }
+    }
+  }
+}
+// times N^-1, [0, 2q) -> [0, q)
+template <int E>
+__device__ __forceinline__ void inv_final(u64 (&x)[E], u64 q, u64 ninv, u64 ninvs) {
+#pragma unroll
+  for (int i = 0; i < E; ++i) {
+    const u64 v = shoup_lazy(x[i], ninv, ninvs, q);
+    x[i] = v >= q ? v - q : v;
+  }
+}
+
 template <int RR>
 __device__ __forceinline__ void fwd_phase(u64* a, int N, int logN, int s0, u64 q, const ulonglong2* __restrict__ tw,
                                           bool last) {
   constexpr int E = 1 << RR;
   const int slog = logN - s0 - RR;  // log2 of the element stride inside a group
   const int groups = N >> RR;
-  const u64 q2 = 2 * q;
   for (int g = threadIdx.x; g < groups; g += blockDim.x) {
     const int base = ((g >> slog) << (slog + RR)) + (g & ((1 << slog) - 1));
     u64 x[E];
 #pragma unroll
     for (int i = 0; i < E; ++i) x[i] = a[nsw(base + (i << slog))];
-#pragma unroll
-    for (int ss = 0; ss < RR; ++ss) {
-      const int s = s0 + ss;
-      const int half = 1 << (RR - 1 - ss);
-      // base has zero bits where i * stride lands, so the twiddle index of
-      // butterfly i splits into a group part and i >> (RR - ss): stage ss of
-      // the phase needs only 2^ss distinct twiddles
-      const int tbase = (1 << s) + (base >> (logN - s));
-      ulonglong2 Wt[1 << (RR - 1)];
-#pragma unroll
-      for (int d = 0; d < (1 << ss); ++d) Wt[d] = __ldg(tw + tbase + d);
-#pragma unroll
-      for (int i = 0; i < E; ++i) {
-        if ((i & half) == 0) {
-          const u64 W = Wt[i >> (RR - ss)].x, Ws = Wt[i >> (RR - ss)].y;
-          u64 U = x[i];
-          U = U >= q2 ? U - q2 : U;
-          const u64 T = shoup_lazy(x[i + half], W, Ws, q);
-          x[i] = U + T;
-          x[i + half] = U + q2 - T;
-        }
-      }
-    }
-    if (last) {
-#pragma unroll
-      for (int i = 0; i < E; ++i) {
-        u64 v = x[i];
-        v = v >= q2 ? v - q2 : v;
-        x[i] = v >= q ? v - q : v;
-      }
-    }
+    fwd_group<RR>(x, base, logN, s0, q, tw);
+    if (last) fwd_final<E>(x, q);
 #pragma unroll
     for (int i = 0; i < E; ++i) a[nsw(base + (i << slog))] = x[i];
   }
@@ -80,39 +129,13 @@ __device__ __forceinline__ void inv_phase(u64* a, int N, int logN, int s0, u64 q
   constexpr int E = 1 << RR;
   const int slog = logN - s0 - RR;
   const int groups = N >> RR;
-  const u64 q2 = 2 * q;
   for (int g = threadIdx.x; g < groups; g += blockDim.x) {
     const int base = ((g >> slog) << (slog + RR)) + (g & ((1 << slog) - 1));
     u64 x[E];
 #pragma unroll
     for (int i = 0; i < E; ++i) x[i] = a[nsw(base + (i << slog))];
-#pragma unroll
-    for (int ss = RR - 1; ss >= 0; --ss) {
-      const int s = s0 + ss;
-      const int half = 1 << (RR - 1 - ss);
-      const int tbase = (1 << s) + (base >> (logN - s));
-      ulonglong2 Wt[1 << (RR - 1)];
-#pragma unroll
-      for (int d = 0; d < (1 << ss); ++d) Wt[d] = __ldg(itw + tbase + d);
-#pragma unroll
-      for (int i = 0; i < E; ++i) {
-        if ((i & half) == 0) {
-          const u64 W = Wt[i >> (RR - ss)].x, Ws = Wt[i >> (RR - ss)].y;
-          const u64 U = x[i], V = x[i + half];
-          u64 S = U + V;
-          S = S >= q2 ? S - q2 : S;
-          x[i] = S;
-          x[i + half] = shoup_lazy(U + q2 - V, W, Ws, q);
-        }
-      }
-    }
-    if (last) {
-#pragma unroll
-      for (int i = 0; i < E; ++i) {
-        const u64 v = shoup_lazy(x[i], ninv, ninvs, q);
-        x[i] = v >= q ? v - q : v;
-      }
-    }
+    inv_group<RR>(x, base, logN, s0, q, itw);
+    if (last) inv_final<E>(x, q, ninv, ninvs);
 #pragma unroll
     for (int i = 0; i < E; ++i) a[nsw(base + (i << slog))] = x[i];
   }
@@ -216,4 +239,93 @@ __device__ __forceinline__ void ntt_inv_fast(u64* a, const DevView& V, int pi) {
     case 14: ntt_inv_fixed<14>(a, P.q, itw, P.ninv, P.ninvs); break;
     default: ntt_inv_block(a, V.N, V.logN, P.q, itw, P.ninv, P.ninvs); break;
   }
+}
+
+// Transforms between a row in global memory and the shared-memory array,
+// with the F = log2(N) mod 3 stages that do not fill a radix-8 phase run on
+// the registers of the global load (forward: stages 0..F-1, before the
+// phases) or of the global store (inverse: stages F-1..0 and the factor
+// N^-1, after the phases).  This saves the shared-memory round trip and the
+// barrier of a phase of F stages; the butterflies and their order are those
+// of ntt_fwd_fixed / ntt_inv_fixed, so are the results.  ld(x) returns
+// element x of the input in [0, 4q); st(x, v) receives output element x.
+// Every thread of the block must call these.
+template <int LOGN, class Load>
+__device__ __forceinline__ void ntt_fwd_load_fixed(u64* a, const Load& ld, u64 q, const ulonglong2* __restrict__ tw) {
+  constexpr int N = 1 << LOGN, F = LOGN % 3;
+  if constexpr (F == 0) {
+    for (int x = threadIdx.x; x < N; x += blockDim.x) a[nsw(x)] = ld(x);
+  } else {
+    constexpr int SLOG = LOGN - F;
+    for (int g = threadIdx.x; g < (N >> F); g += blockDim.x) {
+      u64 x[1 << F];
+#pragma unroll
+      for (int i = 0; i < (1 << F); ++i) x[i] = ld(g + (i << SLOG));
+      nttd::fwd_group<F>(x, g, LOGN, 0, q, tw);
+#pragma unroll
+      for (int i = 0; i < (1 << F); ++i) a[nsw(g + (i << SLOG))] = x[i];
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int s0 = F; s0 < LOGN; s0 += 3) {
+    nttd::fwd_phase<3>(a, N, LOGN, s0, q, tw, s0 + 3 == LOGN);
+    __syncthreads();
+  }
+}
+template <int LOGN, class Store>
+__device__ __forceinline__ void ntt_inv_store_fixed(u64* a, const Store& st, u64 q,
+                                                    const ulonglong2* __restrict__ itw, u64 ninv, u64 ninvs) {
+  constexpr int N = 1 << LOGN, F = LOGN % 3;
+#pragma unroll
+  for (int s0 = LOGN - 3; s0 >= F; s0 -= 3) {
+    nttd::inv_phase<3>(a, N, LOGN, s0, q, itw, s0 == 0, ninv, ninvs);
+    __syncthreads();
+  }
+  if constexpr (F == 0) {
+    for (int x = threadIdx.x; x < N; x += blockDim.x) st(x, a[nsw(x)]);
+  } else {
+    constexpr int SLOG = LOGN - F;
+    for (int g = threadIdx.x; g < (N >> F); g += blockDim.x) {
+      u64 x[1 << F];
+#pragma unroll
+      for (int i = 0; i < (1 << F); ++i) x[i] = a[nsw(g + (i << SLOG))];
+      nttd::inv_group<F>(x, g, LOGN, 0, q, itw);
+      nttd::inv_final<1 << F>(x, q, ninv, ninvs);
+#pragma unroll
+      for (int i = 0; i < (1 << F); ++i) st(g + (i << SLOG), x[i]);
+    }
+  }
+}
+
+// Forward transform of row ld(0..N) into a[] (reduced, shared-memory order
+// nsw), prime pi; the ring sizes of the workloads use the fused form.
+template <class Load>
+__device__ __forceinline__ void ntt_fwd_load(u64* a, const Load& ld, const DevView& V, int pi) {
+  const ulonglong2* tw = V.twp + (size_t)pi * V.N;
+  const u64 q = V.pr[pi].q;
+  switch (V.logN) {
+    case 12: ntt_fwd_load_fixed<12>(a, ld, q, tw); return;
+    case 13: ntt_fwd_load_fixed<13>(a, ld, q, tw); return;
+    case 14: ntt_fwd_load_fixed<14>(a, ld, q, tw); return;
+    default: break;
+  }
+  for (int x = threadIdx.x; x < V.N; x += blockDim.x) a[nsw(x)] = ld(x);
+  __syncthreads();
+  ntt_fwd_block(a, V.N, V.logN, q, tw);
+}
+// Inverse transform of a[] (shared-memory order nsw, values in [0, 2q);
+// callers synchronise after filling it) into st(0..N, .), prime pi.
+template <class Store>
+__device__ __forceinline__ void ntt_inv_store(u64* a, const Store& st, const DevView& V, int pi) {
+  const ulonglong2* itw = V.itwp + (size_t)pi * V.N;
+  const DevPrime P = V.pr[pi];
+  switch (V.logN) {
+    case 12: ntt_inv_store_fixed<12>(a, st, P.q, itw, P.ninv, P.ninvs); return;
+    case 13: ntt_inv_store_fixed<13>(a, st, P.q, itw, P.ninv, P.ninvs); return;
+    case 14: ntt_inv_store_fixed<14>(a, st, P.q, itw, P.ninv, P.ninvs); return;
+    default: break;
+  }
+  ntt_inv_block(a, V.N, V.logN, P.q, itw, P.ninv, P.ninvs);
+  for (int x = threadIdx.x; x < V.N; x += blockDim.x) st(x, a[nsw(x)]);
 }

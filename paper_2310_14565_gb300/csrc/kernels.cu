@@ -35,20 +35,16 @@ __global__ void __launch_bounds__(NTT_MAX_THREADS, 2) k_ntt(DevView V, const u64
   const size_t o = r / np;
   const u64* s = src + o * src_os + (size_t)pl * N;
   u64* d = dst + o * dst_os + (size_t)pl * N;
+  const auto ld = [&](int x) { return s[x]; };
   if (FWD) {
-    // src and dst may alias: every read of the row happens before the barrier
-    // that follows the fused first stages, every write after the last phase
-    ntt_fwd_load(sm, [&](int x) { return s[x]; }, V, p0 + pl);
     if (SPLIT) {
       const u64 sp = V.pr[p0 + pl].split;
-      for (int x = threadIdx.x; x < N; x += blockDim.x) d[x] = to_split(sm[nsw(x)], sp);
+      ntt_fwd_gg(sm, ld, [&](int x, u64 v) { d[x] = to_split(v, sp); }, V, p0 + pl);
     } else {
-      for (int x = threadIdx.x; x < N; x += blockDim.x) d[x] = sm[nsw(x)];
+      ntt_fwd_gg(sm, ld, [&](int x, u64 v) { d[x] = v; }, V, p0 + pl);
     }
   } else {
-    for (int x = threadIdx.x; x < N; x += blockDim.x) sm[nsw(x)] = s[x];
-    __syncthreads();
-    ntt_inv_store(sm, [&](int x, u64 v) { d[x] = v; }, V, p0 + pl);
+    ntt_inv_gg(sm, ld, [&](int x, u64 v) { d[x] = v; }, V, p0 + pl);
   }
 }
 
@@ -928,15 +924,14 @@ __global__ void __launch_bounds__(NTT_MAX_THREADS, 2) k_relin_ntt(DevView V, con
   const size_t l = r / ((size_t)k * (k + 2));
   const DevPrime pj = V.pr[j];
   const u64* row = i < k ? D + ((l * 3 + 2) * k + i) * N : D + ((l * 3 + (i - k)) * k + j) * N;
-  ntt_fwd_load(
+  u64* out = DG + r * N;
+  ntt_fwd_gg(
       sm,
       [&](int x) {
         const u64 w = row[x];
         return w >= pj.q ? barrett64(w, pj) : w;
       },
-      V, j);
-  u64* out = DG + r * N;
-  for (int x = threadIdx.x; x < N; x += blockDim.x) out[x] = sm[nsw(x)];
+      [&](int x, u64 v) { out[x] = v; }, V, j);
 }
 // Phase 2, thread per (l, j, n): R_c = NTT(d_c) + sum_i NTT(d_i) * rlk_i[c],
 // 128-bit lazy sums, one Barrett reduction per output.

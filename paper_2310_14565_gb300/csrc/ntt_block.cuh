@@ -241,91 +241,106 @@ __device__ __forceinline__ void ntt_inv_fast(u64* a, const DevView& V, int pi) {
   }
 }
 
-// Transforms between a row in global memory and the shared-memory array,
-// with the F = log2(N) mod 3 stages that do not fill a radix-8 phase run on
-// the registers of the global load (forward: stages 0..F-1, before the
-// phases) or of the global store (inverse: stages F-1..0 and the factor
-// N^-1, after the phases).  This saves the shared-memory round trip and the
-// barrier of a phase of F stages; the butterflies and their order are those
-// of ntt_fwd_fixed / ntt_inv_fixed, so are the results.  ld(x) returns
-// element x of the input in [0, 4q); st(x, v) receives output element x.
-// Every thread of the block must call these.
-template <int LOGN, class Load>
-__device__ __forceinline__ void ntt_fwd_load_fixed(u64* a, const Load& ld, u64 q, const ulonglong2* __restrict__ tw) {
-  constexpr int N = 1 << LOGN, F = LOGN % 3;
-  if constexpr (F == 0) {
-    for (int x = threadIdx.x; x < N; x += blockDim.x) a[nsw(x)] = ld(x);
-  } else {
-    constexpr int SLOG = LOGN - F;
-    for (int g = threadIdx.x; g < (N >> F); g += blockDim.x) {
-      u64 x[1 << F];
+// Transforms from a row in global memory to a row in global memory through
+// the shared-memory array a[].  The first three stages run on the registers
+// of the global load and the last R stages (R = 1, 2 or 3, the rest after
+// radix-8 phases) on those of the global store, so of the log2(N) stages
+// only the middle ones take shared-memory phases (N = 8192: three instead
+// of five).  The butterflies and their order are those of ntt_fwd_fixed /
+// ntt_inv_fixed, so are the results.  ld(x) returns input element x (forward:
+// in [0, 4q); inverse: in [0, 2q)); st(x, v) receives output element x,
+// reduced.  Every read through ld happens before the first barrier and
+// every st after the last, so input and output rows may alias.  Every
+// thread of the block must call these.
+template <int LOGN, class Load, class Store>
+__device__ __forceinline__ void ntt_fwd_fused(u64* a, const Load& ld, const Store& st, u64 q,
+                                              const ulonglong2* __restrict__ tw) {
+  constexpr int N = 1 << LOGN, R = (LOGN - 4) % 3 + 1, M = (LOGN - 3 - R) / 3, S8 = LOGN - 3;
+  for (int g = threadIdx.x; g < (N >> 3); g += blockDim.x) {  // stages 0-2
+    u64 x[8];
 #pragma unroll
-      for (int i = 0; i < (1 << F); ++i) x[i] = ld(g + (i << SLOG));
-      nttd::fwd_group<F>(x, g, LOGN, 0, q, tw);
+    for (int i = 0; i < 8; ++i) x[i] = ld(g + (i << S8));
+    nttd::fwd_group<3>(x, g, LOGN, 0, q, tw);
 #pragma unroll
-      for (int i = 0; i < (1 << F); ++i) a[nsw(g + (i << SLOG))] = x[i];
-    }
+    for (int i = 0; i < 8; ++i) a[nsw(g + (i << S8))] = x[i];
   }
   __syncthreads();
 #pragma unroll
-  for (int s0 = F; s0 < LOGN; s0 += 3) {
-    nttd::fwd_phase<3>(a, N, LOGN, s0, q, tw, s0 + 3 == LOGN);
+  for (int m = 0; m < M; ++m) {
+    nttd::fwd_phase<3>(a, N, LOGN, 3 + 3 * m, q, tw, false);
     __syncthreads();
+  }
+  for (int g = threadIdx.x; g < (N >> R); g += blockDim.x) {  // stages LOGN-R .. LOGN-1
+    const int base = g << R;
+    u64 x[1 << R];
+#pragma unroll
+    for (int i = 0; i < (1 << R); ++i) x[i] = a[nsw(base + i)];
+    nttd::fwd_group<R>(x, base, LOGN, LOGN - R, q, tw);
+    nttd::fwd_final<1 << R>(x, q);
+#pragma unroll
+    for (int i = 0; i < (1 << R); ++i) st(base + i, x[i]);
   }
 }
-template <int LOGN, class Store>
-__device__ __forceinline__ void ntt_inv_store_fixed(u64* a, const Store& st, u64 q,
-                                                    const ulonglong2* __restrict__ itw, u64 ninv, u64 ninvs) {
-  constexpr int N = 1 << LOGN, F = LOGN % 3;
+template <int LOGN, class Load, class Store>
+__device__ __forceinline__ void ntt_inv_fused(u64* a, const Load& ld, const Store& st, u64 q,
+                                              const ulonglong2* __restrict__ itw, u64 ninv, u64 ninvs) {
+  constexpr int N = 1 << LOGN, R = (LOGN - 4) % 3 + 1, M = (LOGN - 3 - R) / 3, S8 = LOGN - 3;
+  for (int g = threadIdx.x; g < (N >> R); g += blockDim.x) {  // stages LOGN-1 .. LOGN-R
+    const int base = g << R;
+    u64 x[1 << R];
 #pragma unroll
-  for (int s0 = LOGN - 3; s0 >= F; s0 -= 3) {
-    nttd::inv_phase<3>(a, N, LOGN, s0, q, itw, s0 == 0, ninv, ninvs);
+    for (int i = 0; i < (1 << R); ++i) x[i] = ld(base + i);
+    nttd::inv_group<R>(x, base, LOGN, LOGN - R, q, itw);
+#pragma unroll
+    for (int i = 0; i < (1 << R); ++i) a[nsw(base + i)] = x[i];
+  }
+  __syncthreads();
+#pragma unroll
+  for (int m = M - 1; m >= 0; --m) {
+    nttd::inv_phase<3>(a, N, LOGN, 3 + 3 * m, q, itw, false, ninv, ninvs);
     __syncthreads();
   }
-  if constexpr (F == 0) {
-    for (int x = threadIdx.x; x < N; x += blockDim.x) st(x, a[nsw(x)]);
-  } else {
-    constexpr int SLOG = LOGN - F;
-    for (int g = threadIdx.x; g < (N >> F); g += blockDim.x) {
-      u64 x[1 << F];
+  for (int g = threadIdx.x; g < (N >> 3); g += blockDim.x) {  // stages 2-0 and N^-1
+    u64 x[8];
 #pragma unroll
-      for (int i = 0; i < (1 << F); ++i) x[i] = a[nsw(g + (i << SLOG))];
-      nttd::inv_group<F>(x, g, LOGN, 0, q, itw);
-      nttd::inv_final<1 << F>(x, q, ninv, ninvs);
+    for (int i = 0; i < 8; ++i) x[i] = a[nsw(g + (i << S8))];
+    nttd::inv_group<3>(x, g, LOGN, 0, q, itw);
+    nttd::inv_final<8>(x, q, ninv, ninvs);
 #pragma unroll
-      for (int i = 0; i < (1 << F); ++i) st(g + (i << SLOG), x[i]);
-    }
+    for (int i = 0; i < 8; ++i) st(g + (i << S8), x[i]);
   }
 }
 
-// Forward transform of row ld(0..N) into a[] (reduced, shared-memory order
-// nsw), prime pi; the ring sizes of the workloads use the fused form.
-template <class Load>
-__device__ __forceinline__ void ntt_fwd_load(u64* a, const Load& ld, const DevView& V, int pi) {
+// Global-to-global transforms of row pi with the fused forms for the ring
+// sizes of the workloads (N = 4096, 8192, 16384), else load, block
+// transform and store.
+template <class Load, class Store>
+__device__ __forceinline__ void ntt_fwd_gg(u64* a, const Load& ld, const Store& st, const DevView& V, int pi) {
   const ulonglong2* tw = V.twp + (size_t)pi * V.N;
   const u64 q = V.pr[pi].q;
   switch (V.logN) {
-    case 12: ntt_fwd_load_fixed<12>(a, ld, q, tw); return;
-    case 13: ntt_fwd_load_fixed<13>(a, ld, q, tw); return;
-    case 14: ntt_fwd_load_fixed<14>(a, ld, q, tw); return;
+    case 12: ntt_fwd_fused<12>(a, ld, st, q, tw); return;
+    case 13: ntt_fwd_fused<13>(a, ld, st, q, tw); return;
+    case 14: ntt_fwd_fused<14>(a, ld, st, q, tw); return;
     default: break;
   }
   for (int x = threadIdx.x; x < V.N; x += blockDim.x) a[nsw(x)] = ld(x);
   __syncthreads();
   ntt_fwd_block(a, V.N, V.logN, q, tw);
+  for (int x = threadIdx.x; x < V.N; x += blockDim.x) st(x, a[nsw(x)]);
 }
-// Inverse transform of a[] (shared-memory order nsw, values in [0, 2q);
-// callers synchronise after filling it) into st(0..N, .), prime pi.
-template <class Store>
-__device__ __forceinline__ void ntt_inv_store(u64* a, const Store& st, const DevView& V, int pi) {
+template <class Load, class Store>
+__device__ __forceinline__ void ntt_inv_gg(u64* a, const Load& ld, const Store& st, const DevView& V, int pi) {
   const ulonglong2* itw = V.itwp + (size_t)pi * V.N;
   const DevPrime P = V.pr[pi];
   switch (V.logN) {
-    case 12: ntt_inv_store_fixed<12>(a, st, P.q, itw, P.ninv, P.ninvs); return;
-    case 13: ntt_inv_store_fixed<13>(a, st, P.q, itw, P.ninv, P.ninvs); return;
-    case 14: ntt_inv_store_fixed<14>(a, st, P.q, itw, P.ninv, P.ninvs); return;
+    case 12: ntt_inv_fused<12>(a, ld, st, P.q, itw, P.ninv, P.ninvs); return;
+    case 13: ntt_inv_fused<13>(a, ld, st, P.q, itw, P.ninv, P.ninvs); return;
+    case 14: ntt_inv_fused<14>(a, ld, st, P.q, itw, P.ninv, P.ninvs); return;
     default: break;
   }
+  for (int x = threadIdx.x; x < V.N; x += blockDim.x) a[nsw(x)] = ld(x);
+  __syncthreads();
   ntt_inv_block(a, V.N, V.logN, P.q, itw, P.ninv, P.ninvs);
   for (int x = threadIdx.x; x < V.N; x += blockDim.x) st(x, a[nsw(x)]);
 }

@@ -39,8 +39,8 @@ __host__ __device__ __forceinline__ u64 from_split(u64 w, u64 s) { return ((w >>
 struct RnsConst {
   // Garner over Q: cq[i][j] = q_j^-1 mod q_i (j < i)
   u64 cq[PEPSI_MAXQ][PEPSI_MAXQ], cqs[PEPSI_MAXQ][PEPSI_MAXQ];
-  // mixed-radix weights of Q in B: pqb[j][l] = prod_{m<l} q_m mod p_j
-  u64 pqb[PEPSI_MAXB][PEPSI_MAXQ];
+  // radices of Q in B for Horner's rule: qb[j][l] = q_l mod p_j (Shoup)
+  u64 qb[PEPSI_MAXB][PEPSI_MAXQ], qbs[PEPSI_MAXB][PEPSI_MAXQ];
   u64 qhalf_dig[PEPSI_MAXQ];  // mixed-radix digits of (Q-1)/2 over Q
   u64 qmodb[PEPSI_MAXB];      // Q mod p_j
   u64 qhalf_b[PEPSI_MAXB];    // (Q-1)/2 mod p_j
@@ -50,7 +50,7 @@ struct RnsConst {
   u64 t_b[PEPSI_MAXB], t_bs[PEPSI_MAXB];        // t mod p_j
   // Garner over B
   u64 cb[PEPSI_MAXB][PEPSI_MAXB], cbs[PEPSI_MAXB][PEPSI_MAXB];
-  u64 pbq[PEPSI_MAXQ][PEPSI_MAXB];  // prod_{m<l} p_m mod q_i
+  u64 bq[PEPSI_MAXQ][PEPSI_MAXB], bqs[PEPSI_MAXQ][PEPSI_MAXB];  // p_l mod q_i (Shoup)
   u64 bhalf_dig[PEPSI_MAXB];        // mixed-radix digits of (B-1)/2 over B
   u64 bmodq[PEPSI_MAXQ];            // B mod q_i
   // decryption and encoding

@@ -165,7 +165,10 @@ void rns_constants(const std::vector<u64>& Q, const std::vector<u64>& B, u64 t, 
     return r;
   };
   for (size_t j = 0; j < kb; ++j) {
-    for (size_t l = 0; l < k; ++l) rc->pqb[j][l] = prod_mod(Q, l, B[j]);
+    for (size_t l = 0; l < k; ++l) {
+      rc->qb[j][l] = Q[l] % B[j];
+      rc->qbs[j][l] = shoup_of(rc->qb[j][l], B[j]);
+    }
     rc->qmodb[j] = prod_mod(Q, k, B[j]);
     const u64 inv2 = invmod(2, B[j]);
     rc->qhalf_b[j] = mulmod((rc->qmodb[j] + B[j] - 1) % B[j], inv2, B[j]);
@@ -189,7 +192,10 @@ void rns_constants(const std::vector<u64>& Q, const std::vector<u64>& B, u64 t, 
   d = garner(bh, B);
   for (size_t j = 0; j < kb; ++j) rc->bhalf_dig[j] = d[j];
   for (size_t i = 0; i < k; ++i) {
-    for (size_t j = 0; j < kb; ++j) rc->pbq[i][j] = prod_mod(B, j, Q[i]);
+    for (size_t j = 0; j < kb; ++j) {
+      rc->bq[i][j] = B[j] % Q[i];
+      rc->bqs[i][j] = shoup_of(rc->bq[i][j], Q[i]);
+    }
     rc->bmodq[i] = prod_mod(B, kb, Q[i]);
   }
   // decryption / encoding

@@ -693,17 +693,19 @@ __device__ __forceinline__ bool digits_greater(const u64* v, const u64* h, int n
   }
   return gt;
 }
-// value of the Q-digits v (centred when neg) reduced mod B prime j
+// value of the Q-digits v (centred when neg) reduced mod B prime j, by
+// Horner's rule v_0 + q_0 (v_1 + q_1 (v_2 + ...)) with Shoup products: every
+// partial value stays below 2 p_j + 2^60, one reduction at the end
 template <int K>
 __device__ __forceinline__ u64 q_digits_mod_b(const RnsArgs& A, const u64* v, bool neg, int j) {
   constexpr int M = K ? K : PEPSI_MAXQ;
   const int k = K ? K : A.k;
   const DevPrime pb = A.pr[k + j];
-  u64 lo = 0, hi = 0;
+  u64 acc = v[k - 1];
 #pragma unroll
-  for (int l = 0; l < M; ++l)
-    if (K || l < A.k) mac128(lo, hi, v[l], A.rc.pqb[j][l]);
-  const u64 r = reduce128(hi, lo, pb);
+  for (int l = M - 2; l >= 0; --l)
+    if (K || l < k - 1) acc = shoup_lazy(acc, A.rc.qb[j][l], A.rc.qbs[j][l], pb.q) + v[l];
+  const u64 r = barrett64(acc, pb);
   return neg ? submod(r, A.rc.qmodb[j], pb.q) : r;
 }
 
@@ -902,11 +904,12 @@ __global__ void k_scale_round(const __grid_constant__ RnsArgs A, const u64* __re
   for (int i = 0; i < MQ; ++i)
     if (K || i < k) {
       const DevPrime pq = A.pr[i];
-      u64 lo = 0, hi = 0;
+      // Horner over the B digits (each below 2^61): partial values below 2 q_i + 2^61
+      u64 acc = u[kb - 1];
 #pragma unroll
-      for (int j = 0; j < MB; ++j)
-        if (KB || j < kb) mac128(lo, hi, u[j], A.rc.pbq[i][j]);
-      const u64 r = reduce128(hi, lo, pq);
+      for (int j = MB - 2; j >= 0; --j)
+        if (KB || j < kb - 1) acc = shoup_lazy(acc, A.rc.bq[i][j], A.rc.bqs[i][j], pq.q) + u[j];
+      const u64 r = barrett64(acc, pq);
       out[(size_t)i * N] = neg ? submod(r, A.rc.bmodq[i], pq.q) : r;
     }
 }

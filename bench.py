@@ -211,7 +211,7 @@ def run_ours(args):
     ctx = pepsi.Context(N=N, t=65537, prime_bits=WL["prime_bits"], h=WL["h"], ell=WL["ell"],
                         lambda_bar=WL["lambda_bar"], mu=WL["mu"], hash_key=HASH_KEY, key_seed=KEY_SEED,
                         rescale_group=RESCALE["all"], response_primes=RESPONSE_PRIMES,
-                        plaintext_bytes=args.plaintext_bytes)
+                        plaintext_bytes=args.plaintext_bytes or (7 if args.case == "large" else 8))
     ctx.set_rescale_group(RESCALE[args.rescale])
     pbytes = ctx.plaintext_bytes
     sets = make_sets(WL["m"], WL["n"], WL["planted"], bits=WL.get("bits", 64))
@@ -659,7 +659,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--plaintext-bytes", type=int, choices=[0, 7, 8], default=0,
-                    help="storage of the resident plaintexts per word (0 = 8: 64-bit words; 7: three planes)")
+                    help="storage of the resident plaintexts per word: 8 (64-bit words) or 7 (three planes); "
+                         "0: 7 for the large case, whose table is only partly resident, else 8")
     ap.add_argument("--chunk", type=int, default=0,
                     help="circuit chunk in layers (default: autotuned on the request)")
     ap.add_argument("--rescale", choices=["all", "layer"], default="all",

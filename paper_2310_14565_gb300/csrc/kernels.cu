@@ -108,26 +108,28 @@ __global__ void __launch_bounds__(NTT_MAX_THREADS, 2) k_ptgen(DevView V, const u
   for (int jj = 0; jj < JC; ++jj) {
     const int j = j0 + jj;
     if (j >= ell) break;
-    for (int i = threadIdx.x; i < N; i += blockDim.x) {
-      u32 s = brev_bits(i, V.logN);
-      poly[nsw(i)] = (bits[jj * words + (s >> 5)] >> (s & 31)) & 1u;
-    }
-    __syncthreads();
-    ntt_inv_fast(poly, V, V.tidx);
-    for (int i = threadIdx.x; i < N; i += blockDim.x) mbuf[i] = (u32)poly[nsw(i)];
+    // Encode: slot s at position brev(s), inverse NTT mod t into mbuf
+    const u32* bj = bits + jj * words;
+    ntt_inv_gg(
+        poly,
+        [&](int i) -> u64 {
+          const u32 s = brev_bits(i, V.logN);
+          return (bj[s >> 5] >> (s & 31)) & 1u;
+        },
+        [&](int i, u64 v) { mbuf[i] = (u32)v; }, V, V.tidx);
     __syncthreads();
     for (int p = 0; p < k; ++p) {
-      const u64 q = V.pr[p].q;
-      for (int i = threadIdx.x; i < N; i += blockDim.x) {
-        u64 m = mbuf[i];
-        poly[nsw(i)] = m <= thalf ? m : q - (t - m);
-      }
-      __syncthreads();
-      ntt_fwd_fast(poly, V, p);
+      // centred lift to q_p on the load, split operand format on the store
+      const u64 q = V.pr[p].q, sp = V.pr[p].split;
       u64* out = P + (((size_t)l * ell + j) * k + p) * N;
-      const u64 sp = V.pr[p].split;
-      for (int i = threadIdx.x; i < N; i += blockDim.x) out[i] = to_split(poly[nsw(i)], sp);
-      __syncthreads();
+      ntt_fwd_gg(
+          poly,
+          [&](int i) -> u64 {
+            const u64 m = mbuf[i];
+            return m <= thalf ? m : q - (t - m);
+          },
+          [&](int i, u64 v) { out[i] = to_split(v, sp); }, V, p);
+      __syncthreads();  // the next transform overwrites poly
     }
   }
 }

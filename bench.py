@@ -284,7 +284,7 @@ def run_ours(args):
     mac_launch_ms = mac_ms / mac_launches
     achieved = mac_bytes_eval / mac_launches_per_eval / (mac_launch_ms * 1e-3) / 1e9
     peak, peak_kind = measured_peaks()
-    traffic = stored_traffic() if args.case == "paper" else None
+    traffic = stored_traffic() if args.case == "paper" and pbytes == 8 else None
 
     # end to end through the C ABI with host buffers (pinned), copies inside the timed region
     for _ in range(2):

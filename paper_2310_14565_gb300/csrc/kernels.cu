@@ -801,6 +801,76 @@ __global__ void k_tensor(DevView V, const u64* __restrict__ AQ, const u64* __res
   o[(size_t)2 * np * rs] = d2;
 }
 
+// Tensor product fused with its inverse transform: block per row
+// (l, c, pi) of T3[L][3][k+kb][N] computes component c of the tensor of
+// (A_l, B_l) at prime pi on the load of the inverse NTT, and stores the
+// coefficient-form row.  Same values as k_tensor followed by the inverse
+// k_ntt, without the round trip of the NTT-form tensor through memory.
+__global__ void __launch_bounds__(NTT_MAX_THREADS, 2)
+    k_tensor_intt(DevView V, const u64* __restrict__ AQ, const u64* __restrict__ AB, const u64* __restrict__ BQ,
+                  const u64* __restrict__ BB, const u64* __restrict__ cstQ, const u64* __restrict__ side,
+                  u64* __restrict__ T3, int square) {
+  extern __shared__ u64 sm[];
+  const int N = V.N, k = V.k, kb = V.kb, np = k + kb;
+  const size_t r = blockIdx.x;
+  const int pi = (int)(r % np);
+  const size_t o = r / np;  // l * 3 + c
+  const int c = (int)(o % 3);
+  const size_t l = o / 3;
+  const DevPrime pr = V.pr[pi];
+  const u64 *A, *Bp;
+  size_t o0, o1;
+  u64 cb = 0;  // constant added to b0 (NTT form: the same at every point)
+  if (pi < k) {
+    A = AQ;
+    Bp = BQ;
+    o0 = ((l * 2 + 0) * k + pi) * N;
+    o1 = ((l * 2 + 1) * k + pi) * N;
+    if (!square && cstQ) cb = cstQ[pi];
+  } else {
+    A = AB;
+    Bp = BB;
+    o0 = ((l * 2 + 0) * kb + (pi - k)) * N;
+    o1 = ((l * 2 + 1) * kb + (pi - k)) * N;
+    if (!square && side) cb = side[l * kb + (pi - k)];
+  }
+  const u64* a0 = A + o0;
+  const u64* a1 = A + o1;
+  const u64* b0 = Bp + o0;
+  const u64* b1 = Bp + o1;
+  u64* out = T3 + r * N;
+  const auto st = [&](int x, u64 v) { out[x] = v; };
+  if (square) {
+    if (c == 0)
+      ntt_inv_gg(sm, [&](int x) { return mulmod(a0[x], a0[x], pr); }, st, V, pi);
+    else if (c == 1)
+      ntt_inv_gg(
+          sm,
+          [&](int x) {
+            const u64 m = mulmod(a0[x], a1[x], pr);
+            return addmod(m, m, pr.q);
+          },
+          st, V, pi);
+    else
+      ntt_inv_gg(sm, [&](int x) { return mulmod(a1[x], a1[x], pr); }, st, V, pi);
+  } else {
+    if (c == 0)
+      ntt_inv_gg(sm, [&](int x) { return mulmod(a0[x], addmod(b0[x], cb, pr.q), pr); }, st, V, pi);
+    else if (c == 1)
+      ntt_inv_gg(
+          sm,
+          [&](int x) {
+            u64 lo = 0, hi = 0;
+            mac128(lo, hi, a0[x], b1[x]);
+            mac128(lo, hi, a1[x], addmod(b0[x], cb, pr.q));
+            return reduce128(hi, lo, pr);
+          },
+          st, V, pi);
+    else
+      ntt_inv_gg(sm, [&](int x) { return mulmod(a1[x], b1[x], pr); }, st, V, pi);
+  }
+}
+
 // Lazy rescaling: X[c][pi][n] (+)= sum over layers l < L of component c of
 // the tensor of (A_l, B_l), in NTT form over Q u B, each layer's tensor
 // times its value plaintext VP[l][pi][n] when VP is given (labelled PSI /
@@ -1407,6 +1477,14 @@ void launch_tensor(const DevView& V, const u64* AQ, const u64* AB, const u64* BQ
   k_tensor<<<grid_for(total, 256), 256, 0, st>>>(V, AQ, AB, BQ, BB, cstQ, side, T3, L, square ? 1 : 0);
 }
 
+void launch_tensor_intt(const DevView& V, const u64* AQ, const u64* AB, const u64* BQ, const u64* BB,
+                        const u64* cstQ, const u64* side, u64* T3, int L, bool square, cudaStream_t st) {
+  const size_t rows = (size_t)L * 3 * (V.k + V.kb);
+  if (!rows) return;
+  k_tensor_intt<<<(unsigned)rows, ntt_threads(V.N), (size_t)V.N * 8, st>>>(V, AQ, AB, BQ, BB, cstQ, side, T3,
+                                                                          square ? 1 : 0);
+}
+
 void launch_tensor_sum(const DevView& V, const u64* AQ, const u64* AB, const u64* BQ, const u64* BB,
                        const u64* cstQ, const u64* side, const u64* VP, u64* X, int L, bool square, bool init,
                        cudaStream_t st) {
@@ -1551,6 +1629,7 @@ cudaError_t kernels_init(int N) {
   set((const void*)k_mac_multi<1, true>);
   set((const void*)k_mac_multi<2, true>);
   set((const void*)k_relin_ntt);
+  set((const void*)k_tensor_intt);
   set((const void*)k_encrypt);
   set((const void*)k_keygen_sntt);
   set((const void*)k_keygen_rlk);

@@ -74,6 +74,11 @@ void launch_lift(const DevView& V, const u64* src, u64* dstB, int L, const u64* 
 void launch_tensor(const DevView& V, const u64* AQ, const u64* AB, const u64* BQ, const u64* BB, const u64* cstQ,
                    const u64* side, u64* T3, int L, bool square, cudaStream_t st);
 
+// The same tensor followed by the inverse NTT of every row, in one kernel:
+// T3[L][3][k+kb][N] in coefficient form.
+void launch_tensor_intt(const DevView& V, const u64* AQ, const u64* AB, const u64* BQ, const u64* BB,
+                        const u64* cstQ, const u64* side, u64* T3, int L, bool square, cudaStream_t st);
+
 // Exact round(t x / Q) from Q u B residues (coefficient form) -> D[L][3][k][N] mod Q.
 // X[3][k+kb][N] (+)= sum over L layers of the tensor of (A, B) (NTT form over
 // Q u B), each times the layer's value plaintext VP[l][k+kb][N] when VP is

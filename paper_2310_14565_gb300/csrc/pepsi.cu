@@ -83,9 +83,9 @@ struct pepsi_ctx {
   cudaStream_t aux_stream = nullptr;  // overlapped multiply-accumulates of pepsi_eval_batch
   cudaEvent_t aux_ev[4] = {};
   // host requests: copies of the request pieces, overlapped with the
-  // multiply-accumulate of the pieces already on the device (two pieces:
-  // each further MAC launch costs its pipeline fill, measured to outweigh
-  // the copy it hides)
+  // multiply-accumulate of the pieces already on the device (two pieces, the
+  // first short: each further MAC launch costs its pipeline fill, measured to
+  // outweigh the copy it hides)
   static constexpr int kPieces = 2;
   cudaStream_t copy_stream = nullptr;
   cudaEvent_t copy_ready = nullptr, copy_ev[kPieces] = {};
@@ -253,13 +253,10 @@ void extend(pepsi_ctx* c, const u64* src_ntt, u64* coef, u64* Bpart, int L, cons
 // T3 = tensor, then inverse NTT over Q u B, then exact scale-and-round -> D.
 void mult_tail(pepsi_ctx* c, const u64* AQ, const u64* AB, const u64* BQ, const u64* BB, const u64* cQ,
                const u64* side, bool square, u64* T3, u64* D, int L, cudaStream_t st) {
-  const int np = c->k + c->kb;
-  const size_t npN = (size_t)np * c->N;
   {
-    Prof p(c, PC_TENSOR, st);
-    launch_tensor(c->V, AQ, AB, BQ, BB, cQ, side, T3, L, square, st);
+    Prof p(c, PC_TENSOR, st);  // the tensor and its inverse NTT over Q u B
+    launch_tensor_intt(c->V, AQ, AB, BQ, BB, cQ, side, T3, L, square, st);
   }
-  ntt(c, false, T3, T3, (size_t)L * 3, np, 0, npN, npN, st);
   Prof p(c, PC_SCALE, st);
   launch_scale_round(c->V, T3, D, L, st);
 }
@@ -615,9 +612,16 @@ int eval_core(pepsi_ctx* c, int set_id, const u64* cts, u32 layer0, u32 nl, int 
     if (!Hall) return cuda_status(e);
     const PlainTab P0 = S.plain(kN, c->ell, layer0);
     if (pieces) {
-      int jb[pepsi_ctx::kPieces + 1];
-      for (int q = 0; q < npieces; ++q) jb[q] = (c->ell * q / npieces) & ~3;  // multiples of 4 bits
-      jb[npieces] = c->ell;
+      // Piece boundaries in multiples of 4 bits.  The first piece is short, so
+      // that little of the upload is exposed, yet its NTT and MAC must cover
+      // the upload of the rest.  The MAC reads nres*ell*k*N table words while
+      // the rest of the request is 2*(ell - j1)*k*N words, copied from the host
+      // at well over 1/32 of HBM bandwidth: j1 = 64/nres of the bits covers it,
+      // at least 4 bits and at most half.
+      static_assert(pepsi_ctx::kPieces == 2, "two pieces");
+      const double w = std::min(0.5, 64.0 / (double)(res_end - layer0));
+      const int j1 = std::max(4, std::min((int)(c->ell * w) & ~3, (c->ell / 2) & ~3));
+      const int jb[3] = {0, j1, c->ell};
       CKS(ensure_copy_stream(c));
       CKS(cudaEventRecord(c->copy_ready, st));  // earlier work on st no longer reads the request buffer
       CKS(cudaStreamWaitEvent(c->copy_stream, c->copy_ready, 0));

@@ -871,6 +871,34 @@ __global__ void __launch_bounds__(NTT_MAX_THREADS, 2)
   }
 }
 
+// out = a + z * b (NTT form, rows [groups][k][N], z as k residues), fused
+// with the inverse NTT of out into coef: the block of a row computes the
+// row on the transform's load and also stores it (each element is loaded
+// once).  coef may alias b: a block reads its row of b before it writes
+// that row of coef.
+__global__ void __launch_bounds__(NTT_MAX_THREADS, 2)
+    k_axpy_intt(DevView V, const u64* __restrict__ a, const u64* __restrict__ zres, const u64* b, u64* __restrict__ out,
+                u64* coef) {
+  extern __shared__ u64 sm[];
+  const int N = V.N;
+  const size_t r = blockIdx.x;
+  const int p = (int)(r % V.k);
+  const DevPrime pr = V.pr[p];
+  const u64 z = zres[p];
+  const u64* ar = a + r * N;
+  const u64* br = b + r * N;
+  u64* ur = out + r * N;
+  u64* cr = coef + r * N;
+  ntt_inv_gg(
+      sm,
+      [&](int x) {
+        const u64 u = addmod(ar[x], mulmod(z, br[x], pr), pr.q);
+        ur[x] = u;
+        return u;
+      },
+      [&](int x, u64 v) { cr[x] = v; }, V, p);
+}
+
 // Lazy rescaling: X[c][pi][n] (+)= sum over layers l < L of component c of
 // the tensor of (A_l, B_l), in NTT form over Q u B, each layer's tensor
 // times its value plaintext VP[l][pi][n] when VP is given (labelled PSI /
@@ -1542,6 +1570,13 @@ void launch_relin(const DevView& V, const u64* D, const u64* rlk, u64* DG, u64* 
   k_relin_mac<<<grid_for((size_t)L * V.k * V.N, 256), 256, 0, st>>>(V, DG, rlk, R, L);
 }
 
+void launch_axpy_intt(const DevView& V, const u64* a, const u64* zres, const u64* b, u64* out, u64* coef,
+                      size_t groups, cudaStream_t st) {
+  const size_t rows = groups * V.k;
+  if (!rows) return;
+  k_axpy_intt<<<(unsigned)rows, ntt_threads(V.N), (size_t)V.N * 8, st>>>(V, a, zres, b, out, coef);
+}
+
 void launch_axpy(const DevView& V, const u64* a, const u64* zres, const u64* b, u64* out, size_t groups,
                  cudaStream_t st) {
   const size_t total = groups * V.k * V.N;
@@ -1630,6 +1665,7 @@ cudaError_t kernels_init(int N) {
   set((const void*)k_mac_multi<2, true>);
   set((const void*)k_relin_ntt);
   set((const void*)k_tensor_intt);
+  set((const void*)k_axpy_intt);
   set((const void*)k_encrypt);
   set((const void*)k_keygen_sntt);
   set((const void*)k_keygen_rlk);

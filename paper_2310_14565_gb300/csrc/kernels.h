@@ -113,6 +113,10 @@ void launch_relin(const DevView& V, const u64* D, const u64* rlk, u64* DG, u64* 
 void launch_axpy(const DevView& V, const u64* a, const u64* zres, const u64* b, u64* out, size_t groups,
                  cudaStream_t st);
 
+// The same, and the inverse NTT of out into coef (coefficient form) in one kernel; coef may alias b.
+void launch_axpy_intt(const DevView& V, const u64* a, const u64* zres, const u64* b, u64* out, u64* coef,
+                      size_t groups, cudaStream_t st);
+
 // acc[3][k][N] (+)= sum_{l<L} D[l][3][k][N]
 void launch_accum(const DevView& V, const u64* D, int L, u64* acc, bool init, cudaStream_t st);
 

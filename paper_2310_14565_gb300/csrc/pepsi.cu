@@ -250,6 +250,22 @@ void extend(pepsi_ctx* c, const u64* src_ntt, u64* coef, u64* Bpart, int L, cons
   ntt(c, true, Bpart, Bpart, (size_t)L * 2, c->kb, c->k, kbN, kbN, st);
 }
 
+// out = a + z * b, then extend(out) as above, the axpy on the load of the
+// inverse NTT (coef may alias b).
+void axpy_extend(pepsi_ctx* c, const u64* a, const u64* z, const u64* b, u64* out, u64* coef, u64* Bpart, int L,
+                 const u64* cstv, u64* side, cudaStream_t st) {
+  const size_t kbN = (size_t)c->kb * c->N;
+  {
+    Prof p(c, PC_NTT, st);
+    launch_axpy_intt(c->V, a, z, b, out, coef, (size_t)L * 2, st);
+  }
+  {
+    Prof p(c, PC_LIFT, st);
+    launch_lift(c->V, coef, Bpart, L, cstv, side, st);
+  }
+  ntt(c, true, Bpart, Bpart, (size_t)L * 2, c->kb, c->k, kbN, kbN, st);
+}
+
 // T3 = tensor, then inverse NTT over Q u B, then exact scale-and-round -> D.
 void mult_tail(pepsi_ctx* c, const u64* AQ, const u64* AB, const u64* BQ, const u64* BB, const u64* cQ,
                const u64* side, bool square, u64* T3, u64* D, int L, cudaStream_t st) {
@@ -367,8 +383,7 @@ LastMult eq_circuit_front(pepsi_ctx* c, EvalBufs& b, int L, cudaStream_t st) {
       extend(c, b.H, b.Hc, b.XB, L, nullptr, nullptr, st);
       mult_tail(c, b.H, b.XB, b.H, b.XB, nullptr, nullptr, true, b.T3, b.D, L, st);
       relin(c, b.D, b.R, L, st);
-      axpy(c, b.R, cst(c, CS_M3), b.H, b.U, (size_t)L * 2, st);
-      extend(c, b.U, b.X, b.YB, L, cst(c, CS_D_2), b.side, st);
+      axpy_extend(c, b.R, cst(c, CS_M3), b.H, b.U, b.X, b.YB, L, cst(c, CS_D_2), b.side, st);
       last(b.U, b.YB, b.U, b.YB, cst(c, CS_D_2), b.side, false);
       break;
     }
@@ -376,14 +391,11 @@ LastMult eq_circuit_front(pepsi_ctx* c, EvalBufs& b, int L, cudaStream_t st) {
       extend(c, b.H, b.Hc, b.XB, L, nullptr, nullptr, st);
       mult_tail(c, b.H, b.XB, b.H, b.XB, nullptr, nullptr, true, b.T3, b.D, L, st);
       relin(c, b.D, b.R, L, st);
-      axpy(c, b.R, cst(c, CS_M7), b.H, b.U, (size_t)L * 2, st);
-      extend(c, b.U, b.X, b.XB, L, nullptr, nullptr, st);
+      axpy_extend(c, b.R, cst(c, CS_M7), b.H, b.U, b.X, b.XB, L, nullptr, nullptr, st);
       mult_tail(c, b.U, b.XB, b.U, b.XB, nullptr, nullptr, true, b.T3, b.D, L, st);
       relin(c, b.D, b.W, L, st);
-      axpy(c, b.W, cst(c, CS_P12), b.U, b.X, (size_t)L * 2, st);
-      axpy(c, b.W, cst(c, CS_P16), b.U, b.Y, (size_t)L * 2, st);
-      extend(c, b.X, b.R, b.XB, L, nullptr, nullptr, st);
-      extend(c, b.Y, b.U, b.YB, L, cst(c, CS_D_60), b.side, st);
+      axpy_extend(c, b.W, cst(c, CS_P12), b.U, b.X, b.R, b.XB, L, nullptr, nullptr, st);
+      axpy_extend(c, b.W, cst(c, CS_P16), b.U, b.Y, b.U, b.YB, L, cst(c, CS_D_60), b.side, st);
       last(b.X, b.XB, b.Y, b.YB, cst(c, CS_D_60), b.side, false);
       break;
     }

@@ -130,3 +130,16 @@ def test_large_config_streamed_plaintexts():
     assert budget > 0
     assert np.array_equal(slots, brute_indicator(sets.client, sets.server, where, 16384))
     assert int(slots.sum()) == 41
+
+
+def test_paper_host_pieces_equal_device_request(paper_case):
+    """A host request is multiplied in two pieces of code bits (the first 72 of
+    600 bits here); a device request in one launch.  Same words."""
+    torch = torch_cuda()
+    oc, gc, s, rlk, sets, sid, Ts, cts, where = paper_case
+    host = gc.eval(sid, cts)
+    dev_in = torch.from_numpy(np.ascontiguousarray(cts).view(np.int64).copy()).cuda()
+    dev_out = torch.zeros(host.size, dtype=torch.int64, device="cuda")
+    gc.eval(sid, dev_in, out=dev_out)
+    torch.cuda.synchronize()
+    assert np.array_equal(dev_out.cpu().numpy().view(np.uint64).reshape(host.shape), host)

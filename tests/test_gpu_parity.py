@@ -340,3 +340,11 @@ def test_table3_prime_sets_match_oracle(h, bits, N):
     slots, b = gc.decrypt(got)
     assert b > 0
     assert np.array_equal(slots, hashed_indicator(sets.client, sets.server, where, N, 12))
+
+
+def test_host_request_uneven_pieces_match_oracle():
+    """With more than 128 resident layers the first upload piece of a host
+    request is shorter than half the code bits; the result is the oracle's."""
+    oc, gc, s, rlk, sets, Ts, cts, where, sid = _psi_case(64, PAPER, 4, 10, mu=160, m=20, n=70, planted=4, chunk=64)
+    assert Ts.shape[0] >= 160 and gc.ell >= 8
+    assert np.array_equal(gc.eval(sid, cts), oc.eval(rlk, cts, Ts))

@@ -13,11 +13,15 @@
 namespace {
 
 // Threads of a block running the register-blocked NTT: one per group of 8
-// elements, at most NTT_MAX_THREADS (the kernels below are compiled for it).
-constexpr int NTT_MAX_THREADS = 512;
+// elements, at most 512 (two blocks of 64 KB per SM up to N = 8192), and
+// 1024 at N = 16384, whose 128 KB polynomial leaves room for one block per
+// SM.  The kernels below are compiled for 1024 threads at 64 registers, so
+// either shape keeps 32 warps on an SM.
+constexpr int NTT_MAX_THREADS = 1024;
 inline int ntt_threads(int N) {
+  if (N >= 16384) return NTT_MAX_THREADS;
   int t = N / 8;
-  if (t > NTT_MAX_THREADS) t = NTT_MAX_THREADS;
+  if (t > 512) t = 512;
   if (t < 32) t = 32;
   return t;
 }
@@ -26,7 +30,7 @@ inline int ntt_threads(int N) {
 // SPLIT: store the result in the split operand format of the
 // multiply-accumulate (the request's forward transform).
 template <bool FWD, bool SPLIT = false>
-__global__ void __launch_bounds__(NTT_MAX_THREADS, 2) k_ntt(DevView V, const u64* __restrict__ src, u64* dst, int np, int p0, size_t src_os,
+__global__ void __launch_bounds__(NTT_MAX_THREADS, 1) k_ntt(DevView V, const u64* __restrict__ src, u64* dst, int np, int p0, size_t src_os,
                       size_t dst_os) {
   extern __shared__ u64 sm[];
   const int N = V.N;
@@ -82,7 +86,7 @@ __global__ void k_cw_unrank(const u64* __restrict__ T, size_t count, const u64* 
 // Block (layer l, j-chunk): bit planes of the layer's codewords, encoded
 // (inverse NTT mod t of the slot vector in bit-reversed order), centred
 // lift into each q_p and forward NTT; stored in the split operand format.
-__global__ void __launch_bounds__(NTT_MAX_THREADS, 2) k_ptgen(DevView V, const uint16_t* __restrict__ pos, int ell, int h, int JC, u64* P) {
+__global__ void __launch_bounds__(NTT_MAX_THREADS, 1) k_ptgen(DevView V, const uint16_t* __restrict__ pos, int ell, int h, int JC, u64* P) {
   extern __shared__ u64 sm[];
   const int N = V.N, k = V.k;
   const int words = N / 32 > 0 ? N / 32 : 1;
@@ -138,7 +142,7 @@ __global__ void __launch_bounds__(NTT_MAX_THREADS, 2) k_ptgen(DevView V, const u
 // l (one block each), slots V[l][.] -> Encode (inverse NTT mod t, slot s at
 // position brev(s)) -> centred lift -> forward NTT for every prime of
 // Q u B.  Out VP[l][k+kb][N] (plain residues, not the split format).
-__global__ void __launch_bounds__(NTT_MAX_THREADS, 2) k_valgen(DevView V, const u32* __restrict__ vals, u64* VP) {
+__global__ void __launch_bounds__(NTT_MAX_THREADS, 1) k_valgen(DevView V, const u32* __restrict__ vals, u64* VP) {
   extern __shared__ u64 sm[];
   const int N = V.N, np = V.k + V.kb;
   u64* poly = sm;                              // N u64
@@ -806,7 +810,7 @@ __global__ void k_tensor(DevView V, const u64* __restrict__ AQ, const u64* __res
 // (A_l, B_l) at prime pi on the load of the inverse NTT, and stores the
 // coefficient-form row.  Same values as k_tensor followed by the inverse
 // k_ntt, without the round trip of the NTT-form tensor through memory.
-__global__ void __launch_bounds__(NTT_MAX_THREADS, 2)
+__global__ void __launch_bounds__(NTT_MAX_THREADS, 1)
     k_tensor_intt(DevView V, const u64* __restrict__ AQ, const u64* __restrict__ AB, const u64* __restrict__ BQ,
                   const u64* __restrict__ BB, const u64* __restrict__ cstQ, const u64* __restrict__ side,
                   u64* __restrict__ T3, int square) {
@@ -876,7 +880,7 @@ __global__ void __launch_bounds__(NTT_MAX_THREADS, 2)
 // row on the transform's load and also stores it (each element is loaded
 // once).  coef may alias b: a block reads its row of b before it writes
 // that row of coef.
-__global__ void __launch_bounds__(NTT_MAX_THREADS, 2)
+__global__ void __launch_bounds__(NTT_MAX_THREADS, 1)
     k_axpy_intt(DevView V, const u64* __restrict__ a, const u64* __restrict__ zres, const u64* b, u64* __restrict__ out,
                 u64* coef) {
   extern __shared__ u64 sm[];
@@ -1018,7 +1022,7 @@ __global__ void k_scale_round(const __grid_constant__ RnsArgs A, const u64* __re
 // Phase 1, block per row of DG[L][k+2][k][N]: row (l, i, j) holds
 // NTT_{q_j}([d2]_{q_i}) for digits i < k, and NTT_{q_j}(d0), NTT_{q_j}(d1)
 // for i = k, k+1.
-__global__ void __launch_bounds__(NTT_MAX_THREADS, 2) k_relin_ntt(DevView V, const u64* __restrict__ D, u64* __restrict__ DG) {
+__global__ void __launch_bounds__(NTT_MAX_THREADS, 1) k_relin_ntt(DevView V, const u64* __restrict__ D, u64* __restrict__ DG) {
   extern __shared__ u64 sm[];
   const int N = V.N, k = V.k;
   const size_t r = blockIdx.x;
@@ -1092,7 +1096,7 @@ __device__ __forceinline__ u64 smod_dev(i64 v, u64 q) { return v >= 0 ? (u64)v :
 
 // Block per ciphertext j: encode bit plane j, then for each prime sample
 // a, compute c0 = e - a s + round(Q m / t), c1 = a (coefficient form).
-__global__ void __launch_bounds__(NTT_MAX_THREADS, 2) k_encrypt(DevView V, const uint16_t* __restrict__ pos, int h, const u64* __restrict__ s_ntt, u64 seed,
+__global__ void __launch_bounds__(NTT_MAX_THREADS, 1) k_encrypt(DevView V, const uint16_t* __restrict__ pos, int h, const u64* __restrict__ s_ntt, u64 seed,
                           u64 idx0, u64* cts) {
   extern __shared__ u64 sm[];
   const int N = V.N, k = V.k, j = blockIdx.x;
@@ -1142,7 +1146,7 @@ __global__ void k_keygen_s(DevView V, u64 seed, int8_t* s) {
   const u64 key = stream_key(seed, make_stream(STREAM_SK, 0, 0));
   s[n] = (int8_t)((int)sample_uniform(key, n, 3) - 1);
 }
-__global__ void __launch_bounds__(NTT_MAX_THREADS, 2) k_keygen_sntt(DevView V, const int8_t* __restrict__ s, u64* s_ntt) {
+__global__ void __launch_bounds__(NTT_MAX_THREADS, 1) k_keygen_sntt(DevView V, const int8_t* __restrict__ s, u64* s_ntt) {
   extern __shared__ u64 sm[];
   const int p = blockIdx.x, N = V.N;
   const u64 q = V.pr[p].q;
@@ -1153,7 +1157,7 @@ __global__ void __launch_bounds__(NTT_MAX_THREADS, 2) k_keygen_sntt(DevView V, c
 }
 // Block (digit i, prime j): rlk_i = (-a_i s + e_i + g_i s^2, a_i) in NTT form,
 // g_i = 1 mod q_i and 0 mod q_j for j != i.
-__global__ void __launch_bounds__(NTT_MAX_THREADS, 2) k_keygen_rlk(DevView V, u64 seed, const u64* __restrict__ s_ntt, u64* rlk) {
+__global__ void __launch_bounds__(NTT_MAX_THREADS, 1) k_keygen_rlk(DevView V, u64 seed, const u64* __restrict__ s_ntt, u64* rlk) {
   extern __shared__ u64 sm[];
   const int N = V.N, k = V.k;
   const int i = blockIdx.x / k, j = blockIdx.x % k;
@@ -1181,7 +1185,7 @@ __global__ void __launch_bounds__(NTT_MAX_THREADS, 2) k_keygen_rlk(DevView V, u6
 }
 
 // Decryption, step 1: z = c0 + c1 s per prime (coefficient form).
-__global__ void __launch_bounds__(NTT_MAX_THREADS, 2) k_dec_z(DevView V, const u64* __restrict__ ct, const u64* __restrict__ s_ntt, u64* z) {
+__global__ void __launch_bounds__(NTT_MAX_THREADS, 1) k_dec_z(DevView V, const u64* __restrict__ ct, const u64* __restrict__ s_ntt, u64* z) {
   extern __shared__ u64 sm[];
   const int p = blockIdx.x, N = V.N, k = V.k;
   const DevPrime pq = V.pr[p];
@@ -1244,7 +1248,7 @@ __global__ void k_dec_coef(const __grid_constant__ RnsArgs A, DevView V, const u
   }
 }
 // Step 3: slots = values of m at psi_t^(2s+1): forward NTT mod t, slot s in position brev(s).
-__global__ void __launch_bounds__(NTT_MAX_THREADS, 2) k_dec_slots(DevView V, const u32* __restrict__ m, u32* slots) {
+__global__ void __launch_bounds__(NTT_MAX_THREADS, 1) k_dec_slots(DevView V, const u32* __restrict__ m, u32* slots) {
   extern __shared__ u64 sm[];
   const int N = V.N;
   for (int i = threadIdx.x; i < N; i += blockDim.x) sm[nsw(i)] = m[i];
@@ -1290,7 +1294,7 @@ __global__ void k_modswitch(const __grid_constant__ ModSwitchArgs M, DevView V, 
 
 // Cardinality mask (Algorithm 5): r_s uniform in Z_t for s < N-1,
 // r_{N-1} = -sum; c0 += round(Q Encode(r) / t).  One block.
-__global__ void __launch_bounds__(NTT_MAX_THREADS, 2) k_mask(DevView V, u64 seed, u64* ct) {
+__global__ void __launch_bounds__(NTT_MAX_THREADS, 1) k_mask(DevView V, u64 seed, u64* ct) {
   extern __shared__ u64 sm[];
   __shared__ u64 red[32];
   const int N = V.N, k = V.k;

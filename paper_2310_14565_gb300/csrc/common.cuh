@@ -75,7 +75,7 @@ struct DevView {
   int N, logN, k, kb, tidx;  // tidx: index of t among the moduli (= k + kb)
   const DevPrime* pr;        // [k + kb + 1]
   const ulonglong2* twp;     // [np][N] (psi^brev(i), its Shoup companion)
-  const ulonglong2* itwp;    // [np][N] (psi^-brev(i), its Shoup companion)
+  const ulonglong2* itwp;    // [np][N] (psi^-brev(i), its Shoup companion); entry 0: psi^-brev(1) N^-1
   const RnsConst* rc;
   const RnsArgs* host_args;  // host copy for by-value launches (not dereferenced on the device)
 };

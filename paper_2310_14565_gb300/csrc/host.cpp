@@ -130,6 +130,13 @@ void twiddles(u64 q, u64 psi, u32 N, u64* tw, u64* tws, u64* itw, u64* itws) {
     itw[i] = ipw[r];
     itws[i] = shoup_of(itw[i], q);
   }
+  // entry 0 is not a stage twiddle (stage s uses [2^s, 2^(s+1))): the
+  // inverse table keeps there its stage-0 twiddle times N^-1, which the last
+  // inverse stage applies to its difference outputs
+  if (N > 1) {
+    itw[0] = mulmod(itw[1], invmod(N % q, q), q);
+    itws[0] = shoup_of(itw[0], q);
+  }
 }
 
 // Garner digits of the integer whose residues are x over primes p.

@@ -39,16 +39,14 @@ __global__ void __launch_bounds__(NTT_MAX_THREADS, 1) k_ntt(DevView V, const u64
   const size_t o = r / np;
   const u64* s = src + o * src_os + (size_t)pl * N;
   u64* d = dst + o * dst_os + (size_t)pl * N;
-  const auto ld = [&](int x) { return s[x]; };
+  const RowLd ld(s);
   if (FWD) {
-    if (SPLIT) {
-      const u64 sp = V.pr[p0 + pl].split;
-      ntt_fwd_gg(sm, ld, [&](int x, u64 v) { d[x] = to_split(v, sp); }, V, p0 + pl);
-    } else {
-      ntt_fwd_gg(sm, ld, [&](int x, u64 v) { d[x] = v; }, V, p0 + pl);
-    }
+    if (SPLIT)
+      ntt_fwd_gg(sm, ld, SplitSt(d, V.pr[p0 + pl].split), V, p0 + pl);
+    else
+      ntt_fwd_gg(sm, ld, RowSt(d), V, p0 + pl);
   } else {
-    ntt_inv_gg(sm, ld, [&](int x, u64 v) { d[x] = v; }, V, p0 + pl);
+    ntt_inv_gg(sm, ld, RowSt(d), V, p0 + pl);
   }
 }
 
@@ -132,7 +130,7 @@ __global__ void __launch_bounds__(NTT_MAX_THREADS, 1) k_ptgen(DevView V, const u
             const u64 m = mbuf[i];
             return m <= thalf ? m : q - (t - m);
           },
-          [&](int i, u64 v) { out[i] = to_split(v, sp); }, V, p);
+          SplitSt(out, sp), V, p);
       __syncthreads();  // the next transform overwrites poly
     }
   }
@@ -842,8 +840,7 @@ __global__ void __launch_bounds__(NTT_MAX_THREADS, 1)
   const u64* a1 = A + o1;
   const u64* b0 = Bp + o0;
   const u64* b1 = Bp + o1;
-  u64* out = T3 + r * N;
-  const auto st = [&](int x, u64 v) { out[x] = v; };
+  const RowSt st(T3 + r * N);
   if (square) {
     if (c == 0)
       ntt_inv_gg(sm, [&](int x) { return mulmod(a0[x], a0[x], pr); }, st, V, pi);
@@ -900,7 +897,7 @@ __global__ void __launch_bounds__(NTT_MAX_THREADS, 1)
         ur[x] = u;
         return u;
       },
-      [&](int x, u64 v) { cr[x] = v; }, V, p);
+      RowSt(cr), V, p);
 }
 
 // Lazy rescaling: X[c][pi][n] (+)= sum over layers l < L of component c of
@@ -1038,7 +1035,7 @@ __global__ void __launch_bounds__(NTT_MAX_THREADS, 1) k_relin_ntt(DevView V, con
         const u64 w = row[x];
         return w >= pj.q ? barrett64(w, pj) : w;
       },
-      [&](int x, u64 v) { out[x] = v; }, V, j);
+      RowSt(out), V, j);
 }
 // Phase 2, thread per (l, j, n): R_c = NTT(d_c) + sum_i NTT(d_i) * rlk_i[c],
 // 128-bit lazy sums, one Barrett reduction per output.

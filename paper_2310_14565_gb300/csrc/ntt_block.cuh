@@ -19,6 +19,7 @@
 // of consecutive elements stay conflict-free.  Callers filling or reading
 // the array index it through nsw().
 #pragma once
+#include <type_traits>
 #include "common.cuh"
 
 __device__ __forceinline__ int nsw(int x) { return x ^ ((x >> 4) & 15); }
@@ -102,6 +103,46 @@ __device__ __forceinline__ void inv_final(u64 (&x)[E], u64 q, u64 ninv, u64 ninv
   for (int i = 0; i < E; ++i) {
     const u64 v = shoup_lazy(x[i], ninv, ninvs, q);
     x[i] = v >= q ? v - q : v;
+  }
+}
+
+// Stages 2, 1, 0 of the inverse on the radix-8 group at base, with the
+// factor N^-1: the sums of stage 0 are multiplied by N^-1, the differences
+// by the table's entry 0 (the stage-0 twiddle times N^-1) instead of by the
+// twiddle, then every element is reduced to [0, q).  The same residues as
+// inv_group<3> at s0 = 0 followed by inv_final, with half the products of
+// the final scaling.
+__device__ __forceinline__ void inv_group_last(u64 (&x)[8], int base, int logN, u64 q,
+                                               const ulonglong2* __restrict__ itw, u64 ninv, u64 ninvs) {
+  const u64 q2 = 2 * q;
+#pragma unroll
+  for (int ss = 2; ss >= 1; --ss) {
+    const int half = 1 << (2 - ss);
+    const int tbase = (1 << ss) + (base >> (logN - ss));
+    ulonglong2 Wt[4];
+#pragma unroll
+    for (int d = 0; d < (1 << ss); ++d) Wt[d] = __ldg(itw + tbase + d);
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      if ((i & half) == 0) {
+        const u64 W = Wt[i >> (3 - ss)].x, Ws = Wt[i >> (3 - ss)].y;
+        const u64 U = x[i], V = x[i + half];
+        u64 S = U + V;
+        S = S >= q2 ? S - q2 : S;
+        x[i] = S;
+        x[i + half] = shoup_lazy(U + q2 - V, W, Ws, q);
+      }
+    }
+  }
+  const ulonglong2 Wn = __ldg(itw);
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const u64 U = x[i], V = x[i + 4];
+    u64 S = U + V;
+    S = S >= q2 ? S - q2 : S;
+    const u64 a = shoup_lazy(S, ninv, ninvs, q), b = shoup_lazy(U + q2 - V, Wn.x, Wn.y, q);
+    x[i] = a >= q ? a - q : a;
+    x[i + 4] = b >= q ? b - q : b;
   }
 }
 
@@ -241,6 +282,78 @@ __device__ __forceinline__ void ntt_inv_fast(u64* a, const DevView& V, int pi) {
   }
 }
 
+// Row accessors for the global-to-global transforms.  A functor with a
+// pair(x, ...) member moves elements x and x + 1 (x even) together; the
+// transforms use it for the groups of consecutive elements (the first group
+// of the inverse, the last of the forward).  The row accessors do one
+// 16-byte access when the row is 16-byte aligned (rows are whole multiples
+// of N words from their base, so the test is uniform over a block) and two
+// 8-byte accesses otherwise: caller buffers need only 8-byte alignment.
+// Plain lambdas are used element by element.
+template <class T, class = void>
+struct has_pair : std::false_type {};
+template <class T>
+struct has_pair<T, std::void_t<decltype(&T::pair)>> : std::true_type {};
+__device__ __forceinline__ bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
+struct RowLd {
+  const u64* p;
+  bool v16;
+  __device__ __forceinline__ explicit RowLd(const u64* row) : p(row), v16(aligned16(row)) {}
+  __device__ __forceinline__ u64 operator()(int x) const { return p[x]; }
+  __device__ __forceinline__ void pair(int x, u64& a, u64& b) const {
+    if (v16) {
+      const ulonglong2 w = *reinterpret_cast<const ulonglong2*>(p + x);
+      a = w.x;
+      b = w.y;
+    } else {
+      a = p[x];
+      b = p[x + 1];
+    }
+  }
+};
+struct RowSt {
+  u64* p;
+  bool v16;
+  __device__ __forceinline__ explicit RowSt(u64* row) : p(row), v16(aligned16(row)) {}
+  __device__ __forceinline__ void operator()(int x, u64 v) const { p[x] = v; }
+  __device__ __forceinline__ void pair(int x, u64 a, u64 b) const {
+    if (v16) {
+      *reinterpret_cast<ulonglong2*>(p + x) = make_ulonglong2(a, b);
+    } else {
+      p[x] = a;
+      p[x + 1] = b;
+    }
+  }
+};
+// the split operand format of the multiply-accumulate (shift s)
+struct SplitSt {
+  RowSt r;
+  u64 s;
+  __device__ __forceinline__ SplitSt(u64* row, u64 shift) : r(row), s(shift) {}
+  __device__ __forceinline__ void operator()(int x, u64 v) const { r(x, to_split(v, s)); }
+  __device__ __forceinline__ void pair(int x, u64 a, u64 b) const { r.pair(x, to_split(a, s), to_split(b, s)); }
+};
+template <int E, class Load>
+__device__ __forceinline__ void load_run(u64 (&x)[E], const Load& ld, int base) {
+  if constexpr (has_pair<Load>::value && E >= 2) {
+#pragma unroll
+    for (int i = 0; i < E; i += 2) ld.pair(base + i, x[i], x[i + 1]);
+  } else {
+#pragma unroll
+    for (int i = 0; i < E; ++i) x[i] = ld(base + i);
+  }
+}
+template <int E, class Store>
+__device__ __forceinline__ void store_run(const u64 (&x)[E], const Store& st, int base) {
+  if constexpr (has_pair<Store>::value && E >= 2) {
+#pragma unroll
+    for (int i = 0; i < E; i += 2) st.pair(base + i, x[i], x[i + 1]);
+  } else {
+#pragma unroll
+    for (int i = 0; i < E; ++i) st(base + i, x[i]);
+  }
+}
+
 // Transforms from a row in global memory to a row in global memory through
 // the shared-memory array a[].  The first three stages run on the registers
 // of the global load and the last R stages (R = 1, 2 or 3, the rest after
@@ -277,8 +390,7 @@ __device__ __forceinline__ void ntt_fwd_fused(u64* a, const Load& ld, const Stor
     for (int i = 0; i < (1 << R); ++i) x[i] = a[nsw(base + i)];
     nttd::fwd_group<R>(x, base, LOGN, LOGN - R, q, tw);
     nttd::fwd_final<1 << R>(x, q);
-#pragma unroll
-    for (int i = 0; i < (1 << R); ++i) st(base + i, x[i]);
+    store_run<1 << R>(x, st, base);
   }
 }
 template <int LOGN, class Load, class Store>
@@ -288,8 +400,7 @@ __device__ __forceinline__ void ntt_inv_fused(u64* a, const Load& ld, const Stor
   for (int g = threadIdx.x; g < (N >> R); g += blockDim.x) {  // stages LOGN-1 .. LOGN-R
     const int base = g << R;
     u64 x[1 << R];
-#pragma unroll
-    for (int i = 0; i < (1 << R); ++i) x[i] = ld(base + i);
+    load_run<1 << R>(x, ld, base);
     nttd::inv_group<R>(x, base, LOGN, LOGN - R, q, itw);
 #pragma unroll
     for (int i = 0; i < (1 << R); ++i) a[nsw(base + i)] = x[i];
@@ -304,8 +415,7 @@ __device__ __forceinline__ void ntt_inv_fused(u64* a, const Load& ld, const Stor
     u64 x[8];
 #pragma unroll
     for (int i = 0; i < 8; ++i) x[i] = a[nsw(g + (i << S8))];
-    nttd::inv_group<3>(x, g, LOGN, 0, q, itw);
-    nttd::inv_final<8>(x, q, ninv, ninvs);
+    nttd::inv_group_last(x, g, LOGN, q, itw, ninv, ninvs);
 #pragma unroll
     for (int i = 0; i < 8; ++i) st(g + (i << S8), x[i]);
   }

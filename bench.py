@@ -641,14 +641,18 @@ def stored_traffic():
 
 
 def prof_rev():
-    """Identity of the MAC kernel source, to tell whether stored counters are current."""
+    """Identity of the MAC kernel source, to tell whether stored counters are
+    current: a hash of its code with comments and blank lines removed, so
+    that edits of comments alone keep the counters."""
     import hashlib
+    import re
 
     src = os.path.join(ROOT, "paper_2310_14565_gb300", "csrc", "kernels.cu")
     text = open(src).read()
     start = text.find("// ------------------------------------------------------- fused MAC")
     end = text.find("// ---------------------------------------------------- RNS conversions")
-    return hashlib.sha256(text[start:end].encode()).hexdigest()[:16]
+    code = [re.sub(r"//.*$", "", ln).rstrip() for ln in text[start:end].splitlines()]
+    return hashlib.sha256("\n".join(ln for ln in code if ln).encode()).hexdigest()[:16]
 
 
 def main():

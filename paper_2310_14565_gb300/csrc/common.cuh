@@ -4,8 +4,10 @@
 // definitions:
 //  - Shoup's precomputed-quotient multiplication (NTL) for a fixed operand w:
 //    w' = floor(w 2^64 / q); r = w x - umulhi(w', x) q lies in [0, 2q).
-//  - Barrett reduction (Barrett 1986) of a 128-bit value with the two-word
-//    constant floor(2^128 / q).
+//  - Barrett reduction (Barrett 1986): of a product of two values below
+//    2^bits(q) with the one-word constant floor(2^(bits+63) / q), and of a
+//    64-bit value with floor(2^64 / q); a 128-bit value as hi (2^64 mod q)
+//    (Shoup) plus lo (Barrett).
 //  - Harvey's lazy butterflies (Harvey 2014) keep NTT values in [0, 4q).
 // All primes are below 2^61, so 4q < 2^63 and every lazy sum fits in 64 bits.
 #pragma once

@@ -178,8 +178,10 @@ __global__ void __launch_bounds__(NTT_MAX_THREADS, 1) k_valgen(DevView V, const 
 // dimension are zero-filled by the copy engine, and zeros add nothing.
 // Each consumer thread owns one point and LPT layers.  Operands are in the
 // split format (x = hi 2^s + lo, both halves below 2^32): a 64-bit product
-// is four 32x32->64 multiply-adds into three 64-bit partial sums, folded
-// into the reduced accumulator before they can overflow.  Every mbarrier
+// is three 32x32->64 multiply-adds in Karatsuba form into three 64-bit
+// partial sums, folded into the reduced accumulator before they can
+// overflow.  The plaintext tile may also come as 7-byte words in three
+// planes (P7), put back together on the load.  Every mbarrier
 // wait is bounded (about one second); on expiry the block waits, again
 // bounded, for its own copies in flight, sets *err and returns.
 namespace mac {

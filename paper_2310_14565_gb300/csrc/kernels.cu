@@ -910,15 +910,21 @@ __global__ void __launch_bounds__(NTT_MAX_THREADS, 1)
 // stay below 2^127), so the sum is exact mod every prime; the integer it
 // represents is the sum of the layers' exact integer tensors (times the
 // values) as long as B holds it (sized at setup).
-__global__ void k_tensor_sum(DevView V, const u64* __restrict__ AQ, const u64* __restrict__ AB,
+constexpr int TS_PTS = 64, TS_SLICES = 4;
+__global__ void __launch_bounds__(TS_PTS * TS_SLICES) k_tensor_sum(DevView V, const u64* __restrict__ AQ, const u64* __restrict__ AB,
                              const u64* __restrict__ BQ, const u64* __restrict__ BB, const u64* __restrict__ cstQ,
                              const u64* __restrict__ side, const u64* __restrict__ VP, u64* __restrict__ X, int L,
                              int square, int init) {
+  // block: TS_PTS consecutive (prime, point) words x TS_SLICES slices of
+  // the layers; each slice sums every TS_SLICES-th layer, and the slices'
+  // residues are added at the end
+  __shared__ u64 part[3][TS_SLICES][TS_PTS];
   const int N = V.N, k = V.k, kb = V.kb, np = k + kb;
-  const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;  // over np*N
-  if (idx >= (size_t)np * N) return;
-  const int n = (int)(idx % N);
-  const int pi = (int)(idx / N);
+  const int tp = threadIdx.x % TS_PTS, slice = threadIdx.x / TS_PTS;
+  const size_t idx = (size_t)blockIdx.x * TS_PTS + tp;  // over np*N
+  const bool active = idx < (size_t)np * N;  // every thread reaches the barrier below
+  const int n = active ? (int)(idx % N) : 0;
+  const int pi = active ? (int)(idx / N) : 0;
   const DevPrime pr = V.pr[pi];
   const bool inQ = pi < k;
   const int kk = inQ ? k : kb, pp = inQ ? pi : pi - k;
@@ -927,7 +933,8 @@ __global__ void k_tensor_sum(DevView V, const u64* __restrict__ AQ, const u64* _
   const u64 cq = (inQ && cstQ) ? cstQ[pi] : 0;
   const size_t cs = (size_t)kk * N;  // component stride of the operands
   u64 s0l = 0, s0h = 0, s1l = 0, s1h = 0, s2l = 0, s2h = 0;
-  for (int l = 0; l < L; ++l) {
+  int cnt = 0;
+  for (int l = active ? slice : L; l < L; l += TS_SLICES) {
     const size_t o0 = ((size_t)l * 2 * kk + pp) * N + n;
     const u64 a0 = A[o0], a1 = A[o0 + cs];
     u64 b0 = a0, b1 = a1;
@@ -954,19 +961,28 @@ __global__ void k_tensor_sum(DevView V, const u64* __restrict__ AQ, const u64* _
       mac128(s1l, s1h, a1, b0);
       mac128(s2l, s2h, a1, b1);
     }
-    if ((l & 15) == 15) {
+    if ((++cnt & 15) == 0) {
       s0l = reduce128(s0h, s0l, pr);
       s1l = reduce128(s1h, s1l, pr);
       s2l = reduce128(s2h, s2l, pr);
       s0h = s1h = s2h = 0;
     }
   }
-  u64 d[3] = {reduce128(s0h, s0l, pr), reduce128(s1h, s1l, pr),
-              reduce128(s2h, s2l, pr)};
-  u64* o = X + (size_t)pi * N + n;
-  const size_t os = (size_t)np * N;
+  part[0][slice][tp] = reduce128(s0h, s0l, pr);
+  part[1][slice][tp] = reduce128(s1h, s1l, pr);
+  part[2][slice][tp] = reduce128(s2h, s2l, pr);
+  __syncthreads();
+  if (slice == 0 && active) {
+    u64* o = X + (size_t)pi * N + n;
+    const size_t os = (size_t)np * N;
 #pragma unroll
-  for (int c = 0; c < 3; ++c) o[c * os] = init ? d[c] : addmod(d[c], o[c * os], pr.q);
+    for (int c = 0; c < 3; ++c) {
+      u64 d = part[c][0][tp];
+#pragma unroll
+      for (int sl = 1; sl < TS_SLICES; ++sl) d = addmod(d, part[c][sl][tp], pr.q);
+      o[c * os] = init ? d : addmod(d, o[c * os], pr.q);
+    }
+  }
 }
 
 // ------------------------------------------------------ scale and round
@@ -1520,8 +1536,8 @@ void launch_tensor_sum(const DevView& V, const u64* AQ, const u64* AB, const u64
                        const u64* cstQ, const u64* side, const u64* VP, u64* X, int L, bool square, bool init,
                        cudaStream_t st) {
   const size_t total = (size_t)(V.k + V.kb) * V.N;
-  k_tensor_sum<<<grid_for(total, 128), 128, 0, st>>>(V, AQ, AB, BQ, BB, cstQ, side, VP, X, L, square ? 1 : 0,
-                                                      init ? 1 : 0);
+  k_tensor_sum<<<(unsigned)((total + TS_PTS - 1) / TS_PTS), TS_PTS * TS_SLICES, 0, st>>>(V, AQ, AB, BQ, BB, cstQ, side, VP, X, L,
+                                                                          square ? 1 : 0, init ? 1 : 0);
 }
 
 void launch_valgen(const DevView& V, const u32* vals, int L, u64* VP, cudaStream_t st) {

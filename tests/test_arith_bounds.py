@@ -20,9 +20,45 @@ import pytest
 M64 = (1 << 64) - 1
 
 
-def primes_of_sizes():
-    from sympy import nextprime, prevprime
+def is_prime(n):
+    """Miller-Rabin with the first twelve prime bases: deterministic below 3.3e24."""
+    if n < 2:
+        return False
+    bases = (2, 3, 5, 7, 11, 13, 17, 19, 23, 29, 31, 37)
+    for p in bases:
+        if n % p == 0:
+            return n == p
+    d, r = n - 1, 0
+    while d % 2 == 0:
+        d, r = d // 2, r + 1
+    for a in bases:
+        x = pow(a, d, n)
+        if x in (1, n - 1):
+            continue
+        for _ in range(r - 1):
+            x = x * x % n
+            if x == n - 1:
+                break
+        else:
+            return False
+    return True
 
+
+def prevprime(n):
+    n -= 1
+    while not is_prime(n):
+        n -= 1
+    return n
+
+
+def nextprime(n):
+    n += 1
+    while not is_prime(n):
+        n += 1
+    return n
+
+
+def primes_of_sizes():
     qs = [65537]
     for bits in list(range(20, 62)):
         qs.append(prevprime(1 << bits))
@@ -64,8 +100,6 @@ def test_reductions_short_by_their_bound(q):
 
 @pytest.mark.parametrize("bits", list(range(20, 61)))
 def test_karatsuba_sums_fit_over_a_fold(bits):
-    from sympy import prevprime
-
     q = prevprime(1 << bits)
     s = (bits + 1) // 2
     worst = max(bits + 1, 2 * s)

@@ -752,64 +752,11 @@ __global__ void k_lift(const __grid_constant__ RnsArgs A, const u64* __restrict_
 }
 
 // ------------------------------------------------------------ tensor
-__global__ void k_tensor(DevView V, const u64* __restrict__ AQ, const u64* __restrict__ AB,
-                         const u64* __restrict__ BQ, const u64* __restrict__ BB, const u64* __restrict__ cstQ,
-                         const u64* __restrict__ side, u64* __restrict__ T3, int L, int square) {
-  const int N = V.N, k = V.k, kb = V.kb, np = k + kb;
-  const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;  // over L*np*N
-  if (idx >= (size_t)L * np * N) return;
-  const int n = (int)(idx % N);
-  const int pi = (int)((idx / N) % np);
-  const size_t l = idx / ((size_t)N * np);
-  const DevPrime pr = V.pr[pi];
-  const u64* A;
-  const u64* Bp;
-  size_t o0, o1;
-  if (pi < k) {
-    A = AQ;
-    Bp = BQ;
-    o0 = ((l * 2 + 0) * k + pi) * N + n;
-    o1 = ((l * 2 + 1) * k + pi) * N + n;
-  } else {
-    A = AB;
-    Bp = BB;
-    o0 = ((l * 2 + 0) * kb + (pi - k)) * N + n;
-    o1 = ((l * 2 + 1) * kb + (pi - k)) * N + n;
-  }
-  const u64 a0 = A[o0], a1 = A[o1];
-  u64 d0, d1, d2;
-  if (square) {
-    d0 = mulmod(a0, a0, pr);
-    const u64 m = mulmod(a0, a1, pr);
-    d1 = addmod(m, m, pr.q);
-    d2 = mulmod(a1, a1, pr);
-  } else {
-    u64 b0 = Bp[o0];
-    const u64 b1 = Bp[o1];
-    if (pi < k) {
-      if (cstQ) b0 = addmod(b0, cstQ[pi], pr.q);
-    } else if (side) {
-      b0 = addmod(b0, side[l * kb + (pi - k)], pr.q);
-    }
-    d0 = mulmod(a0, b0, pr);
-    u64 lo = 0, hi = 0;
-    mac128(lo, hi, a0, b1);
-    mac128(lo, hi, a1, b0);
-    d1 = reduce128(hi, lo, pr);
-    d2 = mulmod(a1, b1, pr);
-  }
-  const size_t rs = (size_t)N;
-  u64* o = T3 + ((l * 3) * np + pi) * rs + n;
-  o[0] = d0;
-  o[(size_t)np * rs] = d1;
-  o[(size_t)2 * np * rs] = d2;
-}
-
 // Tensor product fused with its inverse transform: block per row
 // (l, c, pi) of T3[L][3][k+kb][N] computes component c of the tensor of
 // (A_l, B_l) at prime pi on the load of the inverse NTT, and stores the
-// coefficient-form row.  Same values as k_tensor followed by the inverse
-// k_ntt, without the round trip of the NTT-form tensor through memory.
+// coefficient-form row: the tensor (a0b0, a0b1 + a1b0, a1b1) and its
+// inverse NTT without a round trip of the NTT-form tensor through memory.
 __global__ void __launch_bounds__(NTT_MAX_THREADS, 1)
     k_tensor_intt(DevView V, const u64* __restrict__ AQ, const u64* __restrict__ AB, const u64* __restrict__ BQ,
                   const u64* __restrict__ BB, const u64* __restrict__ cstQ, const u64* __restrict__ side,
@@ -1515,13 +1462,6 @@ void launch_lift(const DevView& V, const u64* src, u64* dstB, int L, const u64* 
 #define LIFT(KQ, KBB) k_lift<KQ, KBB><<<grid_for(total, 128), 128, 0, st>>>(*V.host_args, src, dstB, L, cst, side)
   PEPSI_RNS_DISPATCH(V, LIFT)
 #undef LIFT
-}
-
-void launch_tensor(const DevView& V, const u64* AQ, const u64* AB, const u64* BQ, const u64* BB, const u64* cstQ,
-                   const u64* side, u64* T3, int L, bool square, cudaStream_t st) {
-  const size_t total = (size_t)L * (V.k + V.kb) * V.N;
-  if (!total) return;
-  k_tensor<<<grid_for(total, 256), 256, 0, st>>>(V, AQ, AB, BQ, BB, cstQ, side, T3, L, square ? 1 : 0);
 }
 
 void launch_tensor_intt(const DevView& V, const u64* AQ, const u64* AB, const u64* BQ, const u64* BB,

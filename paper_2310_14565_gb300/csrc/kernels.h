@@ -69,13 +69,10 @@ void launch_split(const DevView& V, u64* x, size_t groups, bool to, cudaStream_t
 // for coefficient 0 of component 0.
 void launch_lift(const DevView& V, const u64* src, u64* dstB, int L, const u64* cst, u64* side, cudaStream_t st);
 
-// Tensor product over Q u B in NTT form -> T3[L][3][k+kb][N].  square: b = a.
-// cstQ/side (may be NULL): constant added to component 0 of b (Q rows / B rows).
-void launch_tensor(const DevView& V, const u64* AQ, const u64* AB, const u64* BQ, const u64* BB, const u64* cstQ,
-                   const u64* side, u64* T3, int L, bool square, cudaStream_t st);
-
-// The same tensor followed by the inverse NTT of every row, in one kernel:
-// T3[L][3][k+kb][N] in coefficient form.
+// Tensor product over Q u B of the NTT-form ciphertexts (A, B): (a0b0,
+// a0b1+a1b0, a1b1), square: b = a; cstQ/side (may be NULL): constant added to
+// component 0 of b (Q rows / B rows).  Each row is inverse-transformed in the
+// same kernel: T3[L][3][k+kb][N] in coefficient form.
 void launch_tensor_intt(const DevView& V, const u64* AQ, const u64* AB, const u64* BQ, const u64* BB,
                         const u64* cstQ, const u64* side, u64* T3, int L, bool square, cudaStream_t st);
 

@@ -821,6 +821,40 @@ __global__ void __launch_bounds__(NTT_MAX_THREADS, 1)
   }
 }
 
+// Relinearisation fused with the affine step after it: the block of row
+// (l, c, p) of U[L][2][k][N] computes R_c = NTT(d_c) + sum_i NTT(d_i) *
+// rlk_i[c] (the digit rows DG of k_relin_ntt, 128-bit sums, one reduction)
+// and u = R_c + z * H on the load of the inverse NTT of U, stores u and the
+// coefficient-form row.  The same words as k_relin_mac followed by
+// k_axpy_intt, without R in memory.
+__global__ void __launch_bounds__(NTT_MAX_THREADS, 1)
+    k_relin_axpy_intt(DevView V, const u64* __restrict__ DG, const u64* __restrict__ rlk,
+                      const u64* __restrict__ zres, const u64* __restrict__ H, u64* __restrict__ out, u64* coef) {
+  extern __shared__ u64 sm[];
+  const int N = V.N, k = V.k;
+  const size_t r = blockIdx.x;
+  const int p = (int)(r % k);
+  const int c = (int)((r / k) % 2);
+  const size_t l = r / ((size_t)2 * k);
+  const DevPrime pr = V.pr[p];
+  const u64 z = zres[p];
+  const size_t gs = (size_t)k * N;  // digit row stride
+  const u64* g = DG + l * (k + 2) * gs + (size_t)p * N;
+  const u64* key = rlk + ((size_t)c * k + p) * N;  // rlk_i[c] at prime p: key + i * 2 * gs
+  const u64* hr = H + r * N;
+  u64* ur = out + r * N;
+  ntt_inv_gg(
+      sm,
+      [&](int x) {
+        u64 lo = g[(size_t)(k + c) * gs + x], hi = 0;
+        for (int i = 0; i < k; ++i) mac128(lo, hi, g[(size_t)i * gs + x], __ldg(key + (size_t)i * 2 * gs + x));
+        const u64 u = addmod(reduce128(hi, lo, pr), mulmod(z, hr[x], pr), pr.q);
+        ur[x] = u;
+        return u;
+      },
+      RowSt(coef + r * N), V, p);
+}
+
 // out = a + z * b (NTT form, rows [groups][k][N], z as k residues), fused
 // with the inverse NTT of out into coef: the block of a row computes the
 // row on the transform's load and also stores it (each element is loaded
@@ -1529,6 +1563,19 @@ void launch_relin(const DevView& V, const u64* D, const u64* rlk, u64* DG, u64* 
   k_relin_mac<<<grid_for((size_t)L * V.k * V.N, 256), 256, 0, st>>>(V, DG, rlk, R, L);
 }
 
+void launch_relin_digits(const DevView& V, const u64* D, u64* DG, int L, cudaStream_t st) {
+  if (L <= 0) return;
+  const size_t rows = (size_t)L * (V.k + 2) * V.k;
+  k_relin_ntt<<<(unsigned)rows, ntt_threads(V.N), (size_t)V.N * 8, st>>>(V, D, DG);
+}
+
+void launch_relin_axpy_intt(const DevView& V, const u64* DG, const u64* rlk, const u64* zres, const u64* H, u64* out,
+                            u64* coef, int L, cudaStream_t st) {
+  const size_t rows = (size_t)L * 2 * V.k;
+  if (!rows) return;
+  k_relin_axpy_intt<<<(unsigned)rows, ntt_threads(V.N), (size_t)V.N * 8, st>>>(V, DG, rlk, zres, H, out, coef);
+}
+
 void launch_axpy_intt(const DevView& V, const u64* a, const u64* zres, const u64* b, u64* out, u64* coef,
                       size_t groups, cudaStream_t st) {
   const size_t rows = groups * V.k;
@@ -1625,6 +1672,7 @@ cudaError_t kernels_init(int N) {
   set((const void*)k_relin_ntt);
   set((const void*)k_tensor_intt);
   set((const void*)k_axpy_intt);
+  set((const void*)k_relin_axpy_intt);
   set((const void*)k_encrypt);
   set((const void*)k_keygen_sntt);
   set((const void*)k_keygen_rlk);

@@ -106,6 +106,13 @@ void launch_scale_round(const DevView& V, const u64* T3, u64* D, int L, cudaStre
 // -> R[L][2][k][N] NTT form.  DG: scratch [L][k+2][k][N].
 void launch_relin(const DevView& V, const u64* D, const u64* rlk, u64* DG, u64* R, int L, cudaStream_t st);
 
+// The digit transforms of launch_relin alone (DG[L][k+2][k][N]), and the key
+// MAC fused with the affine step after it: out = R + z * H (rows [L][2][k][N],
+// NTT form), stored, and its inverse NTT into coef, R never written.
+void launch_relin_digits(const DevView& V, const u64* D, u64* DG, int L, cudaStream_t st);
+void launch_relin_axpy_intt(const DevView& V, const u64* DG, const u64* rlk, const u64* zres, const u64* H, u64* out,
+                            u64* coef, int L, cudaStream_t st);
+
 // out = a + z * b over `groups` groups of k rows (z as k residues); out may alias a.
 void launch_axpy(const DevView& V, const u64* a, const u64* zres, const u64* b, u64* out, size_t groups,
                  cudaStream_t st);

@@ -250,6 +250,12 @@ void extend(pepsi_ctx* c, const u64* src_ntt, u64* coef, u64* Bpart, int L, cons
   ntt(c, true, Bpart, Bpart, (size_t)L * 2, c->kb, c->k, kbN, kbN, st);
 }
 
+// relin(D) + z * H -> out, then extend(out): the key-switching sum and the
+// affine step on the load of the inverse NTT (the relinearised product
+// itself is not stored).
+void relin_axpy_extend(pepsi_ctx* c, const u64* D, const u64* z, const u64* H, u64* out, u64* coef, u64* Bpart,
+                       int L, const u64* cstv, u64* side, cudaStream_t st);
+
 // out = a + z * b, then extend(out) as above, the axpy on the load of the
 // inverse NTT (coef may alias b).
 void axpy_extend(pepsi_ctx* c, const u64* a, const u64* z, const u64* b, u64* out, u64* coef, u64* Bpart, int L,
@@ -286,6 +292,25 @@ void relin(pepsi_ctx* c, const u64* D, u64* R, int L, cudaStream_t st) {
   Prof p(c, PC_RELIN, st, 2);
   launch_relin(c->V, D, c->d_rlk, DG, R, L, st);
 }
+
+void relin_axpy_extend(pepsi_ctx* c, const u64* D, const u64* z, const u64* H, u64* out, u64* coef, u64* Bpart,
+                       int L, const u64* cstv, u64* side, cudaStream_t st) {
+  const size_t kbN = (size_t)c->kb * c->N;
+  cudaError_t e = cudaSuccess;
+  u64* DG = (u64*)scratch(c, kScratchDG, (size_t)L * (c->k + 2) * c->k * c->N * 8, &e);
+  if (!DG) return;  // the allocation error resurfaces through cudaGetLastError
+  {
+    Prof p(c, PC_RELIN, st, 2);
+    launch_relin_digits(c->V, D, DG, L, st);
+    launch_relin_axpy_intt(c->V, DG, c->d_rlk, z, H, out, coef, L, st);
+  }
+  {
+    Prof p(c, PC_LIFT, st);
+    launch_lift(c->V, coef, Bpart, L, cstv, side, st);
+  }
+  ntt(c, true, Bpart, Bpart, (size_t)L * 2, c->kb, c->k, kbN, kbN, st);
+}
+
 
 void axpy(pepsi_ctx* c, const u64* a, const u64* z, const u64* b, u64* out, size_t groups, cudaStream_t st) {
   Prof p(c, PC_POINTWISE, st);
@@ -382,16 +407,14 @@ LastMult eq_circuit_front(pepsi_ctx* c, EvalBufs& b, int L, cudaStream_t st) {
     case 4: {  // u = R(h'^2) - 3h';  E = Mult(u, u + 2)
       extend(c, b.H, b.Hc, b.XB, L, nullptr, nullptr, st);
       mult_tail(c, b.H, b.XB, b.H, b.XB, nullptr, nullptr, true, b.T3, b.D, L, st);
-      relin(c, b.D, b.R, L, st);
-      axpy_extend(c, b.R, cst(c, CS_M3), b.H, b.U, b.X, b.YB, L, cst(c, CS_D_2), b.side, st);
+      relin_axpy_extend(c, b.D, cst(c, CS_M3), b.H, b.U, b.X, b.YB, L, cst(c, CS_D_2), b.side, st);
       last(b.U, b.YB, b.U, b.YB, cst(c, CS_D_2), b.side, false);
       break;
     }
     case 8: {  // u = R(h'^2) - 7h'; w = R(u^2); E = Mult(w + 12u, w + 16u + 60)
       extend(c, b.H, b.Hc, b.XB, L, nullptr, nullptr, st);
       mult_tail(c, b.H, b.XB, b.H, b.XB, nullptr, nullptr, true, b.T3, b.D, L, st);
-      relin(c, b.D, b.R, L, st);
-      axpy_extend(c, b.R, cst(c, CS_M7), b.H, b.U, b.X, b.XB, L, nullptr, nullptr, st);
+      relin_axpy_extend(c, b.D, cst(c, CS_M7), b.H, b.U, b.X, b.XB, L, nullptr, nullptr, st);
       mult_tail(c, b.U, b.XB, b.U, b.XB, nullptr, nullptr, true, b.T3, b.D, L, st);
       relin(c, b.D, b.W, L, st);
       axpy_extend(c, b.W, cst(c, CS_P12), b.U, b.X, b.R, b.XB, L, nullptr, nullptr, st);

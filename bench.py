@@ -103,6 +103,20 @@ def dist_env():
     return ws, rank, local
 
 
+def max_over_ranks(x):
+    """The largest x over the ranks of the process group (x itself without
+    one): the replicas' step time is that of the slowest."""
+    import torch
+    import torch.distributed as dist
+
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(x)], device=dev, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 # ------------------------------------------------------------------ oracle
 def oracle_setup():
     import oracle
@@ -261,10 +275,7 @@ def run_ours(args):
     ms = e0.elapsed_time(e1) / args.steps
     prof_counts = ctx.profile_read()
     launches = sum(v[0] for v in prof_counts.values())
-    if ws > 1:
-        t = torch.tensor([ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms)
 
     # per-kernel CUDA-event timing pass (same workload, events on the launching stream)
     ctx.profile(True)

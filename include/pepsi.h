@@ -217,7 +217,10 @@ int pepsi_query(pepsi_ctx* ctx, const uint64_t* items, size_t m, uint64_t enc_se
  * out_ct: [B][2][r][N] coefficient form, host or device, with B blocks and
  * r = pepsi_info.response_primes (k unless the response is switched);
  * block j of the response answers request block j, its mask drawn from
- * mask_seed + j.
+ * mask_seed + j.  A host request is uploaded in two pieces of its code bits
+ * (the first short), the copy of the second overlapping the first piece's
+ * transform and multiply-accumulate; the words do not depend on it.  Device
+ * buffers need 8-byte alignment (16-byte aligned rows take wider accesses).
  * Errors: PEPSI_E_PARAM (bad set/mode), PEPSI_E_NOMEM, PEPSI_E_CUDA. */
 int pepsi_eval(pepsi_ctx* ctx, int set_id, const uint64_t* cts, int mode, uint64_t mask_seed, uint64_t* out_ct,
                void* stream);

@@ -163,6 +163,31 @@ int pepsi_get_info(const pepsi_ctx* ctx, pepsi_info* info);
  * stays exact.  Errors: PEPSI_E_PARAM for a null context. */
 int pepsi_set_rescale_group(pepsi_ctx* ctx, uint32_t rescale_group);
 
+/* Evaluation schedule of a context (no counterpart in the paper): how an
+ * evaluation is split into launches, never what it computes.  Every field
+ * leaves the result words unchanged. */
+typedef struct {
+  uint32_t chunk;       /* layers per circuit chunk, 1..4096 (default 64, or the
+                           PEPSI_CHUNK environment variable at setup).  Larger chunks
+                           fill the GPU with more blocks per launch and need more
+                           scratch (about 4.7 MB per layer at N = 8192, k = 4) */
+  uint32_t ntt_threads; /* threads per block of the ciphertext transforms (the NTTs and
+                           the kernels fused with them): 0 = the default for N (N / 8,
+                           at most 512; 1024 at N = 16384), else a power of two in
+                           64..1024 */
+  uint32_t relin_fused; /* 1 (default): where a relinearised product only feeds the
+                           affine step after it (u = R(h'^2) - 3h' and the like), the
+                           key-switching sum runs on the load of the inverse NTT that
+                           extends u, and the relinearised product is never stored;
+                           0: it is stored, then the affine step runs */
+} pepsi_schedule;
+
+/* Read or set the schedule of later evaluations on this context
+ * (pepsi_autotune sets it too).  Errors: PEPSI_E_PARAM for a null pointer
+ * or a field out of range. */
+int pepsi_get_schedule(const pepsi_ctx* ctx, pepsi_schedule* out);
+int pepsi_set_schedule(pepsi_ctx* ctx, const pepsi_schedule* schedule);
+
 /* Server preprocessing, offline (Section 4.1 and App. Alg 7, server side):
  * H_0 to lambda bits, permutation-based hashing into each of the three
  * bins of every item, de-duplication of equal x_L inside a bin, stable
@@ -307,14 +332,18 @@ int pepsi_relin(pepsi_ctx* ctx, const uint64_t* in, size_t n, uint64_t* out, voi
  * array of PEPSI_NOALLOC_SCRATCH_BYTES (16 MiB) that every GPU loading the
  * library holds until the process exits.
  * in: [n][3][k][N], out: [n][2][k][N], coefficient form, device memory.
- * The first call on a device looks up the array's device address (once per
- * device, with that device current); make that first call before any
- * stream capture.  All calls share the one array and it keeps the last
- * call's contents, so calls that overlap on the GPU (other streams, other
- * threads, other contexts) race: serialise them.  Errors: PEPSI_E_PARAM
- * when n ciphertexts need more than the array holds,
- * n * ((k+2) + 2) * k * N * 8 bytes (pepsi_last_error gives the sizes), or
- * when a buffer is not device memory; PEPSI_E_CUDA. */
+ * The device the context was set up on must be the current device (its
+ * launches go to the current device; another current device gives
+ * PEPSI_E_PARAM).  The first call on a device looks up the array's device
+ * address (once per device, with that device current); make that first
+ * call before any stream capture.  All calls share the one array and it
+ * keeps the last call's contents, so calls that overlap on the GPU (other
+ * streams, other threads, other contexts) race: serialise them.  Errors:
+ * PEPSI_E_PARAM when n ciphertexts need more than the array holds
+ * (((k+2) + 2) * k * N * 8 bytes each, so n at most
+ * PEPSI_NOALLOC_SCRATCH_BYTES / that; pepsi_last_error gives the sizes),
+ * when a buffer is not device memory, or when another device is current;
+ * PEPSI_E_CUDA. */
 int pepsi_relin_noalloc(pepsi_ctx* ctx, const uint64_t* in, size_t n, uint64_t* out, void* stream);
 
 /* Test access to the keys: s (int8[N], host) and the relinearisation keys

@@ -56,6 +56,10 @@ class Info(C.Structure):
     ]
 
 
+class Schedule(C.Structure):
+    _fields_ = [("chunk", C.c_uint32), ("ntt_threads", C.c_uint32), ("relin_fused", C.c_uint32)]
+
+
 RESCALE_ALL = 0xFFFFFFFF
 
 SYMBOLS = {
@@ -63,6 +67,8 @@ SYMBOLS = {
     "pepsi_setup": (C.c_int, [C.POINTER(Params), C.c_uint64, C.POINTER(C.c_void_p)]),
     "pepsi_get_info": (C.c_int, [C.c_void_p, C.POINTER(Info)]),
     "pepsi_set_rescale_group": (C.c_int, [C.c_void_p, C.c_uint32]),
+    "pepsi_get_schedule": (C.c_int, [C.c_void_p, C.POINTER(Schedule)]),
+    "pepsi_set_schedule": (C.c_int, [C.c_void_p, C.POINTER(Schedule)]),
     "pepsi_autotune": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.POINTER(C.c_uint32)]),
     "pepsi_wait_probe": (C.c_int, [C.c_void_p, C.c_int]),
     "pepsi_request_bits": (C.c_int, [C.c_uint32, C.c_uint32, C.c_uint64, C.POINTER(C.c_double),
@@ -247,6 +253,22 @@ class Context:
         """Rounding run length of later evaluations (1: per layer;
         RESCALE_ALL: one rounding per evaluation), cut at rescale_cap."""
         _check(lib().pepsi_set_rescale_group(self._h, int(group)), "pepsi_set_rescale_group")
+
+    def schedule(self):
+        """The evaluation schedule: {chunk, ntt_threads, relin_fused}."""
+        sc = Schedule()
+        _check(lib().pepsi_get_schedule(self._h, C.byref(sc)), "pepsi_get_schedule")
+        return {"chunk": int(sc.chunk), "ntt_threads": int(sc.ntt_threads), "relin_fused": int(sc.relin_fused)}
+
+    def set_schedule(self, chunk=None, ntt_threads=None, relin_fused=None):
+        """Change fields of the evaluation schedule (None keeps a field);
+        the result words never depend on it."""
+        cur = self.schedule()
+        sc = Schedule()
+        sc.chunk = cur["chunk"] if chunk is None else int(chunk)
+        sc.ntt_threads = cur["ntt_threads"] if ntt_threads is None else int(ntt_threads)
+        sc.relin_fused = cur["relin_fused"] if relin_fused is None else int(relin_fused)
+        _check(lib().pepsi_set_schedule(self._h, C.byref(sc)), "pepsi_set_schedule")
 
     # ---- server side
     def server_load(self, items):

@@ -80,6 +80,7 @@ struct DevView {
   const ulonglong2* itwp;    // [np][N] (psi^-brev(i), its Shoup companion); entry 0: psi^-brev(1) N^-1
   const RnsConst* rc;
   const RnsArgs* host_args;  // host copy for by-value launches (not dereferenced on the device)
+  int nt;                    // threads per block of the ciphertext transforms (0: the default for N)
 };
 
 // ---------------------------------------------------------------- arithmetic

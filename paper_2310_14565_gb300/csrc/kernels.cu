@@ -25,6 +25,9 @@ inline int ntt_threads(int N) {
   if (t < 32) t = 32;
   return t;
 }
+// Threads of the hot-path transform kernels: the schedule's choice
+// (DevView::nt, picked by the autotuner), else the default above.
+inline int xform_threads(const DevView& V) { return V.nt > 0 ? V.nt : ntt_threads(V.N); }
 
 // ------------------------------------------------------------------ NTT
 // SPLIT: store the result in the split operand format of the
@@ -1333,11 +1336,11 @@ void launch_ntt(const DevView& V, bool fwd, const u64* src, u64* dst, size_t out
   if (!rows) return;
   const size_t smem = (size_t)V.N * sizeof(u64);
   if (fwd && split_out)
-    k_ntt<true, true><<<(unsigned)rows, ntt_threads(V.N), smem, st>>>(V, src, dst, np, p0, src_os, dst_os);
+    k_ntt<true, true><<<(unsigned)rows, xform_threads(V), smem, st>>>(V, src, dst, np, p0, src_os, dst_os);
   else if (fwd)
-    k_ntt<true><<<(unsigned)rows, ntt_threads(V.N), smem, st>>>(V, src, dst, np, p0, src_os, dst_os);
+    k_ntt<true><<<(unsigned)rows, xform_threads(V), smem, st>>>(V, src, dst, np, p0, src_os, dst_os);
   else
-    k_ntt<false><<<(unsigned)rows, ntt_threads(V.N), smem, st>>>(V, src, dst, np, p0, src_os, dst_os);
+    k_ntt<false><<<(unsigned)rows, xform_threads(V), smem, st>>>(V, src, dst, np, p0, src_os, dst_os);
 }
 
 void launch_cw_unrank(const u64* T, size_t count, const u64* binom, int ell, int h, uint16_t* pos, cudaStream_t st) {
@@ -1502,7 +1505,7 @@ void launch_tensor_intt(const DevView& V, const u64* AQ, const u64* AB, const u6
                         const u64* cstQ, const u64* side, u64* T3, int L, bool square, cudaStream_t st) {
   const size_t rows = (size_t)L * 3 * (V.k + V.kb);
   if (!rows) return;
-  k_tensor_intt<<<(unsigned)rows, ntt_threads(V.N), (size_t)V.N * 8, st>>>(V, AQ, AB, BQ, BB, cstQ, side, T3,
+  k_tensor_intt<<<(unsigned)rows, xform_threads(V), (size_t)V.N * 8, st>>>(V, AQ, AB, BQ, BB, cstQ, side, T3,
                                                                           square ? 1 : 0);
 }
 
@@ -1559,28 +1562,28 @@ void launch_scale_round(const DevView& V, const u64* T3, u64* D, int L, cudaStre
 void launch_relin(const DevView& V, const u64* D, const u64* rlk, u64* DG, u64* R, int L, cudaStream_t st) {
   if (L <= 0) return;
   const size_t rows = (size_t)L * (V.k + 2) * V.k;
-  k_relin_ntt<<<(unsigned)rows, ntt_threads(V.N), (size_t)V.N * 8, st>>>(V, D, DG);
+  k_relin_ntt<<<(unsigned)rows, xform_threads(V), (size_t)V.N * 8, st>>>(V, D, DG);
   k_relin_mac<<<grid_for((size_t)L * V.k * V.N, 256), 256, 0, st>>>(V, DG, rlk, R, L);
 }
 
 void launch_relin_digits(const DevView& V, const u64* D, u64* DG, int L, cudaStream_t st) {
   if (L <= 0) return;
   const size_t rows = (size_t)L * (V.k + 2) * V.k;
-  k_relin_ntt<<<(unsigned)rows, ntt_threads(V.N), (size_t)V.N * 8, st>>>(V, D, DG);
+  k_relin_ntt<<<(unsigned)rows, xform_threads(V), (size_t)V.N * 8, st>>>(V, D, DG);
 }
 
 void launch_relin_axpy_intt(const DevView& V, const u64* DG, const u64* rlk, const u64* zres, const u64* H, u64* out,
                             u64* coef, int L, cudaStream_t st) {
   const size_t rows = (size_t)L * 2 * V.k;
   if (!rows) return;
-  k_relin_axpy_intt<<<(unsigned)rows, ntt_threads(V.N), (size_t)V.N * 8, st>>>(V, DG, rlk, zres, H, out, coef);
+  k_relin_axpy_intt<<<(unsigned)rows, xform_threads(V), (size_t)V.N * 8, st>>>(V, DG, rlk, zres, H, out, coef);
 }
 
 void launch_axpy_intt(const DevView& V, const u64* a, const u64* zres, const u64* b, u64* out, u64* coef,
                       size_t groups, cudaStream_t st) {
   const size_t rows = groups * V.k;
   if (!rows) return;
-  k_axpy_intt<<<(unsigned)rows, ntt_threads(V.N), (size_t)V.N * 8, st>>>(V, a, zres, b, out, coef);
+  k_axpy_intt<<<(unsigned)rows, xform_threads(V), (size_t)V.N * 8, st>>>(V, a, zres, b, out, coef);
 }
 
 void launch_axpy(const DevView& V, const u64* a, const u64* zres, const u64* b, u64* out, size_t groups,

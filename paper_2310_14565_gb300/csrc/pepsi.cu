@@ -72,6 +72,7 @@ struct SetGroup {
 
 struct pepsi_ctx {
   pepsi_params prm{};
+  int device = 0;  // the CUDA device current at setup: every launch of the context goes there
   int N = 0, logN = 0, k = 0, kb = 0, ell = 0, h = 0;
   u64 t = 0;
   std::vector<u64> Q, B, psi;
@@ -106,6 +107,7 @@ struct pepsi_ctx {
   // scratch, grown on demand
   std::vector<DevBuf> scratch;
   int chunk = 64;  // layers per circuit chunk (pepsi_autotune may change it)
+  bool relin_fused = true;  // key-switching sum on the load of the affine step's inverse NTT
   u32 rescale_cap = 1;      // most layers one rounding of the last products may cover
   bool value_margin = false;  // B also holds the value products under lazy rescaling
   int resp = 0;               // primes of the evaluation's response (k: no switching)
@@ -254,7 +256,7 @@ void extend(pepsi_ctx* c, const u64* src_ntt, u64* coef, u64* Bpart, int L, cons
 // affine step on the load of the inverse NTT (the relinearised product
 // itself is not stored).
 void relin_axpy_extend(pepsi_ctx* c, const u64* D, const u64* z, const u64* H, u64* out, u64* coef, u64* Bpart,
-                       int L, const u64* cstv, u64* side, cudaStream_t st);
+                       int L, const u64* cstv, u64* side, u64* Rtmp, cudaStream_t st);
 
 // out = a + z * b, then extend(out) as above, the axpy on the load of the
 // inverse NTT (coef may alias b).
@@ -294,7 +296,12 @@ void relin(pepsi_ctx* c, const u64* D, u64* R, int L, cudaStream_t st) {
 }
 
 void relin_axpy_extend(pepsi_ctx* c, const u64* D, const u64* z, const u64* H, u64* out, u64* coef, u64* Bpart,
-                       int L, const u64* cstv, u64* side, cudaStream_t st) {
+                       int L, const u64* cstv, u64* side, u64* Rtmp, cudaStream_t st) {
+  if (!c->relin_fused) {  // the schedule's unfused form: R stored in Rtmp, then the affine step
+    relin(c, D, Rtmp, L, st);
+    axpy_extend(c, Rtmp, z, H, out, coef, Bpart, L, cstv, side, st);
+    return;
+  }
   const size_t kbN = (size_t)c->kb * c->N;
   cudaError_t e = cudaSuccess;
   u64* DG = (u64*)scratch(c, kScratchDG, (size_t)L * (c->k + 2) * c->k * c->N * 8, &e);
@@ -407,14 +414,14 @@ LastMult eq_circuit_front(pepsi_ctx* c, EvalBufs& b, int L, cudaStream_t st) {
     case 4: {  // u = R(h'^2) - 3h';  E = Mult(u, u + 2)
       extend(c, b.H, b.Hc, b.XB, L, nullptr, nullptr, st);
       mult_tail(c, b.H, b.XB, b.H, b.XB, nullptr, nullptr, true, b.T3, b.D, L, st);
-      relin_axpy_extend(c, b.D, cst(c, CS_M3), b.H, b.U, b.X, b.YB, L, cst(c, CS_D_2), b.side, st);
+      relin_axpy_extend(c, b.D, cst(c, CS_M3), b.H, b.U, b.X, b.YB, L, cst(c, CS_D_2), b.side, b.R, st);
       last(b.U, b.YB, b.U, b.YB, cst(c, CS_D_2), b.side, false);
       break;
     }
     case 8: {  // u = R(h'^2) - 7h'; w = R(u^2); E = Mult(w + 12u, w + 16u + 60)
       extend(c, b.H, b.Hc, b.XB, L, nullptr, nullptr, st);
       mult_tail(c, b.H, b.XB, b.H, b.XB, nullptr, nullptr, true, b.T3, b.D, L, st);
-      relin_axpy_extend(c, b.D, cst(c, CS_M7), b.H, b.U, b.X, b.XB, L, nullptr, nullptr, st);
+      relin_axpy_extend(c, b.D, cst(c, CS_M7), b.H, b.U, b.X, b.XB, L, nullptr, nullptr, b.R, st);
       mult_tail(c, b.U, b.XB, b.U, b.XB, nullptr, nullptr, true, b.T3, b.D, L, st);
       relin(c, b.D, b.W, L, st);
       axpy_extend(c, b.W, cst(c, CS_P12), b.U, b.X, b.R, b.XB, L, nullptr, nullptr, st);
@@ -919,13 +926,20 @@ constexpr int kMaxDevices = 64;
 std::mutex g_noalloc_mu;
 u64* g_noalloc_addr[kMaxDevices] = {};
 
-// Device address of the array on the current device.  In host code the
+// Device address of the array on the context's device.  In host code the
 // array's name only stands for it; cudaGetSymbolAddress gives the address
-// that kernels may use.  Looked up once per device, with that device current.
-int noalloc_scratch(u64** out) {
+// that kernels may use.  Looked up once per device, with that device
+// current: the context's device must be the current one (every launch of
+// the call goes to the current device), else PEPSI_E_PARAM.
+int noalloc_scratch(const pepsi_ctx* c, u64** out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return cuda_status(e);
+  if (dev != c->device) {
+    g_last_error = "pepsi_relin_noalloc: the context was set up on device " + std::to_string(c->device) +
+                   " but device " + std::to_string(dev) + " is current";
+    return PEPSI_E_PARAM;
+  }
   if (dev < 0 || dev >= kMaxDevices) return PEPSI_E_PARAM;
   std::lock_guard<std::mutex> lock(g_noalloc_mu);
   if (!g_noalloc_addr[dev]) {
@@ -1139,7 +1153,8 @@ int pepsi_setup(const pepsi_params* params, uint64_t key_seed, pepsi_ctx** out) 
   hostmath::delta(c->Q, c->t, 60, &consts[(size_t)CS_D_60 * c->k]);
 
   // a blocking stream: ordered with the legacy default stream that most callers use
-  cudaError_t e = cudaStreamCreate(&c->stream);
+  cudaError_t e = cudaGetDevice(&c->device);
+  if (e == cudaSuccess) e = cudaStreamCreate(&c->stream);
   if (e == cudaSuccess) e = kernels_init(c->N);
   if (e == cudaSuccess) e = upload((void**)&c->d_pr, pr.data(), pr.size() * sizeof(DevPrime));
   {  // (twiddle, Shoup companion) pairs: one 16-byte load per butterfly group
@@ -1257,6 +1272,24 @@ int pepsi_comm_optimal_h(uint32_t lambda_bar, uint64_t bins, uint32_t h_max, uin
 int pepsi_set_rescale_group(pepsi_ctx* c, uint32_t rescale_group) {
   if (!c) return PEPSI_E_PARAM;
   c->prm.rescale_group = rescale_group;
+  return PEPSI_OK;
+}
+
+int pepsi_get_schedule(const pepsi_ctx* c, pepsi_schedule* out) {
+  if (!c || !out) return PEPSI_E_PARAM;
+  out->chunk = (uint32_t)c->chunk;
+  out->ntt_threads = (uint32_t)c->V.nt;
+  out->relin_fused = c->relin_fused ? 1u : 0u;
+  return PEPSI_OK;
+}
+
+int pepsi_set_schedule(pepsi_ctx* c, const pepsi_schedule* s) {
+  if (!c || !s || s->chunk < 1 || s->chunk > 4096 || s->relin_fused > 1) return PEPSI_E_PARAM;
+  const u32 nt = s->ntt_threads;
+  if (nt && (nt < 64 || nt > 1024 || (nt & (nt - 1)))) return PEPSI_E_PARAM;
+  c->chunk = (int)s->chunk;
+  c->V.nt = (int)nt;
+  c->relin_fused = s->relin_fused != 0;
   return PEPSI_OK;
 }
 
@@ -1739,17 +1772,22 @@ int pepsi_relin_noalloc(pepsi_ctx* c, const uint64_t* in, size_t n, uint64_t* ou
   if (!c || !in || !out) return PEPSI_E_PARAM;
   if (!n) return PEPSI_OK;
   const size_t kN = (size_t)c->k * c->N;
-  const size_t dg_words = n * (size_t)(c->k + 2) * kN, r_words = n * 2 * kN;
-  const size_t need = (dg_words + r_words) * sizeof(u64);
-  if (need > PEPSI_NOALLOC_SCRATCH_BYTES) {
-    g_last_error = "pepsi_relin_noalloc: " + std::to_string(n) + " ciphertexts need " + std::to_string(need) +
-                   " bytes of scratch, the fixed array holds " + std::to_string((size_t)PEPSI_NOALLOC_SCRATCH_BYTES);
+  // bytes per ciphertext: (k+2) digit rows and 2 result rows of k*N words;
+  // n is checked against the array before any product that could wrap
+  const size_t per_ct = (size_t)(c->k + 2 + 2) * kN * sizeof(u64);
+  const size_t max_n = (size_t)PEPSI_NOALLOC_SCRATCH_BYTES / per_ct;
+  if (n > max_n) {
+    g_last_error = "pepsi_relin_noalloc: " + std::to_string(n) + " ciphertexts need " + std::to_string(per_ct) +
+                   " bytes of scratch each, the fixed array holds " +
+                   std::to_string((size_t)PEPSI_NOALLOC_SCRATCH_BYTES) + " bytes (at most " + std::to_string(max_n) +
+                   " ciphertexts)";
     return PEPSI_E_PARAM;
   }
   if (!is_device_ptr(in) || !is_device_ptr(out)) return PEPSI_E_PARAM;
   u64* base = nullptr;
-  int rc = noalloc_scratch(&base);
+  int rc = noalloc_scratch(c, &base);
   if (rc) return rc;
+  const size_t dg_words = n * (size_t)(c->k + 2) * kN;
   u64* DG = base;
   u64* R = base + dg_words;
   cudaStream_t st = pick(c, stream);

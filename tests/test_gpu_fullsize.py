@@ -1,13 +1,14 @@
 """Parity at the paper-shaped size, in the configuration bench.py times:
 N = 8192, four 54/55-bit primes, t = 65537, h = 4, ell = 600, mu = 526,
 1024 client items against 2^20 server items (102 planted), resident
-server plaintexts, one rounding of the layers' last products per
-evaluation and a one-prime response.  The oracle checks sampled outputs one
-by one (the server table, the request words, sampled plaintexts, the h'
-and E words of sampled layers, the response switch of a full ciphertext);
-the final result is checked by properties that hold at any size (decrypts
-to the brute-force intersection with positive budget, the same as with
-per-layer rounding)."""
+server plaintexts, circuit chunks of 256 layers, one rounding of the
+layers' last products per evaluation and a one-prime response.  The oracle
+checks sampled outputs one by one (the server table, the request words,
+sampled plaintexts, the h' and E words of sampled layers) and the whole
+response of every mode word for word (about 80 s of oracle time each on
+16 host cores); the result is also checked by properties that hold at any
+size (decrypts to the brute-force intersection with positive budget, the
+same as with per-layer rounding)."""
 import numpy as np
 import pytest
 
@@ -27,11 +28,32 @@ def paper_case():
     oc, gc, s, rlk = pair(8192, PAPER, 4, 32, mu=526, ell=600, rescale_group=ALL, server_values=1,
                           response_primes=1)
     sets = make_sets(1024, 1 << 20, 102, bits=64)
+    gc.set_schedule(chunk=256)  # the chunk the autotuner picks at this size
     sid = gc.server_load(sets.server)
     rc, Ts, _ = oc.server_table(sets.server)
     assert rc == 0
     cts, where = gc.query(sets.client, 4)
     return oc, gc, s, rlk, sets, sid, Ts, cts, where
+
+
+def _oracle_timed(oc, rlk, cts, Ts, mode=0, mask_seed=0, V=None):
+    """The oracle's response in the timed configuration: one rounding of
+    the last products of all 526 layers, switched to the first prime."""
+    return oc.mod_switch(oc.eval(rlk, cts, Ts, mode=mode, mask_seed=mask_seed, group=526, V=V), 1)
+
+
+@pytest.mark.parametrize("mode,mask_seed", [(0, 0), (1, 5)])
+def test_paper_timed_configuration_words(paper_case, mode, mask_seed):
+    """The whole response of the configuration bench.py times, word for word:
+    256-layer chunks, so each k_tensor_sum launch sums 256 layers (64 per
+    thread slice, through its periodic 128-bit reductions), lazy rescaling
+    over all layers, a one-prime response; indicator and cardinality."""
+    oc, gc, s, rlk, sets, sid, Ts, cts, where = paper_case
+    assert gc.schedule()["chunk"] == 256
+    got = gc.eval(sid, cts, mode=mode, mask_seed=mask_seed)
+    want = _oracle_timed(oc, rlk, cts, Ts, mode, mask_seed)
+    assert got.shape == want.shape == (2, 1, 8192)
+    assert np.array_equal(got, want)
 
 
 def test_paper_table_request_and_plaintexts(paper_case):
@@ -92,10 +114,18 @@ def test_paper_labels_and_sum(paper_case):
     for u, x in enumerate(sets.client.tolist()):
         if x in val_of:
             want[where[u]] = val_of[x]
-    slots, budget = gc.decrypt(gc.eval(vid, cts, mode=2))
+    labels = gc.eval(vid, cts, mode=2)
+    slots, budget = gc.decrypt(labels)
     assert budget > 0 and np.array_equal(slots, want)
-    ss, budget = gc.decrypt(gc.eval(vid, cts, mode=3, mask_seed=9))
+    total = gc.eval(vid, cts, mode=3, mask_seed=9)
+    ss, budget = gc.decrypt(total)
     assert budget > 0 and int(ss.astype(np.int64).sum()) % 65537 == int(want.astype(np.int64).sum()) % 65537
+    # both responses word for word against the oracle, in the timed configuration
+    rc, Tv, V, _ = oc.server_table_values(sets.server, values)
+    assert rc == 0 and np.array_equal(Tv, Ts)
+    assert np.array_equal(gc.server_values(vid, 526), V)
+    assert np.array_equal(labels, _oracle_timed(oc, rlk, cts, Ts, 2, 0, V))
+    assert np.array_equal(total, _oracle_timed(oc, rlk, cts, Ts, 3, 9, V))
 
 
 LARGE = [55] * 6 + [54] * 2

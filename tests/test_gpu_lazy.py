@@ -24,7 +24,7 @@ def _cuda():
     torch_cuda()
 
 
-def _case(N, bits, h, lb, group, chunk=4, resident_bytes=0, m=20, n=70, planted=4, seed=5, mu_min=7):
+def _case(N, bits, h, lb, group, chunk=4, resident_bytes=0, m=20, n=70, planted=4, seed=5, mu_min=7, **ctx_kw):
     import oracle
     from paper_2310_14565_gb300.workload import make_sets
 
@@ -33,7 +33,7 @@ def _case(N, bits, h, lb, group, chunk=4, resident_bytes=0, m=20, n=70, planted=
     mu = max(mu_min, load)
     os.environ["PEPSI_CHUNK"] = str(chunk)
     try:
-        oc, gc, s, rlk = pair(N, bits, h, lb, mu=mu, resident_bytes=resident_bytes, rescale_group=group)
+        oc, gc, s, rlk = pair(N, bits, h, lb, mu=mu, resident_bytes=resident_bytes, rescale_group=group, **ctx_kw)
     finally:
         os.environ.pop("PEPSI_CHUNK", None)
     rc, Ts, _ = oc.server_table(sets.server)
@@ -125,3 +125,35 @@ def test_lazy_toy_size_full_parity():
     slots, b = gc.decrypt(got)
     assert b > 0
     assert np.array_equal(slots, brute_indicator(sets.client, sets.server, where, 4096))
+
+
+@pytest.mark.parametrize("h,bits,lb", [(2, TOY, 8), (4, PAPER, 10), (8, LARGE, 12)])
+def test_lazy_long_chunks_all_modes(h, bits, lb):
+    """Chunks of 128 layers and one rounding for all mu >= 160 layers, as the
+    benchmark runs them at scale: each k_tensor_sum launch sums 128 layers,
+    32 per thread slice, so the slices' periodic 128-bit reductions (every
+    16 layers) run under the word comparison.  All four modes, the value
+    modes with their products summed in the auxiliary base."""
+    import oracle
+
+    oc, gc, s, rlk, sets, Ts, cts, where, sid, mu = _case(64, bits, h, lb, ALL, chunk=128, m=30, n=2200,
+                                                          planted=6, seed=21, mu_min=160, server_values=1)
+    assert mu >= 160 and gc.rescale_cap == mu and gc.schedule()["chunk"] == 128
+    hashed = hashed_indicator(sets.client, sets.server, where, 64, lb)
+    for mode in (0, 1):
+        want = oc.eval(rlk, cts, Ts, mode=mode, mask_seed=5, group=mu)
+        got = gc.eval(sid, cts, mode=mode, mask_seed=5)
+        assert np.array_equal(got, want), mode
+        slots, b = gc.decrypt(got)
+        assert b > 0
+        if mode == 0:
+            assert np.array_equal(slots, hashed)
+    values = (np.arange(len(sets.server), dtype=np.uint64) * 7919 % 65536 + 1).astype(np.uint32)
+    vid = gc.server_load_values(sets.server, values)
+    rc, Tv, V, _ = oracle.simple_hash_values(0x5EED, lb, 6, sets.server, values, mu)
+    assert rc == 0 and np.array_equal(Tv, Ts)
+    for mode in (2, 3):
+        want = oc.eval(rlk, cts, Ts, mode=mode, mask_seed=8, group=mu, V=V)
+        got = gc.eval(vid, cts, mode=mode, mask_seed=8)
+        assert np.array_equal(got, want), mode
+        assert gc.decrypt(got)[1] > 0

@@ -180,6 +180,10 @@ typedef struct {
                            key-switching sum runs on the load of the inverse NTT that
                            extends u, and the relinearised product is never stored;
                            0: it is stored, then the affine step runs */
+  uint32_t batch_points;/* points per block of the multiply-accumulate that serves several
+                           requests with one read of the plaintexts (pepsi_eval_batch):
+                           0 = the default (32), 32 (16 layers per block) or 64 (8 layers:
+                           longer copy rows, more re-reads of the request tiles) */
 } pepsi_schedule;
 
 /* Read or set the schedule of later evaluations on this context
@@ -264,11 +268,13 @@ int pepsi_autotune(pepsi_ctx* ctx, int set_id, const uint64_t* cts, void* stream
 /* Several requests in one call: request i is evaluated against server set
  * set_ids[i] exactly as by pepsi_eval (same output words), with mode
  * modes[i] (NULL: all indicator) and mask seed mask_seeds[i] (NULL: 0).
- * Requests on the same set are processed in groups of up to 2 whose
+ * Requests on the same set are processed in groups of up to 4 whose
  * multiply-accumulate reads the server plaintexts once for the whole group
  * (or generates each plaintext chunk once, when the table is not
- * resident).  cts[i]: [B][ell][2][k][N], out_cts[i]: [B][2][r][N], each host or
- * device.  Errors as pepsi_eval. */
+ * resident); the next group's multiply-accumulate overlaps the current
+ * group's circuits on a second stream of the context.  cts[i]:
+ * [B][ell][2][k][N], out_cts[i]: [B][2][r][N], each host or device.
+ * Errors as pepsi_eval. */
 int pepsi_eval_batch(pepsi_ctx* ctx, int nq, const int* set_ids, const uint64_t* const* cts, const int* modes,
                      const uint64_t* mask_seeds, uint64_t* const* out_cts, void* stream);
 

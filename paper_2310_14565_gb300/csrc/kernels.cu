@@ -6,6 +6,7 @@
 
 #include <algorithm>
 #include <cstdio>
+#include <cstring>
 
 #include "kernels.h"
 #include "ntt_block.cuh"
@@ -447,27 +448,50 @@ __global__ void __launch_bounds__(mac::THREADS, 1)
   }
 }
 
-// Multi-request variant: QB requests (1 or 2) against the same plaintexts.
-// Each P tile is read once and feeds 2*QB multiply-accumulates per word;
-// the requests' tiles come as one 4-D TMA box (points x components x bits x
-// requests).  Same tiling as k_mac (128 points x 8 layers per block, each
-// consumer thread one point and two layers, here for all QB requests), so a
-// request word loaded from shared memory serves two layers.  Same pipeline,
-// split operands, folding and bounded waits as k_mac.
+// Multi-request variant: QB <= 4 requests against the same plaintexts.
+// Each plaintext tile is read from HBM once and feeds 2*QB products per
+// word, so the batch's plaintext stream costs what one request's does and
+// the kernel is bound by the wide multiply-adds instead (6 per plaintext
+// word and request).  A block owns TN = 32*WPS consecutive (prime, point)
+// words and LB = 16/WPS layers.  Each of the 8 consumer warps covers 32
+// points of one layer slice; each consumer thread one point, LPT = 2 layers
+// and all QB requests: a plaintext word loaded from shared memory serves
+// 2*QB products and a request word LPT products, so a 4-request batch
+// reads 10 shared-memory words per 48 multiply-adds (the SM's shared-memory
+// bandwidth is a quarter of its wide multiply-add rate in 8-byte words).
+// Its 48 64-bit partial sums per thread are why there are 8 consumer warps:
+// with the producer, 9 warps put at most 3 on an SM sub-partition, whose
+// 16K registers then allow 168 per thread (13 warps would cap them at
+// 128 and spill).  Each request's tile is one 3-D TMA box (points x
+// components x bits, plain loads of this GPU's memory).  Same
+// pipeline, split operands, Karatsuba sums, folding and bounded waits as
+// k_mac.  Each request has its own tensor map and output, so the requests
+// may live anywhere; the tile width WPS is a schedule choice (wider rows per copy
+// against fewer re-reads of the request tiles, which every layer group
+// reads again from L2).
 namespace macq {
-constexpr int TN = 128, LB = 8, LPT = 2, JS = 4, NST = 4, QMAX = 2;
-constexpr int LG = LB / LPT;
-constexpr int CONSUMER_WARPS = (TN / 32) * LG;  // 16
+constexpr int LPT = 2, JS = 4, NST = 4, QMAX = 4, CONSUMER_WARPS = 8;
 constexpr int THREADS = (CONSUMER_WARPS + 1) * 32;
-constexpr int P_WORDS = LB * JS * TN;
-static_assert(P_WORDS == mac::P_WORDS, "the plaintext tile of both kernels has one shape");
-template <bool P7>
-__host__ __device__ constexpr int stage_bytes() {
-  return mac::p_bytes<P7>() + QMAX * 2 * JS * TN * 8;
+static_assert(QMAX == PEPSI_MAC_MAX_REQUESTS, "one request bound");
+template <int WPS>
+struct Tile {
+  static constexpr int TN = 32 * WPS;                // points per block
+  static constexpr int LG = CONSUMER_WARPS / WPS;    // layer slices
+  static constexpr int LB = LG * LPT;                // layers per block
+  static constexpr int P_WORDS = LB * JS * TN;
+  static_assert(LG * WPS == CONSUMER_WARPS, "whole layer slices");
+};
+template <int QB, int WPS, bool P7>
+__host__ __device__ constexpr int p_bytes() {
+  return Tile<WPS>::P_WORDS * (P7 ? 7 : 8);
 }
-template <bool P7>
+template <int QB, int WPS, bool P7>
+__host__ __device__ constexpr int stage_bytes() {
+  return p_bytes<QB, WPS, P7>() + QB * 2 * JS * Tile<WPS>::TN * 8;
+}
+template <int QB, int WPS, bool P7>
 __host__ __device__ constexpr size_t smem() {
-  return (size_t)NST * stage_bytes<P7>() + 2 * NST * 8 + 16 + 128;
+  return (size_t)NST * stage_bytes<QB, WPS, P7>() + 2 * NST * 8 + 16 + 128;
 }
 }  // namespace macq
 
@@ -479,13 +503,42 @@ __device__ __forceinline__ void tma_load_4d(u32 dst, const CUtensorMap* tm, int 
       : "memory");
 }
 
-template <int QB, bool P7>
+// Plaintext word o of a stage tile of PW words (see tile_word), and the
+// stage's plaintext copies for that tile size.
+template <bool P7, int PW>
+__device__ __forceinline__ void tile_word_pw(const unsigned char* stg, int o, u32 s, u32 lmask, u32& xl, u32& xh) {
+  if constexpr (P7) {
+    const u32 a = reinterpret_cast<const u32*>(stg)[o];
+    const u32 b = reinterpret_cast<const uint16_t*>(stg + PW * 4)[o];
+    const u32 c = stg[PW * 6 + o];
+    const u32 hi = __byte_perm(b, c, 0x2410);
+    xl = a & lmask;
+    xh = __funnelshift_r(a, hi, s);
+  } else {
+    const u64 x = reinterpret_cast<const u64*>(stg)[o];
+    xl = (u32)x;
+    xh = (u32)(x >> 32);
+  }
+}
+template <bool P7, int PW>
+__device__ __forceinline__ void tma_plain_pw(u32 sb, const CUtensorMap* tmP, const CUtensorMap* tmPb,
+                                             const CUtensorMap* tmPc, int x, int j, int l, u32 bar) {
+  tma_load_3d(sb, tmP, x, j, l, bar);
+  if constexpr (P7) {
+    tma_load_3d(sb + PW * 4, tmPb, x, j, l, bar);
+    tma_load_3d(sb + PW * 6, tmPc, x, j, l, bar);
+  }
+}
+
+template <int QB, int WPS, bool P7>
 __global__ void __launch_bounds__(macq::THREADS, 1)
     k_mac_multi(DevView V, const __grid_constant__ CUtensorMap tmP, const __grid_constant__ CUtensorMap tmPb,
-                const __grid_constant__ CUtensorMap tmPc, const __grid_constant__ CUtensorMap tmC,
-                u64* __restrict__ H, size_t hq, int ell, int L, int fold_stages, int* err) {
+                const __grid_constant__ CUtensorMap tmPc, const __grid_constant__ MacRequests rq, int ell, int L,
+                int fold_stages, int* err) {
   using namespace macq;
-  constexpr int SB = stage_bytes<P7>(), PB = mac::p_bytes<P7>();
+  using TL = Tile<WPS>;
+  constexpr int TN = TL::TN, LB = TL::LB, PW = TL::P_WORDS;
+  constexpr int SB = stage_bytes<QB, WPS, P7>(), PB = p_bytes<QB, WPS, P7>();
   extern __shared__ __align__(128) u64 sm_raw[];
   unsigned char* sm =
       reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(sm_raw) + 127) & ~(uintptr_t)127);
@@ -513,8 +566,9 @@ __global__ void __launch_bounds__(macq::THREADS, 1)
   if (warp == CONSUMER_WARPS) {
     if (lane == 0) {
       asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<u64>(&tmP)) : "memory");
-      asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<u64>(&tmC)) : "memory");
-      const u32 bytes = (u32)(PB + QB * 2 * JS * TN * 8);
+#pragma unroll
+      for (int q = 0; q < QB; ++q)
+        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<u64>(&rq.c[q])) : "memory");
       for (int st = 0; st < nst; ++st) {
         const int buf = st % NST;
         if (st >= NST && !mbar_wait_bounded(empty0 + 8 * buf, (u32)(((st / NST) - 1) & 1))) {
@@ -524,15 +578,17 @@ __global__ void __launch_bounds__(macq::THREADS, 1)
         const u32 bar = full0 + 8 * buf;
         const u32 sb = sbase + (u32)(buf * SB);
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        mbar_expect_tx(bar, bytes);
-        tma_plain<P7>(sb, &tmP, &tmPb, &tmPc, (int)idx0, st * JS, l0, bar);
-        tma_load_4d(sb + (u32)PB, &tmC, (int)idx0, 0, st * JS, 0, bar);
+        mbar_expect_tx(bar, (u32)SB);
+        tma_plain_pw<P7, PW>(sb, &tmP, &tmPb, &tmPc, (int)idx0, st * JS, l0, bar);
+#pragma unroll
+        for (int q = 0; q < QB; ++q)
+          tma_load_3d(sb + (u32)(PB + q * 2 * JS * TN * 8), &rq.c[q], (int)idx0, 0, st * JS, bar);
         issued = st + 1;
       }
     }
   } else {
-    const int tp = (warp % (TN / 32)) * 32 + lane;
-    const int g = warp / (TN / 32);  // layer slice
+    const int tp = (warp % WPS) * 32 + lane;  // point within the tile
+    const int g = warp / WPS;                 // layer slice
     const bool active = tp < cnt;
     const size_t idx = idx0 + (active ? tp : 0);
     const DevPrime pr = V.pr[idx / V.N];
@@ -553,31 +609,26 @@ __global__ void __launch_bounds__(macq::THREADS, 1)
         break;
       }
       const unsigned char* stg = sm + (size_t)buf * SB;
-      const int po = g * LPT * JS * TN + tp;  // word (slice, bit 0, point) of the tile
+      const int po = g * LPT * JS * TN + tp;  // word (slice, bit 0, point) of the plaintext tile
       const u64* cs = reinterpret_cast<const u64*>(stg + PB) + tp;
 #pragma unroll
       for (int jj = 0; jj < JS; ++jj) {
-        u32 cl[QB][2], ch[QB][2], csum[QB][2];
+        u32 xl[LPT], xh[LPT], xs[LPT];
+#pragma unroll
+        for (int l = 0; l < LPT; ++l) {
+          tile_word_pw<P7, PW>(stg, po + (l * JS + jj) * TN, s32, lmask, xl[l], xh[l]);
+          xs[l] = xl[l] + xh[l];
+        }
 #pragma unroll
         for (int q = 0; q < QB; ++q)
 #pragma unroll
           for (int c = 0; c < 2; ++c) {
             const u64 w = cs[((q * JS + jj) * 2 + c) * TN];
-            cl[q][c] = (u32)w;
-            ch[q][c] = (u32)(w >> 32);
-            csum[q][c] = cl[q][c] + ch[q][c];
+            const u32 cl = (u32)w, ch = (u32)(w >> 32), csum = cl + ch;
+#pragma unroll
+            for (int l = 0; l < LPT; ++l)
+              kmac(S0[l][q][c], SM[l][q][c], S2[l][q][c], cl, ch, csum, xl[l], xh[l], xs[l]);
           }
-#pragma unroll
-        for (int l = 0; l < LPT; ++l) {
-          u32 xl, xh;
-          tile_word<P7>(stg, po + (l * JS + jj) * TN, s32, lmask, xl, xh);
-          const u32 xs = xl + xh;
-#pragma unroll
-          for (int q = 0; q < QB; ++q)
-#pragma unroll
-            for (int c = 0; c < 2; ++c)
-              kmac(S0[l][q][c], SM[l][q][c], S2[l][q][c], cl[q][c], ch[q][c], csum[q][c], xl, xh, xs);
-        }
       }
       __syncwarp();
       if (lane == 0) mbar_arrive(empty0 + 8 * buf);
@@ -600,7 +651,7 @@ __global__ void __launch_bounds__(macq::THREADS, 1)
           for (int c = 0; c < 2; ++c) {
             fold_inplace(S0[l][q][c], SM[l][q][c], S2[l][q][c], sp, pr);
             const int layer = g * LPT + l;
-            if (layer < nl) H[(size_t)q * hq + ((size_t)(l0 + layer) * 2 + c) * kN + idx] = S0[l][q][c];
+            if (layer < nl) rq.h[q][((size_t)(l0 + layer) * 2 + c) * kN + idx] = S0[l][q][c];
           }
     }
   }
@@ -1416,33 +1467,68 @@ bool encode4d(CUtensorMap* tm, const u64* base, u64 d0, u64 d1, u64 d2, u64 d3, 
 }
 }  // namespace
 
-cudaError_t launch_mac_multi(const DevView& V, const u64* C, int nq, const PlainTab& P, u64* H, size_t hq, int ell,
-                             int L, int fold, int* err, cudaStream_t st) {
-  if (L <= 0 || nq <= 0) return cudaSuccess;
-  if (nq > macq::QMAX) return cudaErrorInvalidValue;
+namespace {
+template <int QB, int WPS, bool P7>
+void mac_multi_go(const DevView& V, const CUtensorMap (&tmP)[3], const MacRequests& rq, int ell, int L,
+                  int fold_stages, int* err, cudaStream_t st) {
+  using TL = macq::Tile<WPS>;
   const u64 kN = (u64)V.k * V.N;
-  CUtensorMap tmP[3], tmC;
-  if (!encode_plain(tmP, P, kN, ell, L, macq::TN, macq::JS, macq::LB) ||
-      !encode4d(&tmC, C, kN, 2, ell, nq, kN, 2 * kN, (u64)ell * 2 * kN, macq::TN, 2, macq::JS, nq))
-    return cudaErrorInvalidValue;
-  const int fold_stages = fold / macq::JS > 0 ? fold / macq::JS : 1;
-  dim3 grid((L + macq::LB - 1) / macq::LB, (unsigned)((kN + macq::TN - 1) / macq::TN));
-#define PEPSI_MACQ(QB, P7)                                                                                      \
-  k_mac_multi<QB, P7><<<grid, macq::THREADS, macq::smem<P7>(), st>>>(V, tmP[0], tmP[1], tmP[2], tmC, H, hq, ell, L, \
-                                                                      fold_stages, err)
-  if (P.packed()) {
-    if (nq == 1)
-      PEPSI_MACQ(1, true);
-    else
-      PEPSI_MACQ(2, true);
-  } else {
-    if (nq == 1)
-      PEPSI_MACQ(1, false);
-    else
-      PEPSI_MACQ(2, false);
+  dim3 grid((L + TL::LB - 1) / TL::LB, (unsigned)((kN + TL::TN - 1) / TL::TN));
+  k_mac_multi<QB, WPS, P7><<<grid, macq::THREADS, macq::smem<QB, WPS, P7>(), st>>>(V, tmP[0], tmP[1], tmP[2], rq, ell,
+                                                                                   L, fold_stages, err);
+}
+template <int WPS, bool P7>
+void mac_multi_q(int nq, const DevView& V, const CUtensorMap (&tmP)[3], const MacRequests& rq, int ell, int L,
+                 int fold_stages, int* err, cudaStream_t st) {
+  switch (nq) {
+    case 2: mac_multi_go<2, WPS, P7>(V, tmP, rq, ell, L, fold_stages, err, st); break;
+    case 3: mac_multi_go<3, WPS, P7>(V, tmP, rq, ell, L, fold_stages, err, st); break;
+    default: mac_multi_go<4, WPS, P7>(V, tmP, rq, ell, L, fold_stages, err, st); break;
   }
-#undef PEPSI_MACQ
+}
+}  // namespace
+
+cudaError_t launch_mac_requests(const DevView& V, int nq, const u64* const* C, const PlainTab& P, u64* const* H,
+                                int ell, int L, int fold, int* err, cudaStream_t st, int tile_points) {
+  if (L <= 0 || nq <= 0) return cudaSuccess;
+  if (nq > macq::QMAX || (tile_points != 32 && tile_points != 64)) return cudaErrorInvalidValue;
+  if (nq == 1) return launch_mac(V, C[0], P, H[0], ell, L, fold, err, st);  // one request: the single-request kernel
+  const u64 kN = (u64)V.k * V.N;
+  const int wps = tile_points / 32;
+  const u32 tn = (u32)tile_points, lb = (u32)(macq::CONSUMER_WARPS / wps * macq::LPT);
+  CUtensorMap tmP[3];
+  MacRequests rq;
+  memset(&rq, 0, sizeof(rq));
+  if (!encode_plain(tmP, P, kN, ell, L, tn, macq::JS, lb)) return cudaErrorInvalidValue;
+  for (int q = 0; q < nq; ++q) {
+    if (!encode3d(&rq.c[q], C[q], kN, 2, ell, kN, 2 * kN, tn, 2, macq::JS)) return cudaErrorInvalidValue;
+    rq.h[q] = H[q];
+  }
+  const int fold_stages = fold / macq::JS > 0 ? fold / macq::JS : 1;
+  if (wps == 1) {
+    if (P.packed())
+      mac_multi_q<1, true>(nq, V, tmP, rq, ell, L, fold_stages, err, st);
+    else
+      mac_multi_q<1, false>(nq, V, tmP, rq, ell, L, fold_stages, err, st);
+  } else {
+    if (P.packed())
+      mac_multi_q<2, true>(nq, V, tmP, rq, ell, L, fold_stages, err, st);
+    else
+      mac_multi_q<2, false>(nq, V, tmP, rq, ell, L, fold_stages, err, st);
+  }
   return cudaSuccess;
+}
+
+cudaError_t launch_mac_multi(const DevView& V, const u64* C, int nq, const PlainTab& P, u64* H, size_t hq, int ell,
+                             int L, int fold, int* err, cudaStream_t st, int tile_points) {
+  if (nq <= 0 || nq > macq::QMAX) return nq <= 0 ? cudaSuccess : cudaErrorInvalidValue;
+  const u64* cq[macq::QMAX];
+  u64* hqv[macq::QMAX];
+  for (int q = 0; q < nq; ++q) {
+    cq[q] = C + (size_t)q * ell * 2 * V.k * V.N;
+    hqv[q] = H + (size_t)q * hq;
+  }
+  return launch_mac_requests(V, nq, cq, P, hqv, ell, L, fold, err, st, tile_points);
 }
 
 cudaError_t launch_mac(const DevView& V, const u64* C, const PlainTab& P, u64* H, int ell, int L, int fold, int* err,
@@ -1668,10 +1754,15 @@ cudaError_t kernels_init(int N) {
   set((const void*)k_valgen);
   set((const void*)k_mac<false>);
   set((const void*)k_mac<true>);
-  set((const void*)k_mac_multi<1, false>);
-  set((const void*)k_mac_multi<2, false>);
-  set((const void*)k_mac_multi<1, true>);
-  set((const void*)k_mac_multi<2, true>);
+#define PEPSI_SET_MACQ(QB)                         \
+  set((const void*)k_mac_multi<QB, 1, false>);     \
+  set((const void*)k_mac_multi<QB, 1, true>);      \
+  set((const void*)k_mac_multi<QB, 2, false>);     \
+  set((const void*)k_mac_multi<QB, 2, true>);
+  PEPSI_SET_MACQ(2)
+  PEPSI_SET_MACQ(3)
+  PEPSI_SET_MACQ(4)
+#undef PEPSI_SET_MACQ
   set((const void*)k_relin_ntt);
   set((const void*)k_tensor_intt);
   set((const void*)k_axpy_intt);

@@ -2,6 +2,8 @@
 // asynchronous on the given stream; errors surface through
 // cudaGetLastError() / the next synchronising call.
 #pragma once
+#include <cuda.h>
+
 #include "common.cuh"
 
 // Batched NTT over rows laid out [outer][np][N]: row r uses prime p0 + (r % np);
@@ -51,15 +53,24 @@ inline PlainTab plain_words(const u64* w) {
 cudaError_t launch_mac(const DevView& V, const u64* C, const PlainTab& P, u64* H, int ell, int L, int fold, int* err,
                        cudaStream_t st, int j0 = 0, int nj = -1, bool acc_in = false);
 
-// The same for nq <= 2 requests sharing the plaintexts: C holds the requests back to back
-// ([nq][ell][2][k][N], split format), H[q] starts at H + q * hq.
+// The same for nq <= PEPSI_MAC_MAX_REQUESTS requests sharing the plaintexts: request q
+// [ell][2][k][N] (split format) at C[q], its h' [L][2][k][N] to H[q].  tile_points: 32
+// or 64 points per block (16 or 8 layers); one request runs launch_mac.
+cudaError_t launch_mac_requests(const DevView& V, int nq, const u64* const* C, const PlainTab& P, u64* const* H,
+                                int ell, int L, int fold, int* err, cudaStream_t st, int tile_points = 32);
+// The same with the requests back to back in C ([nq][ell][2][k][N]) and H[q] at H + q * hq.
 cudaError_t launch_mac_multi(const DevView& V, const u64* C, int nq, const PlainTab& P, u64* H, size_t hq, int ell,
-                             int L, int fold, int* err, cudaStream_t st);
+                             int L, int fold, int* err, cudaStream_t st, int tile_points = 32);
 // count split-format words (rows [..][k][N]) to the three planes of the 7-byte format, and back
 // (reduced values)
 void launch_pack7(const DevView& V, const u64* src, size_t count, u32* a, uint16_t* b, uint8_t* c, cudaStream_t st);
 void launch_unpack7(const u32* a, const uint16_t* b, const uint8_t* c, size_t count, u64* out, cudaStream_t st);
-constexpr int PEPSI_MAC_MAX_REQUESTS = 2;
+constexpr int PEPSI_MAC_MAX_REQUESTS = 4;
+// Per-request operands of the multi-request multiply-accumulate (passed by value).
+struct MacRequests {
+  CUtensorMap c[PEPSI_MAC_MAX_REQUESTS];  // request tiles
+  u64* h[PEPSI_MAC_MAX_REQUESTS];         // h' outputs [L][2][k][N]
+};
 
 // In-place conversion of groups of k rows to (to = true) or from the split operand format.
 void launch_split(const DevView& V, u64* x, size_t groups, bool to, cudaStream_t st);

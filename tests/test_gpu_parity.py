@@ -261,13 +261,15 @@ def test_streamed_plaintexts_match_resident():
     assert np.array_equal(P[mu - 1, 3], oc.server_plaintext(Ts, mu - 1, 3))
 
 
+@pytest.mark.parametrize("batch_points", [32, 64])
 @pytest.mark.parametrize("resident", [True, False])
-def test_eval_batch_matches_single_calls_and_oracle(resident):
-    """pepsi_eval_batch: two server sets, six requests (a group of four and
-    a ragged group on one set, one on the other), mixed modes and seeds;
-    every output equals the single-request call and the oracle."""
+def test_eval_batch_matches_single_calls_and_oracle(resident, batch_points):
+    """pepsi_eval_batch: two server sets, nine requests (groups of four and
+    three on one set, a group of two on the other, so the shared
+    multiply-accumulate runs for 4, 3 and 2 requests), mixed modes and
+    seeds, both tile widths of the shared multiply-accumulate; every output
+    equals the single-request call and the oracle."""
     import oracle
-    import paper_2310_14565_gb300 as pepsi
     from paper_2310_14565_gb300.workload import make_sets
 
     N, bits, h, lb = 64, PAPER, 4, 10
@@ -280,21 +282,23 @@ def test_eval_batch_matches_single_calls_and_oracle(resident):
         oc, gc, s, rlk = pair(N, bits, h, lb, mu=mu, resident_bytes=0 if resident else (1 << 64) - 1)
     finally:
         os.environ.pop("PEPSI_CHUNK", None)
+    gc.set_schedule(batch_points=batch_points)
     sA, sB = gc.server_load(setsA.server), gc.server_load(setsB.server)
     _, TA, _ = oc.server_table(setsA.server)
     _, TB, _ = oc.server_table(setsB.server)
-    clients = [make_sets(16, 60, 3, bits=32, seed_items=20 + i, seed_plant=40 + i).client for i in range(6)]
-    for i in (0, 3):  # plant a few of A's items into two requests
+    nreq = 9
+    clients = [make_sets(16, 60, 3, bits=32, seed_items=20 + i, seed_plant=40 + i).client for i in range(nreq)]
+    for i in (0, 3, 7):  # plant a few of A's items into three requests
         clients[i][:3] = setsA.server[:3]
     cts = [gc.query(cl, 100 + i)[0] for i, cl in enumerate(clients)]
-    set_ids = [sA, sA, sB, sA, sA, sA]
-    modes = [0, 1, 0, 0, 1, 0]
-    seeds = [5, 6, 7, 8, 9, 10]
+    set_ids = [sA, sA, sB, sA, sA, sA, sB, sA, sA]
+    modes = [0, 1, 0, 0, 1, 0, 1, 1, 0]
+    seeds = [5, 6, 7, 8, 9, 10, 11, 12, 13]
     outs = gc.eval_batch(set_ids, cts, modes, seeds)
-    for i in range(6):
+    for i in range(nreq):
         single = gc.eval(set_ids[i], cts[i], mode=modes[i], mask_seed=seeds[i])
         assert np.array_equal(outs[i], single), i
-    for i in (0, 1, 2):
+    for i in (0, 1, 2, 6, 7):
         T_ = TA if set_ids[i] == sA else TB
         assert np.array_equal(outs[i], oc.eval(rlk, cts[i], T_, mode=modes[i], mask_seed=seeds[i])), i
     slots, b = gc.decrypt(outs[0])

@@ -184,6 +184,10 @@ typedef struct {
                            requests with one read of the plaintexts (pepsi_eval_batch):
                            0 = the default (32), 32 (16 layers per block) or 64 (8 layers:
                            longer copy rows, more re-reads of the request tiles) */
+  uint32_t batch_groups;/* warp groups of that multiply-accumulate: 0 = the default (2),
+                           1 = every thread serves all requests of the group (fewer, fuller
+                           warps), 2 = two groups of warps serve half the requests each
+                           (twice the warps; groups of 3 requests always run with 1) */
 } pepsi_schedule;
 
 /* Read or set the schedule of later evaluations on this context

@@ -55,12 +55,15 @@ cudaError_t launch_mac(const DevView& V, const u64* C, const PlainTab& P, u64* H
 
 // The same for nq <= PEPSI_MAC_MAX_REQUESTS requests sharing the plaintexts: request q
 // [ell][2][k][N] (split format) at C[q], its h' [L][2][k][N] to H[q].  tile_points: 32
-// or 64 points per block (16 or 8 layers); one request runs launch_mac.
+// or 64 points per block (16 or 8 layers); groups: 1 = each consumer thread serves every
+// request, 2 = two groups of warps serve half of them each (2 or 4 requests; 3 requests
+// always run in one group); one request runs launch_mac.
 cudaError_t launch_mac_requests(const DevView& V, int nq, const u64* const* C, const PlainTab& P, u64* const* H,
-                                int ell, int L, int fold, int* err, cudaStream_t st, int tile_points = 32);
+                                int ell, int L, int fold, int* err, cudaStream_t st, int tile_points = 32,
+                                int groups = 2);
 // The same with the requests back to back in C ([nq][ell][2][k][N]) and H[q] at H + q * hq.
 cudaError_t launch_mac_multi(const DevView& V, const u64* C, int nq, const PlainTab& P, u64* H, size_t hq, int ell,
-                             int L, int fold, int* err, cudaStream_t st, int tile_points = 32);
+                             int L, int fold, int* err, cudaStream_t st, int tile_points = 32, int groups = 2);
 // count split-format words (rows [..][k][N]) to the three planes of the 7-byte format, and back
 // (reduced values)
 void launch_pack7(const DevView& V, const u64* src, size_t count, u32* a, uint16_t* b, uint8_t* c, cudaStream_t st);

@@ -109,6 +109,7 @@ struct pepsi_ctx {
   int chunk = 64;  // layers per circuit chunk (pepsi_autotune may change it)
   bool relin_fused = true;  // key-switching sum on the load of the affine step's inverse NTT
   int batch_points = 32;    // points per block of the multi-request multiply-accumulate
+  int batch_groups = 2;     // warp groups of the multi-request multiply-accumulate
   u32 rescale_cap = 1;      // most layers one rounding of the last products may cover
   bool value_margin = false;  // B also holds the value products under lazy rescaling
   int resp = 0;               // primes of the evaluation's response (k: no switching)
@@ -821,7 +822,7 @@ int eval_batch_core(pepsi_ctx* c, int nq, const int* set_ids, const u64* const* 
       {
         Prof p(c, PC_MAC, ax);
         CKS(mac_status(launch_mac_multi(c->V, CB, G, S.plain(kN, c->ell), HB, hq, c->ell, (int)mres, c->mac_fold,
-                                        c->d_err, ax, c->batch_points)));
+                                        c->d_err, ax, c->batch_points, c->batch_groups)));
       }
       CKS(cudaEventRecord(mac_done[slot], ax));
       CKS(cudaStreamWaitEvent(st, mac_done[slot], 0));
@@ -840,7 +841,7 @@ int eval_batch_core(pepsi_ctx* c, int nq, const int* set_ids, const u64* const* 
         }
         Prof p(c, PC_MAC, st);
         CKS(mac_status(launch_mac_multi(c->V, CB, G, plain_words(b.Pc), HB, hq, c->ell, L, c->mac_fold, c->d_err, st,
-                                        c->batch_points)));
+                                        c->batch_points, c->batch_groups)));
       }
       for (int g = 0; g < G; ++g) {
         b.H = HB + (size_t)g * hq + (res ? (size_t)l0 * ct2 : 0);
@@ -1284,6 +1285,7 @@ int pepsi_get_schedule(const pepsi_ctx* c, pepsi_schedule* out) {
   out->ntt_threads = (uint32_t)c->V.nt;
   out->relin_fused = c->relin_fused ? 1u : 0u;
   out->batch_points = (uint32_t)c->batch_points;
+  out->batch_groups = (uint32_t)c->batch_groups;
   return PEPSI_OK;
 }
 
@@ -1292,8 +1294,10 @@ int pepsi_set_schedule(pepsi_ctx* c, const pepsi_schedule* s) {
   const u32 nt = s->ntt_threads;
   if (nt && (nt < 64 || nt > 1024 || (nt & (nt - 1)))) return PEPSI_E_PARAM;
   if (s->batch_points != 0 && s->batch_points != 32 && s->batch_points != 64) return PEPSI_E_PARAM;
+  if (s->batch_groups > 2) return PEPSI_E_PARAM;
   c->chunk = (int)s->chunk;
   c->batch_points = s->batch_points ? (int)s->batch_points : 32;
+  c->batch_groups = s->batch_groups ? (int)s->batch_groups : 2;
   c->V.nt = (int)nt;
   c->relin_fused = s->relin_fused != 0;
   return PEPSI_OK;

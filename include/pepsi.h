@@ -371,17 +371,108 @@ int pepsi_wait_probe(pepsi_ctx* ctx, int arrive);
 
 /* Measurement helper (no paper counterpart): the integer-pipe throughput of
  * the multiply forms the kernels use, measured on the current device with
- * independent chains on every SM.  wide = 1: 32x32->64 multiply-adds
- * (mad.wide.u32, the MAC's inner operation); wide = 0: 32-bit multiply-adds.
- * *ops_per_s receives operations per second for the whole GPU.  Allocates
- * 8 bytes of device memory for the duration of the call. */
-int pepsi_int_peak(int wide, double* ops_per_s);
+ * 16 chains per thread on every SM, each step's multiplier taken from
+ * another chain so that no product can be hoisted.  form = 1: 32x32->64
+ * multiply-adds into 64-bit sums (mad.wide.u32, the multiply-accumulate's
+ * inner operation); form = 2: the 32x32->64 product alone (mul.wide.u32);
+ * form = 0: 32-bit multiply-adds (mad.lo.u32).  *ops_per_s receives
+ * operations per second for the whole GPU.  Allocates 8 bytes of device
+ * memory for the duration of the call. */
+int pepsi_int_peak(int form, double* ops_per_s);
 
 /* Per-kernel timing with CUDA events on the launching stream: enable (1) /
  * disable (0) and read back {launches, total milliseconds} per kernel
  * class (names[i] is a static string; returns the number of classes). */
 int pepsi_profile_enable(pepsi_ctx* ctx, int on);
 int pepsi_profile_read(pepsi_ctx* ctx, const char** names, uint64_t* launches, double* total_ms, int max);
+
+/* ------------------------------------------------------------ engine
+ * Continuous-batching request engine (no counterpart in the paper: the
+ * served and batched forms of Algorithm 2's evaluation).  An engine serves
+ * lanes; a lane is one (context, server set) pair with up to `slots`
+ * requests in flight, evaluated by a carousel over the set's layers.  Each
+ * step of a lane takes its next chunk of layers (the context's schedule
+ * chunk; a chunk ends at the resident / regenerated boundary) and runs the
+ * multiply-accumulate of that chunk for every request in the lane with one
+ * read of the chunk's plaintexts (the kernel of pepsi_eval_batch), then
+ * each request's equality circuits and layer sum.  A request admitted at a
+ * step starts at the lane's current layer and is complete once it has
+ * seen all mu layers, wrapping around.  The layer sum does not depend on
+ * the order of the layers (with per-layer rounding, or with one rounding
+ * for all layers), so every result has the words pepsi_eval gives.
+ * Requests that arrive while others are on the GPU join at the lane's next
+ * step, as slots and the HBM budget allow, and their work overlaps on the
+ * device: each lane runs on streams of its own, and up to two steps per
+ * lane are queued ahead of the GPU.  The per-request device state (the
+ * request in NTT form, h' of a chunk, the layer sums) comes from a
+ * stream-ordered memory pool of the engine; a request is admitted only
+ * while the admitted requests' state fits hbm_budget. */
+typedef struct pepsi_engine pepsi_engine;
+
+typedef struct {
+  pepsi_ctx* ctx;  /* the set's context; it must outlive the engine, and load no sets or
+                      change its schedule or rounding while the engine exists */
+  int set_id;      /* a set of ctx with one block of bins (bins = N) */
+  uint32_t slots;  /* requests evaluated together, 1..4 */
+} pepsi_lane;
+
+typedef struct {
+  uint64_t submitted, completed; /* requests */
+  uint64_t steps;                /* lane steps enqueued */
+  uint64_t bytes_in_use;         /* per-request device state of the admitted requests */
+  uint64_t bytes_peak;           /* its maximum so far */
+  uint64_t budget;               /* the admission budget in bytes */
+} pepsi_engine_stats;
+
+/* Create an engine over nlanes lanes.  Each lane gets a context of its own
+ * that shares the lane context's keys, tables and sets (own streams and
+ * scratch; the circuit scratch of one chunk per lane is allocated here).
+ * hbm_budget: bytes of per-request state all admitted requests may hold
+ * together (0: half of the free device memory after the lanes' scratch).
+ * Errors: PEPSI_E_PARAM (a set with more than one block, slots outside
+ * 1..4, a context whose rescale_group rounds runs of more than one layer
+ * but fewer than all of them), PEPSI_E_NOMEM, PEPSI_E_CUDA. */
+int pepsi_engine_create(const pepsi_lane* lanes, int nlanes, uint64_t hbm_budget, pepsi_engine** out);
+
+/* Queue a request on a lane; thread-safe.  cts: [ell][2][k][N]
+ * coefficient form, host (pinned memory keeps the copy asynchronous) or
+ * device, read when the request is admitted; out_ct: [2][r][N] (r =
+ * response_primes), host (pinned) or device, written when it completes.
+ * Both must stay valid until pepsi_engine_wait reports the request done.
+ * *ticket identifies it.  Errors: PEPSI_E_PARAM (lane, mode, a value mode
+ * on a set without values, null buffers). */
+int pepsi_engine_submit(pepsi_engine* e, int lane, const uint64_t* cts, int mode, uint64_t mask_seed,
+                        uint64_t* out_ct, uint64_t* ticket);
+
+/* One scheduling pass by the calling thread: retire the steps the GPU has
+ * completed, admit queued requests into free slots within the budget, and
+ * queue each busy lane's next steps (at most two ahead).  Never waits for
+ * the GPU.  *pending (may be NULL): requests submitted and not yet done.
+ * Use either pepsi_engine_pump / pepsi_engine_run from one thread, or the
+ * engine's own thread (pepsi_engine_start), not both. */
+int pepsi_engine_pump(pepsi_engine* e, uint64_t* pending);
+
+/* Pump until every request submitted so far is done. */
+int pepsi_engine_run(pepsi_engine* e);
+
+/* Start / stop a thread of the engine that pumps continuously (it sleeps
+ * about 20 microseconds between passes while work is in flight). */
+int pepsi_engine_start(pepsi_engine* e);
+int pepsi_engine_stop(pepsi_engine* e);
+
+/* Wait until a request is done (pumping from the calling thread when no
+ * engine thread runs); returns its status (PEPSI_OK, PEPSI_E_TIMEOUT when a
+ * bounded device wait of its steps expired, PEPSI_E_CUDA).  latency_ms (may
+ * be NULL): from its submission to the engine seeing its last step
+ * complete.  Errors: PEPSI_E_PARAM for an unknown ticket. */
+int pepsi_engine_wait(pepsi_engine* e, uint64_t ticket, double* latency_ms);
+
+/* Counters of the engine. */
+int pepsi_engine_get_stats(pepsi_engine* e, pepsi_engine_stats* out);
+
+/* Finish every request in flight, then release the engine and its lanes
+ * (NULL is ignored). */
+void pepsi_engine_destroy(pepsi_engine* e);
 
 /* Release every device buffer of the context (NULL is ignored). */
 void pepsi_destroy(pepsi_ctx* ctx);

@@ -61,6 +61,15 @@ class Schedule(C.Structure):
                 ("batch_points", C.c_uint32), ("batch_groups", C.c_uint32)]
 
 
+class LaneDesc(C.Structure):
+    _fields_ = [("ctx", C.c_void_p), ("set_id", C.c_int), ("slots", C.c_uint32)]
+
+
+class EngineStats(C.Structure):
+    _fields_ = [("submitted", C.c_uint64), ("completed", C.c_uint64), ("steps", C.c_uint64),
+                ("bytes_in_use", C.c_uint64), ("bytes_peak", C.c_uint64), ("budget", C.c_uint64)]
+
+
 RESCALE_ALL = 0xFFFFFFFF
 
 SYMBOLS = {
@@ -98,6 +107,16 @@ SYMBOLS = {
     "pepsi_profile_read": (C.c_int, [C.c_void_p, C.POINTER(C.c_char_p), C.POINTER(C.c_uint64),
                                      C.POINTER(C.c_double), C.c_int]),
     "pepsi_int_peak": (C.c_int, [C.c_int, C.POINTER(C.c_double)]),
+    "pepsi_engine_create": (C.c_int, [C.POINTER(LaneDesc), C.c_int, C.c_uint64, C.POINTER(C.c_void_p)]),
+    "pepsi_engine_submit": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.c_uint64, C.c_void_p,
+                                      C.POINTER(C.c_uint64)]),
+    "pepsi_engine_pump": (C.c_int, [C.c_void_p, C.POINTER(C.c_uint64)]),
+    "pepsi_engine_run": (C.c_int, [C.c_void_p]),
+    "pepsi_engine_start": (C.c_int, [C.c_void_p]),
+    "pepsi_engine_stop": (C.c_int, [C.c_void_p]),
+    "pepsi_engine_wait": (C.c_int, [C.c_void_p, C.c_uint64, C.POINTER(C.c_double)]),
+    "pepsi_engine_get_stats": (C.c_int, [C.c_void_p, C.POINTER(EngineStats)]),
+    "pepsi_engine_destroy": (None, [C.c_void_p]),
     "pepsi_destroy": (None, [C.c_void_p]),
     "pepsi_strerror": (C.c_char_p, [C.c_int]),
     "pepsi_last_error": (C.c_char_p, []),
@@ -194,10 +213,15 @@ def comm_optimal_h(lambda_bar, bins, h_max=64):
     return int(h.value)
 
 
-def int_peak(wide=True):
-    """Measured integer multiply-add throughput of the current GPU (ops/s)."""
+INT_MAD_LO, INT_MAD_WIDE, INT_MUL_WIDE = 0, 1, 2
+
+
+def int_peak(form=INT_MAD_WIDE):
+    """Measured integer multiply throughput of the current GPU (ops/s):
+    INT_MAD_WIDE (32x32->64 multiply-add into a 64-bit sum), INT_MUL_WIDE
+    (the wide product alone) or INT_MAD_LO (32-bit multiply-add)."""
     v = C.c_double(0)
-    _check(lib().pepsi_int_peak(int(wide), C.byref(v)), "pepsi_int_peak")
+    _check(lib().pepsi_int_peak(int(form), C.byref(v)), "pepsi_int_peak")
     return v.value
 
 
@@ -455,3 +479,75 @@ class Context:
         ms = (C.c_double * n)()
         cnt = lib().pepsi_profile_read(self._h, names, launches, ms, n)
         return {names[i].decode(): (int(launches[i]), float(ms[i])) for i in range(cnt)}
+
+
+class Engine:
+    """Continuous-batching request engine (pepsi_engine_*): lanes of
+    (Context, set id, slots); every request's result has the words of
+    Context.eval.  Keeps the contexts and the buffers of requests in flight
+    alive until they are waited for."""
+
+    def __init__(self, lanes, hbm_budget=0):
+        self._ctxs = [lc for lc, _, _ in lanes]
+        arr = (LaneDesc * len(lanes))()
+        for i, (ctx, sid, slots) in enumerate(lanes):
+            arr[i].ctx, arr[i].set_id, arr[i].slots = ctx._h.value, sid, slots
+        self._h = C.c_void_p()
+        _check(lib().pepsi_engine_create(arr, len(lanes), hbm_budget, C.byref(self._h)), "pepsi_engine_create")
+        self._lane_ctx = [ctx for ctx, _, _ in lanes]
+        self._held = {}
+
+    def submit(self, lane, cts, out=None, mode=MODE_INDICATOR, mask_seed=0):
+        """Queue a request; returns (ticket, out).  cts [ell][2][k][N] and
+        out [2][r][N]: numpy (pinned is best) or torch CUDA tensors."""
+        ctx = self._lane_ctx[lane]
+        if out is None:
+            out = np.zeros((2, ctx.response_primes, ctx.N), dtype=np.uint64)
+        _need(cts, ctx.ell * 2 * ctx.k * ctx.N, "engine cts")
+        _need(out, 2 * ctx.response_primes * ctx.N, "engine out")
+        t = C.c_uint64(0)
+        _check(lib().pepsi_engine_submit(self._h, lane, _ptr(cts), mode, mask_seed, _ptr(out), C.byref(t)),
+               "pepsi_engine_submit")
+        self._held[t.value] = (cts, out)
+        return t.value, out
+
+    def pump(self):
+        """One scheduling pass; returns the number of requests not yet done."""
+        p = C.c_uint64(0)
+        _check(lib().pepsi_engine_pump(self._h, C.byref(p)), "pepsi_engine_pump")
+        return int(p.value)
+
+    def run(self):
+        _check(lib().pepsi_engine_run(self._h), "pepsi_engine_run")
+
+    def start(self):
+        _check(lib().pepsi_engine_start(self._h), "pepsi_engine_start")
+
+    def stop(self):
+        _check(lib().pepsi_engine_stop(self._h), "pepsi_engine_stop")
+
+    def wait(self, ticket):
+        """Block until the request is done; its latency in ms (submission to
+        completion seen by the engine)."""
+        ms = C.c_double(0)
+        rc = lib().pepsi_engine_wait(self._h, ticket, C.byref(ms))
+        self._held.pop(ticket, None)
+        _check(rc, "pepsi_engine_wait")
+        return ms.value
+
+    def stats(self):
+        st = EngineStats()
+        _check(lib().pepsi_engine_get_stats(self._h, C.byref(st)), "pepsi_engine_get_stats")
+        return {f: int(getattr(st, f)) for f, _ in EngineStats._fields_}
+
+    def close(self):
+        if self._h:
+            lib().pepsi_engine_destroy(self._h)
+            self._h = C.c_void_p()
+        self._held.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

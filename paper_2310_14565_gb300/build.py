@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 OBJDIR = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libpepsi_gb300.so")
-SOURCES = ["kernels.cu", "pepsi.cu", "host.cpp"]
+SOURCES = ["kernels.cu", "pepsi.cu", "engine.cu", "host.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

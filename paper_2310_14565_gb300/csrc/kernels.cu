@@ -1797,39 +1797,43 @@ cudaError_t kernels_init(int N) {
 }
 
 // ------------------------------------------------------ integer-pipe peak
-// Throughput probe of the two multiply forms the kernels above are built
-// from: 32x32->64 wide multiply-add (mad.wide.u32) and 32-bit
-// multiply-add (mad.lo.u32).  Each thread runs 16 independent chains of
-// `iters` steps; the result is folded into *sink so nothing is dead code.
+// Throughput probe of the multiply forms the kernels above are built from:
+// FORM 1, 32x32->64 wide multiply-add into a 64-bit sum (mad.wide.u32, the
+// multiply-accumulate's operation); FORM 2, the wide product alone
+// (mul.wide.u32); FORM 0, 32-bit multiply-add (mad.lo.u32).  Each thread runs
+// 16 chains; the multiplier of chain i is the low word of chain i+5, so it
+// changes every step and no product can be hoisted out of the loop.  The
+// result is folded into *sink so nothing is dead code.
 namespace {
-template <int WIDE>
+template <int FORM>
 __global__ void k_int_peak(int iters, u32 seed, u64* sink) {
   u64 a[16];
-  u32 b[16];
 #pragma unroll
-  for (int i = 0; i < 16; ++i) {
-    a[i] = seed + threadIdx.x + i;
-    b[i] = seed * (i + 3) + blockIdx.x;
-  }
+  for (int i = 0; i < 16; ++i) a[i] = seed + threadIdx.x * 7 + i;
   const u32 m = seed | 1u;
   for (int it = 0; it < iters; ++it) {
 #pragma unroll
     for (int i = 0; i < 16; ++i) {
-      if (WIDE) {
-        asm volatile("mad.wide.u32 %0, %1, %2, %0;" : "+l"(a[i]) : "r"(b[i]), "r"(m));
+      const u32 x = (u32)a[(i + 5) & 15];
+      if (FORM == 1) {
+        asm volatile("mad.wide.u32 %0, %1, %2, %0;" : "+l"(a[i]) : "r"(x), "r"(m));
+      } else if (FORM == 2) {
+        asm volatile("mul.wide.u32 %0, %1, %2;" : "=l"(a[i]) : "r"(x), "r"(m));
       } else {
-        asm volatile("mad.lo.u32 %0, %0, %1, %2;" : "+r"(b[i]) : "r"(m), "r"((u32)it));
+        u32 l = (u32)a[i];
+        asm volatile("mad.lo.u32 %0, %1, %2, %0;" : "+r"(l) : "r"(x), "r"(m));
+        a[i] = (a[i] & 0xffffffff00000000ull) | l;
       }
     }
   }
   u64 acc = 0;
 #pragma unroll
-  for (int i = 0; i < 16; ++i) acc += a[i] + b[i];
+  for (int i = 0; i < 16; ++i) acc += a[i];
   if (acc == 0x123456789ull) *sink = acc;
 }
 }  // namespace
 
-double measure_int_peak(int wide) {
+double measure_int_peak(int form) {
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -1842,8 +1846,10 @@ double measure_int_peak(int wide) {
   double best = 0;
   for (int rep = 0; rep < 3; ++rep) {
     cudaEventRecord(e0);
-    if (wide)
+    if (form == 1)
       k_int_peak<1><<<blocks, threads>>>(iters, 7u + rep, sink);
+    else if (form == 2)
+      k_int_peak<2><<<blocks, threads>>>(iters, 7u + rep, sink);
     else
       k_int_peak<0><<<blocks, threads>>>(iters, 7u + rep, sink);
     cudaEventRecord(e1);

@@ -156,5 +156,6 @@ void launch_mask(const DevView& V, u64 seed, u64* ct, cudaStream_t st);
 cudaError_t kernels_init(int N);
 
 // Measured throughput (operations per second over the whole GPU) of
-// 32x32->64 wide multiply-adds (wide = 1) or 32-bit multiply-adds (wide = 0).
-double measure_int_peak(int wide);
+// 32x32->64 wide multiply-adds into 64-bit sums (form 1), wide products
+// alone (form 2) or 32-bit multiply-adds (form 0).
+double measure_int_peak(int form);

@@ -44,6 +44,19 @@ WL_LARGE = dict(N=16384, prime_bits=[55] * 6 + [54] * 2, h=8, ell=128, lambda_ba
 # Table 3 for h = 5..8 (204 bits, four 51-bit primes)
 WL_PAPER_EXACT = dict(N=8192, prime_bits=[51] * 4, h=8, ell=24, lambda_bar=19, mu=526, m=1024, n=1 << 20,
                       planted=102, bits=32)
+# the batched and served configurations: server sets of several sizes on
+# contexts of both ring sizes and three Hamming weights; mu is the 2^-40
+# bin-load rule at each (n, b) (the paper's own value at 2^20 / 8192)
+P4, P8 = [55, 55, 54, 54], [55] * 6 + [54] * 2
+MIXED = [
+    # name, N, prime_bits, h, lambda_bar, ell, log2 n, mu
+    ("N=8192 h=2 n=2^16", 8192, P4, 2, 16, 363, 16, 74),
+    ("N=8192 h=4 n=2^20", 8192, P4, 4, 32, 600, 20, 526),  # the paper-shaped context and set
+    ("N=8192 h=8 n=2^22", 8192, P4, 8, 40, 128, 22, 1869),
+    ("N=16384 h=8 n=2^18", 16384, P8, 8, 40, 128, 18, 100),
+    ("N=16384 h=4 n=2^16", 16384, P8, 4, 32, 600, 16, 51),
+]
+SERVE_SETS = (1, 2, 3)  # resident sets of 2^20, 2^22 and 2^18 items, N = 8192 and 16384
 HASH_KEY, KEY_SEED, ENC_SEED = 0x5EED, 3, 4
 WORKLOAD_NAME = ("paper-shaped PSI: N=8192 bins, t=65537, q=4 RNS primes (55,55,54,54 bits), CW code ell=600 h=4, "
                  "mu=526 layers, 1024 client x 2^20 server uniform 64-bit items, 102 planted")
@@ -199,6 +212,217 @@ def run_reference(args):
     }
     print(json.dumps(line), flush=True)
     return 0
+
+
+# ------------------------------------------------ batched and served forms
+def mixed_contexts(pepsi, torch, main_ctx, main_sid):
+    """Contexts, server sets and requests of the batched and served
+    configurations (MIXED): every context rounds its layers once, switches
+    its response to one prime and is autotuned on one of its requests; four
+    distinct requests per set, client sizes log-uniform in [16, 4096] with a
+    tenth of each planted, encrypted straight into device memory.  The
+    paper-shaped context and set of the main measurement are reused."""
+    import math
+
+    import numpy as np
+
+    from paper_2310_14565_gb300.workload import make_sets
+
+    rng = np.random.default_rng(11)
+    out = []
+    for i, (name, N, bits, h, lb, ell, ln, mu) in enumerate(MIXED):
+        seed_items = 1 if (N, h, ln) == (WL["N"], WL["h"], 20) else 200 + i
+        if seed_items == 1:
+            ctx, sid = main_ctx, main_sid
+        else:
+            ctx = pepsi.Context(N=N, t=65537, prime_bits=bits, h=h, ell=ell, lambda_bar=lb, mu=mu, hash_key=HASH_KEY,
+                                key_seed=KEY_SEED, rescale_group=RESCALE["all"], response_primes=RESPONSE_PRIMES)
+            sid = ctx.server_load(make_sets(16, 1 << ln, 0, bits=64, seed_items=seed_items).server)
+        reqs, sizes = [], []
+        for j in range(4):
+            m = int(round(math.exp(rng.uniform(math.log(16), math.log(4096)))))
+            sets = make_sets(m, 1 << ln, max(1, m // 10), bits=64, seed_items=seed_items, seed_plant=300 + 10 * i + j)
+            cts = torch.empty((ell, 2, len(bits), N), dtype=torch.int64, device="cuda")
+            ctx.query(sets.client, 5000 + 10 * i + j, out=cts)
+            reqs.append(cts)
+            sizes.append(m)
+        if seed_items != 1:
+            ctx.autotune(sid, reqs[0])
+        out.append(dict(name=name, ctx=ctx, sid=sid, reqs=reqs, N=N, client_sizes=sizes,
+                        schedule=ctx.schedule()))
+    torch.cuda.synchronize()
+    return out
+
+
+def leg_batched(pepsi, torch, mixed, nq=64):
+    """Configuration 3: nq queries over the mixed sets (set, request, mode and
+    mask seed drawn at random), as nq sequential pepsi_eval calls on one
+    stream, and as one engine run (a lane of four slots per set, all queries
+    submitted at once).  Same outputs required; host wall clock for both."""
+    import numpy as np
+
+    rng = np.random.default_rng(12)
+    picks = [(int(rng.integers(len(mixed))), int(rng.integers(4)), int(rng.integers(2)), 50 + q) for q in range(nq)]
+
+    def buf(a):
+        return torch.zeros((2, RESPONSE_PRIMES, mixed[a]["N"]), dtype=torch.int64, device="cuda")
+
+    outs_seq = [buf(a) for a, _, _, _ in picks]
+    outs_eng = [buf(a) for a, _, _, _ in picks]
+    eng = pepsi.Engine([(m["ctx"], m["sid"], 4) for m in mixed])
+
+    def sequential():
+        for q, (a, r, mode, seed) in enumerate(picks):
+            m = mixed[a]
+            m["ctx"].eval(m["sid"], m["reqs"][r], mode=mode, mask_seed=seed, out=outs_seq[q])
+        torch.cuda.synchronize()
+
+    def engine():
+        tickets = [eng.submit(a, mixed[a]["reqs"][r], out=outs_eng[q], mode=mode, mask_seed=seed)[0]
+                   for q, (a, r, mode, seed) in enumerate(picks)]
+        eng.run()
+        for t in tickets:
+            eng.wait(t)
+
+    sequential()
+    engine()
+    times = {}
+    for name, f in (("sequential", sequential), ("engine", engine), ("sequential2", sequential), ("engine2", engine)):
+        t0 = time.perf_counter()
+        f()
+        times[name] = time.perf_counter() - t0
+    same = all(torch.equal(outs_seq[q], outs_eng[q]) for q in range(nq))
+    t_seq = min(times["sequential"], times["sequential2"])
+    t_eng = min(times["engine"], times["engine2"])
+    st = eng.stats()
+    eng.close()
+    per_set = {m["name"]: sum(1 for a, _, _, _ in picks if a == i) for i, m in enumerate(mixed)}
+    return {"queries": nq, "sets": per_set, "engine_queries_per_s": round(nq / t_eng, 2),
+            "sequential_queries_per_s": round(nq / t_seq, 2), "speedup": round(t_seq / t_eng, 3),
+            "engine_s": round(t_eng, 4), "sequential_s": round(t_seq, 4), "identical_outputs": bool(same),
+            "engine_peak_state_gb": round(st["bytes_peak"] / 1e9, 2), "lane_slots": 4,
+            "client_sizes": {m["name"]: m["client_sizes"] for m in mixed},
+            "schedules": {m["name"]: m["schedule"] for m in mixed},
+            "timing": "host wall clock over the whole batch, GPU synchronised at its end; best of two"}
+
+
+def leg_serve(pepsi, torch, mixed, total=120, loads=(0.5, 0.9, 1.5)):
+    """Configuration 5: Poisson arrivals over the resident sets of 2^20, 2^22
+    and 2^18 items (N = 8192, 8192, 16384; each arrival picks a set and one
+    of its four requests at random), at fractions of the sequential
+    capacity.  Sequential: one pepsi_eval at a time in arrival order,
+    synchronised.  Engine: the engine's thread serves submissions made at
+    the arrival times.  Latency = completion - scheduled arrival."""
+    import numpy as np
+
+    lanes = [mixed[a] for a in SERVE_SETS]
+    svc = []
+    for m in lanes:  # sequential service time per set
+        o = torch.zeros((2, RESPONSE_PRIMES, m["N"]), dtype=torch.int64, device="cuda")
+        m["ctx"].eval(m["sid"], m["reqs"][0], out=o)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for r in range(4):
+            m["ctx"].eval(m["sid"], m["reqs"][r], out=o)
+            torch.cuda.synchronize()
+        svc.append((time.perf_counter() - t0) / 4)
+    capacity = 1.0 / float(np.mean(svc))
+    eng = pepsi.Engine([(m["ctx"], m["sid"], 4) for m in lanes])
+    runs, identical = [], True
+    for li, load in enumerate(loads):
+        rng = np.random.default_rng(13 + li)
+        arrivals = np.cumsum(rng.exponential(1.0 / (load * capacity), size=total))
+        pick = rng.integers(len(lanes), size=total)
+        reqi = rng.integers(4, size=total)
+        seq_out = [torch.zeros((2, RESPONSE_PRIMES, lanes[pick[q]]["N"]), dtype=torch.int64, device="cuda")
+                   for q in range(total)]
+        eng_out = [torch.zeros_like(x) for x in seq_out]
+        torch.cuda.synchronize()
+        # sequential server
+        lat, t0 = [], time.perf_counter()
+        for q in range(total):
+            now = time.perf_counter() - t0
+            if arrivals[q] > now:
+                time.sleep(arrivals[q] - now)
+            m = lanes[pick[q]]
+            m["ctx"].eval(m["sid"], m["reqs"][reqi[q]], mode=q % 2, mask_seed=q, out=seq_out[q])
+            torch.cuda.synchronize()
+            lat.append(time.perf_counter() - t0 - arrivals[q])
+        span_seq = time.perf_counter() - t0
+        # the engine, continuous batching
+        eng.start()
+        tickets, late, t0 = [], [], time.perf_counter()
+        for q in range(total):
+            now = time.perf_counter() - t0
+            if arrivals[q] > now:
+                time.sleep(arrivals[q] - now)
+            late.append(max(0.0, time.perf_counter() - t0 - arrivals[q]))
+            m = lanes[pick[q]]
+            tickets.append(eng.submit(int(pick[q]), m["reqs"][reqi[q]], out=eng_out[q], mode=q % 2, mask_seed=q)[0])
+        lat_e = [late[q] + eng.wait(t) * 1e-3 for q, t in enumerate(tickets)]
+        span_eng = time.perf_counter() - t0
+        eng.stop()
+        identical &= all(torch.equal(seq_out[q], eng_out[q]) for q in range(total))
+        for policy, ls, span in (("sequential", lat, span_seq), ("engine", lat_e, span_eng)):
+            ms = np.array(ls) * 1e3
+            runs.append({"load": load, "policy": policy, "requests": total,
+                         "p50_ms": round(float(np.percentile(ms, 50)), 2),
+                         "p99_ms": round(float(np.percentile(ms, 99)), 2),
+                         "queries_per_s": round(total / span, 2)})
+    st = eng.stats()
+    eng.close()
+    return {"sets": [m["name"] for m in lanes], "sequential_service_ms": [round(x * 1e3, 3) for x in svc],
+            "capacity_queries_per_s": round(capacity, 2), "runs": runs, "identical_outputs": bool(identical),
+            "engine_peak_state_gb": round(st["bytes_peak"] / 1e9, 2),
+            "engine_budget_gb": round(st["budget"] / 1e9, 1), "lane_slots": 4,
+            "arrivals": "Poisson, rate = load x sequential capacity; set and request uniform; modes alternate"}
+
+
+def leg_large(pepsi, torch, steps=3, chunk=128):
+    """Configuration 4 (large) in the default line: N = 16384, eight primes,
+    h = 8, ell = 128, mu = 3487, 4096 client x 2^24 server items; the
+    resident prefix of the 468 GB table in 7-byte words, the rest
+    regenerated per chunk.  A few steps after one warm-up."""
+    from paper_2310_14565_gb300.workload import make_sets
+
+    W = WL_LARGE
+    N, k = W["N"], len(W["prime_bits"])
+    ctx = pepsi.Context(N=N, t=65537, prime_bits=W["prime_bits"], h=W["h"], ell=W["ell"],
+                        lambda_bar=W["lambda_bar"], mu=W["mu"], hash_key=HASH_KEY, key_seed=KEY_SEED,
+                        rescale_group=RESCALE["all"], response_primes=RESPONSE_PRIMES, plaintext_bytes=7)
+    ctx.set_schedule(chunk=chunk)
+    sets = make_sets(W["m"], W["n"], W["planted"], bits=64)
+    t0 = time.perf_counter()
+    sid = ctx.server_load(sets.server)
+    offline = time.perf_counter() - t0
+    cts = torch.empty((W["ell"], 2, k, N), dtype=torch.int64, device="cuda")
+    ctx.query(sets.client, ENC_SEED, out=cts)
+    out = torch.zeros((2, RESPONSE_PRIMES, N), dtype=torch.int64, device="cuda")
+    ctx.eval(sid, cts, out=out)
+    torch.cuda.synchronize()
+    slots, budget = ctx.decrypt(out)
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        ctx.eval(sid, cts, out=out)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    ctx.profile(True)
+    ctx.eval(sid, cts, out=out)
+    prof = ctx.profile_read()
+    ctx.profile(False)
+    total_ms = sum(v[1] for v in prof.values())
+    res = {"workload": "N=16384, 8 primes (55x6, 54x2), h=8, ell=128, mu=3487, 4096 client x 2^24 server items, "
+                       "41 planted; 7-byte resident prefix, the rest regenerated per chunk",
+           "ms_per_step": round(ms, 1), "steps": steps, "layer_chunk": chunk,
+           "correct": bool(int(slots.sum()) == W["planted"] and budget > 0), "noise_budget_bits": round(budget, 2),
+           "offline_server_load_s": round(offline, 2),
+           "ptgen_share": round(prof["ptgen"][1] / total_ms, 3) if total_ms else None,
+           "kernel_ms_per_step": {n: round(v[1], 2) for n, v in prof.items() if v[0]}}
+    ctx.close()
+    return res
 
 
 # --------------------------------------------------------------- our arm
@@ -435,14 +659,21 @@ def run_ours(args):
     ntt_ms = e0.elapsed_time(e1) / 10
     ntt_gbs = 2 * 8 * N * k * count / (ntt_ms * 1e-3) / 1e9
 
-    # integer-pipe peaks (measured here) and the MAC's use of the wide multiply-add:
-    # 2 components x 3 Karatsuba split products per plaintext word
-    wide_peak = pepsi.int_peak(True)
-    mad32_peak = pepsi.int_peak(False)
+    # integer-pipe peaks (measured here, multipliers that change every step) and the
+    # MAC's use of the wide multiply-add: 2 components x 3 Karatsuba split products
+    # per plaintext word and request
+    wide_peak = pepsi.int_peak(pepsi.INT_MAD_WIDE)
+    mul_peak = pepsi.int_peak(pepsi.INT_MUL_WIDE)
+    mad32_peak = pepsi.int_peak(pepsi.INT_MAD_LO)
     mac_wide_rate = 6.0 * mu * ell * k * N / (mac_launch_ms * 1e-3)
-    int_pipe = {"mad_wide_u32_per_s": round(wide_peak / 1e12, 3), "mad_u32_per_s": round(mad32_peak / 1e12, 3),
-                "unit": "T ops/s", "mac_mad_wide_frac": round(mac_wide_rate / wide_peak, 4),
-                "note": "k_mac issues 6 mad.wide.u32 per plaintext word (2 components x 3 Karatsuba split products)"}
+    bmac_ms = batched["kernel_ms_per_call"].get("mac", 0.0)
+    bmac_rate = 6.0 * nbq * mu * ell * k * N / (bmac_ms * 1e-3) if bmac_ms else 0.0
+    int_pipe = {"mad_wide_u32_per_s": round(wide_peak / 1e12, 3), "mul_wide_u32_per_s": round(mul_peak / 1e12, 3),
+                "mad_u32_per_s": round(mad32_peak / 1e12, 3), "unit": "T ops/s",
+                "mac_mad_wide_frac": round(mac_wide_rate / wide_peak, 4),
+                "batched_mac_mad_wide_frac": round(bmac_rate / wide_peak, 4),
+                "note": "the MACs issue 6 mad.wide.u32 per plaintext word and request (2 components x 3 Karatsuba "
+                        "split products); peaks measured with multipliers that change every step"}
 
     line = {
         "metric": METRIC, "value": round(ms, 3), "unit": "ms", "n_gpus": args.gpus, "steps": args.steps,
@@ -470,14 +701,31 @@ def run_ours(args):
                 "d2h_bytes_per_step": int(out_pinned.numel() * 8)},
         "batched": batched,
         "int_pipe": int_pipe,
+        "schedule": ctx.schedule(),
         "gpu_launches": int(launches),
         "clocks": clk,
     }
+    extra = args.case == "paper" and not args.no_extra_legs and ws == 1
+    if extra:
+        # configurations 3 and 5 (batched and served), then 4 (large) after
+        # the paper-shaped tables are released
+        mixed = mixed_contexts(pepsi, torch, ctx, sid)
+        line["batched_mixed"] = leg_batched(pepsi, torch, mixed)
+        line["serving"] = leg_serve(pepsi, torch, mixed)
+        for m in mixed:
+            if m["ctx"] is not ctx:
+                m["ctx"].close()
+        del mixed
+    ctx.close()
+    if extra:
+        del cts_dev, cts_pinned, out_dev, out_pinned
+        torch.cuda.synchronize()
+        torch.cuda.empty_cache()
+        line["large"] = leg_large(pepsi, torch)
     if rank == 0 and args.gpus == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.rescale == "all")
     if rank == 0:
         print(json.dumps(line), flush=True)
-    ctx.close()
     if ws > 1:
         torch.distributed.destroy_process_group()
     return 0
@@ -673,6 +921,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extra-legs", action="store_true",
+                    help="skip the batched (64 mixed queries), serving and large legs of the default run")
     ap.add_argument("--plaintext-bytes", type=int, choices=[0, 7, 8], default=0,
                     help="storage of the resident plaintexts per word: 8 (64-bit words) or 7 (three planes); "
                          "0: 7 for the large case, whose table is only partly resident, else 8")

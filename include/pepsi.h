@@ -188,6 +188,9 @@ typedef struct {
                            1 = every thread serves all requests of the group (fewer, fuller
                            warps), 2 = two groups of warps serve half the requests each
                            (twice the warps; groups of 3 requests always run with 1) */
+  uint32_t batch_requests;/* most requests that share one multiply-accumulate launch in
+                           pepsi_eval_batch and in an engine step (several launches when
+                           more are in flight): 0 = the default (2), else 1..4 */
 } pepsi_schedule;
 
 /* Read or set the schedule of later evaluations on this context
@@ -260,19 +263,25 @@ int pepsi_eval(pepsi_ctx* ctx, int set_id, const uint64_t* cts, int mode, uint64
 
 /* Autotuning of the evaluation schedule (no counterpart in the paper):
  * evaluates the request cts ([B][ell][2][k][N], host or device) against
- * set_id with circuit chunks of 32, 64, 128 and 256 layers (stopping at
- * the first whose scratch does not fit in memory), times two evaluations
- * of each with CUDA events on the stream, and keeps the fastest chunk for
- * later evaluations on this context (*chosen, may be NULL).  Larger chunks
- * fill the GPU with more blocks per launch.  The
- * result words do not depend on the chunk.  Synchronises the stream.
- * Errors: as pepsi_eval. */
+ * set_id, timing two evaluations after a warm-up with CUDA events on the
+ * stream for each candidate, and keeps the fastest schedule for later
+ * evaluations on this context (pepsi_get_schedule reads it), one field at a
+ * time: the circuit chunk (32, 64, 128, 256 layers, stopping at the set's
+ * mu, at 4 GiB of chunk scratch, or at the first that does not fit in
+ * memory), then the threads per transform block (the default for N, half
+ * and twice it), then for h = 4 and 8 the fused against the stored
+ * relinearisation before the affine step, then the requests per shared
+ * multiply-accumulate launch (1, 2 or 4, timed on a batch of four copies of
+ * the request through pepsi_eval_batch).  *chosen (may be NULL) receives
+ * the chunk.  The result words do not depend on the schedule.
+ * Synchronises the stream.  Errors: as pepsi_eval. */
 int pepsi_autotune(pepsi_ctx* ctx, int set_id, const uint64_t* cts, void* stream, uint32_t* chosen);
 
 /* Several requests in one call: request i is evaluated against server set
  * set_ids[i] exactly as by pepsi_eval (same output words), with mode
  * modes[i] (NULL: all indicator) and mask seed mask_seeds[i] (NULL: 0).
- * Requests on the same set are processed in groups of up to 4 whose
+ * Requests on the same set are processed in groups of up to
+ * pepsi_schedule.batch_requests (at most 4) whose
  * multiply-accumulate reads the server plaintexts once for the whole group
  * (or generates each plaintext chunk once, when the table is not
  * resident); the next group's multiply-accumulate overlaps the current

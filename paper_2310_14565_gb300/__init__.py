@@ -58,7 +58,7 @@ class Info(C.Structure):
 
 class Schedule(C.Structure):
     _fields_ = [("chunk", C.c_uint32), ("ntt_threads", C.c_uint32), ("relin_fused", C.c_uint32),
-                ("batch_points", C.c_uint32), ("batch_groups", C.c_uint32)]
+                ("batch_points", C.c_uint32), ("batch_groups", C.c_uint32), ("batch_requests", C.c_uint32)]
 
 
 class LaneDesc(C.Structure):
@@ -284,9 +284,11 @@ class Context:
         sc = Schedule()
         _check(lib().pepsi_get_schedule(self._h, C.byref(sc)), "pepsi_get_schedule")
         return {"chunk": int(sc.chunk), "ntt_threads": int(sc.ntt_threads), "relin_fused": int(sc.relin_fused),
-                "batch_points": int(sc.batch_points), "batch_groups": int(sc.batch_groups)}
+                "batch_points": int(sc.batch_points), "batch_groups": int(sc.batch_groups),
+                "batch_requests": int(sc.batch_requests)}
 
-    def set_schedule(self, chunk=None, ntt_threads=None, relin_fused=None, batch_points=None, batch_groups=None):
+    def set_schedule(self, chunk=None, ntt_threads=None, relin_fused=None, batch_points=None, batch_groups=None,
+                     batch_requests=None):
         """Change fields of the evaluation schedule (None keeps a field);
         the result words never depend on it."""
         cur = self.schedule()
@@ -296,6 +298,7 @@ class Context:
         sc.relin_fused = cur["relin_fused"] if relin_fused is None else int(relin_fused)
         sc.batch_points = cur["batch_points"] if batch_points is None else int(batch_points)
         sc.batch_groups = cur["batch_groups"] if batch_groups is None else int(batch_groups)
+        sc.batch_requests = cur["batch_requests"] if batch_requests is None else int(batch_requests)
         _check(lib().pepsi_set_schedule(self._h, C.byref(sc)), "pepsi_set_schedule")
 
     # ---- server side

@@ -107,6 +107,7 @@ struct pepsi_ctx {
   bool relin_fused = true;  // key-switching sum on the load of the affine step's inverse NTT
   int batch_points = 32;    // points per block of the multi-request multiply-accumulate
   int batch_groups = 2;     // warp groups of the multi-request multiply-accumulate
+  int batch_requests = 2;   // most requests per shared multiply-accumulate launch
   u32 rescale_cap = 1;      // most layers one rounding of the last products may cover
   bool value_margin = false;  // B also holds the value products under lazy rescaling
   int resp = 0;               // primes of the evaluation's response (k: no switching)

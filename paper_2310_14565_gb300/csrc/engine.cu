@@ -3,8 +3,9 @@
 // (contract in include/pepsi.h, pepsi_engine_*).
 //
 // A lane step takes the next chunk [pos, pos + L) of the set's layers.  The
-// multiply-accumulate of the chunk runs once for every request in the lane
-// (one read of the chunk's plaintexts), then each request's equality
+// multiply-accumulate of the chunk runs for the lane's requests in launches
+// of up to the schedule's batch_requests (one read of the chunk's
+// plaintexts per launch), then each request's equality
 // circuits (Algorithm 1) and its share of the layer sum (Algorithm 2) run on
 // the lane's stream.  A request that joins at layer p sees layers p .. mu-1,
 // then 0 .. p-1: its layer sum is the same sum in another order, which is
@@ -183,10 +184,11 @@ int enqueue_step(Lane& L, Step& step) {
     }
     P = plain_words(L.b.Pc);
   }
-  {
+  for (int q0 = 0; q0 < na; q0 += c->batch_requests) {  // launches of at most batch_requests requests
     Prof p(c, PC_MAC, st);
-    const cudaError_t me = mac_status(launch_mac_requests(c->V, na, Cs, P, Hs, c->ell, nl, c->mac_fold, c->d_err, st,
-                                                          c->batch_points, c->batch_groups));
+    const int nq = std::min(c->batch_requests, na - q0);
+    const cudaError_t me = mac_status(launch_mac_requests(c->V, nq, Cs + q0, P, Hs + q0, c->ell, nl, c->mac_fold,
+                                                          c->d_err, st, c->batch_points, c->batch_groups));
     if (me != cudaSuccess) return cuda_status(me);
   }
   for (int i = 0; i < na; ++i) {

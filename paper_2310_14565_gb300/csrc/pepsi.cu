@@ -423,8 +423,8 @@ cudaError_t ensure_copy_stream(pepsi_ctx* c) {
 
 // scratch id of the lazy-rescaling run sum of a single request
 constexpr int kScratchAccX = 46;
-// scratch id of the autotuner's response buffer
-constexpr int kScratchTune = 48;
+// scratch ids of the autotuner's response buffers
+constexpr int kScratchTune = 48, kScratchTuneBatch = 49;
 
 // Core of pepsi_eval / pepsi_eval_layers.
 int eval_core(pepsi_ctx* c, int set_id, const u64* cts, u32 layer0, u32 nl, int mode, u64 mask_seed, u64* out_ct,
@@ -552,7 +552,7 @@ int eval_core(pepsi_ctx* c, int set_id, const u64* cts, u32 layer0, u32 nl, int 
 }
 
 // Core of pepsi_eval_batch: requests grouped by server set, up to
-// PEPSI_MAC_MAX_REQUESTS per group; each group's multiply-accumulate reads
+// batch_requests (at most PEPSI_MAC_MAX_REQUESTS) per group; each group's multiply-accumulate reads
 // the plaintexts once (resident table) or generates each chunk once
 // (streamed table); the equality circuits then run request by request.
 // With a resident table the multiply-accumulate of the next group runs on
@@ -578,7 +578,7 @@ int eval_batch_core(pepsi_ctx* c, int nq, const int* set_ids, const u64* const* 
     for (int i0 = 0; i0 < nq; ++i0) {
       if (done[i0]) continue;
       std::vector<int> grp;
-      for (int i = i0; i < nq && (int)grp.size() < PEPSI_MAC_MAX_REQUESTS; ++i)
+      for (int i = i0; i < nq && (int)grp.size() < c->batch_requests; ++i)
         if (!done[i] && set_ids[i] == set_ids[i0]) grp.push_back(i);
       for (int i : grp) done[i] = 1;
       groups.push_back(grp);
@@ -783,6 +783,7 @@ pepsi_ctx* ctx_fork(const pepsi_ctx* p, cudaError_t* err) {
   c->relin_fused = p->relin_fused;
   c->batch_points = p->batch_points;
   c->batch_groups = p->batch_groups;
+  c->batch_requests = p->batch_requests;
   c->rescale_cap = p->rescale_cap;
   c->value_margin = p->value_margin;
   c->resp = p->resp;
@@ -1193,6 +1194,7 @@ int pepsi_get_schedule(const pepsi_ctx* c, pepsi_schedule* out) {
   out->relin_fused = c->relin_fused ? 1u : 0u;
   out->batch_points = (uint32_t)c->batch_points;
   out->batch_groups = (uint32_t)c->batch_groups;
+  out->batch_requests = (uint32_t)c->batch_requests;
   return PEPSI_OK;
 }
 
@@ -1201,10 +1203,11 @@ int pepsi_set_schedule(pepsi_ctx* c, const pepsi_schedule* s) {
   const u32 nt = s->ntt_threads;
   if (nt && (nt < 64 || nt > 1024 || (nt & (nt - 1)))) return PEPSI_E_PARAM;
   if (s->batch_points != 0 && s->batch_points != 32 && s->batch_points != 64) return PEPSI_E_PARAM;
-  if (s->batch_groups > 2) return PEPSI_E_PARAM;
+  if (s->batch_groups > 2 || s->batch_requests > (uint32_t)PEPSI_MAC_MAX_REQUESTS) return PEPSI_E_PARAM;
   c->chunk = (int)s->chunk;
   c->batch_points = s->batch_points ? (int)s->batch_points : 32;
   c->batch_groups = s->batch_groups ? (int)s->batch_groups : 2;
+  c->batch_requests = s->batch_requests ? (int)s->batch_requests : 2;
   c->V.nt = (int)nt;
   c->relin_fused = s->relin_fused != 0;
   return PEPSI_OK;
@@ -1465,39 +1468,114 @@ int pepsi_autotune(pepsi_ctx* c, int set_id, const uint64_t* cts, void* stream, 
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   CKS(cudaEventCreate(&e0));
   CKS(cudaEventCreate(&e1));
-  const int saved = c->chunk;
-  int best = saved;
-  float best_ms = 0;
-  int rc = PEPSI_OK;
-  for (int chunk : {32, 64, 128, 256}) {
-    c->chunk = chunk;
-    for (int rep = 0; rep < 3 && !rc; ++rep) {  // one warm-up, two timed
+  const pepsi_schedule saved{(uint32_t)c->chunk, (uint32_t)c->V.nt, c->relin_fused ? 1u : 0u,
+                             (uint32_t)c->batch_points, (uint32_t)c->batch_groups, (uint32_t)c->batch_requests};
+  // ms of two evaluations after a warm-up under the current schedule (< 0: error code)
+  auto time_it = [&](float* ms) -> int {
+    int rc = PEPSI_OK;
+    for (int rep = 0; rep < 3 && !rc; ++rep) {
       if (rep == 1) cudaEventRecord(e0, st);
       rc = pepsi_eval(c, set_id, cts, PEPSI_MODE_INDICATOR, 0, out, st);
     }
+    if (rc) return rc;
+    cudaEventRecord(e1, st);
+    cudaError_t ce = cudaEventSynchronize(e1);
+    if (ce == cudaSuccess) ce = cudaEventElapsedTime(ms, e0, e1);
+    return ce == cudaSuccess ? PEPSI_OK : cuda_status(ce);
+  };
+  // circuit scratch per layer of a chunk: the pipeline's buffers (eval_bufs)
+  const size_t kN = (size_t)c->k * c->N, kbN = (size_t)c->kb * c->N;
+  const size_t per_layer = (24 * kN + 7 * kbN) * 8;
+  const size_t scratch_cap = (size_t)4 << 30;
+  int rc = PEPSI_OK;
+  float best_ms = 0;
+  // 1: the layer chunk (larger chunks fill the GPU with more blocks per launch)
+  int best_chunk = c->chunk;
+  for (int chunk : {32, 64, 128, 256}) {
+    if (chunk > 32 && (size_t)chunk * per_layer > scratch_cap) break;
+    c->chunk = chunk;
+    float ms = 0;
+    rc = time_it(&ms);
     if (rc == PEPSI_E_NOMEM && best_ms > 0) {  // this chunk's scratch does not fit: keep the best so far
       cudaGetLastError();
       rc = PEPSI_OK;
       break;
     }
     if (rc) break;
-    cudaEventRecord(e1, st);
-    e = cudaEventSynchronize(e1);
-    float ms = 0;
-    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
-    if (e != cudaSuccess) {
-      rc = cuda_status(e);
-      break;
-    }
     if (best_ms == 0 || ms < best_ms) {
       best_ms = ms;
-      best = chunk;
+      best_chunk = chunk;
     }
+    if ((u32)chunk >= G->mu) break;  // larger chunks run the same launches
   }
-  c->chunk = rc ? saved : best;
+  c->chunk = best_chunk;
+  // 2: threads per transform block (the default, half and twice it)
+  if (!rc) {
+    const int def = c->N >= 16384 ? 1024 : std::max(32, std::min(512, c->N / 8));
+    int best_nt = 0;
+    for (int nt : {def / 2, def * 2}) {
+      if (nt < 64 || nt > 1024) continue;
+      c->V.nt = nt;
+      float ms = 0;
+      rc = time_it(&ms);
+      if (rc) break;
+      if (ms < best_ms) {
+        best_ms = ms;
+        best_nt = nt;
+      }
+    }
+    c->V.nt = best_nt;
+  }
+  // 3: the relinearisation feeding the affine step: fused with its transform, or stored
+  if (!rc && (c->h == 4 || c->h == 8)) {
+    c->relin_fused = false;
+    float ms = 0;
+    rc = time_it(&ms);
+    if (!rc && ms < best_ms) best_ms = ms;
+    else c->relin_fused = true;
+  }
+  // 4: requests per shared multiply-accumulate, on a batch of four copies of the request
+  if (!rc && G->blk.size() == 1) {
+    std::vector<u64*> outs(4, nullptr);
+    u64* ob = (u64*)scratch(c, kScratchTuneBatch, 4 * response_block_words(c) * 8, &e);
+    if (!ob) rc = cuda_status(e);
+    for (int i = 0; i < 4 && !rc; ++i) outs[i] = ob + (size_t)i * response_block_words(c);
+    const int ids[4] = {set_id, set_id, set_id, set_id};
+    const u64* in[4] = {cts, cts, cts, cts};
+    float best_b = 0;
+    int best_r = c->batch_requests;
+    for (int br : {1, 2, 4}) {
+      if (rc) break;
+      c->batch_requests = br;
+      for (int rep = 0; rep < 3 && !rc; ++rep) {
+        if (rep == 1) cudaEventRecord(e0, st);
+        rc = pepsi_eval_batch(c, 4, ids, in, nullptr, nullptr, outs.data(), st);
+      }
+      if (rc) break;
+      cudaEventRecord(e1, st);
+      float ms = 0;
+      cudaError_t ce = cudaEventSynchronize(e1);
+      if (ce == cudaSuccess) ce = cudaEventElapsedTime(&ms, e0, e1);
+      if (ce != cudaSuccess) {
+        rc = cuda_status(ce);
+        break;
+      }
+      if (best_b == 0 || ms < best_b) {
+        best_b = ms;
+        best_r = br;
+      }
+    }
+    c->batch_requests = best_r;
+  }
+  if (rc) {
+    c->chunk = (int)saved.chunk;
+    c->V.nt = (int)saved.ntt_threads;
+    c->relin_fused = saved.relin_fused != 0;
+    c->batch_requests = (int)saved.batch_requests;
+  }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  if (!rc && chosen) *chosen = (uint32_t)best;
+  if (!rc && chosen) *chosen = (uint32_t)c->chunk;
   return rc;
 }
 

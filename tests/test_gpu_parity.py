@@ -261,12 +261,13 @@ def test_streamed_plaintexts_match_resident():
     assert np.array_equal(P[mu - 1, 3], oc.server_plaintext(Ts, mu - 1, 3))
 
 
-@pytest.mark.parametrize("batch_points", [32, 64])
+@pytest.mark.parametrize("batch_points,batch_requests", [(32, 4), (64, 4), (32, 2)])
 @pytest.mark.parametrize("resident", [True, False])
-def test_eval_batch_matches_single_calls_and_oracle(resident, batch_points):
-    """pepsi_eval_batch: two server sets, nine requests (groups of four and
-    three on one set, a group of two on the other, so the shared
-    multiply-accumulate runs for 4, 3 and 2 requests), mixed modes and
+def test_eval_batch_matches_single_calls_and_oracle(resident, batch_points, batch_requests):
+    """pepsi_eval_batch: two server sets, nine requests (with up to four
+    requests per shared multiply-accumulate: groups of four and three on one
+    set and of two on the other, so the shared multiply-accumulate runs for
+    4, 3 and 2 requests; with up to two: pairs and a single), mixed modes and
     seeds, both tile widths of the shared multiply-accumulate; every output
     equals the single-request call and the oracle."""
     import oracle
@@ -282,7 +283,7 @@ def test_eval_batch_matches_single_calls_and_oracle(resident, batch_points):
         oc, gc, s, rlk = pair(N, bits, h, lb, mu=mu, resident_bytes=0 if resident else (1 << 64) - 1)
     finally:
         os.environ.pop("PEPSI_CHUNK", None)
-    gc.set_schedule(batch_points=batch_points)
+    gc.set_schedule(batch_points=batch_points, batch_requests=batch_requests)
     sA, sB = gc.server_load(setsA.server), gc.server_load(setsB.server)
     _, TA, _ = oc.server_table(setsA.server)
     _, TB, _ = oc.server_table(setsB.server)

@@ -668,12 +668,28 @@ def run_ours(args):
     mac_wide_rate = 6.0 * mu * ell * k * N / (mac_launch_ms * 1e-3)
     bmac_ms = batched["kernel_ms_per_call"].get("mac", 0.0)
     bmac_rate = 6.0 * nbq * mu * ell * k * N / (bmac_ms * 1e-3) if bmac_ms else 0.0
+    # the circuit kernels' share of the heavy multiply-add pipe: busy SM-cycles per
+    # evaluation (full-size ncu counters) over this run's CUDA-event time of the class
+    cyc = stored_pipe_cycles() if pbytes == 8 and args.rescale == "all" else None
+    circuits = None
+    if cyc:
+        clock_hz = (clk.get("sm_mhz") or 2070.0) * 1e6
+        sms = torch.cuda.get_device_properties(0).multi_processor_count
+        circuits = {}
+        for cls in ("ntt", "lift", "tensor", "scale_round", "relin", "mac"):
+            launches_c, ms_c = prof.get(cls, (0, 0.0))
+            if cls in cyc and ms_c > 0:
+                per_eval_s = ms_c / psteps * 1e-3
+                circuits[cls] = round(cyc[cls] / (per_eval_s * clock_hz * sms), 3)
     int_pipe = {"mad_wide_u32_per_s": round(wide_peak / 1e12, 3), "mul_wide_u32_per_s": round(mul_peak / 1e12, 3),
                 "mad_u32_per_s": round(mad32_peak / 1e12, 3), "unit": "T ops/s",
                 "mac_mad_wide_frac": round(mac_wide_rate / wide_peak, 4),
                 "batched_mac_mad_wide_frac": round(bmac_rate / wide_peak, 4),
+                "circuits_heavy_pipe_busy": circuits,
                 "note": "the MACs issue 6 mad.wide.u32 per plaintext word and request (2 components x 3 Karatsuba "
-                        "split products); peaks measured with multipliers that change every step"}
+                        "split products); peaks measured with multipliers that change every step; "
+                        "circuits_heavy_pipe_busy: fraction of the SMs' heavy multiply-add pipe cycles each kernel "
+                        "class keeps busy (profiles/circuit_pipes_paper.md counters / this run's event times)"}
 
     line = {
         "metric": METRIC, "value": round(ms, 3), "unit": "ms", "n_gpus": args.gpus, "steps": args.steps,
@@ -896,6 +912,37 @@ def stored_traffic():
             kv = dict(f.split("=") for f in line.split()[1:])
             if kv.get("kernel_rev") == prof_rev():
                 return int(kv["traffic_bytes_per_launch"])
+    return None
+
+
+def kernels_rev():
+    """Identity of all device code (kernels.cu, ntt_block.cuh, common.cuh),
+    comments and blank lines removed: stored pipe counters apply while it
+    matches."""
+    import hashlib
+    import re
+
+    h = hashlib.sha256()
+    for f in ("kernels.cu", "ntt_block.cuh", "common.cuh"):
+        text = open(os.path.join(ROOT, "paper_2310_14565_gb300", "csrc", f)).read()
+        code = [re.sub(r"//.*$", "", ln).rstrip() for ln in text.splitlines()]
+        h.update("\n".join(ln for ln in code if ln).encode())
+    return h.hexdigest()[:16]
+
+
+def stored_pipe_cycles():
+    """Busy SM-cycles of the heavy multiply-add pipe per evaluation and kernel
+    class, from the committed full-size ncu summary, if it was taken on the
+    current device code (else None)."""
+    path = os.path.join(ROOT, "profiles", "circuit_pipes_paper.md")
+    if not os.path.exists(path) or WL["mu"] != 526:
+        return None
+    for line in open(path):
+        if line.startswith("machine-readable:"):
+            kv = dict(f.split("=") for f in line.split()[1:])
+            if kv.pop("kernel_rev", None) != kernels_rev():
+                return None
+            return {c: int(v.split(",")[0]) for c, v in kv.items()}
     return None
 
 

@@ -479,6 +479,32 @@ int pepsi_engine_wait(pepsi_engine* e, uint64_t ticket, double* latency_ms);
 /* Counters of the engine. */
 int pepsi_engine_get_stats(pepsi_engine* e, pepsi_engine_stats* out);
 
+/* The batched form under a captured CUDA graph (no counterpart in the
+ * paper).  Captures the evaluation of every request submitted and not yet
+ * admitted into one graph: the engine schedules them exactly as
+ * pepsi_engine_run would (slots and budget, lane steps), but queues the
+ * whole schedule without waiting for the GPU, inside a stream capture
+ * forked from `stream` (NULL: a stream of the graph) into every lane's
+ * stream and joined back.  Nothing runs until pepsi_graph_launch; the
+ * captured requests' tickets are done when this call returns.  Each launch
+ * reads the same request buffers and writes the same output buffers again,
+ * so refilling the request buffers and launching evaluates new requests of
+ * the same shapes.  The requests must use device buffers; the engine's
+ * thread must be stopped and no request may be in flight.  A launch must
+ * not overlap another launch of a graph of the same engine or the engine's
+ * own work (they share the lanes' scratch).  Errors: PEPSI_E_PARAM,
+ * PEPSI_E_NOMEM, PEPSI_E_CUDA. */
+typedef struct pepsi_graph pepsi_graph;
+int pepsi_engine_capture(pepsi_engine* e, void* stream, pepsi_graph** out);
+
+/* Launch a captured graph on `stream` (NULL: the graph's own stream).
+ * synchronize = 1: wait for it and return PEPSI_E_TIMEOUT if a bounded
+ * device wait of the evaluation expired. */
+int pepsi_graph_launch(pepsi_graph* g, void* stream, int synchronize);
+
+/* Wait for the graph's last launch and release it (NULL is ignored). */
+void pepsi_graph_destroy(pepsi_graph* g);
+
 /* Finish every request in flight, then release the engine and its lanes
  * (NULL is ignored). */
 void pepsi_engine_destroy(pepsi_engine* e);

@@ -117,6 +117,9 @@ SYMBOLS = {
     "pepsi_engine_wait": (C.c_int, [C.c_void_p, C.c_uint64, C.POINTER(C.c_double)]),
     "pepsi_engine_get_stats": (C.c_int, [C.c_void_p, C.POINTER(EngineStats)]),
     "pepsi_engine_destroy": (None, [C.c_void_p]),
+    "pepsi_engine_capture": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(C.c_void_p)]),
+    "pepsi_graph_launch": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int]),
+    "pepsi_graph_destroy": (None, [C.c_void_p]),
     "pepsi_destroy": (None, [C.c_void_p]),
     "pepsi_strerror": (C.c_char_p, [C.c_int]),
     "pepsi_last_error": (C.c_char_p, []),
@@ -538,6 +541,16 @@ class Engine:
         _check(rc, "pepsi_engine_wait")
         return ms.value
 
+    def capture(self, stream=None):
+        """Capture every submitted, not yet admitted request into one CUDA
+        graph (device buffers only); returns an EngineGraph.  The requests'
+        tickets are done; their outputs are written by each launch."""
+        g = C.c_void_p()
+        _check(lib().pepsi_engine_capture(self._h, _stream(stream), C.byref(g)), "pepsi_engine_capture")
+        held = list(self._held.values())
+        self._held.clear()
+        return EngineGraph(g, self, held)
+
     def stats(self):
         st = EngineStats()
         _check(lib().pepsi_engine_get_stats(self._h, C.byref(st)), "pepsi_engine_get_stats")
@@ -548,6 +561,28 @@ class Engine:
             lib().pepsi_engine_destroy(self._h)
             self._h = C.c_void_p()
         self._held.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class EngineGraph:
+    """A captured engine schedule: launch() replays it on its buffers."""
+
+    def __init__(self, handle, engine, held):
+        self._h, self._engine, self._held = handle, engine, held
+
+    def launch(self, stream=None, synchronize=True):
+        _check(lib().pepsi_graph_launch(self._h, _stream(stream), int(synchronize)), "pepsi_graph_launch")
+
+    def close(self):
+        if self._h:
+            lib().pepsi_graph_destroy(self._h)
+            self._h = C.c_void_p()
+        self._held = []
 
     def __del__(self):
         try:

@@ -102,6 +102,16 @@ struct pepsi_engine {
   std::mutex pump_mu;          // one pump at a time
 };
 
+// A captured engine schedule (pepsi_engine_capture).
+struct pepsi_graph {
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  cudaStream_t own = nullptr;  // capture and launch stream when the caller gives none
+  cudaStream_t last = nullptr; // stream of the last launch
+  int* err = nullptr;          // pinned: each lane's error word after the last launch
+  int nlanes = 0;
+};
+
 namespace {
 
 // Bytes of a request's device state on a lane (lazy: with its run sum).
@@ -156,7 +166,7 @@ void release(Slot& S, cudaStream_t st) {
 // Queue one step of the lane: the multiply-accumulate of the next chunk for
 // every busy slot, then each slot's circuits and layer sum; a slot that has
 // seen all layers also runs the output stage and is released.
-int enqueue_step(Lane& L, Step& step) {
+int enqueue_step(Lane& L, Step& step, bool capturing = false) {
   pepsi_ctx* c = L.c;
   cudaStream_t st = c->stream;
   ServerSet& S = c->sets[L.set];
@@ -221,6 +231,7 @@ int enqueue_step(Lane& L, Step& step) {
     }
   }
   L.pos = (L.pos + n) % L.mu;
+  if (capturing) return cuda_status(cudaGetLastError());  // completion is the graph's
   if (L.spare.empty()) {
     cudaEvent_t ev;
     const cudaError_t ce = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
@@ -514,6 +525,154 @@ int pepsi_engine_get_stats(pepsi_engine* e, pepsi_engine_stats* out) {
   out->bytes_peak = e->peak;
   out->budget = e->budget;
   return PEPSI_OK;
+}
+
+int pepsi_engine_capture(pepsi_engine* e, void* stream, pepsi_graph** out) {
+  if (!e || !out) return PEPSI_E_PARAM;
+  *out = nullptr;
+  std::lock_guard<std::mutex> pl(e->pump_mu);
+  std::vector<std::pair<int, u64>> routed;
+  {
+    std::lock_guard<std::mutex> lock(e->mu);
+    if (e->thread_on) return PEPSI_E_PARAM;
+    for (const Lane& L : e->lanes) {
+      if (!L.inflight.empty()) return PEPSI_E_PARAM;
+      for (int s = 0; s < L.nslots; ++s)
+        if (L.slot[s].busy) return PEPSI_E_PARAM;
+    }
+    for (u64 t : e->incoming) {  // captured requests read and write device memory only
+      const Request& r = e->reqs.at(t);
+      if (!is_device_ptr(r.cts) || !is_device_ptr(r.out)) return PEPSI_E_PARAM;
+    }
+    for (const Lane& L : e->lanes)
+      for (u64 t : L.queue)
+        if (!is_device_ptr(e->reqs.at(t).cts) || !is_device_ptr(e->reqs.at(t).out)) return PEPSI_E_PARAM;
+    while (!e->incoming.empty()) {
+      const u64 t = e->incoming.front();
+      e->incoming.pop_front();
+      routed.push_back({e->reqs.at(t).lane, t});
+    }
+  }
+  for (auto& rt : routed) e->lanes[rt.first].queue.push_back(rt.second);
+  auto* g = new pepsi_graph();
+  g->nlanes = (int)e->lanes.size();
+  cudaError_t err = cudaHostAlloc((void**)&g->err, g->nlanes * sizeof(int), 0);
+  if (err == cudaSuccess) memset(g->err, 0, g->nlanes * sizeof(int));
+  cudaStream_t origin = (cudaStream_t)stream;
+  if (err == cudaSuccess && !origin) {
+    err = cudaStreamCreateWithFlags(&g->own, cudaStreamNonBlocking);
+    origin = g->own;
+  }
+  cudaEvent_t fork = nullptr;
+  std::vector<cudaEvent_t> joins(e->lanes.size(), nullptr);
+  if (err == cudaSuccess) err = cudaEventCreateWithFlags(&fork, cudaEventDisableTiming);
+  for (auto& j : joins)
+    if (err == cudaSuccess) err = cudaEventCreateWithFlags(&j, cudaEventDisableTiming);
+  bool capturing = false;
+  if (err == cudaSuccess) err = cudaStreamBeginCapture(origin, cudaStreamCaptureModeRelaxed);
+  capturing = err == cudaSuccess;
+  if (err == cudaSuccess) err = cudaEventRecord(fork, origin);
+  for (Lane& L : e->lanes)
+    if (err == cudaSuccess) err = cudaStreamWaitEvent(L.c->stream, fork, 0);
+  int rc = err == cudaSuccess ? PEPSI_OK : cuda_status(err);
+  // the whole schedule, open loop: a request's state goes back to the budget
+  // as soon as its final step is queued (later steps of the graph reuse it)
+  std::vector<u64> captured;
+  for (bool work = true; work && rc == PEPSI_OK;) {
+    work = false;
+    for (Lane& L : e->lanes) {
+      for (int s = 0; s < L.nslots && !L.queue.empty() && rc == PEPSI_OK; ++s) {
+        if (L.slot[s].busy) continue;
+        const u64 t = L.queue.front();
+        Request r;
+        size_t bytes = 0;
+        {
+          std::lock_guard<std::mutex> lock(e->mu);
+          r = e->reqs.at(t);
+          bytes = request_bytes(L, rescale_run(L.c, L.mu, r.mode) > 1);
+          if (e->used + bytes > e->budget && e->used > 0) break;
+          e->used += bytes;
+          e->peak = std::max(e->peak, e->used);
+        }
+        L.queue.pop_front();
+        rc = admit(e, L, s, t, r, bytes);
+      }
+      bool busy = false;
+      for (int s = 0; s < L.nslots; ++s) busy |= L.slot[s].busy;
+      if (!busy || rc != PEPSI_OK) continue;
+      Step step;
+      rc = enqueue_step(L, step, true);
+      std::lock_guard<std::mutex> lock(e->mu);
+      ++e->steps;
+      e->used -= step.released;
+      for (u64 t : step.finishing) captured.push_back(t);
+      work = true;
+    }
+    for (const Lane& L : e->lanes) work |= !L.queue.empty();
+  }
+  // join every lane back to the origin; each lane's error word is read and cleared there
+  for (size_t i = 0; i < e->lanes.size() && rc == PEPSI_OK; ++i) {
+    pepsi_ctx* c = e->lanes[i].c;
+    err = cudaEventRecord(joins[i], c->stream);
+    if (err == cudaSuccess) err = cudaStreamWaitEvent(origin, joins[i], 0);
+    if (err == cudaSuccess) err = cudaMemcpyAsync(g->err + i, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, origin);
+    if (err == cudaSuccess) err = cudaMemsetAsync(c->d_err, 0, sizeof(int), origin);
+    if (err != cudaSuccess) rc = cuda_status(err);
+  }
+  if (capturing) {
+    const cudaError_t ee = cudaStreamEndCapture(origin, &g->graph);
+    if (rc == PEPSI_OK && ee != cudaSuccess) rc = cuda_status(ee);
+  }
+  if (rc == PEPSI_OK) {
+    err = cudaGraphInstantiate(&g->exec, g->graph, 0);
+    if (err != cudaSuccess) rc = cuda_status(err);
+  }
+  cudaEventDestroy(fork);
+  for (auto j : joins) cudaEventDestroy(j);
+  {  // the captured requests are handed over to the graph: their tickets are done
+    std::lock_guard<std::mutex> lock(e->mu);
+    const Clock::time_point now = Clock::now();
+    for (u64 t : captured) {
+      Request& r = e->reqs.at(t);
+      r.status = rc;
+      r.t_done = now;
+      ++e->completed;
+    }
+  }
+  e->cv.notify_all();
+  if (rc != PEPSI_OK) {
+    for (Lane& L : e->lanes)  // a failed capture leaves no request behind
+      for (int s = 0; s < L.nslots; ++s) L.slot[s] = Slot{};
+    pepsi_graph_destroy(g);
+    return rc;
+  }
+  *out = g;
+  return PEPSI_OK;
+}
+
+int pepsi_graph_launch(pepsi_graph* g, void* stream, int synchronize) {
+  if (!g || !g->exec) return PEPSI_E_PARAM;
+  cudaStream_t st = stream ? (cudaStream_t)stream : g->own;
+  if (!st) return PEPSI_E_PARAM;
+  cudaError_t err = cudaGraphLaunch(g->exec, st);
+  g->last = st;
+  if (err != cudaSuccess) return cuda_status(err);
+  if (!synchronize) return PEPSI_OK;
+  err = cudaStreamSynchronize(st);
+  if (err != cudaSuccess) return cuda_status(err);
+  for (int i = 0; i < g->nlanes; ++i)
+    if (g->err[i]) return PEPSI_E_TIMEOUT;
+  return PEPSI_OK;
+}
+
+void pepsi_graph_destroy(pepsi_graph* g) {
+  if (!g) return;
+  if (g->last) cudaStreamSynchronize(g->last);
+  if (g->exec) cudaGraphExecDestroy(g->exec);
+  if (g->graph) cudaGraphDestroy(g->graph);
+  if (g->own) cudaStreamDestroy(g->own);
+  if (g->err) cudaFreeHost(g->err);
+  delete g;
 }
 
 void pepsi_engine_destroy(pepsi_engine* e) {

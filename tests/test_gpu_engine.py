@@ -167,3 +167,40 @@ def test_engine_rejects_unsupported_lanes():
     with pytest.raises(pepsi.PepsiError):
         eng.submit(0, np.zeros((g1.ell, 2, g1.k, 64), np.uint64), mode=2)  # no values on this set
     eng.close()
+
+
+def test_engine_captured_graph_replays_with_new_requests():
+    """The batched form under one captured CUDA graph: requests on lanes of
+    two contexts captured at once, launched, then the request buffers are
+    refilled with other requests and the graph launched again; every output
+    equals the solo call on the requests of that launch."""
+    import paper_2310_14565_gb300 as pepsi
+
+    torch = torch_cuda()
+    c = _cases()
+    ocA, gA, rlkA, sA1, sA2, a1, a2, valsA, muA = c["A"]
+    ocB, gB, rlkB, sB1, b1, muB = c["B"]
+    eng = pepsi.Engine([(gA, a2, 2), (gB, b1, 3)])
+    first = _requests(gA, sA2, 3, 900) + _requests(gB, sB1, 4, 950)
+    second = _requests(gA, sA2, 3, 1900) + _requests(gB, sB1, 4, 1950)
+    lanes = [0] * 3 + [1] * 4
+    ctxs = [(gA, a2)] * 3 + [(gB, b1)] * 4
+    modes = [0, 1, 0, 1, 0, 1, 1]
+    dev = [torch.from_numpy(x.view(np.int64).copy()).cuda() for x in first]
+    outs = [torch.zeros(2 * g.response_primes * 64, dtype=torch.int64, device="cuda") for g, _ in ctxs]
+    torch.cuda.synchronize()
+    for i in range(len(dev)):
+        eng.submit(lanes[i], dev[i], out=outs[i], mode=modes[i], mask_seed=60 + i)
+    graph = eng.capture()
+    for reqs in (first, second):
+        for i, x in enumerate(reqs):
+            dev[i].copy_(torch.from_numpy(x.view(np.int64)))
+        torch.cuda.synchronize()
+        graph.launch()
+        for i, (g, sid) in enumerate(ctxs):
+            got = outs[i].cpu().numpy().view(np.uint64).reshape(2, g.response_primes, 64)
+            assert np.array_equal(got, g.eval(sid, reqs[i], mode=modes[i], mask_seed=60 + i)), i
+    st = eng.stats()
+    assert st["completed"] == len(dev)
+    graph.close()
+    eng.close()

@@ -257,8 +257,9 @@ def mixed_contexts(pepsi, torch, main_ctx, main_sid):
 def leg_batched(pepsi, torch, mixed, nq=64):
     """Configuration 3: nq queries over the mixed sets (set, request, mode and
     mask seed drawn at random), as nq sequential pepsi_eval calls on one
-    stream, and as one engine run (a lane of four slots per set, all queries
-    submitted at once).  Same outputs required; host wall clock for both."""
+    stream, as one engine run (a lane of four slots per set, all queries
+    submitted at once), and as that schedule captured into one CUDA graph
+    and replayed.  Same outputs required; host wall clock for all three."""
     import numpy as np
 
     rng = np.random.default_rng(12)
@@ -294,12 +295,28 @@ def leg_batched(pepsi, torch, mixed, nq=64):
     same = all(torch.equal(outs_seq[q], outs_eng[q]) for q in range(nq))
     t_seq = min(times["sequential"], times["sequential2"])
     t_eng = min(times["engine"], times["engine2"])
+    # the same batch's whole schedule captured into one CUDA graph and replayed
+    for q in range(nq):
+        outs_eng[q].zero_()
+    torch.cuda.synchronize()
+    for q, (a, r, mode, seed) in enumerate(picks):
+        eng.submit(a, mixed[a]["reqs"][r], out=outs_eng[q], mode=mode, mask_seed=seed)
+    graph = eng.capture()
+    graph.launch()
+    same_graph = all(torch.equal(outs_seq[q], outs_eng[q]) for q in range(nq))
+    t_graph = []
+    for _ in range(2):
+        t0 = time.perf_counter()
+        graph.launch()
+        t_graph.append(time.perf_counter() - t0)
+    graph.close()
     st = eng.stats()
     eng.close()
     per_set = {m["name"]: sum(1 for a, _, _, _ in picks if a == i) for i, m in enumerate(mixed)}
     return {"queries": nq, "sets": per_set, "engine_queries_per_s": round(nq / t_eng, 2),
             "sequential_queries_per_s": round(nq / t_seq, 2), "speedup": round(t_seq / t_eng, 3),
             "engine_s": round(t_eng, 4), "sequential_s": round(t_seq, 4), "identical_outputs": bool(same),
+            "graph_queries_per_s": round(nq / min(t_graph), 2), "graph_identical_outputs": bool(same_graph),
             "engine_peak_state_gb": round(st["bytes_peak"] / 1e9, 2), "lane_slots": 4,
             "client_sizes": {m["name"]: m["client_sizes"] for m in mixed},
             "schedules": {m["name"]: m["schedule"] for m in mixed},
@@ -414,9 +431,36 @@ def leg_large(pepsi, torch, steps=3, chunk=128):
     prof = ctx.profile_read()
     ctx.profile(False)
     total_ms = sum(v[1] for v in prof.values())
+    # four requests in one pepsi_eval_batch call: each regenerated plaintext chunk
+    # serves all four (one shared multiply-accumulate launch per chunk)
+    ctx.set_schedule(batch_requests=4)
+    reqs = [cts]
+    for i in range(3):
+        r = torch.empty_like(cts)
+        ctx.query(sets.client, ENC_SEED + 1 + i, out=r)
+        reqs.append(r)
+    bout = [torch.zeros_like(out) for _ in reqs]
+    sout = [torch.zeros_like(out) for _ in reqs]
+    e0.record(stream)
+    for i in range(4):
+        ctx.eval(sid, reqs[i], out=sout[i])
+    e1.record(stream)
+    torch.cuda.synchronize()
+    seq_ms = e0.elapsed_time(e1)
+    e0.record(stream)
+    ctx.eval_batch([sid] * 4, reqs, outs=bout)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    batch_ms = e0.elapsed_time(e1)
+    same = all(torch.equal(bout[i], sout[i]) for i in range(4))
     res = {"workload": "N=16384, 8 primes (55x6, 54x2), h=8, ell=128, mu=3487, 4096 client x 2^24 server items, "
                        "41 planted; 7-byte resident prefix, the rest regenerated per chunk",
            "ms_per_step": round(ms, 1), "steps": steps, "layer_chunk": chunk,
+           "batched": {"requests": 4, "ms_per_request": round(batch_ms / 4, 1),
+                       "sequential_ms_per_request": round(seq_ms / 4, 1), "speedup": round(seq_ms / batch_ms, 3),
+                       "identical_outputs": bool(same),
+                       "note": "pepsi_eval_batch with batch_requests = 4: one plaintext regeneration per chunk "
+                               "for the four requests"},
            "correct": bool(int(slots.sum()) == W["planted"] and budget > 0), "noise_budget_bits": round(budget, 2),
            "offline_server_load_s": round(offline, 2),
            "ptgen_share": round(prof["ptgen"][1] / total_ms, 3) if total_ms else None,

@@ -946,16 +946,21 @@ def run_serve(args):
 
 
 def stored_traffic():
-    """DRAM bytes per k_mac launch from the committed ncu summary, if it was
-    taken on the current kernel source (else None)."""
-    path = os.path.join(ROOT, "profiles", "k_mac_paper.md")
+    """DRAM bytes of one full k_mac launch, from the committed small-case
+    capture of the same kernel (35 layers) scaled by the layers it
+    processes: the plaintext reads and h' writes grow with the layers, the
+    request is read once per launch.  None unless the capture was taken on
+    the current kernel source."""
+    path = os.path.join(ROOT, "profiles", "k_mac_small_dram.md")
     if not os.path.exists(path) or WL["mu"] != 526:
         return None
     for line in open(path):
         if line.startswith("machine-readable:"):
             kv = dict(f.split("=") for f in line.split()[1:])
-            if kv.get("kernel_rev") == prof_rev():
-                return int(kv["traffic_bytes_per_launch"])
+            if kv.get("kernel_rev") != prof_rev():
+                return None
+            per_layer = (int(kv["traffic_bytes_per_launch"]) - int(kv["request_bytes"])) / int(kv["layers"])
+            return int(round(per_layer * WL["mu"] + int(kv["request_bytes"])))
     return None
 
 

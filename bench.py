@@ -867,12 +867,10 @@ def run_sweep_h(args):
 
 
 def run_serve(args):
-    """Serving on the paper-shaped workload (one resident set of 2^20
-    items): requests arrive as a Poisson process at 0.5 and 0.9 of the
-    measured sequential capacity (seeded exponential gaps), and are served
-    either one pepsi_eval at a time or by pepsi_eval_batch over all that are
-    waiting (up to 4).  Latency = completion - arrival, on the host clock;
-    the request ciphertexts are already on the device."""
+    """The served form alone (configuration 5): the paper-shaped context and
+    the other resident sets of the mixed configurations, Poisson arrivals at
+    several fractions of the sequential capacity, the engine's thread
+    against one pepsi_eval at a time; one JSON line."""
     import torch
 
     import paper_2310_14565_gb300 as pepsi
@@ -882,65 +880,22 @@ def run_serve(args):
     if not os.path.exists(pepsi.LIB_PATH):
         _build.build()
     torch.cuda.set_device(0)
-    N, k = WL["N"], len(WL["prime_bits"])
-    ctx = pepsi.Context(N=N, t=65537, prime_bits=WL["prime_bits"], h=WL["h"], ell=WL["ell"],
+    ctx = pepsi.Context(N=WL["N"], t=65537, prime_bits=WL["prime_bits"], h=WL["h"], ell=WL["ell"],
                         lambda_bar=WL["lambda_bar"], mu=WL["mu"], hash_key=HASH_KEY, key_seed=KEY_SEED,
                         rescale_group=RESCALE["all"], response_primes=RESPONSE_PRIMES)
     sets = make_sets(WL["m"], WL["n"], WL["planted"], bits=64)
     sid = ctx.server_load(sets.server)
-    nreq = 16  # distinct requests, reused round robin
-    reqs = [torch.from_numpy(ctx.query(sets.client, 1000 + i)[0].view("int64")).cuda() for i in range(nreq)]
-    outs = [torch.empty((2, RESPONSE_PRIMES, N), dtype=torch.int64, device="cuda") for _ in range(4)]
-    for _ in range(args.warmup):
-        ctx.eval(sid, reqs[0], out=outs[0])
-    torch.cuda.synchronize()
-    t = time.perf_counter()
-    for i in range(10):
-        ctx.eval(sid, reqs[i % nreq], out=outs[0])
-    torch.cuda.synchronize()
-    t_seq = (time.perf_counter() - t) / 10
-    import numpy as np
-
-    total = max(40, args.steps * 4)
-    runs = []
-    for load in (0.5, 0.9):
-        rate = load / t_seq
-        gaps = np.random.default_rng(7).exponential(1.0 / rate, size=total)
-        arrivals = np.cumsum(gaps)
-        for policy in ("single", "batch"):
-            lat = []
-            served, t0 = 0, time.perf_counter()
-            while served < total:
-                now = time.perf_counter() - t0
-                if arrivals[served] > now:
-                    time.sleep(min(arrivals[served] - now, 0.002))
-                    continue
-                if policy == "single":
-                    take = [served]
-                else:
-                    upto = min(total, served + 4)
-                    take = [i for i in range(served, upto) if arrivals[i] <= now]
-                if len(take) == 1:
-                    ctx.eval(sid, reqs[take[0] % nreq], out=outs[0])
-                else:
-                    ctx.eval_batch([sid] * len(take), [reqs[i % nreq] for i in take], outs=outs[:len(take)])
-                torch.cuda.synchronize()
-                done = time.perf_counter() - t0
-                lat += [done - arrivals[i] for i in take]
-                served += len(take)
-            span = time.perf_counter() - t0
-            lat_ms = np.array(lat) * 1e3
-            runs.append({"load": load, "policy": policy, "requests": total,
-                         "p50_ms": round(float(np.percentile(lat_ms, 50)), 2),
-                         "p99_ms": round(float(np.percentile(lat_ms, 99)), 2),
-                         "queries_per_s": round(total / span, 2)})
-    line = {"metric": "serving latency of pepsi_eval under Poisson arrivals (paper-shaped workload)", "unit": "ms",
-            "n_gpus": 1, "data": "synthetic",
-            "config": {"workload": WORKLOAD_NAME, "arrivals": "Poisson at 0.5 and 0.9 of sequential capacity",
-                       "rescale": RESCALE_NOTE["all"], "response": "switched to one prime"},
-            "sequential_ms_per_request": round(t_seq * 1e3, 3), "capacity_queries_per_s": round(1 / t_seq, 2),
-            "runs": runs}
+    cts = torch.from_numpy(ctx.query(sets.client, ENC_SEED)[0].view("int64")).cuda()
+    ctx.autotune(sid, cts)
+    mixed = mixed_contexts(pepsi, torch, ctx, sid)
+    res = leg_serve(pepsi, torch, mixed, total=max(120, args.steps * 4), loads=(0.5, 0.9, 1.2, 1.5))
+    line = {"metric": "serving latency and throughput under Poisson arrivals (configuration 5)", "unit": "ms",
+            "n_gpus": 1, "data": "synthetic", "config": {"workload": "resident sets " + ", ".join(res["sets"])},
+            **res}
     print(json.dumps(line), flush=True)
+    for m in mixed:
+        if m["ctx"] is not ctx:
+            m["ctx"].close()
     ctx.close()
     return 0
 

@@ -457,11 +457,15 @@ int pepsi_engine_submit(pepsi_engine* e, int lane, const uint64_t* cts, int mode
  * completed, admit queued requests into free slots within the budget, and
  * queue each busy lane's next steps (at most two ahead).  Never waits for
  * the GPU.  *pending (may be NULL): requests submitted and not yet done.
+ * A request whose admission or step fails is done with that error status
+ * (pepsi_engine_wait returns it) and the others are still served; the call
+ * returns the first such error of the pass.
  * Use either pepsi_engine_pump / pepsi_engine_run from one thread, or the
  * engine's own thread (pepsi_engine_start), not both. */
 int pepsi_engine_pump(pepsi_engine* e, uint64_t* pending);
 
-/* Pump until every request submitted so far is done. */
+/* Pump until every request submitted so far is done; returns the first
+ * failed request's status, else PEPSI_OK. */
 int pepsi_engine_run(pepsi_engine* e);
 
 /* Start / stop a thread of the engine that pumps continuously (it sleeps
@@ -471,10 +475,20 @@ int pepsi_engine_stop(pepsi_engine* e);
 
 /* Wait until a request is done (pumping from the calling thread when no
  * engine thread runs); returns its status (PEPSI_OK, PEPSI_E_TIMEOUT when a
- * bounded device wait of its steps expired, PEPSI_E_CUDA).  latency_ms (may
- * be NULL): from its submission to the engine seeing its last step
- * complete.  Errors: PEPSI_E_PARAM for an unknown ticket. */
+ * bounded device wait of its steps expired, PEPSI_E_NOMEM, PEPSI_E_CUDA).
+ * latency_ms (may be NULL): from its submission to the engine seeing its
+ * last step complete.  The engine forgets the ticket once this call has
+ * reported it (tickets that are never waited for keep a few bytes each
+ * until pepsi_engine_destroy).  Errors: PEPSI_E_PARAM for an unknown
+ * ticket. */
 int pepsi_engine_wait(pepsi_engine* e, uint64_t ticket, double* latency_ms);
+
+/* Failure test of the engine (no counterpart in the paper): the next
+ * admission on `lane` fails on the host with `status` (a PEPSI_E_* code)
+ * instead of running, as if allocating or uploading the request had
+ * failed.  That request is done with this status; the engine serves the
+ * others.  Errors: PEPSI_E_PARAM. */
+int pepsi_engine_fail_next(pepsi_engine* e, int lane, int status);
 
 /* Counters of the engine. */
 int pepsi_engine_get_stats(pepsi_engine* e, pepsi_engine_stats* out);

@@ -116,6 +116,7 @@ SYMBOLS = {
     "pepsi_engine_stop": (C.c_int, [C.c_void_p]),
     "pepsi_engine_wait": (C.c_int, [C.c_void_p, C.c_uint64, C.POINTER(C.c_double)]),
     "pepsi_engine_get_stats": (C.c_int, [C.c_void_p, C.POINTER(EngineStats)]),
+    "pepsi_engine_fail_next": (C.c_int, [C.c_void_p, C.c_int, C.c_int]),
     "pepsi_engine_destroy": (None, [C.c_void_p]),
     "pepsi_engine_capture": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(C.c_void_p)]),
     "pepsi_graph_launch": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int]),
@@ -550,6 +551,10 @@ class Engine:
         held = list(self._held.values())
         self._held.clear()
         return EngineGraph(g, self, held)
+
+    def fail_next(self, lane, status):
+        """Test hook: the lane's next admission fails on the host with status."""
+        _check(lib().pepsi_engine_fail_next(self._h, lane, status), "pepsi_engine_fail_next")
 
     def stats(self):
         st = EngineStats()

@@ -83,6 +83,7 @@ struct Lane {
   std::vector<cudaEvent_t> spare;
   int* err_ring = nullptr;  // pinned host words, one per queued step
   u64 nsteps = 0;
+  int fail_next = 0;        // test hook: the next admission reports this status instead of running
 };
 
 }  // namespace
@@ -130,6 +131,11 @@ cudaError_t pool_alloc(pepsi_engine* e, u64** p, size_t words, cudaStream_t st) 
 // Admit the head of the lane's queue into slot s (the engine lock is not
 // held: only the pumping thread touches lanes).
 int admit(pepsi_engine* e, Lane& L, int s, u64 ticket, const Request& r, size_t bytes) {
+  if (L.fail_next) {  // an injected failure, made on the host
+    const int rc = L.fail_next;
+    L.fail_next = 0;
+    return rc;
+  }
   pepsi_ctx* c = L.c;
   cudaStream_t st = c->stream;
   const size_t kN = (size_t)c->k * c->N;
@@ -281,6 +287,21 @@ int retire(pepsi_engine* e, Lane& L, bool* progressed) {
   return done;
 }
 
+// Complete a request with an error status: its slot's state goes back to the
+// pool and its bytes to the budget (a failed admission or step; the next
+// requests are still served).
+void fail_slot(pepsi_engine* e, Lane& L, int s, int status) {
+  Slot& S = L.slot[s];
+  release(S, L.c->stream);
+  std::lock_guard<std::mutex> lock(e->mu);
+  Request& r = e->reqs.at(S.ticket);
+  r.status = status;
+  r.t_done = Clock::now();
+  ++e->completed;
+  e->used -= S.bytes;
+  S = Slot{};
+}
+
 int pump_once(pepsi_engine* e, uint64_t* pending) {
   std::lock_guard<std::mutex> pl(e->pump_mu);
   bool progressed = false;
@@ -315,24 +336,37 @@ int pump_once(pepsi_engine* e, uint64_t* pending) {
           e->peak = std::max(e->peak, e->used);
         }
         L.queue.pop_front();
-        rc = admit(e, L, s, t, r, bytes);
+        const int arc = admit(e, L, s, t, r, bytes);
         progressed = true;
-        if (rc != PEPSI_OK) break;
+        if (arc != PEPSI_OK) {
+          if (rc == PEPSI_OK) rc = arc;
+          L.slot[s].ticket = t;
+          L.slot[s].bytes = bytes;
+          fail_slot(e, L, s, arc);
+          ++completed;
+        }
       }
       bool busy = false;
       for (int s = 0; s < L.nslots; ++s) busy |= L.slot[s].busy;
-      if (!busy || rc != PEPSI_OK) break;
+      if (!busy) break;
       Step step;
-      rc = enqueue_step(L, step);
+      const int src = enqueue_step(L, step);
       {
         std::lock_guard<std::mutex> lock(e->mu);
         ++e->steps;
       }
-      if (rc != PEPSI_OK) break;
+      if (src != PEPSI_OK) {  // the lane's requests in flight fail with the step
+        if (rc == PEPSI_OK) rc = src;
+        for (int s = 0; s < L.nslots; ++s)
+          if (L.slot[s].busy) {
+            fail_slot(e, L, s, src);
+            ++completed;
+          }
+        break;
+      }
       L.inflight.push_back(std::move(step));
       progressed = true;
     }
-    if (rc != PEPSI_OK) break;
   }
   {
     std::lock_guard<std::mutex> lock(e->mu);
@@ -452,11 +486,12 @@ int pepsi_engine_pump(pepsi_engine* e, uint64_t* pending) {
 
 int pepsi_engine_run(pepsi_engine* e) {
   if (!e) return PEPSI_E_PARAM;
+  int first = PEPSI_OK;  // the first failed request's status
   for (;;) {
     uint64_t pending = 0;
     const int rc = pump_once(e, &pending);
-    if (rc != PEPSI_OK) return rc;
-    if (!pending) return PEPSI_OK;
+    if (first == PEPSI_OK) first = rc;
+    if (!pending) return first;
     std::this_thread::sleep_for(std::chrono::microseconds(20));
   }
 }
@@ -506,13 +541,20 @@ int pepsi_engine_wait(pepsi_engine* e, uint64_t ticket, double* latency_ms) {
       else
         self_pump = true;
     }
-    if (self_pump) {
+    if (self_pump) {  // failures complete their requests: this one reports its own status
       uint64_t pending = 0;
-      const int rc = pump_once(e, &pending);
-      if (rc != PEPSI_OK) return rc;
+      pump_once(e, &pending);
       std::this_thread::sleep_for(std::chrono::microseconds(20));
     }
   }
+}
+
+int pepsi_engine_fail_next(pepsi_engine* e, int lane, int status) {
+  if (!e || lane < 0 || lane >= (int)e->lanes.size() || status <= PEPSI_OK || status > PEPSI_E_NOISE)
+    return PEPSI_E_PARAM;
+  std::lock_guard<std::mutex> pl(e->pump_mu);
+  e->lanes[lane].fail_next = status;
+  return PEPSI_OK;
 }
 
 int pepsi_engine_get_stats(pepsi_engine* e, pepsi_engine_stats* out) {
@@ -680,7 +722,8 @@ void pepsi_engine_destroy(pepsi_engine* e) {
   pepsi_engine_stop(e);
   for (int guard = 0; guard < 1000000; ++guard) {  // finish what is in flight
     uint64_t pending = 0;
-    if (pump_once(e, &pending) != PEPSI_OK || !pending) break;
+    pump_once(e, &pending);
+    if (!pending) break;
     std::this_thread::sleep_for(std::chrono::microseconds(50));
   }
   for (Lane& L : e->lanes) {

@@ -204,3 +204,40 @@ def test_engine_captured_graph_replays_with_new_requests():
     assert st["completed"] == len(dev)
     graph.close()
     eng.close()
+
+
+def test_engine_failed_request_reports_its_status_and_others_complete():
+    """A failure made on the host (the lane's next admission reports
+    E_NOMEM instead of running): that request's wait returns the status, the
+    engine's run returns it, and every other request, before and after it on
+    the same lane and on another lane, completes with the solo call's words;
+    the budget is given back."""
+    import paper_2310_14565_gb300 as pepsi
+
+    c = _cases()
+    ocA, gA, rlkA, sA1, sA2, a1, a2, valsA, muA = c["A"]
+    ocB, gB, rlkB, sB1, b1, muB = c["B"]
+    eng = pepsi.Engine([(gA, a2, 2), (gB, b1, 2)])
+    reqA = _requests(gA, sA2, 3, 1100)
+    reqB = _requests(gB, sB1, 2, 1200)
+    tA0, oA0 = eng.submit(0, reqA[0])
+    eng.pump()  # admitted normally
+    eng.fail_next(0, pepsi.E_NOMEM)
+    tA1, oA1 = eng.submit(0, reqA[1], mode=1, mask_seed=3)
+    tA2, oA2 = eng.submit(0, reqA[2])
+    tB = [eng.submit(1, x) for x in reqB]
+    with pytest.raises(pepsi.PepsiError) as err:
+        eng.run()
+    assert err.value.code == pepsi.E_NOMEM
+    with pytest.raises(pepsi.PepsiError) as err:
+        eng.wait(tA1)
+    assert err.value.code == pepsi.E_NOMEM
+    eng.wait(tA0)
+    eng.wait(tA2)
+    assert np.array_equal(oA0, gA.eval(a2, reqA[0])) and np.array_equal(oA2, gA.eval(a2, reqA[2]))
+    for (t, o), x in zip(tB, reqB):
+        eng.wait(t)
+        assert np.array_equal(o, gB.eval(b1, x))
+    st = eng.stats()
+    assert st["completed"] == st["submitted"] == 5 and st["bytes_in_use"] == 0
+    eng.close()

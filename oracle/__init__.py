@@ -98,6 +98,7 @@ def lib():
         L.or_hash_item.argtypes = [C.c_uint64, C.c_uint32, C.c_uint32, C.c_uint64,
                                    C.POINTER(C.c_uint64), u32p]
         L.or_cuckoo.argtypes = [C.c_uint64, C.c_uint32, C.c_uint32, u64p, C.c_uint32, u64p, i32p]
+        L.or_cuckoo_g.argtypes = [C.c_uint64, C.c_uint32, C.c_uint32, C.c_uint32, u64p, C.c_uint32, u64p, i32p]
         L.or_simple_hash.argtypes = [C.c_uint64, C.c_uint32, C.c_uint32, u64p, C.c_uint64, C.c_uint32,
                                      u64p, C.POINTER(C.c_uint32)]
         L.or_keygen.argtypes = [C.c_void_p, C.c_uint64, i8p, u64p]
@@ -212,12 +213,14 @@ def hash_item(hash_key, lambda_bar, logb, x):
     return int(xl.value), [int(b) for b in bins]
 
 
-def cuckoo(hash_key, lambda_bar, logb, items):
+def cuckoo(hash_key, lambda_bar, logb, items, gamma=1):
+    """Client cuckoo hashing into 2^logb bins of gamma slots: (rc, table
+    [bin * gamma + slot] of x_L or DUMMY, where[u] = bin * gamma + slot)."""
     items = np.ascontiguousarray(items, dtype=np.uint64)
-    table = np.zeros(1 << logb, dtype=np.uint64)
+    table = np.zeros((1 << logb) * gamma, dtype=np.uint64)
     where = np.full(len(items), -1, dtype=np.int32)
-    rc = lib().or_cuckoo(hash_key, lambda_bar, logb, items if len(items) else np.zeros(1, np.uint64),
-                         len(items), table, where if len(items) else np.zeros(1, np.int32))
+    rc = lib().or_cuckoo_g(hash_key, lambda_bar, logb, gamma, items if len(items) else np.zeros(1, np.uint64),
+                           len(items), table, where if len(items) else np.zeros(1, np.int32))
     return rc, table, where
 
 
@@ -268,8 +271,10 @@ class Ctx:
     """One BFV parameter set (N, t, prime bit sizes) plus PEPSI's code and
     hashing parameters."""
 
-    def __init__(self, N, t, prime_bits, h=2, ell=0, lambda_bar=16, mu=0, hash_key=0, n_server=None, bins=0):
+    def __init__(self, N, t, prime_bits, h=2, ell=0, lambda_bar=16, mu=0, hash_key=0, n_server=None, bins=0,
+                 gamma=1):
         self.N, self.t, self.h = int(N), int(t), int(h)
+        self.gamma = int(gamma)  # client maximum bin load (Table 2)
         self.prime_bits = list(prime_bits)
         self.k = len(self.prime_bits)
         self.lambda_bar = int(lambda_bar)
@@ -399,7 +404,7 @@ class Ctx:
 
     # ---- PEPSI
     def cuckoo(self, items):
-        return cuckoo(self.hash_key, self.lambda_bar, self.logb, items)
+        return cuckoo(self.hash_key, self.lambda_bar, self.logb, items, self.gamma)
 
     def server_table(self, items, mu=None):
         return simple_hash(self.hash_key, self.lambda_bar, self.logb, items, mu or self.mu)
@@ -419,18 +424,22 @@ class Ctx:
         return m
 
     def query(self, s, items, enc_seed):
-        """Client side: cuckoo into the b bins -> CW bit planes of each block
-        of N bins -> encode -> encrypt (ciphertext i of the request from
-        stream index i).  Returns (rc, cts [ell][2][k][N], or
-        [B][ell][2][k][N] for B > 1 blocks, bin_of_item)."""
+        """Client side: cuckoo into the b bins of gamma slots -> for each
+        block of N bins and each client batch i (slot i of every bin; Section
+        4) the CW bit planes -> encode -> encrypt (ciphertext i of the request
+        from stream index i, the request ordered [block][batch][bit]).
+        Returns (rc, cts [ell][2][k][N], with a leading [gamma] when gamma > 1
+        and [B] when there are B > 1 blocks, bin_of_item = bin*gamma + slot)."""
         rc, table, where = self.cuckoo(items)
         if rc:
             return rc, None, where
-        m = np.concatenate([self.query_plaintexts(table[b * self.N:(b + 1) * self.N]) for b in range(self.blocks)])
+        g = self.gamma
+        cols = table.reshape(self.bins, g)
+        m = np.concatenate([self.query_plaintexts(np.ascontiguousarray(cols[b * self.N:(b + 1) * self.N, i]))
+                            for b in range(self.blocks) for i in range(g)])
         cts = self.encrypt(s, m, enc_seed)
-        if self.blocks > 1:
-            cts = cts.reshape(self.blocks, self.ell, 2, self.k, self.N)
-        return 0, cts, where
+        shape = ((self.blocks,) if self.blocks > 1 else ()) + ((g,) if g > 1 else ()) + (self.ell, 2, self.k, self.N)
+        return 0, cts.reshape(shape), where
 
     def eval(self, rlk, cts, T, mode=0, mask_seed=0, layer0=0, nlayers=None, debug=False, group=1, acc=False,
              V=None):

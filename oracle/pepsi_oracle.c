@@ -593,13 +593,25 @@ void or_hash_item(u64 hash_key, u32 lambda_bar, u32 logb, u64 x, u64* xL, u32* b
 /* Client cuckoo hashing without stash: insert at H_1; an evicted item that
  * sat at H_i moves to H_{i+1 mod 3}; more than 1000 evictions during one
  * insertion is a failure. table_val[b] = x_L or OR_DUMMY. */
-int or_cuckoo(u64 hash_key, u32 lambda_bar, u32 logb, const u64* items, u32 m, u64* table_val, int32_t* bin_of_item) {
+/* Client cuckoo hashing with bins of gamma slots (Section 4: the client's
+ * maximum bin load gamma; gamma = 1 is the paper's evaluation, Section 7).
+ * Items go in input order to the first free slot of their current bin,
+ * starting at H_1; when that bin is full, the occupant of slot
+ * (evictions of this insertion so far) mod gamma is evicted and moves to
+ * its next hash function (H_{i+1 mod 3}); more than 1000 evictions in one
+ * insertion is a failure.  table_val[bin*gamma + slot] (x_L or the dummy);
+ * bin_of_item[u] = bin*gamma + slot. */
+int or_cuckoo_g(u64 hash_key, u32 lambda_bar, u32 logb, u32 gamma, const u64* items, u32 m, u64* table_val,
+                int32_t* bin_of_item) {
   u32 b = 1u << logb;
-  int32_t* occ = (int32_t*)malloc(sizeof(int32_t) * b); /* item index or -1 */
-  u32* occ_h = (u32*)malloc(sizeof(u32) * b);
+  if (gamma < 1) return OR_E_PARAM;
+  size_t cells = (size_t)b * gamma;
+  int32_t* occ = (int32_t*)malloc(sizeof(int32_t) * cells); /* item index or -1, [bin][slot] */
+  u32* occ_h = (u32*)malloc(sizeof(u32) * cells);
+  u32* load = (u32*)calloc(b, sizeof(u32));
   u64* xl = (u64*)malloc(sizeof(u64) * (m ? m : 1));
   u32* bins = (u32*)malloc(sizeof(u32) * 3 * (m ? m : 1));
-  for (u32 i = 0; i < b; i++) occ[i] = -1;
+  for (size_t i = 0; i < cells; i++) occ[i] = -1;
   for (u32 u = 0; u < m; u++) or_hash_item(hash_key, lambda_bar, logb, items[u], &xl[u], &bins[3 * u]);
   int rc = OR_OK;
   for (u32 u = 0; u < m && rc == OR_OK; u++) {
@@ -607,20 +619,30 @@ int or_cuckoo(u64 hash_key, u32 lambda_bar, u32 logb, const u64* items, u32 m, u
     u32 hi = 0, ev = 0;
     for (;;) {
       u32 bin = bins[3 * cur + hi];
-      if (occ[bin] < 0) { occ[bin] = cur; occ_h[bin] = hi; break; }
-      int32_t old = occ[bin];
-      u32 oh = occ_h[bin];
-      occ[bin] = cur; occ_h[bin] = hi;
+      if (load[bin] < gamma) {
+        size_t c = (size_t)bin * gamma + load[bin]++;
+        occ[c] = cur;
+        occ_h[c] = hi;
+        break;
+      }
+      size_t c = (size_t)bin * gamma + ev % gamma;
+      int32_t old = occ[c];
+      u32 oh = occ_h[c];
+      occ[c] = cur; occ_h[c] = hi;
       cur = old; hi = (oh + 1) % 3;
       if (++ev > 1000) { rc = OR_E_CUCKOO_FAIL; break; }
     }
   }
   if (rc == OR_OK) {
-    for (u32 i = 0; i < b; i++) table_val[i] = occ[i] < 0 ? OR_DUMMY : xl[occ[i]];
-    for (u32 i = 0; i < b; i++) if (occ[i] >= 0) bin_of_item[occ[i]] = (int32_t)i;
+    for (size_t i = 0; i < cells; i++) table_val[i] = occ[i] < 0 ? OR_DUMMY : xl[occ[i]];
+    for (size_t i = 0; i < cells; i++) if (occ[i] >= 0) bin_of_item[occ[i]] = (int32_t)i;
   }
-  free(occ); free(occ_h); free(xl); free(bins);
+  free(occ); free(occ_h); free(load); free(xl); free(bins);
   return rc;
+}
+/* gamma = 1 */
+int or_cuckoo(u64 hash_key, u32 lambda_bar, u32 logb, const u64* items, u32 m, u64* table_val, int32_t* bin_of_item) {
+  return or_cuckoo_g(hash_key, lambda_bar, logb, 1, items, m, table_val, bin_of_item);
 }
 /* Server simple hashing (App. Alg 7, server side): every item goes into
  * each distinct bin among its three; an x_L already present in a bin is

@@ -198,6 +198,37 @@ def test_cuckoo_invariants(oracle_mod):
     assert rc == oracle_mod.E_CUCKOO_FAIL
 
 
+@pytest.mark.parametrize("gamma", [2, 3])
+def test_bucketed_cuckoo_invariants(oracle_mod, gamma):
+    """Client bins of gamma slots (the client's maximum bin load, Section 4):
+    more items than bins are placed; every item sits in a slot of one of its
+    three bins with its x_L; no slot holds two items; a bin's occupied slots
+    are its first ones (new items take the first free slot, evictions
+    replace in place); gamma = 1 gives the one-slot table."""
+    rng = np.random.default_rng(14 + gamma)
+    b, logb = 256, 8
+    items = np.unique(rng.integers(0, 2**32, 2 * b, dtype=np.uint64))[: int(0.8 * gamma * b)]
+    rc, table, where = oracle_mod.cuckoo(77, 16, logb, items, gamma)
+    assert rc == 0 and len(items) > b and table.shape == (b * gamma,)
+    assert len(set(where.tolist())) == len(items)
+    for u, x in enumerate(items):
+        xl, bins = oracle_mod.hash_item(77, 16, logb, x)
+        assert where[u] // gamma in bins and table[where[u]] == xl
+    occ = (table != oracle_mod.DUMMY).reshape(b, gamma)
+    assert int(occ.sum()) == len(items)
+    for row in occ:
+        n = int(row.sum())
+        assert row[:n].all() and not row[n:].any()
+    # the gamma = 1 table is the one-slot cuckoo of the same items, where it fits
+    few = items[: b // 2]
+    r1, t1, w1 = oracle_mod.cuckoo(77, 16, logb, few)
+    rg, tg, wg = oracle_mod.cuckoo(77, 16, logb, few, 1)
+    assert r1 == rg == 0 and np.array_equal(t1, tg) and np.array_equal(w1, wg)
+    # more items than the gamma * b slots cannot be placed: failure, not a hang
+    rc, _, _ = oracle_mod.cuckoo(77, 16, 4, np.arange(16 * gamma + 1, dtype=np.uint64), gamma)
+    assert rc == oracle_mod.E_CUCKOO_FAIL
+
+
 def test_simple_hash_invariants(oracle_mod):
     rng = np.random.default_rng(5)
     items = np.unique(rng.integers(0, 2**32, 3000, dtype=np.uint64))
@@ -747,6 +778,44 @@ def test_psi_with_more_bins_than_slots(oracle_mod):
     assert np.array_equal(slots, want) and int(want.sum()) >= 9
     # more client items than one block holds
     assert len(sets.client) > N
+
+
+def test_psi_with_client_bins_of_two_slots(oracle_mod):
+    """gamma = 2: 100 client items in 64 bins (cuckoo with one slot per bin
+    cannot hold them).  The request is two batches of ell ciphertexts (batch
+    i: slot i of every bin); Algorithm 2 returns one indicator ciphertext per
+    batch; together their slots equal the hashed-domain brute force for every
+    client item, at where[u] = bin * 2 + slot.  Cardinality: the two masked
+    responses' slots sum to the intersection size."""
+    from paper_2310_14565_gb300.workload import make_sets
+
+    N, g, lb = 64, 2, 10
+    sets = make_sets(100, 200, 8, bits=32, seed_items=71, seed_plant=72)
+    load = oracle_mod.simple_hash(99, lb, 6, sets.server, 1000)[2]
+    c = oracle_mod.Ctx(N=N, t=T, prime_bits=[55, 55, 54, 54], h=4, lambda_bar=lb, hash_key=99, mu=max(5, load),
+                       gamma=g)
+    s, rlk = c.keygen(3)
+    rc, Ts, _ = c.server_table(sets.server)
+    assert rc == 0
+    assert oracle_mod.cuckoo(99, lb, 6, sets.client)[0] == oracle_mod.E_CUCKOO_FAIL
+    rc, cts, where = c.query(s, sets.client, 4)
+    assert rc == 0 and cts.shape == (g, c.ell, 2, c.k, N)
+    res = [c.decrypt(s, c.eval(rlk, cts[i], Ts)) for i in range(g)]
+    assert all(b > 0 for _, b in res)
+    got = np.stack([sl for sl, _ in res], axis=1).reshape(-1)  # [bin][slot]
+    srv = {}
+    for y in sets.server:
+        yl, bins = oracle_mod.hash_item(99, lb, 6, y)
+        for bb in bins:
+            srv.setdefault(bb, set()).add(yl)
+    want = np.zeros(N * g, np.uint32)
+    for u, x in enumerate(sets.client):
+        xl, _ = oracle_mod.hash_item(99, lb, 6, x)
+        want[where[u]] = int(xl in srv.get(int(where[u]) // g, set()))
+    assert np.array_equal(got, want) and int(want.sum()) >= 8
+    card = sum(int(c.decrypt(s, c.eval(rlk, cts[i], Ts, mode=1, mask_seed=5 + i))[0].astype(np.int64).sum())
+               for i in range(g))
+    assert card % T == int(want.sum())
 
 
 # ------------------------------------------- false matches (Lemma 1)

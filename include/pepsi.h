@@ -113,6 +113,12 @@ typedef struct {
                               multiply-accumulate runs slower on a fully resident table (its
                               unpacking costs more than the saved traffic).  Results are the
                               same either way */
+  uint32_t gamma;          /* client maximum bin load (Table 2, Section 4): 0 or 1 = cuckoo
+                              hashing with one item per bin (the paper's evaluation); 2..16 =
+                              bins of gamma slots, so up to gamma * b client items.  The client
+                              table's batch i is slot i of every bin: a request holds B * gamma
+                              * ell ciphertexts [B][gamma][ell][2][k][N] and Algorithm 2
+                              returns one indicator ciphertext per batch, [B][gamma][2][r][N] */
 } pepsi_params;
 
 /* Derived values of a context (for callers and tests). */
@@ -129,6 +135,7 @@ typedef struct {
   uint32_t response_primes; /* primes of the evaluation's response (k: not switched) */
   uint32_t bins, blocks;     /* b = blocks * N bins */
   uint32_t plaintext_bytes;  /* 7 or 8: storage of the resident server plaintexts per word */
+  uint32_t gamma;            /* client maximum bin load: client batches per block */
 } pepsi_info;
 
 /* Setup (Section 4, parameters of Tables 2-3): derives ell (Eq. 1), the
@@ -234,11 +241,12 @@ int pepsi_server_plaintexts(pepsi_ctx* ctx, int set_id, uint32_t layer0, uint32_
                             void* stream);
 
 /* Client request (App. Alg 7, client side): cuckoo hashing without stash
- * (3 hashes, eviction bound 1000), CW-Encode, batching, symmetric FV
- * encryption under s with randomness from enc_seed (ciphertext i of the
- * request draws from stream index i).  cts: [B][ell][2][k][N]
- * coefficient form (host or device).  bin_of_item: host int32[m], the bin
- * that holds each item.  Errors: PEPSI_E_CUCKOO_FAIL, PEPSI_E_PARAM. */
+ * (3 hashes, eviction bound 1000) into bins of gamma slots, CW-Encode,
+ * batching (batch i = slot i of every bin), symmetric FV encryption under s
+ * with randomness from enc_seed (ciphertext i of the request draws from
+ * stream index i).  cts: [B][gamma][ell][2][k][N] coefficient form (host or
+ * device).  bin_of_item: host int32[m], bin * gamma + slot of each item
+ * (the bin when gamma = 1).  Errors: PEPSI_E_CUCKOO_FAIL, PEPSI_E_PARAM. */
 int pepsi_query(pepsi_ctx* ctx, const uint64_t* items, size_t m, uint64_t enc_seed, uint64_t* cts,
                 int32_t* bin_of_item, void* stream);
 
@@ -249,11 +257,13 @@ int pepsi_query(pepsi_ctx* ctx, const uint64_t* items, size_t m, uint64_t enc_se
  * SUM weight layer i' by its value plaintext val_s[i'] (Algorithms 4-5):
  * with per-layer rounding val_s[i'] multiplies the rounded e; with lazy
  * rescaling it multiplies the exact product before the run's rounding.
- * cts: [B][ell][2][k][N] coefficient form, host or device.
- * out_ct: [B][2][r][N] coefficient form, host or device, with B blocks and
- * r = pepsi_info.response_primes (k unless the response is switched);
- * block j of the response answers request block j, its mask drawn from
- * mask_seed + j.  A host request is uploaded in two pieces of its code bits
+ * cts: [B][gamma][ell][2][k][N] coefficient form, host or device.
+ * out_ct: [B][gamma][2][r][N] coefficient form, host or device, with B
+ * blocks, gamma client batches and r = pepsi_info.response_primes (k unless
+ * the response is switched); ciphertext (j, i) of the response answers
+ * client batch i of request block j, its mask drawn from
+ * mask_seed + j * gamma + i.  With gamma > 1 the batches of a block are
+ * evaluated as by pepsi_eval_batch (shared multiply-accumulates).  A host request is uploaded in two pieces of its code bits
  * (the first short), the copy of the second overlapping the first piece's
  * transform and multiply-accumulate; the words do not depend on it.  Device
  * buffers need 8-byte alignment (16-byte aligned rows take wider accesses).

@@ -41,7 +41,7 @@ class Params(C.Structure):
         ("h", C.c_uint32), ("ell", C.c_uint32), ("lambda_bar", C.c_uint32), ("num_hashes", C.c_uint32),
         ("mu", C.c_uint32), ("hash_key", C.c_uint64), ("resident_bytes", C.c_uint64),
         ("rescale_group", C.c_uint32), ("server_values", C.c_uint32), ("response_primes", C.c_uint32),
-        ("bins", C.c_uint32), ("plaintext_bytes", C.c_uint32),
+        ("bins", C.c_uint32), ("plaintext_bytes", C.c_uint32), ("gamma", C.c_uint32),
     ]
 
 
@@ -52,7 +52,7 @@ class Info(C.Structure):
         ("q", C.c_uint64 * 8), ("psi", C.c_uint64 * 8), ("psi_t", C.c_uint64), ("b_primes", C.c_uint64 * 12),
         ("log2_q", C.c_double), ("rescale_group", C.c_uint32), ("rescale_cap", C.c_uint32),
         ("response_primes", C.c_uint32), ("bins", C.c_uint32), ("blocks", C.c_uint32),
-        ("plaintext_bytes", C.c_uint32),
+        ("plaintext_bytes", C.c_uint32), ("gamma", C.c_uint32),
     ]
 
 
@@ -233,7 +233,8 @@ class Context:
     """One parameter set with its keys, server sets and scratch (pepsi_ctx)."""
 
     def __init__(self, N, t=65537, prime_bits=(36, 36, 37), h=2, ell=0, lambda_bar=16, mu=0, hash_key=0,
-                 key_seed=3, resident_bytes=0, rescale_group=0, server_values=0, response_primes=0, bins=0, plaintext_bytes=0):
+                 key_seed=3, resident_bytes=0, rescale_group=0, server_values=0, response_primes=0, bins=0, plaintext_bytes=0,
+                 gamma=0):
         p = Params()
         p.N, p.t, p.k = N, t, len(prime_bits)
         for i, b in enumerate(prime_bits):
@@ -242,6 +243,7 @@ class Context:
         p.hash_key, p.resident_bytes, p.rescale_group = hash_key, resident_bytes, rescale_group
         p.server_values, p.response_primes, p.bins = server_values, response_primes, bins
         p.plaintext_bytes = plaintext_bytes
+        p.gamma = gamma
         self._h = C.c_void_p()
         _check(lib().pepsi_setup(C.byref(p), key_seed, C.byref(self._h)), "pepsi_setup")
         info = Info()
@@ -256,6 +258,7 @@ class Context:
         self.response_primes = int(info.response_primes)
         self.bins, self.blocks = int(info.bins), int(info.blocks)
         self.plaintext_bytes = int(info.plaintext_bytes)
+        self.gamma = int(info.gamma)
         self.mu = {}
 
     def close(self):
@@ -329,6 +332,12 @@ class Context:
         """Array shape with a leading block dimension when b > N."""
         return (self.blocks,) + tuple(shape) if self.blocks > 1 else tuple(shape)
 
+    def _batched(self, shape):
+        """Request / response shape: [B] when b > N, then [gamma] when the
+        client bins hold gamma > 1 items (one ciphertext set per batch)."""
+        lead = ((self.blocks,) if self.blocks > 1 else ()) + ((self.gamma,) if self.gamma > 1 else ())
+        return lead + tuple(shape)
+
     def server_values(self, set_id, mu):
         out = np.zeros((mu, self.bins), dtype=np.uint32)
         _check(lib().pepsi_server_values(self._h, set_id, _ptr(out)), "pepsi_server_values")
@@ -351,7 +360,7 @@ class Context:
     def query(self, items, enc_seed, out=None, stream=None):
         items = np.ascontiguousarray(items, dtype=np.uint64)
         if out is None:
-            out = np.zeros(self._blocked((self.ell, 2, self.k, self.N)), dtype=np.uint64)
+            out = np.zeros(self._batched((self.ell, 2, self.k, self.N)), dtype=np.uint64)
         _need(out, self._request_words(), "query out")
         where = np.full(max(items.size, 1), -1, dtype=np.int32)
         _check(lib().pepsi_query(self._h, _ptr(items) if items.size else None, items.size, enc_seed, _ptr(out),
@@ -362,7 +371,15 @@ class Context:
         """Slots and noise budget of a ciphertext [2][r][N] over the first r
         primes (r = k, or fewer for a switched response).  A response of B
         blocks [B][2][r][N] gives the B*N slots in bin order and the
-        smallest budget."""
+        smallest budget; one of gamma > 1 client batches ([gamma][2][r][N],
+        or [B][gamma][2][r][N]) gives bins * gamma slots in the order of
+        query's bin_of_item, bin * gamma + batch."""
+        if self.gamma > 1 and len(ct.shape) == (5 if self.blocks > 1 else 4):
+            nb = self.blocks
+            cts = ct.reshape((nb, self.gamma) + tuple(ct.shape[-3:]))
+            parts = [[self.decrypt(cts[b, i]) for i in range(self.gamma)] for b in range(nb)]
+            slots = np.stack([np.stack([p[0] for p in row], axis=1) for row in parts]).reshape(-1)
+            return slots, min(p[1] for row in parts for p in row)
         if len(ct.shape) == 4:
             parts = [self.decrypt(ct[i]) for i in range(int(ct.shape[0]))]
             return np.concatenate([p[0] for p in parts]), min(p[1] for p in parts)
@@ -393,14 +410,14 @@ class Context:
 
     # ---- evaluation
     def _request_words(self):
-        return self.blocks * self.ell * 2 * self.k * self.N
+        return self.blocks * self.gamma * self.ell * 2 * self.k * self.N
 
     def _response_words(self):
-        return self.blocks * 2 * self.response_primes * self.N
+        return self.blocks * self.gamma * 2 * self.response_primes * self.N
 
     def eval(self, set_id, cts, mode=MODE_INDICATOR, mask_seed=0, out=None, stream=None):
         if out is None:
-            out = np.zeros(self._blocked((2, self.response_primes, self.N)), dtype=np.uint64)
+            out = np.zeros(self._batched((2, self.response_primes, self.N)), dtype=np.uint64)
         _need(cts, self._request_words(), "eval cts")
         _need(out, self._response_words(), "eval out")
         _check(lib().pepsi_eval(self._h, set_id, _ptr(cts), mode, mask_seed, _ptr(out), _stream(stream)),
@@ -419,7 +436,7 @@ class Context:
         """pepsi_eval_batch: one output ciphertext per request."""
         nq = len(cts_list)
         if outs is None:
-            outs = [np.zeros(self._blocked((2, self.response_primes, self.N)), dtype=np.uint64) for _ in range(nq)]
+            outs = [np.zeros(self._batched((2, self.response_primes, self.N)), dtype=np.uint64) for _ in range(nq)]
         for x, o in zip(cts_list, outs):
             _need(x, self._request_words(), "eval_batch cts")
             _need(o, self._response_words(), "eval_batch out")
@@ -432,8 +449,8 @@ class Context:
         return outs
 
     def eval_layers(self, set_id, cts, layer0, nl, want_h=True, want_e=True, stream=None):
-        h = np.zeros(self._blocked((nl, 2, self.k, self.N)), dtype=np.uint64) if want_h else None
-        e = np.zeros(self._blocked((nl, 3, self.k, self.N)), dtype=np.uint64) if want_e else None
+        h = np.zeros(self._batched((nl, 2, self.k, self.N)), dtype=np.uint64) if want_h else None
+        e = np.zeros(self._batched((nl, 3, self.k, self.N)), dtype=np.uint64) if want_e else None
         _need(cts, self._request_words(), "eval_layers cts")
         _check(lib().pepsi_eval_layers(self._h, set_id, _ptr(cts), layer0, nl, _ptr(h), _ptr(e), _stream(stream)),
                "pepsi_eval_layers")

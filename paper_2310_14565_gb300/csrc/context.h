@@ -101,6 +101,7 @@ struct pepsi_ctx {
   std::vector<pepsi_detail::ServerSet> sets;   // internal: one per block of a loaded set
   std::vector<pepsi_detail::SetGroup> groups;  // the caller's set ids
   u32 logb = 0, blocks = 1;      // bins = blocks * N = 2^logb
+  u32 gamma = 1;                 // client maximum bin load: client batches per block
   // scratch, grown on demand
   std::vector<pepsi_detail::DevBuf> scratch;
   int chunk = 64;  // layers per circuit chunk (pepsi_autotune may change it)

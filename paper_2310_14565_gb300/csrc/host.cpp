@@ -295,10 +295,18 @@ void Hasher::operator()(u64 x, u64* xL, u32 bins[3]) const {
   bins[2] = (u32)(xh ^ (mix64(*xL ^ k3) & bm));
 }
 
-int cuckoo(const Hasher& H, const u64* items, size_t m, std::vector<u64>& table, std::vector<int32_t>& where) {
+// Cuckoo hashing into bins of gamma slots (Section 4, the client's maximum
+// bin load): items in input order take the first free slot of their current
+// bin, starting at H_1; in a full bin the occupant of slot (evictions of this
+// insertion so far) mod gamma is evicted and moves to its next hash function.
+int cuckoo(const Hasher& H, const u64* items, size_t m, u32 gamma, std::vector<u64>& table,
+           std::vector<int32_t>& where) {
   const u32 b = 1u << H.logb;
-  std::vector<int64_t> slot(b, -1);  // item index
-  std::vector<uint8_t> slot_h(b, 0);
+  if (gamma < 1) return PEPSI_E_PARAM;
+  const size_t cells = (size_t)b * gamma;
+  std::vector<int64_t> slot(cells, -1);  // item index, [bin][slot]
+  std::vector<uint8_t> slot_h(cells, 0);
+  std::vector<u32> load(b, 0);
   std::vector<u64> xl(m);
   std::vector<u32> bins(3 * m);
   for (size_t u = 0; u < m; ++u) H(items[u], &xl[u], &bins[3 * u]);
@@ -307,21 +315,23 @@ int cuckoo(const Hasher& H, const u64* items, size_t m, std::vector<u64>& table,
     int hidx = 0;
     for (int evictions = 0;; ++evictions) {
       const u32 bin = bins[3 * cur + hidx];
-      if (slot[bin] < 0) {
-        slot[bin] = cur;
-        slot_h[bin] = (uint8_t)hidx;
+      if (load[bin] < gamma) {
+        const size_t c = (size_t)bin * gamma + load[bin]++;
+        slot[c] = cur;
+        slot_h[c] = (uint8_t)hidx;
         break;
       }
       if (evictions >= 1000) return PEPSI_E_CUCKOO_FAIL;
-      std::swap(slot[bin], cur);
-      int old_h = slot_h[bin];
-      slot_h[bin] = (uint8_t)hidx;
+      const size_t c = (size_t)bin * gamma + (u32)evictions % gamma;
+      std::swap(slot[c], cur);
+      int old_h = slot_h[c];
+      slot_h[c] = (uint8_t)hidx;
       hidx = (old_h + 1) % 3;
     }
   }
-  table.assign(b, PEPSI_DUMMY);
+  table.assign(cells, PEPSI_DUMMY);
   where.assign(m, -1);
-  for (u32 i = 0; i < b; ++i)
+  for (size_t i = 0; i < cells; ++i)
     if (slot[i] >= 0) {
       table[i] = xl[slot[i]];
       where[slot[i]] = (int32_t)i;

@@ -44,8 +44,10 @@ struct Hasher {
   Hasher(u64 hash_key, u32 lambda_bar, u32 logb);
   void operator()(u64 x, u64* xL, u32 bins[3]) const;
 };
-// client cuckoo hashing without stash; returns 0 or PEPSI_E_CUCKOO_FAIL
-int cuckoo(const Hasher& H, const u64* items, size_t m, std::vector<u64>& table, std::vector<int32_t>& where);
+// client cuckoo hashing without stash into bins of gamma slots: table[bin*gamma + slot],
+// where[u] = bin*gamma + slot; returns 0 or PEPSI_E_CUCKOO_FAIL
+int cuckoo(const Hasher& H, const u64* items, size_t m, u32 gamma, std::vector<u64>& table,
+           std::vector<int32_t>& where);
 // Server simple hashing: T[mu][b] (x_L or PEPSI_DUMMY); with values, also
 // V[mu][b], the value of the item stored at each (layer, bin), 0 for
 // dummies.  Returns 0 or PEPSI_E_BIN_OVERFLOW.

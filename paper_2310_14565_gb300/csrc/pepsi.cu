@@ -779,6 +779,7 @@ pepsi_ctx* ctx_fork(const pepsi_ctx* p, cudaError_t* err) {
   }
   c->logb = p->logb;
   c->blocks = p->blocks;
+  c->gamma = p->gamma;
   c->chunk = p->chunk;
   c->relin_fused = p->relin_fused;
   c->batch_points = p->batch_points;
@@ -967,10 +968,11 @@ int pepsi_setup(const pepsi_params* params, uint64_t key_seed, pepsi_ctx** out) 
       return PEPSI_E_PARAM;
     }
   }
-  if (params->response_primes > (u32)c->k) {
+  if (params->response_primes > (u32)c->k || params->gamma > 16) {
     delete c;
     return PEPSI_E_PARAM;
   }
+  c->gamma = params->gamma ? params->gamma : 1;
   c->resp = params->response_primes ? (int)params->response_primes : c->k;
   // resident plaintexts in 7 bytes per word on request (every q_i < 2^56)
   {
@@ -1145,6 +1147,7 @@ int pepsi_get_info(const pepsi_ctx* c, pepsi_info* info) {
   info->bins = c->blocks * (uint32_t)c->N;
   info->blocks = c->blocks;
   info->plaintext_bytes = c->p7 ? 7 : 8;
+  info->gamma = c->gamma;
   return PEPSI_OK;
 }
 
@@ -1415,31 +1418,37 @@ int pepsi_query(pepsi_ctx* c, const uint64_t* items, size_t m, uint64_t enc_seed
   if (!c || (!items && m) || !cts) return PEPSI_E_PARAM;
   cudaStream_t st = pick(c, stream);
   hostmath::Hasher H(c->prm.hash_key, c->prm.lambda_bar, c->logb);
-  std::vector<u64> table;  // [bins]
+  std::vector<u64> table;  // [bins][gamma]
   std::vector<int32_t> where;
-  int rc = hostmath::cuckoo(H, items, m, table, where);
+  int rc = hostmath::cuckoo(H, items, m, c->gamma, table, where);
   if (rc) return rc;
   if (bin_of_item) memcpy(bin_of_item, where.data(), m * sizeof(int32_t));
   cudaError_t e = cudaSuccess;
-  const size_t N = c->N, bins = (size_t)c->blocks * N;
-  u64* dTc = (u64*)scratch(c, S_TC, bins * 8, &e);
-  uint16_t* dpos = (uint16_t*)scratch(c, S_POS, bins * c->h * sizeof(uint16_t), &e);
-  const size_t words = request_block_words(c) * c->blocks;
+  const size_t N = c->N, bins = (size_t)c->blocks * N, g = c->gamma;
+  // batch i of the client table: slot i of every bin, laid out [gamma][bins]
+  std::vector<u64> batches(bins * g);
+  for (size_t bin = 0; bin < bins; ++bin)
+    for (size_t i = 0; i < g; ++i) batches[i * bins + bin] = table[bin * g + i];
+  u64* dTc = (u64*)scratch(c, S_TC, bins * g * 8, &e);
+  uint16_t* dpos = (uint16_t*)scratch(c, S_POS, bins * g * c->h * sizeof(uint16_t), &e);
+  const size_t words = request_block_words(c) * c->blocks * g;
   const bool dev_out = is_device_ptr(cts);
   u64* dct = dev_out ? cts : (u64*)scratch(c, S_CT, words * 8, &e);
   if (!dTc || !dpos || !dct) return cuda_status(e);
-  CKS(copy_any(dTc, table.data(), bins * 8, st));
+  CKS(copy_any(dTc, batches.data(), bins * g * 8, st));
   {
     Prof p(c, PC_CLIENT, st);
-    launch_cw_unrank(dTc, bins, c->d_binom, c->ell, c->h, dpos, st);
+    launch_cw_unrank(dTc, bins * g, c->d_binom, c->ell, c->h, dpos, st);
   }
-  for (u32 b = 0; b < c->blocks; ++b) {  // block b: ciphertexts b*ell .. b*ell + ell - 1
-    Prof p(c, PC_CLIENT, st);
-    launch_encrypt(c->V, dpos + (size_t)b * N * c->h, c->ell, c->h, c->d_s_ntt, enc_seed, (u64)b * c->ell,
-                   dct + (size_t)b * request_block_words(c), st);
-  }
+  for (u32 b = 0; b < c->blocks; ++b)  // ciphertexts of (block b, batch i): (b * gamma + i) * ell ...
+    for (size_t i = 0; i < g; ++i) {
+      const size_t r = (size_t)b * g + i;
+      Prof p(c, PC_CLIENT, st);
+      launch_encrypt(c->V, dpos + (i * bins + (size_t)b * N) * c->h, c->ell, c->h, c->d_s_ntt, enc_seed,
+                     (u64)r * c->ell, dct + r * request_block_words(c), st);
+    }
   if (!dev_out) CKS(copy_any(cts, dct, words * 8, st));
-  e = cudaStreamSynchronize(st);  // the host cuckoo table must outlive the copy
+  e = cudaStreamSynchronize(st);  // the host tables must outlive the copies
   if (e == cudaSuccess) e = cudaGetLastError();
   if (c->prof) prof_collect(c);
   return cuda_status(e);
@@ -1450,12 +1459,30 @@ int pepsi_eval(pepsi_ctx* c, int set_id, const uint64_t* cts, int mode, uint64_t
   SetGroup* G = group(c, set_id);
   if (!G || !out_ct || !cts) return PEPSI_E_PARAM;
   cudaStream_t st = pick(c, stream);
-  for (size_t b = 0; b < G->blk.size(); ++b) {  // block b: its request block, mask seed + b
-    const int rc = eval_core(c, G->blk[b], cts + b * request_block_words(c), 0, G->mu, mode, mask_seed + b,
-                             out_ct + b * response_block_words(c), nullptr, nullptr, st);
-    if (rc) return rc;
+  if (c->gamma == 1) {
+    for (size_t b = 0; b < G->blk.size(); ++b) {  // block b: its request block, mask seed + b
+      const int rc = eval_core(c, G->blk[b], cts + b * request_block_words(c), 0, G->mu, mode, mask_seed + b,
+                               out_ct + b * response_block_words(c), nullptr, nullptr, st);
+      if (rc) return rc;
+    }
+    return PEPSI_OK;
   }
-  return PEPSI_OK;
+  // gamma client batches per block (Algorithm 2's outer loop): the batches of a
+  // block are requests on the same internal set, evaluated together
+  std::vector<int> ids, md;
+  std::vector<const u64*> in;
+  std::vector<u64*> out;
+  std::vector<u64> seeds;
+  for (size_t b = 0; b < G->blk.size(); ++b)
+    for (size_t i = 0; i < c->gamma; ++i) {
+      const size_t r = b * c->gamma + i;
+      ids.push_back(G->blk[b]);
+      in.push_back(cts + r * request_block_words(c));
+      out.push_back(out_ct + r * response_block_words(c));
+      md.push_back(mode);
+      seeds.push_back(mask_seed + r);
+    }
+  return eval_batch_core(c, (int)ids.size(), ids.data(), in.data(), md.data(), seeds.data(), out.data(), st);
 }
 
 int pepsi_autotune(pepsi_ctx* c, int set_id, const uint64_t* cts, void* stream, uint32_t* chosen) {
@@ -1463,7 +1490,7 @@ int pepsi_autotune(pepsi_ctx* c, int set_id, const uint64_t* cts, void* stream, 
   if (!G || !cts) return PEPSI_E_PARAM;
   cudaStream_t st = pick(c, stream);
   cudaError_t e = cudaSuccess;
-  u64* out = (u64*)scratch(c, kScratchTune, response_block_words(c) * c->blocks * 8, &e);
+  u64* out = (u64*)scratch(c, kScratchTune, response_block_words(c) * c->blocks * c->gamma * 8, &e);
   if (!out) return cuda_status(e);
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   CKS(cudaEventCreate(&e0));
@@ -1535,7 +1562,7 @@ int pepsi_autotune(pepsi_ctx* c, int set_id, const uint64_t* cts, void* stream, 
     else c->relin_fused = true;
   }
   // 4: requests per shared multiply-accumulate, on a batch of four copies of the request
-  if (!rc && G->blk.size() == 1) {
+  if (!rc && G->blk.size() == 1 && c->gamma == 1) {
     std::vector<u64*> outs(4, nullptr);
     u64* ob = (u64*)scratch(c, kScratchTuneBatch, 4 * response_block_words(c) * 8, &e);
     if (!ob) rc = cuda_status(e);
@@ -1591,13 +1618,15 @@ int pepsi_eval_batch(pepsi_ctx* c, int nq, const int* set_ids, const uint64_t* c
   for (int i = 0; i < nq; ++i) {
     SetGroup* G = group(c, set_ids[i]);
     if (!G || !cts[i] || !out_cts[i]) return PEPSI_E_PARAM;
-    for (size_t b = 0; b < G->blk.size(); ++b) {
-      ids.push_back(G->blk[b]);
-      in.push_back(cts[i] + b * request_block_words(c));
-      out.push_back(out_cts[i] + b * response_block_words(c));
-      md.push_back(modes ? modes[i] : PEPSI_MODE_INDICATOR);
-      seeds.push_back((mask_seeds ? mask_seeds[i] : 0) + b);
-    }
+    for (size_t b = 0; b < G->blk.size(); ++b)
+      for (size_t j = 0; j < c->gamma; ++j) {  // (block b, client batch j)
+        const size_t r = b * c->gamma + j;
+        ids.push_back(G->blk[b]);
+        in.push_back(cts[i] + r * request_block_words(c));
+        out.push_back(out_cts[i] + r * response_block_words(c));
+        md.push_back(modes ? modes[i] : PEPSI_MODE_INDICATOR);
+        seeds.push_back((mask_seeds ? mask_seeds[i] : 0) + r);
+      }
   }
   return eval_batch_core(c, (int)ids.size(), ids.data(), in.data(), md.data(), seeds.data(), out.data(),
                          pick(c, stream));
@@ -1609,12 +1638,14 @@ int pepsi_eval_layers(pepsi_ctx* c, int set_id, const uint64_t* cts, uint32_t la
   if (!G || nl == 0 || !cts) return PEPSI_E_PARAM;
   const size_t kN = (size_t)c->k * c->N;
   cudaStream_t st = pick(c, stream);
-  for (size_t b = 0; b < G->blk.size(); ++b) {
-    const int rc = eval_core(c, G->blk[b], cts + b * request_block_words(c), layer0, nl, PEPSI_MODE_INDICATOR, 0,
-                             nullptr, h_out ? h_out + b * nl * 2 * kN : nullptr,
-                             e_out ? e_out + b * nl * 3 * kN : nullptr, st);
-    if (rc) return rc;
-  }
+  for (size_t b = 0; b < G->blk.size(); ++b)
+    for (size_t i = 0; i < c->gamma; ++i) {  // (block b, client batch i)
+      const size_t r = b * c->gamma + i;
+      const int rc = eval_core(c, G->blk[b], cts + r * request_block_words(c), layer0, nl, PEPSI_MODE_INDICATOR,
+                               0, nullptr, h_out ? h_out + r * nl * 2 * kN : nullptr,
+                               e_out ? e_out + r * nl * 3 * kN : nullptr, st);
+      if (rc) return rc;
+    }
   return PEPSI_OK;
 }
 

@@ -175,7 +175,9 @@ int pepsi_set_rescale_group(pepsi_ctx* ctx, uint32_t rescale_group);
  * leaves the result words unchanged. */
 typedef struct {
   uint32_t chunk;       /* layers per circuit chunk, 1..4096 (default 64, or the
-                           PEPSI_CHUNK environment variable at setup).  Larger chunks
+                           PEPSI_CHUNK environment variable at setup); n layers run in
+                           ceil(n / chunk) chunks of equal size (within one layer), so
+                           526 layers at chunk 256 run as 176, 176 and 174.  Larger chunks
                            fill the GPU with more blocks per launch and need more
                            scratch (about 4.7 MB per layer at N = 8192, k = 4) */
   uint32_t ntt_threads; /* threads per block of the ciphertext transforms (the NTTs and
@@ -276,9 +278,10 @@ int pepsi_eval(pepsi_ctx* ctx, int set_id, const uint64_t* cts, int mode, uint64
  * set_id, timing two evaluations after a warm-up with CUDA events on the
  * stream for each candidate, and keeps the fastest schedule for later
  * evaluations on this context (pepsi_get_schedule reads it), one field at a
- * time: the circuit chunk (32, 64, 128, 256 layers, stopping at the set's
- * mu, at 4 GiB of chunk scratch, or at the first that does not fit in
- * memory), then the threads per transform block (the default for N, half
+ * time: the circuit chunk (the balanced chunk sizes of 32, 64, 128, ...,
+ * 4096 layers for the set's mu, up to the one that holds every layer, stopping
+ * at 4 GiB of chunk scratch or at the first that does not fit in memory),
+ * then the threads per transform block (the default for N, half
  * and twice it), then for h = 4 and 8 the fused against the stored
  * relinearisation before the affine step, then the requests per shared
  * multiply-accumulate launch (1, 2 or 4, timed on a batch of four copies of

@@ -3,6 +3,7 @@
 // pipeline and the pipeline's steps (pepsi.cu), used by the request engine
 // (engine.cu).  Not part of the C ABI.
 #pragma once
+#include <algorithm>
 #include <cuda_runtime.h>
 
 #include <memory>
@@ -149,6 +150,15 @@ extern thread_local std::string g_detail;  // names the failing step for the nex
 int cuda_status(cudaError_t e);
 bool is_device_ptr(const void* p);
 cudaStream_t pick(pepsi_ctx* c, void* s);
+// Layers per circuit chunk for n layers under the schedule's chunk: the
+// fewest chunks of at most `chunk` layers, made as equal as possible (526
+// layers at chunk 256: three chunks of 176 and 174 layers, not 256, 256, 14).
+inline int balanced_chunk(int chunk, unsigned n) {
+  if (n == 0) return 1;
+  const unsigned want = (unsigned)std::max(1, chunk) < n ? (unsigned)std::max(1, chunk) : n;
+  const unsigned parts = (n + want - 1) / want;
+  return (int)((n + parts - 1) / parts);
+}
 // scratch slot `id` of the context with at least `bytes`
 void* scratch(pepsi_ctx* c, int id, size_t bytes, cudaError_t* err);
 void prof_collect(pepsi_ctx* c);

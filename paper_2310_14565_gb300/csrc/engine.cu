@@ -434,7 +434,7 @@ int pepsi_engine_create(const pepsi_lane* lanes, int nlanes, uint64_t hbm_budget
     L.mu = S.mu;
     L.mu_res = S.mu_res;
     L.nslots = (int)lanes[i].slots;
-    L.Lc = std::max(1, std::min<int>(L.c->chunk, (int)L.mu));
+    L.Lc = balanced_chunk(L.c->chunk, L.mu);
     err = eval_bufs(L.c, L.Lc, L.mu_res < L.mu, &L.b);
     if (err == cudaSuccess) err = cudaHostAlloc((void**)&L.err_ring, (kStepsAhead + 1) * sizeof(int), 0);
     if (err == cudaSuccess) memset(L.err_ring, 0, (kStepsAhead + 1) * sizeof(int));

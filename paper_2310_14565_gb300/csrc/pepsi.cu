@@ -438,7 +438,7 @@ int eval_core(pepsi_ctx* c, int set_id, const u64* cts, u32 layer0, u32 nl, int 
   const size_t k = c->k, N = c->N;
   const size_t vstride = (size_t)(c->k + c->kb) * N;  // value plaintext words per layer
   const size_t kN = k * N, ct2 = 2 * kN, ct3 = 3 * kN;
-  const int Lc = std::max(1, std::min<int>(c->chunk, (int)nl));
+  const int Lc = balanced_chunk(c->chunk, nl);
   const u32 end = layer0 + nl, res_end = std::min(end, S.mu_res);
   EvalBufs b;
   cudaError_t e = eval_bufs(c, Lc, res_end < end, &b);
@@ -601,7 +601,7 @@ int eval_batch_core(pepsi_ctx* c, int nq, const int* set_ids, const u64* const* 
     const int G = (int)grp.size();
     ServerSet& S = c->sets[set_ids[grp[0]]];
     const u32 mu = S.mu, mres = S.mu_res;
-    const int Lc = std::max(1, std::min<int>(c->chunk, (int)mu));
+    const int Lc = balanced_chunk(c->chunk, mu);
     EvalBufs b;
     e = eval_bufs(c, Lc, mres < mu, &b);
     if (e != cudaSuccess) return cuda_status(e);
@@ -1516,10 +1516,14 @@ int pepsi_autotune(pepsi_ctx* c, int set_id, const uint64_t* cts, void* stream, 
   const size_t scratch_cap = (size_t)4 << 30;
   int rc = PEPSI_OK;
   float best_ms = 0;
-  // 1: the layer chunk (larger chunks fill the GPU with more blocks per launch)
-  int best_chunk = c->chunk;
-  for (int chunk : {32, 64, 128, 256}) {
-    if (chunk > 32 && (size_t)chunk * per_layer > scratch_cap) break;
+  // 1: the layer chunk (larger chunks fill the GPU with more blocks per
+  // launch), as the balanced size an evaluation of the set's mu layers uses
+  int best_chunk = c->chunk, last = 0;
+  for (int want : {32, 64, 128, 256, 512, 1024, 2048, 4096}) {
+    const int chunk = balanced_chunk(want, G->mu);
+    if (chunk == last) continue;
+    last = chunk;
+    if (want > 32 && (size_t)chunk * per_layer > scratch_cap) break;
     c->chunk = chunk;
     float ms = 0;
     rc = time_it(&ms);
@@ -1533,7 +1537,7 @@ int pepsi_autotune(pepsi_ctx* c, int set_id, const uint64_t* cts, void* stream, 
       best_ms = ms;
       best_chunk = chunk;
     }
-    if ((u32)chunk >= G->mu) break;  // larger chunks run the same launches
+    if ((u32)chunk >= G->mu) break;  // one chunk holds every layer
   }
   c->chunk = best_chunk;
   // 2: threads per transform block (the default, half and twice it)

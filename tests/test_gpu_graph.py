@@ -53,7 +53,12 @@ def test_autotune_picks_a_chunk_and_keeps_the_words():
     cts, _ = gc.query(sets.client, 4)
     before = gc.eval(sid, cts)
     chunk = gc.autotune(sid, cts)
-    assert chunk in (32, 64, 128, 256)
+    # the balanced chunk sizes of the candidates for mu layers
+    cands = set()
+    for want in (32, 64, 128, 256, 512, 1024, 2048, 4096):
+        parts = -(-mu // min(want, mu))
+        cands.add(-(-mu // parts))
+    assert chunk in cands and gc.schedule()["chunk"] == chunk
     assert np.array_equal(gc.eval(sid, cts), before)
     _, Ts, _ = oc.server_table(sets.server)
     assert np.array_equal(before, oc.eval(rlk, cts, Ts, group=5))

@@ -395,18 +395,36 @@ def leg_serve(pepsi, torch, mixed, total=120, loads=(0.5, 0.9, 1.5)):
             "arrivals": "Poisson, rate = load x sequential capacity; set and request uniform; modes alternate"}
 
 
-def leg_large(pepsi, torch, steps=3, chunk=128):
+# HBM the large configuration leaves free of resident plaintexts: its evaluation
+# scratch at chunk 128 (the regenerated chunk's 64-bit plaintexts, 17.2 GB; circuit
+# buffers, 4.3 GB; h' of the resident layers, 2 MB each) and the four-request
+# batch's h' of every resident layer (double-buffered, 16.8 MB per layer), with a
+# margin: about 1930 of the 3487 layers stay resident.
+LARGE_RESERVE_GB = 70
+
+
+def leg_large(pepsi, torch, steps=3, chunk=128, reserve_gb=None):
     """Configuration 4 (large) in the default line: N = 16384, eight primes,
     h = 8, ell = 128, mu = 3487, 4096 client x 2^24 server items; the
     resident prefix of the 468 GB table in 7-byte words, the rest
-    regenerated per chunk.  A few steps after one warm-up."""
+    regenerated per chunk.  A few steps after one warm-up.  reserve_gb: HBM
+    left free of resident plaintexts for the evaluation's scratch (None: the
+    library's default budget, 0.6 of the free memory)."""
     from paper_2310_14565_gb300.workload import make_sets
 
     W = WL_LARGE
     N, k = W["N"], len(W["prime_bits"])
+    resident = 0
+    free, _ = torch.cuda.mem_get_info()
+    if reserve_gb is not None:
+        resident = max(1, int(free - reserve_gb * 1e9))
+    # the longest prefix of layers that fits the budget stays resident
+    layer_bytes = W["ell"] * k * N * 7
+    resident_layers = min(W["mu"], int((resident or 0.6 * free) // layer_bytes))
     ctx = pepsi.Context(N=N, t=65537, prime_bits=W["prime_bits"], h=W["h"], ell=W["ell"],
                         lambda_bar=W["lambda_bar"], mu=W["mu"], hash_key=HASH_KEY, key_seed=KEY_SEED,
-                        rescale_group=RESCALE["all"], response_primes=RESPONSE_PRIMES, plaintext_bytes=7)
+                        rescale_group=RESCALE["all"], response_primes=RESPONSE_PRIMES, plaintext_bytes=7,
+                        resident_bytes=resident)
     ctx.set_schedule(chunk=chunk)
     sets = make_sets(W["m"], W["n"], W["planted"], bits=64)
     t0 = time.perf_counter()
@@ -456,6 +474,7 @@ def leg_large(pepsi, torch, steps=3, chunk=128):
     res = {"workload": "N=16384, 8 primes (55x6, 54x2), h=8, ell=128, mu=3487, 4096 client x 2^24 server items, "
                        "41 planted; 7-byte resident prefix, the rest regenerated per chunk",
            "ms_per_step": round(ms, 1), "steps": steps, "layer_chunk": chunk,
+           "resident_layers": resident_layers, "resident_gb": round(resident_layers * layer_bytes / 1e9, 1),
            "batched": {"requests": 4, "ms_per_request": round(batch_ms / 4, 1),
                        "sequential_ms_per_request": round(seq_ms / 4, 1), "speedup": round(seq_ms / batch_ms, 3),
                        "identical_outputs": bool(same),
@@ -781,7 +800,7 @@ def run_ours(args):
         del cts_dev, cts_pinned, out_dev, out_pinned
         torch.cuda.synchronize()
         torch.cuda.empty_cache()
-        line["large"] = leg_large(pepsi, torch)
+        line["large"] = leg_large(pepsi, torch, reserve_gb=LARGE_RESERVE_GB)
     if rank == 0 and args.gpus == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.rescale == "all")
     if rank == 0:

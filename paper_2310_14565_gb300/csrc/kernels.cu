@@ -114,15 +114,26 @@ __global__ void __launch_bounds__(NTT_MAX_THREADS, 1) k_ptgen(DevView V, const u
   for (int jj = 0; jj < JC; ++jj) {
     const int j = j0 + jj;
     if (j >= ell) break;
-    // Encode: slot s at position brev(s), inverse NTT mod t into mbuf
+    // Encode: slot s at position brev(s), inverse NTT mod t into mbuf (in
+    // 32-bit words for t below 2^30)
     const u32* bj = bits + jj * words;
-    ntt_inv_gg(
-        poly,
-        [&](int i) -> u64 {
-          const u32 s = brev_bits(i, V.logN);
-          return (bj[s >> 5] >> (s & 31)) & 1u;
-        },
-        [&](int i, u64 v) { mbuf[i] = (u32)v; }, V, V.tidx);
+    if (t < (1ull << 30)) {
+      ntt_inv_gg_small(
+          reinterpret_cast<u32*>(poly),
+          [&](int i) -> u32 {
+            const u32 s = brev_bits(i, V.logN);
+            return (bj[s >> 5] >> (s & 31)) & 1u;
+          },
+          [&](int i, u32 v) { mbuf[i] = v; }, V, V.tidx);
+    } else {
+      ntt_inv_gg(
+          poly,
+          [&](int i) -> u64 {
+            const u32 s = brev_bits(i, V.logN);
+            return (bj[s >> 5] >> (s & 31)) & 1u;
+          },
+          [&](int i, u64 v) { mbuf[i] = (u32)v; }, V, V.tidx);
+    }
     __syncthreads();
     for (int p = 0; p < k; ++p) {
       // centred lift to q_p on the load, split operand format on the store

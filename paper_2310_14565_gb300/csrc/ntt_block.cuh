@@ -26,6 +26,22 @@ __device__ __forceinline__ int nsw(int x) { return x ^ ((x >> 4) & 15); }
 
 namespace nttd {
 
+// Word types of the transforms: 64-bit words for the ciphertext primes, and
+// 32-bit words for a modulus below 2^30 (the plaintext modulus t), where
+// Shoup's product takes one 32x32 high product and two low ones.  A twiddle
+// pair (w, floor(w 2^64 / q)) gives the 32-bit companion floor(w 2^32 / q)
+// as its upper half.
+__device__ __forceinline__ u64 lazy_mul(u64 x, u64 w, u64 ws, u64 q) { return shoup_lazy(x, w, ws, q); }
+__device__ __forceinline__ u32 lazy_mul(u32 x, u32 w, u32 ws, u32 q) { return x * w - __umulhi(x, ws) * q; }
+__device__ __forceinline__ void tw_split(const ulonglong2& t, u64& w, u64& ws) {
+  w = t.x;
+  ws = t.y;
+}
+__device__ __forceinline__ void tw_split(const ulonglong2& t, u32& w, u32& ws) {
+  w = (u32)t.x;
+  ws = (u32)(t.y >> 32);
+}
+
 // Forward stages [s0, s0 + RR) on one group of 2^RR elements held in
 // registers, element i of the group at base + i * 2^(logN - s0 - RR).
 // Twiddles come as (w, Shoup companion) pairs, one 16-byte load each.
@@ -70,11 +86,11 @@ __device__ __forceinline__ void fwd_final(u64 (&x)[E], u64 q) {
   }
 }
 // Inverse (Gentleman-Sande) stages s0 + RR - 1 down to s0 on one group.
-template <int RR>
-__device__ __forceinline__ void inv_group(u64 (&x)[1 << RR], int base, int logN, int s0, u64 q,
+template <int RR, class T>
+__device__ __forceinline__ void inv_group(T (&x)[1 << RR], int base, int logN, int s0, T q,
                                           const ulonglong2* __restrict__ itw) {
   constexpr int E = 1 << RR;
-  const u64 q2 = 2 * q;
+  const T q2 = 2 * q;
 #pragma unroll
   for (int ss = RR - 1; ss >= 0; --ss) {
     const int s = s0 + ss;
@@ -86,22 +102,23 @@ __device__ __forceinline__ void inv_group(u64 (&x)[1 << RR], int base, int logN,
 #pragma unroll
     for (int i = 0; i < E; ++i) {
       if ((i & half) == 0) {
-        const u64 W = Wt[i >> (RR - ss)].x, Ws = Wt[i >> (RR - ss)].y;
-        const u64 U = x[i], V = x[i + half];
-        u64 S = U + V;
+        T W, Ws;
+        tw_split(Wt[i >> (RR - ss)], W, Ws);
+        const T U = x[i], V = x[i + half];
+        T S = U + V;
         S = S >= q2 ? S - q2 : S;
         x[i] = S;
-        x[i + half] = shoup_lazy(U + q2 - V, W, Ws, q);
+        x[i + half] = lazy_mul((T)(U + q2 - V), W, Ws, q);
       }
     }
   }
 }
 // times N^-1, [0, 2q) -> [0, q)
-template <int E>
-__device__ __forceinline__ void inv_final(u64 (&x)[E], u64 q, u64 ninv, u64 ninvs) {
+template <int E, class T>
+__device__ __forceinline__ void inv_final(T (&x)[E], T q, T ninv, T ninvs) {
 #pragma unroll
   for (int i = 0; i < E; ++i) {
-    const u64 v = shoup_lazy(x[i], ninv, ninvs, q);
+    const T v = lazy_mul(x[i], ninv, ninvs, q);
     x[i] = v >= q ? v - q : v;
   }
 }
@@ -112,9 +129,10 @@ __device__ __forceinline__ void inv_final(u64 (&x)[E], u64 q, u64 ninv, u64 ninv
 // twiddle, then every element is reduced to [0, q).  The same residues as
 // inv_group<3> at s0 = 0 followed by inv_final, with half the products of
 // the final scaling.
-__device__ __forceinline__ void inv_group_last(u64 (&x)[8], int base, int logN, u64 q,
-                                               const ulonglong2* __restrict__ itw, u64 ninv, u64 ninvs) {
-  const u64 q2 = 2 * q;
+template <class T>
+__device__ __forceinline__ void inv_group_last(T (&x)[8], int base, int logN, T q, const ulonglong2* __restrict__ itw,
+                                               T ninv, T ninvs) {
+  const T q2 = 2 * q;
 #pragma unroll
   for (int ss = 2; ss >= 1; --ss) {
     const int half = 1 << (2 - ss);
@@ -125,22 +143,24 @@ __device__ __forceinline__ void inv_group_last(u64 (&x)[8], int base, int logN, 
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
       if ((i & half) == 0) {
-        const u64 W = Wt[i >> (3 - ss)].x, Ws = Wt[i >> (3 - ss)].y;
-        const u64 U = x[i], V = x[i + half];
-        u64 S = U + V;
+        T W, Ws;
+        tw_split(Wt[i >> (3 - ss)], W, Ws);
+        const T U = x[i], V = x[i + half];
+        T S = U + V;
         S = S >= q2 ? S - q2 : S;
         x[i] = S;
-        x[i + half] = shoup_lazy(U + q2 - V, W, Ws, q);
+        x[i + half] = lazy_mul((T)(U + q2 - V), W, Ws, q);
       }
     }
   }
-  const ulonglong2 Wn = __ldg(itw);
+  T Wn, Wns;
+  tw_split(__ldg(itw), Wn, Wns);
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
-    const u64 U = x[i], V = x[i + 4];
-    u64 S = U + V;
+    const T U = x[i], V = x[i + 4];
+    T S = U + V;
     S = S >= q2 ? S - q2 : S;
-    const u64 a = shoup_lazy(S, ninv, ninvs, q), b = shoup_lazy(U + q2 - V, Wn.x, Wn.y, q);
+    const T a = lazy_mul(S, ninv, ninvs, q), b = lazy_mul((T)(U + q2 - V), Wn, Wns, q);
     x[i] = a >= q ? a - q : a;
     x[i + 4] = b >= q ? b - q : b;
   }
@@ -164,15 +184,15 @@ __device__ __forceinline__ void fwd_phase(u64* a, int N, int logN, int s0, u64 q
   }
 }
 
-template <int RR>
-__device__ __forceinline__ void inv_phase(u64* a, int N, int logN, int s0, u64 q, const ulonglong2* __restrict__ itw,
-                                          bool last, u64 ninv, u64 ninvs) {
+template <int RR, class T>
+__device__ __forceinline__ void inv_phase(T* a, int N, int logN, int s0, T q, const ulonglong2* __restrict__ itw,
+                                          bool last, T ninv, T ninvs) {
   constexpr int E = 1 << RR;
   const int slog = logN - s0 - RR;
   const int groups = N >> RR;
   for (int g = threadIdx.x; g < groups; g += blockDim.x) {
     const int base = ((g >> slog) << (slog + RR)) + (g & ((1 << slog) - 1));
-    u64 x[E];
+    T x[E];
 #pragma unroll
     for (int i = 0; i < E; ++i) x[i] = a[nsw(base + (i << slog))];
     inv_group<RR>(x, base, logN, s0, q, itw);
@@ -200,8 +220,9 @@ __device__ __forceinline__ void ntt_fwd_block(u64* a, int N, int logN, u64 q, co
 
 // a[0..N) in [0, 2q) on entry, [0, q) on exit.  The forward phases in
 // reverse order: the remainder first, then three stages at a time.
-__device__ __forceinline__ void ntt_inv_block(u64* a, int N, int logN, u64 q, const ulonglong2* __restrict__ itw,
-                                              u64 ninv, u64 ninvs) {
+template <class T>
+__device__ __forceinline__ void ntt_inv_block(T* a, int N, int logN, T q, const ulonglong2* __restrict__ itw, T ninv,
+                                              T ninvs) {
   const int rem = logN % 3;
   int s0 = logN - rem;
   if (rem == 2) nttd::inv_phase<2>(a, N, logN, s0, q, itw, s0 == 0, ninv, ninvs);
@@ -333,8 +354,8 @@ struct SplitSt {
   __device__ __forceinline__ void operator()(int x, u64 v) const { r(x, to_split(v, s)); }
   __device__ __forceinline__ void pair(int x, u64 a, u64 b) const { r.pair(x, to_split(a, s), to_split(b, s)); }
 };
-template <int E, class Load>
-__device__ __forceinline__ void load_run(u64 (&x)[E], const Load& ld, int base) {
+template <int E, class T, class Load>
+__device__ __forceinline__ void load_run(T (&x)[E], const Load& ld, int base) {
   if constexpr (has_pair<Load>::value && E >= 2) {
 #pragma unroll
     for (int i = 0; i < E; i += 2) ld.pair(base + i, x[i], x[i + 1]);
@@ -393,13 +414,13 @@ __device__ __forceinline__ void ntt_fwd_fused(u64* a, const Load& ld, const Stor
     store_run<1 << R>(x, st, base);
   }
 }
-template <int LOGN, class Load, class Store>
-__device__ __forceinline__ void ntt_inv_fused(u64* a, const Load& ld, const Store& st, u64 q,
-                                              const ulonglong2* __restrict__ itw, u64 ninv, u64 ninvs) {
+template <int LOGN, class T, class Load, class Store>
+__device__ __forceinline__ void ntt_inv_fused(T* a, const Load& ld, const Store& st, T q,
+                                              const ulonglong2* __restrict__ itw, T ninv, T ninvs) {
   constexpr int N = 1 << LOGN, R = (LOGN - 4) % 3 + 1, M = (LOGN - 3 - R) / 3, S8 = LOGN - 3;
   for (int g = threadIdx.x; g < (N >> R); g += blockDim.x) {  // stages LOGN-1 .. LOGN-R
     const int base = g << R;
-    u64 x[1 << R];
+    T x[1 << R];
     load_run<1 << R>(x, ld, base);
     nttd::inv_group<R>(x, base, LOGN, LOGN - R, q, itw);
 #pragma unroll
@@ -412,7 +433,7 @@ __device__ __forceinline__ void ntt_inv_fused(u64* a, const Load& ld, const Stor
     __syncthreads();
   }
   for (int g = threadIdx.x; g < (N >> 3); g += blockDim.x) {  // stages 2-0 and N^-1
-    u64 x[8];
+    T x[8];
 #pragma unroll
     for (int i = 0; i < 8; ++i) x[i] = a[nsw(g + (i << S8))];
     nttd::inv_group_last(x, g, LOGN, q, itw, ninv, ninvs);
@@ -452,5 +473,25 @@ __device__ __forceinline__ void ntt_inv_gg(u64* a, const Load& ld, const Store& 
   for (int x = threadIdx.x; x < V.N; x += blockDim.x) a[nsw(x)] = ld(x);
   __syncthreads();
   ntt_inv_block(a, V.N, V.logN, P.q, itw, P.ninv, P.ninvs);
+  for (int x = threadIdx.x; x < V.N; x += blockDim.x) st(x, a[nsw(x)]);
+}
+
+// ntt_inv_gg for a modulus q_pi below 2^30 (the plaintext modulus) in 32-bit
+// words: a[] holds N 32-bit words, ld(x) returns element x in [0, 2q) as
+// u32, st(x, v) receives it reduced.  The same residues as ntt_inv_gg.
+template <class Load, class Store>
+__device__ __forceinline__ void ntt_inv_gg_small(u32* a, const Load& ld, const Store& st, const DevView& V, int pi) {
+  const ulonglong2* itw = V.itwp + (size_t)pi * V.N;
+  const DevPrime P = V.pr[pi];
+  const u32 q = (u32)P.q, ninv = (u32)P.ninv, ninvs = (u32)(P.ninvs >> 32);
+  switch (V.logN) {
+    case 12: ntt_inv_fused<12>(a, ld, st, q, itw, ninv, ninvs); return;
+    case 13: ntt_inv_fused<13>(a, ld, st, q, itw, ninv, ninvs); return;
+    case 14: ntt_inv_fused<14>(a, ld, st, q, itw, ninv, ninvs); return;
+    default: break;
+  }
+  for (int x = threadIdx.x; x < V.N; x += blockDim.x) a[nsw(x)] = ld(x);
+  __syncthreads();
+  ntt_inv_block(a, V.N, V.logN, q, itw, ninv, ninvs);
   for (int x = threadIdx.x; x < V.N; x += blockDim.x) st(x, a[nsw(x)]);
 }

@@ -119,7 +119,7 @@ namespace {
 size_t request_bytes(const Lane& L, bool lazy) {
   const pepsi_ctx* c = L.c;
   const size_t kN = (size_t)c->k * c->N;
-  size_t w = (size_t)c->ell * 2 * kN + (size_t)L.Lc * 2 * kN + 3 * kN;
+  size_t w = request_prepared_words(c->ell, kN) + (size_t)L.Lc * 2 * kN + 3 * kN;
   if (lazy) w += (size_t)3 * (c->k + c->kb) * c->N;
   return w * 8;
 }
@@ -147,7 +147,7 @@ int admit(pepsi_engine* e, Lane& L, int s, u64 ticket, const Request& r, size_t 
   S.out = r.out;
   S.bytes = bytes;
   const u32 G = rescale_run(c, L.mu, r.mode);
-  cudaError_t err = pool_alloc(e, &S.C, (size_t)c->ell * 2 * kN, st);
+  cudaError_t err = pool_alloc(e, &S.C, request_prepared_words(c->ell, kN), st);
   if (err == cudaSuccess) err = pool_alloc(e, &S.H, (size_t)L.Lc * 2 * kN, st);
   if (err == cudaSuccess) err = pool_alloc(e, &S.acc, 3 * kN, st);
   if (err == cudaSuccess && G > 1) err = pool_alloc(e, &S.X, (size_t)3 * (c->k + c->kb) * c->N, st);

@@ -35,7 +35,7 @@ inline int xform_threads(const DevView& V) { return V.nt > 0 ? V.nt : ntt_thread
 // multiply-accumulate (the request's forward transform).
 template <bool FWD, bool SPLIT = false>
 __global__ void __launch_bounds__(NTT_MAX_THREADS, 1) k_ntt(DevView V, const u64* __restrict__ src, u64* dst, int np, int p0, size_t src_os,
-                      size_t dst_os) {
+                      size_t dst_os, u32* sums) {
   extern __shared__ u64 sm[];
   const int N = V.N;
   const size_t r = blockIdx.x;
@@ -46,7 +46,7 @@ __global__ void __launch_bounds__(NTT_MAX_THREADS, 1) k_ntt(DevView V, const u64
   const RowLd ld(s);
   if (FWD) {
     if (SPLIT)
-      ntt_fwd_gg(sm, ld, SplitSt(d, V.pr[p0 + pl].split), V, p0 + pl);
+      ntt_fwd_gg(sm, ld, SplitSumSt(d, sums + o * dst_os + (size_t)pl * N, V.pr[p0 + pl].split), V, p0 + pl);
     else
       ntt_fwd_gg(sm, ld, RowSt(d), V, p0 + pl);
   } else {
@@ -199,25 +199,27 @@ __global__ void __launch_bounds__(NTT_MAX_THREADS, 1) k_valgen(DevView V, const 
 // planes (P7), put back together on the load.  Every mbarrier
 // wait is bounded (about one second); on expiry the block waits, again
 // bounded, for its own copies in flight, sets *err and returns.
-// Five 40 KB stages (200 KB of the 227 KB a block may hold): at the paper
-// shape the fifth stage took the launch from 12.13 to 11.94 ms, while
-// stages of 2, 3, 5 or 6 bits, or 16 layers a block, were no faster.
+// Five 44 KB stages (220 KB of the 227 KB a block may hold): at the paper
+// shape a fifth stage took the launch from 12.13 to 11.94 ms, while stages
+// of 2, 3, 5 or 6 bits, or 16 layers a block, were no faster.
 namespace mac {
 constexpr int TN = 128, LB = 8, LPT = 2, JS = 4, NST = 5;
 constexpr int LG = LB / LPT;                    // layer slices per block
 constexpr int CONSUMER_WARPS = (TN / 32) * LG;  // 16
 constexpr int THREADS = (CONSUMER_WARPS + 1) * 32;
 constexpr int P_WORDS = LB * JS * TN, C_WORDS = 2 * JS * TN;
-// A stage holds the plaintext tile, then the request tile.  The plaintext
-// tile is 8 bytes per word (split operand format), or 7 bytes per word in
-// three planes one after another: bits 0-31, 32-47 and 48-55 of the value.
+// A stage holds the plaintext tile, then the request tile and the request's
+// half sums (4 bytes per word, read instead of added by every layer slice).
+// The plaintext tile is 8 bytes per word (split operand format), or 7 bytes
+// per word in three planes one after another: bits 0-31, 32-47 and 48-55 of
+// the value.
 template <bool P7>
 __host__ __device__ constexpr int p_bytes() {
   return P_WORDS * (P7 ? 7 : 8);
 }
 template <bool P7>
 __host__ __device__ constexpr int stage_bytes() {
-  return p_bytes<P7>() + C_WORDS * 8;
+  return p_bytes<P7>() + C_WORDS * 12;
 }
 template <bool P7>
 __host__ __device__ constexpr size_t smem() {
@@ -353,8 +355,9 @@ __device__ __forceinline__ void tma_plain(u32 sb, const CUtensorMap* tmP, const 
 template <bool P7>
 __global__ void __launch_bounds__(mac::THREADS, 1)
     k_mac(DevView V, const __grid_constant__ CUtensorMap tmP, const __grid_constant__ CUtensorMap tmPb,
-          const __grid_constant__ CUtensorMap tmPc, const __grid_constant__ CUtensorMap tmC, u64* __restrict__ H,
-          int j0, int nj, int L, int fold_stages, int acc_in, int* err) {
+          const __grid_constant__ CUtensorMap tmPc, const __grid_constant__ CUtensorMap tmC,
+          const __grid_constant__ CUtensorMap tmS, u64* __restrict__ H, int j0, int nj, int L, int fold_stages,
+          int acc_in, int* err) {
   using namespace mac;
   constexpr int SB = stage_bytes<P7>(), PB = p_bytes<P7>();
   extern __shared__ __align__(128) u64 sm_raw[];
@@ -388,6 +391,7 @@ __global__ void __launch_bounds__(mac::THREADS, 1)
     if (lane == 0) {
       asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<u64>(&tmP)) : "memory");
       asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<u64>(&tmC)) : "memory");
+      asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<u64>(&tmS)) : "memory");
       for (int st = 0; st < nst; ++st) {
         const int buf = st % NST;
         if (st >= NST && !mbar_wait_bounded(empty0 + 8 * buf, (u32)(((st / NST) - 1) & 1))) {
@@ -400,6 +404,7 @@ __global__ void __launch_bounds__(mac::THREADS, 1)
         mbar_expect_tx(bar, (u32)SB);
         tma_plain<P7>(sb, &tmP, &tmPb, &tmPc, (int)idx0, j0 + st * JS, l0, bar);
         tma_load_3d(sb + (u32)PB, &tmC, (int)idx0, 0, j0 + st * JS, bar);
+        tma_load_3d(sb + (u32)(PB + C_WORDS * 8), &tmS, (int)idx0, 0, j0 + st * JS, bar);
         issued = st + 1;
       }
     }
@@ -431,11 +436,12 @@ __global__ void __launch_bounds__(mac::THREADS, 1)
       const unsigned char* stg = sm + (size_t)buf * SB;
       const int po = g * LPT * JS * TN + tp;  // word (slice, bit 0, point) of the tile
       const u64* cs = reinterpret_cast<const u64*>(stg + PB) + tp;
+      const u32* ss = reinterpret_cast<const u32*>(stg + PB + C_WORDS * 8) + tp;
 #pragma unroll
       for (int jj = 0; jj < JS; ++jj) {
         const u64 c0 = cs[(jj * 2) * TN], c1 = cs[(jj * 2 + 1) * TN];
         const u32 c0l = (u32)c0, c0h = (u32)(c0 >> 32), c1l = (u32)c1, c1h = (u32)(c1 >> 32);
-        const u32 c0s = c0l + c0h, c1s = c1l + c1h;
+        const u32 c0s = ss[(jj * 2) * TN], c1s = ss[(jj * 2 + 1) * TN];
 #pragma unroll
         for (int l = 0; l < LPT; ++l) {
           u32 xl, xh;
@@ -484,14 +490,16 @@ __global__ void __launch_bounds__(mac::THREADS, 1)
 // words and LB = 16/WPS layers.  Each of the 8 consumer warps covers 32
 // points of one layer slice; each consumer thread one point, LPT = 2 layers
 // and all QB requests: a plaintext word loaded from shared memory serves
-// 2*QB products and a request word LPT products, so a 4-request batch
-// reads 10 shared-memory words per 48 multiply-adds (the SM's shared-memory
-// bandwidth is a quarter of its wide multiply-add rate in 8-byte words).
+// 2*QB products and a request word (with its half sum) LPT products, so a
+// 4-request batch reads 10 shared-memory words and 8 half sums per 48
+// multiply-adds (the SM's shared-memory bandwidth is a quarter of its wide
+// multiply-add rate in 8-byte words).
 // Its 48 64-bit partial sums per thread are why there are 8 consumer warps:
 // with the producer, 9 warps put at most 3 on an SM sub-partition, whose
 // 16K registers then allow 168 per thread (13 warps would cap them at
-// 128 and spill).  Each request's tile is one 3-D TMA box (points x
-// components x bits, plain loads of this GPU's memory).  Same
+// 128 and spill).  Each request's tile is two 3-D TMA boxes (points x
+// components x bits: its split words and their half sums, plain loads of
+// this GPU's memory).  Same
 // pipeline, split operands, Karatsuba sums, folding and bounded waits as
 // k_mac.  Each request has its own tensor map and output, so the requests
 // may live anywhere; the tile width WPS is a schedule choice (wider rows per copy
@@ -514,9 +522,14 @@ template <int QB, int WPS, bool P7>
 __host__ __device__ constexpr int p_bytes() {
   return Tile<WPS>::P_WORDS * (P7 ? 7 : 8);
 }
+// request q's tile of split words, then its tile of half sums
+template <int WPS>
+__host__ __device__ constexpr int req_bytes() {
+  return 2 * JS * Tile<WPS>::TN * 12;
+}
 template <int QB, int WPS, bool P7>
 __host__ __device__ constexpr int stage_bytes() {
-  return p_bytes<QB, WPS, P7>() + QB * 2 * JS * Tile<WPS>::TN * 8;
+  return p_bytes<QB, WPS, P7>() + QB * req_bytes<WPS>();
 }
 template <int QB, int WPS, bool P7>
 __host__ __device__ constexpr size_t smem() {
@@ -597,8 +610,10 @@ __global__ void __launch_bounds__(macq::threads(RG), 1)
     if (lane == 0) {
       asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<u64>(&tmP)) : "memory");
 #pragma unroll
-      for (int q = 0; q < QB; ++q)
+      for (int q = 0; q < QB; ++q) {
         asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<u64>(&rq.c[q])) : "memory");
+        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<u64>(&rq.s[q])) : "memory");
+      }
       for (int st = 0; st < nst; ++st) {
         const int buf = st % NST;
         if (st >= NST && !mbar_wait_bounded(empty0 + 8 * buf, (u32)(((st / NST) - 1) & 1))) {
@@ -611,8 +626,11 @@ __global__ void __launch_bounds__(macq::threads(RG), 1)
         mbar_expect_tx(bar, (u32)SB);
         tma_plain_pw<P7, PW>(sb, &tmP, &tmPb, &tmPc, (int)idx0, st * JS, l0, bar);
 #pragma unroll
-        for (int q = 0; q < QB; ++q)
-          tma_load_3d(sb + (u32)(PB + q * 2 * JS * TN * 8), &rq.c[q], (int)idx0, 0, st * JS, bar);
+        for (int q = 0; q < QB; ++q) {
+          const u32 rb = sb + (u32)(PB + q * req_bytes<WPS>());
+          tma_load_3d(rb, &rq.c[q], (int)idx0, 0, st * JS, bar);
+          tma_load_3d(rb + (u32)(2 * JS * TN * 8), &rq.s[q], (int)idx0, 0, st * JS, bar);
+        }
         issued = st + 1;
       }
     }
@@ -641,7 +659,7 @@ __global__ void __launch_bounds__(macq::threads(RG), 1)
       }
       const unsigned char* stg = sm + (size_t)buf * SB;
       const int po = g * LPT * JS * TN + tp;  // word (slice, bit 0, point) of the plaintext tile
-      const u64* cs = reinterpret_cast<const u64*>(stg + PB) + rg * QT * 2 * JS * TN + tp;
+      const unsigned char* rqt = stg + PB + rg * QT * req_bytes<WPS>();  // this group's request tiles
 #pragma unroll
       for (int jj = 0; jj < JS; ++jj) {
         u32 xl[LPT], xh[LPT], xs[LPT];
@@ -654,8 +672,10 @@ __global__ void __launch_bounds__(macq::threads(RG), 1)
         for (int q = 0; q < QT; ++q)
 #pragma unroll
           for (int c = 0; c < 2; ++c) {
-            const u64 w = cs[((q * JS + jj) * 2 + c) * TN];
-            const u32 cl = (u32)w, ch = (u32)(w >> 32), csum = cl + ch;
+            const unsigned char* t = rqt + q * req_bytes<WPS>();
+            const u64 w = reinterpret_cast<const u64*>(t)[(jj * 2 + c) * TN + tp];
+            const u32 cl = (u32)w, ch = (u32)(w >> 32);
+            const u32 csum = reinterpret_cast<const u32*>(t + 2 * JS * TN * 8)[(jj * 2 + c) * TN + tp];
 #pragma unroll
             for (int l = 0; l < LPT; ++l)
               kmac(S0[l][q][c], SM[l][q][c], S2[l][q][c], cl, ch, csum, xl[l], xh[l], xs[l]);
@@ -1413,16 +1433,16 @@ inline unsigned grid_for(size_t total, int threads) { return (unsigned)((total +
 
 // ------------------------------------------------------------ launchers
 void launch_ntt(const DevView& V, bool fwd, const u64* src, u64* dst, size_t outer, int np, int p0, size_t src_os,
-                size_t dst_os, cudaStream_t st, bool split_out) {
+                size_t dst_os, cudaStream_t st, bool split_out, u32* sums) {
   const size_t rows = outer * (size_t)np;
   if (!rows) return;
   const size_t smem = (size_t)V.N * sizeof(u64);
   if (fwd && split_out)
-    k_ntt<true, true><<<(unsigned)rows, xform_threads(V), smem, st>>>(V, src, dst, np, p0, src_os, dst_os);
+    k_ntt<true, true><<<(unsigned)rows, xform_threads(V), smem, st>>>(V, src, dst, np, p0, src_os, dst_os, sums);
   else if (fwd)
-    k_ntt<true><<<(unsigned)rows, xform_threads(V), smem, st>>>(V, src, dst, np, p0, src_os, dst_os);
+    k_ntt<true><<<(unsigned)rows, xform_threads(V), smem, st>>>(V, src, dst, np, p0, src_os, dst_os, nullptr);
   else
-    k_ntt<false><<<(unsigned)rows, xform_threads(V), smem, st>>>(V, src, dst, np, p0, src_os, dst_os);
+    k_ntt<false><<<(unsigned)rows, xform_threads(V), smem, st>>>(V, src, dst, np, p0, src_os, dst_os, nullptr);
 }
 
 void launch_cw_unrank(const u64* T, size_t count, const u64* binom, int ell, int h, uint16_t* pos, cudaStream_t st) {
@@ -1536,7 +1556,10 @@ cudaError_t launch_mac_requests(const DevView& V, int nq, const u64* const* C, c
   memset(&rq, 0, sizeof(rq));
   if (!encode_plain(tmP, P, kN, ell, L, tn, macq::JS, lb)) return cudaErrorInvalidValue;
   for (int q = 0; q < nq; ++q) {
-    if (!encode3d(&rq.c[q], C[q], kN, 2, ell, kN, 2 * kN, tn, 2, macq::JS)) return cudaErrorInvalidValue;
+    if (!encode3d(&rq.c[q], C[q], kN, 2, ell, kN, 2 * kN, tn, 2, macq::JS) ||
+        !encode3d_t(&rq.s[q], CU_TENSOR_MAP_DATA_TYPE_UINT32, 4, request_sums(C[q], ell, kN), kN, 2, ell, kN, 2 * kN, tn,
+                    2, macq::JS))
+      return cudaErrorInvalidValue;
     rq.h[q] = H[q];
   }
   const int fold_stages = fold / macq::JS > 0 ? fold / macq::JS : 1;
@@ -1560,7 +1583,7 @@ cudaError_t launch_mac_multi(const DevView& V, const u64* C, int nq, const Plain
   const u64* cq[macq::QMAX];
   u64* hqv[macq::QMAX];
   for (int q = 0; q < nq; ++q) {
-    cq[q] = C + (size_t)q * ell * 2 * V.k * V.N;
+    cq[q] = C + (size_t)q * request_prepared_words(ell, (size_t)V.k * V.N);
     hqv[q] = H + (size_t)q * hq;
   }
   return launch_mac_requests(V, nq, cq, P, hqv, ell, L, fold, err, st, tile_points, groups);
@@ -1573,17 +1596,19 @@ cudaError_t launch_mac(const DevView& V, const u64* C, const PlainTab& P, u64* H
   if (j0 < 0 || nj <= 0 || j0 + nj > ell || (j0 % mac::JS) || (j0 + nj < ell && nj % mac::JS))
     return cudaErrorInvalidValue;
   const u64 kN = (u64)V.k * V.N;
-  CUtensorMap tmP[3], tmC;
+  CUtensorMap tmP[3], tmC, tmS;
   if (!encode_plain(tmP, P, kN, ell, L, mac::TN, mac::JS, mac::LB) ||
-      !encode3d(&tmC, C, kN, 2, ell, kN, 2 * kN, mac::TN, 2, mac::JS))
+      !encode3d(&tmC, C, kN, 2, ell, kN, 2 * kN, mac::TN, 2, mac::JS) ||
+      !encode3d_t(&tmS, CU_TENSOR_MAP_DATA_TYPE_UINT32, 4, request_sums(C, ell, kN), kN, 2, ell, kN, 2 * kN, mac::TN, 2,
+                  mac::JS))
     return cudaErrorInvalidValue;
   const int fold_stages = fold / mac::JS > 0 ? fold / mac::JS : 1;
   dim3 grid((L + mac::LB - 1) / mac::LB, (unsigned)((kN + mac::TN - 1) / mac::TN));
   if (P.packed())
-    k_mac<true><<<grid, mac::THREADS, mac::smem<true>(), st>>>(V, tmP[0], tmP[1], tmP[2], tmC, H, j0, nj, L,
+    k_mac<true><<<grid, mac::THREADS, mac::smem<true>(), st>>>(V, tmP[0], tmP[1], tmP[2], tmC, tmS, H, j0, nj, L,
                                                                fold_stages, acc_in ? 1 : 0, err);
   else
-    k_mac<false><<<grid, mac::THREADS, mac::smem<false>(), st>>>(V, tmP[0], tmP[1], tmP[2], tmC, H, j0, nj, L,
+    k_mac<false><<<grid, mac::THREADS, mac::smem<false>(), st>>>(V, tmP[0], tmP[1], tmP[2], tmC, tmS, H, j0, nj, L,
                                                                  fold_stages, acc_in ? 1 : 0, err);
   return cudaSuccess;
 }

@@ -8,8 +8,20 @@
 
 // Batched NTT over rows laid out [outer][np][N]: row r uses prime p0 + (r % np);
 // src and dst may alias (in place).  fwd: coefficient -> evaluation form.
+// split_out (forward only): dst receives the split operand format of the
+// multiply-accumulate, and sums (rows laid out as dst's, 32-bit words) the
+// sum of each word's two halves.
 void launch_ntt(const DevView& V, bool fwd, const u64* src, u64* dst, size_t outer, int np, int p0, size_t src_os,
-                size_t dst_os, cudaStream_t st, bool split_out = false);
+                size_t dst_os, cudaStream_t st, bool split_out = false, u32* sums = nullptr);
+
+// A request prepared for the multiply-accumulate: its ell*2*k*N words in
+// the split operand format, [ell][2][k][N], followed by the 32-bit sums of
+// their halves in the same order (request_sums), 12 bytes per word in all.
+inline size_t request_prepared_words(int ell, size_t kN) { return (size_t)ell * 3 * kN; }
+inline u32* request_sums(u64* C, int ell, size_t kN) { return reinterpret_cast<u32*>(C + (size_t)ell * 2 * kN); }
+inline const u32* request_sums(const u64* C, int ell, size_t kN) {
+  return reinterpret_cast<const u32*>(C + (size_t)ell * 2 * kN);
+}
 
 // CW-Encode of table entries (colex rank -> positions), pos[count][h], dummy -> PEPSI_CW_NONE.
 void launch_cw_unrank(const u64* T, size_t count, const u64* binom, int ell, int h, uint16_t* pos, cudaStream_t st);
@@ -47,21 +59,22 @@ inline PlainTab plain_words(const u64* w) {
 }
 
 // Fused ct x pt multiply-accumulate: H[l][c][p][n] = sum_j C[j][c][p][n] * P[l][j][p][n] mod q_p.
-// C in the split operand format, H reduced.  fold: terms between folds of the
+// C a prepared request (split operand format and half sums), H reduced.  fold: terms between folds of the
 // 64-bit partial sums.  *err is set when a bounded wait for a TMA copy expires.
 // Returns cudaErrorInvalidValue when the tensor maps of the copies cannot be encoded.
 cudaError_t launch_mac(const DevView& V, const u64* C, const PlainTab& P, u64* H, int ell, int L, int fold, int* err,
                        cudaStream_t st, int j0 = 0, int nj = -1, bool acc_in = false);
 
-// The same for nq <= PEPSI_MAC_MAX_REQUESTS requests sharing the plaintexts: request q
-// [ell][2][k][N] (split format) at C[q], its h' [L][2][k][N] to H[q].  tile_points: 32
+// The same for nq <= PEPSI_MAC_MAX_REQUESTS requests sharing the plaintexts: prepared request q
+// at C[q], its h' [L][2][k][N] to H[q].  tile_points: 32
 // or 64 points per block (16 or 8 layers); groups: 1 = each consumer thread serves every
 // request, 2 = two groups of warps serve half of them each (2 or 4 requests; 3 requests
 // always run in one group); one request runs launch_mac.
 cudaError_t launch_mac_requests(const DevView& V, int nq, const u64* const* C, const PlainTab& P, u64* const* H,
                                 int ell, int L, int fold, int* err, cudaStream_t st, int tile_points = 32,
                                 int groups = 2);
-// The same with the requests back to back in C ([nq][ell][2][k][N]) and H[q] at H + q * hq.
+// The same with the prepared requests back to back in C (request_prepared_words apart) and H[q]
+// at H + q * hq.
 cudaError_t launch_mac_multi(const DevView& V, const u64* C, int nq, const PlainTab& P, u64* H, size_t hq, int ell,
                              int L, int fold, int* err, cudaStream_t st, int tile_points = 32, int groups = 2);
 // count split-format words (rows [..][k][N]) to the three planes of the 7-byte format, and back
@@ -72,6 +85,7 @@ constexpr int PEPSI_MAC_MAX_REQUESTS = 4;
 // Per-request operands of the multi-request multiply-accumulate (passed by value).
 struct MacRequests {
   CUtensorMap c[PEPSI_MAC_MAX_REQUESTS];  // request tiles
+  CUtensorMap s[PEPSI_MAC_MAX_REQUESTS];  // their half sums
   u64* h[PEPSI_MAC_MAX_REQUESTS];         // h' outputs [L][2][k][N]
 };
 

@@ -354,6 +354,24 @@ struct SplitSt {
   __device__ __forceinline__ void operator()(int x, u64 v) const { r(x, to_split(v, s)); }
   __device__ __forceinline__ void pair(int x, u64 a, u64 b) const { r.pair(x, to_split(a, s), to_split(b, s)); }
 };
+// the split operand format plus the 32-bit sum of each word's halves
+struct SplitSumSt {
+  SplitSt w;
+  u32* sum;
+  __device__ __forceinline__ SplitSumSt(u64* row, u32* sums, u64 shift) : w(row, shift), sum(sums) {}
+  __device__ __forceinline__ static u32 halves(u64 v) { return (u32)v + (u32)(v >> 32); }
+  __device__ __forceinline__ void operator()(int x, u64 v) const {
+    const u64 t = to_split(v, w.s);
+    w.r(x, t);
+    sum[x] = halves(t);
+  }
+  __device__ __forceinline__ void pair(int x, u64 a, u64 b) const {
+    const u64 ta = to_split(a, w.s), tb = to_split(b, w.s);
+    w.r.pair(x, ta, tb);
+    sum[x] = halves(ta);
+    sum[x + 1] = halves(tb);
+  }
+};
 template <int E, class T, class Load>
 __device__ __forceinline__ void load_run(T (&x)[E], const Load& ld, int base) {
   if constexpr (has_pair<Load>::value && E >= 2) {

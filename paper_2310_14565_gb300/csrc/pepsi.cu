@@ -177,7 +177,7 @@ cudaError_t eval_bufs(pepsi_ctx* c, int Lc, bool need_pc, EvalBufs* b) {
   cudaError_t e = cudaSuccess;
   const size_t N = c->N, k = c->k, kb = c->kb, np = k + kb;
   auto get = [&](int id, size_t words) { return (u64*)scratch(c, id, words * 8, &e); };
-  b->C = get(S_C, (size_t)c->ell * 2 * k * N);
+  b->C = get(S_C, request_prepared_words(c->ell, k * N));
   b->H = get(S_H, Lc * 2 * k * N);
   b->Hc = get(S_HC, Lc * 2 * k * N);
   b->XB = get(S_XB, Lc * 2 * kb * N);
@@ -330,7 +330,8 @@ cudaError_t copy_any(void* dst, const void* src, size_t bytes, cudaStream_t st) 
 }
 
 // a4: request ciphertexts (host or device) to NTT form, then to the split
-// operand format of the multiply-accumulate, into C.
+// operand format of the multiply-accumulate with the sums of the halves,
+// into C (request_prepared_words).
 cudaError_t prepare_request(pepsi_ctx* c, const u64* cts, u64* C, cudaStream_t st) {
   const size_t kN = (size_t)c->k * c->N, words = (size_t)c->ell * 2 * kN;
   const u64* src = cts;
@@ -339,7 +340,7 @@ cudaError_t prepare_request(pepsi_ctx* c, const u64* cts, u64* C, cudaStream_t s
     src = C;
   }
   Prof p(c, PC_NTT, st);  // forward NTT, stored in the split operand format
-  launch_ntt(c->V, true, src, C, (size_t)c->ell * 2, c->k, 0, kN, kN, st, true);
+  launch_ntt(c->V, true, src, C, (size_t)c->ell * 2, c->k, 0, kN, kN, st, true, request_sums(C, c->ell, kN));
   return cudaSuccess;
 }
 
@@ -490,7 +491,8 @@ int eval_core(pepsi_ctx* c, int set_id, const u64* cts, u32 layer0, u32 nl, int 
         {
           Prof p(c, PC_NTT, st);  // forward NTT of the piece, stored in the split format
           launch_ntt(c->V, true, b.C + (size_t)jb[q] * ct2, b.C + (size_t)jb[q] * ct2,
-                     (size_t)(jb[q + 1] - jb[q]) * 2, c->k, 0, kN, kN, st, true);
+                     (size_t)(jb[q + 1] - jb[q]) * 2, c->k, 0, kN, kN, st, true,
+                     request_sums(b.C, c->ell, kN) + (size_t)jb[q] * ct2);
         }
         Prof p(c, PC_MAC, st);
         CKS(mac_status(launch_mac(c->V, b.C, P0, Hall, c->ell, (int)(res_end - layer0), c->mac_fold, c->d_err, st,
@@ -563,7 +565,7 @@ enum { S_CB = 41, S_HB = 42, S_ACCB = 43, S_CB2 = 44, S_HB2 = 45, S_ACCXB = 47 }
 int eval_batch_core(pepsi_ctx* c, int nq, const int* set_ids, const u64* const* cts, const int* modes,
                     const u64* mask_seeds, u64* const* outs, cudaStream_t st) {
   const size_t k = c->k, N = c->N, kN = k * N, ct2 = 2 * kN, ct3 = 3 * kN;
-  const size_t cwords = (size_t)c->ell * ct2;
+  const size_t cwords = request_prepared_words(c->ell, kN);
   for (int i = 0; i < nq; ++i) {
     if (set_ids[i] < 0 || set_ids[i] >= (int)c->sets.size() || !c->sets[set_ids[i]].live || !cts[i] || !outs[i])
       return PEPSI_E_PARAM;

@@ -129,7 +129,9 @@ def test_engine_thread_device_buffers_and_budget():
     dev = [torch.from_numpy(x.view(np.int64).copy()).cuda() for x in reqs]
     outs = [torch.zeros(2 * 64, dtype=torch.int64, device="cuda") for _ in reqs]
     torch.cuda.synchronize()
-    one = (gA.ell * 2 * gA.k * 64 + 3 * 2 * gA.k * 64 + 3 * gA.k * 64 + 3 * (gA.k + gA.kb) * 64) * 8
+    # one request's device state: the prepared request (split words and their 32-bit half sums,
+    # 12 bytes per word), h' of a 3-layer chunk, the layer sum and the lazy run sum
+    one = (gA.ell * 3 * gA.k * 64 + 3 * 2 * gA.k * 64 + 3 * gA.k * 64 + 3 * (gA.k + gA.kb) * 64) * 8
     for budget, slots in ((0, 4), (one, 4)):
         eng = pepsi.Engine([(gA, a2, slots)], hbm_budget=budget)
         eng.start()

@@ -284,8 +284,9 @@ int pepsi_eval(pepsi_ctx* ctx, int set_id, const uint64_t* cts, int mode, uint64
  * then the threads per transform block (the default for N, half
  * and twice it), then for h = 4 and 8 the fused against the stored
  * relinearisation before the affine step, then the requests per shared
- * multiply-accumulate launch (1, 2 or 4, timed on a batch of four copies of
- * the request through pepsi_eval_batch).  *chosen (may be NULL) receives
+ * multiply-accumulate launch with its warp groups ((1), (2, 2), (2, 1),
+ * (4, 2), (4, 1), timed on a batch of four copies of the request through
+ * pepsi_eval_batch).  *chosen (may be NULL) receives
  * the chunk.  The result words do not depend on the schedule.
  * Synchronises the stream.  Errors: as pepsi_eval. */
 int pepsi_autotune(pepsi_ctx* ctx, int set_id, const uint64_t* cts, void* stream, uint32_t* chosen);

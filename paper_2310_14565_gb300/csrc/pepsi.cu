@@ -1576,10 +1576,13 @@ int pepsi_autotune(pepsi_ctx* c, int set_id, const uint64_t* cts, void* stream, 
     const int ids[4] = {set_id, set_id, set_id, set_id};
     const u64* in[4] = {cts, cts, cts, cts};
     float best_b = 0;
-    int best_r = c->batch_requests;
-    for (int br : {1, 2, 4}) {
+    int best_r = c->batch_requests, best_g = c->batch_groups;
+    const int cand[5][2] = {{1, 2}, {2, 2}, {2, 1}, {4, 2}, {4, 1}};  // (requests, warp groups)
+    for (const auto& rg : cand) {
       if (rc) break;
+      const int br = rg[0];
       c->batch_requests = br;
+      c->batch_groups = rg[1];
       for (int rep = 0; rep < 3 && !rc; ++rep) {
         if (rep == 1) cudaEventRecord(e0, st);
         rc = pepsi_eval_batch(c, 4, ids, in, nullptr, nullptr, outs.data(), st);
@@ -1596,15 +1599,18 @@ int pepsi_autotune(pepsi_ctx* c, int set_id, const uint64_t* cts, void* stream, 
       if (best_b == 0 || ms < best_b) {
         best_b = ms;
         best_r = br;
+        best_g = rg[1];
       }
     }
     c->batch_requests = best_r;
+    c->batch_groups = best_g;
   }
   if (rc) {
     c->chunk = (int)saved.chunk;
     c->V.nt = (int)saved.ntt_threads;
     c->relin_fused = saved.relin_fused != 0;
     c->batch_requests = (int)saved.batch_requests;
+    c->batch_groups = (int)saved.batch_groups;
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);

@@ -574,11 +574,11 @@ def run_ours(args):
     mac_launches, mac_ms = prof["mac"]
     mac_launches_per_eval = mac_launches / psteps
     # algorithmic bytes of the MAC per evaluation: the plaintext table (mu*ell*k*N words of
-    # pbytes = 7 or 8 bytes), the request (ell*2*k*N words, read once by each launch) and
-    # h' (mu*2*k*N words), 8 bytes each
+    # pbytes = 7 or 8 bytes), the prepared request (ell*2*k*N words of 8 bytes and their
+    # 4-byte half sums, read once by each launch) and h' (mu*2*k*N words of 8 bytes)
     mu, ell = WL["mu"], WL["ell"]
-    mac_bytes_eval = (pbytes * mu * ell * k * N +
-                      8 * (mac_launches_per_eval * ell * 2 * k * N + mu * 2 * k * N))
+    mac_bytes_eval = (pbytes * mu * ell * k * N + 12 * mac_launches_per_eval * ell * 2 * k * N +
+                      8 * mu * 2 * k * N)
     mac_launch_ms = mac_ms / mac_launches
     achieved = mac_bytes_eval / mac_launches_per_eval / (mac_launch_ms * 1e-3) / 1e9
     peak, peak_kind = measured_peaks()

@@ -161,6 +161,7 @@ inline int balanced_chunk(int chunk, unsigned n) {
 }
 // scratch slot `id` of the context with at least `bytes`
 void* scratch(pepsi_ctx* c, int id, size_t bytes, cudaError_t* err);
+void scratch_release(pepsi_ctx* c, int id);
 void prof_collect(pepsi_ctx* c);
 
 // Per-launch accounting (launch counts always; CUDA events when profiling).

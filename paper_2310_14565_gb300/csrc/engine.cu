@@ -111,6 +111,7 @@ struct pepsi_graph {
   cudaStream_t last = nullptr; // stream of the last launch
   int* err = nullptr;          // pinned: each lane's error word after the last launch
   int nlanes = 0;
+  int device = -1;             // the lanes' device (its graph memory pool)
 };
 
 namespace {
@@ -598,6 +599,7 @@ int pepsi_engine_capture(pepsi_engine* e, void* stream, pepsi_graph** out) {
   for (auto& rt : routed) e->lanes[rt.first].queue.push_back(rt.second);
   auto* g = new pepsi_graph();
   g->nlanes = (int)e->lanes.size();
+  g->device = e->lanes.empty() ? -1 : e->lanes[0].c->device;
   cudaError_t err = cudaHostAlloc((void**)&g->err, g->nlanes * sizeof(int), 0);
   if (err == cudaSuccess) memset(g->err, 0, g->nlanes * sizeof(int));
   cudaStream_t origin = (cudaStream_t)stream;
@@ -710,11 +712,15 @@ int pepsi_graph_launch(pepsi_graph* g, void* stream, int synchronize) {
 void pepsi_graph_destroy(pepsi_graph* g) {
   if (!g) return;
   if (g->last) cudaStreamSynchronize(g->last);
+  const int trim = g->exec ? g->device : -1;
   if (g->exec) cudaGraphExecDestroy(g->exec);
   if (g->graph) cudaGraphDestroy(g->graph);
   if (g->own) cudaStreamDestroy(g->own);
   if (g->err) cudaFreeHost(g->err);
   delete g;
+  // the graph's request state came from the device's graph memory pool,
+  // which keeps its physical memory until trimmed
+  if (trim >= 0) cudaDeviceGraphMemTrim(trim);
 }
 
 void pepsi_engine_destroy(pepsi_engine* e) {

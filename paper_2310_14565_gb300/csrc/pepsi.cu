@@ -63,6 +63,14 @@ void* scratch(pepsi_ctx* c, int id, size_t bytes, cudaError_t* err) {
   return b.p;
 }
 
+// Free scratch slot `id` (after the device has finished with it).
+void scratch_release(pepsi_ctx* c, int id) {
+  if ((int)c->scratch.size() <= id || !c->scratch[id].p) return;
+  cudaDeviceSynchronize();
+  cudaFree(c->scratch[id].p);
+  c->scratch[id].p = nullptr;
+  c->scratch[id].bytes = 0;
+}
 
 void prof_collect(pepsi_ctx* c) {
   for (auto& pe : c->prof_ev) {
@@ -1604,6 +1612,11 @@ int pepsi_autotune(pepsi_ctx* c, int set_id, const uint64_t* cts, void* stream, 
     }
     c->batch_requests = best_r;
     c->batch_groups = best_g;
+    // the batch buffers served only the timing: four requests' prepared
+    // words, h' and sums, twice, are not kept for evaluations that may
+    // never batch
+    for (int id : {(int)S_CB, (int)S_CB2, (int)S_HB, (int)S_HB2, (int)S_ACCB, (int)S_ACCXB, kScratchTuneBatch})
+      scratch_release(c, id);
   }
   if (rc) {
     c->chunk = (int)saved.chunk;

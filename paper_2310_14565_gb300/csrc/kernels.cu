@@ -29,6 +29,11 @@ inline int ntt_threads(int N) {
 // Threads of the hot-path transform kernels: the schedule's choice
 // (DevView::nt, picked by the autotuner), else the default above.
 inline int xform_threads(const DevView& V) { return V.nt > 0 ? V.nt : ntt_threads(V.N); }
+// The relinearisation transforms come in two register budgets: MT = 256 for
+// blocks of at most 256 threads, three per SM (80 registers a thread; at N =
+// 8192 with 256-thread blocks the relinearisation took 1.98 ms against
+// 2.07 ms at 64), and MT = NTT_MAX_THREADS for larger blocks (64 registers).
+constexpr int relin_min_blocks(int MT) { return MT <= 256 ? 3 : 1; }
 
 // ------------------------------------------------------------------ NTT
 // SPLIT: store the result in the split operand format of the
@@ -932,7 +937,8 @@ __global__ void __launch_bounds__(NTT_MAX_THREADS, 1)
 // and u = R_c + z * H on the load of the inverse NTT of U, stores u and the
 // coefficient-form row.  The same words as k_relin_mac followed by
 // k_axpy_intt, without R in memory.
-__global__ void __launch_bounds__(NTT_MAX_THREADS, 1)
+template <int MT>
+__global__ void __launch_bounds__(MT, relin_min_blocks(MT))
     k_relin_axpy_intt(DevView V, const u64* __restrict__ DG, const u64* __restrict__ rlk,
                       const u64* __restrict__ zres, const u64* __restrict__ H, u64* __restrict__ out, u64* coef) {
   extern __shared__ u64 sm[];
@@ -1123,7 +1129,8 @@ __global__ void k_scale_round(const __grid_constant__ RnsArgs A, const u64* __re
 // Phase 1, block per row of DG[L][k+2][k][N]: row (l, i, j) holds
 // NTT_{q_j}([d2]_{q_i}) for digits i < k, and NTT_{q_j}(d0), NTT_{q_j}(d1)
 // for i = k, k+1.
-__global__ void __launch_bounds__(NTT_MAX_THREADS, 1) k_relin_ntt(DevView V, const u64* __restrict__ D, u64* __restrict__ DG) {
+template <int MT>
+__global__ void __launch_bounds__(MT, relin_min_blocks(MT)) k_relin_ntt(DevView V, const u64* __restrict__ D, u64* __restrict__ DG) {
   extern __shared__ u64 sm[];
   const int N = V.N, k = V.k;
   const size_t r = blockIdx.x;
@@ -1705,24 +1712,31 @@ void launch_scale_round(const DevView& V, const u64* T3, u64* D, int L, cudaStre
 #undef SCALE
 }
 
-void launch_relin(const DevView& V, const u64* D, const u64* rlk, u64* DG, u64* R, int L, cudaStream_t st) {
-  if (L <= 0) return;
-  const size_t rows = (size_t)L * (V.k + 2) * V.k;
-  k_relin_ntt<<<(unsigned)rows, xform_threads(V), (size_t)V.N * 8, st>>>(V, D, DG);
-  k_relin_mac<<<grid_for((size_t)L * V.k * V.N, 256), 256, 0, st>>>(V, DG, rlk, R, L);
-}
-
 void launch_relin_digits(const DevView& V, const u64* D, u64* DG, int L, cudaStream_t st) {
   if (L <= 0) return;
   const size_t rows = (size_t)L * (V.k + 2) * V.k;
-  k_relin_ntt<<<(unsigned)rows, xform_threads(V), (size_t)V.N * 8, st>>>(V, D, DG);
+  const int nt = xform_threads(V);
+  if (nt <= 256)
+    k_relin_ntt<256><<<(unsigned)rows, nt, (size_t)V.N * 8, st>>>(V, D, DG);
+  else
+    k_relin_ntt<NTT_MAX_THREADS><<<(unsigned)rows, nt, (size_t)V.N * 8, st>>>(V, D, DG);
+}
+
+void launch_relin(const DevView& V, const u64* D, const u64* rlk, u64* DG, u64* R, int L, cudaStream_t st) {
+  if (L <= 0) return;
+  launch_relin_digits(V, D, DG, L, st);
+  k_relin_mac<<<grid_for((size_t)L * V.k * V.N, 256), 256, 0, st>>>(V, DG, rlk, R, L);
 }
 
 void launch_relin_axpy_intt(const DevView& V, const u64* DG, const u64* rlk, const u64* zres, const u64* H, u64* out,
                             u64* coef, int L, cudaStream_t st) {
   const size_t rows = (size_t)L * 2 * V.k;
   if (!rows) return;
-  k_relin_axpy_intt<<<(unsigned)rows, xform_threads(V), (size_t)V.N * 8, st>>>(V, DG, rlk, zres, H, out, coef);
+  const int nt = xform_threads(V);
+  if (nt <= 256)
+    k_relin_axpy_intt<256><<<(unsigned)rows, nt, (size_t)V.N * 8, st>>>(V, DG, rlk, zres, H, out, coef);
+  else
+    k_relin_axpy_intt<NTT_MAX_THREADS><<<(unsigned)rows, nt, (size_t)V.N * 8, st>>>(V, DG, rlk, zres, H, out, coef);
 }
 
 void launch_axpy_intt(const DevView& V, const u64* a, const u64* zres, const u64* b, u64* out, u64* coef,
@@ -1825,10 +1839,12 @@ cudaError_t kernels_init(int N) {
   PEPSI_SET_MACQ(4, 1)
   PEPSI_SET_MACQ(4, 2)
 #undef PEPSI_SET_MACQ
-  set((const void*)k_relin_ntt);
+  set((const void*)k_relin_ntt<256>);
+  set((const void*)k_relin_ntt<NTT_MAX_THREADS>);
   set((const void*)k_tensor_intt);
   set((const void*)k_axpy_intt);
-  set((const void*)k_relin_axpy_intt);
+  set((const void*)k_relin_axpy_intt<256>);
+  set((const void*)k_relin_axpy_intt<NTT_MAX_THREADS>);
   set((const void*)k_encrypt);
   set((const void*)k_keygen_sntt);
   set((const void*)k_keygen_rlk);

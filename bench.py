@@ -533,6 +533,8 @@ def run_ours(args):
     # the layer-chunk schedule, autotuned on this request unless --chunk fixes
     # it (words do not depend on it)
     chunk = args.chunk if args.chunk else ctx.autotune(sid, cts_dev)
+    if args.ntt_threads:
+        ctx.set_schedule(ntt_threads=args.ntt_threads)
 
     for _ in range(args.warmup):
         step()
@@ -998,6 +1000,9 @@ def main():
                          "0: 7 for the large case, whose table is only partly resident, else 8")
     ap.add_argument("--chunk", type=int, default=0,
                     help="circuit chunk in layers (default: autotuned on the request)")
+    ap.add_argument("--ntt-threads", type=int, default=0,
+                    help="threads per transform block (default: autotuned with the chunk, or the default for N "
+                         "when --chunk fixes the chunk)")
     ap.add_argument("--rescale", choices=["all", "layer"], default="all",
                     help="all: one rounding of the layers' last products per evaluation (lazy rescaling); "
                          "layer: every product rounded (textbook FV words)")

@@ -462,8 +462,11 @@ int pepsi_engine_create(const pepsi_lane* lanes, int nlanes, uint64_t hbm_budget
  * device, read when the request is admitted; out_ct: [2][r][N] (r =
  * response_primes), host (pinned) or device, written when it completes.
  * Both must stay valid until pepsi_engine_wait reports the request done.
- * *ticket identifies it.  Errors: PEPSI_E_PARAM (lane, mode, a value mode
- * on a set without values, null buffers). */
+ * *ticket identifies it.  With client bins of gamma > 1 items, each of a
+ * request's gamma batches is a request of its own: batch i with mask seed
+ * mask_seed + i has the words of pepsi_eval's response i.  Errors:
+ * PEPSI_E_PARAM (lane, mode, a value mode on a set without values, null
+ * buffers). */
 int pepsi_engine_submit(pepsi_engine* e, int lane, const uint64_t* cts, int mode, uint64_t mask_seed,
                         uint64_t* out_ct, uint64_t* ticket);
 

@@ -99,3 +99,30 @@ def test_gamma_one_is_the_one_slot_request():
     assert np.array_equal(a.eval(sa, ca), b.eval(sb, cb))
     with pytest.raises(pepsi.PepsiError):
         pepsi.Context(N=64, prime_bits=PAPER, h=4, lambda_bar=10, mu=12, gamma=17)
+
+
+def test_engine_serves_each_batch_of_a_gamma_request():
+    """An engine lane over a context with gamma = 2 serves each client batch
+    of a request as its own request: batch i with mask seed s + i gives the
+    words of Context.eval on the whole request (indicator and cardinality)."""
+    import paper_2310_14565_gb300 as pepsi
+    from paper_2310_14565_gb300.workload import make_sets
+
+    torch_cuda()
+    gamma, N = 2, 64
+    sets = make_sets(80, 200, 6, bits=32, seed_items=95, seed_plant=96)
+    ctx = pepsi.Context(N=N, prime_bits=PAPER, h=4, lambda_bar=10, mu=24, hash_key=0x5EED, key_seed=3, gamma=gamma,
+                        rescale_group=pepsi.RESCALE_ALL, response_primes=1)
+    sid = ctx.server_load(sets.server)
+    cts, _ = ctx.query(sets.client, 4)
+    assert cts.shape[0] == gamma
+    eng = pepsi.Engine([(ctx, sid, 4)])
+    for mode, seed in ((0, 0), (1, 11)):
+        want = ctx.eval(sid, cts, mode=mode, mask_seed=seed)
+        tickets = [eng.submit(0, np.ascontiguousarray(cts[i]), mode=mode, mask_seed=seed + i) for i in range(gamma)]
+        eng.run()
+        for i, (t, out) in enumerate(tickets):
+            eng.wait(t)
+            assert np.array_equal(out, want[i]), (mode, i)
+    eng.close()
+

@@ -434,6 +434,8 @@ cudaError_t ensure_copy_stream(pepsi_ctx* c) {
 constexpr int kScratchAccX = 46;
 // scratch ids of the autotuner's response buffers
 constexpr int kScratchTune = 48, kScratchTuneBatch = 49;
+// scratch id of k zero residues (a zero scalar of the fused affine step)
+constexpr int kScratchZeroK = 50;
 
 // Core of pepsi_eval / pepsi_eval_layers.
 int eval_core(pepsi_ctx* c, int set_id, const u64* cts, u32 layer0, u32 nl, int mode, u64 mask_seed, u64* out_ct,
@@ -1796,7 +1798,17 @@ int pepsi_ct_mult(pepsi_ctx* c, const uint64_t* a, const uint64_t* b, size_t n, 
   ntt(c, true, AB, AB, n * 2, c->kb, c->k, kbN, kbN, st);
   ntt(c, true, BB, BB, n * 2, c->kb, c->k, kbN, kbN, st);
   mult_tail(c, AQ, AB, BQ, BB, nullptr, nullptr, false, T3, D, L, st);
-  if (relin_flag) {
+  if (relin_flag && c->relin_fused) {
+    // the key-switching sum on the load of the inverse NTT (plus 0 * D, the
+    // affine step of the circuit with a zero scalar): the same words
+    u64* DG = (u64*)scratch(c, kScratchDG, (size_t)L * (k + 2) * kN * 8, &e);
+    u64* zero = (u64*)scratch(c, kScratchZeroK, k * 8, &e);
+    if (!DG || !zero) return cuda_status(e);
+    CKS(cudaMemsetAsync(zero, 0, k * 8, st));
+    Prof p(c, PC_RELIN, st, 2);
+    launch_relin_digits(c->V, D, DG, L, st);
+    launch_relin_axpy_intt(c->V, DG, c->d_rlk, zero, D, R, out, L, st);
+  } else if (relin_flag) {
     relin(c, D, R, L, st);
     ntt(c, false, R, out, n * 2, c->k, 0, kN, kN, st);
   } else {

@@ -29,6 +29,23 @@ inline int ntt_threads(int N) {
 // Threads of the hot-path transform kernels: the schedule's choice
 // (DevView::nt, picked by the autotuner), else the default above.
 inline int xform_threads(const DevView& V) { return V.nt > 0 ? V.nt : ntt_threads(V.N); }
+// SMs of the current device (cached per device).
+inline int sm_count() {
+  static int cached[64] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 0;
+  if (!cached[dev]) cudaDeviceGetAttribute(&cached[dev], cudaDevAttrMultiProcessorCount, dev);
+  return cached[dev];
+}
+// Threads of a transform launch of `rows` blocks: a launch that gives each
+// block an SM of its own (the output stage, the lazy rounding) runs its
+// rows with up to the largest blocks instead, which shortens each
+// transform's chain of phases.
+inline int xform_threads(const DevView& V, size_t rows) {
+  const int base = xform_threads(V);
+  const int wide = std::min(NTT_MAX_THREADS, std::max(32, V.N / 8));
+  return rows <= (size_t)sm_count() && wide > base ? wide : base;
+}
 // The relinearisation transforms come in two register budgets: MT = 256 for
 // blocks of at most 256 threads, three per SM (80 registers a thread; at N =
 // 8192 with 256-thread blocks the relinearisation took 1.98 ms against
@@ -1448,11 +1465,11 @@ void launch_ntt(const DevView& V, bool fwd, const u64* src, u64* dst, size_t out
   if (!rows) return;
   const size_t smem = (size_t)V.N * sizeof(u64);
   if (fwd && split_out)
-    k_ntt<true, true><<<(unsigned)rows, xform_threads(V), smem, st>>>(V, src, dst, np, p0, src_os, dst_os, sums);
+    k_ntt<true, true><<<(unsigned)rows, xform_threads(V, rows), smem, st>>>(V, src, dst, np, p0, src_os, dst_os, sums);
   else if (fwd)
-    k_ntt<true><<<(unsigned)rows, xform_threads(V), smem, st>>>(V, src, dst, np, p0, src_os, dst_os, nullptr);
+    k_ntt<true><<<(unsigned)rows, xform_threads(V, rows), smem, st>>>(V, src, dst, np, p0, src_os, dst_os, nullptr);
   else
-    k_ntt<false><<<(unsigned)rows, xform_threads(V), smem, st>>>(V, src, dst, np, p0, src_os, dst_os, nullptr);
+    k_ntt<false><<<(unsigned)rows, xform_threads(V, rows), smem, st>>>(V, src, dst, np, p0, src_os, dst_os, nullptr);
 }
 
 void launch_cw_unrank(const u64* T, size_t count, const u64* binom, int ell, int h, uint16_t* pos, cudaStream_t st) {
@@ -1661,7 +1678,7 @@ void launch_tensor_intt(const DevView& V, const u64* AQ, const u64* AB, const u6
                         const u64* cstQ, const u64* side, u64* T3, int L, bool square, cudaStream_t st) {
   const size_t rows = (size_t)L * 3 * (V.k + V.kb);
   if (!rows) return;
-  k_tensor_intt<<<(unsigned)rows, xform_threads(V), (size_t)V.N * 8, st>>>(V, AQ, AB, BQ, BB, cstQ, side, T3,
+  k_tensor_intt<<<(unsigned)rows, xform_threads(V, rows), (size_t)V.N * 8, st>>>(V, AQ, AB, BQ, BB, cstQ, side, T3,
                                                                           square ? 1 : 0);
 }
 
@@ -1718,7 +1735,7 @@ void launch_scale_round(const DevView& V, const u64* T3, u64* D, int L, cudaStre
 void launch_relin_digits(const DevView& V, const u64* D, u64* DG, int L, cudaStream_t st) {
   if (L <= 0) return;
   const size_t rows = (size_t)L * (V.k + 2) * V.k;
-  const int nt = xform_threads(V);
+  const int nt = xform_threads(V, rows);
   if (nt <= 256)
     k_relin_ntt<256><<<(unsigned)rows, nt, (size_t)V.N * 8, st>>>(V, D, DG);
   else
@@ -1735,7 +1752,7 @@ void launch_relin_axpy_intt(const DevView& V, const u64* DG, const u64* rlk, con
                             u64* coef, int L, cudaStream_t st) {
   const size_t rows = (size_t)L * 2 * V.k;
   if (!rows) return;
-  const int nt = xform_threads(V);
+  const int nt = xform_threads(V, rows);
   if (nt <= 256)
     k_relin_axpy_intt<256><<<(unsigned)rows, nt, (size_t)V.N * 8, st>>>(V, DG, rlk, zres, H, out, coef);
   else
@@ -1746,7 +1763,7 @@ void launch_axpy_intt(const DevView& V, const u64* a, const u64* zres, const u64
                       size_t groups, cudaStream_t st) {
   const size_t rows = groups * V.k;
   if (!rows) return;
-  k_axpy_intt<<<(unsigned)rows, xform_threads(V), (size_t)V.N * 8, st>>>(V, a, zres, b, out, coef);
+  k_axpy_intt<<<(unsigned)rows, xform_threads(V, rows), (size_t)V.N * 8, st>>>(V, a, zres, b, out, coef);
 }
 
 void launch_axpy(const DevView& V, const u64* a, const u64* zres, const u64* b, u64* out, size_t groups,

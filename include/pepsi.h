@@ -119,6 +119,16 @@ typedef struct {
                               table's batch i is slot i of every bin: a request holds B * gamma
                               * ell ciphertexts [B][gamma][ell][2][k][N] and Algorithm 2
                               returns one indicator ciphertext per batch, [B][gamma][2][r][N] */
+  uint32_t client_cuckoo;  /* placement of pepsi_query's cuckoo hashing (no counterpart in the
+                              paper, which gives no algorithm for it): 0 = on the host, items
+                              inserted in order with eviction chains (the placement the oracle
+                              computes); 1 = on the device, in parallel rounds: every unplaced
+                              item claims its current candidate bin, the smallest claiming item
+                              takes a free slot of the bin or evicts the occupant of slot
+                              (evictions mod gamma), which moves to its next candidate bin, and
+                              the other claimants move to theirs; at most 1000 rounds.  Both
+                              are deterministic valid placements (every item in one of its three
+                              candidate bins, at most gamma per bin); they differ in which */
 } pepsi_params;
 
 /* Derived values of a context (for callers and tests). */

@@ -42,6 +42,7 @@ class Params(C.Structure):
         ("mu", C.c_uint32), ("hash_key", C.c_uint64), ("resident_bytes", C.c_uint64),
         ("rescale_group", C.c_uint32), ("server_values", C.c_uint32), ("response_primes", C.c_uint32),
         ("bins", C.c_uint32), ("plaintext_bytes", C.c_uint32), ("gamma", C.c_uint32),
+        ("client_cuckoo", C.c_uint32),
     ]
 
 
@@ -234,7 +235,7 @@ class Context:
 
     def __init__(self, N, t=65537, prime_bits=(36, 36, 37), h=2, ell=0, lambda_bar=16, mu=0, hash_key=0,
                  key_seed=3, resident_bytes=0, rescale_group=0, server_values=0, response_primes=0, bins=0, plaintext_bytes=0,
-                 gamma=0):
+                 gamma=0, client_cuckoo=0):
         p = Params()
         p.N, p.t, p.k = N, t, len(prime_bits)
         for i, b in enumerate(prime_bits):
@@ -244,6 +245,7 @@ class Context:
         p.server_values, p.response_primes, p.bins = server_values, response_primes, bins
         p.plaintext_bytes = plaintext_bytes
         p.gamma = gamma
+        p.client_cuckoo = client_cuckoo
         self._h = C.c_void_p()
         _check(lib().pepsi_setup(C.byref(p), key_seed, C.byref(self._h)), "pepsi_setup")
         info = Info()

@@ -76,6 +76,52 @@ __global__ void __launch_bounds__(NTT_MAX_THREADS, 1) k_ntt(DevView V, const u64
   }
 }
 
+// ------------------------------------------------ parallel cuckoo rounds
+// One round of the client's cuckoo placement (pepsi_params.client_cuckoo =
+// 1).  state: 0 placed, 1 unplaced, 2 evicted in this round; choice: the
+// item's current candidate (0..2) among bins3[3u..3u+2].  claim[b] holds the
+// smallest unplaced item claiming bin b (UINT32_MAX for none).
+__global__ void k_ck_claim(const u32* __restrict__ bins3, const uint8_t* __restrict__ state,
+                           const uint8_t* __restrict__ choice, u32 m, u32* claim) {
+  const u32 u = blockIdx.x * blockDim.x + threadIdx.x;
+  if (u >= m || state[u] != 1) return;
+  atomicMin(&claim[bins3[3 * (size_t)u + choice[u]]], u);
+}
+// Per bin: its winning claimant takes the first free slot, or the slot
+// (evictions mod gamma) whose occupant is evicted to its next candidate.
+__global__ void k_ck_resolve(u32 nbins, u32 gamma, u32* claim, int32_t* slot_item, u32* load, u32* evictions,
+                             uint8_t* state, uint8_t* choice) {
+  const u32 b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= nbins) return;
+  const u32 w = claim[b];
+  if (w == 0xFFFFFFFFu) return;
+  claim[b] = 0xFFFFFFFFu;
+  size_t c;
+  if (load[b] < gamma) {
+    c = (size_t)b * gamma + load[b]++;
+  } else {
+    c = (size_t)b * gamma + evictions[b]++ % gamma;
+    const int32_t v = slot_item[c];
+    state[v] = 2;
+    choice[v] = (uint8_t)((choice[v] + 1) % 3);
+  }
+  slot_item[c] = (int32_t)w;
+  state[w] = 0;
+}
+// Claimants that lost move to their next candidate; the evicted become
+// unplaced; *unplaced counts both.
+__global__ void k_ck_advance(u32 m, uint8_t* state, uint8_t* choice, u32* unplaced) {
+  const u32 u = blockIdx.x * blockDim.x + threadIdx.x;
+  if (u >= m) return;
+  if (state[u] == 1) {
+    choice[u] = (uint8_t)((choice[u] + 1) % 3);
+    atomicAdd(unplaced, 1u);
+  } else if (state[u] == 2) {
+    state[u] = 1;
+    atomicAdd(unplaced, 1u);
+  }
+}
+
 // ---------------------------------------------------------- CW unranking
 // v = sum_{r=1..h} C(c_r, r) with c_1 < ... < c_h (combinatorial number
 // system); binom[c*(h+1)+r] = C(c, r) for c <= ell.
@@ -1470,6 +1516,14 @@ void launch_ntt(const DevView& V, bool fwd, const u64* src, u64* dst, size_t out
     k_ntt<true><<<(unsigned)rows, xform_threads(V, rows), smem, st>>>(V, src, dst, np, p0, src_os, dst_os, nullptr);
   else
     k_ntt<false><<<(unsigned)rows, xform_threads(V, rows), smem, st>>>(V, src, dst, np, p0, src_os, dst_os, nullptr);
+}
+
+void launch_cuckoo_round(const u32* bins3, u32 m, u32 nbins, u32 gamma, u32* claim, int32_t* slot_item, u32* load,
+                         u32* evictions, uint8_t* state, uint8_t* choice, u32* unplaced, cudaStream_t st) {
+  if (!m) return;
+  k_ck_claim<<<grid_for(m, 256), 256, 0, st>>>(bins3, state, choice, m, claim);
+  k_ck_resolve<<<grid_for(nbins, 256), 256, 0, st>>>(nbins, gamma, claim, slot_item, load, evictions, state, choice);
+  k_ck_advance<<<grid_for(m, 256), 256, 0, st>>>(m, state, choice, unplaced);
 }
 
 void launch_cw_unrank(const u64* T, size_t count, const u64* binom, int ell, int h, uint16_t* pos, cudaStream_t st) {

@@ -23,6 +23,15 @@ inline const u32* request_sums(const u64* C, int ell, size_t kN) {
   return reinterpret_cast<const u32*>(C + (size_t)ell * 2 * kN);
 }
 
+// One round of the parallel cuckoo placement of m items into nbins bins of gamma
+// slots (see pepsi_params.client_cuckoo): bins3[m][3] candidate bins; state[m]
+// (1 = unplaced at the start), choice[m] (current candidate), claim[nbins]
+// (all UINT32_MAX between rounds), slot_item[nbins][gamma] (-1 = free),
+// load[nbins], evictions[nbins]; *unplaced (zeroed by the caller) receives the
+// items left unplaced after the round.
+void launch_cuckoo_round(const u32* bins3, u32 m, u32 nbins, u32 gamma, u32* claim, int32_t* slot_item, u32* load,
+                         u32* evictions, uint8_t* state, uint8_t* choice, u32* unplaced, cudaStream_t st);
+
 // CW-Encode of table entries (colex rank -> positions), pos[count][h], dummy -> PEPSI_CW_NONE.
 void launch_cw_unrank(const u64* T, size_t count, const u64* binom, int ell, int h, uint16_t* pos, cudaStream_t st);
 

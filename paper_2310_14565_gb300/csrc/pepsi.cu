@@ -980,7 +980,7 @@ int pepsi_setup(const pepsi_params* params, uint64_t key_seed, pepsi_ctx** out) 
       return PEPSI_E_PARAM;
     }
   }
-  if (params->response_primes > (u32)c->k || params->gamma > 16) {
+  if (params->response_primes > (u32)c->k || params->gamma > 16 || params->client_cuckoo > 1) {
     delete c;
     return PEPSI_E_PARAM;
   }
@@ -1425,6 +1425,61 @@ int pepsi_server_plaintexts(pepsi_ctx* c, int set_id, uint32_t layer0, uint32_t 
   return PEPSI_OK;
 }
 
+namespace {
+// scratch id of the device cuckoo placement's state
+constexpr int kScratchCuckoo = 51;
+
+// The client's cuckoo placement in parallel rounds on the device (see
+// pepsi_params.client_cuckoo): table [bins][gamma] of x_L values (dummies
+// PEPSI_DUMMY) and where[u] = bin * gamma + slot, as hostmath::cuckoo.
+int device_cuckoo(pepsi_ctx* c, const hostmath::Hasher& H, const u64* items, size_t m, std::vector<u64>& table,
+                  std::vector<int32_t>& where, cudaStream_t st) {
+  const u32 nbins = 1u << c->logb, g = c->gamma;
+  const size_t cells = (size_t)nbins * g;
+  if (m > cells || m > 0x7FFFFFFFu) return PEPSI_E_CUCKOO_FAIL;
+  std::vector<u64> xl(m);
+  std::vector<u32> bins3(3 * m);
+  for (size_t u = 0; u < m; ++u) H(items[u], &xl[u], &bins3[3 * u]);
+  // one buffer: bins3 | claim | slot_item | load | evictions | unplaced | state | choice
+  const size_t o_claim = 3 * m, o_slot = o_claim + nbins, o_load = o_slot + cells, o_ev = o_load + nbins,
+               o_cnt = o_ev + nbins, words = o_cnt + 1;
+  cudaError_t e = cudaSuccess;
+  u32* d = (u32*)scratch(c, kScratchCuckoo, words * 4 + 2 * m + 16, &e);
+  if (!d) return cuda_status(e);
+  uint8_t* state = reinterpret_cast<uint8_t*>(d + words);
+  uint8_t* choice = state + m;
+  CKS(cudaMemcpyAsync(d, bins3.data(), 3 * m * 4, cudaMemcpyHostToDevice, st));
+  CKS(cudaMemsetAsync(d + o_claim, 0xFF, (nbins + cells) * 4, st));  // no claims, free slots (-1)
+  CKS(cudaMemsetAsync(d + o_load, 0, 2 * (size_t)nbins * 4, st));
+  CKS(cudaMemsetAsync(state, 1, m, st));
+  CKS(cudaMemsetAsync(choice, 0, m, st));
+  u32 left = (u32)m;
+  // rounds in groups of four between reads of the count (a round with
+  // nothing unplaced changes nothing), at most 1000
+  for (int r = 0; r < 1000 && left; r += 4) {
+    for (int i = 0; i < 4; ++i) {
+      CKS(cudaMemsetAsync(d + o_cnt, 0, 4, st));
+      launch_cuckoo_round(d, (u32)m, nbins, g, d + o_claim, reinterpret_cast<int32_t*>(d + o_slot), d + o_load,
+                          d + o_ev, state, choice, d + o_cnt, st);
+    }
+    CKS(cudaMemcpyAsync(&left, d + o_cnt, 4, cudaMemcpyDeviceToHost, st));
+    CKS(cudaStreamSynchronize(st));
+  }
+  if (left) return PEPSI_E_CUCKOO_FAIL;
+  std::vector<int32_t> slot(cells);
+  CKS(cudaMemcpyAsync(slot.data(), d + o_slot, cells * 4, cudaMemcpyDeviceToHost, st));
+  CKS(cudaStreamSynchronize(st));
+  table.assign(cells, PEPSI_DUMMY);
+  where.assign(m, -1);
+  for (size_t i = 0; i < cells; ++i)
+    if (slot[i] >= 0) {
+      table[i] = xl[slot[i]];
+      where[slot[i]] = (int32_t)i;
+    }
+  return PEPSI_OK;
+}
+}  // namespace
+
 int pepsi_query(pepsi_ctx* c, const uint64_t* items, size_t m, uint64_t enc_seed, uint64_t* cts,
                 int32_t* bin_of_item, void* stream) {
   if (!c || (!items && m) || !cts) return PEPSI_E_PARAM;
@@ -1432,7 +1487,8 @@ int pepsi_query(pepsi_ctx* c, const uint64_t* items, size_t m, uint64_t enc_seed
   hostmath::Hasher H(c->prm.hash_key, c->prm.lambda_bar, c->logb);
   std::vector<u64> table;  // [bins][gamma]
   std::vector<int32_t> where;
-  int rc = hostmath::cuckoo(H, items, m, c->gamma, table, where);
+  int rc = c->prm.client_cuckoo ? device_cuckoo(c, H, items, m, table, where, st)
+                                 : hostmath::cuckoo(H, items, m, c->gamma, table, where);
   if (rc) return rc;
   if (bin_of_item) memcpy(bin_of_item, where.data(), m * sizeof(int32_t));
   cudaError_t e = cudaSuccess;

@@ -45,7 +45,11 @@ __device__ __forceinline__ void tw_split(const ulonglong2& t, u32& w, u32& ws) {
 // Forward stages [s0, s0 + RR) on one group of 2^RR elements held in
 // registers, element i of the group at base + i * 2^(logN - s0 - RR).
 // Twiddles come as (w, Shoup companion) pairs, one 16-byte load each.
-template <int RR>
+// GROW: the butterfly's sum input is not reduced below 2q first, so values
+// grow by 2q a stage (Shoup's product takes any 64-bit input and returns
+// [0, 2q)): from [0, 4q) they stay below (4 + 2 log2 N) q <= 32 q, which fits
+// 64 bits for q < 2^59; the transform's end reduces them (fwd_final_grow).
+template <int RR, bool GROW = false>
 __device__ __forceinline__ void fwd_group(u64 (&x)[1 << RR], int base, int logN, int s0, u64 q,
                                           const ulonglong2* __restrict__ tw) {
   constexpr int E = 1 << RR;
@@ -66,7 +70,7 @@ __device__ __forceinline__ void fwd_group(u64 (&x)[1 << RR], int base, int logN,
       if ((i & half) == 0) {
         const u64 W = Wt[i >> (RR - ss)].x, Ws = Wt[i >> (RR - ss)].y;
         u64 U = x[i];
-        U = U >= q2 ? U - q2 : U;
+        if constexpr (!GROW) U = U >= q2 ? U - q2 : U;
         const u64 T = shoup_lazy(x[i + half], W, Ws, q);
         x[i] = U + T;
         x[i + half] = U + q2 - T;
@@ -82,6 +86,16 @@ __device__ __forceinline__ void fwd_final(u64 (&x)[E], u64 q) {
   for (int i = 0; i < E; ++i) {
     u64 v = x[i];
     v = v >= q2 ? v - q2 : v;
+    x[i] = v >= q ? v - q : v;
+  }
+}
+// [0, 2^64) -> [0, q): one-word Barrett (floor(x m64 / 2^64) is short of
+// floor(x / q) by at most 1), then one conditional subtraction.
+template <int E>
+__device__ __forceinline__ void fwd_final_grow(u64 (&x)[E], u64 q, u64 m64) {
+#pragma unroll
+  for (int i = 0; i < E; ++i) {
+    const u64 v = x[i] - __umul64hi(x[i], m64) * q;
     x[i] = v >= q ? v - q : v;
   }
 }
@@ -166,7 +180,7 @@ __device__ __forceinline__ void inv_group_last(T (&x)[8], int base, int logN, T 
   }
 }
 
-template <int RR>
+template <int RR, bool GROW = false>
 __device__ __forceinline__ void fwd_phase(u64* a, int N, int logN, int s0, u64 q, const ulonglong2* __restrict__ tw,
                                           bool last) {
   constexpr int E = 1 << RR;
@@ -177,7 +191,7 @@ __device__ __forceinline__ void fwd_phase(u64* a, int N, int logN, int s0, u64 q
     u64 x[E];
 #pragma unroll
     for (int i = 0; i < E; ++i) x[i] = a[nsw(base + (i << slog))];
-    fwd_group<RR>(x, base, logN, s0, q, tw);
+    fwd_group<RR, GROW>(x, base, logN, s0, q, tw);
     if (last) fwd_final<E>(x, q);
 #pragma unroll
     for (int i = 0; i < E; ++i) a[nsw(base + (i << slog))] = x[i];
@@ -404,22 +418,25 @@ __device__ __forceinline__ void store_run(const u64 (&x)[E], const Store& st, in
 // reduced.  Every read through ld happens before the first barrier and
 // every st after the last, so input and output rows may alias.  Every
 // thread of the block must call these.
-template <int LOGN, class Load, class Store>
-__device__ __forceinline__ void ntt_fwd_fused(u64* a, const Load& ld, const Store& st, u64 q,
+// GROW (q < 2^59): butterflies without the reduction of their sum input,
+// one Barrett reduction (m64 = floor(2^64 / q)) at the store; the same
+// residues.
+template <int LOGN, bool GROW, class Load, class Store>
+__device__ __forceinline__ void ntt_fwd_fused(u64* a, const Load& ld, const Store& st, u64 q, u64 m64,
                                               const ulonglong2* __restrict__ tw) {
   constexpr int N = 1 << LOGN, R = (LOGN - 4) % 3 + 1, M = (LOGN - 3 - R) / 3, S8 = LOGN - 3;
   for (int g = threadIdx.x; g < (N >> 3); g += blockDim.x) {  // stages 0-2
     u64 x[8];
 #pragma unroll
     for (int i = 0; i < 8; ++i) x[i] = ld(g + (i << S8));
-    nttd::fwd_group<3>(x, g, LOGN, 0, q, tw);
+    nttd::fwd_group<3, GROW>(x, g, LOGN, 0, q, tw);
 #pragma unroll
     for (int i = 0; i < 8; ++i) a[nsw(g + (i << S8))] = x[i];
   }
   __syncthreads();
 #pragma unroll
   for (int m = 0; m < M; ++m) {
-    nttd::fwd_phase<3>(a, N, LOGN, 3 + 3 * m, q, tw, false);
+    nttd::fwd_phase<3, GROW>(a, N, LOGN, 3 + 3 * m, q, tw, false);
     __syncthreads();
   }
   for (int g = threadIdx.x; g < (N >> R); g += blockDim.x) {  // stages LOGN-R .. LOGN-1
@@ -427,8 +444,11 @@ __device__ __forceinline__ void ntt_fwd_fused(u64* a, const Load& ld, const Stor
     u64 x[1 << R];
 #pragma unroll
     for (int i = 0; i < (1 << R); ++i) x[i] = a[nsw(base + i)];
-    nttd::fwd_group<R>(x, base, LOGN, LOGN - R, q, tw);
-    nttd::fwd_final<1 << R>(x, q);
+    nttd::fwd_group<R, GROW>(x, base, LOGN, LOGN - R, q, tw);
+    if constexpr (GROW)
+      nttd::fwd_final_grow<1 << R>(x, q, m64);
+    else
+      nttd::fwd_final<1 << R>(x, q);
     store_run<1 << R>(x, st, base);
   }
 }
@@ -466,11 +486,17 @@ __device__ __forceinline__ void ntt_inv_fused(T* a, const Load& ld, const Store&
 template <class Load, class Store>
 __device__ __forceinline__ void ntt_fwd_gg(u64* a, const Load& ld, const Store& st, const DevView& V, int pi) {
   const ulonglong2* tw = V.twp + (size_t)pi * V.N;
-  const u64 q = V.pr[pi].q;
-  switch (V.logN) {
-    case 12: ntt_fwd_fused<12>(a, ld, st, q, tw); return;
-    case 13: ntt_fwd_fused<13>(a, ld, st, q, tw); return;
-    case 14: ntt_fwd_fused<14>(a, ld, st, q, tw); return;
+  const DevPrime P = V.pr[pi];
+  const u64 q = P.q;
+  // values reach (4 + 2 log2 N) q <= 32 q without per-stage reduction
+  const bool grow = q < (1ull << 59);
+  switch (V.logN * 2 + (grow ? 1 : 0)) {
+    case 12 * 2: ntt_fwd_fused<12, false>(a, ld, st, q, P.m64, tw); return;
+    case 12 * 2 + 1: ntt_fwd_fused<12, true>(a, ld, st, q, P.m64, tw); return;
+    case 13 * 2: ntt_fwd_fused<13, false>(a, ld, st, q, P.m64, tw); return;
+    case 13 * 2 + 1: ntt_fwd_fused<13, true>(a, ld, st, q, P.m64, tw); return;
+    case 14 * 2: ntt_fwd_fused<14, false>(a, ld, st, q, P.m64, tw); return;
+    case 14 * 2 + 1: ntt_fwd_fused<14, true>(a, ld, st, q, P.m64, tw); return;
     default: break;
   }
   for (int x = threadIdx.x; x < V.N; x += blockDim.x) a[nsw(x)] = ld(x);

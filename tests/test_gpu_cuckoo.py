@@ -12,50 +12,13 @@ import math
 import numpy as np
 import pytest
 
+from cuckoo_rounds import rounds_reference
 from gpu_helpers import T, torch_cuda
 
 pytestmark = pytest.mark.gpu
 
 PAPER = [55, 55, 54, 54]
 DUMMY = (1 << 64) - 1
-
-
-def rounds_reference(bins3, gamma, nbins, max_rounds=1000):
-    m = len(bins3)
-    state, choice = [1] * m, [0] * m
-    slot = [-1] * (nbins * gamma)
-    load, evictions = [0] * nbins, [0] * nbins
-    for _ in range(max_rounds):
-        claim = {}
-        for u in range(m):
-            if state[u] == 1:
-                b = bins3[u][choice[u]]
-                claim[b] = min(claim.get(b, m), u)
-        for b, w in claim.items():
-            if load[b] < gamma:
-                c = b * gamma + load[b]
-                load[b] += 1
-            else:
-                c = b * gamma + evictions[b] % gamma
-                evictions[b] += 1
-                v = slot[c]
-                state[v], choice[v] = 2, (choice[v] + 1) % 3
-            slot[c], state[w] = w, 0
-        left = 0
-        for u in range(m):
-            if state[u] == 1:
-                choice[u] = (choice[u] + 1) % 3
-                left += 1
-            elif state[u] == 2:
-                state[u] = 1
-                left += 1
-        if not left:
-            where = [-1] * m
-            for c, u in enumerate(slot):
-                if u >= 0:
-                    where[u] = c
-            return where
-    return None
 
 
 @pytest.mark.parametrize("gamma,blocks", [(1, 1), (2, 1), (1, 2)])

@@ -1002,13 +1002,16 @@ int pepsi_setup(const pepsi_params* params, uint64_t key_seed, pepsi_ctx** out) 
     const u32 g = params->rescale_group;
     c->rescale_cap = g <= 1 ? 1 : g != PEPSI_RESCALE_ALL ? g : params->mu ? params->mu : 65536u;
   }
-  // auxiliary base B: 61-bit primes with log2 B >= log2(t N Q G) + 3, G the
+  // auxiliary base B: primes with log2 B >= log2(t N Q G) + 3, G the
   // longest run of layers whose exact products are summed before rounding
   // (and, for the value modes, N t / 2 times more: the product with a value
-  // plaintext of centred coefficients)
+  // plaintext of centred coefficients).  59-bit primes where as few of them
+  // cover the bound as of 61-bit ones (their forward transforms then skip the
+  // per-stage reduction: 32 q < 2^64), else 61-bit primes.
   c->value_margin = params->server_values != 0 && c->rescale_cap > 1;
   const double needB = std::log2((double)c->t) + c->logN + lq + std::ceil(std::log2((double)c->rescale_cap)) + 3.0 +
                        (c->value_margin ? std::ceil(c->logN + std::log2((double)c->t) - 1.0) : 0.0);
+  const int bbits = std::ceil(needB / 58.9) <= std::ceil(needB / 60.9) ? 59 : 61;
   double haveB = 0;
   std::vector<u64> taken = c->Q;
   while (haveB < needB) {
@@ -1016,7 +1019,7 @@ int pepsi_setup(const pepsi_params* params, uint64_t key_seed, pepsi_ctx** out) 
       delete c;
       return PEPSI_E_PARAM;
     }
-    u64 p = hostmath::find_prime(61, c->N, taken);
+    u64 p = hostmath::find_prime(bbits, c->N, taken);
     taken.push_back(p);
     c->B.push_back(p);
     haveB += std::log2((double)p);

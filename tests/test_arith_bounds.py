@@ -1,6 +1,6 @@
 """The bounds the device arithmetic relies on, checked with Python integers
 for every prime size the library accepts (ciphertext primes of 20..60 bits,
-61-bit auxiliary primes, t = 65537):
+59- and 61-bit auxiliary primes, t = 65537):
 
 - one-constant Barrett for a b mod q with a, b < 2^n: the quotient
   floor(floor(ab / 2^(n-1)) mu / 2^64), mu = floor(2^(n+63) / q), is short
@@ -12,7 +12,12 @@ for every prime size the library accepts (ciphertext primes of 20..60 bits,
 - the multiply-accumulate's Karatsuba partial sums over one fold interval
   (2^(63 - max(bits + 1, 2s)) terms) plus the residue a fold leaves: S0,
   S2 and the middle sum S1 each stay below 2^64, so S1 = SM - S0 - S2 holds
-  mod 2^64 even where SM wraps."""
+  mod 2^64 even where SM wraps;
+- the forward transforms of primes below 2^59, whose butterflies do not
+  reduce their sum input: below (4 + 2 log2 N) q < 2^64 at every stage, and
+  the residues of the reducing form after one Barrett reduction;
+- Shoup's product in 32-bit words for the plaintext modulus, with the
+  companion taken from the upper half of the 64-bit one."""
 import random
 
 import pytest
@@ -121,3 +126,97 @@ def test_karatsuba_sums_fit_over_a_fold(bits):
         SM = (SM + (cl + ch) * (xl + xh)) & M64
         S1 += cl * xh + ch * xl
     assert (SM - S0 - S2) & M64 == S1
+
+
+def ntt_prime_below(bits, logn):
+    """The largest prime below 2^bits that is 1 mod 2N (N = 2^logn)."""
+    step = 2 << logn
+    q = ((1 << bits) - 1) // step * step + 1
+    while not is_prime(q):
+        q -= step
+    return q
+
+
+def brev(i, bits):
+    return int(format(i, "0%db" % bits)[::-1], 2)
+
+
+def forward_lazy(x, q, logn, grow):
+    """Negacyclic Cooley-Tukey transform of x (values in [0, 4q)), natural
+    order in, bit-reversed order out, in the stage and twiddle order of the
+    library's fused forward transforms: stage s pairs elements N/2^(s+1)
+    apart, block i of the stage takes the twiddle psi^brev(2^s + i).  Each
+    butterfly is (u + T, u + 2q - T), T = w x mod q lazily by Shoup in
+    [0, 2q); without grow, u is first reduced below 2q.  Returns the reduced
+    output and the largest value any stage held."""
+    n = 1 << logn
+    n2 = 2 * n
+    psi = next(p for p in (pow(g, (q - 1) // n2, q) for g in range(2, 200)) if pow(p, n, q) == q - 1)
+    tw = [pow(psi, brev(i, logn), q) for i in range(n)]
+    x = list(x)
+    peak = max(x)
+    for s in range(logn):
+        m, t = 1 << s, n >> (s + 1)
+        for i in range(m):
+            w = tw[m + i]
+            ws = (w << 64) // q
+            for j in range(2 * i * t, 2 * i * t + t):
+                u = x[j]
+                if not grow and u >= 2 * q:
+                    u -= 2 * q
+                v = shoup_lazy(x[j + t], w, ws, q)
+                assert v < 2 * q
+                x[j], x[j + t] = u + v, u + 2 * q - v
+        peak = max(peak, max(x))
+    out = []
+    m64 = (1 << 64) // q
+    for v in x:
+        assert v < (1 << 64)
+        if grow:  # one-word Barrett: [0, 2^64) -> [0, 2q) -> [0, q)
+            v -= ((v * m64) >> 64) * q
+            assert v < 2 * q
+        elif v >= 2 * q:
+            v -= 2 * q
+        out.append(v - q if v >= q else v)
+    return out, peak, psi
+
+
+@pytest.mark.parametrize("logn", [12, 13, 14])
+def test_growing_forward_transform_fits_64_bits_below_2_59(logn):
+    """The forward transforms of primes below 2^59 skip the reduction of the
+    butterfly's sum input: each stage adds less than 2q, so from inputs in
+    [0, 4q) the values stay below (4 + 2 log2 N) q <= 32 q < 2^64, and one
+    Barrett reduction at the store gives the residues of the reducing form.
+    Checked at the largest NTT-friendly prime below 2^59 on the largest
+    inputs the transform accepts and on random ones; the outputs are the
+    evaluations at psi^(2 brev(k) + 1)."""
+    q = ntt_prime_below(59, logn)
+    assert q < (1 << 59) and (4 + 2 * logn) * q < (1 << 64)
+    n = 1 << logn
+    rng = random.Random(logn)
+    for x in ([4 * q - 1] * n, [rng.randrange(4 * q) for _ in range(n)]):
+        grow, peak, psi = forward_lazy(x, q, logn, True)
+        plain, peak_plain, _ = forward_lazy(x, q, logn, False)
+        assert peak < (4 + 2 * logn) * q
+        assert peak_plain < 4 * q
+        assert grow == plain
+        for k in (0, 1, n // 2 + 3, n - 1):
+            z = pow(psi, 2 * brev(k, logn) + 1, q)
+            assert grow[k] == sum(v * pow(z, i, q) for i, v in enumerate(x)) % q
+
+
+@pytest.mark.parametrize("q", [65537, 786433, ntt_prime_below(30, 14)])
+def test_32_bit_shoup_from_the_upper_half_of_the_64_bit_companion(q):
+    """The plaintext-modulus transforms (q < 2^30) run in 32-bit words with
+    the companion floor(w 2^32 / q) taken as the upper half of the 64-bit
+    floor(w 2^64 / q): the two are equal, and x w - floor(x ws / 2^32) q mod
+    2^32 lies in [0, 2q) and is x w mod q for every x < 4q (the inverse
+    butterfly's difference input; 4q < 2^32)."""
+    rng = random.Random(q)
+    M32 = (1 << 32) - 1
+    for w in [1, q - 1, q // 2] + [rng.randrange(q) for _ in range(200)]:
+        ws = ((w << 64) // q) >> 32
+        assert ws == (w << 32) // q
+        for x in [0, 4 * q - 1, 2 * q] + [rng.randrange(4 * q) for _ in range(50)]:
+            r = (x * w - ((x * ws) >> 32) * q) & M32
+            assert r < 2 * q and r % q == x * w % q

@@ -1,6 +1,7 @@
 """The host side of bench.py's multi-rank path on CPU (gloo, two ranks):
 the replicas time their steps between barriers and report the slowest
-(max over ranks); without a process group the value is returned as is."""
+(max over ranks); without a process group the value is returned as is; the
+oracle arm (--impl reference) runs on rank 0 alone."""
 import os
 import socket
 import sys
@@ -53,3 +54,15 @@ def test_max_over_ranks_without_a_group():
     import bench
 
     assert bench.max_over_ranks(12.5) == 12.5
+
+
+def test_reference_arm_runs_on_rank_zero_only():
+    """Under torchrun the oracle arm runs on rank 0 alone: another rank exits
+    0 at once, without output and without a process group."""
+    import subprocess
+
+    env = dict(os.environ, RANK="1", LOCAL_RANK="1", WORLD_SIZE="2", MASTER_ADDR="127.0.0.1", MASTER_PORT="1")
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--gpus", "2",
+                        "--steps", "1", "--warmup", "3"], env=env, capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0, r.stderr
+    assert r.stdout.strip() == ""
